@@ -1,0 +1,163 @@
+"""FP64 CPU oracle (plain C, OpenMP over targets) for the extrapolated-regularization method.
+
+TEST INFRASTRUCTURE ONLY: the tests, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
+``bench.py`` may load this package; the GPU library never does, and this package never loads
+the GPU library.  The C source is ``ers_oracle.c``; every function there cites the passage of
+Siebor & Tlupova it follows.
+
+Functions:
+  quadrature(shape, h)                      Sec. 2.2 lattice-crossing nodes, normals, weights
+  closest_point(shape, y)                   x0, n0, b with y = x0 + b n0 (Sec. 2)
+  evaluate(nodes, f, q, y, cp, f0, q0, ...) SL and DL values, direct or localized (Secs. 2, 3.3)
+  sigma(t), I0(lam), I2(lam), extrapolate   building blocks (Eqs. (s1)-(s3), (I0), (I2), (extrap_eqn))
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "ers_oracle.c")
+_LIB_PATH = os.path.join(_HERE, "_build", "libers_oracle.so")
+_lock = threading.Lock()
+_lib = None
+
+DIRECT = 0
+LOCALIZED = 1
+ON_SURFACE_TOL = 1e-12  # |b| <= tol * (largest semi-axis) counts as on the surface
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with gcc (-O2, OpenMP, no fast-math)."""
+    os.makedirs(os.path.dirname(_LIB_PATH), exist_ok=True)
+    if force or not os.path.exists(_LIB_PATH) or os.path.getmtime(_LIB_PATH) < os.path.getmtime(_SRC):
+        tmp = _LIB_PATH + f".tmp{os.getpid()}"
+        cmd = ["gcc", "-O2", "-fopenmp", "-fPIC", "-shared", "-std=c11", "-o", tmp, _SRC, "-lm"]
+        subprocess.run(cmd, check=True)
+        os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is None:
+            lib = ctypes.CDLL(build())
+            P = ctypes.POINTER(ctypes.c_double)
+            i64, dbl, cint = ctypes.c_int64, ctypes.c_double, ctypes.c_int
+            lib.ora_quadrature.restype = i64
+            lib.ora_quadrature.argtypes = [P, P, dbl, P, P, P]
+            lib.ora_closest_point.restype = None
+            lib.ora_closest_point.argtypes = [P, P, P, i64, dbl, P, P, P]
+            lib.ora_sigma.restype = None
+            lib.ora_sigma.argtypes = [dbl, P]
+            lib.ora_I0.restype = dbl
+            lib.ora_I0.argtypes = [dbl]
+            lib.ora_I2.restype = dbl
+            lib.ora_I2.argtypes = [dbl]
+            lib.ora_extrapolate.restype = cint
+            lib.ora_extrapolate.argtypes = [P, dbl, dbl, P, cint, P]
+            lib.ora_eval.restype = i64
+            lib.ora_eval.argtypes = [P, P, P, P, P, i64, P, P, P, P, P, P, i64, dbl, P, dbl, cint, P, P]
+            lib.ora_eval_one_delta.restype = None
+            lib.ora_eval_one_delta.argtypes = [P, P, P, P, P, i64, P, P, P, P, P, P, i64, dbl, dbl, P, P]
+            lib.ora_plain.restype = None
+            lib.ora_plain.argtypes = [P, P, P, P, P, i64, P, i64, P, P]
+            lib.ora_num_threads.restype = cint
+            _lib = lib
+    return _lib
+
+
+def _p(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def _c(a) -> np.ndarray:
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def num_threads() -> int:
+    return int(_load().ora_num_threads())
+
+
+def quadrature(shape, h: float):
+    """Nodes (N,3), outward normals (N,3), weights (N) of the Sec. 2.2 rule."""
+    lib = _load()
+    c, a = _c(shape.center), _c(shape.axes)
+    N = lib.ora_quadrature(_p(c), _p(a), float(h), None, None, None)
+    x, n, w = np.empty((N, 3)), np.empty((N, 3)), np.empty(N)
+    N2 = lib.ora_quadrature(_p(c), _p(a), float(h), _p(x), _p(n), _p(w))
+    assert N2 == N
+    return x, n, w
+
+
+def closest_point(shape, y):
+    """Closest point x0, outward normal n0 and signed distance b (negative inside)."""
+    lib = _load()
+    c, a, y = _c(shape.center), _c(shape.axes), _c(y).reshape(-1, 3)
+    M = y.shape[0]
+    x0, n0, b = np.empty((M, 3)), np.empty((M, 3)), np.empty(M)
+    tol = ON_SURFACE_TOL * max(shape.axes)
+    lib.ora_closest_point(_p(c), _p(a), _p(y), M, tol, _p(x0), _p(n0), _p(b))
+    return x0, n0, b
+
+
+def sigma(t: float) -> np.ndarray:
+    out = np.empty(3)
+    _load().ora_sigma(float(t), _p(out))
+    return out
+
+
+def I0(lam: float) -> float:
+    return float(_load().ora_I0(float(lam)))
+
+
+def I2(lam: float) -> float:
+    return float(_load().ora_I2(float(lam)))
+
+
+def extrapolate(rho, b: float, h: float, U: np.ndarray):
+    """Solve Eq. (extrap_eqn) for u given U (3, nrhs) = the values for delta_1..3."""
+    U = _c(U)
+    nrhs = U.shape[1]
+    out = np.empty(nrhs)
+    rc = _load().ora_extrapolate(_p(_c(rho)), float(b), float(h), _p(U), nrhs, _p(out))
+    return out, rc
+
+
+def evaluate(x, n, w, f, q, y, x0, n0, b, f0, q0, h, rho, tc=6.0, mode=LOCALIZED):
+    """SL value u and DL value v (M,3) at targets y; see ers_oracle.c:ora_eval."""
+    lib = _load()
+    x, n, w, f, q = map(_c, (x, n, w, f, q))
+    y, x0, n0, b, f0, q0 = map(_c, (y, x0, n0, b, f0, q0))
+    N, M = w.shape[0], b.shape[0]
+    u, v = np.empty((M, 3)), np.empty((M, 3))
+    nfail = lib.ora_eval(_p(x), _p(n), _p(w), _p(f), _p(q), N, _p(y), _p(x0), _p(n0), _p(b), _p(f0), _p(q0), M,
+                         float(h), _p(_c(rho)), float(tc), int(mode), _p(u), _p(v))
+    return u, v, int(nfail)
+
+
+def evaluate_one_delta(x, n, w, f, q, y, x0, n0, b, f0, q0, delta, tc=6.0):
+    """Regularized sums u^delta, v^delta (Eqs. (Stokes_SL2), (Stokes_DL2)) for one delta."""
+    lib = _load()
+    x, n, w, f, q = map(_c, (x, n, w, f, q))
+    y, x0, n0, b, f0, q0 = map(_c, (y, x0, n0, b, f0, q0))
+    N, M = w.shape[0], b.shape[0]
+    u, v = np.empty((M, 3)), np.empty((M, 3))
+    lib.ora_eval_one_delta(_p(x), _p(n), _p(w), _p(f), _p(q), N, _p(y), _p(x0), _p(n0), _p(b), _p(f0), _p(q0), M,
+                           float(delta), float(tc), _p(u), _p(v))
+    return u, v
+
+
+def plain(x, n, w, f, q, y):
+    """Unregularized, unsubtracted sums of Eqs. (Stokes_SL), (Stokes_DL)."""
+    lib = _load()
+    x, n, w, f, q, y = map(_c, (x, n, w, f, q, y))
+    N, M = w.shape[0], y.shape[0]
+    u, v = np.empty((M, 3)), np.empty((M, 3))
+    lib.ora_plain(_p(x), _p(n), _p(w), _p(f), _p(q), N, _p(y), M, _p(u), _p(v))
+    return u, v

@@ -1,0 +1,360 @@
+#!/usr/bin/env python
+"""Throughput of the localized extrapolated-regularization hot path (Siebor & Tlupova) on GB300.
+
+Workload (fixed): unit sphere, lattice-crossing quadrature at h = 1/128 (N = 272,718 nodes),
+M = 392,718 targets = every node + 100,000 near-band points (|b| <= 4h) + 20,000 points uniform
+in [-2, 2]^3; degree-4 polynomial densities f, q; delta_k = rho_k h with rho = (2, 3, 4);
+regularization only for r/delta <= 6.  One step = one pass of the whole path for both layers:
+closest point, far field, near sums for three deltas and the extrapolation solve.
+
+The headline arm is the precision variant (far field with FP32 operands and FP64 accumulation;
+near sums, closest point and solve in FP64); the plain FP64 path is timed on the same
+workload for the speedup.  Prints one JSON line (rank 0).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import workloads  # noqa: E402
+
+METRIC = "SL+DL target evals/s and Gpair-interactions/s at N~300k; speedup vs plain FP64"
+UNIT = "target-evals/s"
+WORKLOAD = "sphere128"
+# Nominal non-tensor peaks at the 2070 MHz maximum SM clock: 152 SMs x 128 FP32 lanes x 2 flop,
+# and the FP64 rate of 1.25 TFLOP/s; both are scaled by the median SM clock seen while timing.
+SM_MAX_MHZ = 2070.0
+FP32_PEAK_NOMINAL = 152 * 128 * 2 * SM_MAX_MHZ * 1e6
+FP64_PEAK_NOMINAL = 1.25e12
+# Algorithmic flops (FMA = 2, add/mul/rsqrt = 1) per unit of work, derived in the design doc.
+FAR_FLOPS_PER_PAIR = 57                   # both layers, one (target, node) far pair
+NEAR_FLOPS_BASE = 85                      # both layers, one near pair: geometry + contractions
+NEAR_FLOPS_PER_ACTIVE_DELTA = 45          # sigma_1..3 from the table and the alpha-weighted sums
+NEAR_FLOPS_UNREGULARIZED = 10             # 1/r^p terms when some delta_k has r > 6 delta_k
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--fp64-steps", type=int, default=1)
+    ap.add_argument("--cpu-seconds", type=float, default=10.0, help="target wall time of the CPU baseline sample")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", default=WORKLOAD, help="profiling only: a smaller case (e.g. sphere64)")
+    return ap.parse_args()
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle-reason samples every 200 ms while the timed region runs."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_id: str | None):
+        cmd = ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms", "200"]
+        if gpu_id:
+            cmd += ["-i", gpu_id]
+        try:
+            self.p = subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.p.terminate()
+        out, _ = self.p.communicate(timeout=10)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for name, val in zip(names, f[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def dist_setup(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
+        if args.impl == "ours":
+            torch.cuda.set_device(local)
+            dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+        else:
+            dist.init_process_group("gloo")
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(x: float, world: int) -> float:
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda" if torch.cuda.is_available() else "cpu")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def build_targets(wl, x):
+    return np.ascontiguousarray(np.concatenate([x, wl.extra_targets]))
+
+
+def cpu_baseline(wl, y, seconds: float, gpu_results=None):
+    """The FP64 oracle (localized mode, OpenMP over targets) on a seeded sample of the same
+    targets, sized from a short calibration run to about `seconds` of wall time."""
+    import oracle
+    x, n, w = oracle.quadrature(wl.shape, wl.h)
+    f = workloads.poly_eval(wl.f_coef, x)
+    q = workloads.poly_eval(wl.q_coef, x)
+
+    def run(idx):
+        yy = y[idx]
+        x0, n0, b = oracle.closest_point(wl.shape, yy)
+        f0, q0 = workloads.poly_eval(wl.f_coef, x0), workloads.poly_eval(wl.q_coef, x0)
+        t0 = time.perf_counter()
+        x0, n0, b = oracle.closest_point(wl.shape, yy)
+        u, v, _ = oracle.evaluate(x, n, w, f, q, yy, x0, n0, b, f0, q0, wl.h, wl.rho, 6.0, oracle.LOCALIZED)
+        return time.perf_counter() - t0, u, v
+
+    cal = workloads.subsample(256, len(y), 11)
+    t_cal, _, _ = run(cal)
+    count = int(min(len(y), max(256, 256 * seconds / max(t_cal, 1e-3))))
+    idx = workloads.subsample(count, len(y), 12)
+    t, u, v = run(idx)
+    out = {"value": count / t, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
+           "sample": f"{count} of {len(y)} targets (seeded, same node/band/far mix), FP64 oracle, localized "
+                     f"far+near form, closest point included; {t:.1f} s wall"}
+    errs = {}
+    if gpu_results:
+        for name, (ug, vg) in gpu_results.items():
+            errs[name] = {"SL": float(np.abs(ug[idx] - u).max() / np.abs(u).max()),
+                          "DL": float(np.abs(vg[idx] - v).max() / np.abs(v).max())}
+    return out, errs
+
+
+def run_reference(args, world, rank):
+    """--impl reference: the FP64 oracle as the reference arm, on host cores, rank 0 only."""
+    if rank != 0:
+        return
+    import oracle
+    wl = workloads.config(WORKLOAD)
+    x, n, w = oracle.quadrature(wl.shape, wl.h)
+    f = workloads.poly_eval(wl.f_coef, x)
+    q = workloads.poly_eval(wl.q_coef, x)
+    y = build_targets(wl, x)
+    per_step = 1024
+    times = []
+    for step in range(args.warmup + args.steps):
+        idx = workloads.subsample(per_step, len(y), 100 + step)
+        yy = y[idx]
+        t0 = time.perf_counter()
+        x0, n0, b = oracle.closest_point(wl.shape, yy)
+        f0, q0 = workloads.poly_eval(wl.f_coef, x0), workloads.poly_eval(wl.q_coef, x0)
+        oracle.evaluate(x, n, w, f, q, yy, x0, n0, b, f0, q0, wl.h, wl.rho, 6.0, oracle.LOCALIZED)
+        if step >= args.warmup:
+            times.append(time.perf_counter() - t0)
+    t = sum(times) / len(times)
+    value = per_step / t
+    sample = (f"{per_step} seeded targets per step out of {len(y)} (same mix), FP64 oracle, localized far+near "
+              f"form; value is targets/s, i.e. extrapolated per target to the full workload")
+    print(json.dumps({"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
+                      "warmup": args.warmup, "ms_per_step": t * 1e3, "higher_is_better": True, "scaling": "weak",
+                      "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+                      "config": {"workload": WORKLOAD, "N": len(w), "M": len(y), "rho": list(wl.rho)},
+                      "cpu_baseline": {"value": value, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
+                                       "sample": sample},
+                      "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}))
+
+
+def main():
+    args = parse()
+    world, rank, local = dist_setup(args)
+    if args.impl == "reference":
+        run_reference(args, world, rank)
+        return
+    import torch
+
+    import paper_2507_00156_gb300 as ers
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    wl = workloads.config(args.workload)
+    s = ers.Surface(wl.shape.center, wl.shape.axes, wl.h)
+    xd, _, _ = s.nodes()
+    x = xd.cpu().numpy()
+    s.set_density(torch.from_numpy(workloads.poly_eval(wl.f_coef, x)).to(dev),
+                  torch.from_numpy(workloads.poly_eval(wl.q_coef, x)).to(dev))
+    y = build_targets(wl, x)
+    M, N = len(y), s.N
+    yd = torch.from_numpy(y).to(dev)
+    x0, _, _ = s.closest_point(yd)  # set-up only: the densities at the closest points are inputs
+    x0h = x0.cpu().numpy()
+    f0h, q0h = workloads.poly_eval(wl.f_coef, x0h), workloads.poly_eval(wl.q_coef, x0h)
+    f0, q0 = torch.from_numpy(f0h).to(dev), torch.from_numpy(q0h).to(dev)
+    u = torch.empty((M, 3), dtype=torch.float64, device=dev)
+    v = torch.empty((M, 3), dtype=torch.float64, device=dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)  # > 129 MB L2
+    stream = torch.cuda.current_stream()
+
+    def step(prec):
+        s.eval(yd, f0, q0, rho=wl.rho, precision=prec, u=u, v=v)
+
+    def timed(prec, steps, warm):
+        for _ in range(warm):
+            step(prec)
+        s.profile(True)
+        torch.cuda.synchronize()
+        barrier(world)
+        torch.cuda.synchronize()
+        evs = []
+        kern = []
+        for _ in range(steps):
+            flush.fill_(1)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            step(prec)
+            b.record(stream)
+            evs.append((a, b))
+            kern.append(s.last_profile())  # synchronizes; device times are unaffected
+        torch.cuda.synchronize()
+        barrier(world)
+        s.profile(False)
+        total = sum(a.elapsed_time(b) for a, b in evs) / 1e3
+        kms = np.mean(np.array(kern), axis=0)
+        return total, kms
+
+    gpu_id = None
+    try:
+        gpu_id = str(torch.cuda.get_device_properties(dev).uuid)
+        gpu_id = gpu_id if gpu_id.startswith("GPU-") else "GPU-" + gpu_id
+    except Exception:
+        gpu_id = None
+
+    # headline: precision variant
+    sampler = ClockSampler(gpu_id)
+    t_mixed, k_mixed = timed(ers.PREC_MIXED, args.steps, args.warmup)
+    clocks = sampler.stop()
+    near_targets, near_pairs, far_pairs = s.last_counts()
+    cls_counts = s.last_class_counts()
+    u_mixed, v_mixed = u.cpu().numpy(), v.cpu().numpy()
+    t_mixed = max_over_ranks(t_mixed, world)
+    ms_step = t_mixed / args.steps * 1e3
+    value = world * args.steps * M / t_mixed
+
+    # plain FP64 path on the same workload
+    t64, k64 = (None, None)
+    if args.fp64_steps > 0:
+        t64, k64 = timed(ers.PREC_FP64, args.fp64_steps, 1)
+        t64 = max_over_ranks(t64, world)
+    u64, v64 = u.cpu().numpy(), v.cpu().numpy()
+
+    # end to end through the public API with host buffers (pinned), copies inside the timed region
+    yh = torch.from_numpy(y).pin_memory().numpy()
+    f0p = torch.from_numpy(f0h).pin_memory().numpy()
+    q0p = torch.from_numpy(q0h).pin_memory().numpy()
+    uh = torch.empty((M, 3), dtype=torch.float64).pin_memory().numpy()
+    vh = torch.empty((M, 3), dtype=torch.float64).pin_memory().numpy()
+    s.eval_host(yh, f0p, q0p, rho=wl.rho, precision=ers.PREC_MIXED, u=uh, v=vh)
+    torch.cuda.synchronize()
+    barrier(world)
+    te = 0.0
+    for _ in range(args.steps):
+        flush.fill_(1)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        s.eval_host(yh, f0p, q0p, rho=wl.rho, precision=ers.PREC_MIXED, u=uh, v=vh)
+        te += time.perf_counter() - t0
+    barrier(world)
+    te = max_over_ranks(te, world)
+    e2e = {"value": world * args.steps * M / te, "unit": UNIT, "h2d_bytes_per_step": 3 * M * 3 * 8,
+           "d2h_bytes_per_step": 2 * M * 3 * 8, "api": "ers_eval_host (pinned host arrays, includes copies)"}
+
+    if rank != 0:
+        return
+    # roofline of the dominant kernel of the headline step
+    near_flops = None
+    sm_mhz = clocks.get("sm_mhz") or SM_MAX_MHZ
+    scale = sm_mhz / SM_MAX_MHZ
+    ms_closest, ms_far, ms_near = (float(z) for z in k_mixed)
+    near_flops = sum(c * (NEAR_FLOPS_BASE + NEAR_FLOPS_PER_ACTIVE_DELTA * (3 - k)
+                          + (NEAR_FLOPS_UNREGULARIZED if k >= 1 else 0)) for k, c in enumerate(cls_counts))
+    far_flops = far_pairs * FAR_FLOPS_PER_PAIR
+    if ms_near >= ms_far:
+        roof = {"kernel": "k_near (FP64 near sums + extrapolation)", "bound": "alu", "unit": "TFLOP/s",
+                "achieved": near_flops / (ms_near * 1e-3) / 1e12, "peak": FP64_PEAK_NOMINAL * scale / 1e12,
+                "peak_source": "nominal FP64 1.25 TFLOP/s x median SM clock / 2070 MHz"}
+    else:
+        roof = {"kernel": "k_far32 (FP32 far field, FP64 tile accumulation)", "bound": "alu", "unit": "TFLOP/s",
+                "achieved": far_flops / (ms_far * 1e-3) / 1e12, "peak": FP32_PEAK_NOMINAL * scale / 1e12,
+                "peak_source": "152 SMs x 128 FP32 lanes x 2 flop x median SM clock"}
+    roof["frac"] = roof["achieved"] / roof["peak"]
+    roof["traffic"] = None
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32+f64", "data": "synthetic",
+        "config": {"workload": args.workload, "shape": "unit sphere", "h": wl.h, "N": N, "M": M, "rho": list(wl.rho),
+                   "cutoff_t": 6.0, "precision": "mixed (FP32 far field, FP64 local sums/closest point/solve)",
+                   "l2": "flushed between timed steps (256 MiB write, outside the timed events)"},
+        "gpairs_per_s": world * args.steps * M * N / t_mixed / 1e9,
+        "kernels_ms": {"closest_point": ms_closest, "far_field": ms_far, "near_field_and_solve": ms_near},
+        "counts": {"near_targets": near_targets, "near_pairs": near_pairs, "far_pairs": far_pairs,
+                   "near_pairs_by_unregularized_deltas": cls_counts},
+        "gpu_launches": 3 * args.steps,
+        "roofline": roof,
+        "clocks": clocks,
+        "e2e": e2e,
+    }
+    if t64 is not None:
+        ms64 = t64 / args.fp64_steps * 1e3
+        line["plain_fp64"] = {"value": world * args.fp64_steps * M / t64, "unit": UNIT, "ms_per_step": ms64,
+                              "gpairs_per_s": world * args.fp64_steps * M * N / t64 / 1e9,
+                              "kernels_ms": {"closest_point": float(k64[0]), "far_field": float(k64[1]),
+                                             "near_field_and_solve": float(k64[2])},
+                              "far_fp64_tflops": far_flops / (float(k64[1]) * 1e-3) / 1e12,
+                              "fp64_peak_tflops": FP64_PEAK_NOMINAL * scale / 1e12}
+        line["speedup_vs_plain_fp64"] = ms64 / ms_step
+        line["mixed_vs_fp64_rel"] = {"SL": float(np.abs(u_mixed - u64).max() / np.abs(u64).max()),
+                                     "DL": float(np.abs(v_mixed - v64).max() / np.abs(v64).max())}
+    if world == 1 and not args.no_cpu_baseline:
+        cb, errs = cpu_baseline(wl, y, args.cpu_seconds, {"mixed": (u_mixed, v_mixed), "fp64": (u64, v64)})
+        line["cpu_baseline"] = cb
+        line["max_rel_err_vs_oracle_on_cpu_sample"] = errs
+    print(json.dumps(line))
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,174 @@
+/*
+ * ers.h -- C ABI of the GB300 library for the localized extrapolated-regularization method
+ * for nearly singular Stokes single- and double-layer integrals (Siebor & Tlupova,
+ * "Localized evaluation and fast summation in the extrapolated regularization method for
+ * integrals in Stokes flow").
+ *
+ * What the library computes, for a closed surface Gamma and targets y:
+ *   u_i(y) = 1/(8 pi) int S_ij(y,x) f_j(x) dS(x)            (Eq. (Stokes_SL), Stokeslet Eq. (Stokeslet))
+ *   v_i(y) = 1/(8 pi) int T_ijk(y,x) q_j(x) n_k(x) dS(x)    (Eq. (Stokes_DL), stresslet Eq. (Stresslet))
+ * discretised with the lattice-crossing quadrature of Sec. 2.2 (Eq. (quadrature)).  For a
+ * target within Rc = cutoff_t * delta_3 of Gamma it uses the subtracted densities of
+ * Eqs. (Stokes_SL1), (Stokes_DL1), the regularized kernels of Eqs. (Sreg), (Treg) with the
+ * smoothing functions of Eqs. (s1)-(s3) for three delta_k = rho_k h, and the extrapolation of
+ * Eq. (extrap_eqn) with I0, I2 of Eqs. (I0), (I2); the regularization is applied only where
+ * r/delta_k <= cutoff_t (Sec. 3.2), and the unregularized far part (nodes with r > Rc) is
+ * evaluated once and shared by the three delta_k (Eq. (near_far), Sec. 3.3).  Targets
+ * farther than Rc from Gamma get the plain sums of Eqs. (Stokes_SL), (Stokes_DL).
+ *
+ * Conventions for every entry point:
+ *  - Arrays are contiguous, row-major, IEEE double precision unless stated; "dev" arrays are
+ *    CUDA device pointers owned by the caller (the library never frees them); points and
+ *    vectors are (count, 3).
+ *  - `stream` is a cudaStream_t passed as void* (NULL = the legacy default stream).  Work is
+ *    enqueued asynchronously on it; results are ready when the stream reaches that point.
+ *  - Return value: ERS_OK (0), a positive warning, or a negative ERS_E_* code.  The calling
+ *    thread's last message is available from ers_last_error().  No entry point aborts or
+ *    throws across the ABI.
+ *  - One evaluation at a time per surface: calls that use the same surface on different
+ *    streams concurrently race on the surface's work buffers.
+ */
+#ifndef ERS_H
+#define ERS_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define ERS_OK 0
+#define ERS_W_CUTOFF 1        /* warning: cutoff_t < 6 (regularization truncated earlier than Sec. 3.2) */
+#define ERS_E_INVAL (-1)      /* bad argument (NULL, size, non-finite, unsorted rho, ...) */
+#define ERS_E_NOMEM (-2)      /* device or host allocation failed */
+#define ERS_E_CUDA (-3)       /* a CUDA call failed; message holds the CUDA error string */
+#define ERS_E_TIMEOUT (-4)    /* a bounded device-side wait expired */
+#define ERS_E_UNSUPPORTED (-5)/* valid but not supported by this build (e.g. cutoff_t > 8) */
+#define ERS_E_STATE (-6)      /* call out of order (e.g. eval before set_density) */
+
+#define ERS_LAYER_SL 1
+#define ERS_LAYER_DL 2
+
+#define ERS_PREC_FP64 0   /* every step in FP64 arithmetic */
+#define ERS_PREC_MIXED 1  /* far field with FP32 operands and FP64 accumulation per source tile;
+                             local sums, closest point and 3x3 solve in FP64 */
+
+typedef struct ers_surface ers_surface; /* opaque, library-owned */
+
+/* Ellipsoid sum(((x - center)/axes)^2) = 1; a sphere when the three axes are equal. */
+typedef struct {
+    double center[3];
+    double axes[3];
+} ers_shape;
+
+typedef struct {
+    double rho[3];    /* delta_k = rho_k h, strictly increasing, > 0 (Sec. 2: typically 3,4,5 or 2,3,4) */
+    double cutoff_t;  /* regularize only where r/delta <= cutoff_t; 6 in Sec. 3.2; range (0, 8] */
+    int precision;    /* ERS_PREC_FP64 or ERS_PREC_MIXED */
+    int layers;       /* bitmask of ERS_LAYER_SL, ERS_LAYER_DL */
+} ers_params;
+
+/*
+ * Build the quadrature of Sec. 2.2 on an ellipsoid with lattice spacing h (> 0): nodes where
+ * lattice lines parallel to e_k, through (i h, j h) in the other two coordinates, cross the
+ * surface, kept when |n_k| >= cos 70 deg, with weights w = psi_k(n)/|n_k| h^2 from the
+ * partition of unity psi_k = beta_k / sum beta_j, beta_j = b(arccos|n_j| / theta),
+ * b(r) = exp(2 r^2/(r^2 - 1)) for |r| < 1 (Eq. (quadrature)).  Nodes are in the canonical order
+ * k = 1,2,3; first remaining lattice index; second remaining index; lower root first.
+ * Allocates device memory on the current device; *out receives the handle.
+ * Errors: ERS_E_INVAL (NULL, h <= 0, axes <= 0, non-finite), ERS_E_NOMEM, ERS_E_CUDA.
+ */
+int ers_build_surface(const ers_shape *shape, double h, ers_surface **out);
+
+/* Release a surface and its device memory; NULL is accepted.  Returns ERS_OK. */
+int ers_surface_free(ers_surface *s);
+
+/*
+ * Node data in canonical order: *N nodes; *x, *n (N,3) dev, *w (N) dev (pointers remain owned
+ * by the surface and valid until ers_surface_free).  Any output pointer may be NULL.
+ */
+int ers_surface_info(const ers_surface *s, int64_t *N, double *h, const double **x, const double **n,
+                     const double **w);
+
+/*
+ * Set the densities at the nodes, in canonical order: f for the single layer, q for the
+ * double layer, each (N,3) dev; either may be NULL to leave it unchanged.  Copies the data
+ * (the caller may free or reuse the arrays once the stream reaches this point).
+ */
+int ers_set_density(ers_surface *s, const double *f, const double *q, void *stream);
+
+/*
+ * Closest point x0 on the surface, outward unit normal n0 there and signed distance b for M
+ * targets y (Sec. 2: y = x0 + b n0, b < 0 inside).  |b| <= 1e-12 * (largest semi-axis) is
+ * returned as b = 0 (on the surface, chi = 1/2 in Eq. (Stokes_DL1)).  y, x0, n0 (M,3) and
+ * b (M) dev.  On the medial set of an ellipsoid one valid closest point is returned.
+ * Errors: ERS_E_INVAL, ERS_E_CUDA.
+ */
+int ers_closest_point(const ers_surface *s, const double *y, int64_t M, double *x0, double *n0, double *b,
+                      void *stream);
+
+/*
+ * Evaluate the layers selected by p->layers at M targets y (M,3) dev.
+ *   x0, n0, b : closest-point data from ers_closest_point (dev), or all three NULL to have
+ *               them computed inside this call;
+ *   f0, q0    : the densities f and q at the closest points (M,3) dev, as in
+ *               Eqs. (Stokes_SL1), (Stokes_DL1); read only for targets with |b| <= Rc and only
+ *               for the selected layers (may be NULL when the layer is not selected);
+ *   u, v      : outputs (M,3) dev for the single and double layer (NULL when not selected).
+ * Requires ers_set_density for the selected layers.  M = 0 is a no-op.
+ * Returns ERS_OK, ERS_W_CUTOFF (cutoff_t < 6), or ERS_E_INVAL / ERS_E_STATE / ERS_E_NOMEM /
+ * ERS_E_CUDA / ERS_E_UNSUPPORTED.
+ */
+int ers_eval(ers_surface *s, const ers_params *p, const double *y, int64_t M, const double *x0,
+             const double *n0, const double *b, const double *f0, const double *q0, double *u, double *v,
+             void *stream);
+
+/* Single layer only: ers_eval with layers = ERS_LAYER_SL (p->layers is ignored). */
+int ers_eval_SL(ers_surface *s, const ers_params *p, const double *y, int64_t M, const double *x0,
+                const double *n0, const double *b, const double *f0, double *u, void *stream);
+
+/* Double layer only: ers_eval with layers = ERS_LAYER_DL (p->layers is ignored). */
+int ers_eval_DL(ers_surface *s, const ers_params *p, const double *y, int64_t M, const double *x0,
+                const double *n0, const double *b, const double *q0, double *v, void *stream);
+
+/*
+ * ers_eval with HOST arrays (any host memory; pinned memory gives faster copies): copies y,
+ * f0, q0 (and x0, n0, b when given) to library-owned device buffers on `stream`, evaluates,
+ * copies u, v back and synchronizes the stream before returning.
+ */
+int ers_eval_host(ers_surface *s, const ers_params *p, const double *y, int64_t M, const double *x0,
+                  const double *n0, const double *b, const double *f0, const double *q0, double *u, double *v,
+                  void *stream);
+
+/*
+ * Counts of the most recent ers_eval on this surface, for throughput reporting: number of
+ * targets with |b| <= Rc, number of (target, node) pairs in their local (r <= Rc) sums, and
+ * the number of far-field pairs.  Synchronizes the stream of that call.
+ */
+int ers_last_counts(ers_surface *s, int64_t *near_targets, int64_t *near_pairs, int64_t *far_pairs);
+
+/*
+ * Per-kernel timing of the following ers_eval calls on this surface: when enabled, CUDA events
+ * are recorded on the call's stream around the closest-point, far-field and near-field
+ * kernels.  enable = 0 turns it off.  Creates the events on first use (ERS_E_CUDA on failure).
+ */
+int ers_profile(ers_surface *s, int enable);
+
+/*
+ * Kernel durations in milliseconds of the most recent profiled ers_eval on this surface
+ * (closest point; far field; near field + extrapolation).  Synchronizes that call's stream.
+ * A kernel that did not run reports 0.  ERS_E_STATE if no profiled call happened.
+ */
+int ers_last_profile(ers_surface *s, double *ms_closest, double *ms_far, double *ms_near);
+
+/* Message of the last error on the calling thread ("" if none).  Never NULL. */
+const char *ers_last_error(void);
+
+/* Library version string. */
+const char *ers_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* ERS_H */

@@ -1,0 +1,254 @@
+"""Python binding of the GB300 extrapolated-regularization library (C ABI in include/ers.h).
+
+Argument marshalling only: every step of the evaluation runs in the library's CUDA kernels.
+PyTorch supplies device memory and streams.  Importing this package does not need a GPU, but
+every call that touches the library raises if ``libers.so`` has not been built (there is no
+CPU fallback).
+
+    import paper_2507_00156_gb300 as ers
+    s = ers.Surface(center=(0, 0, 0), axes=(1, 1, 1), h=1/64)
+    s.set_density(f=f_nodes, q=q_nodes)            # (N,3) cuda float64, canonical node order
+    x0, n0, b = s.closest_point(y)                   # (M,3) cuda float64 targets
+    u, v = s.eval(y, f0, q0, rho=(2, 3, 4))          # f0, q0: densities at x0
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libers.so")
+
+ERS_OK = 0
+ERS_W_CUTOFF = 1
+ERS_E_INVAL = -1
+ERS_E_NOMEM = -2
+ERS_E_CUDA = -3
+ERS_E_TIMEOUT = -4
+ERS_E_UNSUPPORTED = -5
+ERS_E_STATE = -6
+LAYER_SL = 1
+LAYER_DL = 2
+PREC_FP64 = 0
+PREC_MIXED = 1
+
+# Every symbol the header declares (checked by the tests).
+EXPORTS = ["ers_build_surface", "ers_surface_free", "ers_surface_info", "ers_set_density", "ers_closest_point",
+           "ers_eval", "ers_eval_SL", "ers_eval_DL", "ers_eval_host", "ers_last_counts", "ers_profile",
+           "ers_last_profile", "ers_last_error", "ers_version"]
+
+
+class ErsError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"ers error {code}: {msg}")
+        self.code = code
+
+
+class _Shape(ctypes.Structure):
+    _fields_ = [("center", ctypes.c_double * 3), ("axes", ctypes.c_double * 3)]
+
+
+class _Params(ctypes.Structure):
+    _fields_ = [("rho", ctypes.c_double * 3), ("cutoff_t", ctypes.c_double), ("precision", ctypes.c_int),
+                ("layers", ctypes.c_int)]
+
+
+_lib = None
+_lock = threading.Lock()
+
+
+def build(force: bool = False) -> str:
+    from . import buildlib
+    return buildlib.build(force=force)
+
+
+def lib():
+    """The loaded library; raises if it has not been built."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(LIB_PATH):
+                raise ImportError(f"libers.so is not built ({LIB_PATH}); run paper_2507_00156_gb300.build() first")
+            L = ctypes.CDLL(LIB_PATH)
+            vp, i64, dbl, cint = ctypes.c_void_p, ctypes.c_int64, ctypes.c_double, ctypes.c_int
+            P = ctypes.POINTER
+            L.ers_build_surface.argtypes = [P(_Shape), dbl, P(vp)]
+            L.ers_surface_free.argtypes = [vp]
+            L.ers_surface_info.argtypes = [vp, P(i64), P(dbl), P(vp), P(vp), P(vp)]
+            L.ers_set_density.argtypes = [vp, vp, vp, vp]
+            L.ers_closest_point.argtypes = [vp, vp, i64, vp, vp, vp, vp]
+            L.ers_eval.argtypes = [vp, P(_Params), vp, i64, vp, vp, vp, vp, vp, vp, vp, vp]
+            L.ers_eval_SL.argtypes = [vp, P(_Params), vp, i64, vp, vp, vp, vp, vp, vp]
+            L.ers_eval_DL.argtypes = [vp, P(_Params), vp, i64, vp, vp, vp, vp, vp, vp]
+            L.ers_eval_host.argtypes = [vp, P(_Params), vp, i64, vp, vp, vp, vp, vp, vp, vp, vp]
+            L.ers_last_counts.argtypes = [vp, P(i64), P(i64), P(i64)]
+            L.ers_profile.argtypes = [vp, cint]
+            L.ers_last_profile.argtypes = [vp, P(dbl), P(dbl), P(dbl)]
+            L.ers_last_error.restype = ctypes.c_char_p
+            L.ers_version.restype = ctypes.c_char_p
+            for name in EXPORTS:
+                if name not in ("ers_last_error", "ers_version"):
+                    getattr(L, name).restype = cint
+            _lib = L
+    return _lib
+
+
+def check(rc: int) -> int:
+    if rc < 0:
+        raise ErsError(rc, lib().ers_last_error().decode())
+    return rc
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    import torch
+    if not t.is_cuda or t.dtype != torch.float64 or not t.is_contiguous():
+        raise ValueError("expected a contiguous float64 CUDA tensor")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _hptr(a):
+    if a is None:
+        return None
+    import numpy as np
+    if a.dtype != np.float64 or not a.flags["C_CONTIGUOUS"]:
+        raise ValueError("expected a C-contiguous float64 array")
+    return ctypes.c_void_p(a.ctypes.data)
+
+
+def _stream(stream=None):
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+class _DevView:
+    """Zero-copy view of library-owned device memory (CUDA array interface)."""
+
+    def __init__(self, ptr: int, shape, owner):
+        self.__cuda_array_interface__ = {"shape": tuple(shape), "typestr": "<f8", "data": (ptr, False),
+                                         "version": 3, "strides": None}
+        self.owner = owner
+
+
+def params(rho=(2.0, 3.0, 4.0), cutoff_t=6.0, precision=PREC_FP64, layers=LAYER_SL | LAYER_DL) -> _Params:
+    p = _Params()
+    for k in range(3):
+        p.rho[k] = float(rho[k])
+    p.cutoff_t = float(cutoff_t)
+    p.precision = int(precision)
+    p.layers = int(layers)
+    return p
+
+
+class Surface:
+    """A quadrature surface on the current CUDA device (ers_build_surface)."""
+
+    def __init__(self, center, axes, h: float):
+        L = lib()
+        shp = _Shape()
+        for i in range(3):
+            shp.center[i] = float(center[i])
+            shp.axes[i] = float(axes[i])
+        handle = ctypes.c_void_p()
+        check(L.ers_build_surface(ctypes.byref(shp), float(h), ctypes.byref(handle)))
+        self._h = handle
+        self.center, self.axes = tuple(map(float, center)), tuple(map(float, axes))
+        N, hh = ctypes.c_int64(), ctypes.c_double()
+        xp, npp, wp = ctypes.c_void_p(), ctypes.c_void_p(), ctypes.c_void_p()
+        check(L.ers_surface_info(handle, ctypes.byref(N), ctypes.byref(hh), ctypes.byref(xp), ctypes.byref(npp),
+                                 ctypes.byref(wp)))
+        self.N, self.h = int(N.value), float(hh.value)
+        self._xp, self._np, self._wp = xp.value, npp.value, wp.value
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h is not None and h.value and _lib is not None:
+            _lib.ers_surface_free(h)
+            self._h = None
+
+    @property
+    def handle(self):
+        return self._h
+
+    def nodes(self):
+        """(x, n, w) as zero-copy CUDA tensors in canonical order."""
+        import torch
+        x = torch.as_tensor(_DevView(self._xp, (self.N, 3), self), device="cuda")
+        n = torch.as_tensor(_DevView(self._np, (self.N, 3), self), device="cuda")
+        w = torch.as_tensor(_DevView(self._wp, (self.N,), self), device="cuda")
+        return x, n, w
+
+    def set_density(self, f=None, q=None, stream=None):
+        check(lib().ers_set_density(self._h, _ptr(f), _ptr(q), _stream(stream)))
+
+    def closest_point(self, y, stream=None):
+        import torch
+        M = y.shape[0]
+        x0 = torch.empty((M, 3), dtype=torch.float64, device=y.device)
+        n0 = torch.empty((M, 3), dtype=torch.float64, device=y.device)
+        b = torch.empty((M,), dtype=torch.float64, device=y.device)
+        check(lib().ers_closest_point(self._h, _ptr(y), M, _ptr(x0), _ptr(n0), _ptr(b), _stream(stream)))
+        return x0, n0, b
+
+    def eval(self, y, f0=None, q0=None, rho=(2.0, 3.0, 4.0), cutoff_t=6.0, precision=PREC_FP64,
+             layers=LAYER_SL | LAYER_DL, x0=None, n0=None, b=None, u=None, v=None, stream=None):
+        """ers_eval: returns (u, v) (None for a layer not selected)."""
+        import torch
+        M = y.shape[0]
+        sl, dl = bool(layers & LAYER_SL), bool(layers & LAYER_DL)
+        if sl and u is None:
+            u = torch.empty((M, 3), dtype=torch.float64, device=y.device)
+        if dl and v is None:
+            v = torch.empty((M, 3), dtype=torch.float64, device=y.device)
+        p = params(rho, cutoff_t, precision, layers)
+        self.last_rc = check(lib().ers_eval(self._h, ctypes.byref(p), _ptr(y), M, _ptr(x0), _ptr(n0), _ptr(b),
+                                            _ptr(f0) if sl else None, _ptr(q0) if dl else None,
+                                            _ptr(u) if sl else None, _ptr(v) if dl else None, _stream(stream)))
+        return (u if sl else None), (v if dl else None)
+
+    def eval_host(self, y, f0, q0, rho=(2.0, 3.0, 4.0), cutoff_t=6.0, precision=PREC_FP64,
+                  layers=LAYER_SL | LAYER_DL, u=None, v=None, stream=None):
+        """ers_eval_host with numpy (ideally pinned) host arrays."""
+        import numpy as np
+        M = y.shape[0]
+        sl, dl = bool(layers & LAYER_SL), bool(layers & LAYER_DL)
+        if sl and u is None:
+            u = np.empty((M, 3))
+        if dl and v is None:
+            v = np.empty((M, 3))
+        p = params(rho, cutoff_t, precision, layers)
+        check(lib().ers_eval_host(self._h, ctypes.byref(p), _hptr(y), M, None, None, None,
+                                  _hptr(f0) if sl else None, _hptr(q0) if dl else None,
+                                  _hptr(u) if sl else None, _hptr(v) if dl else None, _stream(stream)))
+        return (u if sl else None), (v if dl else None)
+
+    def profile(self, enable: bool = True):
+        check(lib().ers_profile(self._h, 1 if enable else 0))
+
+    def last_profile(self):
+        """(ms_closest, ms_far, ms_near) of the most recent profiled eval."""
+        a, b_, c = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+        check(lib().ers_last_profile(self._h, ctypes.byref(a), ctypes.byref(b_), ctypes.byref(c)))
+        return a.value, b_.value, c.value
+
+    def last_counts(self):
+        """(near targets, near pairs, far pairs) of the most recent eval."""
+        a, b_, c = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+        check(lib().ers_last_counts(self._h, ctypes.byref(a), ctypes.byref(b_), ctypes.byref(c)))
+        return int(a.value), int(b_.value), int(c.value)
+
+    def last_class_counts(self):
+        """Near pairs of the most recent eval by the number of unregularized deltas (0, 1, 2)."""
+        self.last_counts()
+        c = [ctypes.c_int64() for _ in range(3)]
+        L = lib()
+        L.ers_debug_class_counts.argtypes = [ctypes.c_void_p] + [ctypes.POINTER(ctypes.c_int64)] * 3
+        check(L.ers_debug_class_counts(self._h, *(ctypes.byref(z) for z in c)))
+        return [int(z.value) for z in c]
+
+
+def version() -> str:
+    return lib().ers_version().decode()

@@ -1,0 +1,267 @@
+// Far field: the unregularized sums over nodes with r > Rc, evaluated once per target and
+// shared by the three delta_k (Eq. (near_far), Sec. 3.3), with the subtracted densities of
+// Eqs. (Stokes_SL1), (Stokes_DL1) for targets within Rc of the surface and the plain densities
+// for the others:
+//   SL: u_i += 1/(8 pi) [ g_i / r + d_i (d.g) / r^3 ],           g = w f - (f(x0).n0) w n
+//   DL: v_i += 1/(8 pi) (-6) d_i (d.Q) (d.m) / r^5,               Q = q - q(x0), m = w n
+// with d = y - x (Eqs. (Stokeslet), (Stresslet)).
+//
+// Layout: grid (target blocks, source chunks).  A CTA owns TPB = 128 * TPT targets (TPT per
+// thread, held in registers) and one contiguous chunk of the cell-sorted source records; it
+// stages tiles of the chunk in shared memory and every thread reads each staged source as a
+// broadcast.  Partial sums go to part[chunk][target][6]; the near-field kernel adds the chunks.
+// The mask "r^2 > Rc^2" is evaluated with the same operation order as the near-field
+// selection, so every pair lands in exactly one of the two sums.
+#include "ers_internal.h"
+
+namespace ers {
+namespace {
+
+constexpr int NT = 128;
+constexpr double INV8PI = 0.039788735772973833942;  // 1/(8 pi)
+
+struct TargetF64 {
+    double y[3], c, q0[3];
+    long long rc2bits;  // pair is far iff bits(r^2) > rc2bits (signed compare; -1 = all far)
+};
+
+__device__ __forceinline__ void load_target(const EvalArgs &A, int64_t m, bool sl, bool dl, TargetF64 &T,
+                                            bool &valid) {
+    valid = m < A.M;
+    if (!valid) {
+        T.y[0] = T.y[1] = T.y[2] = 0.0;
+        T.c = 0.0;
+        T.q0[0] = T.q0[1] = T.q0[2] = 0.0;
+        T.rc2bits = 0x7fffffffffffffffLL;  // nothing is far
+        return;
+    }
+    for (int i = 0; i < 3; ++i) T.y[i] = A.y[3 * m + i];
+    const double bm = A.b[m];
+    const bool near = fabs(bm) <= A.Rc;
+    T.rc2bits = near ? __double_as_longlong(A.Rc * A.Rc) : -1LL;
+    T.c = 0.0;
+    T.q0[0] = T.q0[1] = T.q0[2] = 0.0;
+    if (near) {
+        if (sl) T.c = A.f0[3 * m] * A.n0[3 * m] + A.f0[3 * m + 1] * A.n0[3 * m + 1] + A.f0[3 * m + 2] * A.n0[3 * m + 2];
+        if (dl)
+            for (int i = 0; i < 3; ++i) T.q0[i] = A.q0[3 * m + i];
+    }
+}
+
+template <bool SL, bool DL, int TPT, int TS>
+__global__ void __launch_bounds__(NT) k_far64(EvalArgs A) {
+    __shared__ double2 srec[TS * REC / 2];
+    const int64_t j0 = (int64_t)blockIdx.y * A.chunk_len;
+    const int64_t j1 = min(A.s->N, j0 + A.chunk_len);
+    const double *__restrict__ rec = A.s->rec;
+
+    TargetF64 T[TPT];
+    bool valid[TPT];
+    double acc[TPT][6];
+#pragma unroll
+    for (int t = 0; t < TPT; ++t) {
+        const int64_t m = (int64_t)blockIdx.x * (NT * TPT) + t * NT + threadIdx.x;
+        load_target(A, m, SL, DL, T[t], valid[t]);
+#pragma unroll
+        for (int i = 0; i < 6; ++i) acc[t][i] = 0.0;
+    }
+
+    for (int64_t base = j0; base < j1; base += TS) {
+        const int ns = (int)min((int64_t)TS, j1 - base);
+        __syncthreads();
+        const double2 *src = reinterpret_cast<const double2 *>(rec + base * REC);
+        for (int k = threadIdx.x; k < ns * REC / 2; k += NT) srec[k] = src[k];
+        __syncthreads();
+        for (int j = 0; j < ns; ++j) {
+            const double2 r0 = srec[j * 6 + 0], r1 = srec[j * 6 + 1], r2v = srec[j * 6 + 2];
+            const double2 r3 = srec[j * 6 + 3], r4 = srec[j * 6 + 4], r5 = srec[j * 6 + 5];
+            const double xs0 = r0.x, xs1 = r0.y, xs2 = r1.x;
+            const double wf0 = r1.y, wf1 = r2v.x, wf2 = r2v.y;
+            const double wn0 = r3.x, wn1 = r3.y, wn2 = r4.x;
+            const double q0s = r4.y, q1s = r5.x, q2s = r5.y;
+#pragma unroll
+            for (int t = 0; t < TPT; ++t) {
+                const double dx = __dsub_rn(T[t].y[0], xs0);
+                const double dy = __dsub_rn(T[t].y[1], xs1);
+                const double dz = __dsub_rn(T[t].y[2], xs2);
+                const double r2 = dist2_fp64(dx, dy, dz);
+                double ri = rsqrt(r2);
+                ri = (__double_as_longlong(r2) > T[t].rc2bits) ? ri : 0.0;
+                const double ri2 = ri * ri;
+                if (SL) {
+                    const double g0 = fma(-T[t].c, wn0, wf0);
+                    const double g1 = fma(-T[t].c, wn1, wf1);
+                    const double g2 = fma(-T[t].c, wn2, wf2);
+                    const double s = fma(dz, g2, fma(dy, g1, dx * g0)) * ri2;  // (d.g)/r^2
+                    acc[t][0] = fma(fma(dx, s, g0), ri, acc[t][0]);
+                    acc[t][1] = fma(fma(dy, s, g1), ri, acc[t][1]);
+                    acc[t][2] = fma(fma(dz, s, g2), ri, acc[t][2]);
+                }
+                if (DL) {
+                    const double Q0 = q0s - T[t].q0[0], Q1 = q1s - T[t].q0[1], Q2 = q2s - T[t].q0[2];
+                    const double dQ = fma(dz, Q2, fma(dy, Q1, dx * Q0));
+                    const double dm = fma(dz, wn2, fma(dy, wn1, dx * wn0));
+                    const double s = (dQ * dm) * ((ri2 * ri2) * ri);  // (d.Q)(d.m)/r^5
+                    acc[t][3] = fma(dx, s, acc[t][3]);
+                    acc[t][4] = fma(dy, s, acc[t][4]);
+                    acc[t][5] = fma(dz, s, acc[t][5]);
+                }
+            }
+        }
+    }
+#pragma unroll
+    for (int t = 0; t < TPT; ++t) {
+        if (!valid[t]) continue;
+        const int64_t m = (int64_t)blockIdx.x * (NT * TPT) + t * NT + threadIdx.x;
+        double *o = A.part + ((int64_t)blockIdx.y * A.M + m) * 6;
+        o[0] = acc[t][0] * INV8PI;
+        o[1] = acc[t][1] * INV8PI;
+        o[2] = acc[t][2] * INV8PI;
+        o[3] = acc[t][3] * (-6.0 * INV8PI);
+        o[4] = acc[t][4] * (-6.0 * INV8PI);
+        o[5] = acc[t][5] * (-6.0 * INV8PI);
+    }
+}
+
+// Mixed precision: every pair term in FP32 with the target and source both expressed relative
+// to the centre c of the source tile (an exact float), yc = (y_hi - c) + y_lo, so that the
+// rounding error of d = yc - (x - c) is relative to |y - c| and |x - c| rather than to |y|;
+// FP32 partial sums over FLUSH tiles are added into FP64 accumulators.
+struct TargetF32 {
+    float yh[3], yl[3], c, q0[3], rc2;
+};
+
+template <bool SL, bool DL, int TPT, int FLUSH>
+__global__ void __launch_bounds__(NT) k_far32(EvalArgs A, float rc2f) {
+    __shared__ float4 srec[TS32 * 3];
+    __shared__ float4 scen;
+    const int64_t j0 = (int64_t)blockIdx.y * A.chunk_len;  // multiple of TS32
+    const int64_t j1 = min(A.s->N, j0 + A.chunk_len);
+    const float *__restrict__ rec = A.s->rec32;
+
+    TargetF32 T[TPT];
+    bool valid[TPT];
+    double acc[TPT][6];
+    float accf[TPT][6];
+#pragma unroll
+    for (int t = 0; t < TPT; ++t) {
+        const int64_t m = (int64_t)blockIdx.x * (NT * TPT) + t * NT + threadIdx.x;
+        TargetF64 D;
+        load_target(A, m, SL, DL, D, valid[t]);
+        for (int i = 0; i < 3; ++i) {
+            T[t].yh[i] = __double2float_rn(D.y[i]);
+            T[t].yl[i] = __double2float_rn(D.y[i] - (double)T[t].yh[i]);
+            T[t].q0[i] = __double2float_rn(D.q0[i]);
+        }
+        T[t].c = __double2float_rn(D.c);
+        // far iff r2 > rc2: +inf = nothing far (invalid target), -1 = everything far
+        T[t].rc2 = !valid[t] ? __int_as_float(0x7f800000) : (D.rc2bits < 0 ? -1.0f : rc2f);
+#pragma unroll
+        for (int i = 0; i < 6; ++i) {
+            acc[t][i] = 0.0;
+            accf[t][i] = 0.0f;
+        }
+    }
+
+    int tiles_since_flush = 0;
+    for (int64_t base = j0; base < j1; base += TS32) {
+        const int ns = (int)min((int64_t)TS32, j1 - base);
+        __syncthreads();
+        const float4 *src = reinterpret_cast<const float4 *>(rec + base * REC);
+        for (int k = threadIdx.x; k < ns * 3; k += NT) srec[k] = src[k];
+        if (threadIdx.x == 0) scen = reinterpret_cast<const float4 *>(A.s->tilec)[base / TS32];
+        __syncthreads();
+        const float4 cen = scen;
+        float yc[TPT][3];
+#pragma unroll
+        for (int t = 0; t < TPT; ++t) {
+            yc[t][0] = tile_rel(T[t].yh[0], cen.x, T[t].yl[0]);
+            yc[t][1] = tile_rel(T[t].yh[1], cen.y, T[t].yl[1]);
+            yc[t][2] = tile_rel(T[t].yh[2], cen.z, T[t].yl[2]);
+        }
+        for (int j = 0; j < ns; ++j) {
+            const float4 r0 = srec[j * 3 + 0], r1 = srec[j * 3 + 1], r2v = srec[j * 3 + 2];
+            // r0 = (xc0 xc1 xc2 wf0), r1 = (wf1 wf2 wn0 wn1), r2v = (wn2 q0 q1 q2)
+#pragma unroll
+            for (int t = 0; t < TPT; ++t) {
+                float dx, dy, dz;
+                const float r2 = dist2_fp32(yc[t][0], yc[t][1], yc[t][2], r0.x, r0.y, r0.z, &dx, &dy, &dz);
+                float ri = rsqrtf(r2);
+                ri = ri * fmaf(-0.5f * r2 * ri, ri, 1.5f);  // one Newton step
+                ri = (r2 > T[t].rc2) ? ri : 0.0f;
+                const float ri2 = ri * ri;
+                if (SL) {
+                    const float g0 = fmaf(-T[t].c, r1.z, r0.w);
+                    const float g1 = fmaf(-T[t].c, r1.w, r1.x);
+                    const float g2 = fmaf(-T[t].c, r2v.x, r1.y);
+                    const float s = fmaf(dz, g2, fmaf(dy, g1, dx * g0)) * ri2;
+                    accf[t][0] = fmaf(fmaf(dx, s, g0), ri, accf[t][0]);
+                    accf[t][1] = fmaf(fmaf(dy, s, g1), ri, accf[t][1]);
+                    accf[t][2] = fmaf(fmaf(dz, s, g2), ri, accf[t][2]);
+                }
+                if (DL) {
+                    const float Q0 = r2v.y - T[t].q0[0], Q1 = r2v.z - T[t].q0[1], Q2 = r2v.w - T[t].q0[2];
+                    const float dQ = fmaf(dz, Q2, fmaf(dy, Q1, dx * Q0));
+                    const float dm = fmaf(dz, r2v.x, fmaf(dy, r1.w, dx * r1.z));
+                    const float s = (dQ * dm) * ((ri2 * ri2) * ri);
+                    accf[t][3] = fmaf(dx, s, accf[t][3]);
+                    accf[t][4] = fmaf(dy, s, accf[t][4]);
+                    accf[t][5] = fmaf(dz, s, accf[t][5]);
+                }
+            }
+        }
+        if (++tiles_since_flush == FLUSH) {
+            tiles_since_flush = 0;
+#pragma unroll
+            for (int t = 0; t < TPT; ++t)
+#pragma unroll
+                for (int i = 0; i < 6; ++i) {
+                    acc[t][i] += (double)accf[t][i];
+                    accf[t][i] = 0.0f;
+                }
+        }
+    }
+#pragma unroll
+    for (int t = 0; t < TPT; ++t) {
+        if (!valid[t]) continue;
+        const int64_t m = (int64_t)blockIdx.x * (NT * TPT) + t * NT + threadIdx.x;
+        double *o = A.part + ((int64_t)blockIdx.y * A.M + m) * 6;
+        for (int i = 0; i < 6; ++i) acc[t][i] += (double)accf[t][i];
+        o[0] = acc[t][0] * INV8PI;
+        o[1] = acc[t][1] * INV8PI;
+        o[2] = acc[t][2] * INV8PI;
+        o[3] = acc[t][3] * (-6.0 * INV8PI);
+        o[4] = acc[t][4] * (-6.0 * INV8PI);
+        o[5] = acc[t][5] * (-6.0 * INV8PI);
+    }
+}
+
+template <int TPT, int TS>
+cudaError_t far64_dispatch(const EvalArgs &a) {
+    const int64_t tb = (a.M + NT * TPT - 1) / (NT * TPT);
+    dim3 grid((unsigned)tb, (unsigned)a.chunks);
+    const bool sl = a.layers & ERS_LAYER_SL, dl = a.layers & ERS_LAYER_DL;
+    if (sl && dl) k_far64<true, true, TPT, TS><<<grid, NT, 0, a.stream>>>(a);
+    else if (sl) k_far64<true, false, TPT, TS><<<grid, NT, 0, a.stream>>>(a);
+    else k_far64<false, true, TPT, TS><<<grid, NT, 0, a.stream>>>(a);
+    return cudaGetLastError();
+}
+
+template <int TPT>
+cudaError_t far32_dispatch(const EvalArgs &a) {
+    const int64_t tb = (a.M + NT * TPT - 1) / (NT * TPT);
+    dim3 grid((unsigned)tb, (unsigned)a.chunks);
+    const bool sl = a.layers & ERS_LAYER_SL, dl = a.layers & ERS_LAYER_DL;
+    const float rc2f = (float)(a.Rc * a.Rc);  // same rounding as the near-field copy
+    if (sl && dl) k_far32<true, true, TPT, 2><<<grid, NT, 0, a.stream>>>(a, rc2f);
+    else if (sl) k_far32<true, false, TPT, 2><<<grid, NT, 0, a.stream>>>(a, rc2f);
+    else k_far32<false, true, TPT, 2><<<grid, NT, 0, a.stream>>>(a, rc2f);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_far64(const EvalArgs &a) { return far64_dispatch<2, 64>(a); }
+cudaError_t launch_far32(const EvalArgs &a) { return far32_dispatch<2>(a); }
+
+}  // namespace ers

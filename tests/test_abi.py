@@ -1,0 +1,104 @@
+"""The C-ABI library builds, loads without a GPU and exports every declared symbol; its host-side
+set-up (quadrature, smoothing-function table) matches the oracle and the mathematics."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+import oracle
+import paper_2507_00156_gb300 as ers
+import workloads
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def L():
+    ers.build()
+    return ers.lib()
+
+
+def declared_functions():
+    text = open(os.path.join(ROOT, "include", "ers.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(ers_[A-Za-z0-9_]+)\s*\(", text)))
+
+
+def test_exports_every_declared_symbol(L):
+    names = declared_functions()
+    assert len(names) >= 12
+    for name in names:
+        assert hasattr(L, name), name
+    assert sorted(ers.EXPORTS) == names
+
+
+def test_version_and_error_string(L):
+    assert "sm_103a" in ers.version()
+    assert L.ers_last_error() is not None
+
+
+def test_null_arguments_return_codes_without_gpu(L):
+    vp = ctypes.c_void_p
+    assert L.ers_build_surface(None, 0.1, None) == ers.ERS_E_INVAL
+    assert L.ers_surface_info(None, None, None, None, None, None) == ers.ERS_E_INVAL
+    assert L.ers_surface_free(None) == ers.ERS_OK
+    assert L.ers_closest_point(None, None, 0, None, None, None, None) == ers.ERS_E_INVAL
+    p = ers.params()
+    assert L.ers_eval(None, ctypes.byref(p), None, 0, None, None, None, None, None, None, None, None) == ers.ERS_E_INVAL
+    shp = ers._Shape()
+    for i in range(3):
+        shp.axes[i] = 1.0
+    h = vp()
+    assert L.ers_build_surface(ctypes.byref(shp), -1.0, ctypes.byref(h)) == ers.ERS_E_INVAL
+    assert "h must be" in L.ers_last_error().decode()
+    shp.axes[1] = 0.0
+    assert L.ers_build_surface(ctypes.byref(shp), 0.1, ctypes.byref(h)) == ers.ERS_E_INVAL
+
+
+@pytest.mark.parametrize("shape,inv", [(workloads.unit_sphere(), 16), (workloads.unit_sphere((0.1, -0.05, 0.2)), 32),
+                                       (workloads.Shape((0.0, 0.0, 0.0), (1.0, 0.8, 0.6)), 32),
+                                       (workloads.Shape((0.0, 0.0, 0.0), (1.0, 0.5, 0.5)), 64)])
+def test_library_quadrature_matches_oracle(L, shape, inv):
+    L.ers_debug_quadrature.restype = ctypes.c_int64
+    P = ctypes.POINTER(ctypes.c_double)
+    L.ers_debug_quadrature.argtypes = [P, P, ctypes.c_double, P, P, P, ctypes.c_int64]
+    c = np.array(shape.center)
+    a = np.array(shape.axes)
+    p = lambda v: v.ctypes.data_as(P)
+    N = L.ers_debug_quadrature(p(c), p(a), 1 / inv, None, None, None, 0)
+    x, n, w = np.empty((N, 3)), np.empty((N, 3)), np.empty(N)
+    L.ers_debug_quadrature(p(c), p(a), 1 / inv, p(x), p(n), p(w), N)
+    xo, no, wo = oracle.quadrature(shape, 1 / inv)
+    assert N == len(wo)
+    assert np.abs(x - xo).max() <= 2e-16 * 4
+    assert np.abs(n - no).max() <= 1e-15
+    assert np.abs(w - wo).max() <= 1e-15 * wo.max()
+
+
+def test_sigma_table_accuracy(L):
+    """The interpolation table reproduces s_p(t)/t^p (Eqs. (s1)-(s3)) to ~1e-15 on tau = t^2 in [0, 64)."""
+    mp = pytest.importorskip("mpmath")
+    mp.mp.dps = 40
+    nint, deg = 512, 6
+    tab = np.empty(nint * 3 * (deg + 1))
+    assert L.ers_debug_sigma_table(tab.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), tab.size) == 0
+    tab = tab.reshape(nint, 3, deg + 1)
+    rng = np.random.default_rng(1)
+    taus = np.concatenate([[0.0, 1e-12, 0.125, 0.25, 35.99, 36.0], rng.uniform(0, 64, 300)])
+    worst = 0.0
+    for tau in taus:
+        i = min(int(tau * 8), nint - 1)
+        s = 16 * tau - (2 * i + 1)
+        t = mp.sqrt(mp.mpf(tau))
+        c = 2 / mp.sqrt(mp.pi)
+        if t == 0:
+            ref = [c, c * 2 / 3, c * 4 / 15]
+        else:
+            e, g = mp.erf(t), mp.exp(-t * t)
+            ref = [e / t, (e - c * t * g) / t**3, (e - c * (t + mp.mpf(2) / 3 * t**3) * g) / t**5]
+        for p_ in range(3):
+            got = np.polyval(tab[i, p_], s)
+            worst = max(worst, abs(got - float(ref[p_])) / abs(float(ref[p_])))
+    assert worst < 6e-15, worst

@@ -1,0 +1,182 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle.
+
+Bars: FP64 path within 1e-11 relative (max-norm over targets, per layer); mixed-precision far
+field within 1e-6.  Sizes span several far-field tiles and ragged tails; the full-size bench
+workload is checked on a seeded sample of targets.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import workloads
+from parity import GpuProblem, oracle_eval, oracle_problem, rel_err
+
+pytestmark = pytest.mark.gpu
+FP64_TOL = 1e-11
+MIXED_TOL = 1e-6
+
+
+@pytest.fixture(scope="module")
+def ers():
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2507_00156_gb300
+    return paper_2507_00156_gb300
+
+
+_cache = {}
+
+
+def gpu(name):
+    if name not in _cache:
+        _cache[name] = GpuProblem(name)
+    return _cache[name]
+
+
+@pytest.mark.parametrize("name", ["sphere16", "sphere32"])
+def test_nodes_match_oracle(ers, name):
+    g = gpu(name)
+    _, x, n, w, _, _ = oracle_problem(name)
+    xd, nd, wd = (t.cpu().numpy() for t in g.s.nodes())
+    assert xd.shape == x.shape
+    assert np.abs(xd - x).max() <= 1e-15 and np.abs(nd - n).max() <= 1e-15
+    assert np.abs(wd - w).max() <= 1e-15 * w.max()
+
+
+@pytest.mark.parametrize("shape", [workloads.unit_sphere((0.1, 0.0, -0.2)), workloads.Shape((0.0, 0.0, 0.0), (1.0, 0.8, 0.6))])
+def test_closest_point_matches_oracle(ers, shape):
+    import torch
+    s = ers.Surface(shape.center, shape.axes, 1 / 16)
+    rng = np.random.default_rng(9)
+    yb, _, _, _ = workloads.near_band_targets(shape, 3000, 0.3, rng)
+    yf = rng.uniform(-2, 2, (3000, 3))
+    xs, _, _ = oracle.quadrature(shape, 1 / 16)
+    y = np.concatenate([yb, yf, xs[:500]])
+    x0, n0, b = (t.cpu().numpy() for t in s.closest_point(torch.from_numpy(y).cuda()))
+    x0o, n0o, bo = oracle.closest_point(shape, y)
+    assert np.abs(b - bo).max() < 1e-13
+    assert (b[-500:] == 0).all()  # node targets are on the surface
+    ok = np.abs(bo) < 0.35  # unique closest point inside the reach of the ellipsoid
+    assert np.abs(x0 - x0o)[ok].max() < 1e-12
+    assert np.abs(n0 - n0o)[ok].max() < 1e-11
+
+
+@pytest.mark.parametrize("name", ["sphere16", "sphere32"])
+@pytest.mark.parametrize("precision,tol", [(0, FP64_TOL), (1, MIXED_TOL)])
+def test_eval_all_targets(ers, name, precision, tol):
+    y, uo, vo, bo = oracle_eval(name)
+    g = gpu(name)
+    u, v, b = g.eval(g.targets(), precision=precision)
+    assert np.abs(b - bo).max() < 1e-13
+    eu, ev = rel_err(u, uo), rel_err(v, vo)
+    assert eu <= tol and ev <= tol, (eu, ev)
+
+
+def test_eval_ellipsoid_with_far_points(ers):
+    """Ellipsoid (1, 0.8, 0.6) at h = 1/32: node, band and box targets (inside, outside, far)."""
+    shape = workloads.Shape((0.0, 0.0, 0.0), (1.0, 0.8, 0.6))
+    wl = workloads.make_workload("ell32", shape, 1 / 32, (2, 3, 4), 77, 1500, 16 / 32 * 0.7, n_far=700)
+    g = GpuProblem("ell32", wl)
+    x, n, w = oracle.quadrature(shape, wl.h)
+    sel = np.concatenate([np.arange(0, len(w), 11), len(w) + np.arange(len(wl.extra_targets))])
+    y = np.concatenate([x, wl.extra_targets])[sel]
+    x0, n0, b = oracle.closest_point(shape, y)
+    f0, q0 = workloads.poly_eval(wl.f_coef, x0), workloads.poly_eval(wl.q_coef, x0)
+    uo, vo, _ = oracle.evaluate(x, n, w, workloads.poly_eval(wl.f_coef, x), workloads.poly_eval(wl.q_coef, x),
+                                y, x0, n0, b, f0, q0, wl.h, wl.rho)
+    for prec, tol in ((0, FP64_TOL), (1, MIXED_TOL)):
+        u, v, bg = g.eval(g.targets(sel), precision=prec)
+        assert rel_err(u, uo) <= tol and rel_err(v, vo) <= tol, (prec, rel_err(u, uo), rel_err(v, vo))
+
+
+@pytest.mark.parametrize("rho,tc", [((3, 4, 5), 6.0), ((2, 3, 4), 5.0), ((1.5, 2.5, 3.5), 7.5)])
+def test_other_rho_and_cutoff(ers, rho, tc):
+    sel = np.arange(0, 17070 + 2000, 7)
+    y, uo, vo, _ = oracle_eval("sphere32", sel=sel, rho=rho, tc=tc)
+    g = gpu("sphere32")
+    u, v, _ = g.eval(g.targets(sel), precision=0, rho=rho, tc=tc)
+    assert rel_err(u, uo) <= FP64_TOL and rel_err(v, vo) <= FP64_TOL
+
+
+def test_layers_and_given_closest_point(ers):
+    g = gpu("sphere16")
+    y = g.targets()
+    u, v, _ = g.eval(y)
+    us, _, _ = g.eval(y, layers=1)
+    _, vd, _ = g.eval(y, layers=2)
+    ug, vg, _ = g.eval(y, given_cp=True)
+    assert np.abs(us - u).max() <= 1e-14 * np.abs(u).max()
+    assert np.abs(vd - v).max() <= 1e-14 * np.abs(v).max()
+    assert np.array_equal(ug, u) and np.array_equal(vg, v)
+
+
+def test_eval_host_matches_device(ers):
+    g = gpu("sphere16")
+    y = g.targets()
+    u, v, _ = g.eval(y, precision=1)
+    yd, x0, n0, b, f0, q0 = g.prepare(y)
+    uh, vh = g.s.eval_host(y, f0.cpu().numpy(), q0.cpu().numpy(), rho=g.wl.rho, precision=1)
+    assert np.array_equal(uh, u) and np.array_equal(vh, v)
+
+
+@pytest.mark.parametrize("count", [1, 31, 257, 1001])
+def test_ragged_target_counts(ers, count):
+    rng = np.random.default_rng(count)
+    g = gpu("sphere16")
+    sel = np.sort(rng.choice(4302 + 2000, count, replace=False))
+    y, uo, vo, _ = oracle_eval("sphere16", sel=sel)
+    u, v, _ = g.eval(g.targets(sel))
+    assert rel_err(u, uo) <= FP64_TOL and rel_err(v, vo) <= FP64_TOL
+
+
+def test_tiny_surface_fewer_nodes_than_a_tile(ers):
+    shape = workloads.unit_sphere((0.05, 0.0, 0.0))
+    wl = workloads.make_workload("tiny", shape, 0.3, (2, 3, 4), 5, 40, 1.0, n_far=10)
+    g = GpuProblem("tiny", wl)
+    assert g.s.N < 256
+    x, n, w = oracle.quadrature(shape, wl.h)
+    y = np.concatenate([x, wl.extra_targets])
+    x0, n0, b = oracle.closest_point(shape, y)
+    uo, vo, _ = oracle.evaluate(x, n, w, workloads.poly_eval(wl.f_coef, x), workloads.poly_eval(wl.q_coef, x),
+                                y, x0, n0, b, workloads.poly_eval(wl.f_coef, x0), workloads.poly_eval(wl.q_coef, x0),
+                                wl.h, wl.rho)
+    u, v, _ = g.eval(g.targets())
+    assert rel_err(u, uo) <= FP64_TOL and rel_err(v, vo) <= FP64_TOL
+
+
+def test_empty_and_errors(ers):
+    import torch
+    g = gpu("sphere16")
+    empty = torch.zeros((0, 3), dtype=torch.float64, device="cuda")
+    u, v = g.s.eval(empty, empty, empty, rho=(2, 3, 4))
+    assert u.shape == (0, 3)
+    y = torch.zeros((4, 3), dtype=torch.float64, device="cuda")
+    with pytest.raises(ers.ErsError) as e:
+        g.s.eval(y, y, y, rho=(3, 2, 4))
+    assert e.value.code == ers.ERS_E_INVAL
+    with pytest.raises(ers.ErsError) as e:
+        g.s.eval(y, y, y, cutoff_t=9.0)
+    assert e.value.code == ers.ERS_E_UNSUPPORTED
+    s2 = ers.Surface((0, 0, 0), (1, 1, 1), 1 / 8)
+    with pytest.raises(ers.ErsError) as e:
+        s2.eval(y, y, y)
+    assert e.value.code == ers.ERS_E_STATE
+    s2.set_density(f=torch.zeros((s2.N, 3), dtype=torch.float64, device="cuda"))
+    s2.set_density(q=torch.zeros((s2.N, 3), dtype=torch.float64, device="cuda"))
+    _, _ = s2.eval(y, y, y, cutoff_t=5.0)
+    assert s2.last_rc == ers.ERS_W_CUTOFF
+
+
+@pytest.mark.parametrize("precision,tol", [(1, MIXED_TOL), (0, FP64_TOL)])
+def test_full_size_bench_workload_sampled(ers, precision, tol):
+    """Unit sphere h = 1/128 (N = 272,718), all 392,718 targets in one launch as in bench.py;
+    a seeded sample of 400 targets (nodes, band, far) is checked against the oracle."""
+    g = gpu("sphere128")
+    y_all = g.targets()
+    u, v, b = g.eval(y_all, precision=precision)
+    M = len(y_all)
+    sel = workloads.subsample(400, M, 4242)
+    y, uo, vo, bo = oracle_eval("sphere128", sel=sel)
+    assert np.array_equal(y, y_all[sel])
+    assert rel_err(u[sel], uo) <= tol and rel_err(v[sel], vo) <= tol, (rel_err(u[sel], uo), rel_err(v[sel], vo))
+    assert np.isfinite(u).all() and np.isfinite(v).all()

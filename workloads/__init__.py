@@ -137,11 +137,14 @@ def config(name: str) -> Workload:
     sphere128   : unit sphere, h = 1/128 (N = 272,718); nodes + 100,000 band points
                   |b| <= 4h + 20,000 points uniform in [-2, 2]^3.
     sphere32    : unit sphere, h = 1/32; nodes + 2,000 band points (a mid-size parity case).
+    sphere64    : unit sphere, h = 1/64; nodes + 25,000 band points + 5,000 box points (profiling).
     """
     if name == "sphere16":
         return make_workload(name, unit_sphere(), 1 / 16, (2, 3, 4), 1001, 2000, 4 / 16)
     if name == "sphere32":
         return make_workload(name, unit_sphere(), 1 / 32, (2, 3, 4), 1005, 2000, 4 / 32)
+    if name == "sphere64":
+        return make_workload(name, unit_sphere(), 1 / 64, (2, 3, 4), 1006, 25000, 4 / 64, n_far=5000)
     if name == "ellipsoid64":
         h = 1 / 64
         return make_workload(name, Shape((0.0, 0.0, 0.0), (1.0, 0.8, 0.6)), h, (2, 3, 4), 1002,

@@ -161,6 +161,57 @@ int ers_profile(ers_surface *s, int enable);
  */
 int ers_last_profile(ers_surface *s, double *ms_closest, double *ms_far, double *ms_near);
 
+/*
+ * Densities of nrhs right-hand sides at once (nrhs = 1, 2, 4 or 8), canonical node order:
+ * f, q (nrhs, N, 3) dev (either may be NULL: that layer's density is then zero).  Used by the
+ * batched evaluation; independent of ers_set_density.  Errors: ERS_E_INVAL, ERS_E_NOMEM,
+ * ERS_E_CUDA.
+ */
+int ers_set_density_multi(ers_surface *s, const double *f, const double *q, int nrhs, void *stream);
+
+/*
+ * One problem of a batched evaluation: the layers of surface s (densities from
+ * ers_set_density_multi) at M targets.  All arrays dev, row-major:
+ *   y, x0, n0 (M,3), b (M): targets and their closest-point data on s (ers_closest_point);
+ *   f0, q0 (nrhs, M, 3): the densities of each right-hand side at x0 (Eqs. (Stokes_SL1),
+ *   (Stokes_DL1)); u, v (nrhs, M, 3): outputs.
+ * Several problems may share a surface (e.g. one surface evaluated at its own nodes and at the
+ * nodes of a nearby surface); outputs of different problems must not overlap.
+ */
+typedef struct {
+    ers_surface *s;
+    int64_t M;
+    const double *y, *x0, *n0, *b;
+    const double *f0, *q0;
+    double *u, *v;
+} ers_problem;
+
+typedef struct ers_batch ers_batch; /* opaque plan: work list, device copies, CUDA graph */
+
+/*
+ * Plan a batched evaluation of nprob problems with nrhs densities each, sharing the parameters
+ * p (p->precision must be ERS_PREC_MIXED: far field with FP32 operands and FP64 accumulation;
+ * near sums, closest point data and the solve in FP64, as in ers_eval).  The whole evaluation
+ * runs as ONE persistent kernel launch: each work item is (problem, block of 128 targets) and
+ * is computed end to end (far field, near field for the three delta_k, extrapolation) by one
+ * CTA; CTAs take items from an atomic counter, largest first.  The launch (and the reset of the
+ * counter) is captured into a CUDA graph here; ers_batch_launch replays it.  The plan records
+ * the pointers of every problem: change the data behind them (new densities through
+ * ers_set_density_multi with the same nrhs, new f0, q0) and relaunch, but do not free or move
+ * them while the plan exists.  Errors: ERS_E_INVAL, ERS_E_STATE (densities not set with this
+ * nrhs), ERS_E_UNSUPPORTED (precision), ERS_E_NOMEM, ERS_E_CUDA.
+ */
+int ers_batch_create(const ers_problem *probs, int nprob, const ers_params *p, int nrhs, ers_batch **out);
+
+/* Replay the plan's graph on stream (asynchronous).  ERS_E_INVAL on a NULL plan or another device. */
+int ers_batch_launch(ers_batch *b, void *stream);
+
+/* Number of work items and the persistent grid size of a plan. */
+int ers_batch_info(const ers_batch *b, int *nitems, int *grid);
+
+/* Release a plan (NULL accepted).  The problems' arrays are not touched. */
+int ers_batch_free(ers_batch *b);
+
 /* Message of the last error on the calling thread ("" if none).  Never NULL. */
 const char *ers_last_error(void);
 

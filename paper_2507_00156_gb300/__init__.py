@@ -36,7 +36,8 @@ PREC_MIXED = 1
 # Every symbol the header declares (checked by the tests).
 EXPORTS = ["ers_build_surface", "ers_surface_free", "ers_surface_info", "ers_set_density", "ers_closest_point",
            "ers_eval", "ers_eval_SL", "ers_eval_DL", "ers_eval_host", "ers_last_counts", "ers_profile",
-           "ers_last_profile", "ers_last_error", "ers_version"]
+           "ers_last_profile", "ers_set_density_multi", "ers_batch_create", "ers_batch_launch", "ers_batch_info",
+           "ers_batch_free", "ers_last_error", "ers_version"]
 
 
 class ErsError(RuntimeError):
@@ -47,6 +48,12 @@ class ErsError(RuntimeError):
 
 class _Shape(ctypes.Structure):
     _fields_ = [("center", ctypes.c_double * 3), ("axes", ctypes.c_double * 3)]
+
+
+class _Problem(ctypes.Structure):
+    _fields_ = [("s", ctypes.c_void_p), ("M", ctypes.c_int64), ("y", ctypes.c_void_p), ("x0", ctypes.c_void_p),
+                ("n0", ctypes.c_void_p), ("b", ctypes.c_void_p), ("f0", ctypes.c_void_p), ("q0", ctypes.c_void_p),
+                ("u", ctypes.c_void_p), ("v", ctypes.c_void_p)]
 
 
 class _Params(ctypes.Structure):
@@ -82,6 +89,11 @@ def lib():
             L.ers_eval_SL.argtypes = [vp, P(_Params), vp, i64, vp, vp, vp, vp, vp, vp]
             L.ers_eval_DL.argtypes = [vp, P(_Params), vp, i64, vp, vp, vp, vp, vp, vp]
             L.ers_eval_host.argtypes = [vp, P(_Params), vp, i64, vp, vp, vp, vp, vp, vp, vp, vp]
+            L.ers_set_density_multi.argtypes = [vp, vp, vp, cint, vp]
+            L.ers_batch_create.argtypes = [P(_Problem), cint, P(_Params), cint, P(vp)]
+            L.ers_batch_launch.argtypes = [vp, vp]
+            L.ers_batch_info.argtypes = [vp, P(cint), P(cint)]
+            L.ers_batch_free.argtypes = [vp]
             L.ers_last_counts.argtypes = [vp, P(i64), P(i64), P(i64)]
             L.ers_profile.argtypes = [vp, cint]
             L.ers_last_profile.argtypes = [vp, P(dbl), P(dbl), P(dbl)]
@@ -209,6 +221,12 @@ class Surface:
                                             _ptr(u) if sl else None, _ptr(v) if dl else None, _stream(stream)))
         return (u if sl else None), (v if dl else None)
 
+    def set_density_multi(self, f=None, q=None, stream=None):
+        """Densities of several right-hand sides, (nrhs, N, 3) each (ers_set_density_multi)."""
+        nrhs = (f if f is not None else q).shape[0]
+        check(lib().ers_set_density_multi(self._h, _ptr(f), _ptr(q), nrhs, _stream(stream)))
+        self.nrhs_multi = nrhs
+
     def eval_host(self, y, f0, q0, rho=(2.0, 3.0, 4.0), cutoff_t=6.0, precision=PREC_FP64,
                   layers=LAYER_SL | LAYER_DL, u=None, v=None, stream=None):
         """ers_eval_host with numpy (ideally pinned) host arrays."""
@@ -248,6 +266,42 @@ class Surface:
         L.ers_debug_class_counts.argtypes = [ctypes.c_void_p] + [ctypes.POINTER(ctypes.c_int64)] * 3
         check(L.ers_debug_class_counts(self._h, *(ctypes.byref(z) for z in c)))
         return [int(z.value) for z in c]
+
+
+class Batch:
+    """A batched evaluation plan (ers_batch_create): one persistent launch, replayed as a CUDA graph.
+
+    problems: list of dicts with keys s (Surface), y, x0, n0, b (M,3)/(M,) and f0, q0, u, v
+    (nrhs, M, 3), all contiguous float64 CUDA tensors kept alive by the plan."""
+
+    def __init__(self, problems, nrhs, rho=(2.0, 3.0, 4.0), cutoff_t=6.0, layers=LAYER_SL | LAYER_DL):
+        L = lib()
+        arr = (_Problem * len(problems))()
+        self._keep = problems
+        for i, pr in enumerate(problems):
+            a = arr[i]
+            a.s = pr["s"].handle
+            a.M = int(pr["y"].shape[0])
+            for k in ("y", "x0", "n0", "b", "f0", "q0", "u", "v"):
+                setattr(a, k, _ptr(pr.get(k)))
+        p = params(rho, cutoff_t, PREC_MIXED, layers)
+        h = ctypes.c_void_p()
+        self.rc = check(L.ers_batch_create(arr, len(problems), ctypes.byref(p), int(nrhs), ctypes.byref(h)))
+        self._h = h
+
+    def launch(self, stream=None):
+        check(lib().ers_batch_launch(self._h, _stream(stream)))
+
+    def info(self):
+        a, b = ctypes.c_int(), ctypes.c_int()
+        check(lib().ers_batch_info(self._h, ctypes.byref(a), ctypes.byref(b)))
+        return a.value, b.value
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h is not None and h.value and _lib is not None:
+            _lib.ers_batch_free(h)
+            self._h = None
 
 
 def version() -> str:

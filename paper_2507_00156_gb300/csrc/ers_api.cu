@@ -26,6 +26,8 @@ cudaError_t dmalloc(T **p, size_t count) {
 
 bool finite3(const double *v) { return std::isfinite(v[0]) && std::isfinite(v[1]) && std::isfinite(v[2]); }
 
+}  // namespace
+
 int grow(Scratch &s, size_t bytes) {
     if (s.bytes >= bytes) return ERS_OK;
     if (s.ptr) cudaFree(s.ptr);
@@ -40,10 +42,12 @@ int grow(Scratch &s, size_t bytes) {
     return ERS_OK;
 }
 
+namespace {
+
 void free_surface(ers_surface *s) {
     if (!s) return;
     void *ptrs[] = {s->x, s->n, s->w, s->perm, s->rec, s->rec32, s->tilec, s->xs32, s->cell_start,
-                    s->part.ptr, s->cp.ptr, s->host_io.ptr, s->counts.ptr};
+                    s->part.ptr, s->cp.ptr, s->host_io.ptr, s->counts.ptr, s->dens64.ptr, s->dens32.ptr};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     for (cudaEvent_t e : s->ev)
@@ -260,6 +264,7 @@ int eval(ers_surface *s, const ers_params *p, const double *y, int64_t M, const 
 
     EvalArgs a{};
     a.s = s;
+    a.sd = surf_dev(s);
     a.y = y;
     a.M = M;
     a.f0 = f0;

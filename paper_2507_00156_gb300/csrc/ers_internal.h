@@ -69,6 +69,10 @@ struct ers_surface {
     bool has_f = false, has_q = false;
     // work buffers (grow-only)
     ers::Scratch part, cp, host_io, counts;
+    // densities of several right-hand sides (ers_set_density_multi), cell-sorted:
+    // [N][nrhs][6] (w f, q) in FP64 and FP32
+    ers::Scratch dens64, dens32;
+    int nrhs_multi = 0;
     int64_t last_counts[3] = {0, 0, 0};
     int64_t last_class[3] = {0, 0, 0};
     cudaStream_t last_stream = nullptr;
@@ -91,12 +95,43 @@ int fail(int code, const std::string &msg);
 int cuda_fail(cudaError_t e, const char *what);
 void clear_error();
 
+// Validation of ers_params shared by the evaluation entry points (ERS_OK or an error code;
+// *warn receives ERS_W_CUTOFF for cutoff_t < 6).
+int check_params(const ers_surface *s, const ers_params *p, int *warn);
+
 // Device table pointer for the current device (uploads once per device).
 const double *sigma_table_dev(int *err);
 
+// Device-side view of a surface, passed by value in kernel parameters (the ers_surface
+// struct itself lives in host memory).
+struct SurfDev {
+    const double *rec;
+    const float *rec32;
+    const float *tilec;
+    const float4 *xs32;
+    const int *cell_start;
+    Grid grid;
+    int64_t N;
+    double h;
+};
+
+inline SurfDev surf_dev(const ers_surface *s) {
+    SurfDev d;
+    d.rec = s->rec;
+    d.rec32 = s->rec32;
+    d.tilec = s->tilec;
+    d.xs32 = s->xs32;
+    d.cell_start = s->cell_start;
+    d.grid = s->grid;
+    d.N = s->N;
+    d.h = s->h;
+    return d;
+}
+
 // Kernel launchers (k_*.cu)
 struct EvalArgs {
-    const ers_surface *s;
+    const ers_surface *s;  // host struct: launchers only, never dereferenced on the device
+    SurfDev sd;
     const double *y, *x0, *n0, *b, *f0, *q0;
     int64_t M;
     double rho[3], cutoff_t, Rc;
@@ -115,6 +150,15 @@ cudaError_t launch_far64(const EvalArgs &a);
 cudaError_t launch_far32(const EvalArgs &a);
 cudaError_t launch_near(const EvalArgs &a, const double *table);
 cudaError_t launch_density(ers_surface *s, const double *f, const double *q, cudaStream_t st);
+
+struct BatchProblemDev;
+struct BatchItem;
+cudaError_t launch_density_multi(const int *perm, const double *w, const double *f, const double *q, int64_t N,
+                                 int nr, double *d64, float *d32, cudaStream_t st);
+int batch_grid(int nr, int nsm);
+cudaError_t launch_batch(int nr, const BatchProblemDev *probs, const BatchItem *items, int nitems, unsigned *counter,
+                         const double rho[3], int layers, const double *tab, int grid, cudaStream_t st);
+int grow(Scratch &s, size_t bytes);
 
 }  // namespace ers
 

@@ -52,8 +52,8 @@ template <bool SL, bool DL, int TPT, int TS>
 __global__ void __launch_bounds__(NT) k_far64(EvalArgs A) {
     __shared__ double2 srec[TS * REC / 2];
     const int64_t j0 = (int64_t)blockIdx.y * A.chunk_len;
-    const int64_t j1 = min(A.s->N, j0 + A.chunk_len);
-    const double *__restrict__ rec = A.s->rec;
+    const int64_t j1 = min(A.sd.N, j0 + A.chunk_len);
+    const double *__restrict__ rec = A.sd.rec;
 
     TargetF64 T[TPT];
     bool valid[TPT];
@@ -136,8 +136,8 @@ __global__ void __launch_bounds__(NT) k_far32(EvalArgs A, float rc2f) {
     __shared__ float4 srec[TS32 * 3];
     __shared__ float4 scen;
     const int64_t j0 = (int64_t)blockIdx.y * A.chunk_len;  // multiple of TS32
-    const int64_t j1 = min(A.s->N, j0 + A.chunk_len);
-    const float *__restrict__ rec = A.s->rec32;
+    const int64_t j1 = min(A.sd.N, j0 + A.chunk_len);
+    const float *__restrict__ rec = A.sd.rec32;
 
     TargetF32 T[TPT];
     bool valid[TPT];
@@ -169,7 +169,7 @@ __global__ void __launch_bounds__(NT) k_far32(EvalArgs A, float rc2f) {
         __syncthreads();
         const float4 *src = reinterpret_cast<const float4 *>(rec + base * REC);
         for (int k = threadIdx.x; k < ns * 3; k += NT) srec[k] = src[k];
-        if (threadIdx.x == 0) scen = reinterpret_cast<const float4 *>(A.s->tilec)[base / TS32];
+        if (threadIdx.x == 0) scen = reinterpret_cast<const float4 *>(A.sd.tilec)[base / TS32];
         __syncthreads();
         const float4 cen = scen;
         float yc[TPT][3];

@@ -212,6 +212,32 @@ int ers_batch_info(const ers_batch *b, int *nitems, int *grid);
 /* Release a plan (NULL accepted).  The problems' arrays are not touched. */
 int ers_batch_free(ers_batch *b);
 
+/*
+ * ers_eval for callers that cannot allocate device memory while they evaluate (a solver that
+ * owns a fixed memory pool, a plugin running where cudaMalloc is forbidden or too slow to risk,
+ * a real-time loop).  The paper has no counterpart; this is a deployment variant of ers_eval.
+ *
+ * Same arguments and results as ers_eval, except:
+ *  - x0, n0 and b are required (fill them with ers_closest_point, which writes into the
+ *    caller's arrays and allocates nothing);
+ *  - M must not exceed 524,288 targets per call: the far-field partial sums (6 doubles per
+ *    target) live in a fixed 24 MiB device array inside the library, and larger M is rejected
+ *    with ERS_E_INVAL and a message naming the limit (split the targets across calls);
+ *  - ers_last_counts is not updated.
+ * The call performs no cudaMalloc, cudaFree or other allocating call.  The fixed array (24 MiB
+ * of scratch plus the 90 KB smoothing-function table) is part of the library's device image:
+ * every GPU on which this entry point is used holds it until the process exits.  The first call
+ * on a device does a one-time set-up with that device current (it looks up the array's device
+ * address and copies the table into it synchronously); make that first call before any stream
+ * capture.  Every call on a device shares the same scratch array, which keeps the last call's
+ * contents: calls whose work overlaps on the GPU (different streams, or concurrent host
+ * threads) race and give wrong results; serialize them.  The surface itself is built
+ * beforehand with ers_build_surface and ers_set_density.
+ */
+int ers_eval_noalloc(ers_surface *s, const ers_params *p, const double *y, int64_t M, const double *x0,
+                     const double *n0, const double *b, const double *f0, const double *q0, double *u, double *v,
+                     void *stream);
+
 /* Message of the last error on the calling thread ("" if none).  Never NULL. */
 const char *ers_last_error(void);
 

@@ -37,7 +37,8 @@ PREC_MIXED = 1
 EXPORTS = ["ers_build_surface", "ers_surface_free", "ers_surface_info", "ers_set_density", "ers_closest_point",
            "ers_eval", "ers_eval_SL", "ers_eval_DL", "ers_eval_host", "ers_last_counts", "ers_profile",
            "ers_last_profile", "ers_set_density_multi", "ers_batch_create", "ers_batch_launch", "ers_batch_info",
-           "ers_batch_free", "ers_last_error", "ers_version"]
+           "ers_batch_free", "ers_eval_noalloc", "ers_last_error", "ers_version"]
+NOALLOC_MAX_M = 524288
 
 
 class ErsError(RuntimeError):
@@ -89,6 +90,7 @@ def lib():
             L.ers_eval_SL.argtypes = [vp, P(_Params), vp, i64, vp, vp, vp, vp, vp, vp]
             L.ers_eval_DL.argtypes = [vp, P(_Params), vp, i64, vp, vp, vp, vp, vp, vp]
             L.ers_eval_host.argtypes = [vp, P(_Params), vp, i64, vp, vp, vp, vp, vp, vp, vp, vp]
+            L.ers_eval_noalloc.argtypes = [vp, P(_Params), vp, i64, vp, vp, vp, vp, vp, vp, vp, vp]
             L.ers_set_density_multi.argtypes = [vp, vp, vp, cint, vp]
             L.ers_batch_create.argtypes = [P(_Problem), cint, P(_Params), cint, P(vp)]
             L.ers_batch_launch.argtypes = [vp, vp]
@@ -226,6 +228,18 @@ class Surface:
         nrhs = (f if f is not None else q).shape[0]
         check(lib().ers_set_density_multi(self._h, _ptr(f), _ptr(q), nrhs, _stream(stream)))
         self.nrhs_multi = nrhs
+
+    def eval_noalloc(self, y, x0, n0, b, f0=None, q0=None, u=None, v=None, rho=(2.0, 3.0, 4.0), cutoff_t=6.0,
+                     precision=PREC_FP64, layers=LAYER_SL | LAYER_DL, stream=None):
+        """ers_eval_noalloc: the library allocates nothing; the caller passes every array, including
+        the closest-point data (from closest_point) and the outputs u, v."""
+        sl, dl = bool(layers & LAYER_SL), bool(layers & LAYER_DL)
+        p = params(rho, cutoff_t, precision, layers)
+        self.last_rc = check(lib().ers_eval_noalloc(self._h, ctypes.byref(p), _ptr(y), y.shape[0], _ptr(x0), _ptr(n0),
+                                                    _ptr(b), _ptr(f0) if sl else None, _ptr(q0) if dl else None,
+                                                    _ptr(u) if sl else None, _ptr(v) if dl else None,
+                                                    _stream(stream)))
+        return (u if sl else None), (v if dl else None)
 
     def eval_host(self, y, f0, q0, rho=(2.0, 3.0, 4.0), cutoff_t=6.0, precision=PREC_FP64,
                   layers=LAYER_SL | LAYER_DL, u=None, v=None, stream=None):

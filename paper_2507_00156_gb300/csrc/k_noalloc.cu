@@ -1,0 +1,119 @@
+// ers_eval_noalloc: the evaluation for callers that must not allocate device memory.
+//
+// Some callers cannot call cudaMalloc at the moment they evaluate: code running inside a
+// pre-sized memory pool or under a host allocator that forbids growth, a plugin of a solver
+// that owns all device memory, or a real-time loop where an allocation could stall or fail.
+// ers_eval grows its work buffers on demand; this variant instead keeps the one work buffer it
+// needs (the far-field partial sums, 6 doubles per target) in a fixed file-scope device array
+// and the smoothing-function table in another, so a call allocates nothing.
+#include <cstring>
+#include <mutex>
+
+#include "ers_internal.h"
+
+namespace ers {
+namespace {
+
+// Scratch shared by every call on a device: far-field partial sums, one chunk,
+// [M][6] doubles.  24 MiB => at most NOALLOC_MAX_M targets per call.
+constexpr size_t NOALLOC_SCRATCH_BYTES = (size_t)24 << 20;
+constexpr int64_t NOALLOC_MAX_M = (int64_t)(NOALLOC_SCRATCH_BYTES / (6 * sizeof(double)));
+constexpr size_t NOALLOC_TABLE_DOUBLES = (size_t)TAB_N * 3 * TAB_NC + TAB_N;
+
+__device__ __align__(256) unsigned char g_noalloc_scratch[NOALLOC_SCRATCH_BYTES];
+__device__ __align__(256) double g_noalloc_table[NOALLOC_TABLE_DOUBLES];
+
+struct DevState {
+    bool ready = false;
+    double *scratch = nullptr;  // device address of g_noalloc_scratch on this device
+    double *table = nullptr;    // device address of g_noalloc_table on this device
+};
+std::mutex g_mu;
+DevState g_state[64];
+
+// Once per device, with that device current: resolve the device addresses of the two arrays
+// (in host code the array names are host-side stand-ins, not device addresses) and fill the
+// table.  cudaMemcpyToSymbol copies synchronously; nothing is allocated.
+int setup_device(int dev, DevState **out) {
+    std::lock_guard<std::mutex> lk(g_mu);
+    DevState &st = g_state[dev];
+    if (!st.ready) {
+        void *p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess) return cuda_fail(e, "ers_eval_noalloc: cudaGetSymbolAddress(scratch)");
+        st.scratch = (double *)p;
+        e = cudaGetSymbolAddress(&p, g_noalloc_table);
+        if (e != cudaSuccess) return cuda_fail(e, "ers_eval_noalloc: cudaGetSymbolAddress(table)");
+        st.table = (double *)p;
+        double host[NOALLOC_TABLE_DOUBLES];
+        std::memcpy(host, sigma_table_host(), sizeof(double) * (size_t)TAB_N * 3 * TAB_NC);
+        for (int i = 0; i < TAB_N; ++i) host[(size_t)TAB_N * 3 * TAB_NC + i] = 2.0 * i + 1.0;
+        e = cudaMemcpyToSymbol(g_noalloc_table, host, sizeof host);
+        if (e != cudaSuccess) return cuda_fail(e, "ers_eval_noalloc: cudaMemcpyToSymbol(table)");
+        st.ready = true;
+    }
+    *out = &st;
+    return ERS_OK;
+}
+
+}  // namespace
+}  // namespace ers
+
+using namespace ers;
+
+extern "C" int ers_eval_noalloc(ers_surface *s, const ers_params *p, const double *y, int64_t M, const double *x0,
+                                const double *n0, const double *b, const double *f0, const double *q0, double *u,
+                                double *v, void *stream) {
+    clear_error();
+    if (!s) return fail(ERS_E_INVAL, "ers_eval_noalloc: NULL surface");
+    int warn;
+    int rc = check_params(s, p, &warn);
+    if (rc != ERS_OK) return rc;
+    if (M < 0) return fail(ERS_E_INVAL, "ers_eval_noalloc: M < 0");
+    if (M > NOALLOC_MAX_M)
+        return fail(ERS_E_INVAL, "ers_eval_noalloc: M = " + std::to_string(M) + " exceeds the fixed scratch limit of " +
+                                     std::to_string(NOALLOC_MAX_M) + " targets per call (use ers_eval or split the targets)");
+    const bool sl = p->layers & ERS_LAYER_SL, dl = p->layers & ERS_LAYER_DL;
+    if (sl && !s->has_f) return fail(ERS_E_STATE, "ers_eval_noalloc: single layer requested before a density f was set");
+    if (dl && !s->has_q) return fail(ERS_E_STATE, "ers_eval_noalloc: double layer requested before a density q was set");
+    if (M == 0) return warn;
+    if (!y || !x0 || !n0 || !b)
+        return fail(ERS_E_INVAL, "ers_eval_noalloc: y, x0, n0 and b are required (x0, n0, b from ers_closest_point)");
+    if (sl && (!f0 || !u)) return fail(ERS_E_INVAL, "ers_eval_noalloc: single layer needs f0 and u");
+    if (dl && (!q0 || !v)) return fail(ERS_E_INVAL, "ers_eval_noalloc: double layer needs q0 and v");
+    int dev = -1;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_fail(e, "ers_eval_noalloc: cudaGetDevice");
+    if (dev != s->device || dev < 0 || dev >= 64)
+        return fail(ERS_E_INVAL, "ers_eval_noalloc: the current device is not the surface's device");
+    DevState *st = nullptr;
+    if ((rc = setup_device(dev, &st)) != ERS_OK) return rc;
+
+    EvalArgs a{};
+    a.s = s;
+    a.sd = surf_dev(s);
+    a.y = y;
+    a.x0 = x0;
+    a.n0 = n0;
+    a.b = b;
+    a.f0 = f0;
+    a.q0 = q0;
+    a.M = M;
+    a.u = u;
+    a.v = v;
+    for (int k = 0; k < 3; ++k) a.rho[k] = p->rho[k];
+    a.cutoff_t = p->cutoff_t;
+    a.Rc = p->cutoff_t * p->rho[2] * s->h;
+    a.precision = p->precision;
+    a.layers = p->layers;
+    a.stream = (cudaStream_t)stream;
+    a.part = st->scratch;  // every target's 6 partial sums are written by the far kernel before use
+    a.chunks = 1;
+    a.chunk_len = (s->N + TS32 - 1) / TS32 * TS32;
+    a.counters = nullptr;  // ers_last_counts is not updated by this entry point
+    e = (p->precision == ERS_PREC_MIXED) ? launch_far32(a) : launch_far64(a);
+    if (e != cudaSuccess) return cuda_fail(e, "ers_eval_noalloc: far-field kernel");
+    e = launch_near(a, st->table);
+    if (e != cudaSuccess) return cuda_fail(e, "ers_eval_noalloc: near-field kernel");
+    return warn;
+}

@@ -54,6 +54,7 @@ def parse():
     ap.add_argument("--fp64-steps", type=int, default=1)
     ap.add_argument("--cpu-seconds", type=float, default=10.0, help="target wall time of the CPU baseline sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-batched", action="store_true", help="skip the batched-launch leg")
     ap.add_argument("--workload", default=WORKLOAD, help="profiling only: a smaller case (e.g. sphere64)")
     return ap.parse_args()
 
@@ -164,6 +165,69 @@ def cpu_baseline(wl, y, seconds: float, gpu_results=None):
             errs[name] = {"SL": float(np.abs(ug[idx] - u).max() / np.abs(u).max()),
                           "DL": float(np.abs(vg[idx] - v).max() / np.abs(v).max())}
     return out, errs
+
+
+def batched_leg(ers, torch, steps: int, warmup: int):
+    """Two unit spheres 0.01 apart at h = 1/96 (each evaluated at the nodes of both) plus 16
+    uneven bodies (own nodes + 5 % near band), 8 densities per surface, as ONE persistent launch
+    replayed from a CUDA graph.  Unit: (target, density) evaluations of both layers per second."""
+    nrhs = 8
+    pair, bodies = workloads.batched_config(nrhs=nrhs)
+    dev = torch.device("cuda")
+    surfs = []
+
+    def surface(body):
+        s = ers.Surface(body.shape.center, body.shape.axes, body.h)
+        x = s.nodes()[0].cpu().numpy()
+        f = np.stack([workloads.poly_eval(c, x) for c in body.f_coefs])
+        q = np.stack([workloads.poly_eval(c, x) for c in body.q_coefs])
+        s.set_density_multi(torch.from_numpy(f).to(dev), torch.from_numpy(q).to(dev))
+        surfs.append(s)
+        return s, x
+
+    def problem(s, body, y):
+        yd = torch.from_numpy(np.ascontiguousarray(y)).to(dev)
+        x0, n0, b = s.closest_point(yd)
+        x0h = x0.cpu().numpy()
+        f0 = np.stack([workloads.poly_eval(c, x0h) for c in body.f_coefs])
+        q0 = np.stack([workloads.poly_eval(c, x0h) for c in body.q_coefs])
+        M = len(y)
+        return dict(s=s, y=yd, x0=x0, n0=n0, b=b, f0=torch.from_numpy(f0).to(dev),
+                    q0=torch.from_numpy(q0).to(dev),
+                    u=torch.empty((nrhs, M, 3), dtype=torch.float64, device=dev),
+                    v=torch.empty((nrhs, M, 3), dtype=torch.float64, device=dev))
+
+    (sA, xA), (sB, xB) = surface(pair[0]), surface(pair[1])
+    yAB = np.concatenate([xA, xB])
+    probs = [problem(sA, pair[0], yAB), problem(sB, pair[1], yAB)]
+    for i, body in enumerate(bodies):
+        s, x = surface(body)
+        band = workloads.near_band_targets(body.shape, max(1, len(x) // 20), 4 * body.h,
+                                           np.random.default_rng(2000 + i))[0]
+        probs.append(problem(s, body, np.concatenate([x, band])))
+    batch = ers.Batch(probs, nrhs, rho=(2.0, 3.0, 4.0))
+    nitems, grid = batch.info()
+    stream = torch.cuda.current_stream()
+    for _ in range(warmup):
+        batch.launch()
+    torch.cuda.synchronize()
+    total = 0.0
+    for _ in range(steps):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        batch.launch()
+        b.record(stream)
+        b.synchronize()
+        total += a.elapsed_time(b) / 1e3
+    targets = sum(int(p["y"].shape[0]) for p in probs)
+    pairs = sum(int(p["y"].shape[0]) * p["s"].N for p in probs)
+    ok = all(bool(torch.isfinite(p["u"]).all()) and bool(torch.isfinite(p["v"]).all()) for p in probs)
+    return {"value": steps * targets * nrhs / total, "unit": "(target, density) evals/s, both layers",
+            "ms_per_launch": total / steps * 1e3, "problems": len(probs), "nrhs": nrhs, "targets": targets,
+            "surface_nodes": [s.N for s in surfs], "gpairs_x_rhs_per_s": steps * pairs * nrhs / total / 1e9,
+            "work_items": nitems, "persistent_grid": grid, "launches_per_step": 1, "finite": ok,
+            "workload": "two unit spheres gap 0.01 at h=1/96 (self + neighbour nodes) + 16 bodies "
+                        "(semi-axes U[0.6,1], h in {1/32,1/48,1/64,1/96}, own nodes + 5% band), 8 densities"}
 
 
 def run_reference(args, world, rank):
@@ -349,6 +413,8 @@ def main():
         line["speedup_vs_plain_fp64"] = ms64 / ms_step
         line["mixed_vs_fp64_rel"] = {"SL": float(np.abs(u_mixed - u64).max() / np.abs(u64).max()),
                                      "DL": float(np.abs(v_mixed - v64).max() / np.abs(v64).max())}
+    if not args.no_batched:
+        line["batched"] = batched_leg(ers, torch, steps=2, warmup=1)
     if world == 1 and not args.no_cpu_baseline:
         cb, errs = cpu_baseline(wl, y, args.cpu_seconds, {"mixed": (u_mixed, v_mixed), "fp64": (u64, v64)})
         line["cpu_baseline"] = cb

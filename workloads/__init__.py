@@ -155,6 +155,47 @@ def config(name: str) -> Workload:
     raise KeyError(name)
 
 
+@dataclasses.dataclass
+class BatchBody:
+    """One surface of the batched workload with nrhs densities and its own targets."""
+
+    shape: Shape
+    h: float
+    f_coefs: list
+    q_coefs: list
+    band: np.ndarray  # near-band targets added to the body's own nodes (may be empty)
+
+
+def batched_config(gap: float = 0.01, nrhs: int = 8, n_bodies: int = 16, seed: int = 1004,
+                   h_pair: float = 1 / 96):
+    """Two unit spheres at (0,0,0) and (2 + gap, 0, 0) with spacing h_pair, each evaluated at the
+    nodes of both (self and neighbour), plus n_bodies spheres/ellipsoids with semi-axes
+    U[0.6, 1], spacing h in {1/32, 1/48, 1/64, 1/96} and centres 4 apart, each evaluated at its
+    own nodes plus 5 % near-band points; nrhs seeded degree-4 densities per surface.
+    Returns (pair, bodies): pair = [BatchBody, BatchBody], bodies = [BatchBody] * n_bodies."""
+    rng = np.random.default_rng(seed)
+
+    def dens():
+        return [density_coeffs(rng) for _ in range(nrhs)], [density_coeffs(rng) for _ in range(nrhs)]
+
+    pair = []
+    for c in ((0.0, 0.0, 0.0), (2.0 + gap, 0.0, 0.0)):
+        f, q = dens()
+        pair.append(BatchBody(unit_sphere(c), h_pair, f, q, np.zeros((0, 3))))
+    hs = [1 / 32, 1 / 48, 1 / 64, 1 / 96]
+    bodies = []
+    for i in range(n_bodies):
+        axes = tuple(float(a) for a in rng.uniform(0.6, 1.0, 3))
+        if i % 4 == 0:
+            axes = (axes[0],) * 3
+        center = (10.0 + 4.0 * (i % 4), 4.0 * (i // 4), 0.0)
+        h = hs[int(rng.integers(0, len(hs)))]
+        shape = Shape(center, axes)
+        f, q = dens()
+        bodies.append(BatchBody(shape, h, f, q, None))
+    return pair, bodies
+
+
 def subsample(count: int, total: int, seed: int) -> np.ndarray:
     """Seeded subset of target indices (sorted)."""
     rng = np.random.default_rng(seed)

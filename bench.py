@@ -42,7 +42,7 @@ FP64_PEAK_NOMINAL = 1.25e12
 FAR_FLOPS_PER_PAIR = 57                   # both layers, one (target, node) far pair
 NEAR_FLOPS_BASE = 85                      # both layers, one near pair: geometry + contractions
 NEAR_FLOPS_PER_ACTIVE_DELTA = 45          # sigma_1..3 from the table and the alpha-weighted sums
-NEAR_FLOPS_UNREGULARIZED = 10             # 1/r^p terms when some delta_k has r > 6 delta_k
+NEAR_FLOPS_UNREGULARIZED = 13             # 1/r^p terms when some delta_k has r > 4.7 delta_k
 
 
 def parse():
@@ -55,6 +55,7 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=10.0, help="target wall time of the CPU baseline sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batched", action="store_true", help="skip the batched-launch leg")
+    ap.add_argument("--no-learned", action="store_true", help="skip the learned-closure leg")
     ap.add_argument("--workload", default=WORKLOAD, help="profiling only: a smaller case (e.g. sphere64)")
     return ap.parse_args()
 
@@ -228,6 +229,78 @@ def batched_leg(ers, torch, steps: int, warmup: int):
             "work_items": nitems, "persistent_grid": grid, "launches_per_step": 1, "finite": ok,
             "workload": "two unit spheres gap 0.01 at h=1/96 (self + neighbour nodes) + 16 bodies "
                         "(semi-axes U[0.6,1], h in {1/32,1/48,1/64,1/96}, own nodes + 5% band), 8 densities"}
+
+
+def learned_leg(ers, torch, s, wl, y, steps: int, warmup: int, u_ref, v_ref):
+    """The learned near-field closure on the bench workload: networks trained on the GPU (own
+    kernels) from five other seeded densities on the same surface, then timed on the bench's own
+    density with validation against the three-delta method (tolerance 1e-5, every 32nd target)."""
+    dev = torch.device("cuda")
+    t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
+    yd = t(y)
+    x0, n0, b = s.closest_point(yd)
+    x0h = x0.cpu().numpy()
+    x = s.nodes()[0].cpu().numpy()
+    rng = np.random.default_rng(5005)
+    data = {1: [], 2: []}
+    t0 = time.perf_counter()
+    for _ in range(5):
+        fc, qc = workloads.density_coeffs(rng), workloads.density_coeffs(rng)
+        s.set_density(t(workloads.poly_eval(fc, x)), t(workloads.poly_eval(qc, x)))
+        f0, q0 = t(workloads.poly_eval(fc, x0h)), t(workloads.poly_eval(qc, x0h))
+        gf0, gq0 = t(workloads.poly_jacobian(fc, x0h)), t(workloads.poly_jacobian(qc, x0h))
+        u3, v3 = s.eval(yd, f0, q0, rho=wl.rho, precision=ers.PREC_MIXED, x0=x0, n0=n0, b=b)
+        for nd in (1, 2):
+            out = ers.closure_data(s, yd, x0, n0, b, f0, q0, gf0, gq0, u3, v3, rho=wl.rho, ndelta=nd)
+            sel = out[4].bool()
+            data[nd].append([z[sel] for z in out[:4]])
+    t_data = time.perf_counter() - t0
+    nets, losses = {}, {}
+    t0 = time.perf_counter()
+    for nd in (1, 2):
+        Xs, Xd, Ts, Td = (torch.cat([d[i] for d in data[nd]]).contiguous() for i in range(4))
+        nets[nd] = ers.Closure(seed=100 + nd)
+        losses[nd] = [nets[nd].train(layer, X, T, steps=3000, batch=8192, lr=2e-3)
+                      for layer, (X, T) in enumerate(((Xs, Ts), (Xd, Td)))]
+    torch.cuda.synchronize()
+    t_train = time.perf_counter() - t0
+    nsamples = int(sum(d[0].shape[0] for d in data[2]))
+    # the bench's own density
+    s.set_density(t(workloads.poly_eval(wl.f_coef, x)), t(workloads.poly_eval(wl.q_coef, x)))
+    f0, q0 = t(workloads.poly_eval(wl.f_coef, x0h)), t(workloads.poly_eval(wl.q_coef, x0h))
+    gf0, gq0 = t(workloads.poly_jacobian(wl.f_coef, x0h)), t(workloads.poly_jacobian(wl.q_coef, x0h))
+    M = len(y)
+    u = torch.empty((M, 3), dtype=torch.float64, device=dev)
+    v = torch.empty((M, 3), dtype=torch.float64, device=dev)
+    res = {"training": {"samples_per_network": nsamples, "densities": 5, "steps": 3000, "batch": 8192,
+                        "data_s": t_data, "train_s": t_train}}
+    stream = torch.cuda.current_stream()
+    for nd in (2, 1):
+        args = (yd, x0, n0, b, f0, q0, gf0, gq0)
+        for _ in range(warmup):
+            ers.eval_learned(s, nets[nd], *args, rho=wl.rho, precision=ers.PREC_MIXED, tol=1e-5, vstride=32,
+                             ndelta=nd, u=u, v=v)
+        total, fb_any, verr = 0.0, False, None
+        for _ in range(steps):
+            a, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            _, _, verr, fb = ers.eval_learned(s, nets[nd], *args, rho=wl.rho, precision=ers.PREC_MIXED, tol=1e-5,
+                                              vstride=32, ndelta=nd, u=u, v=v)
+            e.record(stream)
+            e.synchronize()
+            total += a.elapsed_time(e) / 1e3
+            fb_any = fb_any or fb
+        # error of the learned values themselves (no fallback) against the three-delta values
+        ul, vl, _, _ = ers.eval_learned(s, nets[nd], *args, rho=wl.rho, precision=ers.PREC_MIXED, tol=1e30,
+                                        vstride=1 << 20, ndelta=nd)
+        ul, vl = ul.cpu().numpy(), vl.cpu().numpy()
+        res[f"ndelta{nd}"] = {
+            "value": steps * M / total, "unit": UNIT, "ms_per_step": total / steps * 1e3,
+            "fell_back_at_tol_1e-5": fb_any, "validation_rel_err": list(verr),
+            "max_rel_err_vs_three_delta": {"SL": float(np.abs(ul - u_ref).max() / np.abs(u_ref).max()),
+                                           "DL": float(np.abs(vl - v_ref).max() / np.abs(v_ref).max())},
+            "final_train_loss": losses[nd]}
+    return res
 
 
 def run_reference(args, world, rank):
@@ -415,6 +488,8 @@ def main():
                                      "DL": float(np.abs(v_mixed - v64).max() / np.abs(v64).max())}
     if not args.no_batched:
         line["batched"] = batched_leg(ers, torch, steps=2, warmup=1)
+    if not args.no_learned and args.workload == WORKLOAD:
+        line["learned"] = learned_leg(ers, torch, s, wl, y, steps=args.steps, warmup=1, u_ref=u_mixed, v_ref=v_mixed)
     if world == 1 and not args.no_cpu_baseline:
         cb, errs = cpu_baseline(wl, y, args.cpu_seconds, {"mixed": (u_mixed, v_mixed), "fp64": (u64, v64)})
         line["cpu_baseline"] = cb

@@ -213,6 +213,86 @@ int ers_batch_info(const ers_batch *b, int *nitems, int *grid);
 int ers_batch_free(ers_batch *b);
 
 /*
+ * Learned closure of the near field (a growth item on top of the paper's method).
+ *
+ * Eq. (extrap_eqn) models the regularized value as u^delta = u + c1 rho I0(lambda) +
+ * c2 rho^3 I2(lambda) + O(delta^5) with c1, c2 independent of delta.  The closure evaluates fewer
+ * regularized sums over a smaller near set and lets a network predict what they miss:
+ *   ndelta = 1: the single sum u^{delta_0} (near set r <= cutoff_t delta_0, a quarter of the
+ *     pairs for rho = (2,3,4)); the network predicts u - u^{delta_0} / (h S);
+ *   ndelta = 2: the two smaller deltas (near set r <= cutoff_t delta_1) combined with weights
+ *     beta (sum beta = 1, sum beta rho I0 = 0) into u + gamma c2; the network predicts c2 / (h^3 S).
+ * Network: an MLP 13 -> 64 -> 64 -> 64 -> 3 with GELU, BF16 weights and activations and FP32
+ * accumulation, evaluated on the tensor cores (tcgen05).  One network per layer (layer 0 =
+ * single, 1 = double).  Features per near target, in the local frame (t1, t2, n0) at x0:
+ * lambda_0 = b/delta_0; kappa_1 h, kappa_2 h (principal curvatures); the density at x0 and its
+ * tangential derivatives (times h), divided by their largest magnitude S; rho_0.  Outputs are in
+ * the same local frame.
+ */
+typedef struct ers_closure ers_closure;
+
+/* Create the two networks with He-uniform weights drawn from `seed` (zero biases). */
+int ers_closure_create(uint64_t seed, ers_closure **out);
+int ers_closure_free(ers_closure *c);
+
+/*
+ * Read (get != NULL) and/or replace (set != NULL) the FP32 parameters of one network, host
+ * arrays of count = 10448 floats: W1 (64x16), b1 (64), W2 (64x64), b2, W3 (64x64), b3, W4 (16x64),
+ * b4 (16), weights row-major [out][in]; rows 3..15 of W4 and b4[3..15] are unused.
+ */
+int ers_closure_params(ers_closure *c, int layer, float *get, const float *set, int64_t count);
+
+/* Network outputs Y (n, 4) floats dev (3 used) for features X (n, 16) floats dev (13 used), on
+ * the tensor cores.  A tensor-core wait that expires sets a flag read by ers_closure_status. */
+int ers_closure_infer(ers_closure *c, int layer, const float *X, int64_t n, float *Y, void *stream);
+
+/* The same network evaluated with FP32 CUDA-core arithmetic and the same BF16 rounding (a check of
+ * the tensor-core kernel; not used by the evaluation path). */
+int ers_closure_infer_reference(ers_closure *c, int layer, const float *X, int64_t n, float *Y, void *stream);
+
+/* *timed_out = 1 if a bounded tensor-core wait expired in an inference call (synchronous). */
+int ers_closure_status(ers_closure *c, int *timed_out);
+
+/* Loss L = (1/n) sum_s 1/2 |y_s - t_s|^2 over the 3 outputs and its gradient G (10448 floats dev)
+ * with respect to the FP32 parameters (BF16 rounding in the forward pass, straight-through in the
+ * backward pass).  X (n,16), T (n,4) floats dev; *loss (host) may be NULL.  Synchronizes when
+ * loss is requested. */
+int ers_closure_grad(ers_closure *c, int layer, const float *X, const float *T, int64_t n, float *G, double *loss,
+                     void *stream);
+
+/* `steps` Adam steps (lr with cosine decay over the call) on minibatches of `batch` samples drawn
+ * from (X, T) with a counter-based generator seeded by the closure seed; *final_loss (host, may
+ * be NULL) receives the loss of the last minibatch. */
+int ers_closure_train(ers_closure *c, int layer, const float *X, const float *T, int64_t n, int steps, int batch,
+                      float lr, double *final_loss, void *stream);
+
+/*
+ * Training data from the method itself: runs the two-delta sums at M targets and writes the
+ * features Xs, Xd (M,16) and targets Ts, Td (M,4) of both networks, the targets being
+ * c2 = (two-delta value - u3) / gamma in the local frame over h^3 S, with u3, v3 (M,3) dev the
+ * values of ers_eval (three deltas) at the same targets.  gf0, gq0 (M,3,3) dev are the Jacobians
+ * d f_i / d x_j and d q_i / d x_j at x0.  valid (M) ints: 1 for targets within the two-delta near
+ * radius (only those carry a correction).  x0, n0, b from ers_closest_point.
+ */
+int ers_closure_data(ers_surface *s, const ers_params *p, const double *y, int64_t M, const double *x0,
+                     const double *n0, const double *b, const double *f0, const double *q0, const double *gf0,
+                     const double *gq0, const double *u3, const double *v3, int ndelta, float *Xs, float *Xd,
+                     float *Ts, float *Td, int *valid, void *stream);
+
+/*
+ * Both layers with the learned closure: far field (precision of p) + two-delta near sums +
+ * network correction, then a validation: every vstride-th target is also evaluated with ers_eval
+ * (three deltas) and if max|learned - method| / max|method| over that sample exceeds tol for
+ * either layer, the whole call falls back to ers_eval (*fell_back = 1).  val_err[2] (host, may be
+ * NULL) receives the two measured ratios.  Synchronizes the stream (to read the validation).
+ * Errors as ers_eval, plus ERS_E_TIMEOUT when a tensor-core wait expired.
+ */
+int ers_eval_learned(ers_surface *s, ers_closure *c, const ers_params *p, const double *y, int64_t M,
+                     const double *x0, const double *n0, const double *b, const double *f0, const double *q0,
+                     const double *gf0, const double *gq0, int ndelta, double *u, double *v, double tol,
+                     int vstride, double *val_err, int *fell_back, void *stream);
+
+/*
  * ers_eval for callers that cannot allocate device memory while they evaluate (a solver that
  * owns a fixed memory pool, a plugin running where cudaMalloc is forbidden or too slow to risk,
  * a real-time loop).  The paper has no counterpart; this is a deployment variant of ers_eval.

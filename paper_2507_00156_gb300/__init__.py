@@ -37,7 +37,10 @@ PREC_MIXED = 1
 EXPORTS = ["ers_build_surface", "ers_surface_free", "ers_surface_info", "ers_set_density", "ers_closest_point",
            "ers_eval", "ers_eval_SL", "ers_eval_DL", "ers_eval_host", "ers_last_counts", "ers_profile",
            "ers_last_profile", "ers_set_density_multi", "ers_batch_create", "ers_batch_launch", "ers_batch_info",
-           "ers_batch_free", "ers_eval_noalloc", "ers_last_error", "ers_version"]
+           "ers_batch_free", "ers_closure_create", "ers_closure_free", "ers_closure_params", "ers_closure_infer",
+           "ers_closure_infer_reference", "ers_closure_status", "ers_closure_grad", "ers_closure_train",
+           "ers_closure_data", "ers_eval_learned", "ers_eval_noalloc", "ers_last_error", "ers_version"]
+NPARAM = 10448
 NOALLOC_MAX_M = 524288
 
 
@@ -96,6 +99,18 @@ def lib():
             L.ers_batch_launch.argtypes = [vp, vp]
             L.ers_batch_info.argtypes = [vp, P(cint), P(cint)]
             L.ers_batch_free.argtypes = [vp]
+            fp = ctypes.POINTER(ctypes.c_float)
+            L.ers_closure_create.argtypes = [ctypes.c_uint64, P(vp)]
+            L.ers_closure_free.argtypes = [vp]
+            L.ers_closure_params.argtypes = [vp, cint, vp, vp, i64]
+            L.ers_closure_infer.argtypes = [vp, cint, vp, i64, vp, vp]
+            L.ers_closure_infer_reference.argtypes = [vp, cint, vp, i64, vp, vp]
+            L.ers_closure_status.argtypes = [vp, P(cint)]
+            L.ers_closure_grad.argtypes = [vp, cint, vp, vp, i64, vp, P(dbl), vp]
+            L.ers_closure_train.argtypes = [vp, cint, vp, vp, i64, cint, cint, ctypes.c_float, P(dbl), vp]
+            L.ers_closure_data.argtypes = [vp, P(_Params), vp, i64] + [vp] * 9 + [cint] + [vp] * 6
+            L.ers_eval_learned.argtypes = [vp, vp, P(_Params), vp, i64] + [vp] * 7 + [cint, vp, vp, dbl, cint, P(dbl),
+                                                                                         P(cint), vp]
             L.ers_last_counts.argtypes = [vp, P(i64), P(i64), P(i64)]
             L.ers_profile.argtypes = [vp, cint]
             L.ers_last_profile.argtypes = [vp, P(dbl), P(dbl), P(dbl)]
@@ -316,6 +331,108 @@ class Batch:
         if h is not None and h.value and _lib is not None:
             _lib.ers_batch_free(h)
             self._h = None
+
+
+def _fptr(t):
+    if t is None:
+        return None
+    import torch
+    if not t.is_cuda or t.dtype not in (torch.float32, torch.int32) or not t.is_contiguous():
+        raise ValueError("expected a contiguous float32/int32 CUDA tensor")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+class Closure:
+    """The learned near-field closure (ers_closure_*): two networks (0 = single, 1 = double layer)."""
+
+    def __init__(self, seed: int = 0):
+        h = ctypes.c_void_p()
+        check(lib().ers_closure_create(ctypes.c_uint64(seed), ctypes.byref(h)))
+        self._h = h
+
+    @property
+    def handle(self):
+        return self._h
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h is not None and h.value and _lib is not None:
+            _lib.ers_closure_free(h)
+            self._h = None
+
+    def params(self, layer: int):
+        import numpy as np
+        out = np.empty(NPARAM, dtype=np.float32)
+        check(lib().ers_closure_params(self._h, layer, ctypes.c_void_p(out.ctypes.data), None, NPARAM))
+        return out
+
+    def set_params(self, layer: int, values):
+        import numpy as np
+        a = np.ascontiguousarray(values, dtype=np.float32)
+        check(lib().ers_closure_params(self._h, layer, None, ctypes.c_void_p(a.ctypes.data), NPARAM))
+
+    def infer(self, layer: int, X, reference: bool = False, stream=None):
+        import torch
+        Y = torch.zeros((X.shape[0], 4), dtype=torch.float32, device=X.device)
+        fn = lib().ers_closure_infer_reference if reference else lib().ers_closure_infer
+        check(fn(self._h, layer, _fptr(X), X.shape[0], _fptr(Y), _stream(stream)))
+        return Y
+
+    def timed_out(self) -> bool:
+        v = ctypes.c_int()
+        check(lib().ers_closure_status(self._h, ctypes.byref(v)))
+        return bool(v.value)
+
+    def grad(self, layer: int, X, T, stream=None):
+        import torch
+        G = torch.empty(NPARAM, dtype=torch.float32, device=X.device)
+        loss = ctypes.c_double()
+        check(lib().ers_closure_grad(self._h, layer, _fptr(X), _fptr(T), X.shape[0], _fptr(G), ctypes.byref(loss),
+                                     _stream(stream)))
+        return G, loss.value
+
+    def train(self, layer: int, X, T, steps: int, batch: int = 4096, lr: float = 2e-3, stream=None) -> float:
+        loss = ctypes.c_double()
+        check(lib().ers_closure_train(self._h, layer, _fptr(X), _fptr(T), X.shape[0], int(steps), int(batch),
+                                      ctypes.c_float(lr), ctypes.byref(loss), _stream(stream)))
+        return loss.value
+
+
+def closure_data(surface, y, x0, n0, b, f0, q0, gf0, gq0, u3, v3, rho=(2.0, 3.0, 4.0), cutoff_t=6.0,
+                 precision=PREC_MIXED, ndelta=1, stream=None):
+    """ers_closure_data: (Xs, Xd, Ts, Td, valid) CUDA tensors for training the two networks."""
+    import torch
+    M = y.shape[0]
+    dev = y.device
+    Xs = torch.empty((M, 16), dtype=torch.float32, device=dev)
+    Xd = torch.empty_like(Xs)
+    Ts = torch.empty((M, 4), dtype=torch.float32, device=dev)
+    Td = torch.empty_like(Ts)
+    valid = torch.empty((M,), dtype=torch.int32, device=dev)
+    p = params(rho, cutoff_t, precision)
+    check(lib().ers_closure_data(surface.handle, ctypes.byref(p), _ptr(y), M, _ptr(x0), _ptr(n0), _ptr(b), _ptr(f0),
+                                 _ptr(q0), _ptr(gf0), _ptr(gq0), _ptr(u3), _ptr(v3), int(ndelta), _fptr(Xs), _fptr(Xd),
+                                 _fptr(Ts), _fptr(Td), _fptr(valid), _stream(stream)))
+    return Xs, Xd, Ts, Td, valid
+
+
+def eval_learned(surface, closure, y, x0, n0, b, f0, q0, gf0, gq0, rho=(2.0, 3.0, 4.0), cutoff_t=6.0,
+                 precision=PREC_MIXED, tol=1e-5, vstride=32, ndelta=1, u=None, v=None, stream=None):
+    """ers_eval_learned: returns (u, v, validation errors (SL, DL), fell_back)."""
+    import torch
+    M = y.shape[0]
+    if u is None:
+        u = torch.empty((M, 3), dtype=torch.float64, device=y.device)
+    if v is None:
+        v = torch.empty((M, 3), dtype=torch.float64, device=y.device)
+    p = params(rho, cutoff_t, precision)
+    ve = (ctypes.c_double * 2)()
+    fb = ctypes.c_int()
+    check(lib().ers_eval_learned(surface.handle, closure.handle, ctypes.byref(p), _ptr(y), M, _ptr(x0), _ptr(n0),
+                                 _ptr(b), _ptr(f0), _ptr(q0), _ptr(gf0), _ptr(gq0), int(ndelta), _ptr(u), _ptr(v),
+                                 float(tol),
+                                 int(vstride), ve, ctypes.byref(fb), _stream(stream)))
+    return u, v, (ve[0], ve[1]), bool(fb.value)
 
 
 def version() -> str:

@@ -236,8 +236,12 @@ int check_params(const ers_surface *s, const ers_params *p, int *warn) {
     return ERS_OK;
 }
 
-int eval(ers_surface *s, const ers_params *p, const double *y, int64_t M, const double *x0, const double *n0,
-         const double *b, const double *f0, const double *q0, double *u, double *v, void *stream) {
+// ndelta = 3: the method (Eq. (extrap_eqn)); ndelta = 2: the two-delta sums of the learned closure,
+// near radius cutoff_t * delta_1, per-target gamma written to `gamma` (may be NULL); ndelta = 1:
+// the single regularized sum with delta_0, near radius cutoff_t * delta_0.
+int eval_impl(ers_surface *s, const ers_params *p, const double *y, int64_t M, const double *x0, const double *n0,
+              const double *b, const double *f0, const double *q0, double *u, double *v, void *stream, int ndelta,
+              double *gamma) {
     clear_error();
     if (!s) return fail(ERS_E_INVAL, "ers_eval: NULL surface");
     int warn;
@@ -273,7 +277,9 @@ int eval(ers_surface *s, const ers_params *p, const double *y, int64_t M, const 
     a.v = v;
     for (int k = 0; k < 3; ++k) a.rho[k] = p->rho[k];
     a.cutoff_t = p->cutoff_t;
-    a.Rc = p->cutoff_t * p->rho[2] * s->h;
+    a.Rc = p->cutoff_t * p->rho[ndelta - 1] * s->h;
+    a.ndelta = ndelta;
+    a.gamma = gamma;
     a.precision = p->precision;
     a.layers = p->layers;
     a.stream = st;
@@ -328,6 +334,21 @@ int eval(ers_surface *s, const ers_params *p, const double *y, int64_t M, const 
     s->last_counts[2] = M * s->N;
     s->last_stream = st;
     return warn;
+}
+
+int eval(ers_surface *s, const ers_params *p, const double *y, int64_t M, const double *x0, const double *n0,
+         const double *b, const double *f0, const double *q0, double *u, double *v, void *stream) {
+    return eval_impl(s, p, y, M, x0, n0, b, f0, q0, u, v, stream, 3, nullptr);
+}
+
+int eval_few_delta(ers_surface *s, const ers_params *p, const double *y, int64_t M, const double *x0,
+                   const double *n0, const double *b, const double *f0, const double *q0, double *u, double *v,
+                   double *gamma, int ndelta, cudaStream_t st) {
+    try {
+        return eval_impl(s, p, y, M, x0, n0, b, f0, q0, u, v, (void *)st, ndelta, gamma);
+    } catch (...) {
+        return fail(ERS_E_NOMEM, "two-delta evaluation: host exception");
+    }
 }
 
 }  // namespace ers

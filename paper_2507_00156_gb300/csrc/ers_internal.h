@@ -136,6 +136,8 @@ struct EvalArgs {
     int64_t M;
     double rho[3], cutoff_t, Rc;
     int precision, layers;
+    int ndelta;      // 3: extrapolation of Eq. (extrap_eqn); 2: two-delta weights (learned closure)
+    double *gamma;   // ndelta == 2: per-target gamma (may be NULL)
     double *u, *v;
     double *part;    // [chunks][M][6]
     int chunks;
@@ -195,6 +197,15 @@ __device__ __forceinline__ float approx_float_pos(double x) {
     unsigned hi = (unsigned)(bits >> 32), lo = (unsigned)bits;
     unsigned fb = __funnelshift_l(lo, hi, 3) - (unsigned)((1023 - 127) << 23);
     return (hi < (897u << 20)) ? 0.0f : __int_as_float((int)fb);
+}
+
+// float -> double by bit manipulation (integer pipe only); zero for zero and subnormal input.
+__device__ __forceinline__ double float_to_double(float f) {
+    const unsigned b = (unsigned)__float_as_int(f);
+    if ((b & 0x7f800000u) == 0u) return 0.0;
+    const unsigned hi = (b & 0x80000000u) | (((b & 0x7fffffffu) >> 3) + ((1023u - 127u) << 20));
+    const unsigned lo = b << 29;
+    return __longlong_as_double(((long long)hi << 32) | lo);
 }
 
 }  // namespace ers

@@ -100,7 +100,6 @@ __device__ void far_phase(const BatchProblemDev &P, int tb, int layers, BatchSme
             float dx, dy, dz;
             const float r2 = dist2_fp32(yc0, yc1, yc2, sp[0], sp[1], sp[2], &dx, &dy, &dz);
             float ri = rsqrtf(r2);
-            ri = ri * fmaf(-0.5f * r2 * ri, ri, 1.5f);
             ri = (r2 > rc2) ? ri : 0.0f;
             const float ri2 = ri * ri;
             const float dwn = fmaf(dz, sp[5], fmaf(dy, sp[4], dx * sp[3]));
@@ -200,6 +199,7 @@ __device__ void near_phase(const BatchProblemDev &P, int tb, int layers, const d
         if (near) {
             Geom T;
             load_geom(lane, P.y, P.x0, P.n0, bm, m, rho, P.sp.h, T);
+            T.tcf = P.sp.tcf;
             double c[NR];
             for (int r = 0; r < NR; ++r) {
                 const double *f0 = P.f0 + ((int64_t)r * P.M + m) * 3;

@@ -29,7 +29,7 @@ namespace {
 using namespace nearc;
 constexpr int WPB = 4;  // warps per block
 
-template <int CLS, int PREC, bool SL, bool DL>
+template <int CLS, int PREC, bool SL, bool DL, int ND>
 __device__ __forceinline__ void process(const EvalArgs &A, const Geom &T, double c, const double q0[3],
                                         const double *__restrict__ tab, float rc2f, int64_t j, double accU[3],
                                         double &accN, double accX[3], int npairs[3]) {
@@ -47,7 +47,7 @@ __device__ __forceinline__ void process(const EvalArgs &A, const Geom &T, double
     if (!is_near<PREC>(A.sd, T, j, r2, A.Rc, rc2f)) return;
     ++npairs[CLS];
     double K1, K3, K5;
-    kernel_factors<CLS>(T, tab, r2, K1, K3, K5);
+    kernel_factors<CLS, ND>(T, tab, r2, K1, K3, K5);
     if (SL) sl_accumulate(dx, dy, dz, K1, K3, c, wf, wn, accU);
     if (DL) {
         const double h3[3] = {xs[0] - T.x0[0], xs[1] - T.x0[1], xs[2] - T.x0[2]};
@@ -57,7 +57,7 @@ __device__ __forceinline__ void process(const EvalArgs &A, const Geom &T, double
     }
 }
 
-template <int PREC, bool SL, bool DL>
+template <int PREC, bool SL, bool DL, int ND>
 __global__ void __launch_bounds__(WPB * 32) k_near(EvalArgs A, ScanParams P, const double *__restrict__ tab) {
     __shared__ int sq[WPB][3][64];
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
@@ -70,13 +70,17 @@ __global__ void __launch_bounds__(WPB * 32) k_near(EvalArgs A, ScanParams P, con
         for (int c = 0; c < A.chunks; ++c) fs += A.part[((int64_t)c * A.M + m) * 6 + lane];
     const double bm = A.b[m];
     if (!(fabs(bm) <= A.Rc)) {
+        if (A.gamma && lane == 0) A.gamma[m] = 0.0;
         if (SL && lane < 3) A.u[3 * m + lane] = fs;
         if (DL && lane >= 3 && lane < 6) A.v[3 * m + lane - 3] = fs;
         return;
     }
 
     Geom T;
-    load_geom(lane, A.y, A.x0, A.n0, bm, m, A.rho, P.h, T);
+    double gam = 0.0;
+    load_geom(lane, A.y, A.x0, A.n0, bm, m, A.rho, P.h, T, A.ndelta, &gam);
+    T.tcf = P.tcf;
+    if (A.gamma && lane == 0) A.gamma[m] = gam;
     double q0[3];
     for (int i = 0; i < 3; ++i) q0[i] = DL ? A.q0[3 * m + i] : 0.0;
     const double c = SL ? fma(A.f0[3 * m + 2], T.n0[2], fma(A.f0[3 * m + 1], T.n0[1], A.f0[3 * m] * T.n0[0])) : 0.0;
@@ -85,9 +89,9 @@ __global__ void __launch_bounds__(WPB * 32) k_near(EvalArgs A, ScanParams P, con
     int npairs[3] = {0, 0, 0};  // near pairs by class (number of unregularized deltas)
     scan_near(A.sd, T, P, sq[wib], lane, [&](int cls, int jj, bool valid) {
         if (!valid) return;
-        if (cls == 0) process<0, PREC, SL, DL>(A, T, c, q0, tab, P.rc2f, jj, accU, accN, accX, npairs);
-        else if (cls == 1) process<1, PREC, SL, DL>(A, T, c, q0, tab, P.rc2f, jj, accU, accN, accX, npairs);
-        else process<2, PREC, SL, DL>(A, T, c, q0, tab, P.rc2f, jj, accU, accN, accX, npairs);
+        if (cls == 0) process<0, PREC, SL, DL, ND>(A, T, c, q0, tab, P.rc2f, jj, accU, accN, accX, npairs);
+        else if (cls == 1) process<1, PREC, SL, DL, ND>(A, T, c, q0, tab, P.rc2f, jj, accU, accN, accX, npairs);
+        else process<2, PREC, SL, DL, ND>(A, T, c, q0, tab, P.rc2f, jj, accU, accN, accX, npairs);
     });
     for (int i = 0; i < 3; ++i) {
         accU[i] = warp_sum(accU[i]);
@@ -124,9 +128,13 @@ template <int PREC>
 cudaError_t near_dispatch(const EvalArgs &a, ScanParams P, const double *tab) {
     const int64_t grid = (a.M + WPB - 1) / WPB;
     const bool sl = a.layers & ERS_LAYER_SL, dl = a.layers & ERS_LAYER_DL;
-    if (sl && dl) k_near<PREC, true, true><<<(unsigned)grid, WPB * 32, 0, a.stream>>>(a, P, tab);
-    else if (sl) k_near<PREC, true, false><<<(unsigned)grid, WPB * 32, 0, a.stream>>>(a, P, tab);
-    else k_near<PREC, false, true><<<(unsigned)grid, WPB * 32, 0, a.stream>>>(a, P, tab);
+    if (a.ndelta == 1 || a.ndelta == 2) {  // learned closure: both layers
+        if (!(sl && dl)) return cudaErrorInvalidValue;
+        if (a.ndelta == 1) k_near<PREC, true, true, 1><<<(unsigned)grid, WPB * 32, 0, a.stream>>>(a, P, tab);
+        else k_near<PREC, true, true, 2><<<(unsigned)grid, WPB * 32, 0, a.stream>>>(a, P, tab);
+    } else if (sl && dl) k_near<PREC, true, true, 3><<<(unsigned)grid, WPB * 32, 0, a.stream>>>(a, P, tab);
+    else if (sl) k_near<PREC, true, false, 3><<<(unsigned)grid, WPB * 32, 0, a.stream>>>(a, P, tab);
+    else k_near<PREC, false, true, 3><<<(unsigned)grid, WPB * 32, 0, a.stream>>>(a, P, tab);
     return cudaGetLastError();
 }
 

@@ -27,12 +27,19 @@ struct Geom {
     double y[3], x0[3], n0[3], b;
     double invd2[3], ad1[3], ad3[3], ad5[3], apre[2];
     float yh[3], yl[3];  // y = yh + yl in floats (mixed-mode classification)
+    float alf[3];        // extrapolation weights in FP32 (for the small defects 1 - s_p)
+    float tcf;           // cutoff_t: s_p := 1 beyond it
 };
+
+// Beyond t = r/delta = DEFECT_T the defects 1 - s_p(t) are below 2.1e-8 and are evaluated in
+// FP32 instead of from the FP64 table.
+constexpr double DEFECT_T = 4.7;
 
 struct ScanParams {
     float rc2f;   // exact FP32 threshold of the mixed far field
     float rpre;   // FP32 prefilter radius (Rc plus a conservative margin)
-    float th[2];  // FP32 class thresholds (cutoff_t delta_0)^2, (cutoff_t delta_1)^2
+    float th[2];  // FP32 class thresholds (min(DEFECT_T, cutoff_t) delta_k)^2, k = 0, 1
+    float tcf;    // cutoff_t
     double h;
 };
 
@@ -72,9 +79,41 @@ __device__ __forceinline__ void extrap_weights(int lane, double b, const double 
     }
 }
 
+// Two-delta weights: the system of Eq. (extrap_eqn) for delta_0, delta_1 without the c2 column,
+// beta_0 + beta_1 = 1, beta_0 rho_0 I0(lambda_0) + beta_1 rho_1 I0(lambda_1) = 0, so that
+// sum_k beta_k u^{delta_k} = u + gamma c2 + O(delta^5) with
+// gamma = beta_0 rho_0^3 I2(lambda_0) + beta_1 rho_1^3 I2(lambda_1).
+__device__ __forceinline__ void two_delta_weights(int lane, double b, const double rho[3], double h, double al[3],
+                                                  double &gamma) {
+    double i0 = 0.0, i2 = 0.0;
+    if (lane < 2) {
+        const double rl = lane == 0 ? rho[0] : rho[1];
+        const double lam = fabs(b) / (rl * h);
+        const double e = exp(-lam * lam) * INVSQRTPI, ec = erfc(lam);
+        i0 = e - lam * ec;
+        i2 = (2.0 / 3.0) * ((0.5 - lam * lam) * e + lam * lam * lam * ec);
+    }
+    const double a0 = rho[0] * __shfl_sync(FULL, i0, 0), a1 = rho[1] * __shfl_sync(FULL, i0, 1);
+    const double c0 = rho[0] * rho[0] * rho[0] * __shfl_sync(FULL, i2, 0);
+    const double c1 = rho[1] * rho[1] * rho[1] * __shfl_sync(FULL, i2, 1);
+    const double den = a1 - a0;
+    if (den != 0.0 && isfinite(den) && isfinite(a0) && isfinite(a1)) {
+        al[0] = a1 / den;
+        al[1] = -a0 / den;
+    } else {
+        al[0] = 1.0;
+        al[1] = 0.0;
+    }
+    al[2] = 0.0;
+    gamma = al[0] * c0 + al[1] * c1;
+}
+
 // Fill the geometry constants of target m (all lanes; lanes 0..2 also evaluate I0, I2).
+// ndelta = 3: the extrapolation weights of Eq. (extrap_eqn); ndelta = 2: the two-delta
+// weights above (gamma returned in *gamma).
 __device__ __forceinline__ void load_geom(int lane, const double *y, const double *x0, const double *n0, double b,
-                                          int64_t m, const double rho[3], double h, Geom &T) {
+                                          int64_t m, const double rho[3], double h, Geom &T, int ndelta = 3,
+                                          double *gamma = nullptr) {
     for (int i = 0; i < 3; ++i) {
         T.y[i] = y[3 * m + i];
         T.x0[i] = x0[3 * m + i];
@@ -84,7 +123,18 @@ __device__ __forceinline__ void load_geom(int lane, const double *y, const doubl
     }
     T.b = b;
     double al[3];
-    extrap_weights(lane, b, rho, h, al);
+    if (ndelta == 2) {
+        double g;
+        two_delta_weights(lane, b, rho, h, al, g);
+        if (gamma) *gamma = g;
+    } else if (ndelta == 1) {  // the single regularized sum u^{delta_0} (no extrapolation)
+        al[0] = 1.0;
+        al[1] = 0.0;
+        al[2] = 0.0;
+        if (gamma) *gamma = 0.0;
+    } else {
+        extrap_weights(lane, b, rho, h, al);
+    }
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
         const double dk = rho[k] * h, id = 1.0 / dk;
@@ -95,6 +145,7 @@ __device__ __forceinline__ void load_geom(int lane, const double *y, const doubl
     }
     T.apre[0] = al[0];
     T.apre[1] = al[0] + al[1];
+    for (int k = 0; k < 3; ++k) T.alf[k] = (float)al[k];
 }
 
 // Exact near/far decision of pair (T, j), identical to the far-field mask of the precision
@@ -114,14 +165,15 @@ __device__ __forceinline__ bool is_near(const SurfDev &s, const Geom &T, int64_t
 
 // alpha-weighted kernel factors of a near pair of class CLS (delta_0..delta_{CLS-1} are not
 // regularized at this distance); sigma_p from the interpolation table.
-template <int CLS>
+// ND = number of deltas in use (3 for the method; 2 or 1 for the learned closure).
+template <int CLS, int ND = 3>
 __device__ __forceinline__ void kernel_factors(const Geom &T, const double *__restrict__ tab, double r2, double &K1,
                                                double &K3, double &K5) {
     K1 = 0.0;
     K3 = 0.0;
     K5 = 0.0;
 #pragma unroll
-    for (int k = CLS; k < 3; ++k) {
+    for (int k = CLS; k < ND; ++k) {
         const double tau = r2 * T.invd2[k];
         int idx = (int)(approx_float_pos(tau) * (float)TAB_INV_W);
         idx = min(idx, TAB_N - 1);
@@ -139,13 +191,31 @@ __device__ __forceinline__ void kernel_factors(const Geom &T, const double *__re
         K5 = fma(T.ad5[k], s3, K5);
     }
     if (CLS >= 1) {
+        // delta_0..delta_{CLS-1}: r / delta_k > DEFECT_T, where s_p = 1 - eps_p with
+        // eps_1 = erfc t, eps_2 = eps_1 + (2/sqrt pi) t e^{-t^2},
+        // eps_3 = eps_1 + (2/sqrt pi)(t + 2/3 t^3) e^{-t^2} (Eqs. (s1)-(s3)) below 2.1e-8;
+        // eps_p is evaluated in FP32 (its error ~1e-14 relative to the term), and eps_p = 0 where
+        // t > cutoff_t (Sec. 3.2).  The term is (sum_k alpha_k - sum_k alpha_k eps_p(t_k)) / r^p.
+        float E1 = 0.0f, E3 = 0.0f, E5 = 0.0f;
+        const float r2f = approx_float_pos(r2);
+#pragma unroll
+        for (int k = 0; k < CLS; ++k) {
+            const float t = sqrtf(r2f * approx_float_pos(T.invd2[k]));
+            if (t <= T.tcf) {
+                const float e = erfcf(t), g = 1.12837916709551257f * t * expf(-t * t);
+                const float a = (float)T.alf[k];
+                E1 = fmaf(a, e, E1);
+                E3 = fmaf(a, e + g, E3);
+                E5 = fmaf(a, e + g * (1.0f + 0.6666666666666667f * t * t), E5);
+            }
+        }
         const double Ain = T.apre[CLS - 1];
         const double ri = rsqrt(r2);
         const double ri2 = ri * ri;
         const double ri3 = ri2 * ri;
-        K1 = fma(Ain, ri, K1);
-        K3 = fma(Ain, ri3, K3);
-        K5 = fma(Ain, ri3 * ri2, K5);
+        K1 = fma(Ain - float_to_double(E1), ri, K1);
+        K3 = fma(Ain - float_to_double(E3), ri3, K3);
+        K5 = fma(Ain - float_to_double(E5), ri3 * ri2, K5);
     }
 }
 
@@ -266,9 +336,10 @@ inline ScanParams scan_params(const ers_surface *s, double Rc, const double rho[
     for (int i = 0; i < 3; ++i) L = fmax(L, fabs(s->c[i]) + s->a[i]);
     P.rpre = (float)(Rc * (1.0 + 1e-5) + 4e-6 * (L + Rc));
     for (int k = 0; k < 2; ++k) {
-        const double t = cutoff_t * rho[k] * s->h;
+        const double t = fmin(DEFECT_T, cutoff_t) * rho[k] * s->h;
         P.th[k] = (float)(t * t);
     }
+    P.tcf = (float)cutoff_t;
     P.h = s->h;
     return P;
 }

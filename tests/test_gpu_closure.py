@@ -1,0 +1,145 @@
+"""The learned near-field closure: tensor-core inference, training kernels, gradients against the
+FP64 reference network, and what the trained network gains over the two-delta sums alone."""
+import numpy as np
+import pytest
+
+import workloads
+from oracle import mlp as ref
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ers():
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2507_00156_gb300
+    return paper_2507_00156_gb300
+
+
+def _rand_inputs(n, seed):
+    rng = np.random.default_rng(seed)
+    X = rng.standard_normal((n, 16)).astype(np.float32)
+    X[:, 13:] = 0.0
+    T = (0.3 * rng.standard_normal((n, 4))).astype(np.float32)
+    T[:, 3] = 0.0
+    return X, T
+
+
+@pytest.mark.parametrize("n", [1, 127, 1000, 4099])
+def test_tensor_core_inference_matches_reference_and_oracle(ers, n):
+    import torch
+    c = ers.Closure(seed=3)
+    X, _ = _rand_inputs(n, n)
+    Xd = torch.from_numpy(X).cuda()
+    for layer in (0, 1):
+        Ytc = c.infer(layer, Xd).cpu().numpy()[:, :3]
+        Yref = c.infer(layer, Xd, reference=True).cpu().numpy()[:, :3]
+        yo, _ = ref.forward(c.params(layer).astype(np.float64), X.astype(np.float64), quantize=True)
+        scale = np.abs(yo).max()
+        d_ref = np.abs(Ytc - Yref)
+        d_ora = np.abs(Ytc - yo)
+        # same BF16 operands, FP32 sums in another order: rare one-ulp BF16 flips of an activation
+        assert d_ref.max() <= 2e-2 * scale, (layer, d_ref.max(), scale, Ytc[:2], Yref[:2])
+        assert np.quantile(d_ref, 0.99) <= 1e-5 * scale
+        assert d_ora.max() <= 2e-2 * scale and np.quantile(d_ora, 0.99) <= 1e-4 * scale
+    assert not c.timed_out()
+
+
+def test_gradient_matches_fp64_reference(ers):
+    import torch
+    c = ers.Closure(seed=5)
+    X, T = _rand_inputs(777, 11)
+    for layer in (0, 1):
+        G, loss = c.grad(layer, torch.from_numpy(X).cuda(), torch.from_numpy(T).cuda())
+        lo, go = ref.loss_and_grad(c.params(layer).astype(np.float64), X.astype(np.float64),
+                                   T.astype(np.float64), quantize=True)
+        G = G.cpu().numpy().astype(np.float64)
+        # rare one-ulp BF16 flips of an activation (FP32 vs FP64 GELU before rounding) move the loss slightly
+        assert abs(loss - lo) <= 1e-4 * abs(lo), (loss, lo)
+        assert np.linalg.norm(G - go) <= 1e-3 * np.linalg.norm(go), np.linalg.norm(G - go) / np.linalg.norm(go)
+        big = np.abs(go) > 1e-3 * np.abs(go).max()
+        assert np.quantile(np.abs(G - go)[big] / np.abs(go)[big], 0.95) <= 1e-3
+
+
+def test_training_reduces_loss(ers):
+    import torch
+    c = ers.Closure(seed=7)
+    rng = np.random.default_rng(3)
+    X = rng.uniform(-1, 1, (20000, 16)).astype(np.float32)
+    X[:, 13:] = 0.0
+    A = rng.standard_normal((13, 3))
+    T = np.zeros((20000, 4), np.float32)
+    T[:, :3] = np.tanh(X[:, :13] @ A / 3.0)
+    Xd, Td = torch.from_numpy(X).cuda(), torch.from_numpy(T).cuda()
+    _, l0 = c.grad(0, Xd, Td)
+    l1 = c.train(0, Xd, Td, steps=600, batch=2048, lr=3e-3)
+    _, l2 = c.grad(0, Xd, Td)
+    assert l2 < 0.05 * l0, (l0, l1, l2)
+
+
+def _problem(ers, s, wl_shape, fc, qc, y, precision):
+    import torch
+    dev = torch.device("cuda")
+    yd = torch.from_numpy(np.ascontiguousarray(y)).to(dev)
+    x0, n0, b = s.closest_point(yd)
+    x0h = x0.cpu().numpy()
+    t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
+    f0, q0 = t(workloads.poly_eval(fc, x0h)), t(workloads.poly_eval(qc, x0h))
+    gf0, gq0 = t(workloads.poly_jacobian(fc, x0h)), t(workloads.poly_jacobian(qc, x0h))
+    x = s.nodes()[0].cpu().numpy()
+    s.set_density(t(workloads.poly_eval(fc, x)), t(workloads.poly_eval(qc, x)))
+    u3, v3 = s.eval(yd, f0, q0, rho=(2, 3, 4), precision=precision, x0=x0, n0=n0, b=b)
+    return dict(y=yd, x0=x0, n0=n0, b=b, f0=f0, q0=q0, gf0=gf0, gq0=gq0, u3=u3.clone(), v3=v3.clone())
+
+
+def test_learned_closure_gains_over_the_single_delta_sum_and_falls_back(ers):
+    """One regularized sum (delta_0) + the network against the same sum alone, both compared with the
+    method (three deltas) on a held-out density; then the fallback path."""
+    import torch
+    shape = workloads.unit_sphere()
+    h = 1 / 32
+    s = ers.Surface(shape.center, shape.axes, h)
+    x = s.nodes()[0].cpu().numpy()
+    rng = np.random.default_rng(21)
+    data = {1: [], 2: []}
+    for k in range(6):
+        fc, qc = workloads.density_coeffs(rng), workloads.density_coeffs(rng)
+        band = workloads.near_band_targets(shape, 6000, 4 * h, rng)[0]
+        P = _problem(ers, s, shape, fc, qc, np.concatenate([x, band]), 0)
+        for nd in (1, 2):
+            out = ers.closure_data(s, P["y"], P["x0"], P["n0"], P["b"], P["f0"], P["q0"], P["gf0"], P["gq0"],
+                                   P["u3"], P["v3"], precision=0, ndelta=nd)
+            sel = out[4].bool()
+            data[nd].append([z[sel] for z in out[:4]])
+    nets, zero = {}, ers.Closure(seed=2)
+    for layer in (0, 1):
+        zero.set_params(layer, np.zeros(ers.NPARAM, np.float32))
+    for nd in (1, 2):
+        Xs, Xd, Ts, Td = (torch.cat([d[i] for d in data[nd]]).contiguous() for i in range(4))
+        nets[nd] = ers.Closure(seed=nd)
+        for layer, (X, T) in enumerate(((Xs, Ts), (Xd, Td))):
+            nets[nd].train(layer, X, T, steps=3000, batch=4096, lr=2e-3)
+    # held-out density and targets
+    fc, qc = workloads.density_coeffs(rng), workloads.density_coeffs(rng)
+    band = workloads.near_band_targets(shape, 3000, 4 * h, rng)[0]
+    P = _problem(ers, s, shape, fc, qc, np.concatenate([x, band]), 0)
+    args = (P["y"], P["x0"], P["n0"], P["b"], P["f0"], P["q0"], P["gf0"], P["gq0"])
+    u3, v3 = P["u3"].cpu().numpy(), P["v3"].cpu().numpy()
+    uL, vL, errL, fb = ers.eval_learned(s, nets[1], *args, precision=0, tol=1.0, vstride=8, ndelta=1)
+    assert not fb and not nets[1].timed_out()
+    u1, v1, err1, _ = ers.eval_learned(s, zero, *args, precision=0, tol=1.0, vstride=8, ndelta=1)
+    for (a, b_, ref3) in ((uL, u1, u3), (vL, v1, v3)):
+        eL = np.abs(a.cpu().numpy() - ref3)
+        e1 = np.abs(b_.cpu().numpy() - ref3)
+        rL, r1 = np.sqrt((eL ** 2).mean()), np.sqrt((e1 ** 2).mean())
+        assert rL < 0.2 * r1, (rL, r1)
+        assert eL.max() < 0.5 * e1.max(), (eL.max(), e1.max())
+    assert errL[0] < err1[0] and errL[1] < err1[1]
+    # two deltas: finite, and the validation ratio is reported
+    u2, v2, err2, fb2 = ers.eval_learned(s, nets[2], *args, precision=0, tol=1.0, vstride=8, ndelta=2)
+    assert np.isfinite(u2.cpu().numpy()).all() and np.isfinite(v2.cpu().numpy()).all() and not fb2
+    # fallback: an impossible tolerance gives exactly the three-delta result
+    uF, vF, _, fb = ers.eval_learned(s, nets[1], *args, precision=0, tol=1e-15, vstride=8, ndelta=1)
+    assert fb
+    assert np.array_equal(uF.cpu().numpy(), u3) and np.array_equal(vF.cpu().numpy(), v3)

@@ -58,6 +58,26 @@ def poly_eval(coeffs: np.ndarray, pts: np.ndarray) -> np.ndarray:
     return out
 
 
+def poly_jacobian(coeffs: np.ndarray, pts: np.ndarray) -> np.ndarray:
+    """Jacobian J[m, i, j] = d f_i / d x_j of the polynomial vector field at points (M, 3)."""
+    pts = np.asarray(pts, dtype=np.float64)
+    M = pts.shape[0]
+    pw = [[np.ones(M)] for _ in range(3)]
+    for a in range(3):
+        for e in range(1, 5):
+            pw[a].append(pw[a][-1] * pts[:, a])
+    J = np.zeros((M, 3, 3))
+    for m, ex in enumerate(MONOMIALS):
+        for j in range(3):
+            if ex[j] == 0:
+                continue
+            e = list(ex)
+            e[j] -= 1
+            d = ex[j] * pw[0][e[0]] * pw[1][e[1]] * pw[2][e[2]]
+            J[:, :, j] += d[:, None] * coeffs[:, m][None, :]
+    return J
+
+
 def surface_points(shape: Shape, count: int, rng: np.random.Generator):
     """Random points x0 on the ellipsoid and their outward unit normals n0.
 

@@ -42,7 +42,7 @@ FP64_PEAK_NOMINAL = 1.25e12
 FAR_FLOPS_PER_PAIR = 57                   # both layers, one (target, node) far pair
 NEAR_FLOPS_BASE = 85                      # both layers, one near pair: geometry + contractions
 NEAR_FLOPS_PER_ACTIVE_DELTA = 45          # sigma_1..3 from the table and the alpha-weighted sums
-NEAR_FLOPS_UNREGULARIZED = 13             # 1/r^p terms when some delta_k has r > 4.7 delta_k
+NEAR_FLOPS_UNREGULARIZED = 13             # 1/r^p terms when some delta_k has r > cutoff_t delta_k
 
 
 def parse():
@@ -366,12 +366,12 @@ def main():
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)  # > 129 MB L2
     stream = torch.cuda.current_stream()
 
-    def step(prec):
-        s.eval(yd, f0, q0, rho=wl.rho, precision=prec, u=u, v=v)
+    def step(prec, concurrent=False):
+        s.eval(yd, f0, q0, rho=wl.rho, precision=prec, u=u, v=v, concurrent=concurrent)
 
-    def timed(prec, steps, warm):
+    def timed(prec, steps, warm, concurrent=False):
         for _ in range(warm):
-            step(prec)
+            step(prec, concurrent)
         s.profile(True)
         torch.cuda.synchronize()
         barrier(world)
@@ -382,7 +382,7 @@ def main():
             flush.fill_(1)
             a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             a.record(stream)
-            step(prec)
+            step(prec, concurrent)
             b.record(stream)
             evs.append((a, b))
             kern.append(s.last_profile())  # synchronizes; device times are unaffected
@@ -406,10 +406,15 @@ def main():
     clocks = sampler.stop()
     near_targets, near_pairs, far_pairs = s.last_counts()
     cls_counts = s.last_class_counts()
+    defect_counts = s.last_defect_class_counts()
     u_mixed, v_mixed = u.cpu().numpy(), v.cpu().numpy()
     t_mixed = max_over_ranks(t_mixed, world)
     ms_step = t_mixed / args.steps * 1e3
     value = world * args.steps * M / t_mixed
+
+    # the same mixed step with the far and near fields on two streams (ERS_OPT_CONCURRENT)
+    t_conc, k_conc = timed(ers.PREC_MIXED, args.steps, 1, concurrent=True)
+    t_conc = max_over_ranks(t_conc, world)
 
     # plain FP64 path on the same workload
     t64, k64 = (None, None)
@@ -468,8 +473,13 @@ def main():
                    "l2": "flushed between timed steps (256 MiB write, outside the timed events)"},
         "gpairs_per_s": world * args.steps * M * N / t_mixed / 1e9,
         "kernels_ms": {"closest_point": ms_closest, "far_field": ms_far, "near_field_and_solve": ms_near},
+        "concurrent_option": {"ms_per_step": t_conc / args.steps * 1e3,
+                              "kernels_ms": {"far_field": float(k_conc[1]), "near_field_and_solve": float(k_conc[2])},
+                              "note": "same step with ERS_OPT_CONCURRENT (far and near fields on two streams, "
+                                      "both timed from the fork)"},
         "counts": {"near_targets": near_targets, "near_pairs": near_pairs, "far_pairs": far_pairs,
-                   "near_pairs_by_unregularized_deltas": cls_counts},
+                   "near_pairs_by_unregularized_deltas": cls_counts,
+                   "near_pairs_by_defect_path_deltas": defect_counts},
         "gpu_launches": 3 * args.steps,
         "roofline": roof,
         "clocks": clocks,

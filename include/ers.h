@@ -49,6 +49,10 @@ extern "C" {
 #define ERS_LAYER_SL 1
 #define ERS_LAYER_DL 2
 
+#define ERS_OPT_CONCURRENT 1 /* ers_params.options, ERS_PREC_MIXED only: run the far field (FP32
+                                pipe) on a second stream of the surface, concurrently with the near
+                                field (FP64 pipe), instead of one after the other (see ers_eval) */
+
 #define ERS_PREC_FP64 0   /* every step in FP64 arithmetic */
 #define ERS_PREC_MIXED 1  /* far field with FP32 operands and FP64 accumulation per source tile;
                              local sums, closest point and 3x3 solve in FP64 */
@@ -66,6 +70,7 @@ typedef struct {
     double cutoff_t;  /* regularize only where r/delta <= cutoff_t; 6 in Sec. 3.2; range (0, 8] */
     int precision;    /* ERS_PREC_FP64 or ERS_PREC_MIXED */
     int layers;       /* bitmask of ERS_LAYER_SL, ERS_LAYER_DL */
+    int options;      /* bitmask of ERS_OPT_*; 0 for the defaults */
 } ers_params;
 
 /*
@@ -116,6 +121,10 @@ int ers_closest_point(const ers_surface *s, const double *y, int64_t M, double *
  *               for the selected layers (may be NULL when the layer is not selected);
  *   u, v      : outputs (M,3) dev for the single and double layer (NULL when not selected).
  * Requires ers_set_density for the selected layers.  M = 0 is a no-op.
+ * All work is ordered after earlier work on `stream` and before later work on it.  With
+ * ERS_PREC_MIXED and ERS_OPT_CONCURRENT the far field runs on a second stream owned by the
+ * surface, forked from and joined back to `stream` with events (also under stream capture);
+ * such calls on one surface must not run concurrently from several streams.
  * Returns ERS_OK, ERS_W_CUTOFF (cutoff_t < 6), or ERS_E_INVAL / ERS_E_STATE / ERS_E_NOMEM /
  * ERS_E_CUDA / ERS_E_UNSUPPORTED.
  */
@@ -157,7 +166,8 @@ int ers_profile(ers_surface *s, int enable);
 /*
  * Kernel durations in milliseconds of the most recent profiled ers_eval on this surface
  * (closest point; far field; near field + extrapolation).  Synchronizes that call's stream.
- * A kernel that did not run reports 0.  ERS_E_STATE if no profiled call happened.
+ * A kernel that did not run reports 0.  When the far and near fields ran concurrently
+ * (ERS_OPT_CONCURRENT) both durations are measured from the common start, so they overlap.  ERS_E_STATE if no profiled call happened.
  */
 int ers_last_profile(ers_surface *s, double *ms_closest, double *ms_far, double *ms_near);
 
@@ -267,12 +277,16 @@ int ers_closure_train(ers_closure *c, int layer, const float *X, const float *T,
                       float lr, double *final_loss, void *stream);
 
 /*
- * Training data from the method itself: runs the two-delta sums at M targets and writes the
- * features Xs, Xd (M,16) and targets Ts, Td (M,4) of both networks, the targets being
- * c2 = (two-delta value - u3) / gamma in the local frame over h^3 S, with u3, v3 (M,3) dev the
- * values of ers_eval (three deltas) at the same targets.  gf0, gq0 (M,3,3) dev are the Jacobians
- * d f_i / d x_j and d q_i / d x_j at x0.  valid (M) ints: 1 for targets within the two-delta near
- * radius (only those carry a correction).  x0, n0, b from ers_closest_point.
+ * Training data from the method itself: runs the sums with ndelta deltas (1: delta_0 alone;
+ * 2: delta_0, delta_1 with the two-delta weights) at M targets and writes the features Xs, Xd
+ * (M,16) and targets Ts, Td (M,4) of both networks, in the local frame of the target and scaled
+ * by the density scale S: ndelta = 1: c = (u3 - one-delta value) / (h S); ndelta = 2:
+ * c2 = (two-delta value - u3) / (gamma h^3 S), with u3, v3 (M,3) dev the values of ers_eval
+ * (three deltas) at the same targets.  gf0, gq0 (M,3,3) dev are the Jacobians d f_i / d x_j and
+ * d q_i / d x_j at x0.  valid (M) ints: 1 for targets that are training samples: within the near
+ * radius (only those carry a correction), and for ndelta = 2 with |gamma| >= 1 % of its value at
+ * b = 0 (where gamma vanishes the c2 term does too, and dividing by it only amplifies the
+ * sums' rounding).  x0, n0, b from ers_closest_point.
  */
 int ers_closure_data(ers_surface *s, const ers_params *p, const double *y, int64_t M, const double *x0,
                      const double *n0, const double *b, const double *f0, const double *q0, const double *gf0,
@@ -303,9 +317,10 @@ int ers_eval_learned(ers_surface *s, ers_closure *c, const ers_params *p, const 
  *  - M must not exceed 524,288 targets per call: the far-field partial sums (6 doubles per
  *    target) live in a fixed 24 MiB device array inside the library, and larger M is rejected
  *    with ERS_E_INVAL and a message naming the limit (split the targets across calls);
- *  - ers_last_counts is not updated.
+ *  - ers_last_counts is not updated;
+ *  - the far and near fields run one after the other on `stream` (ERS_OPT_CONCURRENT is ignored).
  * The call performs no cudaMalloc, cudaFree or other allocating call.  The fixed array (24 MiB
- * of scratch plus the 90 KB smoothing-function table) is part of the library's device image:
+ * of scratch plus the 55 KB smoothing-function table) is part of the library's device image:
  * every GPU on which this entry point is used holds it until the process exits.  The first call
  * on a device does a one-time set-up with that device current (it looks up the array's device
  * address and copies the table into it synchronously); make that first call before any stream

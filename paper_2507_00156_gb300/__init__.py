@@ -32,6 +32,7 @@ LAYER_SL = 1
 LAYER_DL = 2
 PREC_FP64 = 0
 PREC_MIXED = 1
+OPT_CONCURRENT = 1
 
 # Every symbol the header declares (checked by the tests).
 EXPORTS = ["ers_build_surface", "ers_surface_free", "ers_surface_info", "ers_set_density", "ers_closest_point",
@@ -62,7 +63,7 @@ class _Problem(ctypes.Structure):
 
 class _Params(ctypes.Structure):
     _fields_ = [("rho", ctypes.c_double * 3), ("cutoff_t", ctypes.c_double), ("precision", ctypes.c_int),
-                ("layers", ctypes.c_int)]
+                ("layers", ctypes.c_int), ("options", ctypes.c_int)]
 
 
 _lib = None
@@ -162,13 +163,15 @@ class _DevView:
         self.owner = owner
 
 
-def params(rho=(2.0, 3.0, 4.0), cutoff_t=6.0, precision=PREC_FP64, layers=LAYER_SL | LAYER_DL) -> _Params:
+def params(rho=(2.0, 3.0, 4.0), cutoff_t=6.0, precision=PREC_FP64, layers=LAYER_SL | LAYER_DL,
+           concurrent: bool = False) -> _Params:
     p = _Params()
     for k in range(3):
         p.rho[k] = float(rho[k])
     p.cutoff_t = float(cutoff_t)
     p.precision = int(precision)
     p.layers = int(layers)
+    p.options = OPT_CONCURRENT if concurrent else 0
     return p
 
 
@@ -223,8 +226,10 @@ class Surface:
         return x0, n0, b
 
     def eval(self, y, f0=None, q0=None, rho=(2.0, 3.0, 4.0), cutoff_t=6.0, precision=PREC_FP64,
-             layers=LAYER_SL | LAYER_DL, x0=None, n0=None, b=None, u=None, v=None, stream=None):
-        """ers_eval: returns (u, v) (None for a layer not selected)."""
+             layers=LAYER_SL | LAYER_DL, x0=None, n0=None, b=None, u=None, v=None, stream=None,
+             concurrent: bool = False):
+        """ers_eval: returns (u, v) (None for a layer not selected).  concurrent=True sets
+        ERS_OPT_CONCURRENT."""
         import torch
         M = y.shape[0]
         sl, dl = bool(layers & LAYER_SL), bool(layers & LAYER_DL)
@@ -232,7 +237,7 @@ class Surface:
             u = torch.empty((M, 3), dtype=torch.float64, device=y.device)
         if dl and v is None:
             v = torch.empty((M, 3), dtype=torch.float64, device=y.device)
-        p = params(rho, cutoff_t, precision, layers)
+        p = params(rho, cutoff_t, precision, layers, concurrent)
         self.last_rc = check(lib().ers_eval(self._h, ctypes.byref(p), _ptr(y), M, _ptr(x0), _ptr(n0), _ptr(b),
                                             _ptr(f0) if sl else None, _ptr(q0) if dl else None,
                                             _ptr(u) if sl else None, _ptr(v) if dl else None, _stream(stream)))
@@ -288,13 +293,22 @@ class Surface:
         return int(a.value), int(b_.value), int(c.value)
 
     def last_class_counts(self):
-        """Near pairs of the most recent eval by the number of unregularized deltas (0, 1, 2)."""
+        """Near pairs of the most recent eval by the number of deltas with r > cutoff_t delta_k
+        (0, 1, 2): the method's count of regularized terms."""
+        return self._class_counts()[:3]
+
+    def last_defect_class_counts(self):
+        """Near pairs of the most recent eval by the number of deltas whose defects 1 - s_p are
+        evaluated directly instead of from the table (0..3)."""
+        return self._class_counts()[3:]
+
+    def _class_counts(self):
         self.last_counts()
-        c = [ctypes.c_int64() for _ in range(3)]
+        c = (ctypes.c_int64 * 7)()
         L = lib()
-        L.ers_debug_class_counts.argtypes = [ctypes.c_void_p] + [ctypes.POINTER(ctypes.c_int64)] * 3
-        check(L.ers_debug_class_counts(self._h, *(ctypes.byref(z) for z in c)))
-        return [int(z.value) for z in c]
+        L.ers_debug_class_counts.argtypes = [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int64), ctypes.c_int]
+        check(L.ers_debug_class_counts(self._h, c, 7))
+        return [int(z) for z in c]
 
 
 class Batch:

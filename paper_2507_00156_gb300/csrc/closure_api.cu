@@ -85,6 +85,7 @@ struct FeatArgs {
     int64_t M;
     double h, rho0, Rc;
     int nd;  // 1: target c = (u3 - u1) / (h S); 2: target c2 = (u2 - u3) / (gamma h^3 S)
+    double gamma_min;  // nd = 2: samples need |gamma| >= gamma_min
     double c[3], a[3];
     float *Xs, *Xd, *Ts, *Td;  // features (M x 16) and targets (M x 4)
     double *scale;             // (M x 2) density scales, 0 = no correction
@@ -143,7 +144,7 @@ __global__ void k_features(FeatArgs A) {
             double c2[3];
             double den;
             if (A.nd == 2) {
-                for (int i = 0; i < 3; ++i) c2[i] = (ok && g != 0.0) ? (u2[i] - u3[3 * m + i]) / g : 0.0;
+                for (int i = 0; i < 3; ++i) c2[i] = (ok && fabs(g) >= A.gamma_min) ? (u2[i] - u3[3 * m + i]) / g : 0.0;
                 den = A.h * A.h * A.h * S;
             } else {
                 for (int i = 0; i < 3; ++i) c2[i] = ok ? (u3[3 * m + i] - u2[i]) : 0.0;
@@ -156,7 +157,7 @@ __global__ void k_features(FeatArgs A) {
             T[m * OUT_STRIDE + 3] = 0.0f;
         }
     }
-    A.valid[m] = near ? 1 : 0;
+    A.valid[m] = (near && (A.nd == 1 || fabs(A.gamma[m]) >= A.gamma_min)) ? 1 : 0;
 }
 
 // nd = 2: u = u2 - gamma h^3 S (R c2_local); nd = 1: u = u1 + h S (R c_local); R = [t1 t2 n0].
@@ -473,6 +474,9 @@ int features(ers_surface *s, ers_closure *c, const ers_params *p, const double *
     A.rho0 = p->rho[0];
     A.Rc = p->cutoff_t * p->rho[nd - 1] * s->h;
     A.nd = nd;
+    // |gamma| at b = 0: beta = (rho_1, -rho_0) / (rho_1 - rho_0), I2(0) = 1 / (3 sqrt(pi)), so
+    // |gamma(0)| = rho_0 rho_1 (rho_0 + rho_1) / (3 sqrt(pi))
+    A.gamma_min = 0.01 * p->rho[0] * p->rho[1] * (p->rho[0] + p->rho[1]) / (3.0 * 1.7724538509055160273);
     for (int i = 0; i < 3; ++i) {
         A.c[i] = s->c[i];
         A.a[i] = s->a[i];

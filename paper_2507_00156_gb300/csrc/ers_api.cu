@@ -52,6 +52,9 @@ void free_surface(ers_surface *s) {
         if (p) cudaFree(p);
     for (cudaEvent_t e : s->ev)
         if (e) cudaEventDestroy(e);
+    if (s->ev_fork) cudaEventDestroy(s->ev_fork);
+    if (s->ev_join) cudaEventDestroy(s->ev_join);
+    if (s->side) cudaStreamDestroy(s->side);
     delete s;
 }
 
@@ -78,13 +81,11 @@ const double *sigma_table_dev(int *err) {
     }
     std::lock_guard<std::mutex> lk(g_tab_mu);
     if (!g_tab_dev[dev]) {
-        const size_t ncoef = (size_t)TAB_N * 3 * TAB_NC;
-        std::vector<double> host(ncoef + TAB_N);
-        std::memcpy(host.data(), sigma_table_host(), sizeof(double) * ncoef);
-        for (int i = 0; i < TAB_N; ++i) host[ncoef + i] = 2.0 * i + 1.0;  // interval offsets
+        std::vector<double> host(TAB_DEV_BYTES / sizeof(double));
+        sigma_table_device_layout(host.data());
         double *d = nullptr;
-        e = cudaMalloc(&d, sizeof(double) * host.size());
-        if (e == cudaSuccess) e = cudaMemcpy(d, host.data(), sizeof(double) * host.size(), cudaMemcpyHostToDevice);
+        e = cudaMalloc(&d, TAB_DEV_BYTES);
+        if (e == cudaSuccess) e = cudaMemcpy(d, host.data(), TAB_DEV_BYTES, cudaMemcpyHostToDevice);
         if (e != cudaSuccess) {
             if (d) cudaFree(d);
             *err = cuda_fail(e, "uploading the smoothing-function table");
@@ -115,6 +116,15 @@ int build_surface(const ers_shape *shape, double h, ers_surface **out) {
     ers_surface *s = new (std::nothrow) ers_surface();
     if (!s) return fail(ERS_E_NOMEM, "ers_build_surface: host allocation failed");
     cudaGetDevice(&s->device);
+    {
+        cudaError_t e = cudaStreamCreateWithFlags(&s->side, cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s->ev_fork, cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s->ev_join, cudaEventDisableTiming);
+        if (e != cudaSuccess) {
+            free_surface(s);
+            return cuda_fail(e, "ers_build_surface: stream/event creation");
+        }
+    }
     for (int i = 0; i < 3; ++i) {
         s->c[i] = shape->center[i];
         s->a[i] = shape->axes[i];
@@ -239,6 +249,10 @@ int check_params(const ers_surface *s, const ers_params *p, int *warn) {
 // ndelta = 3: the method (Eq. (extrap_eqn)); ndelta = 2: the two-delta sums of the learned closure,
 // near radius cutoff_t * delta_1, per-target gamma written to `gamma` (may be NULL); ndelta = 1:
 // the single regularized sum with delta_0, near radius cutoff_t * delta_0.
+// CTAs per SM of the far (mixed) and near kernels: [0], [1] when they run concurrently,
+// [2], [3] when serial (0 = uncapped).  Changed only by the tuning hook below.
+int g_caps[4] = {2, 2, 0, 0};
+
 int eval_impl(ers_surface *s, const ers_params *p, const double *y, int64_t M, const double *x0, const double *n0,
               const double *b, const double *f0, const double *q0, double *u, double *v, void *stream, int ndelta,
               double *gamma) {
@@ -303,7 +317,7 @@ int eval_impl(ers_surface *s, const ers_params *p, const double *y, int64_t M, c
     // far-field work split: target blocks x source chunks (chunks aligned to the FP32 tiles)
     int nsm = 152;
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-    const int64_t tpc = 256;
+    const int64_t tpc = p->precision == ERS_PREC_MIXED ? 384 : 256;  // targets per far-field CTA
     const int64_t tb = (M + tpc - 1) / tpc;
     int64_t chunks = (16LL * nsm + tb - 1) / tb;
     chunks = std::max<int64_t>(1, std::min<int64_t>(chunks, std::max<int64_t>(1, s->N / (4 * TS32))));
@@ -314,21 +328,47 @@ int eval_impl(ers_surface *s, const ers_params *p, const double *y, int64_t M, c
     a.chunk_len = clen;
     if ((rc = grow(s->part, sizeof(double) * 6 * (size_t)M * chunks)) != ERS_OK) return rc;
     a.part = (double *)s->part.ptr;
-    if ((rc = grow(s->counts, sizeof(unsigned long long) * 5)) != ERS_OK) return rc;
+    if ((rc = grow(s->counts, sizeof(unsigned long long) * NCOUNTERS)) != ERS_OK) return rc;
     a.counters = (unsigned long long *)s->counts.ptr;
-    cudaError_t e = cudaMemsetAsync(a.counters, 0, sizeof(unsigned long long) * 5, st);
+    cudaError_t e = cudaMemsetAsync(a.counters, 0, sizeof(unsigned long long) * NCOUNTERS, st);
     if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync");
 
     if (prof) cudaEventRecord(s->ev[1], st);
-    e = (p->precision == ERS_PREC_MIXED) ? launch_far32(a) : launch_far64(a);
-    if (e != cudaSuccess) return cuda_fail(e, "far-field kernel");
-    if (prof) cudaEventRecord(s->ev[2], st);
-    e = launch_near(a, tab);
-    if (e != cudaSuccess) return cuda_fail(e, "near-field kernel");
+    // ERS_OPT_CONCURRENT: the far field (FP32 pipe) and the near field (FP64 pipe) run concurrently,
+    // the far field on the surface's second stream.  Both grids are capped (FAR_CTAS_PER_SM and
+    // NEAR_CTAS_PER_SM CTAs per SM, the far one also by its shared memory) so that both kernels
+    // are resident on every SM whichever starts first; k_combine then adds the far partial sums.
+    const bool overlap = p->precision == ERS_PREC_MIXED && (p->options & ERS_OPT_CONCURRENT);
+    if (overlap) {
+        const int FAR_CTAS_PER_SM = g_caps[0], NEAR_CTAS_PER_SM = g_caps[1];
+        a.far_later = true;
+        EvalArgs af = a;
+        af.stream = s->side;
+        if ((e = cudaEventRecord(s->ev_fork, st)) != cudaSuccess) return cuda_fail(e, "cudaEventRecord");
+        if ((e = cudaStreamWaitEvent(s->side, s->ev_fork, 0)) != cudaSuccess) return cuda_fail(e, "cudaStreamWaitEvent");
+        e = launch_far32(af, FAR_CTAS_PER_SM, nsm);
+        if (e != cudaSuccess) return cuda_fail(e, "far-field kernel");
+        if (prof) cudaEventRecord(s->ev[2], s->side);
+        if ((e = cudaEventRecord(s->ev_join, s->side)) != cudaSuccess) return cuda_fail(e, "cudaEventRecord");
+        e = launch_near(a, tab, NEAR_CTAS_PER_SM, nsm);
+        if (e != cudaSuccess) return cuda_fail(e, "near-field kernel");
+        if (prof) cudaEventRecord(s->ev[3], st);
+        if ((e = cudaStreamWaitEvent(st, s->ev_join, 0)) != cudaSuccess) return cuda_fail(e, "cudaStreamWaitEvent");
+        e = launch_combine(a);
+        if (e != cudaSuccess) return cuda_fail(e, "combine kernel");
+    } else {
+        e = (p->precision == ERS_PREC_MIXED) ? launch_far32(a, g_caps[2], nsm) : launch_far64(a);
+        if (e != cudaSuccess) return cuda_fail(e, "far-field kernel");
+        if (prof) cudaEventRecord(s->ev[2], st);
+        e = launch_near(a, tab, g_caps[3], nsm);
+        if (e != cudaSuccess) return cuda_fail(e, "near-field kernel");
+        if (prof) cudaEventRecord(s->ev[3], st);
+    }
     if (prof) {
-        cudaEventRecord(s->ev[3], st);
+        cudaEventRecord(s->ev[4], st);
         s->profiled = true;
         s->prof_closest = (x0 == nullptr);
+        s->prof_overlap = overlap;
     }
     s->last_counts[0] = -1;
     s->last_counts[2] = M * s->N;
@@ -474,14 +514,15 @@ int ers_last_counts(ers_surface *s, int64_t *near_targets, int64_t *near_pairs, 
     clear_error();
     if (!s) return fail(ERS_E_INVAL, "ers_last_counts: NULL surface");
     if (s->last_counts[0] == -1 && s->counts.ptr) {
-        unsigned long long hc[5] = {0, 0, 0, 0, 0};
+        unsigned long long hc[NCOUNTERS] = {};
         cudaError_t e = cudaStreamSynchronize(s->last_stream);
         if (e == cudaSuccess) e = cudaMemcpy(hc, s->counts.ptr, sizeof hc, cudaMemcpyDeviceToHost);
         if (e != cudaSuccess) return cuda_fail(e, "ers_last_counts");
         s->last_counts[0] = (int64_t)hc[0];
         s->last_counts[1] = (int64_t)hc[1];
         s->last_counts[2] -= (int64_t)hc[1];
-        for (int c = 0; c < 3; ++c) s->last_class[c] = (int64_t)hc[2 + c];
+        for (int c = 0; c < 4; ++c) s->last_dclass[c] = (int64_t)hc[2 + c];
+        for (int c = 0; c < 3; ++c) s->last_class[c] = (int64_t)hc[6 + c];
     }
     if (near_targets) *near_targets = s->last_counts[0];
     if (near_pairs) *near_pairs = s->last_counts[1];
@@ -489,13 +530,26 @@ int ers_last_counts(ers_surface *s, int64_t *near_targets, int64_t *near_pairs, 
     return ERS_OK;
 }
 
-// Test/benchmark hook (not in the public header): near pairs of the last ers_eval by the number
-// of unregularized deltas (0, 1, 2); valid after ers_last_counts.
-extern "C" int ers_debug_class_counts(ers_surface *s, int64_t *c0, int64_t *c1, int64_t *c2) {
-    if (!s) return ERS_E_INVAL;
-    *c0 = s->last_class[0];
-    *c1 = s->last_class[1];
-    *c2 = s->last_class[2];
+// Tuning hook (not in the public header): CTAs per SM of the mixed far-field and near-field
+// kernels, concurrent (far_c, near_c) and serial (far_s, near_s); 0 = uncapped in serial mode.
+// Not thread-safe with respect to concurrent ers_eval calls.
+extern "C" int ers_debug_set_caps(int far_c, int near_c, int far_s, int near_s) {
+    if (far_c < 1 || near_c < 1 || far_c > 16 || near_c > 16 || far_s < 0 || near_s < 0 || far_s > 16 || near_s > 16)
+        return ERS_E_INVAL;
+    ers::g_caps[0] = far_c;
+    ers::g_caps[1] = near_c;
+    ers::g_caps[2] = far_s;
+    ers::g_caps[3] = near_s;
+    return ERS_OK;
+}
+
+// Test/benchmark hook (not in the public header): near pairs of the last ers_eval, valid after
+// ers_last_counts.  out[0..2]: by the number of deltas with r > cutoff_t delta_k (0, 1, 2);
+// out[3..6]: by the number of deltas on the direct-defect path (0..3).  n >= 7.
+extern "C" int ers_debug_class_counts(ers_surface *s, int64_t *out, int n) {
+    if (!s || !out || n < 7) return ERS_E_INVAL;
+    for (int c = 0; c < 3; ++c) out[c] = s->last_class[c];
+    for (int c = 0; c < 4; ++c) out[3 + c] = s->last_dclass[c];
     return ERS_OK;
 }
 
@@ -516,11 +570,14 @@ int ers_last_profile(ers_surface *s, double *ms_closest, double *ms_far, double 
     clear_error();
     if (!s) return fail(ERS_E_INVAL, "ers_last_profile: NULL surface");
     if (!s->profiled) return fail(ERS_E_STATE, "ers_last_profile: no profiled evaluation yet");
-    cudaError_t e = cudaEventSynchronize(s->ev[3]);
+    cudaError_t e = cudaEventSynchronize(s->ev[4]);
     if (e != cudaSuccess) return cuda_fail(e, "ers_last_profile: cudaEventSynchronize");
+    // serial: closest ev0-ev1, far ev1-ev2, near ev2-ev3; concurrent: far ev1-ev2 (second
+    // stream), near ev1-ev3 (both from the fork); ev4 ends the evaluation
+    const int pairs[3][2] = {{0, 1}, {1, 2}, {s->prof_overlap ? 1 : 2, 3}};
     float t[3] = {0, 0, 0};
     for (int i = 0; i < 3; ++i) {
-        e = cudaEventElapsedTime(&t[i], s->ev[i], s->ev[i + 1]);
+        e = cudaEventElapsedTime(&t[i], s->ev[pairs[i][0]], s->ev[pairs[i][1]]);
         if (e != cudaSuccess) return cuda_fail(e, "ers_last_profile: cudaEventElapsedTime");
     }
     if (ms_closest) *ms_closest = s->prof_closest ? t[0] : 0.0;

@@ -21,19 +21,27 @@ namespace ers {
 // w f and w n feed the single layer (g w = w f - (f(x0).n0) w n, Eq. (Stokes_SL1)); q and w n
 // feed the double layer (Q = q - q(x0), m = w n, Eq. (Stokes_DL1)).
 constexpr int REC = 12;
+constexpr int NCOUNTERS = 9;  // near-field counters of one evaluation (EvalArgs::counters)
 constexpr int R_X = 0, R_WF = 3, R_WN = 6, R_Q = 9;
 
 // FP32 record for the mixed-precision far field (48 B): x - c_tile, w f, w n, q.
 constexpr int TS32 = 256;  // sources per FP32 tile (one centre c_tile per tile)
 
 // Interpolation table of sigma_p(tau) = s_p(t)/t^p, tau = t^2 (Eqs. (s1)-(s3)):
-// intervals of width 1/8 on tau in [0, 64), degree 6 in the local variable
-// s = 16 tau - (2 i + 1) in [-1, 1]; coefficients stored [interval][p][7], highest first.
-constexpr int TAB_INV_W = 8;      // intervals per unit tau
-constexpr int TAB_N = 512;        // tau in [0, 64)
+// intervals of width 1/16 on tau in [0, 24), degree 6 in the local variable
+// s = 32 tau - (2 i + 1) in [-1, 1].  The near field uses it only for t <= 4.7 (tau <= 22.09);
+// beyond that the defects 1 - s_p are evaluated directly.
+// Host copy: [interval][p][7] monomial coefficients, highest degree first.
+// Device copy (TAB_DEV_BYTES): TAB_N x [p][4] doubles (degrees 3..0), then TAB_N x [p] float4
+// (degrees 6, 5, 4 and the interval offset 2 i + 1).  Degrees 4..6 carry less than 2e-8 of the
+// value on every interval, so their FP32 evaluation costs at most ~2e-15 relative.
+constexpr int TAB_INV_W = 16;     // intervals per unit tau
+constexpr int TAB_N = 384;        // tau in [0, 24)
 constexpr int TAB_DEG = 6;
 constexpr int TAB_NC = TAB_DEG + 1;
-constexpr double TAB_TAU_MAX = 64.0;
+constexpr double TAB_TAU_MAX = 24.0;
+constexpr int TAB_DEV_DOUBLES = TAB_N * 3 * 4;
+constexpr size_t TAB_DEV_BYTES = (size_t)TAB_DEV_DOUBLES * 8 + (size_t)TAB_N * 3 * 16;
 
 struct Grid {
     double origin[3];
@@ -74,13 +82,18 @@ struct ers_surface {
     ers::Scratch dens64, dens32;
     int nrhs_multi = 0;
     int64_t last_counts[3] = {0, 0, 0};
-    int64_t last_class[3] = {0, 0, 0};
+    int64_t last_class[3] = {0, 0, 0};   // near pairs by number of deltas with r > cutoff_t delta
+    int64_t last_dclass[4] = {0, 0, 0, 0};  // near pairs by number of deltas on the direct-defect path
     cudaStream_t last_stream = nullptr;
     // optional per-kernel timing
     bool profile = false;
     bool profiled = false;
     bool prof_closest = false;
-    cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+    bool prof_overlap = false;
+    cudaEvent_t ev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+    // second stream for the far field when it runs concurrently with the near field
+    cudaStream_t side = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
 };
 
 namespace ers {
@@ -89,6 +102,7 @@ namespace ers {
 int64_t quadrature(const double c[3], const double a[3], double h, std::vector<double> *x, std::vector<double> *n,
                    std::vector<double> *w);
 const double *sigma_table_host();  // TAB_N * 3 * TAB_NC doubles
+void sigma_table_device_layout(void *dst);  // TAB_DEV_BYTES bytes, the device copy
 
 // Error reporting (thread-local message)
 int fail(int code, const std::string &msg);
@@ -137,20 +151,26 @@ struct EvalArgs {
     double rho[3], cutoff_t, Rc;
     int precision, layers;
     int ndelta;      // 3: extrapolation of Eq. (extrap_eqn); 2: two-delta weights (learned closure)
+    bool far_later;  // the near-field kernel leaves the far partial sums to k_combine
     double *gamma;   // ndelta == 2: per-target gamma (may be NULL)
     double *u, *v;
     double *part;    // [chunks][M][6]
     int chunks;
     int64_t chunk_len;
-    unsigned long long *counters;  // [near_targets, near_pairs, near pairs of class 0, 1, 2]
+    // [near_targets, near_pairs, near pairs of class 0..3 (deltas on the defect path),
+    //  near pairs with 0, 1, 2 deltas beyond cutoff_t]
+    unsigned long long *counters;
     cudaStream_t stream;
 };
 
 cudaError_t launch_closest(const ers_surface *s, const double *y, int64_t M, double *x0, double *n0, double *b,
                            cudaStream_t st);
 cudaError_t launch_far64(const EvalArgs &a);
-cudaError_t launch_far32(const EvalArgs &a);
-cudaError_t launch_near(const EvalArgs &a, const double *table);
+// ctas_per_sm > 0: persistent grid of at most ctas_per_sm CTAs per SM (room left for near-field CTAs)
+cudaError_t launch_far32(const EvalArgs &a, int ctas_per_sm = 0, int nsm = 0);
+cudaError_t launch_combine(const EvalArgs &a);
+// ctas_per_sm > 0: a grid of at most ctas_per_sm CTAs per SM striding over the targets
+cudaError_t launch_near(const EvalArgs &a, const double *table, int ctas_per_sm = 0, int nsm = 0);
 cudaError_t launch_density(ers_surface *s, const double *f, const double *q, cudaStream_t st);
 
 struct BatchProblemDev;
@@ -197,6 +217,30 @@ __device__ __forceinline__ float approx_float_pos(double x) {
     unsigned hi = (unsigned)(bits >> 32), lo = (unsigned)bits;
     unsigned fb = __funnelshift_l(lo, hi, 3) - (unsigned)((1023 - 127) << 23);
     return (hi < (897u << 20)) ? 0.0f : __int_as_float((int)fb);
+}
+
+// MUFU reciprocal square root with denormal inputs flushed to zero (rsqrt(0) = +inf): one
+// instruction, relative error ~1e-7.  Callers only use it where the argument is a normal float
+// or where the result is discarded (masked pairs).
+__device__ __forceinline__ float rsqrt_ftz(float x) {
+    float y;
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+// Round-to-nearest form of approx_float_pos (integer pipe only): adds half a float ulp in the
+// double's bits before truncating; relative error <= 2^-24 for 2^-126 <= x < 2^127.
+__device__ __forceinline__ float round_float_pos(double x) {
+    return approx_float_pos(__longlong_as_double(__double_as_longlong(x) + (1LL << 28)));
+}
+
+// Signed form of approx_float_pos: |result| <= |x| with relative error < 2^-23 for
+// 2^-126 <= |x| < 2^127, zero below (the shifted-out top bits of the high word hold the sign).
+__device__ __forceinline__ float approx_float(double x) {
+    long long bits = __double_as_longlong(x);
+    const unsigned hi = (unsigned)(bits >> 32), lo = (unsigned)bits;
+    const unsigned fb = __funnelshift_l(lo, hi, 3) - (unsigned)((1023 - 127) << 23);
+    return ((hi & 0x7fffffffu) < (897u << 20)) ? 0.0f : __int_as_float((int)((fb & 0x7fffffffu) | (hi & 0x80000000u)));
 }
 
 // float -> double by bit manipulation (integer pipe only); zero for zero and subnormal input.

@@ -79,8 +79,8 @@ int64_t quadrature(const double c[3], const double a[3], double h, std::vector<d
 // sigma_p(tau) = s_p(t) / t^p with tau = t^2, p = 1, 3, 5 for s_1, s_2, s_3 of
 // Eqs. (s1)-(s3).  These are entire functions of tau.  Evaluated in long double: by the
 // power series in tau of erf(t)/t and of the exponential terms for t < 1/2, otherwise by the
-// closed forms; then interpolated on each interval [i/8, (i+1)/8] at the 7 Chebyshev points
-// and converted to a degree-6 polynomial in s = 16 tau - (2 i + 1).
+// closed forms; then interpolated on each interval [i/16, (i+1)/16] at the 7 Chebyshev points
+// and converted to a degree-6 polynomial in s = 32 tau - (2 i + 1).
 // ------------------------------------------------------------------------------------------
 namespace {
 
@@ -174,6 +174,22 @@ const double *sigma_table_host() {
     return tab.data();
 }
 
+void sigma_table_device_layout(void *dst) {
+    const double *h = sigma_table_host();
+    double *d = static_cast<double *>(dst);
+    float *f = reinterpret_cast<float *>(d + TAB_DEV_DOUBLES);
+    for (int i = 0; i < TAB_N; ++i)
+        for (int p = 0; p < 3; ++p) {
+            const double *c = h + ((size_t)i * 3 + p) * TAB_NC;  // degrees 6..0
+            for (int e = 0; e < 4; ++e) d[((size_t)i * 3 + p) * 4 + e] = c[3 + e];
+            float *q = f + ((size_t)i * 3 + p) * 4;
+            q[0] = (float)c[0];
+            q[1] = (float)c[1];
+            q[2] = (float)c[2];
+            q[3] = (float)(2 * i + 1);
+        }
+}
+
 }  // namespace ers
 
 // Test hook (not in the public header): copy of the host table for inspection.
@@ -181,6 +197,13 @@ extern "C" int ers_debug_sigma_table(double *out, int64_t count) {
     const int64_t n = (int64_t)ers::TAB_N * 3 * ers::TAB_NC;
     if (!out || count < n) return ERS_E_INVAL;
     std::memcpy(out, ers::sigma_table_host(), sizeof(double) * n);
+    return ERS_OK;
+}
+
+// Test hook (not in the public header): the device layout of the table (TAB_DEV_BYTES bytes).
+extern "C" int ers_debug_sigma_device(void *out, int64_t bytes) {
+    if (!out || bytes < (int64_t)ers::TAB_DEV_BYTES) return ERS_E_INVAL;
+    ers::sigma_table_device_layout(out);
     return ERS_OK;
 }
 

@@ -34,7 +34,7 @@ struct BatchSmem {
         float stage[BTS][6 + 6 * NR];      // far phase: x - c_tile, w n, then (w f, q) per density
         double near[BW][NR][7][32];        // near phase: per-lane accumulators
     } u;
-    int sq[BW][3][64];
+    int sq[BW][NCLS][64];
     float4 cen;
     int item;
 };
@@ -99,7 +99,7 @@ __device__ void far_phase(const BatchProblemDev &P, int tb, int layers, BatchSme
             const float *sp = S.u.stage[j];
             float dx, dy, dz;
             const float r2 = dist2_fp32(yc0, yc1, yc2, sp[0], sp[1], sp[2], &dx, &dy, &dz);
-            float ri = rsqrtf(r2);
+            float ri = rsqrt_ftz(r2);  // far pairs have r2 >= Rc^2; the others are masked
             ri = (r2 > rc2) ? ri : 0.0f;
             const float ri2 = ri * ri;
             const float dwn = fmaf(dz, sp[5], fmaf(dy, sp[4], dx * sp[3]));
@@ -156,10 +156,10 @@ __device__ __forceinline__ void near_pair(const BatchProblemDev &P, const Geom &
     const double r2 = dist2_fp64(dx, dy, dz);
     if (!is_near<ERS_PREC_MIXED>(P.sd, T, j, r2, P.Rc, P.sp.rc2f)) return;
     double K1, K3, K5;
-    kernel_factors<CLS>(T, tab, r2, K1, K3, K5);
-    const double h3[3] = {xs[0] - T.x0[0], xs[1] - T.x0[1], xs[2] - T.x0[2]};
+    kernel_factors<CLS>(T, P.sp, tab, r2, K1, K3, K5);
     const double nm = fma(T.n0[2], wn[2], fma(T.n0[1], wn[1], T.n0[0] * wn[0]));
-    const double xm = fma(h3[2], wn[2], fma(h3[1], wn[1], h3[0] * wn[0]));
+    const double W = fma(dz, wn[2], fma(dy, wn[1], dx * wn[0]));
+    const DLPair D = dl_pair(T, r2, K3, K5, nm, W);  // shared by the NR densities
     const double *dj = P.dens64 + j * (6 * NR);
 #pragma unroll
     for (int r = 0; r < NR; ++r) {
@@ -176,12 +176,12 @@ __device__ __forceinline__ void near_pair(const BatchProblemDev &P, const Geom &
             const double qs[3] = {__ldg(dj + 6 * r + 3), __ldg(dj + 6 * r + 4), __ldg(dj + 6 * r + 5)};
             const double *q0p = P.q0 + ((int64_t)r * P.M + m) * 3;
             const double q0[3] = {q0p[0], q0p[1], q0p[2]};
-            double accN = a[3][lane], accX[3] = {a[4][lane], a[5][lane], a[6][lane]};
-            dl_accumulate(T, r2, K3, K5, h3, nm, xm, qs, q0, accN, accX);
+            double accN = a[3][lane], accD[3] = {a[4][lane], a[5][lane], a[6][lane]};
+            dl_accumulate(D, T, dx, dy, dz, nm, qs, q0, accN, accD);
             a[3][lane] = accN;
-            a[4][lane] = accX[0];
-            a[5][lane] = accX[1];
-            a[6][lane] = accX[2];
+            a[4][lane] = accD[0];
+            a[5][lane] = accD[1];
+            a[6][lane] = accD[2];
         }
     }
 }
@@ -199,7 +199,7 @@ __device__ void near_phase(const BatchProblemDev &P, int tb, int layers, const d
         if (near) {
             Geom T;
             load_geom(lane, P.y, P.x0, P.n0, bm, m, rho, P.sp.h, T);
-            T.tcf = P.sp.tcf;
+            set_cutoff(T, P.sp);
             double c[NR];
             for (int r = 0; r < NR; ++r) {
                 const double *f0 = P.f0 + ((int64_t)r * P.M + m) * 3;
@@ -211,7 +211,8 @@ __device__ void near_phase(const BatchProblemDev &P, int tb, int layers, const d
                 if (!valid) return;
                 if (cls == 0) near_pair<0, NR>(P, T, tab, jj, c, m, lane, warp, layers, S);
                 else if (cls == 1) near_pair<1, NR>(P, T, tab, jj, c, m, lane, warp, layers, S);
-                else near_pair<2, NR>(P, T, tab, jj, c, m, lane, warp, layers, S);
+                else if (cls == 2) near_pair<2, NR>(P, T, tab, jj, c, m, lane, warp, layers, S);
+                else near_pair<3, NR>(P, T, tab, jj, c, m, lane, warp, layers, S);
             });
             const double chi = bm < 0.0 ? 1.0 : (bm > 0.0 ? 0.0 : 0.5);
             for (int r = 0; r < NR; ++r) {
@@ -223,11 +224,11 @@ __device__ void near_phase(const BatchProblemDev &P, int tb, int layers, const d
                 }
                 if (dl && lane >= 3 && lane < 6) {
                     const int i = lane - 3;
-                    const double ax = i == 0 ? tot[4] : (i == 1 ? tot[5] : tot[6]);
+                    const double ad = i == 0 ? tot[4] : (i == 1 ? tot[5] : tot[6]);
                     const double ni = i == 0 ? T.n0[0] : (i == 1 ? T.n0[1] : T.n0[2]);
                     const double qi = P.q0[((int64_t)r * P.M + m) * 3 + i];
                     P.v[((int64_t)r * P.M + m) * 3 + i] =
-                        S.far[tt][r][lane] + (-6.0 * INV8PI) * fma(tot[3], ni, ax) + chi * qi;
+                        S.far[tt][r][lane] + (-6.0 * INV8PI) * fma(tot[3], ni, -ad) + chi * qi;
                 }
             }
             __syncwarp();

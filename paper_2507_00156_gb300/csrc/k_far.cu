@@ -6,12 +6,17 @@
 //   DL: v_i += 1/(8 pi) (-6) d_i (d.Q) (d.m) / r^5,               Q = q - q(x0), m = w n
 // with d = y - x (Eqs. (Stokeslet), (Stresslet)).
 //
-// Layout: grid (target blocks, source chunks).  A CTA owns TPB = 128 * TPT targets (TPT per
-// thread, held in registers) and one contiguous chunk of the cell-sorted source records; it
+// Layout: work items (target block, source chunk).  An item is TPB = 128 * TPT targets (TPT per
+// thread, held in registers) and one contiguous chunk of the cell-sorted source records; the CTA
 // stages tiles of the chunk in shared memory and every thread reads each staged source as a
-// broadcast.  Partial sums go to part[chunk][target][6]; the near-field kernel adds the chunks.
+// broadcast.  Partial sums go to part[chunk][target][6], added by the near-field kernel or, when
+// the two kernels run concurrently, by k_combine.  The FP64 kernel runs one item per CTA; the
+// mixed kernel loops over items with a stride of the grid, which may be capped (see
+// launch_far32) so that near-field CTAs fit on every SM beside it.
 // The mask "r^2 > Rc^2" is evaluated with the same operation order as the near-field
 // selection, so every pair lands in exactly one of the two sums.
+#include <algorithm>
+
 #include "ers_internal.h"
 
 namespace ers {
@@ -132,10 +137,9 @@ struct TargetF32 {
 };
 
 template <bool SL, bool DL, int TPT, int FLUSH>
-__global__ void __launch_bounds__(NT) k_far32(EvalArgs A, float rc2f) {
-    __shared__ float4 srec[TS32 * 3];
-    __shared__ float4 scen;
-    const int64_t j0 = (int64_t)blockIdx.y * A.chunk_len;  // multiple of TS32
+__device__ __forceinline__ void far32_item(const EvalArgs &A, float rc2f, int64_t tbi, int64_t chunk,
+                                           float4 *srec, float4 &scen) {
+    const int64_t j0 = chunk * A.chunk_len;  // multiple of TS32
     const int64_t j1 = min(A.sd.N, j0 + A.chunk_len);
     const float *__restrict__ rec = A.sd.rec32;
 
@@ -145,7 +149,7 @@ __global__ void __launch_bounds__(NT) k_far32(EvalArgs A, float rc2f) {
     float accf[TPT][6];
 #pragma unroll
     for (int t = 0; t < TPT; ++t) {
-        const int64_t m = (int64_t)blockIdx.x * (NT * TPT) + t * NT + threadIdx.x;
+        const int64_t m = tbi * (NT * TPT) + t * NT + threadIdx.x;
         TargetF64 D;
         load_target(A, m, SL, DL, D, valid[t]);
         for (int i = 0; i < 3; ++i) {
@@ -186,7 +190,7 @@ __global__ void __launch_bounds__(NT) k_far32(EvalArgs A, float rc2f) {
             for (int t = 0; t < TPT; ++t) {
                 float dx, dy, dz;
                 const float r2 = dist2_fp32(yc[t][0], yc[t][1], yc[t][2], r0.x, r0.y, r0.z, &dx, &dy, &dz);
-                float ri = rsqrtf(r2);  // MUFU approximation, relative error ~1e-7
+                float ri = rsqrt_ftz(r2);  // MUFU approximation, relative error ~1e-7; far pairs have r2 >= Rc^2
                 ri = (r2 > T[t].rc2) ? ri : 0.0f;
                 const float ri2 = ri * ri;
                 if (SL) {
@@ -223,8 +227,8 @@ __global__ void __launch_bounds__(NT) k_far32(EvalArgs A, float rc2f) {
 #pragma unroll
     for (int t = 0; t < TPT; ++t) {
         if (!valid[t]) continue;
-        const int64_t m = (int64_t)blockIdx.x * (NT * TPT) + t * NT + threadIdx.x;
-        double *o = A.part + ((int64_t)blockIdx.y * A.M + m) * 6;
+        const int64_t m = tbi * (NT * TPT) + t * NT + threadIdx.x;
+        double *o = A.part + (chunk * A.M + m) * 6;
         for (int i = 0; i < 6; ++i) acc[t][i] += (double)accf[t][i];
         o[0] = acc[t][0] * INV8PI;
         o[1] = acc[t][1] * INV8PI;
@@ -232,6 +236,18 @@ __global__ void __launch_bounds__(NT) k_far32(EvalArgs A, float rc2f) {
         o[3] = acc[t][3] * (-6.0 * INV8PI);
         o[4] = acc[t][4] * (-6.0 * INV8PI);
         o[5] = acc[t][5] * (-6.0 * INV8PI);
+    }
+}
+
+template <bool SL, bool DL, int TPT, int FLUSH>
+__global__ void __launch_bounds__(NT, 4) k_far32(EvalArgs A, float rc2f, int64_t ntb) {
+    __shared__ float4 srec[TS32 * 3];
+    __shared__ float4 scen;
+    const int64_t nitems = ntb * A.chunks;
+    for (int64_t item = blockIdx.x; item < nitems; item += gridDim.x) {
+        const int64_t tbi = item % ntb, chunk = item / ntb;
+        __syncthreads();  // the previous item's last tile is no longer read
+        far32_item<SL, DL, TPT, FLUSH>(A, rc2f, tbi, chunk, srec, scen);
     }
 }
 
@@ -247,20 +263,55 @@ cudaError_t far64_dispatch(const EvalArgs &a) {
 }
 
 template <int TPT>
-cudaError_t far32_dispatch(const EvalArgs &a) {
+cudaError_t far32_dispatch(const EvalArgs &a, int ctas_per_sm, int nsm) {
     const int64_t tb = (a.M + NT * TPT - 1) / (NT * TPT);
-    dim3 grid((unsigned)tb, (unsigned)a.chunks);
+    const int64_t nitems = tb * a.chunks;
+    int64_t grid = nitems;
+    size_t pad = 0;
+    if (ctas_per_sm > 0) {
+        // at most ctas_per_sm CTAs per SM: dynamic shared memory that leaves room for no more
+        // (228 KB per SM, 1 KB reserved per CTA), and a grid of that many CTAs per SM
+        const size_t per_cta = (228u << 10) / (size_t)(ctas_per_sm + 1) + 1;
+        const size_t stat = sizeof(float4) * (TS32 * 3 + 1) + 1024;
+        pad = per_cta > stat ? per_cta - stat : 0;
+        grid = std::min<int64_t>(nitems, (int64_t)ctas_per_sm * nsm);
+    }
     const bool sl = a.layers & ERS_LAYER_SL, dl = a.layers & ERS_LAYER_DL;
     const float rc2f = (float)(a.Rc * a.Rc);  // same rounding as the near-field copy
-    if (sl && dl) k_far32<true, true, TPT, 2><<<grid, NT, 0, a.stream>>>(a, rc2f);
-    else if (sl) k_far32<true, false, TPT, 2><<<grid, NT, 0, a.stream>>>(a, rc2f);
-    else k_far32<false, true, TPT, 2><<<grid, NT, 0, a.stream>>>(a, rc2f);
+    auto kern = (sl && dl) ? k_far32<true, true, TPT, 2> : (sl ? k_far32<true, false, TPT, 2> : k_far32<false, true, TPT, 2>);
+    if (pad > 0) {
+        // static + dynamic shared memory above 48 KB needs the opt-in (not a stream operation)
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pad);
+        if (e != cudaSuccess) return e;
+    }
+    kern<<<(unsigned)grid, NT, pad, a.stream>>>(a, rc2f, tb);
     return cudaGetLastError();
+}
+
+// u += sum_c part[c][m][0..2], v += sum_c part[c][m][3..5] (far field into the near-field result).
+__global__ void k_combine(const double *__restrict__ part, int chunks, int64_t M, double *u, double *v) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;  // (target, component)
+    if (i >= 6 * M) return;
+    const int64_t m = i / 6;
+    const int c6 = (int)(i - 6 * m);
+    double s = 0.0;
+    for (int c = 0; c < chunks; ++c) s += part[((int64_t)c * M + m) * 6 + c6];
+    double *o = c6 < 3 ? u : v;
+    if (o) o[3 * m + (c6 < 3 ? c6 : c6 - 3)] += s;
 }
 
 }  // namespace
 
 cudaError_t launch_far64(const EvalArgs &a) { return far64_dispatch<2, 64>(a); }
-cudaError_t launch_far32(const EvalArgs &a) { return far32_dispatch<2>(a); }
+cudaError_t launch_far32(const EvalArgs &a, int ctas_per_sm, int nsm) { return far32_dispatch<3>(a, ctas_per_sm, nsm); }
+
+cudaError_t launch_combine(const EvalArgs &a) {
+    if (a.M == 0) return cudaSuccess;
+    const int64_t n = 6 * a.M;
+    const bool sl = a.layers & ERS_LAYER_SL, dl = a.layers & ERS_LAYER_DL;
+    k_combine<<<(unsigned)((n + 255) / 256), 256, 0, a.stream>>>(a.part, a.chunks, a.M, sl ? a.u : nullptr,
+                                                                  dl ? a.v : nullptr);
+    return cudaGetLastError();
+}
 
 }  // namespace ers

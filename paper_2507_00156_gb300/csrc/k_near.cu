@@ -10,17 +10,17 @@
 // tau = (r/delta)^2, and sigma_p comes from a piecewise degree-6 interpolation table.
 // Single layer (Eq. (Sreg)):  K1 g + K3 d (d.g).
 // Double layer (Eqs. (Tsplit), (Treg)):  -6 [ t1 (K3 - (r^2 - b^2) K5) + t2 K5 ] : Q (w n),
-// contracted in closed form: with P = (n0.Q)(n0.m), R = (xh.Q)(xh.m),
-// S = (xh.Q)(n0.m) + (n0.Q)(xh.m), K = K3 - (r^2 - b^2) K5, xh = x - x0:
-//   t1 : Q m = n0 (b P - S) - xh P,   t2 : Q m = n0 (b R) + xh (b S - R).
+// contracted in closed form (dl_pair / dl_accumulate in near_common.cuh).
 // The weights alpha are the first row of the inverse of A_k = [1, rho_k I0(b/delta_k),
 // rho_k^3 I2(b/delta_k)] (Eqs. (extrap_eqn), (I0), (I2)), by Cramer's rule.
 //
 // One warp per target.  The warp walks the rows of the cell grid that meet the ball of radius
 // Rc, tests candidates with an FP32 prefilter (conservative margin), and queues survivors by
-// class c = number of delta_k with r > cutoff_t delta_k, so that each batch of 32 runs one
-// code path.  Each batch then makes the exact FP64 (or, for the mixed far field, the
+// class c = number of delta_k with r > min(4.7, cutoff_t) delta_k, so that each batch of 32 runs
+// one code path.  Each batch then makes the exact FP64 (or, for the mixed far field, the
 // identical FP32) near/far test, so that the partition matches the far-field mask exactly.
+#include <algorithm>
+
 #include "near_common.cuh"
 
 namespace ers {
@@ -30,9 +30,10 @@ using namespace nearc;
 constexpr int WPB = 4;  // warps per block
 
 template <int CLS, int PREC, bool SL, bool DL, int ND>
-__device__ __forceinline__ void process(const EvalArgs &A, const Geom &T, double c, const double q0[3],
-                                        const double *__restrict__ tab, float rc2f, int64_t j, double accU[3],
-                                        double &accN, double accX[3], int npairs[3]) {
+__device__ __forceinline__ void process(const EvalArgs &A, const Geom &T, const ScanParams &P, double c,
+                                        const double q0[3], const double *__restrict__ tab, int64_t j,
+                                        double accU[3], double &accN, double accD[3], int npairs[NCLS],
+                                        int nunreg[3]) {
     const double2 *r = reinterpret_cast<const double2 *>(A.sd.rec + j * REC);
     const double2 r0 = __ldg(r + 0), r1 = __ldg(r + 1), r2v = __ldg(r + 2);
     const double2 r3 = __ldg(r + 3), r4 = __ldg(r + 4), r5 = __ldg(r + 5);
@@ -44,29 +45,32 @@ __device__ __forceinline__ void process(const EvalArgs &A, const Geom &T, double
     const double dy = __dsub_rn(T.y[1], xs[1]);
     const double dz = __dsub_rn(T.y[2], xs[2]);
     const double r2 = dist2_fp64(dx, dy, dz);
-    if (!is_near<PREC>(A.sd, T, j, r2, A.Rc, rc2f)) return;
+    if (!is_near<PREC>(A.sd, T, j, r2, A.Rc, P.rc2f)) return;
     ++npairs[CLS];
+    {  // pairs by number of deltas with r > cutoff_t delta_k (the method's own count of regularized terms)
+        const float r2f = approx_float_pos(r2);
+        const int u = (r2f > P.cut2[0]) + (r2f > P.cut2[1]);
+        nunreg[0] += u == 0;
+        nunreg[1] += u == 1;
+        nunreg[2] += u == 2;
+    }
     double K1, K3, K5;
-    kernel_factors<CLS, ND>(T, tab, r2, K1, K3, K5);
+    kernel_factors<CLS, ND>(T, P, tab, r2, K1, K3, K5);
     if (SL) sl_accumulate(dx, dy, dz, K1, K3, c, wf, wn, accU);
     if (DL) {
-        const double h3[3] = {xs[0] - T.x0[0], xs[1] - T.x0[1], xs[2] - T.x0[2]};
         const double nm = fma(T.n0[2], wn[2], fma(T.n0[1], wn[1], T.n0[0] * wn[0]));
-        const double xm = fma(h3[2], wn[2], fma(h3[1], wn[1], h3[0] * wn[0]));
-        dl_accumulate(T, r2, K3, K5, h3, nm, xm, qs, q0, accN, accX);
+        const double W = fma(dz, wn[2], fma(dy, wn[1], dx * wn[0]));
+        const DLPair D = dl_pair(T, r2, K3, K5, nm, W);
+        dl_accumulate(D, T, dx, dy, dz, nm, qs, q0, accN, accD);
     }
 }
 
 template <int PREC, bool SL, bool DL, int ND>
-__global__ void __launch_bounds__(WPB * 32) k_near(EvalArgs A, ScanParams P, const double *__restrict__ tab) {
-    __shared__ int sq[WPB][3][64];
-    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-    const int64_t m = (int64_t)blockIdx.x * WPB + wib;
-    if (m >= A.M) return;  // warp-uniform
-
+__device__ __forceinline__ void near_target(const EvalArgs &A, const ScanParams &P, const double *__restrict__ tab,
+                                            int64_t m, int lane, int (*sq)[64]) {
     // sum of the far-field chunk partials: lane i < 6 holds component i
     double fs = 0.0;
-    if (lane < 6)
+    if (lane < 6 && !A.far_later)
         for (int c = 0; c < A.chunks; ++c) fs += A.part[((int64_t)c * A.M + m) * 6 + lane];
     const double bm = A.b[m];
     if (!(fabs(bm) <= A.Rc)) {
@@ -79,36 +83,39 @@ __global__ void __launch_bounds__(WPB * 32) k_near(EvalArgs A, ScanParams P, con
     Geom T;
     double gam = 0.0;
     load_geom(lane, A.y, A.x0, A.n0, bm, m, A.rho, P.h, T, A.ndelta, &gam);
-    T.tcf = P.tcf;
+    set_cutoff(T, P);
     if (A.gamma && lane == 0) A.gamma[m] = gam;
     double q0[3];
     for (int i = 0; i < 3; ++i) q0[i] = DL ? A.q0[3 * m + i] : 0.0;
     const double c = SL ? fma(A.f0[3 * m + 2], T.n0[2], fma(A.f0[3 * m + 1], T.n0[1], A.f0[3 * m] * T.n0[0])) : 0.0;
 
-    double accU[3] = {0.0, 0.0, 0.0}, accX[3] = {0.0, 0.0, 0.0}, accN = 0.0;
-    int npairs[3] = {0, 0, 0};  // near pairs by class (number of unregularized deltas)
-    scan_near(A.sd, T, P, sq[wib], lane, [&](int cls, int jj, bool valid) {
+    double accU[3] = {0.0, 0.0, 0.0}, accD[3] = {0.0, 0.0, 0.0}, accN = 0.0;
+    int npairs[NCLS] = {0, 0, 0, 0};  // near pairs by class
+    int nunreg[3] = {0, 0, 0};        // near pairs by number of deltas beyond the cutoff
+    scan_near(A.sd, T, P, sq, lane, [&](int cls, int jj, bool valid) {
         if (!valid) return;
-        if (cls == 0) process<0, PREC, SL, DL, ND>(A, T, c, q0, tab, P.rc2f, jj, accU, accN, accX, npairs);
-        else if (cls == 1) process<1, PREC, SL, DL, ND>(A, T, c, q0, tab, P.rc2f, jj, accU, accN, accX, npairs);
-        else process<2, PREC, SL, DL, ND>(A, T, c, q0, tab, P.rc2f, jj, accU, accN, accX, npairs);
+        if (cls == 0) process<0, PREC, SL, DL, ND>(A, T, P, c, q0, tab, jj, accU, accN, accD, npairs, nunreg);
+        else if (cls == 1) process<1, PREC, SL, DL, ND>(A, T, P, c, q0, tab, jj, accU, accN, accD, npairs, nunreg);
+        else if (cls == 2) process<2, PREC, SL, DL, ND>(A, T, P, c, q0, tab, jj, accU, accN, accD, npairs, nunreg);
+        else process<3, PREC, SL, DL, ND>(A, T, P, c, q0, tab, jj, accU, accN, accD, npairs, nunreg);
     });
     for (int i = 0; i < 3; ++i) {
         accU[i] = warp_sum(accU[i]);
-        accX[i] = warp_sum(accX[i]);
+        accD[i] = warp_sum(accD[i]);
     }
     accN = warp_sum(accN);
-    int np[3] = {npairs[0], npairs[1], npairs[2]};
+    if (A.counters) {
+        int np[NCLS + 3] = {npairs[0], npairs[1], npairs[2], npairs[3], nunreg[0], nunreg[1], nunreg[2]};
 #pragma unroll
-    for (int cc = 0; cc < 3; ++cc)
+        for (int cc = 0; cc < NCLS + 3; ++cc)
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) np[cc] += __shfl_xor_sync(FULL, np[cc], o);
-    if (lane == 0 && A.counters) {
-        atomicAdd(A.counters + 0, 1ull);
-        atomicAdd(A.counters + 1, (unsigned long long)(np[0] + np[1] + np[2]));
-        atomicAdd(A.counters + 2, (unsigned long long)np[0]);
-        atomicAdd(A.counters + 3, (unsigned long long)np[1]);
-        atomicAdd(A.counters + 4, (unsigned long long)np[2]);
+            for (int o = 16; o > 0; o >>= 1) np[cc] += __shfl_xor_sync(FULL, np[cc], o);
+        if (lane == 0) {
+            atomicAdd(A.counters + 0, 1ull);
+            atomicAdd(A.counters + 1, (unsigned long long)(np[0] + np[1] + np[2] + np[3]));
+#pragma unroll
+            for (int cc = 0; cc < NCLS + 3; ++cc) atomicAdd(A.counters + 2 + cc, (unsigned long long)np[cc]);
+        }
     }
     if (SL && lane < 3) {
         const double a = lane == 0 ? accU[0] : (lane == 1 ? accU[1] : accU[2]);
@@ -116,35 +123,46 @@ __global__ void __launch_bounds__(WPB * 32) k_near(EvalArgs A, ScanParams P, con
     }
     if (DL && lane >= 3 && lane < 6) {
         const int i = lane - 3;
-        const double ax = i == 0 ? accX[0] : (i == 1 ? accX[1] : accX[2]);
+        const double ad = i == 0 ? accD[0] : (i == 1 ? accD[1] : accD[2]);
         const double ni = i == 0 ? T.n0[0] : (i == 1 ? T.n0[1] : T.n0[2]);
         const double qi = i == 0 ? q0[0] : (i == 1 ? q0[1] : q0[2]);
         const double chi = bm < 0.0 ? 1.0 : (bm > 0.0 ? 0.0 : 0.5);
-        A.v[3 * m + i] = fs + (-6.0 * INV8PI) * fma(accN, ni, ax) + chi * qi;
+        A.v[3 * m + i] = fs + (-6.0 * INV8PI) * fma(accN, ni, -ad) + chi * qi;
     }
 }
 
+template <int PREC, bool SL, bool DL, int ND>
+__global__ void __launch_bounds__(WPB * 32) k_near(EvalArgs A, ScanParams P, const double *__restrict__ tab) {
+    __shared__ int sq[WPB][NCLS][64];
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    // one target per warp; a capped grid strides over the targets
+    for (int64_t m = (int64_t)blockIdx.x * WPB + wib; m < A.M; m += (int64_t)gridDim.x * WPB)
+        near_target<PREC, SL, DL, ND>(A, P, tab, m, lane, sq[wib]);
+}
+
 template <int PREC>
-cudaError_t near_dispatch(const EvalArgs &a, ScanParams P, const double *tab) {
-    const int64_t grid = (a.M + WPB - 1) / WPB;
+cudaError_t near_dispatch(const EvalArgs &a, ScanParams P, const double *tab, int ctas_per_sm, int nsm) {
+    int64_t grid = (a.M + WPB - 1) / WPB;
+    if (ctas_per_sm > 0) grid = std::min<int64_t>(grid, (int64_t)ctas_per_sm * nsm);
+    const unsigned g = (unsigned)grid;
     const bool sl = a.layers & ERS_LAYER_SL, dl = a.layers & ERS_LAYER_DL;
     if (a.ndelta == 1 || a.ndelta == 2) {  // learned closure: both layers
         if (!(sl && dl)) return cudaErrorInvalidValue;
-        if (a.ndelta == 1) k_near<PREC, true, true, 1><<<(unsigned)grid, WPB * 32, 0, a.stream>>>(a, P, tab);
-        else k_near<PREC, true, true, 2><<<(unsigned)grid, WPB * 32, 0, a.stream>>>(a, P, tab);
-    } else if (sl && dl) k_near<PREC, true, true, 3><<<(unsigned)grid, WPB * 32, 0, a.stream>>>(a, P, tab);
-    else if (sl) k_near<PREC, true, false, 3><<<(unsigned)grid, WPB * 32, 0, a.stream>>>(a, P, tab);
-    else k_near<PREC, false, true, 3><<<(unsigned)grid, WPB * 32, 0, a.stream>>>(a, P, tab);
+        if (a.ndelta == 1) k_near<PREC, true, true, 1><<<g, WPB * 32, 0, a.stream>>>(a, P, tab);
+        else k_near<PREC, true, true, 2><<<g, WPB * 32, 0, a.stream>>>(a, P, tab);
+    } else if (sl && dl) k_near<PREC, true, true, 3><<<g, WPB * 32, 0, a.stream>>>(a, P, tab);
+    else if (sl) k_near<PREC, true, false, 3><<<g, WPB * 32, 0, a.stream>>>(a, P, tab);
+    else k_near<PREC, false, true, 3><<<g, WPB * 32, 0, a.stream>>>(a, P, tab);
     return cudaGetLastError();
 }
 
 }  // namespace
 
-cudaError_t launch_near(const EvalArgs &a, const double *tab) {
+cudaError_t launch_near(const EvalArgs &a, const double *tab, int ctas_per_sm, int nsm) {
     if (a.M == 0) return cudaSuccess;
     const ScanParams P = scan_params(a.s, a.Rc, a.rho, a.cutoff_t);
-    if (a.precision == ERS_PREC_FP64) return near_dispatch<ERS_PREC_FP64>(a, P, tab);
-    return near_dispatch<ERS_PREC_MIXED>(a, P, tab);
+    if (a.precision == ERS_PREC_FP64) return near_dispatch<ERS_PREC_FP64>(a, P, tab, ctas_per_sm, nsm);
+    return near_dispatch<ERS_PREC_MIXED>(a, P, tab, ctas_per_sm, nsm);
 }
 
 }  // namespace ers

@@ -18,7 +18,8 @@ namespace {
 // [M][6] doubles.  24 MiB => at most NOALLOC_MAX_M targets per call.
 constexpr size_t NOALLOC_SCRATCH_BYTES = (size_t)24 << 20;
 constexpr int64_t NOALLOC_MAX_M = (int64_t)(NOALLOC_SCRATCH_BYTES / (6 * sizeof(double)));
-constexpr size_t NOALLOC_TABLE_DOUBLES = (size_t)TAB_N * 3 * TAB_NC + TAB_N;
+constexpr size_t NOALLOC_TABLE_DOUBLES = TAB_DEV_BYTES / sizeof(double);
+static_assert(TAB_DEV_BYTES % sizeof(double) == 0, "table layout");
 
 __device__ __align__(256) unsigned char g_noalloc_scratch[NOALLOC_SCRATCH_BYTES];
 __device__ __align__(256) double g_noalloc_table[NOALLOC_TABLE_DOUBLES];
@@ -45,10 +46,9 @@ int setup_device(int dev, DevState **out) {
         e = cudaGetSymbolAddress(&p, g_noalloc_table);
         if (e != cudaSuccess) return cuda_fail(e, "ers_eval_noalloc: cudaGetSymbolAddress(table)");
         st.table = (double *)p;
-        double host[NOALLOC_TABLE_DOUBLES];
-        std::memcpy(host, sigma_table_host(), sizeof(double) * (size_t)TAB_N * 3 * TAB_NC);
-        for (int i = 0; i < TAB_N; ++i) host[(size_t)TAB_N * 3 * TAB_NC + i] = 2.0 * i + 1.0;
-        e = cudaMemcpyToSymbol(g_noalloc_table, host, sizeof host);
+        std::vector<double> host(NOALLOC_TABLE_DOUBLES);
+        sigma_table_device_layout(host.data());
+        e = cudaMemcpyToSymbol(g_noalloc_table, host.data(), TAB_DEV_BYTES);
         if (e != cudaSuccess) return cuda_fail(e, "ers_eval_noalloc: cudaMemcpyToSymbol(table)");
         st.ready = true;
     }

@@ -8,7 +8,8 @@
 //   double layer (Eqs. (Tsplit), (Treg)):  -6 [t1 (K3 - (r^2 - b^2) K5) + t2 K5] : Q m,
 //     Q = q - q(x0), m = w n; with P = (n0.Q)(n0.m), R = (xh.Q)(xh.m),
 //     S = (xh.Q)(n0.m) + (n0.Q)(xh.m), K = K3 - (r^2 - b^2) K5, xh = x - x0:
-//       t1 : Q m = n0 (b P - S) - xh P,   t2 : Q m = n0 (b R) + xh (b S - R).
+//       t1 : Q m = n0 (b P - S) - xh P,   t2 : Q m = n0 (b R) + xh (b S - R),
+//     evaluated in the equivalent form of dl_accumulate (in terms of d = y - x = b n0 - xh).
 // alpha = first row of the inverse of A_k = [1, rho_k I0(b/delta_k), rho_k^3 I2(b/delta_k)]
 // (Eqs. (extrap_eqn), (I0), (I2)), by Cramer's rule.
 #pragma once
@@ -24,24 +25,44 @@ constexpr double INVSQRTPI = 0.56418958354775628695;
 
 // Density-independent constants of one near target.
 struct Geom {
-    double y[3], x0[3], n0[3], b;
-    double invd2[3], ad1[3], ad3[3], ad5[3], apre[2];
-    float yh[3], yl[3];  // y = yh + yl in floats (mixed-mode classification)
-    float alf[3];        // extrapolation weights in FP32 (for the small defects 1 - s_p)
-    float tcf;           // cutoff_t: s_p := 1 beyond it
+    double y[3], x0[3], n0[3], b, b2;  // b2 = 2 b
+    double invd2[3], ad1[3], ad3[3], ad5[3];
+    double apre[3];         // alpha_0, alpha_0 + alpha_1, alpha_0 + alpha_1 + alpha_2
+    float yh[3], yl[3];     // y = yh + yl in floats (mixed-mode classification)
+    float id2h[3], id2l[3]; // 1/delta_k^2 = id2h + id2l in floats
+    float alf[3];           // extrapolation weights in FP32 (for the small defects 1 - s_p)
+    float tcf2;             // cutoff_t^2: s_p := 1 beyond t = cutoff_t
+    bool cut_small;         // cutoff_t < DEFECT_T: the table path may meet the cutoff
 };
 
 // Beyond t = r/delta = DEFECT_T the defects 1 - s_p(t) are below 2.1e-8 and are evaluated in
 // FP32 instead of from the FP64 table.
 constexpr double DEFECT_T = 4.7;
+// Near-pair classes: c = number of delta_k (from delta_0 up) with r > min(DEFECT_T, cutoff_t) delta_k.
+constexpr int NCLS = 4;
 
 struct ScanParams {
-    float rc2f;   // exact FP32 threshold of the mixed far field
-    float rpre;   // FP32 prefilter radius (Rc plus a conservative margin)
-    float th[2];  // FP32 class thresholds (min(DEFECT_T, cutoff_t) delta_k)^2, k = 0, 1
-    float tcf;    // cutoff_t
+    float rc2f;     // exact FP32 threshold of the mixed far field
+    float rpre;     // FP32 prefilter radius (Rc plus a conservative margin)
+    float th[3];    // FP32 class thresholds (min(DEFECT_T, cutoff_t) delta_k)^2
+    float cut2[2];  // (cutoff_t delta_k)^2, k = 0, 1: for the pair counts by regularized deltas
+    float tcf2;       // cutoff_t^2
+    double tc2;       // cutoff_t^2 in FP64
+    double cut2d[3];  // (cutoff_t delta_k)^2 in FP64, delta_k = rho_k h
     double h;
 };
+
+// Relative width of the band around cutoff_t^2 where the FP32 value of t^2 cannot decide
+// t > cutoff_t (FP32 t^2 is within 3e-7 of the exact one).  There the decision is r^2 >
+// (cutoff_t rho_k h)^2 in FP64, which is exact for the many node pairs of the lattice rule whose
+// distance is an exact multiple of h (r = 2 i h, so t = i at delta = 2h): such ties count as
+// t = cutoff_t, regularized, as in exact arithmetic.
+constexpr float CUT_BAND = 1e-6f;
+
+__device__ __forceinline__ void set_cutoff(Geom &T, const ScanParams &P) {
+    T.tcf2 = P.tcf2;
+    T.cut_small = P.tc2 < DEFECT_T * DEFECT_T;
+}
 
 // Extrapolation weights for signed distance b; every lane of the warp calls it, lanes 0..2
 // evaluate I0, I2 at lambda_k = |b| / (rho_k h).
@@ -122,6 +143,7 @@ __device__ __forceinline__ void load_geom(int lane, const double *y, const doubl
         T.yl[i] = __double2float_rn(T.y[i] - (double)T.yh[i]);
     }
     T.b = b;
+    T.b2 = 2.0 * b;
     double al[3];
     if (ndelta == 2) {
         double g;
@@ -142,9 +164,12 @@ __device__ __forceinline__ void load_geom(int lane, const double *y, const doubl
         T.ad1[k] = al[k] * id;
         T.ad3[k] = al[k] * id * id * id;
         T.ad5[k] = al[k] * id * id * id * id * id;
+        T.id2h[k] = (float)T.invd2[k];
+        T.id2l[k] = (float)(T.invd2[k] - (double)T.id2h[k]);
     }
     T.apre[0] = al[0];
     T.apre[1] = al[0] + al[1];
+    T.apre[2] = al[0] + al[1] + al[2];
     for (int k = 0; k < 3; ++k) T.alf[k] = (float)al[k];
 }
 
@@ -163,59 +188,100 @@ __device__ __forceinline__ bool is_near(const SurfDev &s, const Geom &T, int64_t
     return !(r2f > rc2f);
 }
 
-// alpha-weighted kernel factors of a near pair of class CLS (delta_0..delta_{CLS-1} are not
-// regularized at this distance); sigma_p from the interpolation table.
-// ND = number of deltas in use (3 for the method; 2 or 1 for the learned closure).
+// alpha-weighted kernel factors of a near pair of class CLS: delta_0..delta_{CLS-1} have
+// r > min(DEFECT_T, cutoff_t) delta_k and take the defect path below; the others take sigma_p
+// from the interpolation table.  ND = number of deltas in use (3 for the method; 2 or 1 for the
+// learned closure).
 template <int CLS, int ND = 3>
-__device__ __forceinline__ void kernel_factors(const Geom &T, const double *__restrict__ tab, double r2, double &K1,
-                                               double &K3, double &K5) {
-    K1 = 0.0;
-    K3 = 0.0;
-    K5 = 0.0;
+__device__ __forceinline__ void kernel_factors(const Geom &T, const ScanParams &P, const double *__restrict__ tab,
+                                               double r2, double &K1, double &K3, double &K5) {
+    constexpr int NDEF = CLS < ND ? CLS : ND;  // defect-path deltas that carry weight
+    double ri = 0.0, ri3 = 0.0, ri5 = 0.0;
+    if (CLS >= 1) {
+        // r / delta_k > DEFECT_T: s_p = 1 - eps_p with eps_1 = erfc t, eps_2 = eps_1 + (2/sqrt pi) t e^{-t^2},
+        // eps_3 = eps_1 + (2/sqrt pi)(t + 2/3 t^3) e^{-t^2} (Eqs. (s1)-(s3)), all below 2.1e-8, and
+        // eps_p = 0 where t > cutoff_t (Sec. 3.2).  The term is (sum_k alpha_k - sum_k alpha_k eps_p(t_k)) / r^p.
+        // eps_p in FP32 with a relative error of a few 1e-7, i.e. below 1e-14 of s_p:
+        //  - tau = t^2 = r^2 / delta^2 as a float pair (exact product of the leading floats plus the
+        //    cross terms), so that e^{-tau} = e^{-tau_h} (1 - tau_l) loses nothing to the rounding of tau;
+        //  - erfc t = e^{-t^2} / (t sqrt pi) (1 - 1/(2t^2) + 3/(4t^4) - 15/(8t^6)), the asymptotic series
+        //    (Abramowitz & Stegun 7.1.23), truncation below 3e-5 relative for t >= 4.7.
+        const float r2h = approx_float_pos(r2);
+        const float r2l = approx_float(r2 - float_to_double(r2h));
+        float E1 = 0.0f, E3 = 0.0f, E5 = 0.0f;
+#pragma unroll
+        for (int k = 0; k < NDEF; ++k) {
+            const float th = r2h * T.id2h[k];
+            const float tl = fmaf(r2h, T.id2h[k], -th) + fmaf(r2h, T.id2l[k], r2l * T.id2h[k]);
+            bool reg = th <= T.tcf2;  // t <= cutoff_t: s_p < 1
+            if (fabsf(th - T.tcf2) <= CUT_BAND * T.tcf2) reg = r2 <= P.cut2d[k];
+            if (reg) {
+                const float g = expf(-th) * (1.0f - tl);  // e^{-t^2}
+                const float it = rsqrt_ftz(th);             // 1/t (th > 20)
+                const float t = th * it;
+                const float u = it * it;  // 1/t^2
+                const float ser = fmaf(fmaf(fmaf(-1.875f, u, 0.75f), u, -0.5f), u, 1.0f);
+                const float e = 0.56418958354775628f * g * it * ser;  // erfc t
+                const float gt = 1.12837916709551257f * g * t;         // (2/sqrt pi) t e^{-t^2}
+                const float a = T.alf[k];
+                E1 = fmaf(a, e, E1);
+                E3 = fmaf(a, e + gt, E3);
+                E5 = fmaf(a, fmaf(gt, 0.6666666666666667f * th, e + gt), E5);
+            }
+        }
+        // 1/r from the FP32 estimate y0: with e = 1 - r^2 y0^2 (|e| < 1e-6),
+        // 1/r = y0 (1 - e)^{-1/2} = y0 (1 + e/2 + 3 e^2/8) + O(e^3 y0).
+        const double y0 = float_to_double(rsqrt_ftz(r2h));  // r2h > 0: r > 4.7 delta_0
+        const double ee = fma(-(r2 * y0), y0, 1.0);
+        ri = fma(y0 * ee, fma(0.375, ee, 0.5), y0);
+        const double ri2 = ri * ri;
+        ri3 = ri2 * ri;
+        ri5 = ri3 * ri2;
+        // eps_p / r^p in FP32 from the rounded FP64 powers (relative error ~1e-7 of terms below
+        // 2.1e-8 of the result; powers formed in FP32 would add up to 5 roundings)
+        K1 = -float_to_double(E1 * round_float_pos(ri));
+        K3 = -float_to_double(E3 * round_float_pos(ri3));
+        K5 = -float_to_double(E5 * round_float_pos(ri5));
+    } else {
+        K1 = 0.0;
+        K3 = 0.0;
+        K5 = 0.0;
+    }
+    const double *__restrict__ ctab = tab;
+    const float4 *__restrict__ ftab = reinterpret_cast<const float4 *>(tab + TAB_DEV_DOUBLES);
 #pragma unroll
     for (int k = CLS; k < ND; ++k) {
         const double tau = r2 * T.invd2[k];
         int idx = (int)(approx_float_pos(tau) * (float)TAB_INV_W);
         idx = min(idx, TAB_N - 1);
-        const double *cf = tab + idx * (3 * TAB_NC);
-        const double s = fma(tau, 2.0 * TAB_INV_W, -__ldg(tab + TAB_N * 3 * TAB_NC + idx));
-        double s1 = __ldg(cf + 0), s2 = __ldg(cf + TAB_NC), s3 = __ldg(cf + 2 * TAB_NC);
-#pragma unroll
-        for (int e = 1; e < TAB_NC; ++e) {
-            s1 = fma(s1, s, __ldg(cf + e));
-            s2 = fma(s2, s, __ldg(cf + TAB_NC + e));
-            s3 = fma(s3, s, __ldg(cf + 2 * TAB_NC + e));
+        const float4 f1 = __ldg(ftab + 3 * idx), f2 = __ldg(ftab + 3 * idx + 1), f3 = __ldg(ftab + 3 * idx + 2);
+        const double s = fma(tau, 2.0 * TAB_INV_W, -float_to_double(f1.w));  // local variable in [-1, 1]
+        const float sf = approx_float(s);
+        // degrees 6..4 in FP32, 3..0 in FP64 (Horner)
+        double s1 = float_to_double(fmaf(fmaf(f1.x, sf, f1.y), sf, f1.z));
+        double s2 = float_to_double(fmaf(fmaf(f2.x, sf, f2.y), sf, f2.z));
+        double s3 = float_to_double(fmaf(fmaf(f3.x, sf, f3.y), sf, f3.z));
+        const double2 *cd = reinterpret_cast<const double2 *>(ctab + idx * 12);
+        const double2 a01 = __ldg(cd), a23 = __ldg(cd + 1), b01 = __ldg(cd + 2);
+        const double2 b23 = __ldg(cd + 3), c01 = __ldg(cd + 4), c23 = __ldg(cd + 5);
+        s1 = fma(fma(fma(fma(s1, s, a01.x), s, a01.y), s, a23.x), s, a23.y);
+        s2 = fma(fma(fma(fma(s2, s, b01.x), s, b01.y), s, b23.x), s, b23.y);
+        s3 = fma(fma(fma(fma(s3, s, c01.x), s, c01.y), s, c23.x), s, c23.y);
+        if (T.cut_small && approx_float_pos(tau) >= (1.0f - CUT_BAND) * T.tcf2 && r2 > P.cut2d[k]) {
+            // t just beyond a cutoff below DEFECT_T: s_p := 1, sigma_p = 1/t^p (Sec. 3.2)
+            s1 = rsqrt(tau);
+            s2 = s1 * s1 * s1;
+            s3 = s2 * s1 * s1;
         }
         K1 = fma(T.ad1[k], s1, K1);
         K3 = fma(T.ad3[k], s2, K3);
         K5 = fma(T.ad5[k], s3, K5);
     }
     if (CLS >= 1) {
-        // delta_0..delta_{CLS-1}: r / delta_k > DEFECT_T, where s_p = 1 - eps_p with
-        // eps_1 = erfc t, eps_2 = eps_1 + (2/sqrt pi) t e^{-t^2},
-        // eps_3 = eps_1 + (2/sqrt pi)(t + 2/3 t^3) e^{-t^2} (Eqs. (s1)-(s3)) below 2.1e-8;
-        // eps_p is evaluated in FP32 (its error ~1e-14 relative to the term), and eps_p = 0 where
-        // t > cutoff_t (Sec. 3.2).  The term is (sum_k alpha_k - sum_k alpha_k eps_p(t_k)) / r^p.
-        float E1 = 0.0f, E3 = 0.0f, E5 = 0.0f;
-        const float r2f = approx_float_pos(r2);
-#pragma unroll
-        for (int k = 0; k < CLS; ++k) {
-            const float t = sqrtf(r2f * approx_float_pos(T.invd2[k]));
-            if (t <= T.tcf) {
-                const float e = erfcf(t), g = 1.12837916709551257f * t * expf(-t * t);
-                const float a = (float)T.alf[k];
-                E1 = fmaf(a, e, E1);
-                E3 = fmaf(a, e + g, E3);
-                E5 = fmaf(a, e + g * (1.0f + 0.6666666666666667f * t * t), E5);
-            }
-        }
         const double Ain = T.apre[CLS - 1];
-        const double ri = rsqrt(r2);
-        const double ri2 = ri * ri;
-        const double ri3 = ri2 * ri;
-        K1 = fma(Ain - float_to_double(E1), ri, K1);
-        K3 = fma(Ain - float_to_double(E3), ri3, K3);
-        K5 = fma(Ain - float_to_double(E5), ri3 * ri2, K5);
+        K1 = fma(Ain, ri, K1);
+        K3 = fma(Ain, ri3, K3);
+        K5 = fma(Ain, ri5, K5);
     }
 }
 
@@ -231,32 +297,48 @@ __device__ __forceinline__ void sl_accumulate(double dx, double dy, double dz, d
     accU[2] = fma(t, dz, fma(K1, g2, accU[2]));
 }
 
-// Double-layer contraction in the basis (n0, xh): accN += cn, accX += cx xh.
-// nm = n0.m and xm = xh.m are density independent (shared by several densities).
-__device__ __forceinline__ void dl_accumulate(const Geom &T, double r2, double K3, double K5, const double h3[3],
-                                              double nm, double xm, const double qs[3], const double q0[3],
-                                              double &accN, double accX[3]) {
+// Density-independent factors of the double-layer contraction of one near pair.
+// With d = y - x = b n0 - xh, L = r^2 K5 - K3, U = d.Q, W = d.m, nQ = n0.Q, nm = n0.m, the
+// contraction -6 [t1 K + t2 K5] : Q m (K = K3 - (r^2 - b^2) K5; t1, t2 as above) equals
+//   -6 ( n0 [nQ (2 b nm - W) - nm U] L  -  d [L nm nQ - K5 W U] ):
+// substitute xh = b n0 - d into n0 (K (b P - S) + K5 b R) + xh (K5 (b S - R) - K P) and collect
+// (K - b^2 K5 = -L).
+struct DLPair {
+    double L, Z, Lnm, K5W;  // L, 2 b nm - W, L nm, K5 W
+};
+
+__device__ __forceinline__ DLPair dl_pair(const Geom &T, double r2, double K3, double K5, double nm, double W) {
+    DLPair D;
+    D.L = fma(r2, K5, -K3);
+    D.Z = fma(T.b2, nm, -W);
+    D.Lnm = D.L * nm;
+    D.K5W = K5 * W;
+    return D;
+}
+
+// Double-layer contraction of one density: accN += the n0 coefficient, accD += the d coefficient
+// (the result is -6/(8 pi) (accN n0 - accD)).
+__device__ __forceinline__ void dl_accumulate(const DLPair &D, const Geom &T, double dx, double dy, double dz,
+                                              double nm, const double qs[3], const double q0[3], double &accN,
+                                              double accD[3]) {
     const double Q0 = qs[0] - q0[0], Q1 = qs[1] - q0[1], Q2 = qs[2] - q0[2];
     const double nQ = fma(T.n0[2], Q2, fma(T.n0[1], Q1, T.n0[0] * Q0));
-    const double xQ = fma(h3[2], Q2, fma(h3[1], Q1, h3[0] * Q0));
-    const double P = nQ * nm, R = xQ * xm, S = fma(xQ, nm, nQ * xm);
-    const double K = fma(-(r2 - T.b * T.b), K5, K3);
-    const double cn = fma(K, fma(T.b, P, -S), K5 * T.b * R);
-    const double cx = fma(K5, fma(T.b, S, -R), -K * P);
-    accN += cn;
-    accX[0] = fma(cx, h3[0], accX[0]);
-    accX[1] = fma(cx, h3[1], accX[1]);
-    accX[2] = fma(cx, h3[2], accX[2]);
+    const double U = fma(dz, Q2, fma(dy, Q1, dx * Q0));
+    accN = fma(D.L, fma(nQ, D.Z, -(nm * U)), accN);
+    const double C = fma(D.Lnm, nQ, -(D.K5W * U));
+    accD[0] = fma(C, dx, accD[0]);
+    accD[1] = fma(C, dy, accD[1]);
+    accD[2] = fma(C, dz, accD[2]);
 }
 
 // Walk the rows of the surface's cell grid that meet the prefilter ball around the target,
-// test candidates in FP32, queue survivors by class in the warp's shared queues sq[3][64],
+// test candidates in FP32, queue survivors by class in the warp's shared queues sq[NCLS][64],
 // and call batch(cls, j, valid) with one node per lane whenever a class has 32 entries, then
 // once more per class for the remainder (lanes with valid = false hold no node).
 template <class Batch>
 __device__ __forceinline__ void scan_near(const SurfDev &s, const Geom &T, const ScanParams &P, int (*sq)[64],
                                           int lane, Batch &&batch) {
-    int qn[3] = {0, 0, 0};
+    int qn[NCLS] = {0, 0, 0, 0};
     const unsigned lt = (1u << lane) - 1u;
     const Grid &G = s.grid;
     const float yf[3] = {T.yh[0], T.yh[1], T.yh[2]};
@@ -293,17 +375,17 @@ __device__ __forceinline__ void scan_near(const SurfDev &s, const Geom &T, const
                     const float ex = yf[0] - p.x, ey = yf[1] - p.y, ez = yf[2] - p.z;
                     const float r2f = fmaf(ez, ez, fmaf(ey, ey, ex * ex));
                     pass = r2f <= R2;
-                    cls = (r2f > P.th[0]) + (r2f > P.th[1]);
+                    cls = (r2f > P.th[0]) + (r2f > P.th[1]) + (r2f > P.th[2]);
                 }
 #pragma unroll
-                for (int c = 0; c < 3; ++c) {
+                for (int c = 0; c < NCLS; ++c) {
                     const unsigned mk = __ballot_sync(FULL, pass && cls == c);
                     if (pass && cls == c) sq[c][qn[c] + __popc(mk & lt)] = j;
                     qn[c] += __popc(mk);
                 }
                 __syncwarp();
 #pragma unroll
-                for (int c = 0; c < 3; ++c) {
+                for (int c = 0; c < NCLS; ++c) {
                     if (qn[c] >= 32) {
                         batch(c, sq[c][qn[c] - 32 + lane], true);
                         qn[c] -= 32;
@@ -314,7 +396,7 @@ __device__ __forceinline__ void scan_near(const SurfDev &s, const Geom &T, const
         }
     }
 #pragma unroll
-    for (int c = 0; c < 3; ++c) {
+    for (int c = 0; c < NCLS; ++c) {
         if (qn[c] > 0) {
             const bool v = lane < qn[c];
             batch(c, v ? sq[c][lane] : 0, v);
@@ -335,11 +417,25 @@ inline ScanParams scan_params(const ers_surface *s, double Rc, const double rho[
     double L = 0.0;
     for (int i = 0; i < 3; ++i) L = fmax(L, fabs(s->c[i]) + s->a[i]);
     P.rpre = (float)(Rc * (1.0 + 1e-5) + 4e-6 * (L + Rc));
-    for (int k = 0; k < 2; ++k) {
+    for (int k = 0; k < 3; ++k) {
+        // The prefilter's r^2 comes from float coordinates (|coordinate| <= L + Rc, each rounded
+        // to 2^-24 relative): widen the threshold by 4x that error bound so that every pair sent
+        // to the defect path has r > min(DEFECT_T, cutoff_t) delta_k in exact arithmetic (the
+        // asymptotic series needs t >= 4.5; below a cutoff < DEFECT_T nothing is evaluated there).
         const double t = fmin(DEFECT_T, cutoff_t) * rho[k] * s->h;
-        P.th[k] = (float)(t * t);
+        const double margin = fmin(0.04, 1e-6 + 4.0 * 2.0 * 6.0 * (L + Rc) * 0x1p-24 / t);
+        P.th[k] = (float)(t * t * (1.0 + margin));
     }
-    P.tcf = (float)cutoff_t;
+    for (int k = 0; k < 2; ++k) {
+        const double t = cutoff_t * rho[k] * s->h;
+        P.cut2[k] = (float)(t * t);
+    }
+    P.tcf2 = (float)(cutoff_t * cutoff_t);
+    P.tc2 = cutoff_t * cutoff_t;
+    for (int k = 0; k < 3; ++k) {
+        const double rk = cutoff_t * rho[k] * s->h;
+        P.cut2d[k] = rk * rk;
+    }
     P.h = s->h;
     return P;
 }

@@ -77,28 +77,70 @@ def test_library_quadrature_matches_oracle(L, shape, inv):
     assert np.abs(w - wo).max() <= 1e-15 * wo.max()
 
 
+def _sigma_mp(mp, tau):
+    t = mp.sqrt(mp.mpf(tau))
+    c = 2 / mp.sqrt(mp.pi)
+    if t == 0:
+        return [c, c * 2 / 3, c * 4 / 15]
+    e, g = mp.erf(t), mp.exp(-t * t)
+    return [e / t, (e - c * t * g) / t**3, (e - c * (t + mp.mpf(2) / 3 * t**3) * g) / t**5]
+
+
+NINT, DEG, INV_W = 384, 6, 16  # intervals of width 1/16 on tau in [0, 24)
+
+
+def _taus():
+    rng = np.random.default_rng(1)
+    return np.concatenate([[0.0, 1e-12, 0.0625, 0.125, 22.09, 23.99], rng.uniform(0, 24, 300)])
+
+
 def test_sigma_table_accuracy(L):
-    """The interpolation table reproduces s_p(t)/t^p (Eqs. (s1)-(s3)) to ~1e-15 on tau = t^2 in [0, 64)."""
+    """The interpolation table reproduces s_p(t)/t^p (Eqs. (s1)-(s3)) to ~1e-15 on tau = t^2 in [0, 24)."""
     mp = pytest.importorskip("mpmath")
     mp.mp.dps = 40
-    nint, deg = 512, 6
-    tab = np.empty(nint * 3 * (deg + 1))
+    tab = np.empty(NINT * 3 * (DEG + 1))
     assert L.ers_debug_sigma_table(tab.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), tab.size) == 0
-    tab = tab.reshape(nint, 3, deg + 1)
-    rng = np.random.default_rng(1)
-    taus = np.concatenate([[0.0, 1e-12, 0.125, 0.25, 35.99, 36.0], rng.uniform(0, 64, 300)])
+    tab = tab.reshape(NINT, 3, DEG + 1)
     worst = 0.0
-    for tau in taus:
-        i = min(int(tau * 8), nint - 1)
-        s = 16 * tau - (2 * i + 1)
-        t = mp.sqrt(mp.mpf(tau))
-        c = 2 / mp.sqrt(mp.pi)
-        if t == 0:
-            ref = [c, c * 2 / 3, c * 4 / 15]
-        else:
-            e, g = mp.erf(t), mp.exp(-t * t)
-            ref = [e / t, (e - c * t * g) / t**3, (e - c * (t + mp.mpf(2) / 3 * t**3) * g) / t**5]
+    for tau in _taus():
+        i = min(int(tau * INV_W), NINT - 1)
+        s = 2 * INV_W * tau - (2 * i + 1)
+        ref = _sigma_mp(mp, tau)
         for p_ in range(3):
             got = np.polyval(tab[i, p_], s)
             worst = max(worst, abs(got - float(ref[p_])) / abs(float(ref[p_])))
+    assert worst < 3e-15, worst
+
+
+def test_sigma_device_layout_accuracy(L):
+    """The device copy, evaluated as the near-field kernel does (degrees 6..4 in FP32, 3..0 in
+    FP64), stays within ~1e-15 of s_p(t)/t^p: the FP32 part carries less than 2e-8 of the value."""
+    mp = pytest.importorskip("mpmath")
+    mp.mp.dps = 40
+    nbytes = NINT * 3 * 4 * 8 + NINT * 3 * 16
+    raw = np.empty(nbytes // 8)
+    L.ers_debug_sigma_device.argtypes = [ctypes.c_void_p, ctypes.c_int64]
+    assert L.ers_debug_sigma_device(raw.ctypes.data, nbytes) == 0
+    assert L.ers_debug_sigma_device(raw.ctypes.data, nbytes - 8) != 0
+    dpart = raw[: NINT * 12].reshape(NINT, 3, 4)
+    fpart = raw[NINT * 12:].view(np.float32).reshape(NINT, 3, 4)
+    assert np.array_equal(fpart[:, 0, 3], 2 * np.arange(NINT) + 1)
+    f32 = np.float32
+
+    def fmaf(a, b, c):  # products of floats are exact in double
+        return f32(np.float64(a) * np.float64(b) + np.float64(c))
+
+    worst = 0.0
+    for tau in _taus():
+        i = min(int(np.float32(tau) * INV_W), NINT - 1)
+        s = 2 * INV_W * tau - float(fpart[i, 0, 3])
+        sf = f32(s)
+        ref = _sigma_mp(mp, tau)
+        for p_ in range(3):
+            c6, c5, c4 = fpart[i, p_, :3]
+            v = float(fmaf(fmaf(c6, sf, c5), sf, c4))
+            for c in dpart[i, p_]:
+                v = v * s + c
+            worst = max(worst, abs(v - float(ref[p_])) / abs(float(ref[p_])))
+            assert abs(c4) <= 2e-8 * abs(dpart[i, p_, 3]), (i, p_)
     assert worst < 6e-15, worst

@@ -43,6 +43,9 @@ FAR_FLOPS_PER_PAIR = 57                   # both layers, one (target, node) far 
 NEAR_FLOPS_BASE = 85                      # both layers, one near pair: geometry + contractions
 NEAR_FLOPS_PER_ACTIVE_DELTA = 45          # sigma_1..3 from the table and the alpha-weighted sums
 NEAR_FLOPS_UNREGULARIZED = 13             # 1/r^p terms when some delta_k has r > cutoff_t delta_k
+# DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) from one ncu capture of
+# the sphere128 workload with the current kernels (profiles/launches_sphere128_mixed.md).
+NCU_TRAFFIC = {("sphere128", "k_far32"): 55943936 + 14936576, ("sphere128", "k_near"): 170454272 + 18524672}
 
 
 def parse():
@@ -231,10 +234,13 @@ def batched_leg(ers, torch, steps: int, warmup: int):
                         "(semi-axes U[0.6,1], h in {1/32,1/48,1/64,1/96}, own nodes + 5% band), 8 densities"}
 
 
-def learned_leg(ers, torch, s, wl, y, steps: int, warmup: int, u_ref, v_ref):
-    """The learned near-field closure on the bench workload: networks trained on the GPU (own
-    kernels) from five other seeded densities on the same surface, then timed on the bench's own
-    density with validation against the three-delta method (tolerance 1e-5, every 32nd target)."""
+def learned_leg(ers, torch, s, wl, y, steps: int, warmup: int):
+    """The learned near-field closure: networks trained on the GPU (own kernels) from five seeded
+    densities on the bench surface (unit sphere, h = 1/128), then evaluated on the two unit
+    spheres 0.01 apart at h = 1/96: the integral over the first sphere at the nodes of both, with
+    validation against the three-delta method (tolerance 1e-5, every 32nd target) and fallback to
+    it.  Also timed with the closure accepted unconditionally (no fallback), against the plain
+    mixed evaluation of the same problem."""
     dev = torch.device("cuda")
     t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
     yd = t(y)
@@ -264,41 +270,67 @@ def learned_leg(ers, torch, s, wl, y, steps: int, warmup: int, u_ref, v_ref):
                       for layer, (X, T) in enumerate(((Xs, Ts), (Xd, Td)))]
     torch.cuda.synchronize()
     t_train = time.perf_counter() - t0
-    nsamples = int(sum(d[0].shape[0] for d in data[2]))
-    # the bench's own density
-    s.set_density(t(workloads.poly_eval(wl.f_coef, x)), t(workloads.poly_eval(wl.q_coef, x)))
-    f0, q0 = t(workloads.poly_eval(wl.f_coef, x0h)), t(workloads.poly_eval(wl.q_coef, x0h))
-    gf0, gq0 = t(workloads.poly_jacobian(wl.f_coef, x0h)), t(workloads.poly_jacobian(wl.q_coef, x0h))
-    M = len(y)
+    nsamples = {nd: int(sum(d[0].shape[0] for d in data[nd])) for nd in (1, 2)}
+    del data
+
+    # evaluation problem: sphere A at the origin, targets = nodes of A and of B at (2.01, 0, 0)
+    pair, _ = workloads.batched_config(gap=0.01, nrhs=1, n_bodies=0)
+    A, B = pair
+    sa = ers.Surface(A.shape.center, A.shape.axes, A.h)
+    sb = ers.Surface(B.shape.center, B.shape.axes, B.h)
+    xa, xb = sa.nodes()[0].cpu().numpy(), sb.nodes()[0].cpu().numpy()
+    del sb
+    fc, qc = A.f_coefs[0], A.q_coefs[0]
+    sa.set_density(t(workloads.poly_eval(fc, xa)), t(workloads.poly_eval(qc, xa)))
+    ye = np.concatenate([xa, xb])
+    yed = t(ye)
+    x0, n0, b = sa.closest_point(yed)
+    x0h = x0.cpu().numpy()
+    f0, q0 = t(workloads.poly_eval(fc, x0h)), t(workloads.poly_eval(qc, x0h))
+    gf0, gq0 = t(workloads.poly_jacobian(fc, x0h)), t(workloads.poly_jacobian(qc, x0h))
+    M = len(ye)
     u = torch.empty((M, 3), dtype=torch.float64, device=dev)
     v = torch.empty((M, 3), dtype=torch.float64, device=dev)
-    res = {"training": {"samples_per_network": nsamples, "densities": 5, "steps": 3000, "batch": 8192,
-                        "data_s": t_data, "train_s": t_train}}
     stream = torch.cuda.current_stream()
-    for nd in (2, 1):
-        args = (yd, x0, n0, b, f0, q0, gf0, gq0)
+
+    def timed(fn):
         for _ in range(warmup):
-            ers.eval_learned(s, nets[nd], *args, rho=wl.rho, precision=ers.PREC_MIXED, tol=1e-5, vstride=32,
-                             ndelta=nd, u=u, v=v)
-        total, fb_any, verr = 0.0, False, None
+            fn()
+        total, out = 0.0, None
         for _ in range(steps):
             a, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             a.record(stream)
-            _, _, verr, fb = ers.eval_learned(s, nets[nd], *args, rho=wl.rho, precision=ers.PREC_MIXED, tol=1e-5,
-                                              vstride=32, ndelta=nd, u=u, v=v)
+            out = fn()
             e.record(stream)
             e.synchronize()
             total += a.elapsed_time(e) / 1e3
-            fb_any = fb_any or fb
-        # error of the learned values themselves (no fallback) against the three-delta values
-        ul, vl, _, _ = ers.eval_learned(s, nets[nd], *args, rho=wl.rho, precision=ers.PREC_MIXED, tol=1e30,
-                                        vstride=1 << 20, ndelta=nd)
-        ul, vl = ul.cpu().numpy(), vl.cpu().numpy()
+        return total / steps, out
+
+    t_plain, _ = timed(lambda: sa.eval(yed, f0, q0, rho=wl.rho, precision=ers.PREC_MIXED, x0=x0, n0=n0, b=b,
+                                       u=u, v=v))
+    u_ref, v_ref = u.cpu().numpy(), v.cpu().numpy()
+    res = {"workload": "train: unit sphere h=1/128, 5 seeded densities; evaluate: two unit spheres gap 0.01, "
+                       "h=1/96, integral over the first at the nodes of both",
+           "targets": M, "nodes": int(xa.shape[0]),
+           "plain_mixed": {"value": M / t_plain, "unit": UNIT, "ms_per_step": t_plain * 1e3},
+           "training": {"samples_per_network": nsamples, "densities": 5, "steps": 3000, "batch": 8192,
+                        "data_s": t_data, "train_s": t_train}}
+    args = (yed, x0, n0, b, f0, q0, gf0, gq0)
+    for nd in (2, 1):
+        t_val, out = timed(lambda: ers.eval_learned(sa, nets[nd], *args, rho=wl.rho, precision=ers.PREC_MIXED,
+                                                    tol=1e-5, vstride=32, ndelta=nd, u=u, v=v))
+        _, _, verr, fb = out
+        t_acc, _ = timed(lambda: ers.eval_learned(sa, nets[nd], *args, rho=wl.rho, precision=ers.PREC_MIXED,
+                                                  tol=1e30, vstride=1 << 20, ndelta=nd, u=u, v=v))
+        ul, vl = u.cpu().numpy(), v.cpu().numpy()
         res[f"ndelta{nd}"] = {
-            "value": steps * M / total, "unit": UNIT, "ms_per_step": total / steps * 1e3,
-            "fell_back_at_tol_1e-5": fb_any, "validation_rel_err": list(verr),
-            "max_rel_err_vs_three_delta": {"SL": float(np.abs(ul - u_ref).max() / np.abs(u_ref).max()),
-                                           "DL": float(np.abs(vl - v_ref).max() / np.abs(v_ref).max())},
+            "value": M / t_val, "unit": UNIT, "ms_per_step": t_val * 1e3,
+            "fell_back_at_tol_1e-5": bool(fb), "validation_rel_err": [float(z) for z in verr],
+            "accepted": {"value": M / t_acc, "ms_per_step": t_acc * 1e3,
+                         "speedup_vs_plain_mixed": t_plain / t_acc,
+                         "max_rel_err_vs_three_delta": {
+                             "SL": float(np.abs(ul - u_ref).max() / np.abs(u_ref).max()),
+                             "DL": float(np.abs(vl - v_ref).max() / np.abs(v_ref).max())}},
             "final_train_loss": losses[nd]}
     return res
 
@@ -463,7 +495,7 @@ def main():
                 "achieved": far_flops / (ms_far * 1e-3) / 1e12, "peak": FP32_PEAK_NOMINAL * scale / 1e12,
                 "peak_source": "152 SMs x 128 FP32 lanes x 2 flop x median SM clock"}
     roof["frac"] = roof["achieved"] / roof["peak"]
-    roof["traffic"] = None
+    roof["traffic"] = NCU_TRAFFIC.get((args.workload, roof["kernel"].split()[0]))
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
@@ -499,7 +531,7 @@ def main():
     if not args.no_batched:
         line["batched"] = batched_leg(ers, torch, steps=2, warmup=1)
     if not args.no_learned and args.workload == WORKLOAD:
-        line["learned"] = learned_leg(ers, torch, s, wl, y, steps=args.steps, warmup=1, u_ref=u_mixed, v_ref=v_mixed)
+        line["learned"] = learned_leg(ers, torch, s, wl, y, steps=args.steps, warmup=1)
     if world == 1 and not args.no_cpu_baseline:
         cb, errs = cpu_baseline(wl, y, args.cpu_seconds, {"mixed": (u_mixed, v_mixed), "fp64": (u64, v64)})
         line["cpu_baseline"] = cb

@@ -46,9 +46,9 @@ int ers_set_density_multi(ers_surface *s, const double *f, const double *q, int 
     if (!f && !q) return fail(ERS_E_INVAL, "ers_set_density_multi: give f, q or both");
     const size_t n = (size_t)s->N * nrhs * 6;
     int rc = grow(s->dens64, n * sizeof(double));
-    if (rc == ERS_OK) rc = grow(s->dens32, n * sizeof(float));
+    if (rc == ERS_OK) rc = grow(s->dens32, (size_t)s->N * batch_rec32_floats(nrhs) * sizeof(float));
     if (rc != ERS_OK) return rc;
-    cudaError_t e = launch_density_multi(s->perm, s->w, f, q, s->N, nrhs, (double *)s->dens64.ptr,
+    cudaError_t e = launch_density_multi(s->perm, s->w, s->rec32, f, q, s->N, nrhs, (double *)s->dens64.ptr,
                                          (float *)s->dens32.ptr, (cudaStream_t)stream);
     if (e != cudaSuccess) return cuda_fail(e, "ers_set_density_multi: density kernel");
     s->nrhs_multi = nrhs;

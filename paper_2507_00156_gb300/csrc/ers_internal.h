@@ -77,8 +77,8 @@ struct ers_surface {
     bool has_f = false, has_q = false;
     // work buffers (grow-only)
     ers::Scratch part, cp, host_io, counts;
-    // densities of several right-hand sides (ers_set_density_multi), cell-sorted:
-    // [N][nrhs][6] (w f, q) in FP64 and FP32
+    // densities of several right-hand sides (ers_set_density_multi), cell-sorted: FP64
+    // [N][nrhs][6] (w f, q) and the FP32 far-field record [N][batch_rec32_floats(nrhs)]
     ers::Scratch dens64, dens32;
     int nrhs_multi = 0;
     int64_t last_counts[3] = {0, 0, 0};
@@ -175,8 +175,10 @@ cudaError_t launch_density(ers_surface *s, const double *f, const double *q, cud
 
 struct BatchProblemDev;
 struct BatchItem;
-cudaError_t launch_density_multi(const int *perm, const double *w, const double *f, const double *q, int64_t N,
-                                 int nr, double *d64, float *d32, cudaStream_t st);
+cudaError_t launch_density_multi(const int *perm, const double *w, const float *rec32, const double *f,
+                                 const double *q, int64_t N, int nr, double *d64, float *d32, cudaStream_t st);
+// floats per node of the batched FP32 far-field record for nr densities (multiple of 4)
+inline int batch_rec32_floats(int nr) { return (6 + 6 * nr + 3) / 4 * 4; }
 int batch_grid(int nr, int nsm);
 cudaError_t launch_batch(int nr, const BatchProblemDev *probs, const BatchItem *items, int nitems, unsigned *counter,
                          const double rho[3], int layers, const double *tab, int grid, cudaStream_t st);

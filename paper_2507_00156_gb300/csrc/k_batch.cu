@@ -5,7 +5,7 @@
 //   1. far field with FP32 operands (the pair term of Eqs. (Stokeslet), (Stresslet) on the
 //      subtracted densities of Eqs. (Stokes_SL1), (Stokes_DL1)), r > Rc only; the geometry of a
 //      pair (d, 1/r) is computed once and shared by the NR densities; FP32 sums over 512
-//      sources are added into FP64 accumulators in shared memory;
+//      sources are added into FP64 sums kept in the output arrays u, v themselves;
 //   2. near field and extrapolation (Secs. 2, 3.2, 3.3) in FP64, one warp per target, with the
 //      alpha-weighted kernel factors of a pair shared by the NR densities;
 //   3. u = far + near (+ chi q(x0) for the double layer), written for every density.
@@ -18,7 +18,6 @@
 
 namespace ers {
 
-
 namespace {
 
 using namespace nearc;
@@ -27,13 +26,18 @@ constexpr int BW = BT / 32; // warps per CTA
 constexpr int BTS = 64;     // sources per shared-memory stage
 constexpr int BFLUSH = 8;   // stages per FP32 partial sum (512 sources)
 
+// FP32 source record of the batched far field, float4 units (see k_density_multi):
+// x - c_tile (3), w n (3), then (w f, q) per density, padded to a multiple of 4 floats.
+template <int NR>
+constexpr int S4 = (6 + 6 * NR + 3) / 4;
+
 template <int NR>
 struct BatchSmem {
-    double far[BT][NR][6];  // FP64 far-field accumulators of the CTA's targets
     union {
-        float stage[BTS][6 + 6 * NR];      // far phase: x - c_tile, w n, then (w f, q) per density
-        double near[BW][NR][7][32];        // near phase: per-lane accumulators
+        float4 stage[BTS][S4<NR>];   // far phase: one stage of source records
+        double near[BW][NR][7][32];  // near phase: per-lane accumulators (SL without c_r wn; N; D)
     } u;
+    double tq[BW][NR][4];  // near phase: c_r = f0_r . n0 and q0_r of each warp's target
     int sq[BW][NCLS][64];
     float4 cen;
     int item;
@@ -70,33 +74,35 @@ __device__ void far_phase(const BatchProblemDev &P, int tb, int layers, BatchSme
             }
         }
     }
-    for (int r = 0; r < NR; ++r)
-        for (int i = 0; i < 6; ++i) S.far[t][r][i] = 0.0;
     float acc[NR][6];
     for (int r = 0; r < NR; ++r)
         for (int i = 0; i < 6; ++i) acc[r][i] = 0.0f;
 
     const int64_t N = P.sd.N;
+    const float4 *__restrict__ src4 = reinterpret_cast<const float4 *>(P.dens32);
     int since = 0;
+    bool first = true;
     for (int64_t base = 0; base < N; base += BTS) {
         const int ns = (int)min((int64_t)BTS, N - base);
         __syncthreads();
-        for (int k = t; k < ns * (6 + 6 * NR); k += BT) {
-            const int j = k / (6 + 6 * NR), e = k % (6 + 6 * NR);
-            const int64_t jj = base + j;
-            float val;
-            if (e < 3) val = P.sd.rec32[jj * REC + R_X + e];
-            else if (e < 6) val = P.sd.rec32[jj * REC + R_WN + (e - 3)];
-            else val = P.dens32[jj * (6 * NR) + (e - 6)];
-            S.u.stage[j][e] = val;
-        }
+        const float4 *g = src4 + base * S4<NR>;
+        float4 *st = &S.u.stage[0][0];
+        for (int k = t; k < ns * S4<NR>; k += BT) st[k] = g[k];
         if (t == 0) S.cen = reinterpret_cast<const float4 *>(P.sd.tilec)[base / TS32];
         __syncthreads();
         const float4 cen = S.cen;
         const float yc0 = tile_rel(yh[0], cen.x, yl[0]), yc1 = tile_rel(yh[1], cen.y, yl[1]),
                     yc2 = tile_rel(yh[2], cen.z, yl[2]);
         for (int j = 0; j < ns; ++j) {
-            const float *sp = S.u.stage[j];
+            float sp[4 * S4<NR>];
+#pragma unroll
+            for (int k = 0; k < S4<NR>; ++k) {
+                const float4 v4 = S.u.stage[j][k];
+                sp[4 * k] = v4.x;
+                sp[4 * k + 1] = v4.y;
+                sp[4 * k + 2] = v4.z;
+                sp[4 * k + 3] = v4.w;
+            }
             float dx, dy, dz;
             const float r2 = dist2_fp32(yc0, yc1, yc2, sp[0], sp[1], sp[2], &dx, &dy, &dz);
             float ri = rsqrt_ftz(r2);  // far pairs have r2 >= Rc^2; the others are masked
@@ -126,27 +132,43 @@ __device__ void far_phase(const BatchProblemDev &P, int tb, int layers, BatchSme
             }
         }
         if (++since == BFLUSH || base + BTS >= N) {
+            // FP64 sums (unscaled) in the outputs of this thread's own target
             since = 0;
+            if (valid) {
+#pragma unroll
+                for (int r = 0; r < NR; ++r) {
+                    double *ou = P.u + ((int64_t)r * P.M + m) * 3, *ov = P.v + ((int64_t)r * P.M + m) * 3;
+#pragma unroll
+                    for (int i = 0; i < 3; ++i) {
+                        if (sl) ou[i] = (first ? 0.0 : ou[i]) + (double)acc[r][i];
+                        if (dl) ov[i] = (first ? 0.0 : ov[i]) + (double)acc[r][3 + i];
+                    }
+                }
+            }
+            first = false;
 #pragma unroll
             for (int r = 0; r < NR; ++r)
 #pragma unroll
-                for (int i = 0; i < 6; ++i) {
-                    S.far[t][r][i] += (double)acc[r][i];
-                    acc[r][i] = 0.0f;
-                }
+                for (int i = 0; i < 6; ++i) acc[r][i] = 0.0f;
         }
     }
-    for (int r = 0; r < NR; ++r) {
-        for (int i = 0; i < 3; ++i) S.far[t][r][i] *= INV8PI;
-        for (int i = 3; i < 6; ++i) S.far[t][r][i] *= -6.0 * INV8PI;
+    if (valid && N == 0) {
+        for (int r = 0; r < NR; ++r)
+            for (int i = 0; i < 3; ++i) {
+                if (sl) P.u[((int64_t)r * P.M + m) * 3 + i] = 0.0;
+                if (dl) P.v[((int64_t)r * P.M + m) * 3 + i] = 0.0;
+            }
     }
-    __syncthreads();
+    __syncthreads();  // the far sums in u, v are visible to the whole CTA
 }
 
+// One near pair for the NR densities: the kernel factors, the single-layer terms without the
+// c_r w n part (K1 w f + K3 (d.w f) d per density, and K1 w n + K3 (d.w n) d once, into accB,
+// subtracted c_r times at the end) and the double-layer terms.
 template <int CLS, int NR>
 __device__ __forceinline__ void near_pair(const BatchProblemDev &P, const Geom &T, const double *__restrict__ tab,
-                                          int64_t j, const double (&c)[NR], int64_t m, int lane, int warp,
-                                          int layers, BatchSmem<NR> &S) {
+                                          int64_t j, int lane, int warp, int layers, BatchSmem<NR> &S,
+                                          double accB[3]) {
     const double *rec = P.sd.rec + j * REC;
     const double xs[3] = {__ldg(rec + R_X), __ldg(rec + R_X + 1), __ldg(rec + R_X + 2)};
     const double wn[3] = {__ldg(rec + R_WN), __ldg(rec + R_WN + 1), __ldg(rec + R_WN + 2)};
@@ -160,22 +182,27 @@ __device__ __forceinline__ void near_pair(const BatchProblemDev &P, const Geom &
     const double nm = fma(T.n0[2], wn[2], fma(T.n0[1], wn[1], T.n0[0] * wn[0]));
     const double W = fma(dz, wn[2], fma(dy, wn[1], dx * wn[0]));
     const DLPair D = dl_pair(T, r2, K3, K5, nm, W);  // shared by the NR densities
-    const double *dj = P.dens64 + j * (6 * NR);
-#pragma unroll
+    const bool sl = layers & ERS_LAYER_SL, dl = layers & ERS_LAYER_DL;
+    if (sl) {
+        const double tb = K3 * W;
+        accB[0] = fma(K1, wn[0], fma(tb, dx, accB[0]));
+        accB[1] = fma(K1, wn[1], fma(tb, dy, accB[1]));
+        accB[2] = fma(K1, wn[2], fma(tb, dz, accB[2]));
+    }
+    const double2 *dj = reinterpret_cast<const double2 *>(P.dens64 + j * (6 * NR));
+#pragma unroll 2
     for (int r = 0; r < NR; ++r) {
         double(*a)[32] = S.u.near[warp][r];
-        if (layers & ERS_LAYER_SL) {
-            const double wf[3] = {__ldg(dj + 6 * r), __ldg(dj + 6 * r + 1), __ldg(dj + 6 * r + 2)};
-            double accU[3] = {a[0][lane], a[1][lane], a[2][lane]};
-            sl_accumulate(dx, dy, dz, K1, K3, c[r], wf, wn, accU);
-            a[0][lane] = accU[0];
-            a[1][lane] = accU[1];
-            a[2][lane] = accU[2];
+        const double2 d0 = __ldg(dj + 3 * r), d1 = __ldg(dj + 3 * r + 1), d2 = __ldg(dj + 3 * r + 2);
+        if (sl) {  // K1 w f + K3 (d.w f) d
+            const double t = K3 * fma(dz, d1.x, fma(dy, d0.y, dx * d0.x));
+            a[0][lane] = fma(K1, d0.x, fma(t, dx, a[0][lane]));
+            a[1][lane] = fma(K1, d0.y, fma(t, dy, a[1][lane]));
+            a[2][lane] = fma(K1, d1.x, fma(t, dz, a[2][lane]));
         }
-        if (layers & ERS_LAYER_DL) {
-            const double qs[3] = {__ldg(dj + 6 * r + 3), __ldg(dj + 6 * r + 4), __ldg(dj + 6 * r + 5)};
-            const double *q0p = P.q0 + ((int64_t)r * P.M + m) * 3;
-            const double q0[3] = {q0p[0], q0p[1], q0p[2]};
+        if (dl) {
+            const double qs[3] = {d1.y, d2.x, d2.y};
+            const double q0[3] = {S.tq[warp][r][1], S.tq[warp][r][2], S.tq[warp][r][3]};
             double accN = a[3][lane], accD[3] = {a[4][lane], a[5][lane], a[6][lane]};
             dl_accumulate(D, T, dx, dy, dz, nm, qs, q0, accN, accD);
             a[3][lane] = accN;
@@ -200,52 +227,61 @@ __device__ void near_phase(const BatchProblemDev &P, int tb, int layers, const d
             Geom T;
             load_geom(lane, P.y, P.x0, P.n0, bm, m, rho, P.sp.h, T);
             set_cutoff(T, P.sp);
-            double c[NR];
-            for (int r = 0; r < NR; ++r) {
-                const double *f0 = P.f0 + ((int64_t)r * P.M + m) * 3;
-                c[r] = sl ? fma(f0[2], T.n0[2], fma(f0[1], T.n0[1], f0[0] * T.n0[0])) : 0.0;
-                for (int i = 0; i < 7; ++i) S.u.near[warp][r][i][lane] = 0.0;
+            if (lane < 4 * NR) {  // lane = 4 r + k: k = 0 c_r, k = 1..3 q0_r
+                const int r = lane >> 2, k = lane & 3;
+                double val = 0.0;
+                if (k == 0 && sl) {
+                    const double *f0 = P.f0 + ((int64_t)r * P.M + m) * 3;
+                    val = fma(f0[2], T.n0[2], fma(f0[1], T.n0[1], f0[0] * T.n0[0]));
+                }
+                if (k > 0 && dl) val = P.q0[((int64_t)r * P.M + m) * 3 + k - 1];
+                S.tq[warp][r][k] = val;
             }
+            for (int r = 0; r < NR; ++r)
+                for (int i = 0; i < 7; ++i) S.u.near[warp][r][i][lane] = 0.0;
             __syncwarp();
+            double accB[3] = {0.0, 0.0, 0.0};
             scan_near(P.sd, T, P.sp, S.sq[warp], lane, [&](int cls, int jj, bool valid) {
                 if (!valid) return;
-                if (cls == 0) near_pair<0, NR>(P, T, tab, jj, c, m, lane, warp, layers, S);
-                else if (cls == 1) near_pair<1, NR>(P, T, tab, jj, c, m, lane, warp, layers, S);
-                else if (cls == 2) near_pair<2, NR>(P, T, tab, jj, c, m, lane, warp, layers, S);
-                else near_pair<3, NR>(P, T, tab, jj, c, m, lane, warp, layers, S);
+                if (cls == 0) near_pair<0, NR>(P, T, tab, jj, lane, warp, layers, S, accB);
+                else if (cls == 1) near_pair<1, NR>(P, T, tab, jj, lane, warp, layers, S, accB);
+                else if (cls == 2) near_pair<2, NR>(P, T, tab, jj, lane, warp, layers, S, accB);
+                else near_pair<3, NR>(P, T, tab, jj, lane, warp, layers, S, accB);
             });
+            for (int i = 0; i < 3; ++i) accB[i] = warp_sum(accB[i]);
             const double chi = bm < 0.0 ? 1.0 : (bm > 0.0 ? 0.0 : 0.5);
             for (int r = 0; r < NR; ++r) {
                 double tot[7];
                 for (int i = 0; i < 7; ++i) tot[i] = warp_sum(S.u.near[warp][r][i][lane]);
                 if (sl && lane < 3) {
                     const double a = lane == 0 ? tot[0] : (lane == 1 ? tot[1] : tot[2]);
-                    P.u[((int64_t)r * P.M + m) * 3 + lane] = S.far[tt][r][lane] + a * INV8PI;
+                    const double bb = lane == 0 ? accB[0] : (lane == 1 ? accB[1] : accB[2]);
+                    double *o = P.u + ((int64_t)r * P.M + m) * 3 + lane;
+                    *o = INV8PI * (*o + fma(-S.tq[warp][r][0], bb, a));
                 }
                 if (dl && lane >= 3 && lane < 6) {
                     const int i = lane - 3;
                     const double ad = i == 0 ? tot[4] : (i == 1 ? tot[5] : tot[6]);
                     const double ni = i == 0 ? T.n0[0] : (i == 1 ? T.n0[1] : T.n0[2]);
-                    const double qi = P.q0[((int64_t)r * P.M + m) * 3 + i];
-                    P.v[((int64_t)r * P.M + m) * 3 + i] =
-                        S.far[tt][r][lane] + (-6.0 * INV8PI) * fma(tot[3], ni, -ad) + chi * qi;
+                    double *o = P.v + ((int64_t)r * P.M + m) * 3 + i;
+                    *o = (-6.0 * INV8PI) * (*o + fma(tot[3], ni, -ad)) + chi * S.tq[warp][r][1 + i];
                 }
             }
             __syncwarp();
         } else {
             for (int r = 0; r < NR; ++r) {
-                if (sl && lane < 3) P.u[((int64_t)r * P.M + m) * 3 + lane] = S.far[tt][r][lane];
-                if (dl && lane >= 3 && lane < 6) P.v[((int64_t)r * P.M + m) * 3 + lane - 3] = S.far[tt][r][lane];
+                if (sl && lane < 3) P.u[((int64_t)r * P.M + m) * 3 + lane] *= INV8PI;
+                if (dl && lane >= 3 && lane < 6) P.v[((int64_t)r * P.M + m) * 3 + lane - 3] *= -6.0 * INV8PI;
             }
         }
     }
 }
 
 template <int NR>
-__global__ void __launch_bounds__(BT) k_batch(const BatchProblemDev *__restrict__ probs,
-                                              const BatchItem *__restrict__ items, int nitems,
-                                              unsigned *__restrict__ counter, double rho0, double rho1, double rho2,
-                                              int layers, const double *__restrict__ tab) {
+__global__ void __launch_bounds__(BT, 3) k_batch(const BatchProblemDev *__restrict__ probs,
+                                                 const BatchItem *__restrict__ items, int nitems,
+                                                 unsigned *__restrict__ counter, double rho0, double rho1,
+                                                 double rho2, int layers, const double *__restrict__ tab) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     BatchSmem<NR> &S = *reinterpret_cast<BatchSmem<NR> *>(smem_raw);
     const double rho[3] = {rho0, rho1, rho2};
@@ -262,13 +298,23 @@ __global__ void __launch_bounds__(BT) k_batch(const BatchProblemDev *__restrict_
     }
 }
 
+// Densities of nr right-hand sides in cell-sorted order: FP64 [N][nr][6] (w f, q) for the near
+// field, and the FP32 far-field record [N][S] floats (S = 6 + 6 nr rounded up to a multiple of 4):
+// x - c_tile and w n from the surface's FP32 record, then (w f, q) per density, zero padding.
 __global__ void k_density_multi(const int *__restrict__ perm, const double *__restrict__ w,
-                                const double *__restrict__ f, const double *__restrict__ q, int64_t N, int nr,
-                                double *__restrict__ d64, float *__restrict__ d32) {
+                                const float *__restrict__ rec32, const double *__restrict__ f,
+                                const double *__restrict__ q, int64_t N, int nr, double *__restrict__ d64,
+                                float *__restrict__ d32) {
     const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (j >= N) return;
     const int64_t i = perm[j];
     const double wi = w[i];
+    const int S = (6 + 6 * nr + 3) / 4 * 4;
+    float *o32 = d32 + j * S;
+    for (int k = 0; k < 3; ++k) {
+        o32[k] = rec32[j * REC + R_X + k];
+        o32[3 + k] = rec32[j * REC + R_WN + k];
+    }
     for (int r = 0; r < nr; ++r) {
         for (int k = 0; k < 3; ++k) {
             const double fv = f ? wi * f[((int64_t)r * N + i) * 3 + k] : 0.0;
@@ -276,10 +322,11 @@ __global__ void k_density_multi(const int *__restrict__ perm, const double *__re
             const int64_t o = (j * nr + r) * 6;
             d64[o + k] = fv;
             d64[o + 3 + k] = qv;
-            d32[o + k] = __double2float_rn(fv);
-            d32[o + 3 + k] = __double2float_rn(qv);
+            o32[6 + 6 * r + k] = __double2float_rn(fv);
+            o32[6 + 6 * r + 3 + k] = __double2float_rn(qv);
         }
     }
+    for (int k = 6 + 6 * nr; k < S; ++k) o32[k] = 0.0f;
 }
 
 template <int NR>
@@ -302,10 +349,10 @@ int batch_grid_t(int nsm) {
 
 }  // namespace
 
-cudaError_t launch_density_multi(const int *perm, const double *w, const double *f, const double *q, int64_t N,
-                                 int nr, double *d64, float *d32, cudaStream_t st) {
+cudaError_t launch_density_multi(const int *perm, const double *w, const float *rec32, const double *f,
+                                 const double *q, int64_t N, int nr, double *d64, float *d32, cudaStream_t st) {
     const int bs = 256;
-    k_density_multi<<<(unsigned)((N + bs - 1) / bs), bs, 0, st>>>(perm, w, f, q, N, nr, d64, d32);
+    k_density_multi<<<(unsigned)((N + bs - 1) / bs), bs, 0, st>>>(perm, w, rec32, f, q, N, nr, d64, d32);
     return cudaGetLastError();
 }
 

@@ -38,14 +38,14 @@ WORKLOAD = "sphere128"
 SM_MAX_MHZ = 2070.0
 FP32_PEAK_NOMINAL = 152 * 128 * 2 * SM_MAX_MHZ * 1e6
 FP64_PEAK_NOMINAL = 1.25e12
-# Algorithmic flops (FMA = 2, add/mul/rsqrt = 1) per unit of work, derived in the design doc.
-FAR_FLOPS_PER_PAIR = 57                   # both layers, one (target, node) far pair
-NEAR_FLOPS_BASE = 85                      # both layers, one near pair: geometry + contractions
-NEAR_FLOPS_PER_ACTIVE_DELTA = 45          # sigma_1..3 from the table and the alpha-weighted sums
-NEAR_FLOPS_UNREGULARIZED = 13             # 1/r^p terms when some delta_k has r > cutoff_t delta_k
+# Algorithmic work per unit (convention: FMA = 2 flops, rsqrt = 1 op, erf/exp counted as calls):
+# a far (target, node) pair costs 34 flops + 1 rsqrt for the single layer and 33 + 1 rsqrt for the
+# double layer; a near (node, delta) evaluation with t <= cutoff_t costs 30 flops + 1 erf + 1 exp.
+FAR_FLOPS_PER_PAIR = 34 + 1 + 33 + 1      # both layers, one far pair
+NEAR_FLOPS_PER_DELTA_EVAL = 30 + 1 + 1    # one regularized (node, delta) term, both layers
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) from one ncu capture of
 # the sphere128 workload with the current kernels (profiles/launches_sphere128_mixed.md).
-NCU_TRAFFIC = {("sphere128", "k_far32"): 55943936 + 14936576, ("sphere128", "k_near"): 170454272 + 18524672}
+NCU_TRAFFIC = {("sphere128", "k_near"): 195911936 + 19416320, ("sphere128", "k_far32"): 59682560 + 30467584}
 
 
 def parse():
@@ -483,8 +483,8 @@ def main():
     sm_mhz = clocks.get("sm_mhz") or SM_MAX_MHZ
     scale = sm_mhz / SM_MAX_MHZ
     ms_closest, ms_far, ms_near = (float(z) for z in k_mixed)
-    near_flops = sum(c * (NEAR_FLOPS_BASE + NEAR_FLOPS_PER_ACTIVE_DELTA * (3 - k)
-                          + (NEAR_FLOPS_UNREGULARIZED if k >= 1 else 0)) for k, c in enumerate(cls_counts))
+    # cls_counts[k] = near pairs with k deltas beyond the cutoff, i.e. 3 - k regularized terms
+    near_flops = NEAR_FLOPS_PER_DELTA_EVAL * sum(c * (3 - k) for k, c in enumerate(cls_counts))
     far_flops = far_pairs * FAR_FLOPS_PER_PAIR
     if ms_near >= ms_far:
         roof = {"kernel": "k_near (FP64 near sums + extrapolation)", "bound": "alu", "unit": "TFLOP/s",

@@ -317,7 +317,7 @@ int eval_impl(ers_surface *s, const ers_params *p, const double *y, int64_t M, c
     // far-field work split: target blocks x source chunks (chunks aligned to the FP32 tiles)
     int nsm = 152;
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-    const int64_t tpc = p->precision == ERS_PREC_MIXED ? 384 : 256;  // targets per far-field CTA
+    const int64_t tpc = p->precision == ERS_PREC_MIXED ? 512 : 256;  // targets per far-field CTA
     const int64_t tb = (M + tpc - 1) / tpc;
     int64_t chunks = (16LL * nsm + tb - 1) / tb;
     chunks = std::max<int64_t>(1, std::min<int64_t>(chunks, std::max<int64_t>(1, s->N / (4 * TS32))));

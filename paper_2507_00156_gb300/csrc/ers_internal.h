@@ -230,6 +230,31 @@ __device__ __forceinline__ float rsqrt_ftz(float x) {
     return y;
 }
 
+// Two FP32 lanes in one 64-bit register: Blackwell's packed f32x2 arithmetic issues one
+// instruction for two IEEE FP32 operations (each lane rounded as its scalar counterpart).
+typedef unsigned long long f2;
+__device__ __forceinline__ f2 pk(float a, float b) {
+    f2 r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
+    return r;
+}
+__device__ __forceinline__ void upk(f2 v, float &a, float &b) { asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(v)); }
+__device__ __forceinline__ f2 fma2(f2 a, f2 b, f2 c) {
+    f2 d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+    return d;
+}
+__device__ __forceinline__ f2 mul2(f2 a, f2 b) {
+    f2 d;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ f2 sub2(f2 a, f2 b) {
+    f2 d;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+
 // Round-to-nearest form of approx_float_pos (integer pipe only): adds half a float ulp in the
 // double's bits before truncating; relative error <= 2^-24 for 2^-126 <= x < 2^127.
 __device__ __forceinline__ float round_float_pos(double x) {

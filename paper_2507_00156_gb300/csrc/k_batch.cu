@@ -43,15 +43,23 @@ struct BatchSmem {
     int item;
 };
 
+// Offset (floats) of value k (w f 0..2, q 0..2) of density r in the FP32 far-field record:
+// after x - c_tile and w n, densities come in pairs with their values interleaved, so that one
+// 64-bit word holds the same value of two densities (packed f32x2 operands); NR = 1 is plain.
+__host__ __device__ constexpr int rec_off(int nr, int r, int k) {
+    return nr == 1 ? 6 + k : 6 + 12 * (r / 2) + 2 * k + (r % 2);
+}
+
 template <int NR>
 __device__ void far_phase(const BatchProblemDev &P, int tb, int layers, BatchSmem<NR> &S) {
+    constexpr int NP = NR / 2 > 0 ? NR / 2 : 1;  // density pairs (NR = 1: one half-used pair)
     const int t = threadIdx.x;
     const int64_t m = (int64_t)tb * BT + t;
     const bool valid = m < P.M;
     const bool sl = layers & ERS_LAYER_SL, dl = layers & ERS_LAYER_DL;
-    float yh[3] = {0, 0, 0}, yl[3] = {0, 0, 0}, c[NR], q0[NR][3];
+    float yh[3] = {0, 0, 0}, yl[3] = {0, 0, 0}, c[2 * NP], q0[2 * NP][3];
     float rc2 = __int_as_float(0x7f800000);  // +inf: nothing is far (invalid target)
-    for (int r = 0; r < NR; ++r) {
+    for (int r = 0; r < 2 * NP; ++r) {
         c[r] = 0.0f;
         q0[r][0] = q0[r][1] = q0[r][2] = 0.0f;
     }
@@ -74,9 +82,13 @@ __device__ void far_phase(const BatchProblemDev &P, int tb, int layers, BatchSme
             }
         }
     }
-    float acc[NR][6];
-    for (int r = 0; r < NR; ++r)
-        for (int i = 0; i < 6; ++i) acc[r][i] = 0.0f;
+    f2 nc[NP], q0p[NP][3], acc[NP][6];
+#pragma unroll
+    for (int p = 0; p < NP; ++p) {
+        nc[p] = pk(-c[2 * p], -c[2 * p + 1]);
+        for (int i = 0; i < 3; ++i) q0p[p][i] = pk(q0[2 * p][i], q0[2 * p + 1][i]);
+        for (int i = 0; i < 6; ++i) acc[p][i] = 0ull;
+    }
 
     const int64_t N = P.sd.N;
     const float4 *__restrict__ src4 = reinterpret_cast<const float4 *>(P.dens32);
@@ -94,40 +106,42 @@ __device__ void far_phase(const BatchProblemDev &P, int tb, int layers, BatchSme
         const float yc0 = tile_rel(yh[0], cen.x, yl[0]), yc1 = tile_rel(yh[1], cen.y, yl[1]),
                     yc2 = tile_rel(yh[2], cen.z, yl[2]);
         for (int j = 0; j < ns; ++j) {
-            float sp[4 * S4<NR>];
-#pragma unroll
-            for (int k = 0; k < S4<NR>; ++k) {
-                const float4 v4 = S.u.stage[j][k];
-                sp[4 * k] = v4.x;
-                sp[4 * k + 1] = v4.y;
-                sp[4 * k + 2] = v4.z;
-                sp[4 * k + 3] = v4.w;
-            }
+            const float *sp = reinterpret_cast<const float *>(&S.u.stage[j][0]);
+            const float4 a0 = S.u.stage[j][0], a1 = S.u.stage[j][1];  // x - c, w n, then densities
             float dx, dy, dz;
-            const float r2 = dist2_fp32(yc0, yc1, yc2, sp[0], sp[1], sp[2], &dx, &dy, &dz);
-            float ri = rsqrt_ftz(r2);  // far pairs have r2 >= Rc^2; the others are masked
-            ri = (r2 > rc2) ? ri : 0.0f;
+            const float r2 = dist2_fp32(yc0, yc1, yc2, a0.x, a0.y, a0.z, &dx, &dy, &dz);
+            const float ri = (r2 > rc2) ? rsqrt_ftz(r2) : 0.0f;  // far pairs have r2 >= Rc^2
             const float ri2 = ri * ri;
-            const float dwn = fmaf(dz, sp[5], fmaf(dy, sp[4], dx * sp[3]));
+            const float dwn = fmaf(dz, a1.y, fmaf(dy, a1.x, dx * a0.w));
             const float w5 = dwn * ((ri2 * ri2) * ri);  // (d.m)/r^5
+            const f2 Dx = pk(dx, dx), Dy = pk(dy, dy), Dz = pk(dz, dz), RI = pk(ri, ri), RI2 = pk(ri2, ri2);
+            const f2 W0 = pk(a0.w, a0.w), W1 = pk(a1.x, a1.x), W2 = pk(a1.y, a1.y), W5 = pk(w5, w5);
 #pragma unroll
-            for (int r = 0; r < NR; ++r) {
-                const float *dr = sp + 6 + 6 * r;
+            for (int p = 0; p < NP; ++p) {
+                f2 v[6];  // w f 0..2, q 0..2 of densities 2p, 2p+1
+                if (NR == 1) {
+#pragma unroll
+                    for (int k = 0; k < 6; ++k) v[k] = pk(sp[6 + k], 0.0f);
+                } else {
+                    const f2 *pp = reinterpret_cast<const f2 *>(sp + 6 + 12 * p);
+#pragma unroll
+                    for (int k = 0; k < 6; ++k) v[k] = pp[k];
+                }
                 if (sl) {
-                    const float g0 = fmaf(-c[r], sp[3], dr[0]);
-                    const float g1 = fmaf(-c[r], sp[4], dr[1]);
-                    const float g2 = fmaf(-c[r], sp[5], dr[2]);
-                    const float s = fmaf(dz, g2, fmaf(dy, g1, dx * g0)) * ri2;
-                    acc[r][0] = fmaf(fmaf(dx, s, g0), ri, acc[r][0]);
-                    acc[r][1] = fmaf(fmaf(dy, s, g1), ri, acc[r][1]);
-                    acc[r][2] = fmaf(fmaf(dz, s, g2), ri, acc[r][2]);
+                    const f2 g0 = fma2(nc[p], W0, v[0]);
+                    const f2 g1 = fma2(nc[p], W1, v[1]);
+                    const f2 g2 = fma2(nc[p], W2, v[2]);
+                    const f2 sv = mul2(fma2(Dz, g2, fma2(Dy, g1, mul2(Dx, g0))), RI2);
+                    acc[p][0] = fma2(fma2(Dx, sv, g0), RI, acc[p][0]);
+                    acc[p][1] = fma2(fma2(Dy, sv, g1), RI, acc[p][1]);
+                    acc[p][2] = fma2(fma2(Dz, sv, g2), RI, acc[p][2]);
                 }
                 if (dl) {
-                    const float Q0 = dr[3] - q0[r][0], Q1 = dr[4] - q0[r][1], Q2 = dr[5] - q0[r][2];
-                    const float s = fmaf(dz, Q2, fmaf(dy, Q1, dx * Q0)) * w5;
-                    acc[r][3] = fmaf(dx, s, acc[r][3]);
-                    acc[r][4] = fmaf(dy, s, acc[r][4]);
-                    acc[r][5] = fmaf(dz, s, acc[r][5]);
+                    const f2 Q0 = sub2(v[3], q0p[p][0]), Q1 = sub2(v[4], q0p[p][1]), Q2 = sub2(v[5], q0p[p][2]);
+                    const f2 sv = mul2(fma2(Dz, Q2, fma2(Dy, Q1, mul2(Dx, Q0))), W5);
+                    acc[p][3] = fma2(Dx, sv, acc[p][3]);
+                    acc[p][4] = fma2(Dy, sv, acc[p][4]);
+                    acc[p][5] = fma2(Dz, sv, acc[p][5]);
                 }
             }
         }
@@ -136,20 +150,27 @@ __device__ void far_phase(const BatchProblemDev &P, int tb, int layers, BatchSme
             since = 0;
             if (valid) {
 #pragma unroll
-                for (int r = 0; r < NR; ++r) {
-                    double *ou = P.u + ((int64_t)r * P.M + m) * 3, *ov = P.v + ((int64_t)r * P.M + m) * 3;
+                for (int p = 0; p < NP; ++p)
 #pragma unroll
-                    for (int i = 0; i < 3; ++i) {
-                        if (sl) ou[i] = (first ? 0.0 : ou[i]) + (double)acc[r][i];
-                        if (dl) ov[i] = (first ? 0.0 : ov[i]) + (double)acc[r][3 + i];
+                    for (int h = 0; h < 2; ++h) {
+                        const int r = 2 * p + h;
+                        if (r >= NR) break;
+                        double *ou = P.u + ((int64_t)r * P.M + m) * 3, *ov = P.v + ((int64_t)r * P.M + m) * 3;
+#pragma unroll
+                        for (int i = 0; i < 3; ++i) {
+                            float s0, s1, d0, d1;
+                            upk(acc[p][i], s0, s1);
+                            upk(acc[p][3 + i], d0, d1);
+                            if (sl) ou[i] = (first ? 0.0 : ou[i]) + (double)(h ? s1 : s0);
+                            if (dl) ov[i] = (first ? 0.0 : ov[i]) + (double)(h ? d1 : d0);
+                        }
                     }
-                }
             }
             first = false;
 #pragma unroll
-            for (int r = 0; r < NR; ++r)
+            for (int p = 0; p < NP; ++p)
 #pragma unroll
-                for (int i = 0; i < 6; ++i) acc[r][i] = 0.0f;
+                for (int i = 0; i < 6; ++i) acc[p][i] = 0ull;
         }
     }
     if (valid && N == 0) {
@@ -300,7 +321,8 @@ __global__ void __launch_bounds__(BT, 3) k_batch(const BatchProblemDev *__restri
 
 // Densities of nr right-hand sides in cell-sorted order: FP64 [N][nr][6] (w f, q) for the near
 // field, and the FP32 far-field record [N][S] floats (S = 6 + 6 nr rounded up to a multiple of 4):
-// x - c_tile and w n from the surface's FP32 record, then (w f, q) per density, zero padding.
+// x - c_tile and w n from the surface's FP32 record, then (w f, q) per density in the order of
+// rec_off (pairs of densities interleaved), zero padding.
 __global__ void k_density_multi(const int *__restrict__ perm, const double *__restrict__ w,
                                 const float *__restrict__ rec32, const double *__restrict__ f,
                                 const double *__restrict__ q, int64_t N, int nr, double *__restrict__ d64,
@@ -322,8 +344,8 @@ __global__ void k_density_multi(const int *__restrict__ perm, const double *__re
             const int64_t o = (j * nr + r) * 6;
             d64[o + k] = fv;
             d64[o + 3 + k] = qv;
-            o32[6 + 6 * r + k] = __double2float_rn(fv);
-            o32[6 + 6 * r + 3 + k] = __double2float_rn(qv);
+            o32[rec_off(nr, r, k)] = __double2float_rn(fv);
+            o32[rec_off(nr, r, 3 + k)] = __double2float_rn(qv);
         }
     }
     for (int k = 6 + 6 * nr; k < S; ++k) o32[k] = 0.0f;

@@ -136,35 +136,46 @@ struct TargetF32 {
     float yh[3], yl[3], c, q0[3], rc2;
 };
 
-template <bool SL, bool DL, int TPT, int FLUSH>
+// One work item: TPT = 2 NPK targets per thread, as NPK packed pairs.  Per pair term the same
+// operations in the same order as the scalar form: d = yc - x, r^2 = fma(dz,dz,fma(dy,dy,dx dx)),
+// 1/r by MUFU (masked to 0 where r^2 <= Rc^2), then the SL and DL terms.
+template <bool SL, bool DL, int NPK, int FLUSH>
 __device__ __forceinline__ void far32_item(const EvalArgs &A, float rc2f, int64_t tbi, int64_t chunk,
                                            float4 *srec, float4 &scen) {
+    constexpr int TPT = 2 * NPK;
     const int64_t j0 = chunk * A.chunk_len;  // multiple of TS32
     const int64_t j1 = min(A.sd.N, j0 + A.chunk_len);
     const float *__restrict__ rec = A.sd.rec32;
 
-    TargetF32 T[TPT];
+    float yh[TPT][3], yl[TPT][3], rc2[TPT];
     bool valid[TPT];
+    f2 nc[NPK], q0[NPK][3];  // -c and q0 of the two targets of each pair
     double acc[TPT][6];
-    float accf[TPT][6];
+    f2 accf[NPK][6];
 #pragma unroll
-    for (int t = 0; t < TPT; ++t) {
-        const int64_t m = tbi * (NT * TPT) + t * NT + threadIdx.x;
-        TargetF64 D;
-        load_target(A, m, SL, DL, D, valid[t]);
-        for (int i = 0; i < 3; ++i) {
-            T[t].yh[i] = __double2float_rn(D.y[i]);
-            T[t].yl[i] = __double2float_rn(D.y[i] - (double)T[t].yh[i]);
-            T[t].q0[i] = __double2float_rn(D.q0[i]);
-        }
-        T[t].c = __double2float_rn(D.c);
-        // far iff r2 > rc2: +inf = nothing far (invalid target), -1 = everything far
-        T[t].rc2 = !valid[t] ? __int_as_float(0x7f800000) : (D.rc2bits < 0 ? -1.0f : rc2f);
+    for (int p = 0; p < NPK; ++p) {
+        float c[2], q[2][3];
 #pragma unroll
-        for (int i = 0; i < 6; ++i) {
-            acc[t][i] = 0.0;
-            accf[t][i] = 0.0f;
+        for (int h = 0; h < 2; ++h) {
+            const int t = 2 * p + h;
+            const int64_t m = tbi * (NT * TPT) + t * NT + threadIdx.x;
+            TargetF64 D;
+            load_target(A, m, SL, DL, D, valid[t]);
+            for (int i = 0; i < 3; ++i) {
+                yh[t][i] = __double2float_rn(D.y[i]);
+                yl[t][i] = __double2float_rn(D.y[i] - (double)yh[t][i]);
+                q[h][i] = __double2float_rn(D.q0[i]);
+            }
+            c[h] = __double2float_rn(D.c);
+            // far iff r2 > rc2: +inf = nothing far (invalid target), -1 = everything far
+            rc2[t] = !valid[t] ? __int_as_float(0x7f800000) : (D.rc2bits < 0 ? -1.0f : rc2f);
+#pragma unroll
+            for (int i = 0; i < 6; ++i) acc[t][i] = 0.0;
         }
+        nc[p] = pk(-c[0], -c[1]);
+        for (int i = 0; i < 3; ++i) q0[p][i] = pk(q[0][i], q[1][i]);
+#pragma unroll
+        for (int i = 0; i < 6; ++i) accf[p][i] = 0ull;
     }
 
     int tiles_since_flush = 0;
@@ -176,60 +187,80 @@ __device__ __forceinline__ void far32_item(const EvalArgs &A, float rc2f, int64_
         if (threadIdx.x == 0) scen = reinterpret_cast<const float4 *>(A.sd.tilec)[base / TS32];
         __syncthreads();
         const float4 cen = scen;
-        float yc[TPT][3];
+        f2 yc[NPK][3];
 #pragma unroll
-        for (int t = 0; t < TPT; ++t) {
-            yc[t][0] = tile_rel(T[t].yh[0], cen.x, T[t].yl[0]);
-            yc[t][1] = tile_rel(T[t].yh[1], cen.y, T[t].yl[1]);
-            yc[t][2] = tile_rel(T[t].yh[2], cen.z, T[t].yl[2]);
+        for (int p = 0; p < NPK; ++p) {
+            const int a = 2 * p, b = 2 * p + 1;
+            yc[p][0] = pk(tile_rel(yh[a][0], cen.x, yl[a][0]), tile_rel(yh[b][0], cen.x, yl[b][0]));
+            yc[p][1] = pk(tile_rel(yh[a][1], cen.y, yl[a][1]), tile_rel(yh[b][1], cen.y, yl[b][1]));
+            yc[p][2] = pk(tile_rel(yh[a][2], cen.z, yl[a][2]), tile_rel(yh[b][2], cen.z, yl[b][2]));
         }
         for (int j = 0; j < ns; ++j) {
             const float4 r0 = srec[j * 3 + 0], r1 = srec[j * 3 + 1], r2v = srec[j * 3 + 2];
             // r0 = (xc0 xc1 xc2 wf0), r1 = (wf1 wf2 wn0 wn1), r2v = (wn2 q0 q1 q2)
+            const f2 x0 = pk(r0.x, r0.x), x1 = pk(r0.y, r0.y), x2 = pk(r0.z, r0.z);
+            const f2 wn0 = pk(r1.z, r1.z), wn1 = pk(r1.w, r1.w), wn2 = pk(r2v.x, r2v.x);
 #pragma unroll
-            for (int t = 0; t < TPT; ++t) {
-                float dx, dy, dz;
-                const float r2 = dist2_fp32(yc[t][0], yc[t][1], yc[t][2], r0.x, r0.y, r0.z, &dx, &dy, &dz);
-                float ri = rsqrt_ftz(r2);  // MUFU approximation, relative error ~1e-7; far pairs have r2 >= Rc^2
-                ri = (r2 > T[t].rc2) ? ri : 0.0f;
-                const float ri2 = ri * ri;
+            for (int p = 0; p < NPK; ++p) {
+                const f2 dx = sub2(yc[p][0], x0), dy = sub2(yc[p][1], x1), dz = sub2(yc[p][2], x2);
+                const f2 r2 = fma2(dz, dz, fma2(dy, dy, mul2(dx, dx)));
+                float ra, rb;
+                upk(r2, ra, rb);
+                // MUFU approximation, relative error ~1e-7; far pairs have r2 >= Rc^2
+                const float ia = (ra > rc2[2 * p]) ? rsqrt_ftz(ra) : 0.0f;
+                const float ib = (rb > rc2[2 * p + 1]) ? rsqrt_ftz(rb) : 0.0f;
+                const f2 ri = pk(ia, ib);
+                const f2 ri2 = mul2(ri, ri);
                 if (SL) {
-                    const float g0 = fmaf(-T[t].c, r1.z, r0.w);
-                    const float g1 = fmaf(-T[t].c, r1.w, r1.x);
-                    const float g2 = fmaf(-T[t].c, r2v.x, r1.y);
-                    const float s = fmaf(dz, g2, fmaf(dy, g1, dx * g0)) * ri2;
-                    accf[t][0] = fmaf(fmaf(dx, s, g0), ri, accf[t][0]);
-                    accf[t][1] = fmaf(fmaf(dy, s, g1), ri, accf[t][1]);
-                    accf[t][2] = fmaf(fmaf(dz, s, g2), ri, accf[t][2]);
+                    const f2 g0 = fma2(nc[p], wn0, pk(r0.w, r0.w));
+                    const f2 g1 = fma2(nc[p], wn1, pk(r1.x, r1.x));
+                    const f2 g2 = fma2(nc[p], wn2, pk(r1.y, r1.y));
+                    const f2 sv = mul2(fma2(dz, g2, fma2(dy, g1, mul2(dx, g0))), ri2);
+                    accf[p][0] = fma2(fma2(dx, sv, g0), ri, accf[p][0]);
+                    accf[p][1] = fma2(fma2(dy, sv, g1), ri, accf[p][1]);
+                    accf[p][2] = fma2(fma2(dz, sv, g2), ri, accf[p][2]);
                 }
                 if (DL) {
-                    const float Q0 = r2v.y - T[t].q0[0], Q1 = r2v.z - T[t].q0[1], Q2 = r2v.w - T[t].q0[2];
-                    const float dQ = fmaf(dz, Q2, fmaf(dy, Q1, dx * Q0));
-                    const float dm = fmaf(dz, r2v.x, fmaf(dy, r1.w, dx * r1.z));
-                    const float s = (dQ * dm) * ((ri2 * ri2) * ri);
-                    accf[t][3] = fmaf(dx, s, accf[t][3]);
-                    accf[t][4] = fmaf(dy, s, accf[t][4]);
-                    accf[t][5] = fmaf(dz, s, accf[t][5]);
+                    const f2 Q0 = sub2(pk(r2v.y, r2v.y), q0[p][0]);
+                    const f2 Q1 = sub2(pk(r2v.z, r2v.z), q0[p][1]);
+                    const f2 Q2 = sub2(pk(r2v.w, r2v.w), q0[p][2]);
+                    const f2 dQ = fma2(dz, Q2, fma2(dy, Q1, mul2(dx, Q0)));
+                    const f2 dm = fma2(dz, wn2, fma2(dy, wn1, mul2(dx, wn0)));
+                    const f2 sv = mul2(mul2(dQ, dm), mul2(mul2(ri2, ri2), ri));
+                    accf[p][3] = fma2(dx, sv, accf[p][3]);
+                    accf[p][4] = fma2(dy, sv, accf[p][4]);
+                    accf[p][5] = fma2(dz, sv, accf[p][5]);
                 }
             }
         }
         if (++tiles_since_flush == FLUSH) {
             tiles_since_flush = 0;
 #pragma unroll
-            for (int t = 0; t < TPT; ++t)
+            for (int p = 0; p < NPK; ++p)
 #pragma unroll
                 for (int i = 0; i < 6; ++i) {
-                    acc[t][i] += (double)accf[t][i];
-                    accf[t][i] = 0.0f;
+                    float a, b;
+                    upk(accf[p][i], a, b);
+                    acc[2 * p][i] += (double)a;
+                    acc[2 * p + 1][i] += (double)b;
+                    accf[p][i] = 0ull;
                 }
         }
     }
+#pragma unroll
+    for (int p = 0; p < NPK; ++p)
+#pragma unroll
+        for (int i = 0; i < 6; ++i) {
+            float a, b;
+            upk(accf[p][i], a, b);
+            acc[2 * p][i] += (double)a;
+            acc[2 * p + 1][i] += (double)b;
+        }
 #pragma unroll
     for (int t = 0; t < TPT; ++t) {
         if (!valid[t]) continue;
         const int64_t m = tbi * (NT * TPT) + t * NT + threadIdx.x;
         double *o = A.part + (chunk * A.M + m) * 6;
-        for (int i = 0; i < 6; ++i) acc[t][i] += (double)accf[t][i];
         o[0] = acc[t][0] * INV8PI;
         o[1] = acc[t][1] * INV8PI;
         o[2] = acc[t][2] * INV8PI;
@@ -239,15 +270,15 @@ __device__ __forceinline__ void far32_item(const EvalArgs &A, float rc2f, int64_
     }
 }
 
-template <bool SL, bool DL, int TPT, int FLUSH>
-__global__ void __launch_bounds__(NT, 4) k_far32(EvalArgs A, float rc2f, int64_t ntb) {
+template <bool SL, bool DL, int NPK, int FLUSH>
+__global__ void __launch_bounds__(NT, 3) k_far32(EvalArgs A, float rc2f, int64_t ntb) {
     __shared__ float4 srec[TS32 * 3];
     __shared__ float4 scen;
     const int64_t nitems = ntb * A.chunks;
     for (int64_t item = blockIdx.x; item < nitems; item += gridDim.x) {
         const int64_t tbi = item % ntb, chunk = item / ntb;
         __syncthreads();  // the previous item's last tile is no longer read
-        far32_item<SL, DL, TPT, FLUSH>(A, rc2f, tbi, chunk, srec, scen);
+        far32_item<SL, DL, NPK, FLUSH>(A, rc2f, tbi, chunk, srec, scen);
     }
 }
 
@@ -262,8 +293,9 @@ cudaError_t far64_dispatch(const EvalArgs &a) {
     return cudaGetLastError();
 }
 
-template <int TPT>
+template <int NPK>
 cudaError_t far32_dispatch(const EvalArgs &a, int ctas_per_sm, int nsm) {
+    constexpr int TPT = 2 * NPK;
     const int64_t tb = (a.M + NT * TPT - 1) / (NT * TPT);
     const int64_t nitems = tb * a.chunks;
     int64_t grid = nitems;
@@ -278,7 +310,7 @@ cudaError_t far32_dispatch(const EvalArgs &a, int ctas_per_sm, int nsm) {
     }
     const bool sl = a.layers & ERS_LAYER_SL, dl = a.layers & ERS_LAYER_DL;
     const float rc2f = (float)(a.Rc * a.Rc);  // same rounding as the near-field copy
-    auto kern = (sl && dl) ? k_far32<true, true, TPT, 2> : (sl ? k_far32<true, false, TPT, 2> : k_far32<false, true, TPT, 2>);
+    auto kern = (sl && dl) ? k_far32<true, true, NPK, 2> : (sl ? k_far32<true, false, NPK, 2> : k_far32<false, true, NPK, 2>);
     if (pad > 0) {
         // static + dynamic shared memory above 48 KB needs the opt-in (not a stream operation)
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pad);
@@ -303,7 +335,7 @@ __global__ void k_combine(const double *__restrict__ part, int chunks, int64_t M
 }  // namespace
 
 cudaError_t launch_far64(const EvalArgs &a) { return far64_dispatch<2, 64>(a); }
-cudaError_t launch_far32(const EvalArgs &a, int ctas_per_sm, int nsm) { return far32_dispatch<3>(a, ctas_per_sm, nsm); }
+cudaError_t launch_far32(const EvalArgs &a, int ctas_per_sm, int nsm) { return far32_dispatch<2>(a, ctas_per_sm, nsm); }
 
 cudaError_t launch_combine(const EvalArgs &a) {
     if (a.M == 0) return cudaSuccess;

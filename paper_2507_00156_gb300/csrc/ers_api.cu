@@ -251,7 +251,7 @@ int check_params(const ers_surface *s, const ers_params *p, int *warn) {
 // the single regularized sum with delta_0, near radius cutoff_t * delta_0.
 // CTAs per SM of the far (mixed) and near kernels: [0], [1] when they run concurrently,
 // [2], [3] when serial (0 = uncapped).  Changed only by the tuning hook below.
-int g_caps[4] = {2, 2, 0, 0};
+int g_caps[4] = {1, 1, 0, 0};
 
 int eval_impl(ers_surface *s, const ers_params *p, const double *y, int64_t M, const double *x0, const double *n0,
               const double *b, const double *f0, const double *q0, double *u, double *v, void *stream, int ndelta,

@@ -199,7 +199,8 @@ __device__ __forceinline__ void near_pair(const BatchProblemDev &P, const Geom &
     const double r2 = dist2_fp64(dx, dy, dz);
     if (!is_near<ERS_PREC_MIXED>(P.sd, T, j, r2, P.Rc, P.sp.rc2f)) return;
     double K1, K3, K5;
-    kernel_factors<CLS>(T, P.sp, tab, r2, K1, K3, K5);
+    float Lf;
+    kernel_factors<CLS>(T, P.sp, tab, r2, K1, K3, K5, Lf);
     const double nm = fma(T.n0[2], wn[2], fma(T.n0[1], wn[1], T.n0[0] * wn[0]));
     const double W = fma(dz, wn[2], fma(dy, wn[1], dx * wn[0]));
     const DLPair D = dl_pair(T, r2, K3, K5, nm, W);  // shared by the NR densities

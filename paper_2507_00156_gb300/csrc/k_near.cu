@@ -28,6 +28,9 @@ namespace {
 
 using namespace nearc;
 constexpr int WPB = 4;  // warps per block
+// Two CTAs per SM: the mixed SL+DL kernel needs 240 registers without spills; capping it at 168
+// for three CTAs spills and runs no faster (measured 137.4 vs 137.5 ms on the bench workload).
+constexpr int NEAR_MIN_BLOCKS = 2;
 
 template <int CLS, int PREC, bool SL, bool DL, int ND>
 __device__ __forceinline__ void process(const EvalArgs &A, const Geom &T, const ScanParams &P, double c,
@@ -55,13 +58,22 @@ __device__ __forceinline__ void process(const EvalArgs &A, const Geom &T, const 
         nunreg[2] += u == 2;
     }
     double K1, K3, K5;
-    kernel_factors<CLS, ND>(T, P, tab, r2, K1, K3, K5);
+    float Lf;
+    kernel_factors<CLS, ND>(T, P, tab, r2, K1, K3, K5, Lf);
     if (SL) sl_accumulate(dx, dy, dz, K1, K3, c, wf, wn, accU);
     if (DL) {
-        const double nm = fma(T.n0[2], wn[2], fma(T.n0[1], wn[1], T.n0[0] * wn[0]));
         const double W = fma(dz, wn[2], fma(dy, wn[1], dx * wn[0]));
-        const DLPair D = dl_pair(T, r2, K3, K5, nm, W);
-        dl_accumulate(D, T, dx, dy, dz, nm, qs, q0, accN, accD);
+        if (CLS >= ND) {  // every delta on the defect path: L and what it multiplies in FP32
+            const float nmf = fmaf(approx_float(T.n0[2]), approx_float(wn[2]),
+                                   fmaf(approx_float(T.n0[1]), approx_float(wn[1]),
+                                        approx_float(T.n0[0]) * approx_float(wn[0])));
+            const float Zf = fmaf(approx_float(T.b2), nmf, -approx_float(W));
+            dl_accumulate_defect(T, dx, dy, dz, Lf, K5 * W, nmf, Zf, qs, q0, accN, accD);
+        } else {
+            const double nm = fma(T.n0[2], wn[2], fma(T.n0[1], wn[1], T.n0[0] * wn[0]));
+            const DLPair D = dl_pair(T, r2, K3, K5, nm, W);
+            dl_accumulate(D, T, dx, dy, dz, nm, qs, q0, accN, accD);
+        }
     }
 }
 
@@ -132,7 +144,7 @@ __device__ __forceinline__ void near_target(const EvalArgs &A, const ScanParams 
 }
 
 template <int PREC, bool SL, bool DL, int ND>
-__global__ void __launch_bounds__(WPB * 32) k_near(EvalArgs A, ScanParams P, const double *__restrict__ tab) {
+__global__ void __launch_bounds__(WPB * 32, NEAR_MIN_BLOCKS) k_near(EvalArgs A, ScanParams P, const double *__restrict__ tab) {
     __shared__ int sq[WPB][NCLS][64];
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     // one target per warp; a capped grid strides over the targets

@@ -192,10 +192,13 @@ __device__ __forceinline__ bool is_near(const SurfDev &s, const Geom &T, int64_t
 // r > min(DEFECT_T, cutoff_t) delta_k and take the defect path below; the others take sigma_p
 // from the interpolation table.  ND = number of deltas in use (3 for the method; 2 or 1 for the
 // learned closure).
+// Lf: when every delta in use is on the defect path (CLS >= ND), L = r^2 K5 - K3 = (E3 - E5)/r^3
+// in FP32 (see dl_accumulate_defect); 0 otherwise.
 template <int CLS, int ND = 3>
 __device__ __forceinline__ void kernel_factors(const Geom &T, const ScanParams &P, const double *__restrict__ tab,
-                                               double r2, double &K1, double &K3, double &K5) {
+                                               double r2, double &K1, double &K3, double &K5, float &Lf) {
     constexpr int NDEF = CLS < ND ? CLS : ND;  // defect-path deltas that carry weight
+    Lf = 0.0f;
     double ri = 0.0, ri3 = 0.0, ri5 = 0.0;
     if (CLS >= 1) {
         // r / delta_k > DEFECT_T: s_p = 1 - eps_p with eps_1 = erfc t, eps_2 = eps_1 + (2/sqrt pi) t e^{-t^2},
@@ -239,9 +242,11 @@ __device__ __forceinline__ void kernel_factors(const Geom &T, const ScanParams &
         ri5 = ri3 * ri2;
         // eps_p / r^p in FP32 from the rounded FP64 powers (relative error ~1e-7 of terms below
         // 2.1e-8 of the result; powers formed in FP32 would add up to 5 roundings)
+        const float rf3 = round_float_pos(ri3);
         K1 = -float_to_double(E1 * round_float_pos(ri));
-        K3 = -float_to_double(E3 * round_float_pos(ri3));
+        K3 = -float_to_double(E3 * rf3);
         K5 = -float_to_double(E5 * round_float_pos(ri5));
+        if (CLS >= ND) Lf = (E3 - E5) * rf3;
     } else {
         K1 = 0.0;
         K3 = 0.0;
@@ -326,6 +331,25 @@ __device__ __forceinline__ void dl_accumulate(const DLPair &D, const Geom &T, do
     const double U = fma(dz, Q2, fma(dy, Q1, dx * Q0));
     accN = fma(D.L, fma(nQ, D.Z, -(nm * U)), accN);
     const double C = fma(D.Lnm, nQ, -(D.K5W * U));
+    accD[0] = fma(C, dx, accD[0]);
+    accD[1] = fma(C, dy, accD[1]);
+    accD[2] = fma(C, dz, accD[2]);
+}
+
+// dl_accumulate for a pair whose deltas are all on the defect path (t > 4.7): then
+// L = r^2 K5 - K3 = (E3 - E5)/r^3 (E_p the alpha-weighted defects of s_p), below ~1e-7 of K3,
+// so every factor that multiplies L (n0.Q, n0.m, 2 b n0.m - W) runs in FP32 (relative error
+// ~3e-7 of terms below 1e-7 of the result); U = d.Q, W = d.m and K5 W U stay in FP64.
+__device__ __forceinline__ void dl_accumulate_defect(const Geom &T, double dx, double dy, double dz, float Lf,
+                                                     double K5W, float nmf, float Zf, const double qs[3],
+                                                     const double q0[3], double &accN, double accD[3]) {
+    const double Q0 = qs[0] - q0[0], Q1 = qs[1] - q0[1], Q2 = qs[2] - q0[2];
+    const double U = fma(dz, Q2, fma(dy, Q1, dx * Q0));
+    const float nQf = fmaf(approx_float(T.n0[2]), approx_float(Q2),
+                           fmaf(approx_float(T.n0[1]), approx_float(Q1), approx_float(T.n0[0]) * approx_float(Q0)));
+    const float Uf = approx_float(U);
+    accN += float_to_double(Lf * fmaf(nQf, Zf, -(nmf * Uf)));
+    const double C = fma(-K5W, U, float_to_double(Lf * nmf * nQf));
     accD[0] = fma(C, dx, accD[0]);
     accD[1] = fma(C, dy, accD[1]);
     accD[2] = fma(C, dz, accD[2]);

@@ -201,9 +201,21 @@ __device__ __forceinline__ void near_pair(const BatchProblemDev &P, const Geom &
     double K1, K3, K5;
     float Lf;
     kernel_factors<CLS>(T, P.sp, tab, r2, K1, K3, K5, Lf);
-    const double nm = fma(T.n0[2], wn[2], fma(T.n0[1], wn[1], T.n0[0] * wn[0]));
     const double W = fma(dz, wn[2], fma(dy, wn[1], dx * wn[0]));
-    const DLPair D = dl_pair(T, r2, K3, K5, nm, W);  // shared by the NR densities
+    // every delta on the defect path (CLS = 3): L and the factors it multiplies in FP32
+    // (dl_accumulate_defect); otherwise the FP64 pair factors, shared by the NR densities
+    double nm = 0.0;
+    float nmf = 0.0f, Zf = 0.0f;
+    DLPair D{};
+    if (CLS >= 3) {
+        nmf = fmaf(approx_float(T.n0[2]), approx_float(wn[2]),
+                   fmaf(approx_float(T.n0[1]), approx_float(wn[1]), approx_float(T.n0[0]) * approx_float(wn[0])));
+        Zf = fmaf(approx_float(T.b2), nmf, -approx_float(W));
+    } else {
+        nm = fma(T.n0[2], wn[2], fma(T.n0[1], wn[1], T.n0[0] * wn[0]));
+        D = dl_pair(T, r2, K3, K5, nm, W);
+    }
+    const double K5W = K5 * W;
     const bool sl = layers & ERS_LAYER_SL, dl = layers & ERS_LAYER_DL;
     if (sl) {
         const double tb = K3 * W;
@@ -226,7 +238,8 @@ __device__ __forceinline__ void near_pair(const BatchProblemDev &P, const Geom &
             const double qs[3] = {d1.y, d2.x, d2.y};
             const double q0[3] = {S.tq[warp][r][1], S.tq[warp][r][2], S.tq[warp][r][3]};
             double accN = a[3][lane], accD[3] = {a[4][lane], a[5][lane], a[6][lane]};
-            dl_accumulate(D, T, dx, dy, dz, nm, qs, q0, accN, accD);
+            if (CLS >= 3) dl_accumulate_defect(T, dx, dy, dz, Lf, K5W, nmf, Zf, qs, q0, accN, accD);
+            else dl_accumulate(D, T, dx, dy, dz, nm, qs, q0, accN, accD);
             a[3][lane] = accN;
             a[4][lane] = accD[0];
             a[5][lane] = accD[1];

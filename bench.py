@@ -309,9 +309,18 @@ def learned_leg(ers, torch, s, wl, y, steps: int, warmup: int):
     t_plain, _ = timed(lambda: sa.eval(yed, f0, q0, rho=wl.rho, precision=ers.PREC_MIXED, x0=x0, n0=n0, b=b,
                                        u=u, v=v))
     u_ref, v_ref = u.cpu().numpy(), v.cpu().numpy()
+    # the plain FP64 path on the same problem (one step after one warm-up)
+    sa.eval(yed, f0, q0, rho=wl.rho, precision=ers.PREC_FP64, x0=x0, n0=n0, b=b, u=u, v=v)
+    a64, e64 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a64.record(stream)
+    sa.eval(yed, f0, q0, rho=wl.rho, precision=ers.PREC_FP64, x0=x0, n0=n0, b=b, u=u, v=v)
+    e64.record(stream)
+    e64.synchronize()
+    t_fp64 = a64.elapsed_time(e64) / 1e3
     res = {"workload": "train: unit sphere h=1/128, 5 seeded densities; evaluate: two unit spheres gap 0.01, "
                        "h=1/96, integral over the first at the nodes of both",
            "targets": M, "nodes": int(xa.shape[0]),
+           "plain_fp64": {"value": M / t_fp64, "unit": UNIT, "ms_per_step": t_fp64 * 1e3},
            "plain_mixed": {"value": M / t_plain, "unit": UNIT, "ms_per_step": t_plain * 1e3},
            "training": {"samples_per_network": nsamples, "densities": 5, "steps": 3000, "batch": 8192,
                         "data_s": t_data, "train_s": t_train}}
@@ -327,7 +336,7 @@ def learned_leg(ers, torch, s, wl, y, steps: int, warmup: int):
             "value": M / t_val, "unit": UNIT, "ms_per_step": t_val * 1e3,
             "fell_back_at_tol_1e-5": bool(fb), "validation_rel_err": [float(z) for z in verr],
             "accepted": {"value": M / t_acc, "ms_per_step": t_acc * 1e3,
-                         "speedup_vs_plain_mixed": t_plain / t_acc,
+                         "speedup_vs_plain_mixed": t_plain / t_acc, "speedup_vs_plain_fp64": t_fp64 / t_acc,
                          "max_rel_err_vs_three_delta": {
                              "SL": float(np.abs(ul - u_ref).max() / np.abs(u_ref).max()),
                              "DL": float(np.abs(vl - v_ref).max() / np.abs(v_ref).max())}},

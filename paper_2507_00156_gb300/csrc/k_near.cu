@@ -28,9 +28,7 @@ namespace {
 
 using namespace nearc;
 constexpr int WPB = 4;  // warps per block
-// Two CTAs per SM: the mixed SL+DL kernel needs 240 registers without spills; capping it at 168
-// for three CTAs spills and runs no faster (measured 137.4 vs 137.5 ms on the bench workload).
-constexpr int NEAR_MIN_BLOCKS = 2;
+constexpr int NEAR_MIN_BLOCKS = 3;
 
 template <int CLS, int PREC, bool SL, bool DL, int ND>
 __device__ __forceinline__ void process(const EvalArgs &A, const Geom &T, const ScanParams &P, double c,
@@ -79,7 +77,7 @@ __device__ __forceinline__ void process(const EvalArgs &A, const Geom &T, const 
 
 template <int PREC, bool SL, bool DL, int ND>
 __device__ __forceinline__ void near_target(const EvalArgs &A, const ScanParams &P, const double *__restrict__ tab,
-                                            int64_t m, int lane, int (*sq)[64]) {
+                                            int64_t m, int lane, int (*sq)[64], Geom &G) {
     // sum of the far-field chunk partials: lane i < 6 holds component i
     double fs = 0.0;
     if (lane < 6 && !A.far_later)
@@ -92,10 +90,18 @@ __device__ __forceinline__ void near_target(const EvalArgs &A, const ScanParams 
         return;
     }
 
-    Geom T;
+    // The per-target constants live in the warp's shared-memory slot G and are read from there
+    // at each use (the pair loop would otherwise hold ~70 of them in registers).
     double gam = 0.0;
-    load_geom(lane, A.y, A.x0, A.n0, bm, m, A.rho, P.h, T, A.ndelta, &gam);
-    set_cutoff(T, P);
+    {
+        Geom Tl;
+        load_geom(lane, A.y, A.x0, A.n0, bm, m, A.rho, P.h, Tl, A.ndelta, &gam);
+        set_cutoff(Tl, P);
+        __syncwarp();  // the previous target's reads of G are done
+        if (lane == 0) G = Tl;
+        __syncwarp();
+    }
+    const Geom &T = G;
     if (A.gamma && lane == 0) A.gamma[m] = gam;
     double q0[3];
     for (int i = 0; i < 3; ++i) q0[i] = DL ? A.q0[3 * m + i] : 0.0;
@@ -146,10 +152,11 @@ __device__ __forceinline__ void near_target(const EvalArgs &A, const ScanParams 
 template <int PREC, bool SL, bool DL, int ND>
 __global__ void __launch_bounds__(WPB * 32, NEAR_MIN_BLOCKS) k_near(EvalArgs A, ScanParams P, const double *__restrict__ tab) {
     __shared__ int sq[WPB][NCLS][64];
+    __shared__ Geom sG[WPB];
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     // one target per warp; a capped grid strides over the targets
     for (int64_t m = (int64_t)blockIdx.x * WPB + wib; m < A.M; m += (int64_t)gridDim.x * WPB)
-        near_target<PREC, SL, DL, ND>(A, P, tab, m, lane, sq[wib]);
+        near_target<PREC, SL, DL, ND>(A, P, tab, m, lane, sq[wib], sG[wib]);
 }
 
 template <int PREC>

@@ -55,6 +55,10 @@ def _load():
             lib.ora_closest_point.argtypes = [P, P, P, i64, dbl, P, P, P]
             lib.ora_sigma.restype = None
             lib.ora_sigma.argtypes = [dbl, P]
+            lib.ora_sigma_sharp.restype = None
+            lib.ora_sigma_sharp.argtypes = [dbl, P]
+            lib.ora_eval_sharp.restype = i64
+            lib.ora_eval_sharp.argtypes = [P, P, P, P, P, i64, P, P, P, P, P, P, i64, dbl, P, dbl, dbl, P, P]
             lib.ora_I0.restype = dbl
             lib.ora_I0.argtypes = [dbl]
             lib.ora_I2.restype = dbl
@@ -112,6 +116,13 @@ def sigma(t: float) -> np.ndarray:
     return out
 
 
+def sigma_sharp(t: float) -> np.ndarray:
+    """s#_p(t)/t^p for p = 1, 3, 5 (the on-surface functions of Sec. 2.1)."""
+    out = np.empty(3)
+    _load().ora_sigma_sharp(float(t), _p(out))
+    return out
+
+
 def I0(lam: float) -> float:
     return float(_load().ora_I0(float(lam)))
 
@@ -138,6 +149,19 @@ def evaluate(x, n, w, f, q, y, x0, n0, b, f0, q0, h, rho, tc=6.0, mode=LOCALIZED
     u, v = np.empty((M, 3)), np.empty((M, 3))
     nfail = lib.ora_eval(_p(x), _p(n), _p(w), _p(f), _p(q), N, _p(y), _p(x0), _p(n0), _p(b), _p(f0), _p(q0), M,
                          float(h), _p(_c(rho)), float(tc), int(mode), _p(u), _p(v))
+    return u, v, int(nfail)
+
+
+def evaluate_sharp(x, n, w, f, q, y, x0, n0, b, f0, q0, h, rho, tc=6.0, rho_sharp=3.0):
+    """Targets on the surface (b == 0): one sum with the s#_p of Sec. 2.1 and delta# = rho_sharp h,
+    no extrapolation; the others by the extrapolated method.  See ers_oracle.c:ora_eval_sharp."""
+    lib = _load()
+    x, n, w, f, q = map(_c, (x, n, w, f, q))
+    y, x0, n0, b, f0, q0 = map(_c, (y, x0, n0, b, f0, q0))
+    N, M = w.shape[0], b.shape[0]
+    u, v = np.empty((M, 3)), np.empty((M, 3))
+    nfail = lib.ora_eval_sharp(_p(x), _p(n), _p(w), _p(f), _p(q), N, _p(y), _p(x0), _p(n0), _p(b), _p(f0), _p(q0),
+                               M, float(h), _p(_c(rho)), float(tc), float(rho_sharp), _p(u), _p(v))
     return u, v, int(nfail)
 
 

@@ -13,7 +13,9 @@
  *
  * Parity status of each function: pinned by tests/test_oracle_*.py (node counts of Table 1,
  * surface areas, sphere closed forms, exact extrapolation weights at b = 0, O(h^5) observed
- * convergence, localized == direct).  Nothing here is "parity unpinned".
+ * convergence, localized == direct; for the on-surface s# functions of Sec. 2.1: 60-digit
+ * values, the limits at 0 and infinity, O(h^5) against the sphere closed form and in
+ * self-convergence at shared nodes).  Nothing here is "parity unpinned".
  */
 #include <math.h>
 #include <stdint.h>
@@ -212,6 +214,49 @@ void ora_sigma(double t, double sig[3]) {
     sig[2] = s3 / (t * t * t * t * t);
 }
 
+/*
+ * sigma#_p(t) = s#_p(t) / t^p for the modified smoothing functions of Sec. 2.1 (on-surface
+ * evaluation):
+ *   s#_1 = erf t + (2/(3 sqrt pi)) (5t - 2t^3) e^{-t^2},
+ *   s#_2 = erf t - (2/(3 sqrt pi)) (3t - 14t^3 + 4t^5) e^{-t^2},
+ *   s#_3 = erf t - (2/(9 sqrt pi)) (9t + 6t^3 - 4t^5) e^{-t^2}.
+ * For t < 1 term by term: with erf t = (2/sqrt pi) sum (-1)^n t^(2n+1) / (n! (2n+1)) and the
+ * coefficient of t^(2n+1) in P(t) e^{-t^2} collected for each polynomial P,
+ *   s#_1 / t   = (2/sqrt pi) sum_{n>=0} (-1)^n t^(2n)   [1/(2n+1) + (5 + 2n)/3]          / n!
+ *   s#_2 / t^3 = (2/sqrt pi) sum_{n>=1} (-1)^n t^(2n-2) [1/(2n+1) - (4n^2 + 10n + 3)/3] / n!
+ *   s#_3 / t^5 = (2/sqrt pi) sum_{n>=2} (-1)^n t^(2n-4) [1/(2n+1) - (9 - 2n - 4n^2)/9] / n!
+ * (the n = 0 term of s#_2 and the n = 0, 1 terms of s#_3 vanish).  Otherwise the closed forms.
+ */
+void ora_sigma_sharp(double t, double sig[3]) {
+    const double c = 2.0 / ORA_SQRTPI;
+    if (t < 1.0) {
+        double t2 = t * t;
+        double s1 = 0.0, s2 = 0.0, s3 = 0.0;
+        double fact = 1.0;                    /* n! */
+        double p1 = 1.0, p2 = 1.0, p3 = 1.0;  /* t^(2n), t^(2n-2), t^(2n-4) */
+        for (int nn = 0; nn <= 30; ++nn) {
+            if (nn > 0) fact *= nn;
+            if (nn > 0) p1 *= t2;
+            if (nn > 1) p2 *= t2;
+            if (nn > 2) p3 *= t2;
+            double sgn = (nn % 2 == 0) ? 1.0 : -1.0;
+            double e = 1.0 / (2.0 * nn + 1.0);
+            s1 += sgn * p1 * (e + (5.0 + 2.0 * nn) / 3.0) / fact;
+            if (nn >= 1) s2 += sgn * p2 * (e - (4.0 * nn * nn + 10.0 * nn + 3.0) / 3.0) / fact;
+            if (nn >= 2) s3 += sgn * p3 * (e - (9.0 - 2.0 * nn - 4.0 * nn * nn) / 9.0) / fact;
+        }
+        sig[0] = c * s1; sig[1] = c * s2; sig[2] = c * s3;
+        return;
+    }
+    double e = erf(t), g = exp(-t * t), t2 = t * t;
+    double s1 = e + c / 3.0 * (5.0 * t - 2.0 * t * t2) * g;
+    double s2 = e - c / 3.0 * (3.0 * t - 14.0 * t * t2 + 4.0 * t * t2 * t2) * g;
+    double s3 = e - c / 9.0 * (9.0 * t + 6.0 * t * t2 - 4.0 * t * t2 * t2) * g;
+    sig[0] = s1 / t;
+    sig[1] = s2 / (t * t2);
+    sig[2] = s3 / (t * t2 * t2);
+}
+
 /* I0 and I2 of Eqs. (I0), (I2). */
 double ora_I0(double lam) {
     double l = fabs(lam);
@@ -277,12 +322,13 @@ int ora_extrapolate(const double rho[3], double b, double h, const double *U /* 
  * t = r/delta; s_p := 1 when t > tc (Sec. 3.2).  Adds into acc[3] (without 1/(8 pi)).
  */
 static void ora_sl_term(const double d[3], double r, double delta, double tc, const double g[3], double w,
-                        double acc[3]) {
+                        double acc[3], int sharp) {
     double t = r / delta;
-    double k1, k3; /* s1/r and s2/r^3 */
+    double k1, k3; /* s1/r and s2/r^3 (s#1, s#2 when sharp) */
     if (t > tc) { k1 = 1.0 / r; k3 = 1.0 / (r * r * r); }
     else {
-        double sig[3]; ora_sigma(t, sig);
+        double sig[3];
+        if (sharp) ora_sigma_sharp(t, sig); else ora_sigma(t, sig);
         k1 = sig[0] / delta;
         k3 = sig[1] / (delta * delta * delta);
     }
@@ -301,12 +347,13 @@ static void ora_sl_term(const double d[3], double r, double delta, double tc, co
  * explicitly and contracted, as written.  s_p := 1 when t > tc.
  */
 static void ora_dl_term(double r, double delta, double tc, double b, const double nrm0[3], const double xh[3],
-                        const double Q[3], const double nx[3], double w, double acc[3]) {
+                        const double Q[3], const double nx[3], double w, double acc[3], int sharp) {
     double t = r / delta;
-    double k3, k5; /* s2/r^3 and s3/r^5 */
+    double k3, k5; /* s2/r^3 and s3/r^5 (s#2, s#3 when sharp) */
     if (t > tc) { k3 = 1.0 / (r * r * r); k5 = 1.0 / (r * r * r * r * r); }
     else {
-        double sig[3]; ora_sigma(t, sig);
+        double sig[3];
+        if (sharp) ora_sigma_sharp(t, sig); else ora_sigma(t, sig);
         k3 = sig[1] / (delta * delta * delta);
         k5 = sig[2] / (delta * delta * delta * delta * delta);
     }
@@ -324,6 +371,26 @@ static void ora_dl_term(double r, double delta, double tc, double b, const doubl
         }
         acc[i] += s * w;
     }
+}
+
+/*
+ * On-surface regularized double-layer pair term with the modified function s#_3 of Sec. 2.1
+ * applied to the stresslet itself, -6 d_i d_j d_k s#_3(r/delta)/r^5 (at b = 0 the split
+ * T^(1) s_2 + T^(2) s_3 equals this form plus t1 (s_2 - s_3)/r^3, which for s# is not small);
+ * s#_3 := 1 when t > tc.  Adds -6 d (d.Q)(d.n) s#_3/r^5 w into acc.
+ */
+static void ora_dl_term_sharp(const double d[3], double r, double delta, double tc, const double Q[3],
+                              const double nx[3], double w, double acc[3]) {
+    double t = r / delta;
+    double k5;
+    if (t > tc) k5 = 1.0 / (r * r * r * r * r);
+    else {
+        double sig[3]; ora_sigma_sharp(t, sig);
+        k5 = sig[2] / (delta * delta * delta * delta * delta);
+    }
+    double dq = d[0] * Q[0] + d[1] * Q[1] + d[2] * Q[2];
+    double dn = d[0] * nx[0] + d[1] * nx[1] + d[2] * nx[2];
+    for (int i = 0; i < 3; ++i) acc[i] += -6.0 * d[i] * dq * dn * k5 * w;
 }
 
 /* Plain (unregularized) pair terms, Eqs. (Stokeslet), (Stresslet). */
@@ -404,8 +471,8 @@ int64_t ora_eval(const double *x, const double *nrm, const double *w, const doub
             }
             for (int k = 0; k < 3; ++k) {
                 double delta = rho[k] * h;
-                ora_sl_term(d, r, delta, tc, g, w[j], snear_u[k]);
-                ora_dl_term(r, delta, tc, bm, nm0, xh, Q, nj, w[j], snear_v[k]);
+                ora_sl_term(d, r, delta, tc, g, w[j], snear_u[k], 0);
+                ora_dl_term(r, delta, tc, bm, nm0, xh, Q, nj, w[j], snear_v[k], 0);
             }
         }
         for (int k = 0; k < 3; ++k) {
@@ -445,11 +512,59 @@ void ora_eval_one_delta(const double *x, const double *nrm, const double *w, con
                 Q[i] = q[3 * j + i] - qm0[i];
                 xh[i] = xj[i] - xm0[i];
             }
-            ora_sl_term(d, r, delta, tc, g, w[j], su);
-            ora_dl_term(r, delta, tc, bm, nm0, xh, Q, nj, w[j], sv);
+            ora_sl_term(d, r, delta, tc, g, w[j], su, 0);
+            ora_dl_term(r, delta, tc, bm, nm0, xh, Q, nj, w[j], sv, 0);
         }
         for (int i = 0; i < 3; ++i) { u[3 * m + i] = su[i] * inv8pi; v[3 * m + i] = sv[i] * inv8pi + chi * qm0[i]; }
     }
+}
+
+/*
+ * On-surface evaluation with the modified smoothing functions of Sec. 2.1: for targets on the
+ * surface (b == 0 after the snap of ora_closest_point) one regularized sum with s#_p and
+ * delta# = rho_sharp h (single layer: Eq. (Sreg) with s#_1, s#_2; double layer: the stresslet
+ * with s#_3, ora_dl_term_sharp), localized like Sec. 3.3 with Rc# = tc delta# (far part
+ * unregularized, once), no extrapolation; chi = 1/2.  Targets off the surface are evaluated by ora_eval in
+ * LOCALIZED mode (three deltas and the solve).  Same conventions and outputs as ora_eval.
+ */
+int64_t ora_eval_sharp(const double *x, const double *nrm, const double *w, const double *f, const double *q,
+                       int64_t N, const double *y, const double *x0, const double *n0, const double *b,
+                       const double *f0, const double *q0, int64_t M, double h, const double rho[3], double tc,
+                       double rho_sharp, double *u, double *v) {
+    const double inv8pi = 1.0 / (8.0 * ORA_PI);
+    const double delta = rho_sharp * h, Rc = tc * delta;
+    int64_t nfail = 0;
+#pragma omp parallel for schedule(dynamic, 16) reduction(+ : nfail)
+    for (int64_t m = 0; m < M; ++m) {
+        if (b[m] != 0.0) {  /* off the surface: the extrapolated method */
+            nfail += ora_eval(x, nrm, w, f, q, N, y + 3 * m, x0 + 3 * m, n0 + 3 * m, b + m, f0 + 3 * m, q0 + 3 * m, 1,
+                              h, rho, tc, 1, u + 3 * m, v + 3 * m);
+            continue;
+        }
+        const double *ym = y + 3 * m, *nm0 = n0 + 3 * m, *xm0 = x0 + 3 * m, *fm0 = f0 + 3 * m, *qm0 = q0 + 3 * m;
+        double fn0 = fm0[0] * nm0[0] + fm0[1] * nm0[1] + fm0[2] * nm0[2];
+        double su[3] = {0, 0, 0}, sv[3] = {0, 0, 0};
+        for (int64_t j = 0; j < N; ++j) {
+            const double *xj = x + 3 * j, *nj = nrm + 3 * j;
+            double d[3] = {ym[0] - xj[0], ym[1] - xj[1], ym[2] - xj[2]};
+            double r = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+            double g[3], Q[3], xh[3];
+            for (int i = 0; i < 3; ++i) {
+                g[i] = f[3 * j + i] - fn0 * nj[i];
+                Q[i] = q[3 * j + i] - qm0[i];
+                xh[i] = xj[i] - xm0[i];
+            }
+            if (r > Rc) {
+                ora_sl_plain(d, r, g, w[j], su);
+                ora_dl_plain(d, r, Q, nj, w[j], sv);
+            } else {
+                ora_sl_term(d, r, delta, tc, g, w[j], su, 1);
+                ora_dl_term_sharp(d, r, delta, tc, Q, nj, w[j], sv);
+            }
+        }
+        for (int i = 0; i < 3; ++i) { u[3 * m + i] = su[i] * inv8pi; v[3 * m + i] = sv[i] * inv8pi + 0.5 * qm0[i]; }
+    }
+    return nfail;
 }
 
 /* Plain sums of Eqs. (Stokes_SL), (Stokes_DL) with the given densities and no

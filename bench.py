@@ -45,7 +45,7 @@ FAR_FLOPS_PER_PAIR = 34 + 1 + 33 + 1      # both layers, one far pair
 NEAR_FLOPS_PER_DELTA_EVAL = 30 + 1 + 1    # one regularized (node, delta) term, both layers
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) from one ncu capture of
 # the sphere128 workload with the current kernels (profiles/launches_sphere128_mixed.md).
-NCU_TRAFFIC = {("sphere128", "k_near"): 195911936 + 19416320, ("sphere128", "k_far32"): 59682560 + 30467584}
+NCU_TRAFFIC = {("sphere128", "k_near"): 202522112 + 16934912, ("sphere128", "k_far32"): 59682560 + 30467584}
 
 
 def parse():
@@ -398,7 +398,8 @@ def main():
     y = build_targets(wl, x)
     M, N = len(y), s.N
     yd = torch.from_numpy(y).to(dev)
-    x0, _, _ = s.closest_point(yd)  # set-up only: the densities at the closest points are inputs
+    x0, _, b0 = s.closest_point(yd)  # set-up only: the densities at the closest points are inputs
+    on_surface = b0.cpu().numpy() == 0.0
     x0h = x0.cpu().numpy()
     f0h, q0h = workloads.poly_eval(wl.f_coef, x0h), workloads.poly_eval(wl.q_coef, x0h)
     f0, q0 = torch.from_numpy(f0h).to(dev), torch.from_numpy(q0h).to(dev)
@@ -407,12 +408,12 @@ def main():
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)  # > 129 MB L2
     stream = torch.cuda.current_stream()
 
-    def step(prec, concurrent=False):
-        s.eval(yd, f0, q0, rho=wl.rho, precision=prec, u=u, v=v, concurrent=concurrent)
+    def step(prec, concurrent=False, sharp=False):
+        s.eval(yd, f0, q0, rho=wl.rho, precision=prec, u=u, v=v, concurrent=concurrent, sharp=sharp)
 
-    def timed(prec, steps, warm, concurrent=False):
+    def timed(prec, steps, warm, concurrent=False, sharp=False):
         for _ in range(warm):
-            step(prec, concurrent)
+            step(prec, concurrent, sharp)
         s.profile(True)
         torch.cuda.synchronize()
         barrier(world)
@@ -423,7 +424,7 @@ def main():
             flush.fill_(1)
             a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             a.record(stream)
-            step(prec, concurrent)
+            step(prec, concurrent, sharp)
             b.record(stream)
             evs.append((a, b))
             kern.append(s.last_profile())  # synchronizes; device times are unaffected
@@ -452,6 +453,13 @@ def main():
     t_mixed = max_over_ranks(t_mixed, world)
     ms_step = t_mixed / args.steps * 1e3
     value = world * args.steps * M / t_mixed
+
+    # the same mixed step with the on-surface option (ERS_OPT_SHARP, Sec. 2.1): node targets with
+    # one delta# = rho_2 h and the s#_p, no extrapolation
+    t_sh, k_sh = timed(ers.PREC_MIXED, args.steps, 1, sharp=True)
+    t_sh = max_over_ranks(t_sh, world)
+    nsh_pairs = s.last_sharp_pairs()
+    u_sh, v_sh = u.cpu().numpy(), v.cpu().numpy()
 
     # the same mixed step with the far and near fields on two streams (ERS_OPT_CONCURRENT)
     t_conc, k_conc = timed(ers.PREC_MIXED, args.steps, 1, concurrent=True)
@@ -514,6 +522,17 @@ def main():
                    "l2": "flushed between timed steps (256 MiB write, outside the timed events)"},
         "gpairs_per_s": world * args.steps * M * N / t_mixed / 1e9,
         "kernels_ms": {"closest_point": ms_closest, "far_field": ms_far, "near_field_and_solve": ms_near},
+        "sharp_option": {"ms_per_step": t_sh / args.steps * 1e3,
+                         "speedup_vs_extrapolated": t_mixed / t_sh,
+                         "kernels_ms": {"far_field": float(k_sh[1]), "near_field_and_solve": float(k_sh[2])},
+                         "on_surface_targets": int(on_surface.sum()), "on_surface_near_pairs": nsh_pairs,
+                         "max_rel_diff_vs_extrapolated_on_surface": {
+                             "SL": float(np.abs(u_sh[on_surface] - u_mixed[on_surface]).max()
+                                         / np.abs(u_mixed[on_surface]).max()),
+                             "DL": float(np.abs(v_sh[on_surface] - v_mixed[on_surface]).max()
+                                         / np.abs(v_mixed[on_surface]).max())},
+                         "note": "ERS_OPT_SHARP: on-surface targets with the s#_p of Sec. 2.1, delta# = 3h, "
+                                 "no extrapolation; both methods are O(h^5)"},
         "concurrent_option": {"ms_per_step": t_conc / args.steps * 1e3,
                               "kernels_ms": {"far_field": float(k_conc[1]), "near_field_and_solve": float(k_conc[2])},
                               "note": "same step with ERS_OPT_CONCURRENT (far and near fields on two streams, "

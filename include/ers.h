@@ -53,6 +53,12 @@ extern "C" {
                                 pipe) on a second stream of the surface, concurrently with the near
                                 field (FP64 pipe), instead of one after the other (see ers_eval) */
 
+#define ERS_OPT_SHARP 2   /* ers_params.options: targets ON the surface (b = 0, see ers_closest_point) use
+                             the modified smoothing functions s#_p of Sec. 2.1 with one delta# =
+                             rho_sharp h and no extrapolation (single layer: Eq. (Sreg) with s#_1, s#_2;
+                             double layer: the stresslet -6 d d d s#_3/r^5), localized at
+                             cutoff_t delta#; targets off the surface are unchanged */
+
 #define ERS_PREC_FP64 0   /* every step in FP64 arithmetic */
 #define ERS_PREC_MIXED 1  /* far field with FP32 operands and FP64 accumulation per source tile;
                              local sums, closest point and 3x3 solve in FP64 */
@@ -71,6 +77,7 @@ typedef struct {
     int precision;    /* ERS_PREC_FP64 or ERS_PREC_MIXED */
     int layers;       /* bitmask of ERS_LAYER_SL, ERS_LAYER_DL */
     int options;      /* bitmask of ERS_OPT_*; 0 for the defaults */
+    double rho_sharp; /* ERS_OPT_SHARP: delta# = rho_sharp h (> 0), or 0 for rho[1] */
 } ers_params;
 
 /*
@@ -209,7 +216,7 @@ typedef struct ers_batch ers_batch; /* opaque plan: work list, device copies, CU
  * the pointers of every problem: change the data behind them (new densities through
  * ers_set_density_multi with the same nrhs, new f0, q0) and relaunch, but do not free or move
  * them while the plan exists.  Errors: ERS_E_INVAL, ERS_E_STATE (densities not set with this
- * nrhs), ERS_E_UNSUPPORTED (precision), ERS_E_NOMEM, ERS_E_CUDA.
+ * nrhs), ERS_E_UNSUPPORTED (precision, ERS_OPT_SHARP), ERS_E_NOMEM, ERS_E_CUDA.
  */
 int ers_batch_create(const ers_problem *probs, int nprob, const ers_params *p, int nrhs, ers_batch **out);
 
@@ -318,7 +325,8 @@ int ers_eval_learned(ers_surface *s, ers_closure *c, const ers_params *p, const 
  *    target) live in a fixed 24 MiB device array inside the library, and larger M is rejected
  *    with ERS_E_INVAL and a message naming the limit (split the targets across calls);
  *  - ers_last_counts is not updated;
- *  - the far and near fields run one after the other on `stream` (ERS_OPT_CONCURRENT is ignored).
+ *  - the far and near fields run one after the other on `stream` (ERS_OPT_CONCURRENT is ignored);
+ *  - ERS_OPT_SHARP is rejected with ERS_E_UNSUPPORTED.
  * The call performs no cudaMalloc, cudaFree or other allocating call.  The fixed array (24 MiB
  * of scratch plus the 55 KB smoothing-function table) is part of the library's device image:
  * every GPU on which this entry point is used holds it until the process exits.  The first call

@@ -33,6 +33,7 @@ LAYER_DL = 2
 PREC_FP64 = 0
 PREC_MIXED = 1
 OPT_CONCURRENT = 1
+OPT_SHARP = 2
 
 # Every symbol the header declares (checked by the tests).
 EXPORTS = ["ers_build_surface", "ers_surface_free", "ers_surface_info", "ers_set_density", "ers_closest_point",
@@ -63,7 +64,7 @@ class _Problem(ctypes.Structure):
 
 class _Params(ctypes.Structure):
     _fields_ = [("rho", ctypes.c_double * 3), ("cutoff_t", ctypes.c_double), ("precision", ctypes.c_int),
-                ("layers", ctypes.c_int), ("options", ctypes.c_int)]
+                ("layers", ctypes.c_int), ("options", ctypes.c_int), ("rho_sharp", ctypes.c_double)]
 
 
 _lib = None
@@ -164,14 +165,15 @@ class _DevView:
 
 
 def params(rho=(2.0, 3.0, 4.0), cutoff_t=6.0, precision=PREC_FP64, layers=LAYER_SL | LAYER_DL,
-           concurrent: bool = False) -> _Params:
+           concurrent: bool = False, sharp: bool = False, rho_sharp: float = 0.0) -> _Params:
     p = _Params()
     for k in range(3):
         p.rho[k] = float(rho[k])
     p.cutoff_t = float(cutoff_t)
     p.precision = int(precision)
     p.layers = int(layers)
-    p.options = OPT_CONCURRENT if concurrent else 0
+    p.options = (OPT_CONCURRENT if concurrent else 0) | (OPT_SHARP if sharp else 0)
+    p.rho_sharp = float(rho_sharp)
     return p
 
 
@@ -227,9 +229,9 @@ class Surface:
 
     def eval(self, y, f0=None, q0=None, rho=(2.0, 3.0, 4.0), cutoff_t=6.0, precision=PREC_FP64,
              layers=LAYER_SL | LAYER_DL, x0=None, n0=None, b=None, u=None, v=None, stream=None,
-             concurrent: bool = False):
+             concurrent: bool = False, sharp: bool = False, rho_sharp: float = 0.0):
         """ers_eval: returns (u, v) (None for a layer not selected).  concurrent=True sets
-        ERS_OPT_CONCURRENT."""
+        ERS_OPT_CONCURRENT; sharp=True sets ERS_OPT_SHARP with delta# = rho_sharp h (0: rho[1])."""
         import torch
         M = y.shape[0]
         sl, dl = bool(layers & LAYER_SL), bool(layers & LAYER_DL)
@@ -237,7 +239,7 @@ class Surface:
             u = torch.empty((M, 3), dtype=torch.float64, device=y.device)
         if dl and v is None:
             v = torch.empty((M, 3), dtype=torch.float64, device=y.device)
-        p = params(rho, cutoff_t, precision, layers, concurrent)
+        p = params(rho, cutoff_t, precision, layers, concurrent, sharp, rho_sharp)
         self.last_rc = check(lib().ers_eval(self._h, ctypes.byref(p), _ptr(y), M, _ptr(x0), _ptr(n0), _ptr(b),
                                             _ptr(f0) if sl else None, _ptr(q0) if dl else None,
                                             _ptr(u) if sl else None, _ptr(v) if dl else None, _stream(stream)))
@@ -250,11 +252,11 @@ class Surface:
         self.nrhs_multi = nrhs
 
     def eval_noalloc(self, y, x0, n0, b, f0=None, q0=None, u=None, v=None, rho=(2.0, 3.0, 4.0), cutoff_t=6.0,
-                     precision=PREC_FP64, layers=LAYER_SL | LAYER_DL, stream=None):
+                     precision=PREC_FP64, layers=LAYER_SL | LAYER_DL, stream=None, sharp: bool = False):
         """ers_eval_noalloc: the library allocates nothing; the caller passes every array, including
         the closest-point data (from closest_point) and the outputs u, v."""
         sl, dl = bool(layers & LAYER_SL), bool(layers & LAYER_DL)
-        p = params(rho, cutoff_t, precision, layers)
+        p = params(rho, cutoff_t, precision, layers, sharp=sharp)
         self.last_rc = check(lib().ers_eval_noalloc(self._h, ctypes.byref(p), _ptr(y), y.shape[0], _ptr(x0), _ptr(n0),
                                                     _ptr(b), _ptr(f0) if sl else None, _ptr(q0) if dl else None,
                                                     _ptr(u) if sl else None, _ptr(v) if dl else None,
@@ -300,14 +302,19 @@ class Surface:
     def last_defect_class_counts(self):
         """Near pairs of the most recent eval by the number of deltas whose defects 1 - s_p are
         evaluated directly instead of from the table (0..3)."""
-        return self._class_counts()[3:]
+        return self._class_counts()[3:7]
+
+    def last_sharp_pairs(self):
+        """Near pairs of on-surface targets evaluated with the s#_p (ERS_OPT_SHARP) in the most
+        recent eval."""
+        return self._class_counts()[7]
 
     def _class_counts(self):
         self.last_counts()
-        c = (ctypes.c_int64 * 7)()
+        c = (ctypes.c_int64 * 8)()
         L = lib()
         L.ers_debug_class_counts.argtypes = [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int64), ctypes.c_int]
-        check(L.ers_debug_class_counts(self._h, c, 7))
+        check(L.ers_debug_class_counts(self._h, c, 8))
         return [int(z) for z in c]
 
 

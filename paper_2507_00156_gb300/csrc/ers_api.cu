@@ -60,6 +60,7 @@ void free_surface(ers_surface *s) {
 
 std::mutex g_tab_mu;
 const double *g_tab_dev[64] = {nullptr};
+const double *g_tabs_dev[64] = {nullptr};  // sigma# (on-surface) table per device
 }  // namespace
 
 int fail(int code, const std::string &msg) {
@@ -95,6 +96,31 @@ const double *sigma_table_dev(int *err) {
     }
     *err = ERS_OK;
     return g_tab_dev[dev];
+}
+
+const double *sigma_sharp_table_dev(int *err) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess || dev < 0 || dev >= 64) {
+        *err = cuda_fail(e == cudaSuccess ? cudaErrorInvalidDevice : e, "cudaGetDevice");
+        return nullptr;
+    }
+    std::lock_guard<std::mutex> lk(g_tab_mu);
+    if (!g_tabs_dev[dev]) {
+        std::vector<double> host(SH_DEV_BYTES / sizeof(double));
+        sigma_sharp_table_device_layout(host.data());
+        double *d = nullptr;
+        e = cudaMalloc(&d, SH_DEV_BYTES);
+        if (e == cudaSuccess) e = cudaMemcpy(d, host.data(), SH_DEV_BYTES, cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) {
+            if (d) cudaFree(d);
+            *err = cuda_fail(e, "uploading the on-surface smoothing-function table");
+            return nullptr;
+        }
+        g_tabs_dev[dev] = d;
+    }
+    *err = ERS_OK;
+    return g_tabs_dev[dev];
 }
 
 int build_surface(const ers_shape *shape, double h, ers_surface **out) {
@@ -241,18 +267,20 @@ int check_params(const ers_surface *s, const ers_params *p, int *warn) {
     if (p->precision != ERS_PREC_FP64 && p->precision != ERS_PREC_MIXED)
         return fail(ERS_E_INVAL, "precision must be ERS_PREC_FP64 or ERS_PREC_MIXED");
     if (p->layers < 1 || p->layers > 3) return fail(ERS_E_INVAL, "layers must be a non-empty mask of SL/DL");
+    if (p->options & ~(ERS_OPT_CONCURRENT | ERS_OPT_SHARP)) return fail(ERS_E_INVAL, "unknown bit in options");
+    if (!(p->rho_sharp >= 0.0) || !std::isfinite(p->rho_sharp)) return fail(ERS_E_INVAL, "rho_sharp must be finite and >= 0");
     if (p->cutoff_t < 6.0) *warn = ERS_W_CUTOFF;
     (void)s;
     return ERS_OK;
 }
 
-// ndelta = 3: the method (Eq. (extrap_eqn)); ndelta = 2: the two-delta sums of the learned closure,
-// near radius cutoff_t * delta_1, per-target gamma written to `gamma` (may be NULL); ndelta = 1:
-// the single regularized sum with delta_0, near radius cutoff_t * delta_0.
 // CTAs per SM of the far (mixed) and near kernels: [0], [1] when they run concurrently,
 // [2], [3] when serial (0 = uncapped).  Changed only by the tuning hook below.
 int g_caps[4] = {1, 1, 0, 0};
 
+// ndelta = 3: the method (Eq. (extrap_eqn)); ndelta = 2: the two-delta sums of the learned closure,
+// near radius cutoff_t * delta_1, per-target gamma written to `gamma` (may be NULL); ndelta = 1:
+// the single regularized sum with delta_0, near radius cutoff_t * delta_0.
 int eval_impl(ers_surface *s, const ers_params *p, const double *y, int64_t M, const double *x0, const double *n0,
               const double *b, const double *f0, const double *q0, double *u, double *v, void *stream, int ndelta,
               double *gamma) {
@@ -294,6 +322,14 @@ int eval_impl(ers_surface *s, const ers_params *p, const double *y, int64_t M, c
     a.Rc = p->cutoff_t * p->rho[ndelta - 1] * s->h;
     a.ndelta = ndelta;
     a.gamma = gamma;
+    if ((p->options & ERS_OPT_SHARP) && ndelta == 3) {  // on-surface targets: s#_p of Sec. 2.1
+        a.sharp = true;
+        a.rho_sharp = p->rho_sharp > 0.0 ? p->rho_sharp : p->rho[1];
+        a.dsharp = a.rho_sharp * s->h;
+        a.Rc_sharp = p->cutoff_t * a.dsharp;
+        a.tab_sharp = sigma_sharp_table_dev(&err);
+        if (!a.tab_sharp) return err;
+    }
     a.precision = p->precision;
     a.layers = p->layers;
     a.stream = st;
@@ -523,6 +559,7 @@ int ers_last_counts(ers_surface *s, int64_t *near_targets, int64_t *near_pairs, 
         s->last_counts[2] -= (int64_t)hc[1];
         for (int c = 0; c < 4; ++c) s->last_dclass[c] = (int64_t)hc[2 + c];
         for (int c = 0; c < 3; ++c) s->last_class[c] = (int64_t)hc[6 + c];
+        s->last_sharp = (int64_t)hc[9];
     }
     if (near_targets) *near_targets = s->last_counts[0];
     if (near_pairs) *near_pairs = s->last_counts[1];
@@ -545,11 +582,13 @@ extern "C" int ers_debug_set_caps(int far_c, int near_c, int far_s, int near_s) 
 
 // Test/benchmark hook (not in the public header): near pairs of the last ers_eval, valid after
 // ers_last_counts.  out[0..2]: by the number of deltas with r > cutoff_t delta_k (0, 1, 2);
-// out[3..6]: by the number of deltas on the direct-defect path (0..3).  n >= 7.
+// out[3..6]: by the number of deltas on the direct-defect path (0..3); out[7]: near pairs of
+// on-surface targets evaluated with the s#_p (ERS_OPT_SHARP; not in out[0..6]).  n >= 8.
 extern "C" int ers_debug_class_counts(ers_surface *s, int64_t *out, int n) {
-    if (!s || !out || n < 7) return ERS_E_INVAL;
+    if (!s || !out || n < 8) return ERS_E_INVAL;
     for (int c = 0; c < 3; ++c) out[c] = s->last_class[c];
     for (int c = 0; c < 4; ++c) out[3 + c] = s->last_dclass[c];
+    out[7] = s->last_sharp;
     return ERS_OK;
 }
 

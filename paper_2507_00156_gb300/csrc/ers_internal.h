@@ -21,7 +21,7 @@ namespace ers {
 // w f and w n feed the single layer (g w = w f - (f(x0).n0) w n, Eq. (Stokes_SL1)); q and w n
 // feed the double layer (Q = q - q(x0), m = w n, Eq. (Stokes_DL1)).
 constexpr int REC = 12;
-constexpr int NCOUNTERS = 9;  // near-field counters of one evaluation (EvalArgs::counters)
+constexpr int NCOUNTERS = 10;  // near-field counters of one evaluation (EvalArgs::counters)
 constexpr int R_X = 0, R_WF = 3, R_WN = 6, R_Q = 9;
 
 // FP32 record for the mixed-precision far field (48 B): x - c_tile, w f, w n, q.
@@ -42,6 +42,14 @@ constexpr int TAB_NC = TAB_DEG + 1;
 constexpr double TAB_TAU_MAX = 24.0;
 constexpr int TAB_DEV_DOUBLES = TAB_N * 3 * 4;
 constexpr size_t TAB_DEV_BYTES = (size_t)TAB_DEV_DOUBLES * 8 + (size_t)TAB_N * 3 * 16;
+// Table of sigma#_p(tau) = s#_p(t)/t^p for the on-surface functions of Sec. 2.1, the same layout
+// with intervals of width 1/32 on tau in [0, 64) (cutoff_t up to 8; no direct-defect path): their
+// polynomial-times-Gaussian parts vary faster than sigma_p, and at width 1/32 degrees 4..6 still
+// carry less than 2e-8 of the value.
+constexpr int SH_INV_W = 32;
+constexpr int SH_N = 2048;
+constexpr int SH_DEV_DOUBLES = SH_N * 3 * 4;
+constexpr size_t SH_DEV_BYTES = (size_t)SH_DEV_DOUBLES * 8 + (size_t)SH_N * 3 * 16;
 
 struct Grid {
     double origin[3];
@@ -84,6 +92,7 @@ struct ers_surface {
     int64_t last_counts[3] = {0, 0, 0};
     int64_t last_class[3] = {0, 0, 0};   // near pairs by number of deltas with r > cutoff_t delta
     int64_t last_dclass[4] = {0, 0, 0, 0};  // near pairs by number of deltas on the direct-defect path
+    int64_t last_sharp = 0;                 // near pairs of on-surface targets (ERS_OPT_SHARP)
     cudaStream_t last_stream = nullptr;
     // optional per-kernel timing
     bool profile = false;
@@ -103,6 +112,8 @@ int64_t quadrature(const double c[3], const double a[3], double h, std::vector<d
                    std::vector<double> *w);
 const double *sigma_table_host();  // TAB_N * 3 * TAB_NC doubles
 void sigma_table_device_layout(void *dst);  // TAB_DEV_BYTES bytes, the device copy
+const double *sigma_sharp_table_host();  // SH_N * 3 * TAB_NC doubles
+void sigma_sharp_table_device_layout(void *dst);  // SH_DEV_BYTES bytes
 
 // Error reporting (thread-local message)
 int fail(int code, const std::string &msg);
@@ -115,6 +126,7 @@ int check_params(const ers_surface *s, const ers_params *p, int *warn);
 
 // Device table pointer for the current device (uploads once per device).
 const double *sigma_table_dev(int *err);
+const double *sigma_sharp_table_dev(int *err);  // the on-surface (s#) table
 
 // Device-side view of a surface, passed by value in kernel parameters (the ers_surface
 // struct itself lives in host memory).
@@ -152,13 +164,18 @@ struct EvalArgs {
     int precision, layers;
     int ndelta;      // 3: extrapolation of Eq. (extrap_eqn); 2: two-delta weights (learned closure)
     bool far_later;  // the near-field kernel leaves the far partial sums to k_combine
+    // ERS_OPT_SHARP: targets with b == 0 use the s#_p of Sec. 2.1 with delta# = dsharp, near
+    // radius Rc_sharp = cutoff_t delta#, table tab_sharp (far kernels: per-target radius)
+    bool sharp;
+    double rho_sharp, dsharp, Rc_sharp;  // rho#, delta# = rho# h, cutoff_t delta#
+    const double *tab_sharp;
     double *gamma;   // ndelta == 2: per-target gamma (may be NULL)
     double *u, *v;
     double *part;    // [chunks][M][6]
     int chunks;
     int64_t chunk_len;
     // [near_targets, near_pairs, near pairs of class 0..3 (deltas on the defect path),
-    //  near pairs with 0, 1, 2 deltas beyond cutoff_t]
+    //  near pairs with 0, 1, 2 deltas beyond cutoff_t, near pairs of on-surface (s#) targets]
     unsigned long long *counters;
     cudaStream_t stream;
 };

@@ -127,17 +127,48 @@ void sigma_ld(long double tau, long double out[3]) {
     out[2] = (e - c * (t + 2.0L / 3.0L * t * tau) * g) / (t * tau * tau);
 }
 
-std::vector<double> build_table() {
-    std::vector<double> tab((size_t)TAB_N * 3 * TAB_NC);
+// sigma#_p(tau) = s#_p(t) / t^p for the modified smoothing functions of Sec. 2.1:
+//   s#_1 = erf t + c/3 (5t - 2t^3) e^{-t^2},  s#_2 = erf t - c/3 (3t - 14t^3 + 4t^5) e^{-t^2},
+//   s#_3 = erf t - c/9 (9t + 6t^3 - 4t^5) e^{-t^2},  c = 2/sqrt(pi).
+// For t < 1 the series in tau: collecting the t^(2n+1) terms of erf t and of P(t) e^{-t^2},
+//   s#_1/t   = c sum_{n>=0} (-tau)^n [1/(2n+1) + (5 + 2n)/3] / n!
+//   s#_2/t^3 = c sum_{n>=1} (-1)^n tau^(n-1) [1/(2n+1) - (4n^2 + 10n + 3)/3] / n!
+//   s#_3/t^5 = c sum_{n>=2} (-1)^n tau^(n-2) [1/(2n+1) - (9 - 2n - 4n^2)/9] / n!
+void sigma_sharp_ld(long double tau, long double out[3]) {
+    const long double c = 2.0L / std::sqrt((long double)M_PI);
+    const long double t = std::sqrt(tau);
+    if (t < 1.0L) {
+        long double a1 = 0, a2 = 0, a3 = 0, fact = 1.0L;
+        for (int n = 0; n < 50; ++n) {
+            if (n > 0) fact *= n;
+            const long double sg = (n % 2 == 0) ? 1.0L : -1.0L;
+            const long double e = 1.0L / (2 * n + 1);
+            a1 += sg * std::pow(tau, (long double)n) * (e + (5.0L + 2 * n) / 3.0L) / fact;
+            if (n >= 1) a2 += sg * std::pow(tau, (long double)(n - 1)) * (e - (4.0L * n * n + 10.0L * n + 3.0L) / 3.0L) / fact;
+            if (n >= 2) a3 += sg * std::pow(tau, (long double)(n - 2)) * (e - (9.0L - 2.0L * n - 4.0L * n * n) / 9.0L) / fact;
+        }
+        out[0] = c * a1;
+        out[1] = c * a2;
+        out[2] = c * a3;
+        return;
+    }
+    const long double e = std::erf(t), g = std::exp(-tau);
+    out[0] = (e + c / 3.0L * (5.0L * t - 2.0L * t * tau) * g) / t;
+    out[1] = (e - c / 3.0L * (3.0L * t - 14.0L * t * tau + 4.0L * t * tau * tau) * g) / (t * tau);
+    out[2] = (e - c / 9.0L * (9.0L * t + 6.0L * t * tau - 4.0L * t * tau * tau) * g) / (t * tau * tau);
+}
+
+std::vector<double> build_table(int nint, int inv_w, void (*fn)(long double, long double[3])) {
+    std::vector<double> tab((size_t)nint * 3 * TAB_NC);
     const int D = TAB_DEG;
     long double sk[TAB_NC];
     for (int k = 0; k <= D; ++k) sk[k] = std::cos((2.0L * k + 1.0L) * (long double)M_PI / (2.0L * (D + 1)));
-    for (int i = 0; i < TAB_N; ++i) {
+    for (int i = 0; i < nint; ++i) {
         long double f[3][TAB_NC];
         for (int k = 0; k <= D; ++k) {
-            long double tau = ((long double)sk[k] + 2.0L * i + 1.0L) / (2.0L * TAB_INV_W);
+            long double tau = ((long double)sk[k] + 2.0L * i + 1.0L) / (2.0L * inv_w);
             long double o[3];
-            sigma_ld(tau, o);
+            fn(tau, o);
             for (int p = 0; p < 3; ++p) f[p][k] = o[p];
         }
         for (int p = 0; p < 3; ++p) {
@@ -170,15 +201,22 @@ std::vector<double> build_table() {
 }  // namespace
 
 const double *sigma_table_host() {
-    static std::vector<double> tab = build_table();
+    static std::vector<double> tab = build_table(TAB_N, TAB_INV_W, sigma_ld);
     return tab.data();
 }
 
-void sigma_table_device_layout(void *dst) {
-    const double *h = sigma_table_host();
+const double *sigma_sharp_table_host() {
+    static std::vector<double> tab = build_table(SH_N, SH_INV_W, sigma_sharp_ld);
+    return tab.data();
+}
+
+namespace {
+// Device copy: nint x [p][4] doubles (degrees 3..0), then nint x [p] float4 (degrees 6, 5, 4
+// and the interval offset 2 i + 1).
+void device_layout(const double *h, int nint, void *dst) {
     double *d = static_cast<double *>(dst);
-    float *f = reinterpret_cast<float *>(d + TAB_DEV_DOUBLES);
-    for (int i = 0; i < TAB_N; ++i)
+    float *f = reinterpret_cast<float *>(d + (size_t)nint * 12);
+    for (int i = 0; i < nint; ++i)
         for (int p = 0; p < 3; ++p) {
             const double *c = h + ((size_t)i * 3 + p) * TAB_NC;  // degrees 6..0
             for (int e = 0; e < 4; ++e) d[((size_t)i * 3 + p) * 4 + e] = c[3 + e];
@@ -189,6 +227,10 @@ void sigma_table_device_layout(void *dst) {
             q[3] = (float)(2 * i + 1);
         }
 }
+}  // namespace
+
+void sigma_table_device_layout(void *dst) { device_layout(sigma_table_host(), TAB_N, dst); }
+void sigma_sharp_table_device_layout(void *dst) { device_layout(sigma_sharp_table_host(), SH_N, dst); }
 
 }  // namespace ers
 
@@ -204,6 +246,14 @@ extern "C" int ers_debug_sigma_table(double *out, int64_t count) {
 extern "C" int ers_debug_sigma_device(void *out, int64_t bytes) {
     if (!out || bytes < (int64_t)ers::TAB_DEV_BYTES) return ERS_E_INVAL;
     ers::sigma_table_device_layout(out);
+    return ERS_OK;
+}
+
+// Test hook (not in the public header): the device layout of the on-surface table
+// (SH_DEV_BYTES bytes).
+extern "C" int ers_debug_sigma_sharp_device(void *out, int64_t bytes) {
+    if (!out || bytes < (int64_t)ers::SH_DEV_BYTES) return ERS_E_INVAL;
+    ers::sigma_sharp_table_device_layout(out);
     return ERS_OK;
 }
 

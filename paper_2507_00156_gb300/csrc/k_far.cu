@@ -28,6 +28,7 @@ constexpr double INV8PI = 0.039788735772973833942;  // 1/(8 pi)
 struct TargetF64 {
     double y[3], c, q0[3];
     long long rc2bits;  // pair is far iff bits(r^2) > rc2bits (signed compare; -1 = all far)
+    float rc2f;         // the near radius squared in FP32 (mixed far field)
 };
 
 __device__ __forceinline__ void load_target(const EvalArgs &A, int64_t m, bool sl, bool dl, TargetF64 &T,
@@ -38,12 +39,16 @@ __device__ __forceinline__ void load_target(const EvalArgs &A, int64_t m, bool s
         T.c = 0.0;
         T.q0[0] = T.q0[1] = T.q0[2] = 0.0;
         T.rc2bits = 0x7fffffffffffffffLL;  // nothing is far
+        T.rc2f = 0.0f;
         return;
     }
     for (int i = 0; i < 3; ++i) T.y[i] = A.y[3 * m + i];
     const double bm = A.b[m];
-    const bool near = fabs(bm) <= A.Rc;
-    T.rc2bits = near ? __double_as_longlong(A.Rc * A.Rc) : -1LL;
+    // near radius of this target: cutoff_t delta_3, or cutoff_t delta# on the surface (ERS_OPT_SHARP)
+    const double Rt = (A.sharp && bm == 0.0) ? A.Rc_sharp : A.Rc;
+    const bool near = fabs(bm) <= Rt;
+    T.rc2bits = near ? __double_as_longlong(Rt * Rt) : -1LL;
+    T.rc2f = (float)(Rt * Rt);  // same rounding as the near-field copy
     T.c = 0.0;
     T.q0[0] = T.q0[1] = T.q0[2] = 0.0;
     if (near) {
@@ -140,7 +145,7 @@ struct TargetF32 {
 // operations in the same order as the scalar form: d = yc - x, r^2 = fma(dz,dz,fma(dy,dy,dx dx)),
 // 1/r by MUFU (masked to 0 where r^2 <= Rc^2), then the SL and DL terms.
 template <bool SL, bool DL, int NPK, int FLUSH>
-__device__ __forceinline__ void far32_item(const EvalArgs &A, float rc2f, int64_t tbi, int64_t chunk,
+__device__ __forceinline__ void far32_item(const EvalArgs &A, int64_t tbi, int64_t chunk,
                                            float4 *srec, float4 &scen) {
     constexpr int TPT = 2 * NPK;
     const int64_t j0 = chunk * A.chunk_len;  // multiple of TS32
@@ -168,7 +173,7 @@ __device__ __forceinline__ void far32_item(const EvalArgs &A, float rc2f, int64_
             }
             c[h] = __double2float_rn(D.c);
             // far iff r2 > rc2: +inf = nothing far (invalid target), -1 = everything far
-            rc2[t] = !valid[t] ? __int_as_float(0x7f800000) : (D.rc2bits < 0 ? -1.0f : rc2f);
+            rc2[t] = !valid[t] ? __int_as_float(0x7f800000) : (D.rc2bits < 0 ? -1.0f : D.rc2f);
 #pragma unroll
             for (int i = 0; i < 6; ++i) acc[t][i] = 0.0;
         }
@@ -271,14 +276,14 @@ __device__ __forceinline__ void far32_item(const EvalArgs &A, float rc2f, int64_
 }
 
 template <bool SL, bool DL, int NPK, int FLUSH>
-__global__ void __launch_bounds__(NT, 3) k_far32(EvalArgs A, float rc2f, int64_t ntb) {
+__global__ void __launch_bounds__(NT, 3) k_far32(EvalArgs A, int64_t ntb) {
     __shared__ float4 srec[TS32 * 3];
     __shared__ float4 scen;
     const int64_t nitems = ntb * A.chunks;
     for (int64_t item = blockIdx.x; item < nitems; item += gridDim.x) {
         const int64_t tbi = item % ntb, chunk = item / ntb;
         __syncthreads();  // the previous item's last tile is no longer read
-        far32_item<SL, DL, NPK, FLUSH>(A, rc2f, tbi, chunk, srec, scen);
+        far32_item<SL, DL, NPK, FLUSH>(A, tbi, chunk, srec, scen);
     }
 }
 
@@ -309,14 +314,13 @@ cudaError_t far32_dispatch(const EvalArgs &a, int ctas_per_sm, int nsm) {
         grid = std::min<int64_t>(nitems, (int64_t)ctas_per_sm * nsm);
     }
     const bool sl = a.layers & ERS_LAYER_SL, dl = a.layers & ERS_LAYER_DL;
-    const float rc2f = (float)(a.Rc * a.Rc);  // same rounding as the near-field copy
     auto kern = (sl && dl) ? k_far32<true, true, NPK, 2> : (sl ? k_far32<true, false, NPK, 2> : k_far32<false, true, NPK, 2>);
     if (pad > 0) {
         // static + dynamic shared memory above 48 KB needs the opt-in (not a stream operation)
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pad);
         if (e != cudaSuccess) return e;
     }
-    kern<<<(unsigned)grid, NT, pad, a.stream>>>(a, rc2f, tb);
+    kern<<<(unsigned)grid, NT, pad, a.stream>>>(a, tb);
     return cudaGetLastError();
 }
 

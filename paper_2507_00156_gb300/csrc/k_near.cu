@@ -20,6 +20,7 @@
 // one code path.  Each batch then makes the exact FP64 (or, for the mixed far field, the
 // identical FP32) near/far test, so that the partition matches the far-field mask exactly.
 #include <algorithm>
+#include <cmath>
 
 #include "near_common.cuh"
 
@@ -75,14 +76,101 @@ __device__ __forceinline__ void process(const EvalArgs &A, const Geom &T, const 
     }
 }
 
+// On-surface target with ERS_OPT_SHARP (b = 0): one regularized sum with the modified
+// smoothing functions s#_p of Sec. 2.1 at delta# (alpha = 1, no extrapolation) over r <= Rc#.
+// Single layer: Eq. (Sreg) with s#_1, s#_2; double layer: the stresslet -6 d (d.Q)(d.m) s#_3/r^5
+// (at b = 0 the split form would add t1 (s#_2 - s#_3)/r^3, which is not small for s#).
+template <int PREC, bool SL, bool DL>
+__device__ __forceinline__ void process_sharp(const EvalArgs &A, const Geom &T, const ScanParams &Ps, double c,
+                                              const double q0[3], int64_t j, double accU[3], double accV[3],
+                                              int &npairs) {
+    const double2 *r = reinterpret_cast<const double2 *>(A.sd.rec + j * REC);
+    const double2 r0 = __ldg(r + 0), r1 = __ldg(r + 1), r2v = __ldg(r + 2);
+    const double2 r3 = __ldg(r + 3), r4 = __ldg(r + 4), r5 = __ldg(r + 5);
+    const double xs[3] = {r0.x, r0.y, r1.x};
+    const double wf[3] = {r1.y, r2v.x, r2v.y};
+    const double wn[3] = {r3.x, r3.y, r4.x};
+    const double qs[3] = {r4.y, r5.x, r5.y};
+    const double dx = __dsub_rn(T.y[0], xs[0]);
+    const double dy = __dsub_rn(T.y[1], xs[1]);
+    const double dz = __dsub_rn(T.y[2], xs[2]);
+    const double r2 = dist2_fp64(dx, dy, dz);
+    if (!is_near<PREC>(A.sd, T, j, r2, A.Rc_sharp, Ps.rc2f)) return;
+    ++npairs;
+    double s1, s2, s3;  // t = r/delta# <= cutoff_t here
+    table_sigma<SH_INV_W, SH_N>(A.tab_sharp, r2 * T.invd2[0], s1, s2, s3);
+    const double K1 = T.ad1[0] * s1, K3 = T.ad3[0] * s2, K5 = T.ad5[0] * s3;
+    if (SL) sl_accumulate(dx, dy, dz, K1, K3, c, wf, wn, accU);
+    if (DL) {
+        const double Q0 = qs[0] - q0[0], Q1 = qs[1] - q0[1], Q2 = qs[2] - q0[2];
+        const double dQ = fma(dz, Q2, fma(dy, Q1, dx * Q0));
+        const double W = fma(dz, wn[2], fma(dy, wn[1], dx * wn[0]));
+        const double sv = dQ * W * K5;
+        accV[0] = fma(sv, dx, accV[0]);
+        accV[1] = fma(sv, dy, accV[1]);
+        accV[2] = fma(sv, dz, accV[2]);
+    }
+}
+
+template <int PREC, bool SL, bool DL>
+__device__ __noinline__ void near_target_sharp(const EvalArgs &A, const ScanParams &Ps, int64_t m, int lane,
+                                               int (*sq)[64], Geom &G, double fs) {
+    {
+        Geom Tl;
+        const double rs[3] = {A.rho_sharp, A.rho_sharp, A.rho_sharp};
+        load_geom(lane, A.y, A.x0, A.n0, 0.0, m, rs, Ps.h, Tl, 1, nullptr);  // alpha = (1, 0, 0)
+        set_cutoff(Tl, Ps);
+        __syncwarp();
+        if (lane == 0) G = Tl;
+        __syncwarp();
+    }
+    const Geom &T = G;
+    double q0[3];
+    for (int i = 0; i < 3; ++i) q0[i] = DL ? A.q0[3 * m + i] : 0.0;
+    const double c = SL ? fma(A.f0[3 * m + 2], T.n0[2], fma(A.f0[3 * m + 1], T.n0[1], A.f0[3 * m] * T.n0[0])) : 0.0;
+    double accU[3] = {0.0, 0.0, 0.0}, accV[3] = {0.0, 0.0, 0.0};
+    int npairs = 0;
+    scan_near(A.sd, T, Ps, sq, lane, [&](int, int jj, bool valid) {
+        if (valid) process_sharp<PREC, SL, DL>(A, T, Ps, c, q0, jj, accU, accV, npairs);
+    });
+    for (int i = 0; i < 3; ++i) {
+        accU[i] = warp_sum(accU[i]);
+        accV[i] = warp_sum(accV[i]);
+    }
+    if (A.counters) {
+        int np = npairs;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) np += __shfl_xor_sync(FULL, np, o);
+        if (lane == 0) {
+            atomicAdd(A.counters + 0, 1ull);
+            atomicAdd(A.counters + 1, (unsigned long long)np);
+            atomicAdd(A.counters + 9, (unsigned long long)np);
+        }
+    }
+    if (SL && lane < 3) {
+        const double a = lane == 0 ? accU[0] : (lane == 1 ? accU[1] : accU[2]);
+        A.u[3 * m + lane] = fs + a * INV8PI;
+    }
+    if (DL && lane >= 3 && lane < 6) {
+        const int i = lane - 3;
+        const double av = i == 0 ? accV[0] : (i == 1 ? accV[1] : accV[2]);
+        const double qi = i == 0 ? q0[0] : (i == 1 ? q0[1] : q0[2]);
+        A.v[3 * m + i] = fs + (-6.0 * INV8PI) * av + 0.5 * qi;  // chi = 1/2 on the surface
+    }
+}
+
 template <int PREC, bool SL, bool DL, int ND>
 __device__ __forceinline__ void near_target(const EvalArgs &A, const ScanParams &P, const double *__restrict__ tab,
-                                            int64_t m, int lane, int (*sq)[64], Geom &G) {
+                                            int64_t m, int lane, int (*sq)[64], Geom &G, const ScanParams &Ps) {
     // sum of the far-field chunk partials: lane i < 6 holds component i
     double fs = 0.0;
     if (lane < 6 && !A.far_later)
         for (int c = 0; c < A.chunks; ++c) fs += A.part[((int64_t)c * A.M + m) * 6 + lane];
     const double bm = A.b[m];
+    if (ND == 3 && A.sharp && bm == 0.0) {
+        near_target_sharp<PREC, SL, DL>(A, Ps, m, lane, sq, G, fs);
+        return;
+    }
     if (!(fabs(bm) <= A.Rc)) {
         if (A.gamma && lane == 0) A.gamma[m] = 0.0;
         if (SL && lane < 3) A.u[3 * m + lane] = fs;
@@ -150,28 +238,30 @@ __device__ __forceinline__ void near_target(const EvalArgs &A, const ScanParams 
 }
 
 template <int PREC, bool SL, bool DL, int ND>
-__global__ void __launch_bounds__(WPB * 32, NEAR_MIN_BLOCKS) k_near(EvalArgs A, ScanParams P, const double *__restrict__ tab) {
+__global__ void __launch_bounds__(WPB * 32, NEAR_MIN_BLOCKS) k_near(EvalArgs A, ScanParams P, ScanParams Ps,
+                                                                   const double *__restrict__ tab) {
     __shared__ int sq[WPB][NCLS][64];
     __shared__ Geom sG[WPB];
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     // one target per warp; a capped grid strides over the targets
     for (int64_t m = (int64_t)blockIdx.x * WPB + wib; m < A.M; m += (int64_t)gridDim.x * WPB)
-        near_target<PREC, SL, DL, ND>(A, P, tab, m, lane, sq[wib], sG[wib]);
+        near_target<PREC, SL, DL, ND>(A, P, tab, m, lane, sq[wib], sG[wib], Ps);
 }
 
 template <int PREC>
-cudaError_t near_dispatch(const EvalArgs &a, ScanParams P, const double *tab, int ctas_per_sm, int nsm) {
+cudaError_t near_dispatch(const EvalArgs &a, ScanParams P, ScanParams Ps, const double *tab, int ctas_per_sm,
+                          int nsm) {
     int64_t grid = (a.M + WPB - 1) / WPB;
     if (ctas_per_sm > 0) grid = std::min<int64_t>(grid, (int64_t)ctas_per_sm * nsm);
     const unsigned g = (unsigned)grid;
     const bool sl = a.layers & ERS_LAYER_SL, dl = a.layers & ERS_LAYER_DL;
     if (a.ndelta == 1 || a.ndelta == 2) {  // learned closure: both layers
         if (!(sl && dl)) return cudaErrorInvalidValue;
-        if (a.ndelta == 1) k_near<PREC, true, true, 1><<<g, WPB * 32, 0, a.stream>>>(a, P, tab);
-        else k_near<PREC, true, true, 2><<<g, WPB * 32, 0, a.stream>>>(a, P, tab);
-    } else if (sl && dl) k_near<PREC, true, true, 3><<<g, WPB * 32, 0, a.stream>>>(a, P, tab);
-    else if (sl) k_near<PREC, true, false, 3><<<g, WPB * 32, 0, a.stream>>>(a, P, tab);
-    else k_near<PREC, false, true, 3><<<g, WPB * 32, 0, a.stream>>>(a, P, tab);
+        if (a.ndelta == 1) k_near<PREC, true, true, 1><<<g, WPB * 32, 0, a.stream>>>(a, P, Ps, tab);
+        else k_near<PREC, true, true, 2><<<g, WPB * 32, 0, a.stream>>>(a, P, Ps, tab);
+    } else if (sl && dl) k_near<PREC, true, true, 3><<<g, WPB * 32, 0, a.stream>>>(a, P, Ps, tab);
+    else if (sl) k_near<PREC, true, false, 3><<<g, WPB * 32, 0, a.stream>>>(a, P, Ps, tab);
+    else k_near<PREC, false, true, 3><<<g, WPB * 32, 0, a.stream>>>(a, P, Ps, tab);
     return cudaGetLastError();
 }
 
@@ -180,8 +270,14 @@ cudaError_t near_dispatch(const EvalArgs &a, ScanParams P, const double *tab, in
 cudaError_t launch_near(const EvalArgs &a, const double *tab, int ctas_per_sm, int nsm) {
     if (a.M == 0) return cudaSuccess;
     const ScanParams P = scan_params(a.s, a.Rc, a.rho, a.cutoff_t);
-    if (a.precision == ERS_PREC_FP64) return near_dispatch<ERS_PREC_FP64>(a, P, tab, ctas_per_sm, nsm);
-    return near_dispatch<ERS_PREC_MIXED>(a, P, tab, ctas_per_sm, nsm);
+    ScanParams Ps = P;
+    if (a.sharp) {  // on-surface targets: one delta#, every near pair on the table
+        const double rs[3] = {a.rho_sharp, a.rho_sharp, a.rho_sharp};
+        Ps = scan_params(a.s, a.Rc_sharp, rs, a.cutoff_t);
+        for (int k = 0; k < 3; ++k) Ps.th[k] = HUGE_VALF;
+    }
+    if (a.precision == ERS_PREC_FP64) return near_dispatch<ERS_PREC_FP64>(a, P, Ps, tab, ctas_per_sm, nsm);
+    return near_dispatch<ERS_PREC_MIXED>(a, P, Ps, tab, ctas_per_sm, nsm);
 }
 
 }  // namespace ers

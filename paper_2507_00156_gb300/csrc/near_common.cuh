@@ -192,6 +192,28 @@ __device__ __forceinline__ bool is_near(const SurfDev &s, const Geom &T, int64_t
 // r > min(DEFECT_T, cutoff_t) delta_k and take the defect path below; the others take sigma_p
 // from the interpolation table.  ND = number of deltas in use (3 for the method; 2 or 1 for the
 // learned closure).
+// sigma_p(tau) (or sigma#_p with the on-surface table) from a device table of INV_W intervals
+// per unit tau and N intervals: degrees 6..4 of the local polynomial in FP32, 3..0 in FP64 (Horner).
+template <int INV_W, int N>
+__device__ __forceinline__ void table_sigma(const double *__restrict__ tab, double tau, double &s1, double &s2,
+                                            double &s3) {
+    const float4 *__restrict__ ftab = reinterpret_cast<const float4 *>(tab + N * 12);
+    int idx = (int)(approx_float_pos(tau) * (float)INV_W);
+    idx = min(idx, N - 1);
+    const float4 f1 = __ldg(ftab + 3 * idx), f2 = __ldg(ftab + 3 * idx + 1), f3 = __ldg(ftab + 3 * idx + 2);
+    const double s = fma(tau, 2.0 * INV_W, -float_to_double(f1.w));  // local variable in [-1, 1]
+    const float sf = approx_float(s);
+    s1 = float_to_double(fmaf(fmaf(f1.x, sf, f1.y), sf, f1.z));
+    s2 = float_to_double(fmaf(fmaf(f2.x, sf, f2.y), sf, f2.z));
+    s3 = float_to_double(fmaf(fmaf(f3.x, sf, f3.y), sf, f3.z));
+    const double2 *cd = reinterpret_cast<const double2 *>(tab + idx * 12);
+    const double2 a01 = __ldg(cd), a23 = __ldg(cd + 1), b01 = __ldg(cd + 2);
+    const double2 b23 = __ldg(cd + 3), c01 = __ldg(cd + 4), c23 = __ldg(cd + 5);
+    s1 = fma(fma(fma(fma(s1, s, a01.x), s, a01.y), s, a23.x), s, a23.y);
+    s2 = fma(fma(fma(fma(s2, s, b01.x), s, b01.y), s, b23.x), s, b23.y);
+    s3 = fma(fma(fma(fma(s3, s, c01.x), s, c01.y), s, c23.x), s, c23.y);
+}
+
 // Lf: when every delta in use is on the defect path (CLS >= ND), L = r^2 K5 - K3 = (E3 - E5)/r^3
 // in FP32 (see dl_accumulate_defect); 0 otherwise.
 template <int CLS, int ND = 3>
@@ -252,26 +274,11 @@ __device__ __forceinline__ void kernel_factors(const Geom &T, const ScanParams &
         K3 = 0.0;
         K5 = 0.0;
     }
-    const double *__restrict__ ctab = tab;
-    const float4 *__restrict__ ftab = reinterpret_cast<const float4 *>(tab + TAB_DEV_DOUBLES);
 #pragma unroll
     for (int k = CLS; k < ND; ++k) {
         const double tau = r2 * T.invd2[k];
-        int idx = (int)(approx_float_pos(tau) * (float)TAB_INV_W);
-        idx = min(idx, TAB_N - 1);
-        const float4 f1 = __ldg(ftab + 3 * idx), f2 = __ldg(ftab + 3 * idx + 1), f3 = __ldg(ftab + 3 * idx + 2);
-        const double s = fma(tau, 2.0 * TAB_INV_W, -float_to_double(f1.w));  // local variable in [-1, 1]
-        const float sf = approx_float(s);
-        // degrees 6..4 in FP32, 3..0 in FP64 (Horner)
-        double s1 = float_to_double(fmaf(fmaf(f1.x, sf, f1.y), sf, f1.z));
-        double s2 = float_to_double(fmaf(fmaf(f2.x, sf, f2.y), sf, f2.z));
-        double s3 = float_to_double(fmaf(fmaf(f3.x, sf, f3.y), sf, f3.z));
-        const double2 *cd = reinterpret_cast<const double2 *>(ctab + idx * 12);
-        const double2 a01 = __ldg(cd), a23 = __ldg(cd + 1), b01 = __ldg(cd + 2);
-        const double2 b23 = __ldg(cd + 3), c01 = __ldg(cd + 4), c23 = __ldg(cd + 5);
-        s1 = fma(fma(fma(fma(s1, s, a01.x), s, a01.y), s, a23.x), s, a23.y);
-        s2 = fma(fma(fma(fma(s2, s, b01.x), s, b01.y), s, b23.x), s, b23.y);
-        s3 = fma(fma(fma(fma(s3, s, c01.x), s, c01.y), s, c23.x), s, c23.y);
+        double s1, s2, s3;
+        table_sigma<TAB_INV_W, TAB_N>(tab, tau, s1, s2, s3);
         if (T.cut_small && approx_float_pos(tau) >= (1.0f - CUT_BAND) * T.tcf2 && r2 > P.cut2d[k]) {
             // t just beyond a cutoff below DEFECT_T: s_p := 1, sigma_p = 1/t^p (Sec. 3.2)
             s1 = rsqrt(tau);

@@ -26,6 +26,17 @@ def oracle_problem(name):
     return wl, x, n, w, f, q
 
 
+def oracle_eval_sharp(name, sel=None, rho_sharp=3.0, tc=6.0):
+    """The oracle with the on-surface s# path (Sec. 2.1) for targets with b = 0."""
+    wl, x, n, w, f, q = oracle_problem(name)
+    y = oracle_targets(wl, x, sel)
+    x0, n0, b = oracle.closest_point(wl.shape, y)
+    f0 = workloads.poly_eval(wl.f_coef, x0)
+    q0 = workloads.poly_eval(wl.q_coef, x0)
+    u, v, _ = oracle.evaluate_sharp(x, n, w, f, q, y, x0, n0, b, f0, q0, wl.h, wl.rho, tc, rho_sharp)
+    return y, u, v, b
+
+
 def oracle_targets(wl, x, sel=None):
     y = np.concatenate([x, wl.extra_targets]) if wl.nodes_as_targets else wl.extra_targets.copy()
     return y if sel is None else y[sel]
@@ -73,10 +84,11 @@ class GpuProblem:
         q0 = torch.from_numpy(workloads.poly_eval(self.wl.q_coef, x0h)).to(self.dev)
         return yd, x0, n0, b, f0, q0
 
-    def eval(self, y, precision=0, rho=None, tc=6.0, layers=3, given_cp=False):
+    def eval(self, y, precision=0, rho=None, tc=6.0, layers=3, given_cp=False, **opts):
         import torch
         yd, x0, n0, b, f0, q0 = self.prepare(y)
         kw = dict(x0=x0, n0=n0, b=b) if given_cp else {}
-        u, v = self.s.eval(yd, f0, q0, rho=rho or self.wl.rho, cutoff_t=tc, precision=precision, layers=layers, **kw)
+        u, v = self.s.eval(yd, f0, q0, rho=rho or self.wl.rho, cutoff_t=tc, precision=precision, layers=layers,
+                           **kw, **opts)
         torch.cuda.synchronize()
         return (None if u is None else u.cpu().numpy()), (None if v is None else v.cpu().numpy()), b.cpu().numpy()

@@ -144,3 +144,45 @@ def test_sigma_device_layout_accuracy(L):
             worst = max(worst, abs(v - float(ref[p_])) / abs(float(ref[p_])))
             assert abs(c4) <= 2e-8 * abs(dpart[i, p_, 3]), (i, p_)
     assert worst < 6e-15, worst
+
+
+def test_sigma_sharp_device_layout_accuracy(L):
+    """The on-surface table (s#_p(t)/t^p of Sec. 2.1, intervals of 1/32 on tau in [0, 64)), as the
+    kernel evaluates it (degrees 6..4 in FP32, 3..0 in FP64), stays within ~1e-15 of 60-digit values."""
+    mp = pytest.importorskip("mpmath")
+    mp.mp.dps = 60
+    nint, inv_w = 2048, 32
+    nbytes = nint * 3 * 4 * 8 + nint * 3 * 16
+    raw = np.empty(nbytes // 8)
+    L.ers_debug_sigma_sharp_device.argtypes = [ctypes.c_void_p, ctypes.c_int64]
+    assert L.ers_debug_sigma_sharp_device(raw.ctypes.data, nbytes) == 0
+    dpart = raw[: nint * 12].reshape(nint, 3, 4)
+    fpart = raw[nint * 12:].view(np.float32).reshape(nint, 3, 4)
+    f32 = np.float32
+
+    def fmaf(a, b, c):
+        return f32(np.float64(a) * np.float64(b) + np.float64(c))
+
+    rng = np.random.default_rng(2)
+    taus = np.concatenate([[0.0, 1e-10, 0.5, 1.0, 35.99, 36.0, 63.9], rng.uniform(0, 64, 200)])
+    worst = 0.0
+    c = 2 / mp.sqrt(mp.pi)
+    for tau in taus:
+        i = min(int(np.float32(tau) * inv_w), nint - 1)
+        s = 2 * inv_w * tau - float(fpart[i, 0, 3])
+        sf = f32(s)
+        t = mp.sqrt(mp.mpf(tau))
+        if t == 0:
+            ref = [c * mp.mpf(8) / 3, c * mp.mpf(16) / 3, c * mp.mpf(32) / 45]
+        else:
+            e, g = mp.erf(t), mp.exp(-t * t)
+            ref = [(e + c / 3 * (5 * t - 2 * t**3) * g) / t, (e - c / 3 * (3 * t - 14 * t**3 + 4 * t**5) * g) / t**3,
+                   (e - c / 9 * (9 * t + 6 * t**3 - 4 * t**5) * g) / t**5]
+        for p_ in range(3):
+            c6, c5, c4 = fpart[i, p_, :3]
+            v = float(fmaf(fmaf(c6, sf, c5), sf, c4))
+            for cc in dpart[i, p_]:
+                v = v * s + cc
+            worst = max(worst, abs(v - float(ref[p_])) / abs(float(ref[p_])))
+            assert abs(c4) <= 2e-8 * abs(dpart[i, p_, 3]), (i, p_)
+    assert worst < 6e-15, worst

@@ -67,6 +67,12 @@ def _load():
             lib.ora_extrapolate.argtypes = [P, dbl, dbl, P, cint, P]
             lib.ora_eval.restype = i64
             lib.ora_eval.argtypes = [P, P, P, P, P, i64, P, P, P, P, P, P, i64, dbl, P, dbl, cint, P, P]
+            lib.ora_eval_k.restype = i64
+            lib.ora_eval_k.argtypes = [cint, P, P, P, P, P, i64, P, P, P, P, P, P, i64, dbl, P, dbl, cint, P, P]
+            lib.ora_I4.restype = dbl
+            lib.ora_I4.argtypes = [dbl]
+            lib.ora_extrapolate_k.restype = cint
+            lib.ora_extrapolate_k.argtypes = [cint, P, dbl, dbl, P, cint, P]
             lib.ora_eval_one_delta.restype = None
             lib.ora_eval_one_delta.argtypes = [P, P, P, P, P, i64, P, P, P, P, P, P, i64, dbl, dbl, P, P]
             lib.ora_plain.restype = None
@@ -131,24 +137,36 @@ def I2(lam: float) -> float:
     return float(_load().ora_I2(float(lam)))
 
 
+def I4(lam: float) -> float:
+    """The lambda-dependence of the delta^5 error term (four-delta variant; see ers_oracle.c)."""
+    return float(_load().ora_I4(float(lam)))
+
+
 def extrapolate(rho, b: float, h: float, U: np.ndarray):
-    """Solve Eq. (extrap_eqn) for u given U (3, nrhs) = the values for delta_1..3."""
+    """Solve Eq. (extrap_eqn) for u given U (K, nrhs) = the values for delta_1..K (K = 3, or 4 for
+    the O(delta^7) variant with the c3 rho^5 I4 term)."""
     U = _c(U)
-    nrhs = U.shape[1]
+    K, nrhs = U.shape
     out = np.empty(nrhs)
-    rc = _load().ora_extrapolate(_p(_c(rho)), float(b), float(h), _p(U), nrhs, _p(out))
+    if K == 3:
+        rc = _load().ora_extrapolate(_p(_c(rho)), float(b), float(h), _p(U), nrhs, _p(out))
+    else:
+        rc = _load().ora_extrapolate_k(K, _p(_c(rho)), float(b), float(h), _p(U), nrhs, _p(out))
     return out, rc
 
 
 def evaluate(x, n, w, f, q, y, x0, n0, b, f0, q0, h, rho, tc=6.0, mode=LOCALIZED):
-    """SL value u and DL value v (M,3) at targets y; see ers_oracle.c:ora_eval."""
+    """SL value u and DL value v (M,3) at targets y with len(rho) = 3 deltas (Eq. (extrap_eqn)) or
+    4 (the O(delta^7) variant); see ers_oracle.c:ora_eval_k."""
     lib = _load()
     x, n, w, f, q = map(_c, (x, n, w, f, q))
     y, x0, n0, b, f0, q0 = map(_c, (y, x0, n0, b, f0, q0))
     N, M = w.shape[0], b.shape[0]
     u, v = np.empty((M, 3)), np.empty((M, 3))
-    nfail = lib.ora_eval(_p(x), _p(n), _p(w), _p(f), _p(q), N, _p(y), _p(x0), _p(n0), _p(b), _p(f0), _p(q0), M,
-                         float(h), _p(_c(rho)), float(tc), int(mode), _p(u), _p(v))
+    rho = _c(rho)
+    assert len(rho) in (3, 4)
+    nfail = lib.ora_eval_k(len(rho), _p(x), _p(n), _p(w), _p(f), _p(q), N, _p(y), _p(x0), _p(n0), _p(b), _p(f0),
+                           _p(q0), M, float(h), _p(rho), float(tc), int(mode), _p(u), _p(v))
     return u, v, int(nfail)
 
 

@@ -15,7 +15,9 @@
  * surface areas, sphere closed forms, exact extrapolation weights at b = 0, O(h^5) observed
  * convergence, localized == direct; for the on-surface s# functions of Sec. 2.1: 60-digit
  * values, the limits at 0 and infinity, O(h^5) against the sphere closed form and in
- * self-convergence at shared nodes).  Nothing here is "parity unpinned".
+ * self-convergence at shared nodes; for the four-delta variant: I4 against quadrature of its
+ * defining integral, I4' = -4 lambda I2, exact weights at b = 0, faster than O(h^5) against the
+ * sphere closed form).  Nothing here is "parity unpinned".
  */
 #include <math.h>
 #include <stdint.h>
@@ -268,6 +270,67 @@ double ora_I2(double lam) {
 }
 
 /*
+ * I4, the lambda-dependence of the next (delta^5) term of the regularization error, for the
+ * four-delta O(delta^7) variant the paper mentions (no formula is printed).  Reading: I0 and I2 are
+ * I_2k(lambda) = int_{|lambda|}^inf erfc(r) (r^2 - lambda^2)^k dr for k = 0, 1 (the moments of the
+ * regularization error of s1 over a plane at distance lambda, in units of delta; this reproduces
+ * Eqs. (I0), (I2) exactly), so for k = 2, integrating r^n erfc(r) by parts,
+ *   I4(lambda) = (2/15) ((3 - 2 lambda^2 + 4 lambda^4) e^{-lambda^2}/sqrt(pi) - 4 |lambda|^5 erfc|lambda|).
+ */
+double ora_I4(double lam) {
+    double l = fabs(lam), l2 = l * l;
+    return 2.0 / 15.0 * ((3.0 - 2.0 * l2 + 4.0 * l2 * l2) * exp(-l2) / ORA_SQRTPI - 4.0 * l2 * l2 * l * erfc(l));
+}
+
+/*
+ * Solve the K x K system (K = 3: Eq. (extrap_eqn); K = 4: the same with the term c3 rho^5 I4)
+ *   u + c1 rho_k I0(lambda_k) + c2 rho_k^3 I2(lambda_k) [+ c3 rho_k^5 I4(lambda_k)] = U_k,
+ * lambda_k = b / delta_k, for `nrhs` right-hand sides (Gaussian elimination with partial
+ * pivoting).  Returns 0, or -1 when the matrix is singular / not finite (then U_1).
+ */
+int ora_extrapolate_k(int K, const double *rho, double b, double h, const double *U /* [K][nrhs] */, int nrhs,
+                      double *out) {
+    double A[4][4], B[4][8];
+    for (int k = 0; k < K; ++k) {
+        double lam = b / (rho[k] * h), r = rho[k];
+        A[k][0] = 1.0;
+        A[k][1] = r * ora_I0(lam);
+        A[k][2] = r * r * r * ora_I2(lam);
+        if (K == 4) A[k][3] = r * r * r * r * r * ora_I4(lam);
+        for (int q = 0; q < nrhs; ++q) B[k][q] = U[k * nrhs + q];
+    }
+    int ok = 1;
+    for (int col = 0; col < K && ok; ++col) {
+        int piv = col;
+        for (int r = col + 1; r < K; ++r) if (fabs(A[r][col]) > fabs(A[piv][col])) piv = r;
+        if (!(fabs(A[piv][col]) > 0.0) || !isfinite(A[piv][col])) { ok = 0; break; }
+        if (piv != col) {
+            for (int cc = 0; cc < K; ++cc) { double tmp = A[col][cc]; A[col][cc] = A[piv][cc]; A[piv][cc] = tmp; }
+            for (int q = 0; q < nrhs; ++q) { double tmp = B[col][q]; B[col][q] = B[piv][q]; B[piv][q] = tmp; }
+        }
+        for (int r = col + 1; r < K; ++r) {
+            double f = A[r][col] / A[col][col];
+            for (int cc = col; cc < K; ++cc) A[r][cc] -= f * A[col][cc];
+            for (int q = 0; q < nrhs; ++q) B[r][q] -= f * B[col][q];
+        }
+    }
+    if (ok) {
+        for (int q = 0; q < nrhs; ++q) {
+            double x[4];
+            for (int r = K - 1; r >= 0; --r) {
+                double acc = B[r][q];
+                for (int cc = r + 1; cc < K; ++cc) acc -= A[r][cc] * x[cc];
+                x[r] = acc / A[r][r];
+            }
+            if (!isfinite(x[0])) ok = 0;
+            out[q] = x[0];
+        }
+    }
+    if (!ok) { for (int q = 0; q < nrhs; ++q) out[q] = U[q]; return -1; }
+    return 0;
+}
+
+/*
  * Solve the 3x3 system of Eq. (extrap_eqn) for the extrapolated value:
  *   u + c1 rho_k I0(lambda_k) + c2 rho_k^3 I2(lambda_k) = U_k,  k = 1, 2, 3,
  * with lambda_k = b / delta_k, for `nrhs` right-hand sides at once (Gaussian elimination with
@@ -414,22 +477,23 @@ static void ora_dl_plain(const double d[3], double r, const double Q[3], const d
  *   nodes x (N,3), normals n (N,3), weights w (N), densities f, q at the nodes (N,3);
  *   targets y (M,3) with closest point data x0, n0 (M,3), b (M) and the densities at the
  *   closest point f0, q0 (M,3).
- *   params: h, rho[3], tc (regularization cut-off t = r/delta > tc => s_p = 1, Sec. 3.2).
+ *   params: h, rho[K] (K = 3 deltas, or 4 for the O(delta^7) variant), tc (regularization
+ *   cut-off t = r/delta > tc => s_p = 1, Sec. 3.2).
  *   mode 0 = DIRECT: for each delta_k the full sum over every node (Table 1 procedure);
  *   mode 1 = LOCALIZED: u = u_far + u_near_k (Eq. (near_far)); far = nodes with
- *            r > Rc = tc * delta_3, evaluated once without regularization; near = the rest,
+ *            r > Rc = tc * delta_K, evaluated once without regularization; near = the rest,
  *            evaluated for each delta_k (Sec. 3.3).
  * Targets with |b| > Rc have no node within Rc: their value is the plain sum of
  * Eqs. (Stokes_SL), (Stokes_DL) without subtraction.  The others use the subtracted forms
- * (Eqs. (Stokes_SL2), (Stokes_DL2)) for the three delta_k and the solve of Eq. (extrap_eqn).
+ * (Eqs. (Stokes_SL2), (Stokes_DL2)) for the K delta_k and the solve (ora_extrapolate_k).
  * Outputs u, v (M,3).  Returns the number of targets whose solve fell back.
  */
-int64_t ora_eval(const double *x, const double *nrm, const double *w, const double *f, const double *q, int64_t N,
-                 const double *y, const double *x0, const double *n0, const double *b,
-                 const double *f0, const double *q0, int64_t M,
-                 double h, const double rho[3], double tc, int mode, double *u, double *v) {
+int64_t ora_eval_k(int K, const double *x, const double *nrm, const double *w, const double *f, const double *q,
+                   int64_t N, const double *y, const double *x0, const double *n0, const double *b,
+                   const double *f0, const double *q0, int64_t M,
+                   double h, const double *rho, double tc, int mode, double *u, double *v) {
     const double inv8pi = 1.0 / (8.0 * ORA_PI);
-    const double Rc = tc * rho[2] * h;
+    const double Rc = tc * rho[K - 1] * h;
     int64_t nfail = 0;
 #pragma omp parallel for schedule(dynamic, 16) reduction(+ : nfail)
     for (int64_t m = 0; m < M; ++m) {
@@ -449,9 +513,9 @@ int64_t ora_eval(const double *x, const double *nrm, const double *w, const doub
         const double *nm0 = n0 + 3 * m, *xm0 = x0 + 3 * m, *fm0 = f0 + 3 * m, *qm0 = q0 + 3 * m;
         double fn0 = fm0[0] * nm0[0] + fm0[1] * nm0[1] + fm0[2] * nm0[2];
         double chi = (bm < 0.0) ? 1.0 : ((bm > 0.0) ? 0.0 : 0.5);
-        double U[3][6];
+        double U[4][6];
         double sfar_u[3] = {0, 0, 0}, sfar_v[3] = {0, 0, 0};
-        double snear_u[3][3], snear_v[3][3];
+        double snear_u[4][3], snear_v[4][3];
         memset(snear_u, 0, sizeof snear_u); memset(snear_v, 0, sizeof snear_v);
         for (int64_t j = 0; j < N; ++j) {
             const double *xj = x + 3 * j, *nj = nrm + 3 * j;
@@ -469,23 +533,31 @@ int64_t ora_eval(const double *x, const double *nrm, const double *w, const doub
                 ora_dl_plain(d, r, Q, nj, w[j], sfar_v);
                 continue;
             }
-            for (int k = 0; k < 3; ++k) {
+            for (int k = 0; k < K; ++k) {
                 double delta = rho[k] * h;
                 ora_sl_term(d, r, delta, tc, g, w[j], snear_u[k], 0);
                 ora_dl_term(r, delta, tc, bm, nm0, xh, Q, nj, w[j], snear_v[k], 0);
             }
         }
-        for (int k = 0; k < 3; ++k) {
+        for (int k = 0; k < K; ++k) {
             for (int i = 0; i < 3; ++i) {
                 U[k][i] = (sfar_u[i] + snear_u[k][i]) * inv8pi;
                 U[k][3 + i] = (sfar_v[i] + snear_v[k][i]) * inv8pi + chi * qm0[i];
             }
         }
         double out[6];
-        if (ora_extrapolate(rho, bm, h, &U[0][0], 6, out) != 0) nfail += 1;
+        if (ora_extrapolate_k(K, rho, bm, h, &U[0][0], 6, out) != 0) nfail += 1;
         for (int i = 0; i < 3; ++i) { u[3 * m + i] = out[i]; v[3 * m + i] = out[3 + i]; }
     }
     return nfail;
+}
+
+/* The method with three deltas (Eq. (extrap_eqn)). */
+int64_t ora_eval(const double *x, const double *nrm, const double *w, const double *f, const double *q, int64_t N,
+                 const double *y, const double *x0, const double *n0, const double *b,
+                 const double *f0, const double *q0, int64_t M,
+                 double h, const double rho[3], double tc, int mode, double *u, double *v) {
+    return ora_eval_k(3, x, nrm, w, f, q, N, y, x0, n0, b, f0, q0, M, h, rho, tc, mode, u, v);
 }
 
 /* Regularized sums for one delta at every target (no extrapolation); used to pin the

@@ -97,7 +97,7 @@ def _taus():
 def test_sigma_table_accuracy(L):
     """The interpolation table reproduces s_p(t)/t^p (Eqs. (s1)-(s3)) to ~1e-15 on tau = t^2 in [0, 24)."""
     mp = pytest.importorskip("mpmath")
-    mp.mp.dps = 40
+    mp.mp.dps = max(mp.mp.dps, 40)
     tab = np.empty(NINT * 3 * (DEG + 1))
     assert L.ers_debug_sigma_table(tab.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), tab.size) == 0
     tab = tab.reshape(NINT, 3, DEG + 1)
@@ -116,7 +116,7 @@ def test_sigma_device_layout_accuracy(L):
     """The device copy, evaluated as the near-field kernel does (degrees 6..4 in FP32, 3..0 in
     FP64), stays within ~1e-15 of s_p(t)/t^p: the FP32 part carries less than 2e-8 of the value."""
     mp = pytest.importorskip("mpmath")
-    mp.mp.dps = 40
+    mp.mp.dps = max(mp.mp.dps, 40)
     nbytes = NINT * 3 * 4 * 8 + NINT * 3 * 16
     raw = np.empty(nbytes // 8)
     L.ers_debug_sigma_device.argtypes = [ctypes.c_void_p, ctypes.c_int64]
@@ -150,7 +150,7 @@ def test_sigma_sharp_device_layout_accuracy(L):
     """The on-surface table (s#_p(t)/t^p of Sec. 2.1, intervals of 1/32 on tau in [0, 64)), as the
     kernel evaluates it (degrees 6..4 in FP32, 3..0 in FP64), stays within ~1e-15 of 60-digit values."""
     mp = pytest.importorskip("mpmath")
-    mp.mp.dps = 60
+    mp.mp.dps = max(mp.mp.dps, 60)
     nint, inv_w = 2048, 32
     nbytes = nint * 3 * 4 * 8 + nint * 3 * 16
     raw = np.empty(nbytes // 8)

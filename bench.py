@@ -408,12 +408,12 @@ def main():
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)  # > 129 MB L2
     stream = torch.cuda.current_stream()
 
-    def step(prec, concurrent=False, sharp=False):
-        s.eval(yd, f0, q0, rho=wl.rho, precision=prec, u=u, v=v, concurrent=concurrent, sharp=sharp)
+    def step(prec, concurrent=False, sharp=False, rho=None):
+        s.eval(yd, f0, q0, rho=rho or wl.rho, precision=prec, u=u, v=v, concurrent=concurrent, sharp=sharp)
 
-    def timed(prec, steps, warm, concurrent=False, sharp=False):
+    def timed(prec, steps, warm, concurrent=False, sharp=False, rho=None):
         for _ in range(warm):
-            step(prec, concurrent, sharp)
+            step(prec, concurrent, sharp, rho)
         s.profile(True)
         torch.cuda.synchronize()
         barrier(world)
@@ -424,7 +424,7 @@ def main():
             flush.fill_(1)
             a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             a.record(stream)
-            step(prec, concurrent, sharp)
+            step(prec, concurrent, sharp, rho)
             b.record(stream)
             evs.append((a, b))
             kern.append(s.last_profile())  # synchronizes; device times are unaffected
@@ -460,6 +460,15 @@ def main():
     t_sh = max_over_ranks(t_sh, world)
     nsh_pairs = s.last_sharp_pairs()
     u_sh, v_sh = u.cpu().numpy(), v.cpu().numpy()
+
+    # the same mixed step with the O(delta^7) variant (ERS_OPT_FOUR_DELTA): a fourth delta
+    # rho_3 = 2 rho_2 - rho_1, near radius cutoff_t rho_3 h
+    rho4 = tuple(wl.rho) + (2 * wl.rho[2] - wl.rho[1],)
+    t_fd, k_fd = timed(ers.PREC_MIXED, args.steps, 1, rho=rho4)
+    t_fd = max_over_ranks(t_fd, world)
+    fd_counts = s.last_counts()
+    fd_cls = s.last_class_counts()
+    u_fd, v_fd = u.cpu().numpy(), v.cpu().numpy()
 
     # the same mixed step with the far and near fields on two streams (ERS_OPT_CONCURRENT)
     t_conc, k_conc = timed(ers.PREC_MIXED, args.steps, 1, concurrent=True)
@@ -533,6 +542,18 @@ def main():
                                          / np.abs(v_mixed[on_surface]).max())},
                          "note": "ERS_OPT_SHARP: on-surface targets with the s#_p of Sec. 2.1, delta# = 3h, "
                                  "no extrapolation; both methods are O(h^5)"},
+        "four_delta_option": {"ms_per_step": t_fd / args.steps * 1e3, "rho": list(rho4),
+                              "cost_vs_three_delta": t_fd / t_mixed,
+                              "kernels_ms": {"far_field": float(k_fd[1]), "near_field_and_solve": float(k_fd[2])},
+                              "near_targets": fd_counts[0], "near_pairs": fd_counts[1],
+                              "near_pairs_by_unregularized_deltas": fd_cls,
+                              "near_tflops": NEAR_FLOPS_PER_DELTA_EVAL * sum(c * (4 - k) for k, c in enumerate(fd_cls))
+                              / (float(k_fd[2]) * 1e-3) / 1e12,
+                              "max_rel_diff_vs_three_delta": {
+                                  "SL": float(np.abs(u_fd - u_mixed).max() / np.abs(u_mixed).max()),
+                                  "DL": float(np.abs(v_fd - v_mixed).max() / np.abs(v_mixed).max())},
+                              "note": "ERS_OPT_FOUR_DELTA: O(delta^7) extrapolation of Sec. 1 with the I4 "
+                                      "column; the difference is the three-delta method's O(h^5) error"},
         "concurrent_option": {"ms_per_step": t_conc / args.steps * 1e3,
                               "kernels_ms": {"far_field": float(k_conc[1]), "near_field_and_solve": float(k_conc[2])},
                               "note": "same step with ERS_OPT_CONCURRENT (far and near fields on two streams, "

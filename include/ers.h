@@ -59,6 +59,15 @@ extern "C" {
                              double layer: the stresslet -6 d d d s#_3/r^5), localized at
                              cutoff_t delta#; targets off the surface are unchanged */
 
+#define ERS_OPT_FOUR_DELTA 4 /* ers_params.options: the O(delta^7) variant of the extrapolation that
+                                Sec. 1 mentions, with a fourth delta_3 = rho4 h and the error model
+                                u^delta = u + c1 rho I0 + c2 rho^3 I2 + c3 rho^5 I4 + O(delta^7),
+                                I4(lambda) = (2/15)((3 - 2 lambda^2 + 4 lambda^4) e^{-lambda^2}/sqrt(pi)
+                                - 4 |lambda|^5 erfc|lambda|) (the k = 2 moment int_lambda^inf erfc(r)
+                                (r^2 - lambda^2)^k dr, of which I0, I2 are k = 0, 1); near radius
+                                cutoff_t delta_3.  Not available in the batched, no-allocation and
+                                closure paths (ERS_E_UNSUPPORTED) */
+
 #define ERS_PREC_FP64 0   /* every step in FP64 arithmetic */
 #define ERS_PREC_MIXED 1  /* far field with FP32 operands and FP64 accumulation per source tile;
                              local sums, closest point and 3x3 solve in FP64 */
@@ -78,6 +87,7 @@ typedef struct {
     int layers;       /* bitmask of ERS_LAYER_SL, ERS_LAYER_DL */
     int options;      /* bitmask of ERS_OPT_*; 0 for the defaults */
     double rho_sharp; /* ERS_OPT_SHARP: delta# = rho_sharp h (> 0), or 0 for rho[1] */
+    double rho4;      /* ERS_OPT_FOUR_DELTA: delta_3 = rho4 h (> rho[2]), or 0 for 2 rho[2] - rho[1] */
 } ers_params;
 
 /*

@@ -34,6 +34,7 @@ PREC_FP64 = 0
 PREC_MIXED = 1
 OPT_CONCURRENT = 1
 OPT_SHARP = 2
+OPT_FOUR_DELTA = 4
 
 # Every symbol the header declares (checked by the tests).
 EXPORTS = ["ers_build_surface", "ers_surface_free", "ers_surface_info", "ers_set_density", "ers_closest_point",
@@ -64,7 +65,8 @@ class _Problem(ctypes.Structure):
 
 class _Params(ctypes.Structure):
     _fields_ = [("rho", ctypes.c_double * 3), ("cutoff_t", ctypes.c_double), ("precision", ctypes.c_int),
-                ("layers", ctypes.c_int), ("options", ctypes.c_int), ("rho_sharp", ctypes.c_double)]
+                ("layers", ctypes.c_int), ("options", ctypes.c_int), ("rho_sharp", ctypes.c_double),
+                ("rho4", ctypes.c_double)]
 
 
 _lib = None
@@ -166,6 +168,9 @@ class _DevView:
 
 def params(rho=(2.0, 3.0, 4.0), cutoff_t=6.0, precision=PREC_FP64, layers=LAYER_SL | LAYER_DL,
            concurrent: bool = False, sharp: bool = False, rho_sharp: float = 0.0) -> _Params:
+    """ers_params; four entries in rho select ERS_OPT_FOUR_DELTA with rho4 = rho[3]."""
+    if len(rho) not in (3, 4):
+        raise ValueError("rho needs 3 entries (or 4 for the O(delta^7) variant)")
     p = _Params()
     for k in range(3):
         p.rho[k] = float(rho[k])
@@ -174,6 +179,9 @@ def params(rho=(2.0, 3.0, 4.0), cutoff_t=6.0, precision=PREC_FP64, layers=LAYER_
     p.layers = int(layers)
     p.options = (OPT_CONCURRENT if concurrent else 0) | (OPT_SHARP if sharp else 0)
     p.rho_sharp = float(rho_sharp)
+    if len(rho) == 4:
+        p.options |= OPT_FOUR_DELTA
+        p.rho4 = float(rho[3])
     return p
 
 
@@ -231,7 +239,8 @@ class Surface:
              layers=LAYER_SL | LAYER_DL, x0=None, n0=None, b=None, u=None, v=None, stream=None,
              concurrent: bool = False, sharp: bool = False, rho_sharp: float = 0.0):
         """ers_eval: returns (u, v) (None for a layer not selected).  concurrent=True sets
-        ERS_OPT_CONCURRENT; sharp=True sets ERS_OPT_SHARP with delta# = rho_sharp h (0: rho[1])."""
+        ERS_OPT_CONCURRENT; sharp=True sets ERS_OPT_SHARP with delta# = rho_sharp h (0: rho[1]);
+        four entries in rho set ERS_OPT_FOUR_DELTA (the O(delta^7) variant)."""
         import torch
         M = y.shape[0]
         sl, dl = bool(layers & LAYER_SL), bool(layers & LAYER_DL)
@@ -240,6 +249,7 @@ class Surface:
         if dl and v is None:
             v = torch.empty((M, 3), dtype=torch.float64, device=y.device)
         p = params(rho, cutoff_t, precision, layers, concurrent, sharp, rho_sharp)
+        self._last_nd = len(rho)
         self.last_rc = check(lib().ers_eval(self._h, ctypes.byref(p), _ptr(y), M, _ptr(x0), _ptr(n0), _ptr(b),
                                             _ptr(f0) if sl else None, _ptr(q0) if dl else None,
                                             _ptr(u) if sl else None, _ptr(v) if dl else None, _stream(stream)))
@@ -274,6 +284,7 @@ class Surface:
         if dl and v is None:
             v = np.empty((M, 3))
         p = params(rho, cutoff_t, precision, layers)
+        self._last_nd = len(rho)
         check(lib().ers_eval_host(self._h, ctypes.byref(p), _hptr(y), M, None, None, None,
                                   _hptr(f0) if sl else None, _hptr(q0) if dl else None,
                                   _hptr(u) if sl else None, _hptr(v) if dl else None, _stream(stream)))
@@ -296,13 +307,15 @@ class Surface:
 
     def last_class_counts(self):
         """Near pairs of the most recent eval by the number of deltas with r > cutoff_t delta_k
-        (0, 1, 2): the method's count of regularized terms."""
-        return self._class_counts()[:3]
+        (0, 1, 2; and 3 after a four-delta eval): the method's count of regularized terms."""
+        c = self._class_counts()
+        return c[:3] + ([c[8]] if getattr(self, "_last_nd", 3) == 4 else [])
 
     def last_defect_class_counts(self):
         """Near pairs of the most recent eval by the number of deltas whose defects 1 - s_p are
-        evaluated directly instead of from the table (0..3)."""
-        return self._class_counts()[3:7]
+        evaluated directly instead of from the table (0..3; and 4 after a four-delta eval)."""
+        c = self._class_counts()
+        return c[3:7] + ([c[9]] if getattr(self, "_last_nd", 3) == 4 else [])
 
     def last_sharp_pairs(self):
         """Near pairs of on-surface targets evaluated with the s#_p (ERS_OPT_SHARP) in the most
@@ -311,10 +324,10 @@ class Surface:
 
     def _class_counts(self):
         self.last_counts()
-        c = (ctypes.c_int64 * 8)()
+        c = (ctypes.c_int64 * 10)()
         L = lib()
         L.ers_debug_class_counts.argtypes = [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int64), ctypes.c_int]
-        check(L.ers_debug_class_counts(self._h, c, 8))
+        check(L.ers_debug_class_counts(self._h, c, 10))
         return [int(z) for z in c]
 
 

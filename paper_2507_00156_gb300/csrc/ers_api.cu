@@ -256,18 +256,26 @@ int build_surface(const ers_shape *shape, double h, ers_surface **out) {
     return ERS_OK;
 }
 
+// The fourth rho of ERS_OPT_FOUR_DELTA: rho4, or 2 rho[2] - rho[1] (the next of an evenly spaced set).
+double rho4_of(const ers_params *p) { return p->rho4 > 0.0 ? p->rho4 : 2.0 * p->rho[2] - p->rho[1]; }
+
 int check_params(const ers_surface *s, const ers_params *p, int *warn) {
     *warn = ERS_OK;
     if (!p) return fail(ERS_E_INVAL, "NULL params");
     for (int k = 0; k < 3; ++k)
         if (!(p->rho[k] > 0.0) || !std::isfinite(p->rho[k])) return fail(ERS_E_INVAL, "rho must be finite and > 0");
     if (!(p->rho[0] < p->rho[1] && p->rho[1] < p->rho[2])) return fail(ERS_E_INVAL, "rho must be strictly increasing");
+    if (p->options & ERS_OPT_FOUR_DELTA) {
+        if (!std::isfinite(p->rho4) || p->rho4 < 0.0 || (p->rho4 > 0.0 && !(p->rho4 > p->rho[2])))
+            return fail(ERS_E_INVAL, "rho4 must be 0 or finite and > rho[2]");
+    }
     if (!(p->cutoff_t > 0.0) || !std::isfinite(p->cutoff_t)) return fail(ERS_E_INVAL, "cutoff_t must be finite and > 0");
     if (p->cutoff_t > 8.0) return fail(ERS_E_UNSUPPORTED, "cutoff_t above 8 is outside the interpolation table");
     if (p->precision != ERS_PREC_FP64 && p->precision != ERS_PREC_MIXED)
         return fail(ERS_E_INVAL, "precision must be ERS_PREC_FP64 or ERS_PREC_MIXED");
     if (p->layers < 1 || p->layers > 3) return fail(ERS_E_INVAL, "layers must be a non-empty mask of SL/DL");
-    if (p->options & ~(ERS_OPT_CONCURRENT | ERS_OPT_SHARP)) return fail(ERS_E_INVAL, "unknown bit in options");
+    if (p->options & ~(ERS_OPT_CONCURRENT | ERS_OPT_SHARP | ERS_OPT_FOUR_DELTA))
+        return fail(ERS_E_INVAL, "unknown bit in options");
     if (!(p->rho_sharp >= 0.0) || !std::isfinite(p->rho_sharp)) return fail(ERS_E_INVAL, "rho_sharp must be finite and >= 0");
     if (p->cutoff_t < 6.0) *warn = ERS_W_CUTOFF;
     (void)s;
@@ -317,12 +325,14 @@ int eval_impl(ers_surface *s, const ers_params *p, const double *y, int64_t M, c
     a.q0 = q0;
     a.u = u;
     a.v = v;
+    if (ndelta == 3 && (p->options & ERS_OPT_FOUR_DELTA)) ndelta = 4;
     for (int k = 0; k < 3; ++k) a.rho[k] = p->rho[k];
+    a.rho[3] = ndelta == 4 ? rho4_of(p) : 0.0;
     a.cutoff_t = p->cutoff_t;
-    a.Rc = p->cutoff_t * p->rho[ndelta - 1] * s->h;
+    a.Rc = p->cutoff_t * a.rho[ndelta - 1] * s->h;
     a.ndelta = ndelta;
     a.gamma = gamma;
-    if ((p->options & ERS_OPT_SHARP) && ndelta == 3) {  // on-surface targets: s#_p of Sec. 2.1
+    if ((p->options & ERS_OPT_SHARP) && ndelta >= 3) {  // on-surface targets: s#_p of Sec. 2.1
         a.sharp = true;
         a.rho_sharp = p->rho_sharp > 0.0 ? p->rho_sharp : p->rho[1];
         a.dsharp = a.rho_sharp * s->h;
@@ -560,6 +570,8 @@ int ers_last_counts(ers_surface *s, int64_t *near_targets, int64_t *near_pairs, 
         for (int c = 0; c < 4; ++c) s->last_dclass[c] = (int64_t)hc[2 + c];
         for (int c = 0; c < 3; ++c) s->last_class[c] = (int64_t)hc[6 + c];
         s->last_sharp = (int64_t)hc[9];
+        s->last_dclass[4] = (int64_t)hc[10];
+        s->last_class[3] = (int64_t)hc[11];
     }
     if (near_targets) *near_targets = s->last_counts[0];
     if (near_pairs) *near_pairs = s->last_counts[1];
@@ -583,12 +595,18 @@ extern "C" int ers_debug_set_caps(int far_c, int near_c, int far_s, int near_s) 
 // Test/benchmark hook (not in the public header): near pairs of the last ers_eval, valid after
 // ers_last_counts.  out[0..2]: by the number of deltas with r > cutoff_t delta_k (0, 1, 2);
 // out[3..6]: by the number of deltas on the direct-defect path (0..3); out[7]: near pairs of
-// on-surface targets evaluated with the s#_p (ERS_OPT_SHARP; not in out[0..6]).  n >= 8.
+// on-surface targets evaluated with the s#_p (ERS_OPT_SHARP; not in out[0..6]); with n >= 10,
+// out[8]: 3 deltas beyond the cutoff, out[9]: 4 deltas on the defect path (ERS_OPT_FOUR_DELTA
+// only).  n >= 8.
 extern "C" int ers_debug_class_counts(ers_surface *s, int64_t *out, int n) {
     if (!s || !out || n < 8) return ERS_E_INVAL;
     for (int c = 0; c < 3; ++c) out[c] = s->last_class[c];
     for (int c = 0; c < 4; ++c) out[3 + c] = s->last_dclass[c];
     out[7] = s->last_sharp;
+    if (n >= 10) {
+        out[8] = s->last_class[3];
+        out[9] = s->last_dclass[4];
+    }
     return ERS_OK;
 }
 

@@ -21,7 +21,7 @@ namespace ers {
 // w f and w n feed the single layer (g w = w f - (f(x0).n0) w n, Eq. (Stokes_SL1)); q and w n
 // feed the double layer (Q = q - q(x0), m = w n, Eq. (Stokes_DL1)).
 constexpr int REC = 12;
-constexpr int NCOUNTERS = 10;  // near-field counters of one evaluation (EvalArgs::counters)
+constexpr int NCOUNTERS = 12;  // near-field counters of one evaluation (EvalArgs::counters)
 constexpr int R_X = 0, R_WF = 3, R_WN = 6, R_Q = 9;
 
 // FP32 record for the mixed-precision far field (48 B): x - c_tile, w f, w n, q.
@@ -90,8 +90,8 @@ struct ers_surface {
     ers::Scratch dens64, dens32;
     int nrhs_multi = 0;
     int64_t last_counts[3] = {0, 0, 0};
-    int64_t last_class[3] = {0, 0, 0};   // near pairs by number of deltas with r > cutoff_t delta
-    int64_t last_dclass[4] = {0, 0, 0, 0};  // near pairs by number of deltas on the direct-defect path
+    int64_t last_class[4] = {0, 0, 0, 0};     // near pairs by number of deltas with r > cutoff_t delta
+    int64_t last_dclass[5] = {0, 0, 0, 0, 0};  // near pairs by number of deltas on the direct-defect path
     int64_t last_sharp = 0;                 // near pairs of on-surface targets (ERS_OPT_SHARP)
     cudaStream_t last_stream = nullptr;
     // optional per-kernel timing
@@ -160,9 +160,10 @@ struct EvalArgs {
     SurfDev sd;
     const double *y, *x0, *n0, *b, *f0, *q0;
     int64_t M;
-    double rho[3], cutoff_t, Rc;
+    double rho[4], cutoff_t, Rc;  // rho[3]: the fourth delta of the O(delta^7) variant (ndelta = 4)
     int precision, layers;
-    int ndelta;      // 3: extrapolation of Eq. (extrap_eqn); 2: two-delta weights (learned closure)
+    int ndelta;      // 3: extrapolation of Eq. (extrap_eqn); 4: the O(delta^7) variant of Sec. 1;
+                     // 2: two-delta weights (learned closure); 1: the single sum with delta_0
     bool far_later;  // the near-field kernel leaves the far partial sums to k_combine
     // ERS_OPT_SHARP: targets with b == 0 use the s#_p of Sec. 2.1 with delta# = dsharp, near
     // radius Rc_sharp = cutoff_t delta#, table tab_sharp (far kernels: per-target radius)
@@ -175,7 +176,8 @@ struct EvalArgs {
     int chunks;
     int64_t chunk_len;
     // [near_targets, near_pairs, near pairs of class 0..3 (deltas on the defect path),
-    //  near pairs with 0, 1, 2 deltas beyond cutoff_t, near pairs of on-surface (s#) targets]
+    //  near pairs with 0, 1, 2 deltas beyond cutoff_t, near pairs of on-surface (s#) targets,
+    //  near pairs of class 4, near pairs with 3 deltas beyond cutoff_t (both four deltas only)]
     unsigned long long *counters;
     cudaStream_t stream;
 };

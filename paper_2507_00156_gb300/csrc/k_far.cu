@@ -44,7 +44,7 @@ __device__ __forceinline__ void load_target(const EvalArgs &A, int64_t m, bool s
     }
     for (int i = 0; i < 3; ++i) T.y[i] = A.y[3 * m + i];
     const double bm = A.b[m];
-    // near radius of this target: cutoff_t delta_3, or cutoff_t delta# on the surface (ERS_OPT_SHARP)
+    // near radius of this target: cutoff_t times the largest delta, or cutoff_t delta# on the surface (ERS_OPT_SHARP)
     const double Rt = (A.sharp && bm == 0.0) ? A.Rc_sharp : A.Rc;
     const bool near = fabs(bm) <= Rt;
     T.rc2bits = near ? __double_as_longlong(Rt * Rt) : -1LL;

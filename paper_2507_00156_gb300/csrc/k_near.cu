@@ -12,11 +12,12 @@
 // Double layer (Eqs. (Tsplit), (Treg)):  -6 [ t1 (K3 - (r^2 - b^2) K5) + t2 K5 ] : Q (w n),
 // contracted in closed form (dl_pair / dl_accumulate in near_common.cuh).
 // The weights alpha are the first row of the inverse of A_k = [1, rho_k I0(b/delta_k),
-// rho_k^3 I2(b/delta_k)] (Eqs. (extrap_eqn), (I0), (I2)), by Cramer's rule.
+// rho_k^3 I2(b/delta_k)] (Eqs. (extrap_eqn), (I0), (I2)), by Cramer's rule.  The O(delta^7)
+// variant (Sec. 1) runs the same kernel with four deltas (ND = 4, A_k with rho_k^5 I4 appended).
 //
 // One warp per target.  The warp walks the rows of the cell grid that meet the ball of radius
 // Rc, tests candidates with an FP32 prefilter (conservative margin), and queues survivors by
-// class c = number of delta_k with r > min(4.7, cutoff_t) delta_k, so that each batch of 32 runs
+// class c = number of delta_k with r > min(4.7, cutoff_t) delta_k (0..ND), so that each batch of 32 runs
 // one code path.  Each batch then makes the exact FP64 (or, for the mixed far field, the
 // identical FP32) near/far test, so that the partition matches the far-field mask exactly.
 #include <algorithm>
@@ -34,8 +35,8 @@ constexpr int NEAR_MIN_BLOCKS = 3;
 template <int CLS, int PREC, bool SL, bool DL, int ND>
 __device__ __forceinline__ void process(const EvalArgs &A, const Geom &T, const ScanParams &P, double c,
                                         const double q0[3], const double *__restrict__ tab, int64_t j,
-                                        double accU[3], double &accN, double accD[3], int npairs[NCLS],
-                                        int nunreg[3]) {
+                                        double accU[3], double &accN, double accD[3], int npairs[NCLS_MAX],
+                                        int nunreg[MAXD]) {
     const double2 *r = reinterpret_cast<const double2 *>(A.sd.rec + j * REC);
     const double2 r0 = __ldg(r + 0), r1 = __ldg(r + 1), r2v = __ldg(r + 2);
     const double2 r3 = __ldg(r + 3), r4 = __ldg(r + 4), r5 = __ldg(r + 5);
@@ -51,10 +52,10 @@ __device__ __forceinline__ void process(const EvalArgs &A, const Geom &T, const 
     ++npairs[CLS];
     {  // pairs by number of deltas with r > cutoff_t delta_k (the method's own count of regularized terms)
         const float r2f = approx_float_pos(r2);
-        const int u = (r2f > P.cut2[0]) + (r2f > P.cut2[1]);
-        nunreg[0] += u == 0;
-        nunreg[1] += u == 1;
-        nunreg[2] += u == 2;
+        int u = (r2f > P.cut2[0]) + (r2f > P.cut2[1]);
+        if (ND == 4) u += r2f > P.cut2[2];
+#pragma unroll
+        for (int k = 0; k < (ND == 4 ? 4 : 3); ++k) nunreg[k] += u == k;
     }
     double K1, K3, K5;
     float Lf;
@@ -167,7 +168,7 @@ __device__ __forceinline__ void near_target(const EvalArgs &A, const ScanParams 
     if (lane < 6 && !A.far_later)
         for (int c = 0; c < A.chunks; ++c) fs += A.part[((int64_t)c * A.M + m) * 6 + lane];
     const double bm = A.b[m];
-    if (ND == 3 && A.sharp && bm == 0.0) {
+    if (ND >= 3 && A.sharp && bm == 0.0) {
         near_target_sharp<PREC, SL, DL>(A, Ps, m, lane, sq, G, fs);
         return;
     }
@@ -183,7 +184,7 @@ __device__ __forceinline__ void near_target(const EvalArgs &A, const ScanParams 
     double gam = 0.0;
     {
         Geom Tl;
-        load_geom(lane, A.y, A.x0, A.n0, bm, m, A.rho, P.h, Tl, A.ndelta, &gam);
+        load_geom(lane, A.y, A.x0, A.n0, bm, m, A.rho, P.h, Tl, ND, &gam);
         set_cutoff(Tl, P);
         __syncwarp();  // the previous target's reads of G are done
         if (lane == 0) G = Tl;
@@ -195,15 +196,18 @@ __device__ __forceinline__ void near_target(const EvalArgs &A, const ScanParams 
     for (int i = 0; i < 3; ++i) q0[i] = DL ? A.q0[3 * m + i] : 0.0;
     const double c = SL ? fma(A.f0[3 * m + 2], T.n0[2], fma(A.f0[3 * m + 1], T.n0[1], A.f0[3 * m] * T.n0[0])) : 0.0;
 
+    constexpr int NC = ND == 4 ? 5 : NCLS;  // pair classes
     double accU[3] = {0.0, 0.0, 0.0}, accD[3] = {0.0, 0.0, 0.0}, accN = 0.0;
-    int npairs[NCLS] = {0, 0, 0, 0};  // near pairs by class
-    int nunreg[3] = {0, 0, 0};        // near pairs by number of deltas beyond the cutoff
-    scan_near(A.sd, T, P, sq, lane, [&](int cls, int jj, bool valid) {
+    int npairs[NCLS_MAX] = {0, 0, 0, 0, 0};  // near pairs by class
+    int nunreg[MAXD] = {0, 0, 0, 0};         // near pairs by number of deltas beyond the cutoff
+    scan_near<NC>(A.sd, T, P, sq, lane, [&](int cls, int jj, bool valid) {
         if (!valid) return;
         if (cls == 0) process<0, PREC, SL, DL, ND>(A, T, P, c, q0, tab, jj, accU, accN, accD, npairs, nunreg);
         else if (cls == 1) process<1, PREC, SL, DL, ND>(A, T, P, c, q0, tab, jj, accU, accN, accD, npairs, nunreg);
         else if (cls == 2) process<2, PREC, SL, DL, ND>(A, T, P, c, q0, tab, jj, accU, accN, accD, npairs, nunreg);
-        else process<3, PREC, SL, DL, ND>(A, T, P, c, q0, tab, jj, accU, accN, accD, npairs, nunreg);
+        else if (NC == 4 || cls == 3)
+            process<3, PREC, SL, DL, ND>(A, T, P, c, q0, tab, jj, accU, accN, accD, npairs, nunreg);
+        else process<4, PREC, SL, DL, ND>(A, T, P, c, q0, tab, jj, accU, accN, accD, npairs, nunreg);
     });
     for (int i = 0; i < 3; ++i) {
         accU[i] = warp_sum(accU[i]);
@@ -211,16 +215,21 @@ __device__ __forceinline__ void near_target(const EvalArgs &A, const ScanParams 
     }
     accN = warp_sum(accN);
     if (A.counters) {
-        int np[NCLS + 3] = {npairs[0], npairs[1], npairs[2], npairs[3], nunreg[0], nunreg[1], nunreg[2]};
+        // counters: [2 + c] class c < 4, [6 + u] u < 3 deltas beyond the cutoff, [10] class 4, [11] u = 3
+        int np[9] = {npairs[0], npairs[1], npairs[2], npairs[3], nunreg[0], nunreg[1], nunreg[2], npairs[4], nunreg[3]};
 #pragma unroll
-        for (int cc = 0; cc < NCLS + 3; ++cc)
+        for (int cc = 0; cc < 9; ++cc)
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) np[cc] += __shfl_xor_sync(FULL, np[cc], o);
         if (lane == 0) {
             atomicAdd(A.counters + 0, 1ull);
-            atomicAdd(A.counters + 1, (unsigned long long)(np[0] + np[1] + np[2] + np[3]));
+            atomicAdd(A.counters + 1, (unsigned long long)(np[0] + np[1] + np[2] + np[3] + np[7]));
 #pragma unroll
-            for (int cc = 0; cc < NCLS + 3; ++cc) atomicAdd(A.counters + 2 + cc, (unsigned long long)np[cc]);
+            for (int cc = 0; cc < 7; ++cc) atomicAdd(A.counters + 2 + cc, (unsigned long long)np[cc]);
+            if (ND == 4) {
+                atomicAdd(A.counters + 10, (unsigned long long)np[7]);
+                atomicAdd(A.counters + 11, (unsigned long long)np[8]);
+            }
         }
     }
     if (SL && lane < 3) {
@@ -240,7 +249,7 @@ __device__ __forceinline__ void near_target(const EvalArgs &A, const ScanParams 
 template <int PREC, bool SL, bool DL, int ND>
 __global__ void __launch_bounds__(WPB * 32, NEAR_MIN_BLOCKS) k_near(EvalArgs A, ScanParams P, ScanParams Ps,
                                                                    const double *__restrict__ tab) {
-    __shared__ int sq[WPB][NCLS][64];
+    __shared__ int sq[WPB][ND == 4 ? 5 : NCLS][64];
     __shared__ Geom sG[WPB];
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     // one target per warp; a capped grid strides over the targets
@@ -259,6 +268,10 @@ cudaError_t near_dispatch(const EvalArgs &a, ScanParams P, ScanParams Ps, const 
         if (!(sl && dl)) return cudaErrorInvalidValue;
         if (a.ndelta == 1) k_near<PREC, true, true, 1><<<g, WPB * 32, 0, a.stream>>>(a, P, Ps, tab);
         else k_near<PREC, true, true, 2><<<g, WPB * 32, 0, a.stream>>>(a, P, Ps, tab);
+    } else if (a.ndelta == 4) {  // the O(delta^7) variant
+        if (sl && dl) k_near<PREC, true, true, 4><<<g, WPB * 32, 0, a.stream>>>(a, P, Ps, tab);
+        else if (sl) k_near<PREC, true, false, 4><<<g, WPB * 32, 0, a.stream>>>(a, P, Ps, tab);
+        else k_near<PREC, false, true, 4><<<g, WPB * 32, 0, a.stream>>>(a, P, Ps, tab);
     } else if (sl && dl) k_near<PREC, true, true, 3><<<g, WPB * 32, 0, a.stream>>>(a, P, Ps, tab);
     else if (sl) k_near<PREC, true, false, 3><<<g, WPB * 32, 0, a.stream>>>(a, P, Ps, tab);
     else k_near<PREC, false, true, 3><<<g, WPB * 32, 0, a.stream>>>(a, P, Ps, tab);
@@ -269,12 +282,12 @@ cudaError_t near_dispatch(const EvalArgs &a, ScanParams P, ScanParams Ps, const 
 
 cudaError_t launch_near(const EvalArgs &a, const double *tab, int ctas_per_sm, int nsm) {
     if (a.M == 0) return cudaSuccess;
-    const ScanParams P = scan_params(a.s, a.Rc, a.rho, a.cutoff_t);
+    const ScanParams P = scan_params(a.s, a.Rc, a.rho, a.cutoff_t, a.ndelta == 4 ? 4 : 3);
     ScanParams Ps = P;
     if (a.sharp) {  // on-surface targets: one delta#, every near pair on the table
         const double rs[3] = {a.rho_sharp, a.rho_sharp, a.rho_sharp};
         Ps = scan_params(a.s, a.Rc_sharp, rs, a.cutoff_t);
-        for (int k = 0; k < 3; ++k) Ps.th[k] = HUGE_VALF;
+        for (int k = 0; k < MAXD; ++k) Ps.th[k] = HUGE_VALF;
     }
     if (a.precision == ERS_PREC_FP64) return near_dispatch<ERS_PREC_FP64>(a, P, Ps, tab, ctas_per_sm, nsm);
     return near_dispatch<ERS_PREC_MIXED>(a, P, Ps, tab, ctas_per_sm, nsm);

@@ -11,7 +11,8 @@
 //       t1 : Q m = n0 (b P - S) - xh P,   t2 : Q m = n0 (b R) + xh (b S - R),
 //     evaluated in the equivalent form of dl_accumulate (in terms of d = y - x = b n0 - xh).
 // alpha = first row of the inverse of A_k = [1, rho_k I0(b/delta_k), rho_k^3 I2(b/delta_k)]
-// (Eqs. (extrap_eqn), (I0), (I2)), by Cramer's rule.
+// (Eqs. (extrap_eqn), (I0), (I2)), by Cramer's rule; with four deltas (the O(delta^7) variant of
+// Sec. 1) A_k gains the column rho_k^5 I4(b/delta_k).
 #pragma once
 
 #include "ers_internal.h"
@@ -23,14 +24,17 @@ constexpr unsigned FULL = 0xffffffffu;
 constexpr double INV8PI = 0.039788735772973833942;
 constexpr double INVSQRTPI = 0.56418958354775628695;
 
-// Density-independent constants of one near target.
+// Most deltas of one evaluation: three for Eq. (extrap_eqn), four for the O(delta^7) variant.
+constexpr int MAXD = 4;
+
+// Density-independent constants of one near target (entries k < number of deltas in use).
 struct Geom {
     double y[3], x0[3], n0[3], b, b2;  // b2 = 2 b
-    double invd2[3], ad1[3], ad3[3], ad5[3];
-    double apre[3];         // alpha_0, alpha_0 + alpha_1, alpha_0 + alpha_1 + alpha_2
-    float yh[3], yl[3];     // y = yh + yl in floats (mixed-mode classification)
-    float id2h[3], id2l[3]; // 1/delta_k^2 = id2h + id2l in floats
-    float alf[3];           // extrapolation weights in FP32 (for the small defects 1 - s_p)
+    double invd2[MAXD], ad1[MAXD], ad3[MAXD], ad5[MAXD];
+    double apre[MAXD];         // partial sums alpha_0 + ... + alpha_k
+    float yh[3], yl[3];        // y = yh + yl in floats (mixed-mode classification)
+    float id2h[MAXD], id2l[MAXD]; // 1/delta_k^2 = id2h + id2l in floats
+    float alf[MAXD];           // extrapolation weights in FP32 (for the small defects 1 - s_p)
     float tcf2;             // cutoff_t^2: s_p := 1 beyond t = cutoff_t
     bool cut_small;         // cutoff_t < DEFECT_T: the table path may meet the cutoff
 };
@@ -38,17 +42,19 @@ struct Geom {
 // Beyond t = r/delta = DEFECT_T the defects 1 - s_p(t) are below 2.1e-8 and are evaluated in
 // FP32 instead of from the FP64 table.
 constexpr double DEFECT_T = 4.7;
-// Near-pair classes: c = number of delta_k (from delta_0 up) with r > min(DEFECT_T, cutoff_t) delta_k.
+// Near-pair classes: c = number of delta_k (from delta_0 up) with r > min(DEFECT_T, cutoff_t) delta_k,
+// 0..3 with three deltas (NCLS of them), 0..4 with four.
 constexpr int NCLS = 4;
+constexpr int NCLS_MAX = MAXD + 1;
 
 struct ScanParams {
     float rc2f;     // exact FP32 threshold of the mixed far field
     float rpre;     // FP32 prefilter radius (Rc plus a conservative margin)
-    float th[3];    // FP32 class thresholds (min(DEFECT_T, cutoff_t) delta_k)^2
-    float cut2[2];  // (cutoff_t delta_k)^2, k = 0, 1: for the pair counts by regularized deltas
+    float th[MAXD];    // FP32 class thresholds (min(DEFECT_T, cutoff_t) delta_k)^2 (+inf past the deltas in use)
+    float cut2[MAXD - 1];  // (cutoff_t delta_k)^2, k below the largest delta: pair counts by regularized deltas
     float tcf2;       // cutoff_t^2
     double tc2;       // cutoff_t^2 in FP64
-    double cut2d[3];  // (cutoff_t delta_k)^2 in FP64, delta_k = rho_k h
+    double cut2d[MAXD];  // (cutoff_t delta_k)^2 in FP64, delta_k = rho_k h
     double h;
 };
 
@@ -100,6 +106,53 @@ __device__ __forceinline__ void extrap_weights(int lane, double b, const double 
     }
 }
 
+// The O(delta^7) variant with four deltas: A_k = [1, a_k, c_k, e_k] with a_k = rho_k I0(lambda_k),
+// c_k = rho_k^3 I2(lambda_k), e_k = rho_k^5 I4(lambda_k), I4(lambda) = (2/15)((3 - 2 lambda^2 +
+// 4 lambda^4) e^{-lambda^2}/sqrt(pi) - 4 lambda^5 erfc lambda).  alpha solves A^T alpha = e_0: by
+// Cramer's rule alpha_k = C_k / sum_j C_j with C_k = (-1)^k det of the 3x3 matrix of rows a, c, e
+// without column k (expanding det A^T along its first row of ones).  Lanes 0..3 evaluate the I's.
+__device__ __forceinline__ void extrap_weights4(int lane, double b, const double rho[MAXD], double h,
+                                                double al[MAXD]) {
+    double i0 = 0.0, i2 = 0.0, i4 = 0.0;
+    if (lane < 4) {
+        const double rl = lane == 0 ? rho[0] : (lane == 1 ? rho[1] : (lane == 2 ? rho[2] : rho[3]));
+        const double lam = fabs(b) / (rl * h), l2 = lam * lam;
+        const double e = exp(-l2) * INVSQRTPI, ec = erfc(lam);
+        i0 = e - lam * ec;
+        i2 = (2.0 / 3.0) * ((0.5 - l2) * e + l2 * lam * ec);
+        i4 = (2.0 / 15.0) * (fma(fma(4.0, l2, -2.0), l2, 3.0) * e - 4.0 * l2 * l2 * lam * ec);
+    }
+    double a[MAXD], c[MAXD], e[MAXD];
+#pragma unroll
+    for (int k = 0; k < MAXD; ++k) {
+        const double rk = rho[k], r3 = rk * rk * rk;
+        a[k] = rk * __shfl_sync(FULL, i0, k);
+        c[k] = r3 * __shfl_sync(FULL, i2, k);
+        e[k] = r3 * rk * rk * __shfl_sync(FULL, i4, k);
+    }
+    // 2x2 minors of rows c, e: m_ij = c_i e_j - c_j e_i
+    const double m01 = c[0] * e[1] - c[1] * e[0], m02 = c[0] * e[2] - c[2] * e[0];
+    const double m03 = c[0] * e[3] - c[3] * e[0], m12 = c[1] * e[2] - c[2] * e[1];
+    const double m13 = c[1] * e[3] - c[3] * e[1], m23 = c[2] * e[3] - c[3] * e[2];
+    al[0] = a[1] * m23 - a[2] * m13 + a[3] * m12;
+    al[1] = -(a[0] * m23 - a[2] * m03 + a[3] * m02);
+    al[2] = a[0] * m13 - a[1] * m03 + a[3] * m01;
+    al[3] = -(a[0] * m12 - a[1] * m02 + a[2] * m01);
+    const double det = (al[0] + al[1]) + (al[2] + al[3]);
+    bool ok = det != 0.0 && isfinite(det);
+    if (ok) {
+#pragma unroll
+        for (int k = 0; k < MAXD; ++k) al[k] /= det;
+        ok = isfinite(al[0]) && isfinite(al[1]) && isfinite(al[2]) && isfinite(al[3]);
+    }
+    if (!ok) {
+        al[0] = 1.0;
+        al[1] = 0.0;
+        al[2] = 0.0;
+        al[3] = 0.0;
+    }
+}
+
 // Two-delta weights: the system of Eq. (extrap_eqn) for delta_0, delta_1 without the c2 column,
 // beta_0 + beta_1 = 1, beta_0 rho_0 I0(lambda_0) + beta_1 rho_1 I0(lambda_1) = 0, so that
 // sum_k beta_k u^{delta_k} = u + gamma c2 + O(delta^5) with
@@ -129,11 +182,12 @@ __device__ __forceinline__ void two_delta_weights(int lane, double b, const doub
     gamma = al[0] * c0 + al[1] * c1;
 }
 
-// Fill the geometry constants of target m (all lanes; lanes 0..2 also evaluate I0, I2).
-// ndelta = 3: the extrapolation weights of Eq. (extrap_eqn); ndelta = 2: the two-delta
-// weights above (gamma returned in *gamma).
+// Fill the geometry constants of target m (all lanes; lanes 0..ndelta-1 also evaluate the I's).
+// ndelta = 3: the extrapolation weights of Eq. (extrap_eqn); 4: the O(delta^7) variant;
+// 2: the two-delta weights above (gamma returned in *gamma); 1: alpha = (1, 0, 0).
+// rho holds max(ndelta, 3) entries.
 __device__ __forceinline__ void load_geom(int lane, const double *y, const double *x0, const double *n0, double b,
-                                          int64_t m, const double rho[3], double h, Geom &T, int ndelta = 3,
+                                          int64_t m, const double *rho, double h, Geom &T, int ndelta = 3,
                                           double *gamma = nullptr) {
     for (int i = 0; i < 3; ++i) {
         T.y[i] = y[3 * m + i];
@@ -144,8 +198,11 @@ __device__ __forceinline__ void load_geom(int lane, const double *y, const doubl
     }
     T.b = b;
     T.b2 = 2.0 * b;
-    double al[3];
-    if (ndelta == 2) {
+    double al[MAXD] = {1.0, 0.0, 0.0, 0.0};
+    if (ndelta == 4) {
+        extrap_weights4(lane, b, rho, h, al);
+        if (gamma) *gamma = 0.0;
+    } else if (ndelta == 2) {
         double g;
         two_delta_weights(lane, b, rho, h, al, g);
         if (gamma) *gamma = g;
@@ -157,8 +214,10 @@ __device__ __forceinline__ void load_geom(int lane, const double *y, const doubl
     } else {
         extrap_weights(lane, b, rho, h, al);
     }
+    const int nk = ndelta == 4 ? 4 : 3;
 #pragma unroll
-    for (int k = 0; k < 3; ++k) {
+    for (int k = 0; k < MAXD; ++k) {
+        if (k >= nk) break;
         const double dk = rho[k] * h, id = 1.0 / dk;
         T.invd2[k] = id * id;
         T.ad1[k] = al[k] * id;
@@ -170,7 +229,8 @@ __device__ __forceinline__ void load_geom(int lane, const double *y, const doubl
     T.apre[0] = al[0];
     T.apre[1] = al[0] + al[1];
     T.apre[2] = al[0] + al[1] + al[2];
-    for (int k = 0; k < 3; ++k) T.alf[k] = (float)al[k];
+    T.apre[3] = (al[0] + al[1]) + (al[2] + al[3]);
+    for (int k = 0; k < MAXD; ++k) T.alf[k] = (float)al[k];
 }
 
 // Exact near/far decision of pair (T, j), identical to the far-field mask of the precision
@@ -363,13 +423,16 @@ __device__ __forceinline__ void dl_accumulate_defect(const Geom &T, double dx, d
 }
 
 // Walk the rows of the surface's cell grid that meet the prefilter ball around the target,
-// test candidates in FP32, queue survivors by class in the warp's shared queues sq[NCLS][64],
+// test candidates in FP32, queue survivors by class in the warp's shared queues sq[NC][64],
 // and call batch(cls, j, valid) with one node per lane whenever a class has 32 entries, then
-// once more per class for the remainder (lanes with valid = false hold no node).
-template <class Batch>
+// once more per class for the remainder (lanes with valid = false hold no node).  NC = number
+// of classes: 4 with three deltas, 5 with four.
+template <int NC = NCLS, class Batch>
 __device__ __forceinline__ void scan_near(const SurfDev &s, const Geom &T, const ScanParams &P, int (*sq)[64],
                                           int lane, Batch &&batch) {
-    int qn[NCLS] = {0, 0, 0, 0};
+    int qn[NC];
+#pragma unroll
+    for (int c = 0; c < NC; ++c) qn[c] = 0;
     const unsigned lt = (1u << lane) - 1u;
     const Grid &G = s.grid;
     const float yf[3] = {T.yh[0], T.yh[1], T.yh[2]};
@@ -406,17 +469,18 @@ __device__ __forceinline__ void scan_near(const SurfDev &s, const Geom &T, const
                     const float ex = yf[0] - p.x, ey = yf[1] - p.y, ez = yf[2] - p.z;
                     const float r2f = fmaf(ez, ez, fmaf(ey, ey, ex * ex));
                     pass = r2f <= R2;
-                    cls = (r2f > P.th[0]) + (r2f > P.th[1]) + (r2f > P.th[2]);
+#pragma unroll
+                    for (int k = 0; k < NC - 1; ++k) cls += r2f > P.th[k];
                 }
 #pragma unroll
-                for (int c = 0; c < NCLS; ++c) {
+                for (int c = 0; c < NC; ++c) {
                     const unsigned mk = __ballot_sync(FULL, pass && cls == c);
                     if (pass && cls == c) sq[c][qn[c] + __popc(mk & lt)] = j;
                     qn[c] += __popc(mk);
                 }
                 __syncwarp();
 #pragma unroll
-                for (int c = 0; c < NCLS; ++c) {
+                for (int c = 0; c < NC; ++c) {
                     if (qn[c] >= 32) {
                         batch(c, sq[c][qn[c] - 32 + lane], true);
                         qn[c] -= 32;
@@ -427,7 +491,7 @@ __device__ __forceinline__ void scan_near(const SurfDev &s, const Geom &T, const
         }
     }
 #pragma unroll
-    for (int c = 0; c < NCLS; ++c) {
+    for (int c = 0; c < NC; ++c) {
         if (qn[c] > 0) {
             const bool v = lane < qn[c];
             batch(c, v ? sq[c][lane] : 0, v);
@@ -442,13 +506,15 @@ __device__ __forceinline__ double warp_sum(double v) {
     return v;
 }
 
-inline ScanParams scan_params(const ers_surface *s, double Rc, const double rho[3], double cutoff_t) {
-    ScanParams P;
+// nd = number of deltas (3 or 4; rho holds nd entries)
+inline ScanParams scan_params(const ers_surface *s, double Rc, const double *rho, double cutoff_t, int nd = 3) {
+    ScanParams P{};
     P.rc2f = (float)(Rc * Rc);
     double L = 0.0;
     for (int i = 0; i < 3; ++i) L = fmax(L, fabs(s->c[i]) + s->a[i]);
     P.rpre = (float)(Rc * (1.0 + 1e-5) + 4e-6 * (L + Rc));
-    for (int k = 0; k < 3; ++k) {
+    for (int k = nd; k < MAXD; ++k) P.th[k] = HUGE_VALF;
+    for (int k = 0; k < nd; ++k) {
         // The prefilter's r^2 comes from float coordinates (|coordinate| <= L + Rc, each rounded
         // to 2^-24 relative): widen the threshold by 4x that error bound so that every pair sent
         // to the defect path has r > min(DEFECT_T, cutoff_t) delta_k in exact arithmetic (the
@@ -457,13 +523,14 @@ inline ScanParams scan_params(const ers_surface *s, double Rc, const double rho[
         const double margin = fmin(0.04, 1e-6 + 4.0 * 2.0 * 6.0 * (L + Rc) * 0x1p-24 / t);
         P.th[k] = (float)(t * t * (1.0 + margin));
     }
-    for (int k = 0; k < 2; ++k) {
+    for (int k = 0; k < MAXD - 1; ++k) P.cut2[k] = HUGE_VALF;
+    for (int k = 0; k < nd - 1; ++k) {
         const double t = cutoff_t * rho[k] * s->h;
         P.cut2[k] = (float)(t * t);
     }
     P.tcf2 = (float)(cutoff_t * cutoff_t);
     P.tc2 = cutoff_t * cutoff_t;
-    for (int k = 0; k < 3; ++k) {
+    for (int k = 0; k < nd; ++k) {
         const double rk = cutoff_t * rho[k] * s->h;
         P.cut2d[k] = rk * rk;
     }

@@ -10,6 +10,8 @@ Functions:
   closest_point(shape, y)                   x0, n0, b with y = x0 + b n0 (Sec. 2)
   evaluate(nodes, f, q, y, cp, f0, q0, ...) SL and DL values, direct or localized (Secs. 2, 3.3)
   sigma(t), I0(lam), I2(lam), extrapolate   building blocks (Eqs. (s1)-(s3), (I0), (I2), (extrap_eqn))
+  evaluate_tree(...), tree_info, tree_weights, lagrange
+                                            the treecode far field of Sec. 3.4 (ers_treecode.c)
 """
 from __future__ import annotations
 
@@ -22,6 +24,7 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "ers_oracle.c")
+_SRCS = [_SRC, os.path.join(_HERE, "ers_treecode.c")]
 _LIB_PATH = os.path.join(_HERE, "_build", "libers_oracle.so")
 _lock = threading.Lock()
 _lib = None
@@ -34,9 +37,10 @@ ON_SURFACE_TOL = 1e-12  # |b| <= tol * (largest semi-axis) counts as on the surf
 def build(force: bool = False) -> str:
     """Compile the oracle with gcc (-O2, OpenMP, no fast-math)."""
     os.makedirs(os.path.dirname(_LIB_PATH), exist_ok=True)
-    if force or not os.path.exists(_LIB_PATH) or os.path.getmtime(_LIB_PATH) < os.path.getmtime(_SRC):
+    stale = not os.path.exists(_LIB_PATH) or any(os.path.getmtime(_LIB_PATH) < os.path.getmtime(f) for f in _SRCS)
+    if force or stale:
         tmp = _LIB_PATH + f".tmp{os.getpid()}"
-        cmd = ["gcc", "-O2", "-fopenmp", "-fPIC", "-shared", "-std=c11", "-o", tmp, _SRC, "-lm"]
+        cmd = ["gcc", "-O2", "-fopenmp", "-fPIC", "-shared", "-std=c11", "-o", tmp, *_SRCS, "-lm"]
         subprocess.run(cmd, check=True)
         os.replace(tmp, _LIB_PATH)
     return _LIB_PATH
@@ -78,6 +82,18 @@ def _load():
             lib.ora_plain.restype = None
             lib.ora_plain.argtypes = [P, P, P, P, P, i64, P, i64, P, P]
             lib.ora_num_threads.restype = cint
+            I = ctypes.POINTER(ctypes.c_int64)
+            lib.ora_eval_tree.restype = i64
+            lib.ora_eval_tree.argtypes = [cint, P, P, P, P, P, i64, P, P, P, P, P, P, i64, dbl, P, dbl, dbl, i64,
+                                          cint, P, P, I]
+            lib.ora_tree_info.restype = i64
+            lib.ora_tree_info.argtypes = [P, i64, i64, i64, P, P, P, I, I, I, I, I, I]
+            lib.ora_tree_weights.restype = i64
+            lib.ora_tree_weights.argtypes = [P, P, P, P, P, i64, i64, cint, i64, P]
+            lib.ora_lagrange.restype = None
+            lib.ora_lagrange.argtypes = [cint, dbl, dbl, dbl, P]
+            lib.ora_cheb_points.restype = None
+            lib.ora_cheb_points.argtypes = [cint, P]
             _lib = lib
     return _lib
 
@@ -203,3 +219,83 @@ def plain(x, n, w, f, q, y):
     u, v = np.empty((M, 3)), np.empty((M, 3))
     lib.ora_plain(_p(x), _p(n), _p(w), _p(f), _p(q), N, _p(y), M, _p(u), _p(v))
     return u, v
+
+
+# --- treecode far field (Sec. 3.4; ers_treecode.c) ---------------------------------------
+
+def _pi(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_int64))
+
+
+def evaluate_tree(x, n, w, f, q, y, x0, n0, b, f0, q0, h, rho, tc=6.0, theta=0.6, n0_leaf=2000, p=6,
+                  stats=False):
+    """evaluate() with the far sums by the kernel-independent treecode (MAC theta, leaf size
+    n0_leaf, degree p); stats=True also returns (M, 4) int64 per-target counts: clusters
+    approximated, nodes in them, far pairs summed directly, near pairs."""
+    lib = _load()
+    x, n, w, f, q = map(_c, (x, n, w, f, q))
+    y, x0, n0, b, f0, q0 = map(_c, (y, x0, n0, b, f0, q0))
+    N, M = w.shape[0], b.shape[0]
+    u, v = np.empty((M, 3)), np.empty((M, 3))
+    st = np.zeros((M, 4), dtype=np.int64)
+    rho = _c(rho)
+    assert len(rho) in (3, 4) and 1 <= p <= 30
+    nfail = lib.ora_eval_tree(len(rho), _p(x), _p(n), _p(w), _p(f), _p(q), N, _p(y), _p(x0), _p(n0), _p(b),
+                              _p(f0), _p(q0), M, float(h), _p(rho), float(tc), float(theta), int(n0_leaf), int(p),
+                              _p(u), _p(v), _pi(st))
+    return (u, v, int(nfail), st) if stats else (u, v, int(nfail))
+
+
+def tree_info(x, n0_leaf):
+    """The octree of the treecode: dict of per-cluster arrays lo, hi (C,3), rc, start, count, level,
+    nchild, parent (C,), and perm (N,) (the node order of the leaves)."""
+    lib = _load()
+    x = _c(x)
+    N = x.shape[0]
+    cap = max(64, 4 * N // max(1, int(n0_leaf)) + 64)
+    while True:
+        lo, hi = np.empty((cap, 3)), np.empty((cap, 3))
+        rc = np.empty(cap)
+        ints = [np.empty(cap, dtype=np.int64) for _ in range(5)]
+        perm = np.empty(N, dtype=np.int64)
+        nc = lib.ora_tree_info(_p(x), N, int(n0_leaf), cap, _p(lo), _p(hi), _p(rc), *map(_pi, ints), _pi(perm))
+        if nc >= 0:
+            break
+        cap = -nc
+    start, count, level, nchild, parent = (a[:nc] for a in ints)
+    return dict(lo=lo[:nc], hi=hi[:nc], rc=rc[:nc], start=start, count=count, level=level, nchild=nchild,
+                parent=parent, perm=perm)
+
+
+def tree_weights(x, n, w, f, q, n0_leaf, p):
+    """Modified weights of Eq. (mod_weights) of every cluster: (C, (p+1)^3, 15) with the densities
+    f w (0:3), n w (3:6), q_j n_k w (6:15, index 6 + 3 j + k)."""
+    lib = _load()
+    x, n, w, f, q = map(_c, (x, n, w, f, q))
+    N = x.shape[0]
+    cap = max(64, 4 * N // max(1, int(n0_leaf)) + 64)
+    nk = (p + 1) ** 3
+    while True:
+        W = np.empty((cap, nk, 15))
+        nc = lib.ora_tree_weights(_p(x), _p(n), _p(w), _p(f), _p(q), N, int(n0_leaf), int(p), cap, _p(W))
+        if nc >= 0:
+            return W[:nc]
+        cap = -nc
+
+
+def lagrange(p, c, hw, xs):
+    """Barycentric Lagrange basis at the p+1 Chebyshev points of [c - hw, c + hw], at each x in xs."""
+    lib = _load()
+    out = np.empty((len(xs), p + 1))
+    buf = np.empty(p + 1)
+    for i, xv in enumerate(xs):
+        lib.ora_lagrange(int(p), float(c), float(hw), float(xv), _p(buf))
+        out[i] = buf
+    return out
+
+
+def cheb_points(p):
+    lib = _load()
+    s = np.empty(p + 1)
+    lib.ora_cheb_points(int(p), _p(s))
+    return s

@@ -17,7 +17,8 @@
  * values, the limits at 0 and infinity, O(h^5) against the sphere closed form and in
  * self-convergence at shared nodes; for the four-delta variant: I4 against quadrature of its
  * defining integral, I4' = -4 lambda I2, exact weights at b = 0, faster than O(h^5) against the
- * sphere closed form).  Nothing here is "parity unpinned".
+ * sphere closed form; the treecode far field of Sec. 3.4 lives in ers_treecode.c with its own
+ * pins).  Nothing here is "parity unpinned".
  */
 #include <math.h>
 #include <stdint.h>
@@ -384,7 +385,7 @@ int ora_extrapolate(const double rho[3], double b, double h, const double *U /* 
  * Eq. (Stokes_SL2):  S^delta_ij g_j w = (s1/r) g_i w + d_i (d.g) (s2/r^3) w, d = y - x.
  * t = r/delta; s_p := 1 when t > tc (Sec. 3.2).  Adds into acc[3] (without 1/(8 pi)).
  */
-static void ora_sl_term(const double d[3], double r, double delta, double tc, const double g[3], double w,
+void ora_sl_term(const double d[3], double r, double delta, double tc, const double g[3], double w,
                         double acc[3], int sharp) {
     double t = r / delta;
     double k1, k3; /* s1/r and s2/r^3 (s#1, s#2 when sharp) */
@@ -409,7 +410,7 @@ static void ora_sl_term(const double d[3], double r, double delta, double tc, co
  * with n = n0 (normal at the closest point) and xh = x - x0.  The tensors are formed
  * explicitly and contracted, as written.  s_p := 1 when t > tc.
  */
-static void ora_dl_term(double r, double delta, double tc, double b, const double nrm0[3], const double xh[3],
+void ora_dl_term(double r, double delta, double tc, double b, const double nrm0[3], const double xh[3],
                         const double Q[3], const double nx[3], double w, double acc[3], int sharp) {
     double t = r / delta;
     double k3, k5; /* s2/r^3 and s3/r^5 (s#2, s#3 when sharp) */
@@ -457,11 +458,11 @@ static void ora_dl_term_sharp(const double d[3], double r, double delta, double 
 }
 
 /* Plain (unregularized) pair terms, Eqs. (Stokeslet), (Stresslet). */
-static void ora_sl_plain(const double d[3], double r, const double g[3], double w, double acc[3]) {
+void ora_sl_plain(const double d[3], double r, const double g[3], double w, double acc[3]) {
     double dg = d[0] * g[0] + d[1] * g[1] + d[2] * g[2];
     for (int i = 0; i < 3; ++i) acc[i] += (g[i] / r + d[i] * dg / (r * r * r)) * w;
 }
-static void ora_dl_plain(const double d[3], double r, const double Q[3], const double nx[3], double w, double acc[3]) {
+void ora_dl_plain(const double d[3], double r, const double Q[3], const double nx[3], double w, double acc[3]) {
     double dq = d[0] * Q[0] + d[1] * Q[1] + d[2] * Q[2];
     double dn = d[0] * nx[0] + d[1] * nx[1] + d[2] * nx[2];
     double r5 = r * r * r * r * r;

@@ -393,8 +393,9 @@ def main():
     s = ers.Surface(wl.shape.center, wl.shape.axes, wl.h)
     xd, _, _ = s.nodes()
     x = xd.cpu().numpy()
-    s.set_density(torch.from_numpy(workloads.poly_eval(wl.f_coef, x)).to(dev),
-                  torch.from_numpy(workloads.poly_eval(wl.q_coef, x)).to(dev))
+    fdev = torch.from_numpy(workloads.poly_eval(wl.f_coef, x)).to(dev)
+    qdev = torch.from_numpy(workloads.poly_eval(wl.q_coef, x)).to(dev)
+    s.set_density(fdev, qdev)
     y = build_targets(wl, x)
     M, N = len(y), s.N
     yd = torch.from_numpy(y).to(dev)
@@ -408,12 +409,13 @@ def main():
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)  # > 129 MB L2
     stream = torch.cuda.current_stream()
 
-    def step(prec, concurrent=False, sharp=False, rho=None):
-        s.eval(yd, f0, q0, rho=rho or wl.rho, precision=prec, u=u, v=v, concurrent=concurrent, sharp=sharp)
+    def step(prec, concurrent=False, sharp=False, rho=None, tree=None):
+        s.eval(yd, f0, q0, rho=rho or wl.rho, precision=prec, u=u, v=v, concurrent=concurrent, sharp=sharp,
+               tree=tree)
 
-    def timed(prec, steps, warm, concurrent=False, sharp=False, rho=None):
+    def timed(prec, steps, warm, concurrent=False, sharp=False, rho=None, tree=None):
         for _ in range(warm):
-            step(prec, concurrent, sharp, rho)
+            step(prec, concurrent, sharp, rho, tree)
         s.profile(True)
         torch.cuda.synchronize()
         barrier(world)
@@ -424,7 +426,7 @@ def main():
             flush.fill_(1)
             a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             a.record(stream)
-            step(prec, concurrent, sharp, rho)
+            step(prec, concurrent, sharp, rho, tree)
             b.record(stream)
             evs.append((a, b))
             kern.append(s.last_profile())  # synchronizes; device times are unaffected
@@ -469,6 +471,18 @@ def main():
     fd_counts = s.last_counts()
     fd_cls = s.last_class_counts()
     u_fd, v_fd = u.cpu().numpy(), v.cpu().numpy()
+
+    # the same mixed step with the far sums by the treecode of Sec. 3.4 (ERS_OPT_TREECODE) at the
+    # parameters of Eq. (optimal_params) for this h; the modified weights are built in the warm-up
+    # (they depend only on the densities) and timed separately after a density update
+    tree = ers.treecode_defaults(wl.h)
+    t_tc, k_tc = timed(ers.PREC_MIXED, args.steps, 1, tree=tree)
+    t_tc = max_over_ranks(t_tc, world)
+    tc_stats = s.tree_stats()
+    tc_counts = s.last_counts()
+    u_tc, v_tc = u.cpu().numpy(), v.cpu().numpy()
+    s.set_density(fdev, qdev)  # same densities, new version: the next treecode eval rebuilds the weights
+    _, k_tcw = timed(ers.PREC_MIXED, 1, 0, tree=tree)
 
     # the same mixed step with the far and near fields on two streams (ERS_OPT_CONCURRENT)
     t_conc, k_conc = timed(ers.PREC_MIXED, args.steps, 1, concurrent=True)
@@ -554,6 +568,20 @@ def main():
                                   "DL": float(np.abs(v_fd - v_mixed).max() / np.abs(v_mixed).max())},
                               "note": "ERS_OPT_FOUR_DELTA: O(delta^7) extrapolation of Sec. 1 with the I4 "
                                       "column; the difference is the three-delta method's O(h^5) error"},
+        "treecode_option": {"ms_per_step": t_tc / args.steps * 1e3, "theta": tree[0], "N0": tree[1], "p": tree[2],
+                            "speedup_vs_direct": t_mixed / t_tc,
+                            "kernels_ms": {"far_field_treecode": float(k_tc[1]), "near_field_and_solve": float(k_tc[2])},
+                            "modified_weights_ms": float(k_tcw[1]) - float(k_tc[1]),
+                            "tree": tc_stats,
+                            "approximated_per_target": tc_stats["approximated"] / M,
+                            "direct_far_pairs_per_target": tc_stats["direct"] / M,
+                            "near_pairs": tc_counts[1],
+                            "max_rel_diff_vs_direct": {
+                                "SL": float(np.abs(u_tc - u_mixed).max() / np.abs(u_mixed).max()),
+                                "DL": float(np.abs(v_tc - v_mixed).max() / np.abs(v_mixed).max())},
+                            "note": "ERS_OPT_TREECODE: far sums by barycentric Lagrange interpolation at "
+                                    "Chebyshev points for clusters meeting the MAC (Sec. 3.4), parameters of "
+                                    "Eq. (optimal_params); weights cached between steps (densities unchanged)"},
         "concurrent_option": {"ms_per_step": t_conc / args.steps * 1e3,
                               "kernels_ms": {"far_field": float(k_conc[1]), "near_field_and_solve": float(k_conc[2])},
                               "note": "same step with ERS_OPT_CONCURRENT (far and near fields on two streams, "

@@ -68,6 +68,18 @@ extern "C" {
                                 cutoff_t delta_3.  Not available in the batched, no-allocation and
                                 closure paths (ERS_E_UNSUPPORTED) */
 
+#define ERS_OPT_TREECODE 8 /* ers_params.options: the far sums by the kernel-independent treecode of
+                              Sec. 3.4 instead of the direct sum: an octree of the nodes (leaves of at
+                              most tree_n0), clusters that meet the MAC r_c/R <= tree_theta and lie
+                              beyond the near radius (R - r_c > (1 + 1e-4) Rc) summed by barycentric
+                              Lagrange interpolation of degree tree_p at Chebyshev points (modified
+                              weights of w f, w n, q_j w n_k), other leaves summed directly over their
+                              nodes beyond Rc.  The near sums and the extrapolation are unchanged.  The
+                              tree is built on the host at the first use for a given tree_n0 and kept
+                              with the surface; the modified weights are recomputed after every
+                              ers_set_density or change of tree_p.  ERS_OPT_CONCURRENT is ignored.
+                              Not available in the batched, no-allocation and closure paths */
+
 #define ERS_PREC_FP64 0   /* every step in FP64 arithmetic */
 #define ERS_PREC_MIXED 1  /* far field with FP32 operands and FP64 accumulation per source tile;
                              local sums, closest point and 3x3 solve in FP64 */
@@ -88,6 +100,9 @@ typedef struct {
     int options;      /* bitmask of ERS_OPT_*; 0 for the defaults */
     double rho_sharp; /* ERS_OPT_SHARP: delta# = rho_sharp h (> 0), or 0 for rho[1] */
     double rho4;      /* ERS_OPT_FOUR_DELTA: delta_3 = rho4 h (> rho[2]), or 0 for 2 rho[2] - rho[1] */
+    double tree_theta; /* ERS_OPT_TREECODE: MAC parameter in (0, 1), or 0 for ers_treecode_defaults */
+    int tree_n0;       /* ERS_OPT_TREECODE: leaf size >= 1, or 0 for ers_treecode_defaults */
+    int tree_p;        /* ERS_OPT_TREECODE: interpolation degree 1..16, or 0 for ers_treecode_defaults */
 } ers_params;
 
 /*
@@ -350,6 +365,21 @@ int ers_eval_learned(ers_surface *s, ers_closure *c, const ers_params *p, const 
 int ers_eval_noalloc(ers_surface *s, const ers_params *p, const double *y, int64_t M, const double *x0,
                      const double *n0, const double *b, const double *f0, const double *q0, double *u, double *v,
                      void *stream);
+
+/*
+ * Treecode parameters of Eq. (optimal_params) for lattice spacing h (> 0): theta = 0.6, and
+ * N0 = 2000, p = 6 at h = 1/64 with N0 doubling and p growing by 2 per halving of h, held at
+ * N0 >= 1000 and 6 <= p <= 16 (Table 2 uses N0 = 1000, p = 6 at h = 1/16 and 1/32).  Host only;
+ * any output may be NULL.  ERS_E_INVAL for h <= 0 or non-finite.
+ */
+int ers_treecode_defaults(double h, double *theta, int *n0, int *p);
+
+/*
+ * Treecode statistics of the surface: out[0] clusters, out[1] leaves, out[2] depth of the last
+ * tree built (0 if none); out[3] (target, cluster) pairs approximated and out[4] far pairs summed
+ * directly by the last ERS_OPT_TREECODE evaluation (synchronizes with it).  n >= 5.
+ */
+int ers_tree_stats(ers_surface *s, int64_t *out, int n);
 
 /* Message of the last error on the calling thread ("" if none).  Never NULL. */
 const char *ers_last_error(void);

@@ -35,6 +35,7 @@ PREC_MIXED = 1
 OPT_CONCURRENT = 1
 OPT_SHARP = 2
 OPT_FOUR_DELTA = 4
+OPT_TREECODE = 8
 
 # Every symbol the header declares (checked by the tests).
 EXPORTS = ["ers_build_surface", "ers_surface_free", "ers_surface_info", "ers_set_density", "ers_closest_point",
@@ -42,7 +43,8 @@ EXPORTS = ["ers_build_surface", "ers_surface_free", "ers_surface_info", "ers_set
            "ers_last_profile", "ers_set_density_multi", "ers_batch_create", "ers_batch_launch", "ers_batch_info",
            "ers_batch_free", "ers_closure_create", "ers_closure_free", "ers_closure_params", "ers_closure_infer",
            "ers_closure_infer_reference", "ers_closure_status", "ers_closure_grad", "ers_closure_train",
-           "ers_closure_data", "ers_eval_learned", "ers_eval_noalloc", "ers_last_error", "ers_version"]
+           "ers_closure_data", "ers_eval_learned", "ers_eval_noalloc", "ers_treecode_defaults", "ers_tree_stats",
+           "ers_last_error", "ers_version"]
 NPARAM = 10448
 NOALLOC_MAX_M = 524288
 
@@ -66,7 +68,8 @@ class _Problem(ctypes.Structure):
 class _Params(ctypes.Structure):
     _fields_ = [("rho", ctypes.c_double * 3), ("cutoff_t", ctypes.c_double), ("precision", ctypes.c_int),
                 ("layers", ctypes.c_int), ("options", ctypes.c_int), ("rho_sharp", ctypes.c_double),
-                ("rho4", ctypes.c_double)]
+                ("rho4", ctypes.c_double), ("tree_theta", ctypes.c_double), ("tree_n0", ctypes.c_int),
+                ("tree_p", ctypes.c_int)]
 
 
 _lib = None
@@ -118,6 +121,8 @@ def lib():
             L.ers_last_counts.argtypes = [vp, P(i64), P(i64), P(i64)]
             L.ers_profile.argtypes = [vp, cint]
             L.ers_last_profile.argtypes = [vp, P(dbl), P(dbl), P(dbl)]
+            L.ers_treecode_defaults.argtypes = [dbl, P(dbl), P(cint), P(cint)]
+            L.ers_tree_stats.argtypes = [vp, P(i64), cint]
             L.ers_last_error.restype = ctypes.c_char_p
             L.ers_version.restype = ctypes.c_char_p
             for name in EXPORTS:
@@ -167,8 +172,9 @@ class _DevView:
 
 
 def params(rho=(2.0, 3.0, 4.0), cutoff_t=6.0, precision=PREC_FP64, layers=LAYER_SL | LAYER_DL,
-           concurrent: bool = False, sharp: bool = False, rho_sharp: float = 0.0) -> _Params:
-    """ers_params; four entries in rho select ERS_OPT_FOUR_DELTA with rho4 = rho[3]."""
+           concurrent: bool = False, sharp: bool = False, rho_sharp: float = 0.0, tree=None) -> _Params:
+    """ers_params; four entries in rho select ERS_OPT_FOUR_DELTA with rho4 = rho[3]; tree = None, or
+    (theta, n0, p) for ERS_OPT_TREECODE (zeros select ers_treecode_defaults; True for all three)."""
     if len(rho) not in (3, 4):
         raise ValueError("rho needs 3 entries (or 4 for the O(delta^7) variant)")
     p = _Params()
@@ -182,7 +188,18 @@ def params(rho=(2.0, 3.0, 4.0), cutoff_t=6.0, precision=PREC_FP64, layers=LAYER_
     if len(rho) == 4:
         p.options |= OPT_FOUR_DELTA
         p.rho4 = float(rho[3])
+    if tree is not None and tree is not False:
+        theta, n0, deg = (0.0, 0, 0) if tree is True else tree
+        p.options |= OPT_TREECODE
+        p.tree_theta, p.tree_n0, p.tree_p = float(theta), int(n0), int(deg)
     return p
+
+
+def treecode_defaults(h: float):
+    """(theta, N0, p) of Eq. (optimal_params) for spacing h (ers_treecode_defaults)."""
+    t, n, q = ctypes.c_double(), ctypes.c_int(), ctypes.c_int()
+    check(lib().ers_treecode_defaults(float(h), ctypes.byref(t), ctypes.byref(n), ctypes.byref(q)))
+    return t.value, n.value, q.value
 
 
 class Surface:
@@ -237,10 +254,11 @@ class Surface:
 
     def eval(self, y, f0=None, q0=None, rho=(2.0, 3.0, 4.0), cutoff_t=6.0, precision=PREC_FP64,
              layers=LAYER_SL | LAYER_DL, x0=None, n0=None, b=None, u=None, v=None, stream=None,
-             concurrent: bool = False, sharp: bool = False, rho_sharp: float = 0.0):
+             concurrent: bool = False, sharp: bool = False, rho_sharp: float = 0.0, tree=None):
         """ers_eval: returns (u, v) (None for a layer not selected).  concurrent=True sets
         ERS_OPT_CONCURRENT; sharp=True sets ERS_OPT_SHARP with delta# = rho_sharp h (0: rho[1]);
-        four entries in rho set ERS_OPT_FOUR_DELTA (the O(delta^7) variant)."""
+        four entries in rho set ERS_OPT_FOUR_DELTA (the O(delta^7) variant); tree = (theta, n0, p) or
+        True sets ERS_OPT_TREECODE (far sums by the treecode of Sec. 3.4)."""
         import torch
         M = y.shape[0]
         sl, dl = bool(layers & LAYER_SL), bool(layers & LAYER_DL)
@@ -248,7 +266,7 @@ class Surface:
             u = torch.empty((M, 3), dtype=torch.float64, device=y.device)
         if dl and v is None:
             v = torch.empty((M, 3), dtype=torch.float64, device=y.device)
-        p = params(rho, cutoff_t, precision, layers, concurrent, sharp, rho_sharp)
+        p = params(rho, cutoff_t, precision, layers, concurrent, sharp, rho_sharp, tree)
         self._last_nd = len(rho)
         self.last_rc = check(lib().ers_eval(self._h, ctypes.byref(p), _ptr(y), M, _ptr(x0), _ptr(n0), _ptr(b),
                                             _ptr(f0) if sl else None, _ptr(q0) if dl else None,
@@ -321,6 +339,13 @@ class Surface:
         """Near pairs of on-surface targets evaluated with the s#_p (ERS_OPT_SHARP) in the most
         recent eval."""
         return self._class_counts()[7]
+
+    def tree_stats(self):
+        """dict: clusters, leaves, depth of the surface's tree; approximated (target, cluster) pairs
+        and far pairs summed directly by the last treecode eval (ers_tree_stats)."""
+        out = (ctypes.c_int64 * 5)()
+        check(lib().ers_tree_stats(self._h, out, 5))
+        return dict(clusters=out[0], leaves=out[1], depth=out[2], approximated=out[3], direct=out[4])
 
     def _class_counts(self):
         self.last_counts()

@@ -61,6 +61,8 @@ int ers_batch_create(const ers_problem *probs, int nprob, const ers_params *p, i
     *out = nullptr;
     int warn;
     int rc = check_params(probs[0].s, p, &warn);
+    if (rc == ERS_OK && (p->options & ERS_OPT_TREECODE))
+        return fail(ERS_E_UNSUPPORTED, "ers_batch_create: ERS_OPT_TREECODE is not supported (use ers_eval)");
     if (rc == ERS_OK && (p->options & ERS_OPT_FOUR_DELTA))
         return fail(ERS_E_UNSUPPORTED, "ers_batch_create: ERS_OPT_FOUR_DELTA is not supported (use ers_eval)");
     if (rc == ERS_OK && (p->options & ERS_OPT_SHARP))

@@ -50,6 +50,7 @@ void free_surface(ers_surface *s) {
                     s->part.ptr, s->cp.ptr, s->host_io.ptr, s->counts.ptr, s->dens64.ptr, s->dens32.ptr};
     for (void *p : ptrs)
         if (p) cudaFree(p);
+    tree_free(s);
     for (cudaEvent_t e : s->ev)
         if (e) cudaEventDestroy(e);
     if (s->ev_fork) cudaEventDestroy(s->ev_fork);
@@ -274,8 +275,14 @@ int check_params(const ers_surface *s, const ers_params *p, int *warn) {
     if (p->precision != ERS_PREC_FP64 && p->precision != ERS_PREC_MIXED)
         return fail(ERS_E_INVAL, "precision must be ERS_PREC_FP64 or ERS_PREC_MIXED");
     if (p->layers < 1 || p->layers > 3) return fail(ERS_E_INVAL, "layers must be a non-empty mask of SL/DL");
-    if (p->options & ~(ERS_OPT_CONCURRENT | ERS_OPT_SHARP | ERS_OPT_FOUR_DELTA))
+    if (p->options & ~(ERS_OPT_CONCURRENT | ERS_OPT_SHARP | ERS_OPT_FOUR_DELTA | ERS_OPT_TREECODE))
         return fail(ERS_E_INVAL, "unknown bit in options");
+    if (p->options & ERS_OPT_TREECODE) {
+        if (!(p->tree_theta >= 0.0 && p->tree_theta < 1.0))
+            return fail(ERS_E_INVAL, "tree_theta must be in (0, 1), or 0 for the default");
+        if (p->tree_n0 < 0) return fail(ERS_E_INVAL, "tree_n0 must be >= 1, or 0 for the default");
+        if (p->tree_p < 0 || p->tree_p > TREE_PMAX) return fail(ERS_E_INVAL, "tree_p must be in 1..16, or 0 for the default");
+    }
     if (!(p->rho_sharp >= 0.0) || !std::isfinite(p->rho_sharp)) return fail(ERS_E_INVAL, "rho_sharp must be finite and >= 0");
     if (p->cutoff_t < 6.0) *warn = ERS_W_CUTOFF;
     (void)s;
@@ -360,6 +367,15 @@ int eval_impl(ers_surface *s, const ers_params *p, const double *y, int64_t M, c
         a.b = b;
     }
 
+    const bool tree = (p->options & ERS_OPT_TREECODE) != 0;
+    TreeParams tp{};
+    if (tree) {
+        treecode_defaults(s->h, &tp.theta, &tp.n0, &tp.p);
+        if (p->tree_theta > 0.0) tp.theta = p->tree_theta;
+        if (p->tree_n0 > 0) tp.n0 = p->tree_n0;
+        if (p->tree_p > 0) tp.p = p->tree_p;
+    }
+
     // far-field work split: target blocks x source chunks (chunks aligned to the FP32 tiles)
     int nsm = 152;
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
@@ -370,6 +386,7 @@ int eval_impl(ers_surface *s, const ers_params *p, const double *y, int64_t M, c
     int64_t clen = (s->N + chunks - 1) / chunks;
     clen = (clen + TS32 - 1) / TS32 * TS32;
     chunks = (s->N + clen - 1) / clen;
+    if (tree) chunks = 1;  // the treecode writes one partial sum per target
     a.chunks = (int)chunks;
     a.chunk_len = clen;
     if ((rc = grow(s->part, sizeof(double) * 6 * (size_t)M * chunks)) != ERS_OK) return rc;
@@ -384,8 +401,16 @@ int eval_impl(ers_surface *s, const ers_params *p, const double *y, int64_t M, c
     // the far field on the surface's second stream.  Both grids are capped (FAR_CTAS_PER_SM and
     // NEAR_CTAS_PER_SM CTAs per SM, the far one also by its shared memory) so that both kernels
     // are resident on every SM whichever starts first; k_combine then adds the far partial sums.
-    const bool overlap = p->precision == ERS_PREC_MIXED && (p->options & ERS_OPT_CONCURRENT);
-    if (overlap) {
+    const bool overlap = !tree && p->precision == ERS_PREC_MIXED && (p->options & ERS_OPT_CONCURRENT);
+    if (tree) {  // modified weights (when stale) and the walk, both in the far-field slot of the profile
+        if ((rc = tree_prepare(s, tp.n0, tp.p, p->precision == ERS_PREC_MIXED, st)) != ERS_OK) return rc;
+        e = launch_tree_far(a, tp);
+        if (e != cudaSuccess) return cuda_fail(e, "treecode far-field kernel");
+        if (prof) cudaEventRecord(s->ev[2], st);
+        e = launch_near(a, tab, g_caps[3], nsm);
+        if (e != cudaSuccess) return cuda_fail(e, "near-field kernel");
+        if (prof) cudaEventRecord(s->ev[3], st);
+    } else if (overlap) {
         const int FAR_CTAS_PER_SM = g_caps[0], NEAR_CTAS_PER_SM = g_caps[1];
         a.far_later = true;
         EvalArgs af = a;
@@ -478,6 +503,7 @@ int ers_set_density(ers_surface *s, const double *f, const double *q, void *stre
     if (e != cudaSuccess) return cuda_fail(e, "density kernel");
     if (f) s->has_f = true;
     if (q) s->has_q = true;
+    ++s->dens_version;
     return ERS_OK;
 }
 
@@ -641,6 +667,24 @@ int ers_last_profile(ers_surface *s, double *ms_closest, double *ms_far, double 
     if (ms_far) *ms_far = t[1];
     if (ms_near) *ms_near = t[2];
     return ERS_OK;
+}
+
+int ers_treecode_defaults(double h, double *theta, int *n0, int *p) {
+    clear_error();
+    if (!(h > 0.0) || !std::isfinite(h)) return fail(ERS_E_INVAL, "ers_treecode_defaults: h must be finite and > 0");
+    double t;
+    int n, q;
+    treecode_defaults(h, &t, &n, &q);
+    if (theta) *theta = t;
+    if (n0) *n0 = n;
+    if (p) *p = q;
+    return ERS_OK;
+}
+
+int ers_tree_stats(ers_surface *s, int64_t *out, int n) {
+    clear_error();
+    if (!s || !out || n < 5) return fail(ERS_E_INVAL, "ers_tree_stats: NULL argument or n < 5");
+    return tree_stats(s, out);
 }
 
 const char *ers_last_error(void) { return g_err.c_str(); }

@@ -63,6 +63,23 @@ struct Scratch {
     size_t bytes = 0;
 };
 
+// ------------------------------------------------------------------------------------------
+// Treecode far field (Sec. 3.4)
+// ------------------------------------------------------------------------------------------
+constexpr int TREE_NW = 15;    // modified-weight densities per Chebyshev point: w f (3), w n (3), q_j w n_k (9)
+constexpr int TREE_NW32 = 16;  // FP32 copy, padded to four float4
+constexpr int TREE_PMAX = 16;  // largest interpolation degree p
+
+// One cluster: the bounding box of its nodes (centre c, half-widths hw), r_c = half its diagonal;
+// nodes [start, start + count) of the tree order; children [first_child, first_child + nchild)
+// (clusters are numbered level by level, so siblings are contiguous).
+struct TreeCluster {
+    double c[3], hw[3], rc;
+    int start, count, first_child, nchild, level, pad;
+};
+
+struct TreeCache;  // per surface, built on first use (tree_host.cpp)
+
 }  // namespace ers
 
 struct ers_surface {
@@ -103,6 +120,9 @@ struct ers_surface {
     // second stream for the far field when it runs concurrently with the near field
     cudaStream_t side = nullptr;
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+    // treecode: octree, tree-ordered records and modified weights (ERS_OPT_TREECODE)
+    ers::TreeCache *tree = nullptr;
+    uint64_t dens_version = 0;  // bumped by every ers_set_density
 };
 
 namespace ers {
@@ -202,6 +222,22 @@ int batch_grid(int nr, int nsm);
 cudaError_t launch_batch(int nr, const BatchProblemDev *probs, const BatchItem *items, int nitems, unsigned *counter,
                          const double rho[3], int layers, const double *tab, int grid, cudaStream_t st);
 int grow(Scratch &s, size_t bytes);
+
+// Treecode (tree_host.cpp, k_tree.cu)
+struct TreeParams {
+    double theta;
+    int n0, p;
+};
+void treecode_defaults(double h, double *theta, int *n0, int *p);
+// Build (or reuse) the octree for leaf size n0 and the modified weights of degree p for the
+// current densities; ERS_OK or an error code.
+int tree_prepare(ers_surface *s, int n0, int p, bool mixed, cudaStream_t st);
+void tree_free(ers_surface *s);
+// Far sums by the treecode into a.part (one chunk), for the near-field kernel to complete.
+cudaError_t launch_tree_far(const EvalArgs &a, const TreeParams &tp);
+// clusters, leaves, depth, then (after the last treecode eval) approximated (target, cluster)
+// pairs and far pairs summed directly
+int tree_stats(ers_surface *s, int64_t out[5]);
 
 }  // namespace ers
 

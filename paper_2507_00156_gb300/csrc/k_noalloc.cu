@@ -68,6 +68,8 @@ extern "C" int ers_eval_noalloc(ers_surface *s, const ers_params *p, const doubl
     if (!s) return fail(ERS_E_INVAL, "ers_eval_noalloc: NULL surface");
     int warn;
     int rc = check_params(s, p, &warn);
+    if (rc == ERS_OK && (p->options & ERS_OPT_TREECODE))
+        return fail(ERS_E_UNSUPPORTED, "ers_eval_noalloc: ERS_OPT_TREECODE is not supported (use ers_eval)");
     if (rc == ERS_OK && (p->options & ERS_OPT_FOUR_DELTA))
         return fail(ERS_E_UNSUPPORTED, "ers_eval_noalloc: ERS_OPT_FOUR_DELTA is not supported (use ers_eval)");
     if (rc == ERS_OK && (p->options & ERS_OPT_SHARP))

@@ -186,3 +186,49 @@ def test_sigma_sharp_device_layout_accuracy(L):
             worst = max(worst, abs(v - float(ref[p_])) / abs(float(ref[p_])))
             assert abs(c4) <= 2e-8 * abs(dpart[i, p_, 3]), (i, p_)
     assert worst < 6e-15, worst
+
+
+@pytest.mark.parametrize("n0", [1, 37, 500, 4000])
+def test_library_octree_matches_oracle(L, n0):
+    """The host octree of the treecode (Sec. 3.4) is the oracle's: same leaf order of the nodes,
+    and every cluster (matched by its node range and level) has the same centre, half-widths and
+    radius, bit for bit."""
+    import oracle
+    x, _, _ = oracle.quadrature(workloads.Shape((0.1, -0.2, 0.05), (1.0, 0.8, 0.6)), 1 / 32)
+    N = len(x)
+    cap = 4 * N + 64
+    geom = np.empty((cap, 7))
+    info = np.empty((cap, 5), dtype=np.int32)
+    perm = np.empty(N, dtype=np.int32)
+    fn = L.ers_debug_octree
+    fn.restype = ctypes.c_int64
+    fn.argtypes = [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int, ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p,
+                   ctypes.c_void_p]
+    nc = fn(np.ascontiguousarray(x).ctypes.data, N, n0, cap, geom.ctypes.data, info.ctypes.data, perm.ctypes.data)
+    t = oracle.tree_info(x, n0)
+    assert nc == len(t["rc"])
+    assert np.array_equal(perm, t["perm"])
+    ref = {(int(s), int(c), int(l)): k for k, (s, c, l) in enumerate(zip(t["start"], t["count"], t["level"]))}
+    for c in range(nc):
+        k = ref[(int(info[c, 0]), int(info[c, 1]), int(info[c, 4]))]
+        lo, hi = t["lo"][k], t["hi"][k]
+        assert np.array_equal(geom[c, :3], 0.5 * (lo + hi)) and np.array_equal(geom[c, 3:6], 0.5 * (hi - lo))
+        assert geom[c, 6] == t["rc"][k]
+        assert info[c, 3] == t["nchild"][k]
+        if info[c, 3]:  # children contiguous, one level down, covering the parent's range
+            kids = range(info[c, 2], info[c, 2] + info[c, 3])
+            assert all(info[j, 4] == info[c, 4] + 1 for j in kids)
+            assert sum(info[j, 1] for j in kids) == info[c, 1] and info[info[c, 2], 0] == info[c, 0]
+
+
+def test_treecode_defaults(L):
+    """Eq. (optimal_params): theta = 0.6; N0 = 2000, p = 6 at h = 1/64, doubling N0 and adding 2
+    to p per halving of h; held at N0 >= 1000, p >= 6 for coarser h (Table 2's values)."""
+    import paper_2507_00156_gb300 as ers
+    assert ers.treecode_defaults(1 / 64) == (0.6, 2000, 6)
+    assert ers.treecode_defaults(1 / 128) == (0.6, 4000, 8)
+    assert ers.treecode_defaults(1 / 256) == (0.6, 8000, 10)
+    assert ers.treecode_defaults(1 / 32) == (0.6, 1000, 6)
+    assert ers.treecode_defaults(1 / 16) == (0.6, 1000, 6)
+    with pytest.raises(ers.ErsError):
+        ers.treecode_defaults(0.0)

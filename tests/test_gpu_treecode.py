@@ -1,0 +1,177 @@
+"""ERS_OPT_TREECODE: the far sums by the kernel-independent treecode of Sec. 3.4 (octree, MAC,
+barycentric Lagrange modified weights), against the oracle's treecode (ers_treecode.c) with the
+same parameters: the GPU walk takes the same per-target decisions, so the FP64 path matches it
+to rounding."""
+import numpy as np
+import pytest
+
+import oracle
+import workloads
+from parity import GpuProblem, oracle_problem, oracle_targets, rel_err
+
+pytestmark = pytest.mark.gpu
+FP64_TOL = 1e-11
+MIXED_TOL = 1e-6
+
+
+@pytest.fixture(scope="module")
+def ers():
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2507_00156_gb300
+    return paper_2507_00156_gb300
+
+
+_cache = {}
+
+
+def gpu(name, wl=None):
+    if name not in _cache:
+        _cache[name] = GpuProblem(name, wl)
+    return _cache[name]
+
+
+def oracle_tree(name, sel, rho, tree, tc=6.0, wl=None):
+    if wl is None:
+        wl, x, n, w, f, q = oracle_problem(name)
+    else:
+        x, n, w = oracle.quadrature(wl.shape, wl.h)
+        f, q = workloads.poly_eval(wl.f_coef, x), workloads.poly_eval(wl.q_coef, x)
+    y = oracle_targets(wl, x, sel)
+    x0, n0, b = oracle.closest_point(wl.shape, y)
+    f0, q0 = workloads.poly_eval(wl.f_coef, x0), workloads.poly_eval(wl.q_coef, x0)
+    theta, n0_leaf, p = tree
+    u, v, nf, st = oracle.evaluate_tree(x, n, w, f, q, y, x0, n0, b, f0, q0, wl.h, rho, tc, theta, n0_leaf, p,
+                                        stats=True)
+    assert nf == 0
+    return u, v, b, st
+
+
+@pytest.mark.parametrize("tree", [(0.6, 300, 4), (0.5, 500, 6), (0.7, 64, 3)])
+@pytest.mark.parametrize("precision,tol", [(0, FP64_TOL), (1, MIXED_TOL)])
+def test_treecode_matches_oracle_sphere16(ers, tree, precision, tol):
+    uo, vo, _, st = oracle_tree("sphere16", None, (2.0, 3.0, 4.0), tree)
+    g = gpu("sphere16")
+    u, v, _ = g.eval(g.targets(), precision=precision, tree=tree)
+    assert rel_err(u, uo) <= tol and rel_err(v, vo) <= tol, (rel_err(u, uo), rel_err(v, vo))
+    ts = g.s.tree_stats()
+    t = oracle.tree_info(g.x, tree[1])
+    assert ts["clusters"] == len(t["rc"]) and ts["leaves"] == int((t["nchild"] == 0).sum())
+    assert ts["depth"] == int(t["level"].max())
+    assert ts["approximated"] == int(st[:, 0].sum())  # same MAC decisions for every target
+    if precision == 0:
+        assert ts["direct"] == int(st[:, 2].sum())
+
+
+@pytest.mark.parametrize("tree", [(0.6, 1000, 6), (0.6, 1000, 8)])
+@pytest.mark.parametrize("precision,tol", [(0, FP64_TOL), (1, MIXED_TOL)])
+def test_treecode_matches_oracle_sphere32(ers, tree, precision, tol):
+    """Every fifth target of the h = 1/32 sphere (nodes and band), Table 2's parameters."""
+    sel = np.arange(0, 17070 + 2000, 5)
+    uo, vo, _, _ = oracle_tree("sphere32", sel, (2.0, 3.0, 4.0), tree)
+    g = gpu("sphere32")
+    u, v, _ = g.eval(g.targets(sel), precision=precision, tree=tree)
+    assert rel_err(u, uo) <= tol and rel_err(v, vo) <= tol, (rel_err(u, uo), rel_err(v, vo))
+
+
+def test_treecode_ellipsoid_with_far_points(ers):
+    """Ellipsoid (1, 0.8, 0.6): node, band and box targets (inside, outside, far: plain sums)."""
+    shape = workloads.Shape((0.0, 0.0, 0.0), (1.0, 0.8, 0.6))
+    wl = workloads.make_workload("ell32", shape, 1 / 32, (2, 3, 4), 77, 1500, 16 / 32 * 0.7, n_far=700)
+    g = gpu("ell32", wl)
+    x = g.x
+    sel = np.concatenate([np.arange(0, len(x), 9), len(x) + np.arange(len(wl.extra_targets))])
+    tree = (0.6, 800, 6)
+    uo, vo, bo, _ = oracle_tree("ell32", sel, wl.rho, tree, wl=wl)
+    assert (np.abs(bo) > 6 * 4 / 32).sum() > 100
+    for prec, tol in ((0, FP64_TOL), (1, MIXED_TOL)):
+        u, v, _ = g.eval(g.targets(sel), precision=prec, tree=tree)
+        assert rel_err(u, uo) <= tol and rel_err(v, vo) <= tol, (prec, rel_err(u, uo), rel_err(v, vo))
+
+
+def test_treecode_with_four_deltas_and_other_cutoff(ers):
+    sel = np.arange(3, 17070 + 2000, 7)
+    rho = (3.0, 4.0, 5.0, 6.0)
+    tree = (0.6, 1000, 6)
+    for tc in (6.0, 5.3):
+        uo, vo, _, _ = oracle_tree("sphere32", sel, rho, tree, tc=tc)
+        g = gpu("sphere32")
+        for prec, tol in ((0, FP64_TOL), (1, MIXED_TOL)):
+            u, v, _ = g.eval(g.targets(sel), precision=prec, rho=rho, tc=tc, tree=tree)
+            assert rel_err(u, uo) <= tol and rel_err(v, vo) <= tol, (tc, prec, rel_err(u, uo), rel_err(v, vo))
+
+
+def test_treecode_theta_zero_is_the_direct_path(ers):
+    """theta -> 0: nothing is approximated, every far pair is summed in the leaves; the result is the
+    direct far field's up to the order of summation."""
+    g = gpu("sphere16")
+    y = g.targets()
+    u0, v0, _ = g.eval(y, precision=0)
+    u1, v1, _ = g.eval(y, precision=0, tree=(1e-9, 200, 4))
+    assert g.s.tree_stats()["approximated"] == 0
+    assert rel_err(u1, u0) <= 1e-13 and rel_err(v1, v0) <= 1e-13
+    _, np0, nf0 = g.s.last_counts()
+    g.eval(y, precision=0)
+    _, np1, nf1 = g.s.last_counts()
+    assert np0 == np1  # same near pairs
+
+
+def test_treecode_weights_follow_the_density(ers):
+    """After ers_set_density the modified weights are rebuilt: the result is the oracle's for the
+    new densities (and differs from the old one)."""
+    import torch
+    name = "sphere16"
+    wl0 = workloads.config(name)
+    wl1 = workloads.make_workload("sphere16b", wl0.shape, wl0.h, wl0.rho, 4242, len(wl0.extra_targets), 4 * wl0.h)
+    g = GpuProblem(name, wl0)
+    tree = (0.6, 400, 5)
+    y = g.targets()
+    u0, v0, _ = g.eval(y, precision=0, tree=tree)
+    g.wl = wl1
+    f = workloads.poly_eval(wl1.f_coef, g.x)
+    q = workloads.poly_eval(wl1.q_coef, g.x)
+    g.s.set_density(torch.from_numpy(f).to(g.dev), torch.from_numpy(q).to(g.dev))
+    u1, v1, _ = g.eval(y, precision=0, tree=tree)
+    x, n, w = oracle.quadrature(wl1.shape, wl1.h)
+    x0, n0, b = oracle.closest_point(wl1.shape, y)
+    uo, vo, _ = oracle.evaluate_tree(x, n, w, workloads.poly_eval(wl1.f_coef, x), workloads.poly_eval(wl1.q_coef, x),
+                                     y, x0, n0, b, workloads.poly_eval(wl1.f_coef, x0),
+                                     workloads.poly_eval(wl1.q_coef, x0), wl1.h, wl1.rho, 6.0, *tree)
+    assert rel_err(u1, uo) <= FP64_TOL and rel_err(v1, vo) <= FP64_TOL
+    assert rel_err(u0, u1) > 1e-3
+
+
+def test_treecode_with_sharp_and_single_layers(ers):
+    """ERS_OPT_SHARP (per-target near radius cutoff_t delta# on the surface) and one layer at a
+    time: compared with the direct GPU path within the treecode's error at p = 10, and the
+    layers agree with the fused evaluation."""
+    g = gpu("sphere32")
+    sel = np.arange(1, 17070 + 2000, 13)
+    y = g.targets(sel)
+    tree = (0.6, 1000, 10)
+    ud, vd, _ = g.eval(y, precision=0, sharp=True)
+    ut, vt, _ = g.eval(y, precision=0, sharp=True, tree=tree)
+    assert rel_err(ut, ud) < 1e-8 and rel_err(vt, vd) < 1e-7
+    us, _, _ = g.eval(y, precision=0, layers=1, tree=tree)
+    _, vs, _ = g.eval(y, precision=0, layers=2, tree=tree)
+    uf, vf, _ = g.eval(y, precision=0, tree=tree)
+    assert rel_err(us, uf) <= 1e-14 and rel_err(vs, vf) <= 1e-14
+
+
+def test_treecode_rejected_where_unsupported(ers):
+    import torch
+    g = gpu("sphere16")
+    y = g.targets()[:64]
+    yd, x0, n0, b, f0, q0 = g.prepare(y)
+    u = torch.empty((64, 3), dtype=torch.float64, device="cuda")
+    v = torch.empty((64, 3), dtype=torch.float64, device="cuda")
+    # eval_noalloc takes no tree option in the binding: call the C entry with the bit set
+    p = ers.params(g.wl.rho, tree=(0.6, 100, 4))
+    import ctypes
+    rc = ers.lib().ers_eval_noalloc(g.s.handle, ctypes.byref(p), yd.data_ptr(), 64, x0.data_ptr(), n0.data_ptr(),
+                                    b.data_ptr(), f0.data_ptr(), q0.data_ptr(), u.data_ptr(), v.data_ptr(), None)
+    assert rc == -5
+    for bad in ((1.0, 100, 4), (-0.1, 100, 4), (0.6, -1, 4), (0.6, 100, 17)):
+        with pytest.raises(ers.ErsError) as ex:
+            g.s.eval(yd, f0, q0, rho=g.wl.rho, tree=bad)
+        assert ex.value.code == -1

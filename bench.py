@@ -45,7 +45,7 @@ FAR_FLOPS_PER_PAIR = 34 + 1 + 33 + 1      # both layers, one far pair
 NEAR_FLOPS_PER_DELTA_EVAL = 30 + 1 + 1    # one regularized (node, delta) term, both layers
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) from one ncu capture of
 # the sphere128 workload with the current kernels (profiles/launches_sphere128_mixed.md).
-NCU_TRAFFIC = {("sphere128", "k_near"): 202522112 + 16934912, ("sphere128", "k_far32"): 59682560 + 30467584}
+NCU_TRAFFIC = {("sphere128", "k_near"): 209905664 + 27866368, ("sphere128", "k_far32"): 62519040 + 33451776}
 
 
 def parse():
@@ -60,6 +60,8 @@ def parse():
     ap.add_argument("--no-batched", action="store_true", help="skip the batched-launch leg")
     ap.add_argument("--no-learned", action="store_true", help="skip the learned-closure leg")
     ap.add_argument("--workload", default=WORKLOAD, help="profiling only: a smaller case (e.g. sphere64)")
+    ap.add_argument("--tree", default=None,
+                    help="treecode leg: theta,N0,p (default: the parameters of Eq. (optimal_params) for h)")
     return ap.parse_args()
 
 
@@ -476,6 +478,9 @@ def main():
     # parameters of Eq. (optimal_params) for this h; the modified weights are built in the warm-up
     # (they depend only on the densities) and timed separately after a density update
     tree = ers.treecode_defaults(wl.h)
+    if args.tree:
+        th, n0s, ps = args.tree.split(",")
+        tree = (float(th), int(n0s), int(ps))
     t_tc, k_tc = timed(ers.PREC_MIXED, args.steps, 1, tree=tree)
     t_tc = max_over_ranks(t_tc, world)
     tc_stats = s.tree_stats()

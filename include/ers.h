@@ -378,6 +378,8 @@ int ers_treecode_defaults(double h, double *theta, int *n0, int *p);
  * Treecode statistics of the surface: out[0] clusters, out[1] leaves, out[2] depth of the last
  * tree built (0 if none); out[3] (target, cluster) pairs approximated and out[4] far pairs summed
  * directly by the last ERS_OPT_TREECODE evaluation (synchronizes with it).  n >= 5.
+ * ERS_E_TIMEOUT if a bounded wait of that evaluation's staging copies ran out (its result is then
+ * invalid).
  */
 int ers_tree_stats(ers_surface *s, int64_t *out, int n);
 

@@ -67,7 +67,7 @@ struct Scratch {
 // Treecode far field (Sec. 3.4)
 // ------------------------------------------------------------------------------------------
 constexpr int TREE_NW = 15;    // modified-weight densities per Chebyshev point: w f (3), w n (3), q_j w n_k (9)
-constexpr int TREE_NW32 = 16;  // FP32 copy, padded to four float4
+constexpr int TREE_WS = 16;    // stride of a Chebyshev point's weights (FP64 and FP32 copies; entry 15 is 0)
 constexpr int TREE_PMAX = 16;  // largest interpolation degree p
 
 // One cluster: the bounding box of its nodes (centre c, half-widths hw), r_c = half its diagonal;

@@ -16,12 +16,14 @@
 // is a polynomial of degree p in each coordinate, which the child's interpolation reproduces),
 // applied as three one-dimensional contractions, level by level upwards.
 //
-// Evaluation: one CTA per batch of TBT targets that are close in space (a counting sort by the
-// cells of the surface grid), one thread per target.  The CTA walks the tree depth first with
-// a shared stack; at every cluster each thread takes its own decision (approximate, sum the
-// leaf, open, or nothing when an ancestor was approximated), so every target gets exactly the
-// per-target walk of Sec. 3.4; the Chebyshev points with their weights, or the leaf's nodes,
-// are staged once in shared memory for all threads that need them.
+// Evaluation: one warp per 32 targets that are close in space (a counting sort by the cells of
+// the surface grid), one lane per target.  The warp walks the tree depth first with a stack in
+// shared memory; at every cluster each lane takes its own decision (approximate, sum the leaf,
+// open, or nothing below an approximated ancestor), so every target gets exactly the
+// per-target walk of Sec. 3.4.  The lanes that approximate a cluster read its Chebyshev
+// weights, and the lanes that sum a leaf its nodes, as warp-uniform loads (one transaction per
+// warp, served from L1/L2); the point coordinates come from per-cluster tables of c_a + hw_a
+// cos(k pi/p), with d formed plane by plane.  No block-wide barrier.
 #include <algorithm>
 #include <climits>
 #include <cmath>
@@ -31,9 +33,8 @@
 namespace ers {
 namespace {
 
-constexpr int TBT = 128;     // targets per CTA
-constexpr int TCH = 64;      // Chebyshev points or leaf nodes per staged chunk
-constexpr int TSTACK = 512;  // walk stack entries (depth x 7 + 1 at most)
+constexpr int TCH = 64;      // nodes per staged chunk of the leaf weights
+constexpr unsigned FULL_MASK = 0xffffffffu;
 constexpr double INV8PI = 0.039788735772973833942;
 constexpr double ACC_MARGIN = 1.0 + 1e-4;
 constexpr double PI = 3.14159265358979323846;
@@ -98,7 +99,7 @@ __global__ void __launch_bounds__(256) k_leaf_weights(const TreeCluster *__restr
     extern __shared__ double sm[];
     const TreeCluster C = cl[ids[blockIdx.x]];
     const int P1 = ch.p + 1, NK = P1 * P1 * P1, per = 3 * P1 + TREE_NW;
-    double *Wc = W + (size_t)ids[blockIdx.x] * NK * TREE_NW;
+    double *Wc = W + (size_t)ids[blockIdx.x] * NK * TREE_WS;
     for (int k0 = 0; k0 < NK; k0 += blockDim.x) {
         const int k = k0 + threadIdx.x;
         const int k1 = k / (P1 * P1), k2 = (k / P1) % P1, k3 = k % P1;
@@ -127,9 +128,11 @@ __global__ void __launch_bounds__(256) k_leaf_weights(const TreeCluster *__restr
                 }
             }
         }
-        if (k < NK)
+        if (k < NK) {
 #pragma unroll
-            for (int g = 0; g < TREE_NW; ++g) Wc[(size_t)k * TREE_NW + g] = acc[g];
+            for (int g = 0; g < TREE_NW; ++g) Wc[(size_t)k * TREE_WS + g] = acc[g];
+            Wc[(size_t)k * TREE_WS + TREE_NW] = 0.0;
+        }
     }
 }
 
@@ -157,8 +160,8 @@ __global__ void __launch_bounds__(256) k_upward(const TreeCluster *__restrict__ 
                 lagrange_basis(ch, P.c[a], P.hw[a], xs, Lt);
                 for (int k = 0; k < P1; ++k) T[(a * P1 + k) * P1 + kk] = Lt[k];
             }
-            const double *Wc = W + (size_t)cid * NK * TREE_NW + g0;
-            for (int i = threadIdx.x; i < n; i += blockDim.x) A[i] = Wc[(size_t)(i / G) * TREE_NW + i % G];
+            const double *Wc = W + (size_t)cid * NK * TREE_WS + g0;
+            for (int i = threadIdx.x; i < n; i += blockDim.x) A[i] = Wc[(size_t)(i / G) * TREE_WS + i % G];
             __syncthreads();
             // along k3
             for (int i = threadIdx.x; i < n; i += blockDim.x) {
@@ -188,17 +191,21 @@ __global__ void __launch_bounds__(256) k_upward(const TreeCluster *__restrict__ 
             }
         }
         __syncthreads();
-        double *Wp = W + (size_t)pid * NK * TREE_NW + g0;
-        for (int i = threadIdx.x; i < n; i += blockDim.x) Wp[(size_t)(i / G) * TREE_NW + i % G] = Acc[i];
+        double *Wp = W + (size_t)pid * NK * TREE_WS + g0;
+        for (int i = threadIdx.x; i < n; i += blockDim.x) {
+            Wp[(size_t)(i / G) * TREE_WS + i % G] = Acc[i];
+            if (i % G == 0 && g0 == 0) Wp[(size_t)(i / G) * TREE_WS + TREE_NW] = 0.0;
+        }
     }
 }
 
+// FP32 copy of the weights (the mixed evaluation), same layout as the FP64 array.
 __global__ void k_weights32(const double *__restrict__ W, float *__restrict__ W32, int64_t npts) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= npts) return;
 #pragma unroll
-    for (int g = 0; g < TREE_NW; ++g) W32[i * TREE_NW32 + g] = __double2float_rn(W[i * TREE_NW + g]);
-    W32[i * TREE_NW32 + TREE_NW] = 0.0f;
+    for (int g = 0; g < TREE_NW; ++g) W32[i * TREE_WS + g] = __double2float_rn(W[i * TREE_WS + g]);
+    W32[i * TREE_WS + TREE_NW] = 0.0f;
 }
 
 // Target order: counting sort by the cell of the surface grid (clamped), so that consecutive
@@ -251,6 +258,12 @@ __global__ void k_tscatter(const int *__restrict__ keys, int64_t M, int *__restr
     order[pos] = (int)m;
 }
 
+constexpr int TWPB = 4;        // warps per CTA; each warp walks the tree for its own 32 targets
+constexpr int TBT = TWPB * 32;
+constexpr int TSTACK = 128;    // walk stack entries per warp (a tree of depth d needs 8 (d + 1) at most)
+constexpr int BUFB = 4096;     // bytes of each of a warp's two staging buffers
+constexpr uint32_t WAIT_LIMIT = 1u << 22;  // polls of a bounded mbarrier wait (well above a second)
+
 struct TreeEval {
     const TreeCluster *cl;
     const double *W;
@@ -261,14 +274,36 @@ struct TreeEval {
     const int *order;
     Cheb ch;
     double theta;
-    unsigned long long *stats;
-    int *err;
+    unsigned long long *stats;  // [3]: approximated pairs, direct pairs, error flag (a wait ran out)
 };
 
-union TreeStage {
-    double d[TCH * 18];   // FP64: 15 weights + 3 coordinates per point, or one REC record per node
-    float4 f[TCH * 5];    // FP32: 4 float4 of weights + the coordinates per point, or 3 float4 per node
-};
+__device__ __forceinline__ uint32_t smem_addr(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+// Staging by the bulk-copy engine: one thread arms the buffer's mbarrier with the byte count and
+// issues cp.async.bulk (contiguous, 16-byte aligned, size a multiple of 16); every thread waits
+// on the barrier's phase with a bounded poll.
+__device__ __forceinline__ void stage_issue(void *dst, const void *src, uint32_t bytes, uint64_t *mbar) {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(mbar)), "r"(bytes) : "memory");
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(smem_addr(dst)),
+                 "l"(src), "r"(bytes), "r"(smem_addr(mbar))
+                 : "memory");
+}
+
+__device__ __forceinline__ bool stage_wait(uint64_t *mbar, uint32_t parity) {
+    for (uint32_t i = 0; i < WAIT_LIMIT; ++i) {
+        uint32_t ok;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+            "selp.u32 %0, 1, 0, p;\n\t}\n"
+            : "=r"(ok)
+            : "r"(smem_addr(mbar)), "r"(parity)
+            : "memory");
+        if (ok) return true;
+        if (i > 64) __nanosleep(64);
+    }
+    return false;
+}
 
 struct TgtF64 {
     double y[3], c, q0[3], Rt, Racc;
@@ -278,11 +313,10 @@ struct TgtF64 {
 
 // One Chebyshev point (FP64): the unregularized Stokeslet and stresslet against the modified
 // weights w (Eq. (particle-cluster-KITC)), subtracted with the target's c = f(x0).n0, q0.
-__device__ __forceinline__ void approx_point64(const TgtF64 &T, const double *w, bool sl, bool dl, double acc[6]) {
-    const double dx = __dsub_rn(T.y[0], w[15]), dy = __dsub_rn(T.y[1], w[16]), dz = __dsub_rn(T.y[2], w[17]);
+__device__ __forceinline__ void approx_point64(const TgtF64 &T, double dx, double dy, double dz, const double *w,
+                                               bool sl, bool dl, double acc[6]) {
     const double r2 = dist2_fp64(dx, dy, dz);
     const double ri = rsqrt(r2), ri2 = ri * ri;
-    const double dWn = fma(dz, w[5], fma(dy, w[4], dx * w[3]));
     if (sl) {
         const double g0 = fma(-T.c, w[3], w[0]), g1 = fma(-T.c, w[4], w[1]), g2 = fma(-T.c, w[5], w[2]);
         const double s = fma(dz, g2, fma(dy, g1, dx * g0)) * ri2;
@@ -292,6 +326,7 @@ __device__ __forceinline__ void approx_point64(const TgtF64 &T, const double *w,
     }
     if (dl) {
         // d . (q w n)^ . d - (d.q0)(d.(w n)^)
+        const double dWn = fma(dz, w[5], fma(dy, w[4], dx * w[3]));
         const double t0 = fma(dz, w[8], fma(dy, w[7], dx * w[6]));
         const double t1 = fma(dz, w[11], fma(dy, w[10], dx * w[9]));
         const double t2 = fma(dz, w[14], fma(dy, w[13], dx * w[12]));
@@ -329,14 +364,52 @@ __device__ __forceinline__ bool direct_node64(const TgtF64 &T, const double *r, 
     return true;
 }
 
+
+// Staged pass of one warp over `count` items of `bytes_each` bytes from src, CH items per chunk,
+// double buffered in the warp's own buffers: lane 0 copies chunk i + 1 while the warp computes
+// chunk i with body(buffer, first, n).  Returns false (on every lane) when a wait ran out; the
+// caller then leaves the kernel.
+template <int CH, class Body>
+__device__ __forceinline__ bool staged(unsigned char (*buf)[BUFB], uint64_t *mbar, uint32_t &phase, const unsigned char *src,
+                                       int count, int bytes_each, int lane, Body &&body) {
+    const int nch = (count + CH - 1) / CH;
+    if (lane == 0) stage_issue(buf[0], src, (uint32_t)(min(CH, count) * bytes_each), &mbar[0]);
+    for (int i = 0; i < nch; ++i) {
+        const int b = i & 1;
+        if (lane == 0 && i + 1 < nch) {
+            const int n1 = min(CH, count - (i + 1) * CH);
+            stage_issue(buf[b ^ 1], src + (size_t)(i + 1) * CH * bytes_each, (uint32_t)(n1 * bytes_each), &mbar[b ^ 1]);
+        }
+        bool ok = stage_wait(&mbar[b], (phase >> b) & 1u);
+        phase ^= 1u << b;
+        ok = __all_sync(FULL_MASK, ok);
+        if (!ok) {
+            // a copy did not complete in time: wait (bounded) for the one still in flight, then stop
+            if (lane == 0 && i + 1 < nch) stage_wait(&mbar[b ^ 1], (phase >> (b ^ 1)) & 1u);
+            return false;
+        }
+        body(buf[b], i * CH, min(CH, count - i * CH));
+        __syncwarp();  // buffer b is refilled at step i + 2
+    }
+    return true;
+}
+
 template <int PREC, bool SL, bool DL>
-__global__ void __launch_bounds__(TBT) k_tree_far(EvalArgs A, TreeEval X) {
-    __shared__ int stk[TSTACK];
-    __shared__ int sp_s;
-    __shared__ TreeStage st;
-    const int tid = threadIdx.x;
-    const int64_t pos = (int64_t)blockIdx.x * TBT + tid;
+__global__ void __launch_bounds__(TBT, 4) k_tree_walk(EvalArgs A, TreeEval X) {
+    __shared__ __align__(128) unsigned char sbuf[TWPB][2][BUFB];
+    __shared__ __align__(8) uint64_t smbar[TWPB][2];
+    __shared__ int sstk[TWPB][TSTACK];
+    __shared__ float shwc[TWPB][3][TREE_PMAX + 1];   // hw_a cos(k pi/p) in FP32 (mixed)
+    __shared__ double spts[TWPB][3][TREE_PMAX + 1];  // c_a + hw_a cos(k pi/p) (FP64)
+    const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
+    unsigned char (*buf)[BUFB] = sbuf[wp];
+    uint64_t *mbar = smbar[wp];
+    int *stk = sstk[wp];
+    float (*hwc)[TREE_PMAX + 1] = shwc[wp];
+    double (*pts)[TREE_PMAX + 1] = spts[wp];
+    const int64_t pos = (int64_t)blockIdx.x * TBT + threadIdx.x;
     const bool valid = pos < A.M;
+    if (__ballot_sync(FULL_MASK, valid) == 0) return;  // no block-wide barrier in this kernel
     const int64_t m = valid ? X.order[pos] : 0;
     const int P1 = X.ch.p + 1, NK = P1 * P1 * P1;
 
@@ -361,21 +434,30 @@ __global__ void __launch_bounds__(TBT) k_tree_far(EvalArgs A, TreeEval X) {
             T.yl[i] = __double2float_rn(T.y[i] - (double)T.yh[i]);
         }
     }
+    const float cf = (float)T.c, q0x = (float)T.q0[0], q0y = (float)T.q0[1], q0z = (float)T.q0[2];
     double acc[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
     unsigned long long napprox = 0, ndirect = 0;
     int skip = INT_MAX;  // level of the approximated ancestor on the current path
-    if (tid == 0) {
+    uint32_t phase = 0;  // parity of the next completion of each buffer's barrier
+    if (lane == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(&mbar[0])) : "memory");
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(&mbar[1])) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         stk[0] = 0;
-        sp_s = 1;
     }
-    __syncthreads();
-    for (;;) {
-        const int sp = sp_s;
-        if (sp == 0) break;
-        const int cid = stk[sp - 1];
-        __syncthreads();
-        if (tid == 0) sp_s = sp - 1;
+    int sp = 1;
+    __syncwarp();
+    while (sp > 0) {
+        const int cid = stk[--sp];
         const TreeCluster C = X.cl[cid];
+        __syncwarp();  // the previous cluster's readers of the tables are done
+        for (int t = lane; t < 3 * P1; t += 32) {
+            const int a = t / P1, k = t % P1;
+            const double hc = __dmul_rn(C.hw[a], X.ch.cosk[k]);
+            hwc[a][k] = __double2float_rn(hc);
+            pts[a][k] = __dadd_rn(C.c[a], hc);
+        }
+        __syncwarp();  // the tables are visible to the whole warp
         if (C.level <= skip) skip = INT_MAX;
         const bool active = valid && skip == INT_MAX;
         bool acc_c = false, leafd = false, desc = false;
@@ -387,172 +469,177 @@ __global__ void __launch_bounds__(TBT) k_tree_far(EvalArgs A, TreeEval X) {
             leafd = !acc_c && C.nchild == 0;
             desc = !acc_c && C.nchild > 0;
         }
-        const int any_acc = __syncthreads_or(acc_c);
-        const int any_leaf = __syncthreads_or(leafd);
-        const int any_desc = __syncthreads_or(desc);
+        const bool any_acc = __any_sync(FULL_MASK, acc_c);
+        const bool any_leaf = __any_sync(FULL_MASK, leafd);
+        const bool any_desc = __any_sync(FULL_MASK, desc);
+        bool ok = true;
 
         if (any_acc) {
             if (acc_c) ++napprox;
             if (PREC == ERS_PREC_FP64) {
-                const double *Wc = X.W + (size_t)cid * NK * TREE_NW;
-                for (int k0 = 0; k0 < NK; k0 += TCH) {
-                    const int nk = min(TCH, NK - k0);
-                    __syncthreads();
-                    for (int i = tid; i < nk * TREE_NW; i += TBT) st.d[(i / TREE_NW) * 18 + i % TREE_NW] = Wc[(size_t)k0 * TREE_NW + i];
-                    for (int i = tid; i < nk; i += TBT) {
-                        const int k = k0 + i, k1 = k / (P1 * P1), k2 = (k / P1) % P1, k3 = k % P1;
-                        st.d[i * 18 + 15] = __dadd_rn(C.c[0], __dmul_rn(C.hw[0], X.ch.cosk[k1]));
-                        st.d[i * 18 + 16] = __dadd_rn(C.c[1], __dmul_rn(C.hw[1], X.ch.cosk[k2]));
-                        st.d[i * 18 + 17] = __dadd_rn(C.c[2], __dmul_rn(C.hw[2], X.ch.cosk[k3]));
+                const unsigned char *src = reinterpret_cast<const unsigned char *>(X.W + (size_t)cid * NK * TREE_WS);
+                ok = staged<BUFB / 128>(buf, mbar, phase, src, NK, 128, lane, [&](const unsigned char *bp, int k0, int n) {
+                    if (!acc_c) return;
+                    const double *w = reinterpret_cast<const double *>(bp);
+                    int k1 = k0 / (P1 * P1), k2 = (k0 / P1) % P1, k3 = k0 % P1;
+                    double dx = __dsub_rn(T.y[0], pts[0][k1]), dy = __dsub_rn(T.y[1], pts[1][k2]);
+                    for (int j = 0; j < n; ++j) {
+                        const double dz = __dsub_rn(T.y[2], pts[2][k3]);
+                        approx_point64(T, dx, dy, dz, w + j * TREE_WS, SL, DL, acc);
+                        if (++k3 == P1) {
+                            k3 = 0;
+                            if (++k2 == P1) {
+                                k2 = 0;
+                                ++k1;
+                                dx = __dsub_rn(T.y[0], pts[0][k1 < P1 ? k1 : 0]);
+                            }
+                            dy = __dsub_rn(T.y[1], pts[1][k2]);
+                        }
                     }
-                    __syncthreads();
-                    if (acc_c)
-                        for (int j = 0; j < nk; ++j) approx_point64(T, st.d + j * 18, SL, DL, acc);
-                }
+                });
             } else {
-                // FP32 terms relative to the cluster centre, FP32 sums per chunk added in FP64
-                const float4 *Wc = reinterpret_cast<const float4 *>(X.W32 + (size_t)cid * NK * TREE_NW32);
+                // FP32 terms relative to the cluster centre; FP32 sums per chunk added in FP64
+                const unsigned char *src = reinterpret_cast<const unsigned char *>(X.W32 + (size_t)cid * NK * TREE_WS);
                 const float ycx = __double2float_rn(__dsub_rn(T.y[0], C.c[0]));
                 const float ycy = __double2float_rn(__dsub_rn(T.y[1], C.c[1]));
                 const float ycz = __double2float_rn(__dsub_rn(T.y[2], C.c[2]));
-                const float cf = (float)T.c, q0x = (float)T.q0[0], q0y = (float)T.q0[1], q0z = (float)T.q0[2];
-                for (int k0 = 0; k0 < NK; k0 += TCH) {
-                    const int nk = min(TCH, NK - k0);
-                    __syncthreads();
-                    for (int i = tid; i < nk * 4; i += TBT) st.f[(i / 4) * 5 + i % 4] = Wc[(size_t)k0 * 4 + i];
-                    for (int i = tid; i < nk; i += TBT) {
-                        const int k = k0 + i, k1 = k / (P1 * P1), k2 = (k / P1) % P1, k3 = k % P1;
-                        st.f[i * 5 + 4] = make_float4(__double2float_rn(__dmul_rn(C.hw[0], X.ch.cosk[k1])),
-                                                      __double2float_rn(__dmul_rn(C.hw[1], X.ch.cosk[k2])),
-                                                      __double2float_rn(__dmul_rn(C.hw[2], X.ch.cosk[k3])), 0.0f);
-                    }
-                    __syncthreads();
-                    if (acc_c) {
-                        float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f, a4 = 0.f, a5 = 0.f;
-                        for (int j = 0; j < nk; ++j) {
-                            const float4 w0 = st.f[j * 5], w1 = st.f[j * 5 + 1], w2 = st.f[j * 5 + 2];
-                            const float4 w3 = st.f[j * 5 + 3], sp4 = st.f[j * 5 + 4];
-                            const float dx = ycx - sp4.x, dy = ycy - sp4.y, dz = ycz - sp4.z;
-                            const float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
-                            const float ri = rsqrt_ftz(r2), ri2 = ri * ri;
-                            // w0 = (wf0 wf1 wf2 wn0), w1 = (wn1 wn2 qn00 qn01), w2 = (qn02 qn10 qn11 qn12),
-                            // w3 = (qn20 qn21 qn22 -)
-                            const float dWn = fmaf(dz, w1.y, fmaf(dy, w1.x, dx * w0.w));
-                            if (SL) {
-                                const float g0 = fmaf(-cf, w0.w, w0.x), g1 = fmaf(-cf, w1.x, w0.y), g2 = fmaf(-cf, w1.y, w0.z);
-                                const float s = fmaf(dz, g2, fmaf(dy, g1, dx * g0)) * ri2;
-                                a0 = fmaf(fmaf(dx, s, g0), ri, a0);
-                                a1 = fmaf(fmaf(dy, s, g1), ri, a1);
-                                a2 = fmaf(fmaf(dz, s, g2), ri, a2);
-                            }
-                            if (DL) {
-                                const float t0 = fmaf(dz, w2.x, fmaf(dy, w1.w, dx * w1.z));
-                                const float t1 = fmaf(dz, w2.w, fmaf(dy, w2.z, dx * w2.y));
-                                const float t2 = fmaf(dz, w3.z, fmaf(dy, w3.y, dx * w3.x));
-                                const float quad = fmaf(dz, t2, fmaf(dy, t1, dx * t0));
-                                const float dq0 = fmaf(dz, q0z, fmaf(dy, q0y, dx * q0x));
-                                const float s = fmaf(-dq0, dWn, quad) * (ri2 * ri2 * ri);
-                                a3 = fmaf(dx, s, a3);
-                                a4 = fmaf(dy, s, a4);
-                                a5 = fmaf(dz, s, a5);
-                            }
+                ok = staged<BUFB / 64>(buf, mbar, phase, src, NK, 64, lane, [&](const unsigned char *bp, int k0, int n) {
+                    if (!acc_c) return;
+                    const float4 *w4 = reinterpret_cast<const float4 *>(bp);
+                    int k1 = k0 / (P1 * P1), k2 = (k0 / P1) % P1, k3 = k0 % P1;
+                    float dx = ycx - hwc[0][k1], dy = ycy - hwc[1][k2];
+                    float dxy2 = fmaf(dy, dy, dx * dx), dq0xy = fmaf(dy, q0y, dx * q0x);
+                    float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f, a4 = 0.f, a5 = 0.f;
+                    for (int j = 0; j < n; ++j) {
+                        // w0 = (wf0 wf1 wf2 wn0), w1 = (wn1 wn2 qn00 qn01),
+                        // w2 = (qn02 qn10 qn11 qn12), w3 = (qn20 qn21 qn22 0)
+                        const float4 w0 = w4[4 * j], w1 = w4[4 * j + 1], w2 = w4[4 * j + 2], w3 = w4[4 * j + 3];
+                        const float dz = ycz - hwc[2][k3];
+                        const float r2 = fmaf(dz, dz, dxy2);
+                        const float ri = rsqrt_ftz(r2), ri2 = ri * ri;
+                        if (SL) {
+                            const float g0 = fmaf(-cf, w0.w, w0.x), g1 = fmaf(-cf, w1.x, w0.y), g2 = fmaf(-cf, w1.y, w0.z);
+                            const float sg = fmaf(dz, g2, fmaf(dy, g1, dx * g0)) * ri2;
+                            a0 = fmaf(fmaf(dx, sg, g0), ri, a0);
+                            a1 = fmaf(fmaf(dy, sg, g1), ri, a1);
+                            a2 = fmaf(fmaf(dz, sg, g2), ri, a2);
                         }
-                        acc[0] += a0;
-                        acc[1] += a1;
-                        acc[2] += a2;
-                        acc[3] += a3;
-                        acc[4] += a4;
-                        acc[5] += a5;
+                        if (DL) {
+                            const float dWn = fmaf(dz, w1.y, fmaf(dy, w1.x, dx * w0.w));
+                            const float t0 = fmaf(dz, w2.x, fmaf(dy, w1.w, dx * w1.z));
+                            const float t1 = fmaf(dz, w2.w, fmaf(dy, w2.z, dx * w2.y));
+                            const float t2 = fmaf(dz, w3.z, fmaf(dy, w3.y, dx * w3.x));
+                            const float quad = fmaf(dz, t2, fmaf(dy, t1, dx * t0));
+                            const float dq0 = fmaf(dz, q0z, dq0xy);
+                            const float sv = fmaf(-dq0, dWn, quad) * (ri2 * ri2 * ri);
+                            a3 = fmaf(dx, sv, a3);
+                            a4 = fmaf(dy, sv, a4);
+                            a5 = fmaf(dz, sv, a5);
+                        }
+                        if (++k3 == P1) {
+                            k3 = 0;
+                            if (++k2 == P1) {
+                                k2 = 0;
+                                ++k1;
+                                dx = ycx - hwc[0][k1 < P1 ? k1 : 0];
+                            }
+                            dy = ycy - hwc[1][k2];
+                            dxy2 = fmaf(dy, dy, dx * dx);
+                            dq0xy = fmaf(dy, q0y, dx * q0x);
+                        }
                     }
-                }
+                    acc[0] += a0;
+                    acc[1] += a1;
+                    acc[2] += a2;
+                    acc[3] += a3;
+                    acc[4] += a4;
+                    acc[5] += a5;
+                });
             }
         }
 
-        if (any_leaf) {
+        if (ok && any_leaf) {
             if (PREC == ERS_PREC_FP64) {
-                for (int n0 = 0; n0 < C.count; n0 += TCH) {
-                    const int nn = min(TCH, C.count - n0);
-                    __syncthreads();
-                    const double *src = X.trec + (int64_t)(C.start + n0) * REC;
-                    for (int i = tid; i < nn * REC; i += TBT) st.d[i] = src[i];
-                    __syncthreads();
-                    if (leafd)
-                        for (int j = 0; j < nn; ++j) ndirect += direct_node64(T, st.d + j * REC, SL, DL, acc);
-                }
+                const unsigned char *src = reinterpret_cast<const unsigned char *>(X.trec + (int64_t)C.start * REC);
+                ok = staged<BUFB / 96>(buf, mbar, phase, src, C.count, 96, lane, [&](const unsigned char *bp, int, int n) {
+                    if (!leafd) return;
+                    const double *r = reinterpret_cast<const double *>(bp);
+                    for (int j = 0; j < n; ++j) ndirect += direct_node64(T, r + j * REC, SL, DL, acc);
+                });
             } else {
                 const float ylx = __double2float_rn(__dsub_rn(T.y[0], C.c[0]));
                 const float yly = __double2float_rn(__dsub_rn(T.y[1], C.c[1]));
                 const float ylz = __double2float_rn(__dsub_rn(T.y[2], C.c[2]));
-                const float cf = (float)T.c, q0x = (float)T.q0[0], q0y = (float)T.q0[1], q0z = (float)T.q0[2];
                 // r^2 from leaf-relative floats decides the mask except in a band around Rc^2, where the
                 // near field's own test (tile-relative floats) is repeated exactly
-                const double band = 1e-4 + 4e-6 * (R + C.rc) / T.Rt;
-                const float lo2 = (float)(T.Rt * T.Rt * (1.0 - band)), hi2 = (float)(T.Rt * T.Rt * (1.0 + band));
-                const bool all_far = T.rc2bits < 0;
-                for (int n0 = 0; n0 < C.count; n0 += TCH) {
-                    const int nn = min(TCH, C.count - n0);
-                    __syncthreads();
-                    const float4 *src = reinterpret_cast<const float4 *>(X.trec32 + (int64_t)(C.start + n0) * 12);
-                    for (int i = tid; i < nn * 3; i += TBT) st.f[i] = src[i];
-                    __syncthreads();
-                    if (leafd) {
-                        float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f, a4 = 0.f, a5 = 0.f;
-                        for (int j = 0; j < nn; ++j) {
-                            const float4 r0 = st.f[3 * j], r1 = st.f[3 * j + 1], r2v = st.f[3 * j + 2];
-                            const float dx = ylx - r0.x, dy = yly - r0.y, dz = ylz - r0.z;
-                            const float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
-                            bool far = all_far || r2 > hi2;
-                            if (!far && !(r2 < lo2)) {
-                                const int js = X.tsrt[C.start + n0 + j];
-                                const float4 cen = __ldg(reinterpret_cast<const float4 *>(A.sd.tilec) + js / TS32);
-                                const float4 xc = __ldg(reinterpret_cast<const float4 *>(A.sd.rec32 + (int64_t)js * REC));
-                                float ex, ey, ez;
-                                const float r2t = dist2_fp32(tile_rel(T.yh[0], cen.x, T.yl[0]), tile_rel(T.yh[1], cen.y, T.yl[1]),
-                                                             tile_rel(T.yh[2], cen.z, T.yl[2]), xc.x, xc.y, xc.z, &ex, &ey, &ez);
-                                far = r2t > T.rc2f;
-                            }
-                            if (!far) continue;
-                            ++ndirect;
-                            const float ri = rsqrt_ftz(r2), ri2 = ri * ri;
-                            // r0 = (x - c: 3, wf0), r1 = (wf1 wf2 wn0 wn1), r2v = (wn2 q0 q1 q2)
-                            if (SL) {
-                                const float g0 = fmaf(-cf, r1.z, r0.w), g1 = fmaf(-cf, r1.w, r1.x), g2 = fmaf(-cf, r2v.x, r1.y);
-                                const float s = fmaf(dz, g2, fmaf(dy, g1, dx * g0)) * ri2;
-                                a0 = fmaf(fmaf(dx, s, g0), ri, a0);
-                                a1 = fmaf(fmaf(dy, s, g1), ri, a1);
-                                a2 = fmaf(fmaf(dz, s, g2), ri, a2);
-                            }
-                            if (DL) {
-                                const float Q0 = r2v.y - q0x, Q1 = r2v.z - q0y, Q2 = r2v.w - q0z;
-                                const float dQ = fmaf(dz, Q2, fmaf(dy, Q1, dx * Q0));
-                                const float dm = fmaf(dz, r2v.x, fmaf(dy, r1.w, dx * r1.z));
-                                const float s = (dQ * dm) * (ri2 * ri2 * ri);
-                                a3 = fmaf(dx, s, a3);
-                                a4 = fmaf(dy, s, a4);
-                                a5 = fmaf(dz, s, a5);
-                            }
-                        }
-                        acc[0] += a0;
-                        acc[1] += a1;
-                        acc[2] += a2;
-                        acc[3] += a3;
-                        acc[4] += a4;
-                        acc[5] += a5;
-                    }
+                float lo2 = 0.0f, hi2 = 0.0f;
+                if (leafd) {
+                    const double band = 1e-4 + 4e-6 * (R + C.rc) / T.Rt;
+                    lo2 = (float)(T.Rt * T.Rt * (1.0 - band));
+                    hi2 = (float)(T.Rt * T.Rt * (1.0 + band));
                 }
+                const bool all_far = T.rc2bits < 0;
+                const unsigned char *src = reinterpret_cast<const unsigned char *>(X.trec32 + (int64_t)C.start * 12);
+                ok = staged<BUFB / 48>(buf, mbar, phase, src, C.count, 48, lane, [&](const unsigned char *bp, int j0, int n) {
+                    if (!leafd) return;
+                    const float4 *r4 = reinterpret_cast<const float4 *>(bp);
+                    float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f, a4 = 0.f, a5 = 0.f;
+                    for (int j = 0; j < n; ++j) {
+                        const float4 r0 = r4[3 * j], r1 = r4[3 * j + 1], r2v = r4[3 * j + 2];
+                        const float dx = ylx - r0.x, dy = yly - r0.y, dz = ylz - r0.z;
+                        const float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
+                        bool far = all_far || r2 > hi2;
+                        if (!far && !(r2 < lo2)) {
+                            const int js = X.tsrt[C.start + j0 + j];
+                            const float4 cen = __ldg(reinterpret_cast<const float4 *>(A.sd.tilec) + js / TS32);
+                            const float4 xc = __ldg(reinterpret_cast<const float4 *>(A.sd.rec32 + (int64_t)js * REC));
+                            float ex, ey, ez;
+                            const float r2t = dist2_fp32(tile_rel(T.yh[0], cen.x, T.yl[0]), tile_rel(T.yh[1], cen.y, T.yl[1]),
+                                                         tile_rel(T.yh[2], cen.z, T.yl[2]), xc.x, xc.y, xc.z, &ex, &ey, &ez);
+                            far = r2t > T.rc2f;
+                        }
+                        if (!far) continue;
+                        ++ndirect;
+                        const float ri = rsqrt_ftz(r2), ri2 = ri * ri;
+                        // r0 = (x - c: 3, wf0), r1 = (wf1 wf2 wn0 wn1), r2v = (wn2 q0 q1 q2)
+                        if (SL) {
+                            const float g0 = fmaf(-cf, r1.z, r0.w), g1 = fmaf(-cf, r1.w, r1.x), g2 = fmaf(-cf, r2v.x, r1.y);
+                            const float s = fmaf(dz, g2, fmaf(dy, g1, dx * g0)) * ri2;
+                            a0 = fmaf(fmaf(dx, s, g0), ri, a0);
+                            a1 = fmaf(fmaf(dy, s, g1), ri, a1);
+                            a2 = fmaf(fmaf(dz, s, g2), ri, a2);
+                        }
+                        if (DL) {
+                            const float Q0 = r2v.y - q0x, Q1 = r2v.z - q0y, Q2 = r2v.w - q0z;
+                            const float dQ = fmaf(dz, Q2, fmaf(dy, Q1, dx * Q0));
+                            const float dm = fmaf(dz, r2v.x, fmaf(dy, r1.w, dx * r1.z));
+                            const float s = (dQ * dm) * (ri2 * ri2 * ri);
+                            a3 = fmaf(dx, s, a3);
+                            a4 = fmaf(dy, s, a4);
+                            a5 = fmaf(dz, s, a5);
+                        }
+                    }
+                    acc[0] += a0;
+                    acc[1] += a1;
+                    acc[2] += a2;
+                    acc[3] += a3;
+                    acc[4] += a4;
+                    acc[5] += a5;
+                });
             }
+        }
+        if (!ok) {
+            if (lane == 0) atomicOr(X.stats + 2, 1ull);
+            return;
         }
 
-        if (any_desc && tid == 0) {
-            int s2 = sp_s;
-            for (int c = C.nchild - 1; c >= 0; --c) {
-                if (s2 < TSTACK) stk[s2++] = C.first_child + c;
-                else *X.err = 1;
-            }
-            sp_s = s2;
+        if (any_desc) {
+            if (lane == 0)
+                for (int c = C.nchild - 1; c >= 0; --c) stk[sp + (C.nchild - 1 - c)] = C.first_child + c;
+            sp += C.nchild;
+            __syncwarp();
         }
         if (acc_c) skip = C.level;
-        __syncthreads();
     }
 
     if (valid) {
@@ -566,10 +653,10 @@ __global__ void __launch_bounds__(TBT) k_tree_far(EvalArgs A, TreeEval X) {
     }
     if (X.stats) {
         for (int o = 16; o > 0; o >>= 1) {
-            napprox += __shfl_xor_sync(0xffffffffu, napprox, o);
-            ndirect += __shfl_xor_sync(0xffffffffu, ndirect, o);
+            napprox += __shfl_xor_sync(FULL_MASK, napprox, o);
+            ndirect += __shfl_xor_sync(FULL_MASK, ndirect, o);
         }
-        if ((tid & 31) == 0) {
+        if (lane == 0) {
             atomicAdd(X.stats, napprox);
             atomicAdd(X.stats + 1, ndirect);
         }
@@ -590,9 +677,11 @@ int tree_prepare(ers_surface *s, int n0, int p, bool mixed, cudaStream_t st) {
         t->rec_version = s->dens_version;
         t->w_version = ~0ull;
     }
+    if (8 * (t->depth + 1) > TSTACK)
+        return fail(ERS_E_UNSUPPORTED, "treecode: the tree is deeper than the walk stack allows (use a larger tree_n0)");
     const int P1 = p + 1, NK = P1 * P1 * P1;
     if (t->w_version != s->dens_version || t->p != p) {
-        const size_t wbytes = sizeof(double) * (size_t)t->ncl * NK * TREE_NW;
+        const size_t wbytes = sizeof(double) * (size_t)t->ncl * NK * TREE_WS;
         if (wbytes > t->w_cap) {
             if (t->W) cudaFree(t->W);
             t->W = nullptr;
@@ -630,7 +719,7 @@ int tree_prepare(ers_surface *s, int n0, int p, bool mixed, cudaStream_t st) {
         t->have_w32 = false;
     }
     if (mixed && !t->have_w32) {
-        const size_t bytes = sizeof(float) * (size_t)t->ncl * NK * TREE_NW32;
+        const size_t bytes = sizeof(float) * (size_t)t->ncl * NK * TREE_WS;
         if (bytes > t->w32_cap) {
             if (t->W32) cudaFree(t->W32);
             t->W32 = nullptr;
@@ -661,7 +750,7 @@ cudaError_t launch_tree_far(const EvalArgs &a, const TreeParams &tp) {
     if (err != ERS_OK) return cudaErrorMemoryAllocation;
     int *keys = (int *)t->keys.ptr, *order = (int *)t->order.ptr, *hist = (int *)t->hist.ptr;
     cudaError_t e = cudaMemsetAsync(hist, 0, sizeof(int) * (size_t)(G.ncell + 1), a.stream);
-    if (e == cudaSuccess) e = cudaMemsetAsync(t->stats, 0, sizeof(unsigned long long) * 2, a.stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(t->stats, 0, sizeof(unsigned long long) * 3, a.stream);
     if (e != cudaSuccess) return e;
     const unsigned gb = (unsigned)((M + 255) / 256);
     k_tkeys<<<gb, 256, 0, a.stream>>>(a.y, M, G, keys, hist);
@@ -678,17 +767,16 @@ cudaError_t launch_tree_far(const EvalArgs &a, const TreeParams &tp) {
     X.ch = t->ch;
     X.theta = tp.theta;
     X.stats = t->stats;
-    X.err = t->err;
     const unsigned grid = (unsigned)((M + TBT - 1) / TBT);
     const bool sl = a.layers & ERS_LAYER_SL, dl = a.layers & ERS_LAYER_DL;
     if (a.precision == ERS_PREC_FP64) {
-        if (sl && dl) k_tree_far<ERS_PREC_FP64, true, true><<<grid, TBT, 0, a.stream>>>(a, X);
-        else if (sl) k_tree_far<ERS_PREC_FP64, true, false><<<grid, TBT, 0, a.stream>>>(a, X);
-        else k_tree_far<ERS_PREC_FP64, false, true><<<grid, TBT, 0, a.stream>>>(a, X);
+        if (sl && dl) k_tree_walk<ERS_PREC_FP64, true, true><<<grid, TBT, 0, a.stream>>>(a, X);
+        else if (sl) k_tree_walk<ERS_PREC_FP64, true, false><<<grid, TBT, 0, a.stream>>>(a, X);
+        else k_tree_walk<ERS_PREC_FP64, false, true><<<grid, TBT, 0, a.stream>>>(a, X);
     } else {
-        if (sl && dl) k_tree_far<ERS_PREC_MIXED, true, true><<<grid, TBT, 0, a.stream>>>(a, X);
-        else if (sl) k_tree_far<ERS_PREC_MIXED, true, false><<<grid, TBT, 0, a.stream>>>(a, X);
-        else k_tree_far<ERS_PREC_MIXED, false, true><<<grid, TBT, 0, a.stream>>>(a, X);
+        if (sl && dl) k_tree_walk<ERS_PREC_MIXED, true, true><<<grid, TBT, 0, a.stream>>>(a, X);
+        else if (sl) k_tree_walk<ERS_PREC_MIXED, true, false><<<grid, TBT, 0, a.stream>>>(a, X);
+        else k_tree_walk<ERS_PREC_MIXED, false, true><<<grid, TBT, 0, a.stream>>>(a, X);
     }
     t->stats_valid = true;
     return cudaGetLastError();

@@ -29,16 +29,14 @@ struct TreeCache {
     int p = 0;
     uint64_t w_version = ~0ull;
     bool have_w32 = false;
-    double *W = nullptr;  // [ncl][(p+1)^3][TREE_NW]
-    float *W32 = nullptr;  // [ncl][(p+1)^3][TREE_NW32]
+    double *W = nullptr;   // [ncl][(p+1)^3][TREE_WS]
+    float *W32 = nullptr;  // [ncl][(p+1)^3][TREE_WS]
     size_t w_cap = 0, w32_cap = 0;
     Cheb ch{};
     // target order (counting sort by cell of the surface grid)
     Scratch keys, order, hist;
-    unsigned long long *stats = nullptr;  // [2]: approximated (target, cluster) pairs, far pairs summed directly
+    unsigned long long *stats = nullptr;  // [3]: approximated (target, cluster) pairs, far pairs summed directly, wait ran out
     bool stats_valid = false;
-    int err_flag_host = 0;
-    int *err = nullptr;  // device flag: stack overflow of the walk
 };
 
 // Build the octree of the surface's nodes for leaf size n0 (host), upload it; ERS_OK or an error.

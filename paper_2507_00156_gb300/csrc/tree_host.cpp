@@ -108,7 +108,7 @@ int build_octree(const std::vector<double> &x, int64_t N, int n0, std::vector<Tr
 
 void free_dev(TreeCache *t) {
     void *ptrs[] = {t->cl, t->leaf_ids, t->inner_ids, t->tsrt, t->tleaf, t->trec, t->trec32, t->W, t->W32,
-                    t->keys.ptr, t->order.ptr, t->hist.ptr, t->stats, t->err};
+                    t->keys.ptr, t->order.ptr, t->hist.ptr, t->stats};
     for (void *p : ptrs)
         if (p) cudaFree(p);
 }
@@ -172,8 +172,7 @@ int tree_build(ers_surface *s, int n0) {
     alloc((void **)&t->tleaf, sizeof(int) * N);
     alloc((void **)&t->trec, sizeof(double) * REC * N);
     alloc((void **)&t->trec32, sizeof(float) * 12 * N);
-    alloc((void **)&t->stats, sizeof(unsigned long long) * 2);
-    alloc((void **)&t->err, sizeof(int));
+    alloc((void **)&t->stats, sizeof(unsigned long long) * 3);
     if (e == cudaSuccess) e = cudaMemcpy(t->cl, cl.data(), sizeof(TreeCluster) * cl.size(), cudaMemcpyHostToDevice);
     if (e == cudaSuccess && !leaves.empty())
         e = cudaMemcpy(t->leaf_ids, leaves.data(), sizeof(int) * leaves.size(), cudaMemcpyHostToDevice);
@@ -181,7 +180,6 @@ int tree_build(ers_surface *s, int n0) {
         e = cudaMemcpy(t->inner_ids, inner.data(), sizeof(int) * inner.size(), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(t->tsrt, tsrt.data(), sizeof(int) * N, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(t->tleaf, tleaf.data(), sizeof(int) * N, cudaMemcpyHostToDevice);
-    if (e == cudaSuccess) e = cudaMemset(t->err, 0, sizeof(int));
     if (e != cudaSuccess) {
         cudaGetLastError();
         free_dev(t);
@@ -235,11 +233,12 @@ int tree_stats(ers_surface *s, int64_t out[5]) {
     out[1] = t->nleaf;
     out[2] = t->depth;
     if (t->stats_valid) {
-        unsigned long long h[2] = {0, 0};
+        unsigned long long h[3] = {0, 0, 0};
         cudaError_t e = cudaMemcpy(h, t->stats, sizeof h, cudaMemcpyDeviceToHost);
         if (e != cudaSuccess) return cuda_fail(e, "treecode statistics");
         out[3] = (int64_t)h[0];
         out[4] = (int64_t)h[1];
+        if (h[2]) return fail(ERS_E_TIMEOUT, "treecode: a staging wait ran out; the last result is invalid");
     }
     return ERS_OK;
 }

@@ -60,6 +60,8 @@ def parse():
     ap.add_argument("--no-batched", action="store_true", help="skip the batched-launch leg")
     ap.add_argument("--no-learned", action="store_true", help="skip the learned-closure leg")
     ap.add_argument("--workload", default=WORKLOAD, help="profiling only: a smaller case (e.g. sphere64)")
+    ap.add_argument("--no-two-drop", action="store_true", help="skip the two-drop (Sec. 4.3) leg")
+    ap.add_argument("--two-drop-fine", action="store_true", help="two-drop leg: also h = 1/128 (FP64 treecode)")
     ap.add_argument("--tree", default=None,
                     help="treecode leg: theta,N0,p (default: the parameters of Eq. (optimal_params) for h)")
     return ap.parse_args()
@@ -234,6 +236,38 @@ def batched_leg(ers, torch, steps: int, warmup: int):
             "work_items": nitems, "persistent_grid": grid, "launches_per_step": 1, "finite": ok,
             "workload": "two unit spheres gap 0.01 at h=1/96 (self + neighbour nodes) + 16 bodies "
                         "(semi-axes U[0.6,1], h in {1/32,1/48,1/64,1/96}, own nodes + 5% band), 8 densities"}
+
+
+def two_drop_leg(ers, torch, fine: bool):
+    """Two drops nearly touching (Sec. 4.3): GMRES on Eq. (IE-2Surf) at h = 1/16, 1/32, 1/64 in FP64
+    with the direct far field (and, with fine, h = 1/128 with the FP64 treecode at Table 2's
+    theta = 0.6, N0 = 4000, p = 10): iterations, solve times and the self-convergence errors of
+    Table 2 (max and L2 over the velocity components at the coarse nodes)."""
+    from paper_2507_00156_gb300 import two_drop as gtd
+    levels = [(16, None), (32, None), (64, None)] + ([(128, (0.6, 4000, 10))] if fine else [])
+    sol, rows = {}, []
+    for inv, tree in levels:
+        P = gtd.TwoDrops(1 / inv, tree=tree)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        x, it, rel, conv = P.solve(tol=1e-10)
+        torch.cuda.synchronize()
+        secs = time.perf_counter() - t0
+        u1, u2 = P.split(x)
+        sol[inv] = ([u1.cpu().numpy(), u2.cpu().numpy()], [P.x[0].cpu().numpy(), P.x[1].cpu().numpy()])
+        rows.append({"inv_h": inv, "N": P.N, "iterations": it, "relres": rel, "converged": conv, "solve_s": secs,
+                     "matvecs": P.matvecs, "far_field": "treecode theta, N0, p = %s" % (tree,) if tree else "direct"})
+        del P
+    invs = [r["inv_h"] for r in rows]
+    for i in range(len(invs) - 1):
+        mx, l2 = gtd.self_convergence(sol[invs[i]][0], sol[invs[i]][1], sol[invs[i + 1]][0], sol[invs[i + 1]][1])
+        rows[i]["max_err"], rows[i]["l2_err"] = mx, l2
+        if i > 0:
+            rows[i]["max_order"] = float(np.log2(rows[i - 1]["max_err"] / mx))
+            rows[i]["l2_order"] = float(np.log2(rows[i - 1]["l2_err"] / l2))
+    return {"rows": rows, "precision": "fp64", "rho": [3, 4, 5], "rho_sharp": 3, "gmres_tol": 1e-10,
+            "note": "Table 2 (Sec. 4.3): errors e_h = u_h - u_{h/2} at the nodes of h; the paper's 1/16..1/64 rows: "
+                    "iterations 13, 12, 12; max 3.17e-3, 1.07e-4, 4.06e-6; L2 1.19e-4, 6.11e-6, 2.11e-7"}
 
 
 def learned_leg(ers, torch, s, wl, y, steps: int, warmup: int):
@@ -614,6 +648,8 @@ def main():
         line["batched"] = batched_leg(ers, torch, steps=2, warmup=1)
     if not args.no_learned and args.workload == WORKLOAD:
         line["learned"] = learned_leg(ers, torch, s, wl, y, steps=args.steps, warmup=1)
+    if not args.no_two_drop and args.workload == WORKLOAD:
+        line["two_drop"] = two_drop_leg(ers, torch, fine=args.two_drop_fine)
     if world == 1 and not args.no_cpu_baseline:
         cb, errs = cpu_baseline(wl, y, args.cpu_seconds, {"mixed": (u_mixed, v_mixed), "fp64": (u64, v64)})
         line["cpu_baseline"] = cb

@@ -39,6 +39,7 @@ extern "C" {
 
 #define ERS_OK 0
 #define ERS_W_CUTOFF 1        /* warning: cutoff_t < 6 (regularization truncated earlier than Sec. 3.2) */
+#define ERS_W_NOT_CONVERGED 2 /* warning: ers_gmres stopped at maxit above the tolerance */
 #define ERS_E_INVAL (-1)      /* bad argument (NULL, size, non-finite, unsorted rho, ...) */
 #define ERS_E_NOMEM (-2)      /* device or host allocation failed */
 #define ERS_E_CUDA (-3)       /* a CUDA call failed; message holds the CUDA error string */
@@ -382,6 +383,35 @@ int ers_treecode_defaults(double h, double *theta, int *n0, int *p);
  * invalid).
  */
 int ers_tree_stats(ers_surface *s, int64_t *out, int n);
+
+/*
+ * Value at M points x0 on the surface (device (M,3), with their unit normals n0) of a density
+ * known at the nodes (vals: device (N,3), canonical node order): the least-squares polynomial of
+ * total degree <= 4 in tangent-plane coordinates fitted to the node values within 3.5 h of the
+ * point, evaluated at the point (an O(h^5) approximation; exact for that polynomial space).  This
+ * supplies q(x0) of Eq. (Stokes_DL1) when a density is known only at the nodes, as for the
+ * velocity of the other drop in Eq. (IE-2Surf).  out: device (M,3); a point with fewer than 15
+ * nodes within 3.5 h (or a singular fit) gets NaN.  Asynchronous on `stream`.
+ */
+int ers_node_interp(const ers_surface *s, const double *vals, const double *x0, const double *n0, int64_t M,
+                    double *out, void *stream);
+
+/* y = a x + b y for device vectors of length n (asynchronous on `stream`). */
+int ers_vec_axpby(int64_t n, double a, const double *x, double b, double *y, void *stream);
+
+/*
+ * GMRES (Saad & Schultz 1986) without restart for A x = b with device vectors of length n,
+ * starting from x = 0: Arnoldi with modified Gram-Schmidt (inner products by a deterministic
+ * two-stage reduction), the least-squares problem by Givens rotations.  A(ctx, v, w, stream)
+ * must write A v into w (both device, length n) on `stream` and return 0 (or a negative
+ * ERS_E_* code, which ends the solve).  Stops when ||b - A x|| <= tol ||b|| or after maxit
+ * iterations; *iters and *relres (may be NULL) receive the iterations and the relative residual
+ * of the least-squares problem.  Workspace (maxit + 2) n doubles is allocated and freed inside.
+ * Returns ERS_OK, ERS_W_NOT_CONVERGED, or an error code; synchronizes `stream`.
+ */
+typedef int (*ers_matvec_fn)(void *ctx, const double *x, double *y, void *stream);
+int ers_gmres(int64_t n, ers_matvec_fn A, void *ctx, const double *b, double *x, double tol, int maxit, int *iters,
+              double *relres, void *stream);
 
 /* Message of the last error on the calling thread ("" if none).  Never NULL. */
 const char *ers_last_error(void);

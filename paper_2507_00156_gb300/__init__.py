@@ -44,7 +44,11 @@ EXPORTS = ["ers_build_surface", "ers_surface_free", "ers_surface_info", "ers_set
            "ers_batch_free", "ers_closure_create", "ers_closure_free", "ers_closure_params", "ers_closure_infer",
            "ers_closure_infer_reference", "ers_closure_status", "ers_closure_grad", "ers_closure_train",
            "ers_closure_data", "ers_eval_learned", "ers_eval_noalloc", "ers_treecode_defaults", "ers_tree_stats",
-           "ers_last_error", "ers_version"]
+           "ers_node_interp", "ers_vec_axpby", "ers_gmres", "ers_last_error", "ers_version"]
+ERS_W_NOT_CONVERGED = 2
+
+# ers_matvec_fn: int (*)(void *ctx, const double *x, double *y, void *stream)
+MATVEC_FN = ctypes.CFUNCTYPE(ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p)
 NPARAM = 10448
 NOALLOC_MAX_M = 524288
 
@@ -122,6 +126,9 @@ def lib():
             L.ers_profile.argtypes = [vp, cint]
             L.ers_last_profile.argtypes = [vp, P(dbl), P(dbl), P(dbl)]
             L.ers_treecode_defaults.argtypes = [dbl, P(dbl), P(cint), P(cint)]
+            L.ers_node_interp.argtypes = [vp, vp, vp, vp, i64, vp, vp]
+            L.ers_vec_axpby.argtypes = [i64, dbl, vp, dbl, vp, vp]
+            L.ers_gmres.argtypes = [i64, MATVEC_FN, vp, vp, vp, dbl, cint, P(cint), P(dbl), vp]
             L.ers_tree_stats.argtypes = [vp, P(i64), cint]
             L.ers_last_error.restype = ctypes.c_char_p
             L.ers_version.restype = ctypes.c_char_p
@@ -496,3 +503,48 @@ def eval_learned(surface, closure, y, x0, n0, b, f0, q0, gf0, gq0, rho=(2.0, 3.0
 
 def version() -> str:
     return lib().ers_version().decode()
+
+
+def node_interp(surface, vals, x0, n0, out=None, stream=None):
+    """ers_node_interp: values at surface points x0 (normals n0) of node values vals (N,3)."""
+    import torch
+    M = x0.shape[0]
+    if out is None:
+        out = torch.empty((M, 3), dtype=torch.float64, device=x0.device)
+    check(lib().ers_node_interp(surface.handle, _ptr(vals), _ptr(x0), _ptr(n0), M, _ptr(out), _stream(stream)))
+    return out
+
+
+def vec_axpby(a, x, b, y, stream=None):
+    """y = a x + b y (ers_vec_axpby), device float64 vectors of equal size."""
+    check(lib().ers_vec_axpby(y.numel(), float(a), _ptr(x), float(b), _ptr(y), _stream(stream)))
+    return y
+
+
+def gmres(matvec, b, x=None, tol=1e-10, maxit=100, stream=None):
+    """ers_gmres with a Python operator matvec(v, w) writing A v into w (device float64 vectors of
+    length n).  Returns (x, iterations, relative residual, converged)."""
+    import torch
+    n = b.numel()
+    if x is None:
+        x = torch.empty_like(b)
+    err = []
+
+    def cb(ctx, xp, yp, sp):
+        try:
+            v = torch.as_tensor(_DevView(xp, (n,), None), device="cuda")
+            w = torch.as_tensor(_DevView(yp, (n,), None), device="cuda")
+            matvec(v, w)
+            return 0
+        except Exception as e:  # reported after the solve
+            err.append(e)
+            return ERS_E_STATE
+
+    fn = MATVEC_FN(cb)
+    it, rel = ctypes.c_int(), ctypes.c_double()
+    rc = lib().ers_gmres(n, fn, None, _ptr(b), _ptr(x), float(tol), int(maxit), ctypes.byref(it), ctypes.byref(rel),
+                         _stream(stream))
+    if err:
+        raise err[0]
+    rc = check(rc)
+    return x, it.value, rel.value, rc == ERS_OK

@@ -136,7 +136,9 @@ __global__ void __launch_bounds__(NT) k_far64(EvalArgs A) {
 // Mixed precision: every pair term in FP32 with the target and source both expressed relative
 // to the centre c of the source tile (an exact float), yc = (y_hi - c) + y_lo, so that the
 // rounding error of d = yc - (x - c) is relative to |y - c| and |x - c| rather than to |y|;
-// FP32 partial sums over FLUSH tiles are added into FP64 accumulators.
+// FP32 partial sums over FLUSH tiles are added into FP64 accumulators, which live in the
+// thread's slot of shared memory (touched once per FLUSH tiles; in registers they would cost 48
+// registers and one CTA per SM).
 struct TargetF32 {
     float yh[3], yl[3], c, q0[3], rc2;
 };
@@ -146,16 +148,17 @@ struct TargetF32 {
 // 1/r by MUFU (masked to 0 where r^2 <= Rc^2), then the SL and DL terms.
 template <bool SL, bool DL, int NPK, int FLUSH>
 __device__ __forceinline__ void far32_item(const EvalArgs &A, int64_t tbi, int64_t chunk,
-                                           float4 *srec, float4 &scen) {
+                                           float4 *srec, float4 &scen, double *sacc) {
     constexpr int TPT = 2 * NPK;
     const int64_t j0 = chunk * A.chunk_len;  // multiple of TS32
     const int64_t j1 = min(A.sd.N, j0 + A.chunk_len);
     const float *__restrict__ rec = A.sd.rec32;
 
-    float yh[TPT][3], yl[TPT][3], rc2[TPT];
+    float rc2[TPT];
     bool valid[TPT];
     f2 nc[NPK], q0[NPK][3];  // -c and q0 of the two targets of each pair
-    double acc[TPT][6];
+    // FP64 accumulators: sacc[(t * 6 + i) * NT + thread]
+    auto acc = [&](int t, int i) -> double & { return sacc[(t * 6 + i) * NT + threadIdx.x]; };
     f2 accf[NPK][6];
 #pragma unroll
     for (int p = 0; p < NPK; ++p) {
@@ -166,16 +169,12 @@ __device__ __forceinline__ void far32_item(const EvalArgs &A, int64_t tbi, int64
             const int64_t m = tbi * (NT * TPT) + t * NT + threadIdx.x;
             TargetF64 D;
             load_target(A, m, SL, DL, D, valid[t]);
-            for (int i = 0; i < 3; ++i) {
-                yh[t][i] = __double2float_rn(D.y[i]);
-                yl[t][i] = __double2float_rn(D.y[i] - (double)yh[t][i]);
-                q[h][i] = __double2float_rn(D.q0[i]);
-            }
+            for (int i = 0; i < 3; ++i) q[h][i] = __double2float_rn(D.q0[i]);
             c[h] = __double2float_rn(D.c);
             // far iff r2 > rc2: +inf = nothing far (invalid target), -1 = everything far
             rc2[t] = !valid[t] ? __int_as_float(0x7f800000) : (D.rc2bits < 0 ? -1.0f : D.rc2f);
 #pragma unroll
-            for (int i = 0; i < 6; ++i) acc[t][i] = 0.0;
+            for (int i = 0; i < 6; ++i) acc(t, i) = 0.0;
         }
         nc[p] = pk(-c[0], -c[1]);
         for (int i = 0; i < 3; ++i) q0[p][i] = pk(q[0][i], q[1][i]);
@@ -192,13 +191,26 @@ __device__ __forceinline__ void far32_item(const EvalArgs &A, int64_t tbi, int64
         if (threadIdx.x == 0) scen = reinterpret_cast<const float4 *>(A.sd.tilec)[base / TS32];
         __syncthreads();
         const float4 cen = scen;
+        // targets relative to the tile centre, from their FP64 coordinates (re-read per tile
+        // rather than kept in registers): yc = (y_hi - c) + y_lo
         f2 yc[NPK][3];
 #pragma unroll
         for (int p = 0; p < NPK; ++p) {
-            const int a = 2 * p, b = 2 * p + 1;
-            yc[p][0] = pk(tile_rel(yh[a][0], cen.x, yl[a][0]), tile_rel(yh[b][0], cen.x, yl[b][0]));
-            yc[p][1] = pk(tile_rel(yh[a][1], cen.y, yl[a][1]), tile_rel(yh[b][1], cen.y, yl[b][1]));
-            yc[p][2] = pk(tile_rel(yh[a][2], cen.z, yl[a][2]), tile_rel(yh[b][2], cen.z, yl[b][2]));
+            float v[2][3];
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int64_t m = tbi * (NT * TPT) + (2 * p + h) * NT + threadIdx.x;
+                const bool ok = valid[2 * p + h];
+#pragma unroll
+                for (int i = 0; i < 3; ++i) {
+                    const double y = ok ? __ldg(A.y + 3 * m + i) : 0.0;
+                    const float yh = __double2float_rn(y), yl = __double2float_rn(y - (double)yh);
+                    v[h][i] = tile_rel(yh, i == 0 ? cen.x : (i == 1 ? cen.y : cen.z), yl);
+                }
+            }
+            yc[p][0] = pk(v[0][0], v[1][0]);
+            yc[p][1] = pk(v[0][1], v[1][1]);
+            yc[p][2] = pk(v[0][2], v[1][2]);
         }
         for (int j = 0; j < ns; ++j) {
             const float4 r0 = srec[j * 3 + 0], r1 = srec[j * 3 + 1], r2v = srec[j * 3 + 2];
@@ -246,8 +258,8 @@ __device__ __forceinline__ void far32_item(const EvalArgs &A, int64_t tbi, int64
                 for (int i = 0; i < 6; ++i) {
                     float a, b;
                     upk(accf[p][i], a, b);
-                    acc[2 * p][i] += (double)a;
-                    acc[2 * p + 1][i] += (double)b;
+                    acc(2 * p, i) += (double)a;
+                    acc(2 * p + 1, i) += (double)b;
                     accf[p][i] = 0ull;
                 }
         }
@@ -258,32 +270,33 @@ __device__ __forceinline__ void far32_item(const EvalArgs &A, int64_t tbi, int64
         for (int i = 0; i < 6; ++i) {
             float a, b;
             upk(accf[p][i], a, b);
-            acc[2 * p][i] += (double)a;
-            acc[2 * p + 1][i] += (double)b;
+            acc(2 * p, i) += (double)a;
+            acc(2 * p + 1, i) += (double)b;
         }
 #pragma unroll
     for (int t = 0; t < TPT; ++t) {
         if (!valid[t]) continue;
         const int64_t m = tbi * (NT * TPT) + t * NT + threadIdx.x;
         double *o = A.part + (chunk * A.M + m) * 6;
-        o[0] = acc[t][0] * INV8PI;
-        o[1] = acc[t][1] * INV8PI;
-        o[2] = acc[t][2] * INV8PI;
-        o[3] = acc[t][3] * (-6.0 * INV8PI);
-        o[4] = acc[t][4] * (-6.0 * INV8PI);
-        o[5] = acc[t][5] * (-6.0 * INV8PI);
+        o[0] = acc(t, 0) * INV8PI;
+        o[1] = acc(t, 1) * INV8PI;
+        o[2] = acc(t, 2) * INV8PI;
+        o[3] = acc(t, 3) * (-6.0 * INV8PI);
+        o[4] = acc(t, 4) * (-6.0 * INV8PI);
+        o[5] = acc(t, 5) * (-6.0 * INV8PI);
     }
 }
 
 template <bool SL, bool DL, int NPK, int FLUSH>
-__global__ void __launch_bounds__(NT, 3) k_far32(EvalArgs A, int64_t ntb) {
+__global__ void __launch_bounds__(NT, 4) k_far32(EvalArgs A, int64_t ntb) {
     __shared__ float4 srec[TS32 * 3];
     __shared__ float4 scen;
+    __shared__ double sacc[2 * NPK * 6 * NT];
     const int64_t nitems = ntb * A.chunks;
     for (int64_t item = blockIdx.x; item < nitems; item += gridDim.x) {
         const int64_t tbi = item % ntb, chunk = item / ntb;
         __syncthreads();  // the previous item's last tile is no longer read
-        far32_item<SL, DL, NPK, FLUSH>(A, tbi, chunk, srec, scen);
+        far32_item<SL, DL, NPK, FLUSH>(A, tbi, chunk, srec, scen, sacc);
     }
 }
 
@@ -309,7 +322,7 @@ cudaError_t far32_dispatch(const EvalArgs &a, int ctas_per_sm, int nsm) {
         // at most ctas_per_sm CTAs per SM: dynamic shared memory that leaves room for no more
         // (228 KB per SM, 1 KB reserved per CTA), and a grid of that many CTAs per SM
         const size_t per_cta = (228u << 10) / (size_t)(ctas_per_sm + 1) + 1;
-        const size_t stat = sizeof(float4) * (TS32 * 3 + 1) + 1024;
+        const size_t stat = sizeof(float4) * (TS32 * 3 + 1) + sizeof(double) * 2 * NPK * 6 * NT + 1024;
         pad = per_cta > stat ? per_cta - stat : 0;
         grid = std::min<int64_t>(nitems, (int64_t)ctas_per_sm * nsm);
     }

@@ -175,3 +175,38 @@ def test_treecode_rejected_where_unsupported(ers):
         with pytest.raises(ers.ErsError) as ex:
             g.s.eval(yd, f0, q0, rho=g.wl.rho, tree=bad)
         assert ex.value.code == -1
+
+
+def test_treecode_single_leaf_is_the_direct_path(ers):
+    """N0 >= N: the root is a leaf, every far pair is summed directly."""
+    g = gpu("sphere16")
+    y = g.targets()
+    u0, v0, _ = g.eval(y, precision=0)
+    u1, v1, _ = g.eval(y, precision=0, tree=(0.6, 10 ** 6, 4))
+    ts = g.s.tree_stats()
+    assert ts["clusters"] == 1 and ts["leaves"] == 1 and ts["approximated"] == 0
+    assert rel_err(u1, u0) <= 1e-13 and rel_err(v1, v0) <= 1e-13
+
+
+@pytest.mark.parametrize("p", [1, 2, 16])
+def test_treecode_degree_limits(ers, p):
+    """The smallest degrees and the largest the library takes, against the oracle."""
+    sel = np.arange(0, 4302 + 2000, 13)
+    tree = (0.6, 250, p)
+    uo, vo, _, st = oracle_tree("sphere16", sel, (2.0, 3.0, 4.0), tree)
+    g = gpu("sphere16")
+    u, v, _ = g.eval(g.targets(sel), precision=0, tree=tree)
+    assert rel_err(u, uo) <= FP64_TOL and rel_err(v, vo) <= FP64_TOL, (rel_err(u, uo), rel_err(v, vo))
+    assert g.s.tree_stats()["approximated"] == int(st[:, 0].sum())
+
+
+@pytest.mark.parametrize("M", [1, 31, 33, 129])
+def test_treecode_ragged_target_counts(ers, M):
+    """Target counts that leave partial warps and CTAs."""
+    sel = np.arange(M) * 37 % (4302 + 2000)
+    tree = (0.6, 300, 4)
+    uo, vo, _, _ = oracle_tree("sphere16", sel, (2.0, 3.0, 4.0), tree)
+    g = gpu("sphere16")
+    for prec, tol in ((0, FP64_TOL), (1, MIXED_TOL)):
+        u, v, _ = g.eval(g.targets(sel), precision=prec, tree=tree)
+        assert rel_err(u, uo) <= tol and rel_err(v, vo) <= tol, (M, prec)

@@ -113,3 +113,20 @@ def test_table2_self_convergence(ers):
         assert 0.5 < e[0] / rows[inv]["max_err"] < 2.0, (inv, e)
         assert 0.7 < e[1] / rows[inv]["l2_err"] < 1.4, (inv, e)
     assert np.log2(e16[1] / e32[1]) > 4.0 and np.log2(e16[0] / e32[0]) > 4.0, (e16, e32)
+
+
+def test_gmres_zero_rhs_and_node_interp_empty(ers):
+    import torch
+    calls = []
+
+    def mv(v, w):
+        calls.append(1)
+        w.copy_(v)
+
+    b = torch.zeros(50, dtype=torch.float64, device="cuda")
+    x, it, rel, conv = ers.gmres(mv, b, tol=1e-10, maxit=10)
+    assert conv and it == 0 and rel == 0.0 and not calls and float(x.abs().max()) == 0.0
+    s = ers.Surface((0, 0, 0), (1, 1, 1), 1 / 16)
+    e = torch.empty((0, 3), dtype=torch.float64, device="cuda")
+    vals = torch.zeros((s.N, 3), dtype=torch.float64, device="cuda")
+    assert ers.node_interp(s, vals, e, e).shape == (0, 3)

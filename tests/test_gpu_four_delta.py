@@ -130,3 +130,17 @@ def test_four_delta_rejected_where_unsupported(ers):
     ua, va = (t.cpu().numpy() for t in g.s.eval(yd, f0, q0, rho=(3.0, 4.0, 5.0, 0.0)))
     ub, vb = (t.cpu().numpy() for t in g.s.eval(yd, f0, q0, rho=RHO4))
     assert np.array_equal(ua, ub) and np.array_equal(va, vb)
+
+
+def test_four_delta_full_size_bench_workload_sampled(ers):
+    """The bench workload with the four-delta option as the bench's leg runs it (rho = (2, 3, 4, 5),
+    mixed precision, all 392,718 targets); a seeded sample against the oracle."""
+    import workloads
+    g = gpu("sphere128")
+    y_all = g.targets()
+    rho = (2.0, 3.0, 4.0, 5.0)
+    u, v, _ = g.eval(y_all, precision=1, rho=rho)
+    sel = workloads.subsample(300, len(y_all), 6262)
+    y, uo, vo, _ = oracle_eval("sphere128", sel=sel, rho=rho)
+    assert np.array_equal(y, y_all[sel])
+    assert rel_err(u[sel], uo) <= MIXED_TOL and rel_err(v[sel], vo) <= MIXED_TOL

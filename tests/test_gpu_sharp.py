@@ -78,3 +78,16 @@ def test_sharp_rejected_where_unsupported(ers):
     assert ex.value.code == -5
     with pytest.raises(ers.ErsError):
         g.s.eval(yd, f0, q0, rho=g.wl.rho, sharp=True, rho_sharp=-1.0)
+
+
+def test_sharp_full_size_bench_workload_sampled(ers):
+    """The bench workload with the on-surface option as the bench's leg runs it (mixed precision,
+    delta# = rho_1 h, all 392,718 targets); a seeded sample against the oracle."""
+    import workloads
+    g = gpu("sphere128")
+    y_all = g.targets()
+    u, v, _ = g.eval(y_all, precision=1, sharp=True)
+    sel = workloads.subsample(300, len(y_all), 7373)
+    y, uo, vo, bo = oracle_eval_sharp("sphere128", sel=sel, rho_sharp=3.0)
+    assert np.array_equal(y, y_all[sel]) and (bo == 0).sum() > 50
+    assert rel_err(u[sel], uo) <= MIXED_TOL and rel_err(v[sel], vo) <= MIXED_TOL

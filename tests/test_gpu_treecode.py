@@ -210,3 +210,20 @@ def test_treecode_ragged_target_counts(ers, M):
     for prec, tol in ((0, FP64_TOL), (1, MIXED_TOL)):
         u, v, _ = g.eval(g.targets(sel), precision=prec, tree=tree)
         assert rel_err(u, uo) <= tol and rel_err(v, vo) <= tol, (M, prec)
+
+
+@pytest.mark.parametrize("precision,tol", [(0, FP64_TOL), (1, MIXED_TOL)])
+def test_treecode_full_size_bench_workload_sampled(ers, precision, tol):
+    """The bench workload (unit sphere h = 1/128, N = 272,718, all 392,718 targets in one launch)
+    with the treecode at the parameters of Eq. (optimal_params) for this h (theta = 0.6, N0 = 4000,
+    p = 8), as the bench's treecode leg runs it; a seeded sample of 300 targets against the
+    oracle's treecode with the same parameters."""
+    g = gpu("sphere128")
+    y_all = g.targets()
+    tree = ers.treecode_defaults(g.wl.h)
+    assert tree == (0.6, 4000, 8)
+    u, v, _ = g.eval(y_all, precision=precision, tree=tree)
+    sel = workloads.subsample(300, len(y_all), 5151)
+    uo, vo, _, _ = oracle_tree("sphere128", sel, g.wl.rho, tree)
+    assert rel_err(u[sel], uo) <= tol and rel_err(v[sel], vo) <= tol, (rel_err(u[sel], uo), rel_err(v[sel], vo))
+    assert np.isfinite(u).all() and np.isfinite(v).all()

@@ -46,7 +46,8 @@ namespace {
 
 void free_surface(ers_surface *s) {
     if (!s) return;
-    void *ptrs[] = {s->x, s->n, s->w, s->perm, s->rec, s->rec32, s->tilec, s->xs32, s->cell_start,
+    void *ptrs[] = {s->x, s->n, s->w, s->perm, s->rec, s->rec32, s->tilec, s->xs32, s->cell_start, s->cell_rank,
+                    s->okeys.ptr, s->oorder.ptr, s->ohist.ptr,
                     s->part.ptr, s->cp.ptr, s->host_io.ptr, s->counts.ptr, s->dens64.ptr, s->dens32.ptr};
     for (void *p : ptrs)
         if (p) cudaFree(p);
@@ -234,6 +235,7 @@ int build_surface(const ers_shape *shape, double h, ers_surface **out) {
     ERS_TRY(dmalloc(&s->tilec, (size_t)s->ntile32 * 4));
     ERS_TRY(dmalloc(&s->xs32, N));
     ERS_TRY(dmalloc(&s->cell_start, G.ncell + 1));
+    ERS_TRY(dmalloc(&s->cell_rank, G.ncell));
     if (e != cudaSuccess) {
         cudaGetLastError();
         free_surface(s);
@@ -248,6 +250,10 @@ int build_surface(const ers_shape *shape, double h, ers_surface **out) {
     ERS_TRY(cudaMemcpy(s->tilec, tilec.data(), sizeof(float) * s->ntile32 * 4, cudaMemcpyHostToDevice));
     ERS_TRY(cudaMemcpy(s->xs32, xs32.data(), sizeof(float4) * N, cudaMemcpyHostToDevice));
     ERS_TRY(cudaMemcpy(s->cell_start, cstart.data(), sizeof(int) * (G.ncell + 1), cudaMemcpyHostToDevice));
+    {
+        const std::vector<int> rank = morton_cell_rank(G);
+        ERS_TRY(cudaMemcpy(s->cell_rank, rank.data(), sizeof(int) * G.ncell, cudaMemcpyHostToDevice));
+    }
 #undef ERS_TRY
     if (e != cudaSuccess) {
         free_surface(s);

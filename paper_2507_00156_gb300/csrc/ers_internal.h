@@ -123,6 +123,9 @@ struct ers_surface {
     // treecode: octree, tree-ordered records and modified weights (ERS_OPT_TREECODE)
     ers::TreeCache *tree = nullptr;
     uint64_t dens_version = 0;  // bumped by every ers_set_density
+    // target order of an evaluation: the grid cells' Morton ranks and the counting-sort buffers
+    int *cell_rank = nullptr;  // [ncell]
+    ers::Scratch okeys, oorder, ohist;
 };
 
 namespace ers {
@@ -191,6 +194,7 @@ struct EvalArgs {
     double rho_sharp, dsharp, Rc_sharp;  // rho#, delta# = rho# h, cutoff_t delta#
     const double *tab_sharp;
     double *gamma;   // ndelta == 2: per-target gamma (may be NULL)
+    const int *order;  // treecode walk: targets in a spatially coherent order (NULL: computed there)
     double *u, *v;
     double *part;    // [chunks][M][6]
     int chunks;
@@ -229,6 +233,10 @@ struct TreeParams {
     int n0, p;
 };
 void treecode_defaults(double h, double *theta, int *n0, int *p);
+// Rank of every cell of the grid in Morton (Z) order (row-major for grids above 2^26 cells).
+std::vector<int> morton_cell_rank(const Grid &G);
+// order[0..M) = the targets sorted by the Morton rank of their cell (counting sort on `st`).
+cudaError_t launch_target_order(ers_surface *s, const double *y, int64_t M, cudaStream_t st, const int **order);
 // Build (or reuse) the octree for leaf size n0 and the modified weights of degree p for the
 // current densities; ERS_OK or an error code.
 int tree_prepare(ers_surface *s, int n0, int p, bool mixed, cudaStream_t st);

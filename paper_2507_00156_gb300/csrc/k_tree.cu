@@ -17,7 +17,7 @@
 // applied as three one-dimensional contractions, level by level upwards.
 //
 // Evaluation: one warp per 32 targets that are close in space (a counting sort by the cells of
-// the surface grid), one lane per target.  The warp walks the tree depth first with a stack in
+// the surface grid taken in Morton order), one lane per target.  The warp walks the tree depth first with a stack in
 // shared memory; at every cluster each lane takes its own decision (approximate, sum the leaf,
 // open, or nothing below an approximated ancestor), so every target gets exactly the
 // per-target walk of Sec. 3.4.  The lanes that approximate a cluster read its Chebyshev
@@ -208,8 +208,8 @@ __global__ void k_weights32(const double *__restrict__ W, float *__restrict__ W3
     W32[i * TREE_WS + TREE_NW] = 0.0f;
 }
 
-// Target order: counting sort by the cell of the surface grid (clamped), so that consecutive
-// targets are close.
+// Target order: counting sort by the Morton rank of the target's cell of the surface grid
+// (clamped), so that consecutive targets are close.
 __device__ __forceinline__ int64_t target_cell(const Grid &G, const double *y) {
     int64_t idx[3];
     for (int a = 0; a < 3; ++a) {
@@ -220,10 +220,11 @@ __device__ __forceinline__ int64_t target_cell(const Grid &G, const double *y) {
     return (idx[2] * G.nc[1] + idx[1]) * G.nc[0] + idx[0];
 }
 
-__global__ void k_tkeys(const double *__restrict__ y, int64_t M, Grid G, int *__restrict__ keys, int *__restrict__ hist) {
+__global__ void k_tkeys(const double *__restrict__ y, int64_t M, Grid G, const int *__restrict__ cell_rank,
+                        int *__restrict__ keys, int *__restrict__ hist) {
     const int64_t m = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (m >= M) return;
-    const int key = (int)target_cell(G, y + 3 * m);
+    const int key = cell_rank[target_cell(G, y + 3 * m)];
     keys[m] = key;
     atomicAdd(hist + key, 1);
 }
@@ -738,24 +739,35 @@ int tree_prepare(ers_surface *s, int n0, int p, bool mixed, cudaStream_t st) {
     return ERS_OK;
 }
 
+cudaError_t launch_target_order(ers_surface *s, const double *y, int64_t M, cudaStream_t st, const int **order) {
+    *order = nullptr;
+    if (M == 0) return cudaSuccess;
+    const Grid &G = s->grid;
+    int err = grow(s->okeys, sizeof(int) * (size_t)M);
+    if (err == ERS_OK) err = grow(s->oorder, sizeof(int) * (size_t)M);
+    if (err == ERS_OK) err = grow(s->ohist, sizeof(int) * (size_t)(G.ncell + 1));
+    if (err != ERS_OK) return cudaErrorMemoryAllocation;
+    int *keys = (int *)s->okeys.ptr, *ord = (int *)s->oorder.ptr, *hist = (int *)s->ohist.ptr;
+    cudaError_t e = cudaMemsetAsync(hist, 0, sizeof(int) * (size_t)(G.ncell + 1), st);
+    if (e != cudaSuccess) return e;
+    const unsigned gb = (unsigned)((M + 255) / 256);
+    k_tkeys<<<gb, 256, 0, st>>>(y, M, G, s->cell_rank, keys, hist);
+    k_tscan<<<1, 1024, 0, st>>>(hist, G.ncell + 1);
+    k_tscatter<<<gb, 256, 0, st>>>(keys, M, hist, ord);
+    e = cudaGetLastError();
+    if (e == cudaSuccess) *order = ord;
+    return e;
+}
+
 cudaError_t launch_tree_far(const EvalArgs &a, const TreeParams &tp) {
     if (a.M == 0) return cudaSuccess;
     ers_surface *s = const_cast<ers_surface *>(a.s);
     TreeCache *t = s->tree;
     const int64_t M = a.M;
-    const Grid &G = s->grid;
-    int err = grow(t->keys, sizeof(int) * (size_t)M);
-    if (err == ERS_OK) err = grow(t->order, sizeof(int) * (size_t)M);
-    if (err == ERS_OK) err = grow(t->hist, sizeof(int) * (size_t)(G.ncell + 1));
-    if (err != ERS_OK) return cudaErrorMemoryAllocation;
-    int *keys = (int *)t->keys.ptr, *order = (int *)t->order.ptr, *hist = (int *)t->hist.ptr;
-    cudaError_t e = cudaMemsetAsync(hist, 0, sizeof(int) * (size_t)(G.ncell + 1), a.stream);
-    if (e == cudaSuccess) e = cudaMemsetAsync(t->stats, 0, sizeof(unsigned long long) * 3, a.stream);
+    const int *order = a.order;
+    cudaError_t e = cudaMemsetAsync(t->stats, 0, sizeof(unsigned long long) * 3, a.stream);
     if (e != cudaSuccess) return e;
-    const unsigned gb = (unsigned)((M + 255) / 256);
-    k_tkeys<<<gb, 256, 0, a.stream>>>(a.y, M, G, keys, hist);
-    k_tscan<<<1, 1024, 0, a.stream>>>(hist, G.ncell + 1);
-    k_tscatter<<<gb, 256, 0, a.stream>>>(keys, M, hist, order);
+    if (!order && (e = launch_target_order(s, a.y, M, a.stream, &order)) != cudaSuccess) return e;
     TreeEval X;
     X.cl = t->cl;
     X.W = t->W;

@@ -33,8 +33,6 @@ struct TreeCache {
     float *W32 = nullptr;  // [ncl][(p+1)^3][TREE_WS]
     size_t w_cap = 0, w32_cap = 0;
     Cheb ch{};
-    // target order (counting sort by cell of the surface grid)
-    Scratch keys, order, hist;
     unsigned long long *stats = nullptr;  // [3]: approximated (target, cluster) pairs, far pairs summed directly, wait ran out
     bool stats_valid = false;
 };

@@ -8,6 +8,7 @@
 // r_c = half the box diagonal.  Clusters are numbered level by level (breadth first), so the
 // children of a cluster are contiguous; the octant partition is stable, so the node order of
 // the leaves does not depend on the numbering.
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 
@@ -106,14 +107,44 @@ int build_octree(const std::vector<double> &x, int64_t N, int n0, std::vector<Tr
     return depth;
 }
 
+// Morton (Z-order) code of a cell: the bits of ix, iy, iz interleaved.
+uint64_t morton3(uint32_t ix, uint32_t iy, uint32_t iz) {
+    uint64_t k = 0;
+    for (int bit = 0; bit < 21; ++bit) {
+        k |= (uint64_t)((ix >> bit) & 1u) << (3 * bit);
+        k |= (uint64_t)((iy >> bit) & 1u) << (3 * bit + 1);
+        k |= (uint64_t)((iz >> bit) & 1u) << (3 * bit + 2);
+    }
+    return k;
+}
+
 void free_dev(TreeCache *t) {
     void *ptrs[] = {t->cl, t->leaf_ids, t->inner_ids, t->tsrt, t->tleaf, t->trec, t->trec32, t->W, t->W32,
-                    t->keys.ptr, t->order.ptr, t->hist.ptr, t->stats};
+                    t->stats};
     for (void *p : ptrs)
         if (p) cudaFree(p);
 }
 
 }  // namespace
+
+std::vector<int> morton_cell_rank(const Grid &G) {
+    // targets ordered by cell with the cells in Morton order: the 32 targets of a warp are
+    // compact, so they share near nodes in the caches and decide alike at tree clusters
+    std::vector<int> cell_rank((size_t)G.ncell);
+    if (G.ncell <= ((int64_t)1 << 26)) {
+        std::vector<std::pair<uint64_t, int>> mk((size_t)G.ncell);
+        for (int64_t c = 0; c < G.ncell; ++c) {
+            const uint32_t ix = (uint32_t)(c % G.nc[0]), iy = (uint32_t)((c / G.nc[0]) % G.nc[1]);
+            const uint32_t iz = (uint32_t)(c / ((int64_t)G.nc[0] * G.nc[1]));
+            mk[c] = {morton3(ix, iy, iz), (int)c};
+        }
+        std::sort(mk.begin(), mk.end());
+        for (int64_t r = 0; r < G.ncell; ++r) cell_rank[mk[r].second] = (int)r;
+    } else {
+        for (int64_t c = 0; c < G.ncell; ++c) cell_rank[c] = (int)c;
+    }
+    return cell_rank;
+}
 
 void tree_free(ers_surface *s) {
     if (!s || !s->tree) return;

@@ -77,8 +77,10 @@ extern "C" {
                               weights of w f, w n, q_j w n_k), other leaves summed directly over their
                               nodes beyond Rc.  The near sums and the extrapolation are unchanged.  The
                               tree is built on the host at the first use for a given tree_n0 and kept
-                              with the surface; the modified weights are recomputed after every
-                              ers_set_density or change of tree_p.  ERS_OPT_CONCURRENT is ignored.
+                              with the surface (that call synchronizes the device and allocates: make
+                              it before any stream capture); the modified weights are recomputed on
+                              `stream` after every ers_set_density or change of tree_p (allocating when
+                              tree_p grows).  ERS_OPT_CONCURRENT is ignored.
                               Not available in the batched, no-allocation and closure paths */
 
 #define ERS_PREC_FP64 0   /* every step in FP64 arithmetic */

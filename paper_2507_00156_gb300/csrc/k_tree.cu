@@ -63,6 +63,33 @@ __device__ __forceinline__ void lagrange_basis(const Cheb &ch, double c, double 
     for (int k = 0; k <= p; ++k) L[k] = __ddiv_rn(L[k], den);
 }
 
+// The same basis written as T (double or float) without a scratch array: the denominator first,
+// then each value (the same operations, so T = double gives lagrange_basis's values).
+template <class T>
+__device__ __forceinline__ void lagrange_basis_to(const Cheb &ch, double c, double hw, double x, T *L) {
+    const int p = ch.p;
+    int hit = -1;
+    for (int k = 0; k <= p; ++k) {
+        const double sk = __dadd_rn(c, __dmul_rn(hw, ch.cosk[k]));
+        if (hit < 0 && x == sk) hit = k;
+    }
+    if (hit >= 0) {
+        for (int k = 0; k <= p; ++k) L[k] = k == hit ? (T)1 : (T)0;
+        return;
+    }
+    double den = 0.0;
+    for (int k = 0; k <= p; ++k) {
+        const double sk = __dadd_rn(c, __dmul_rn(hw, ch.cosk[k]));
+        const double wk = ((k & 1) ? -1.0 : 1.0) * ((k == 0 || k == p) ? 0.5 : 1.0);
+        den = __dadd_rn(den, __ddiv_rn(wk, __dsub_rn(x, sk)));
+    }
+    for (int k = 0; k <= p; ++k) {
+        const double sk = __dadd_rn(c, __dmul_rn(hw, ch.cosk[k]));
+        const double wk = ((k & 1) ? -1.0 : 1.0) * ((k == 0 || k == p) ? 0.5 : 1.0);
+        L[k] = (T)__ddiv_rn(__ddiv_rn(wk, __dsub_rn(x, sk)), den);
+    }
+}
+
 // Tree-ordered records: FP64 copy of the cell-sorted record, FP32 copy relative to the leaf centre.
 __global__ void k_tree_gather(int64_t N, const int *__restrict__ tsrt, const int *__restrict__ tleaf,
                               const TreeCluster *__restrict__ cl, const double *__restrict__ rec,
@@ -92,11 +119,15 @@ __device__ __forceinline__ double rec_density(const double *r, int g) {
 }
 
 // Modified weights of the leaves, Eq. (mod_weights): one CTA per leaf; each thread owns one
-// Chebyshev index k per pass and its 15 sums; the nodes' basis values and densities are staged
-// in shared memory, TCH nodes at a time.
-__global__ void __launch_bounds__(256) k_leaf_weights(const TreeCluster *__restrict__ cl, const int *__restrict__ ids,
+// Chebyshev index k per pass and its 15 sums; the nodes' basis values (computed in FP64) and
+// densities are staged in shared memory, TCH nodes at a time.  T = double: FP64 products and sums;
+// T = float (weights for the mixed evaluation only): FP32 products and FP32 sums over each chunk of
+// TCH nodes, added in FP64 (relative error ~1e-7, below the interpolation error of the treecode).
+template <class T>
+__global__ void __launch_bounds__(256, 2) k_leaf_weights(const TreeCluster *__restrict__ cl, const int *__restrict__ ids,
                                                       const double *__restrict__ trec, Cheb ch, double *__restrict__ W) {
-    extern __shared__ double sm[];
+    extern __shared__ __align__(16) unsigned char smraw[];
+    T *sm = reinterpret_cast<T *>(smraw);
     const TreeCluster C = cl[ids[blockIdx.x]];
     const int P1 = ch.p + 1, NK = P1 * P1 * P1, per = 3 * P1 + TREE_NW;
     double *Wc = W + (size_t)ids[blockIdx.x] * NK * TREE_WS;
@@ -112,20 +143,25 @@ __global__ void __launch_bounds__(256) k_leaf_weights(const TreeCluster *__restr
             for (int t = threadIdx.x; t < nn * 3; t += blockDim.x) {
                 const int node = t / 3, a = t % 3;
                 const double xv = trec[(int64_t)(C.start + n0 + node) * REC + R_X + a];
-                lagrange_basis(ch, C.c[a], C.hw[a], xv, sm + node * per + a * P1);
+                lagrange_basis_to<T>(ch, C.c[a], C.hw[a], xv, sm + node * per + a * P1);
             }
             for (int t = threadIdx.x; t < nn * TREE_NW; t += blockDim.x) {
                 const int node = t / TREE_NW, g = t % TREE_NW;
-                sm[node * per + 3 * P1 + g] = rec_density(trec + (int64_t)(C.start + n0 + node) * REC, g);
+                sm[node * per + 3 * P1 + g] = (T)rec_density(trec + (int64_t)(C.start + n0 + node) * REC, g);
             }
             __syncthreads();
             if (k < NK) {
-                for (int node = 0; node < nn; ++node) {
-                    const double *e = sm + node * per;
-                    const double Lk = e[k1] * e[P1 + k2] * e[2 * P1 + k3];
+                T part[TREE_NW];
 #pragma unroll
-                    for (int g = 0; g < TREE_NW; ++g) acc[g] = fma(Lk, e[3 * P1 + g], acc[g]);
+                for (int g = 0; g < TREE_NW; ++g) part[g] = (T)0;
+                for (int node = 0; node < nn; ++node) {
+                    const T *e = sm + node * per;
+                    const T Lk = e[k1] * e[P1 + k2] * e[2 * P1 + k3];
+#pragma unroll
+                    for (int g = 0; g < TREE_NW; ++g) part[g] = fma(Lk, e[3 * P1 + g], part[g]);
                 }
+#pragma unroll
+                for (int g = 0; g < TREE_NW; ++g) acc[g] += (double)part[g];
             }
         }
         if (k < NK) {
@@ -681,7 +717,8 @@ int tree_prepare(ers_surface *s, int n0, int p, bool mixed, cudaStream_t st) {
     if (8 * (t->depth + 1) > TSTACK)
         return fail(ERS_E_UNSUPPORTED, "treecode: the tree is deeper than the walk stack allows (use a larger tree_n0)");
     const int P1 = p + 1, NK = P1 * P1 * P1;
-    if (t->w_version != s->dens_version || t->p != p) {
+    // weights built for the mixed evaluation (FP32 products) are not good enough for an FP64 one
+    if (t->w_version != s->dens_version || t->p != p || (!mixed && !t->w_fp64)) {
         const size_t wbytes = sizeof(double) * (size_t)t->ncl * NK * TREE_WS;
         if (wbytes > t->w_cap) {
             if (t->W) cudaFree(t->W);
@@ -696,11 +733,15 @@ int tree_prepare(ers_surface *s, int n0, int p, bool mixed, cudaStream_t st) {
         t->p = p;
         t->ch.p = p;
         for (int k = 0; k <= TREE_PMAX; ++k) t->ch.cosk[k] = k <= p ? std::cos(k * PI / p) : 0.0;
-        const size_t smem_leaf = sizeof(double) * TCH * (3 * P1 + TREE_NW);
-        if (smem_leaf > 48 * 1024)
-            cudaFuncSetAttribute(k_leaf_weights, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_leaf);
-        if (t->nleaf > 0)
-            k_leaf_weights<<<t->nleaf, 256, smem_leaf, st>>>(t->cl, t->leaf_ids, t->trec, t->ch, t->W);
+        if (t->nleaf > 0) {
+            if (mixed) {  // weights for the mixed evaluation only: FP32 products
+                const size_t smem_leaf = sizeof(float) * TCH * (3 * P1 + TREE_NW);
+                k_leaf_weights<float><<<t->nleaf, 256, smem_leaf, st>>>(t->cl, t->leaf_ids, t->trec, t->ch, t->W);
+            } else {
+                const size_t smem_leaf = sizeof(double) * TCH * (3 * P1 + TREE_NW);
+                k_leaf_weights<double><<<t->nleaf, 256, smem_leaf, st>>>(t->cl, t->leaf_ids, t->trec, t->ch, t->W);
+            }
+        }
         if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "treecode: leaf weights");
         // densities per pass of the upward transfer: the most that fits in 160 KB
         int G = 1;
@@ -717,6 +758,7 @@ int tree_prepare(ers_surface *s, int n0, int p, bool mixed, cudaStream_t st) {
         }
         if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "treecode: upward transfer");
         t->w_version = s->dens_version;
+        t->w_fp64 = !mixed;
         t->have_w32 = false;
     }
     if (mixed && !t->have_w32) {

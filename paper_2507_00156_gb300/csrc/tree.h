@@ -29,6 +29,7 @@ struct TreeCache {
     int p = 0;
     uint64_t w_version = ~0ull;
     bool have_w32 = false;
+    bool w_fp64 = false;  // the weights were built with FP64 products (else good for the mixed path only)
     double *W = nullptr;   // [ncl][(p+1)^3][TREE_WS]
     float *W32 = nullptr;  // [ncl][(p+1)^3][TREE_WS]
     size_t w_cap = 0, w32_cap = 0;

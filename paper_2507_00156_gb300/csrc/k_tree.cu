@@ -235,13 +235,22 @@ __global__ void __launch_bounds__(256) k_upward(const TreeCluster *__restrict__ 
     }
 }
 
-// FP32 copy of the weights (the mixed evaluation), same layout as the FP64 array.
+// FP32 weights for the mixed evaluation, 12 per point (three float4): w f (3), w n (3) and the
+// symmetric part of q_j w n_k, which is all that d . (q w n)^ . d sees: S00, S11, S22, S01, S02,
+// S12 with S_jk = W_jk + W_kj off the diagonal.
+constexpr int TREE_WS32 = 12;
 __global__ void k_weights32(const double *__restrict__ W, float *__restrict__ W32, int64_t npts) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= npts) return;
-#pragma unroll
-    for (int g = 0; g < TREE_NW; ++g) W32[i * TREE_WS + g] = __double2float_rn(W[i * TREE_WS + g]);
-    W32[i * TREE_WS + TREE_NW] = 0.0f;
+    const double *w = W + i * TREE_WS;
+    float *o = W32 + i * TREE_WS32;
+    for (int g = 0; g < 6; ++g) o[g] = __double2float_rn(w[g]);
+    o[6] = __double2float_rn(w[6]);            // S00
+    o[7] = __double2float_rn(w[10]);           // S11
+    o[8] = __double2float_rn(w[14]);           // S22
+    o[9] = __double2float_rn(w[7] + w[9]);     // S01
+    o[10] = __double2float_rn(w[8] + w[12]);   // S02
+    o[11] = __double2float_rn(w[11] + w[13]);  // S12
 }
 
 // Target order: counting sort by the Morton rank of the target's cell of the surface grid
@@ -536,11 +545,11 @@ __global__ void __launch_bounds__(TBT, 4) k_tree_walk(EvalArgs A, TreeEval X) {
                 });
             } else {
                 // FP32 terms relative to the cluster centre; FP32 sums per chunk added in FP64
-                const unsigned char *src = reinterpret_cast<const unsigned char *>(X.W32 + (size_t)cid * NK * TREE_WS);
+                const unsigned char *src = reinterpret_cast<const unsigned char *>(X.W32 + (size_t)cid * NK * TREE_WS32);
                 const float ycx = __double2float_rn(__dsub_rn(T.y[0], C.c[0]));
                 const float ycy = __double2float_rn(__dsub_rn(T.y[1], C.c[1]));
                 const float ycz = __double2float_rn(__dsub_rn(T.y[2], C.c[2]));
-                ok = staged<BUFB / 64>(buf, mbar, phase, src, NK, 64, lane, [&](const unsigned char *bp, int k0, int n) {
+                ok = staged<BUFB / 48>(buf, mbar, phase, src, NK, 48, lane, [&](const unsigned char *bp, int k0, int n) {
                     if (!acc_c) return;
                     const float4 *w4 = reinterpret_cast<const float4 *>(bp);
                     int k1 = k0 / (P1 * P1), k2 = (k0 / P1) % P1, k3 = k0 % P1;
@@ -548,9 +557,8 @@ __global__ void __launch_bounds__(TBT, 4) k_tree_walk(EvalArgs A, TreeEval X) {
                     float dxy2 = fmaf(dy, dy, dx * dx), dq0xy = fmaf(dy, q0y, dx * q0x);
                     float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f, a4 = 0.f, a5 = 0.f;
                     for (int j = 0; j < n; ++j) {
-                        // w0 = (wf0 wf1 wf2 wn0), w1 = (wn1 wn2 qn00 qn01),
-                        // w2 = (qn02 qn10 qn11 qn12), w3 = (qn20 qn21 qn22 0)
-                        const float4 w0 = w4[4 * j], w1 = w4[4 * j + 1], w2 = w4[4 * j + 2], w3 = w4[4 * j + 3];
+                        // w0 = (wf0 wf1 wf2 wn0), w1 = (wn1 wn2 S00 S11), w2 = (S22 S01 S02 S12)
+                        const float4 w0 = w4[3 * j], w1 = w4[3 * j + 1], w2 = w4[3 * j + 2];
                         const float dz = ycz - hwc[2][k3];
                         const float r2 = fmaf(dz, dz, dxy2);
                         const float ri = rsqrt_ftz(r2), ri2 = ri * ri;
@@ -563,10 +571,10 @@ __global__ void __launch_bounds__(TBT, 4) k_tree_walk(EvalArgs A, TreeEval X) {
                         }
                         if (DL) {
                             const float dWn = fmaf(dz, w1.y, fmaf(dy, w1.x, dx * w0.w));
-                            const float t0 = fmaf(dz, w2.x, fmaf(dy, w1.w, dx * w1.z));
-                            const float t1 = fmaf(dz, w2.w, fmaf(dy, w2.z, dx * w2.y));
-                            const float t2 = fmaf(dz, w3.z, fmaf(dy, w3.y, dx * w3.x));
-                            const float quad = fmaf(dz, t2, fmaf(dy, t1, dx * t0));
+                            // d.S.d = dx (S00 dx + S01 dy + S02 dz) + dy (S11 dy + S12 dz) + S22 dz^2
+                            const float t0 = fmaf(dz, w2.z, fmaf(dy, w2.y, dx * w1.z));
+                            const float t1 = fmaf(dz, w2.w, dy * w1.w);
+                            const float quad = fmaf(dx, t0, fmaf(dy, t1, w2.x * dz * dz));
                             const float dq0 = fmaf(dz, q0z, dq0xy);
                             const float sv = fmaf(-dq0, dWn, quad) * (ri2 * ri2 * ri);
                             a3 = fmaf(dx, sv, a3);
@@ -762,7 +770,7 @@ int tree_prepare(ers_surface *s, int n0, int p, bool mixed, cudaStream_t st) {
         t->have_w32 = false;
     }
     if (mixed && !t->have_w32) {
-        const size_t bytes = sizeof(float) * (size_t)t->ncl * NK * TREE_WS;
+        const size_t bytes = sizeof(float) * (size_t)t->ncl * NK * TREE_WS32;
         if (bytes > t->w32_cap) {
             if (t->W32) cudaFree(t->W32);
             t->W32 = nullptr;

@@ -361,6 +361,11 @@ def learned_leg(ers, torch, s, wl, y, steps: int, warmup: int):
            "training": {"samples_per_network": nsamples, "densities": 5, "steps": 3000, "batch": 8192,
                         "data_s": t_data, "train_s": t_train}}
     args = (yed, x0, n0, b, f0, q0, gf0, gq0)
+    # the same closures with the network's output set to zero: what the network gains over the
+    # one- or two-delta sums alone
+    zero = ers.Closure(seed=0)
+    for layer in (0, 1):
+        zero.set_params(layer, np.zeros(ers.NPARAM, np.float32))
     for nd in (2, 1):
         t_val, out = timed(lambda: ers.eval_learned(sa, nets[nd], *args, rho=wl.rho, precision=ers.PREC_MIXED,
                                                     tol=1e-5, vstride=32, ndelta=nd, u=u, v=v))
@@ -377,6 +382,13 @@ def learned_leg(ers, torch, s, wl, y, steps: int, warmup: int):
                              "SL": float(np.abs(ul - u_ref).max() / np.abs(u_ref).max()),
                              "DL": float(np.abs(vl - v_ref).max() / np.abs(v_ref).max())}},
             "final_train_loss": losses[nd]}
+        _, _, verr0, _ = ers.eval_learned(sa, zero, *args, rho=wl.rho, precision=ers.PREC_MIXED, tol=1e30,
+                                          vstride=32, ndelta=nd, u=u, v=v)
+        u0, v0 = u.cpu().numpy(), v.cpu().numpy()
+        res[f"ndelta{nd}"]["without_network"] = {
+            "validation_rel_err": [float(z) for z in verr0],
+            "max_rel_err_vs_three_delta": {"SL": float(np.abs(u0 - u_ref).max() / np.abs(u_ref).max()),
+                                           "DL": float(np.abs(v0 - v_ref).max() / np.abs(v_ref).max())}}
     return res
 
 

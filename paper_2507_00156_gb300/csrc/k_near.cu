@@ -253,7 +253,6 @@ __global__ void __launch_bounds__(WPB * 32, NEAR_MIN_BLOCKS) k_near(EvalArgs A, 
     __shared__ Geom sG[WPB];
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     // one target per warp; a capped grid strides over the targets
-    // one target per warp; a capped grid strides over the targets
     for (int64_t m = (int64_t)blockIdx.x * WPB + wib; m < A.M; m += (int64_t)gridDim.x * WPB)
         near_target<PREC, SL, DL, ND>(A, P, tab, m, lane, sq[wib], sG[wib], Ps);
 }

@@ -136,9 +136,18 @@ def test_learned_closure_gains_over_the_single_delta_sum_and_falls_back(ers):
         assert rL < 0.2 * r1, (rL, r1)
         assert eL.max() < 0.5 * e1.max(), (eL.max(), e1.max())
     assert errL[0] < err1[0] and errL[1] < err1[1]
-    # two deltas: finite, and the validation ratio is reported
+    # two deltas: the network predicts the c2 term of the two-delta combination.  c2 carries
+    # quadrature error that local features do not determine, and at h = 1/32 the prediction gains
+    # nothing (single layer RMS error 2.25e-4 with the network, 2.18e-4 without); it must not do
+    # worse than the combination alone by more than that.
     u2, v2, err2, fb2 = ers.eval_learned(s, nets[2], *args, precision=0, tol=1.0, vstride=8, ndelta=2)
     assert np.isfinite(u2.cpu().numpy()).all() and np.isfinite(v2.cpu().numpy()).all() and not fb2
+    u20, v20, err20, _ = ers.eval_learned(s, zero, *args, precision=0, tol=1.0, vstride=8, ndelta=2)
+    for (a, b_, ref3) in ((u2, u20, u3), (v2, v20, v3)):
+        rL = np.sqrt(((a.cpu().numpy() - ref3) ** 2).mean())
+        r0 = np.sqrt(((b_.cpu().numpy() - ref3) ** 2).mean())
+        print("two-delta RMS error with / without the network:", rL, r0)
+        assert rL < 1.25 * r0, (rL, r0)
     # fallback: an impossible tolerance gives exactly the three-delta result
     uF, vF, _, fb = ers.eval_learned(s, nets[1], *args, precision=0, tol=1e-15, vstride=8, ndelta=1)
     assert fb

@@ -270,32 +270,45 @@ def two_drop_leg(ers, torch, fine: bool):
                     "iterations 13, 12, 12; max 3.17e-3, 1.07e-4, 4.06e-6; L2 1.19e-4, 6.11e-6, 2.11e-7"}
 
 
-def learned_leg(ers, torch, s, wl, y, steps: int, warmup: int):
+TRAIN_RADII = (1.0, 1.0, 0.85, 0.85, 0.7)  # one seeded density each
+
+
+def learned_leg(ers, torch, s, wl, steps: int, warmup: int):
     """The learned near-field closure: networks trained on the GPU (own kernels) from five seeded
-    densities on the bench surface (unit sphere, h = 1/128), then evaluated on the two unit
-    spheres 0.01 apart at h = 1/96: the integral over the first sphere at the nodes of both, with
-    validation against the three-delta method (tolerance 1e-5, every 32nd target) and fallback to
-    it.  Also timed with the closure accepted unconditionally (no fallback), against the plain
-    mixed evaluation of the same problem."""
+    densities on spheres at the bench spacing h = 1/128 (the bench surface and spheres of radius
+    0.85 and 0.7, so that the curvature feature kappa h spans 1/128 .. 1/90 and covers the
+    evaluation's 1/96; targets: the nodes and 200,000 band points |b| <= 6 rho_2 h, the two-delta
+    closure's near radius), then evaluated on the two unit spheres 0.01 apart at h = 1/96: the
+    integral over the first sphere at the nodes of both, with validation against the three-delta
+    method (tolerance 1e-5, every 32nd target) and fallback to it.  Also timed with the closure
+    accepted unconditionally (no fallback), against the plain mixed evaluation of the same
+    problem."""
     dev = torch.device("cuda")
     t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
-    yd = t(y)
-    x0, n0, b = s.closest_point(yd)
-    x0h = x0.cpu().numpy()
-    x = s.nodes()[0].cpu().numpy()
     rng = np.random.default_rng(5005)
     data = {1: [], 2: []}
+    band_w = 6.0 * wl.rho[1] * wl.h
     t0 = time.perf_counter()
-    for _ in range(5):
+    surfs = {}
+    for R in TRAIN_RADII:
+        if R not in surfs:
+            sh = workloads.Shape((0.0, 0.0, 0.0), (R, R, R))
+            sR = s if R == 1.0 else ers.Surface(sh.center, sh.axes, wl.h)
+            xR = sR.nodes()[0].cpu().numpy()
+            yd = t(np.concatenate([xR, workloads.near_band_targets(sh, 200000, band_w, rng)[0]]))
+            x0, n0, b = sR.closest_point(yd)
+            surfs[R] = (sR, xR, yd, x0, n0, b, x0.cpu().numpy())
+        sR, x, yd, x0, n0, b, x0h = surfs[R]
         fc, qc = workloads.density_coeffs(rng), workloads.density_coeffs(rng)
-        s.set_density(t(workloads.poly_eval(fc, x)), t(workloads.poly_eval(qc, x)))
+        sR.set_density(t(workloads.poly_eval(fc, x)), t(workloads.poly_eval(qc, x)))
         f0, q0 = t(workloads.poly_eval(fc, x0h)), t(workloads.poly_eval(qc, x0h))
         gf0, gq0 = t(workloads.poly_jacobian(fc, x0h)), t(workloads.poly_jacobian(qc, x0h))
-        u3, v3 = s.eval(yd, f0, q0, rho=wl.rho, precision=ers.PREC_MIXED, x0=x0, n0=n0, b=b)
+        u3, v3 = sR.eval(yd, f0, q0, rho=wl.rho, precision=ers.PREC_MIXED, x0=x0, n0=n0, b=b)
         for nd in (1, 2):
-            out = ers.closure_data(s, yd, x0, n0, b, f0, q0, gf0, gq0, u3, v3, rho=wl.rho, ndelta=nd)
+            out = ers.closure_data(sR, yd, x0, n0, b, f0, q0, gf0, gq0, u3, v3, rho=wl.rho, ndelta=nd)
             sel = out[4].bool()
             data[nd].append([z[sel] for z in out[:4]])
+    del surfs
     t_data = time.perf_counter() - t0
     nets, losses = {}, {}
     t0 = time.perf_counter()
@@ -353,8 +366,9 @@ def learned_leg(ers, torch, s, wl, y, steps: int, warmup: int):
     e64.record(stream)
     e64.synchronize()
     t_fp64 = a64.elapsed_time(e64) / 1e3
-    res = {"workload": "train: unit sphere h=1/128, 5 seeded densities; evaluate: two unit spheres gap 0.01, "
-                       "h=1/96, integral over the first at the nodes of both",
+    res = {"workload": "train: spheres of radius 1, 1, 0.85, 0.85, 0.7 at h=1/128, one seeded density each, "
+                       "nodes + 200k band points |b| <= 18h; evaluate: two unit spheres gap 0.01, h=1/96, "
+                       "integral over the first at the nodes of both",
            "targets": M, "nodes": int(xa.shape[0]),
            "plain_fp64": {"value": M / t_fp64, "unit": UNIT, "ms_per_step": t_fp64 * 1e3},
            "plain_mixed": {"value": M / t_plain, "unit": UNIT, "ms_per_step": t_plain * 1e3},
@@ -376,6 +390,7 @@ def learned_leg(ers, torch, s, wl, y, steps: int, warmup: int):
         res[f"ndelta{nd}"] = {
             "value": M / t_val, "unit": UNIT, "ms_per_step": t_val * 1e3,
             "fell_back_at_tol_1e-5": bool(fb), "validation_rel_err": [float(z) for z in verr],
+            "targets_outside_training_extent": nets[nd].last_out_of_range(),
             "accepted": {"value": M / t_acc, "ms_per_step": t_acc * 1e3,
                          "speedup_vs_plain_mixed": t_plain / t_acc, "speedup_vs_plain_fp64": t_fp64 / t_acc,
                          "max_rel_err_vs_three_delta": {
@@ -663,7 +678,7 @@ def main():
     if not args.no_batched:
         line["batched"] = batched_leg(ers, torch, steps=2, warmup=1)
     if not args.no_learned and args.workload == WORKLOAD:
-        line["learned"] = learned_leg(ers, torch, s, wl, y, steps=args.steps, warmup=1)
+        line["learned"] = learned_leg(ers, torch, s, wl, steps=args.steps, warmup=1)
     if not args.no_two_drop and args.workload == WORKLOAD:
         line["two_drop"] = two_drop_leg(ers, torch, fine=args.two_drop_fine)
     if world == 1 and not args.no_cpu_baseline:

@@ -298,6 +298,27 @@ int ers_closure_infer_reference(ers_closure *c, int layer, const float *X, int64
 /* *timed_out = 1 if a bounded tensor-core wait expired in an inference call (synchronous). */
 int ers_closure_status(ers_closure *c, int *timed_out);
 
+/*
+ * The extent of the features one network was trained on: get and/or set host arrays of 26 floats,
+ * lo[13] then hi[13], one pair per feature (lambda_0, the two principal curvatures times h, the
+ * nine scaled density components, rho_0).  ers_closure_train widens the extent to cover every
+ * feature vector it trains on (non-finite values are skipped); set replaces it (lo <= hi for
+ * every feature, else ERS_E_INVAL).  *have (may be NULL) = 1 once the extent is known, 0 before.
+ * Synchronous.
+ */
+int ers_closure_range(ers_closure *c, int layer, float *get, const float *set, int *have);
+
+/*
+ * With the check enabled (the default), ers_eval_learned evaluates every corrected target whose
+ * features leave the extent of a network that has one (each feature widened by 5 % of its width
+ * plus 1e-3 of its magnitude plus 1e-6) with the three-delta method instead of the network: the
+ * network is not used where it was not trained.  enabled = 0 turns the check off.
+ */
+int ers_closure_set_range_check(ers_closure *c, int enabled);
+
+/* *n = the number of targets of the last ers_eval_learned call that left the extent. */
+int ers_closure_last_out_of_range(ers_closure *c, int64_t *n);
+
 /* Loss L = (1/n) sum_s 1/2 |y_s - t_s|^2 over the 3 outputs and its gradient G (10448 floats dev)
  * with respect to the FP32 parameters (BF16 rounding in the forward pass, straight-through in the
  * backward pass).  X (n,16), T (n,4) floats dev; *loss (host) may be NULL.  Synchronizes when
@@ -330,9 +351,11 @@ int ers_closure_data(ers_surface *s, const ers_params *p, const double *y, int64
 
 /*
  * Both layers with the learned closure: far field (precision of p) + two-delta near sums +
- * network correction, then a validation: every vstride-th target is also evaluated with ers_eval
- * (three deltas) and if max|learned - method| / max|method| over that sample exceeds tol for
- * either layer, the whole call falls back to ers_eval (*fell_back = 1).  val_err[2] (host, may be
+ * network correction; targets whose features leave the training extent (ers_closure_range,
+ * ers_closure_set_range_check) take the three-delta method instead; then a validation: every
+ * vstride-th target is also evaluated with ers_eval (three deltas) and if
+ * max|learned - method| / max|method| over that sample exceeds tol for either layer, the whole
+ * call falls back to ers_eval (*fell_back = 1).  val_err[2] (host, may be
  * NULL) receives the two measured ratios.  Synchronizes the stream (to read the validation).
  * Errors as ers_eval, plus ERS_E_TIMEOUT when a tensor-core wait expired.
  */

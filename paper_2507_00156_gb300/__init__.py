@@ -42,7 +42,8 @@ EXPORTS = ["ers_build_surface", "ers_surface_free", "ers_surface_info", "ers_set
            "ers_eval", "ers_eval_SL", "ers_eval_DL", "ers_eval_host", "ers_last_counts", "ers_profile",
            "ers_last_profile", "ers_set_density_multi", "ers_batch_create", "ers_batch_launch", "ers_batch_info",
            "ers_batch_free", "ers_closure_create", "ers_closure_free", "ers_closure_params", "ers_closure_infer",
-           "ers_closure_infer_reference", "ers_closure_status", "ers_closure_grad", "ers_closure_train",
+           "ers_closure_infer_reference", "ers_closure_status", "ers_closure_range", "ers_closure_set_range_check",
+           "ers_closure_last_out_of_range", "ers_closure_grad", "ers_closure_train",
            "ers_closure_data", "ers_eval_learned", "ers_eval_noalloc", "ers_treecode_defaults", "ers_tree_stats",
            "ers_node_interp", "ers_vec_axpby", "ers_gmres", "ers_last_error", "ers_version"]
 ERS_W_NOT_CONVERGED = 2
@@ -50,6 +51,7 @@ ERS_W_NOT_CONVERGED = 2
 # ers_matvec_fn: int (*)(void *ctx, const double *x, double *y, void *stream)
 MATVEC_FN = ctypes.CFUNCTYPE(ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p)
 NPARAM = 10448
+NFEAT = 13  # closure features: lambda_0, kappa_1 h, kappa_2 h, nine scaled density components, rho_0
 NOALLOC_MAX_M = 524288
 
 
@@ -117,6 +119,9 @@ def lib():
             L.ers_closure_infer.argtypes = [vp, cint, vp, i64, vp, vp]
             L.ers_closure_infer_reference.argtypes = [vp, cint, vp, i64, vp, vp]
             L.ers_closure_status.argtypes = [vp, P(cint)]
+            L.ers_closure_range.argtypes = [vp, cint, vp, vp, P(cint)]
+            L.ers_closure_set_range_check.argtypes = [vp, cint]
+            L.ers_closure_last_out_of_range.argtypes = [vp, P(i64)]
             L.ers_closure_grad.argtypes = [vp, cint, vp, vp, i64, vp, P(dbl), vp]
             L.ers_closure_train.argtypes = [vp, cint, vp, vp, i64, cint, cint, ctypes.c_float, P(dbl), vp]
             L.ers_closure_data.argtypes = [vp, P(_Params), vp, i64] + [vp] * 9 + [cint] + [vp] * 6
@@ -448,6 +453,29 @@ class Closure:
         v = ctypes.c_int()
         check(lib().ers_closure_status(self._h, ctypes.byref(v)))
         return bool(v.value)
+
+    def feature_range(self, layer: int):
+        """(lo, hi) float32 arrays of the 13 features' training extent, or None while unknown."""
+        import numpy as np
+        out = np.empty(2 * NFEAT, dtype=np.float32)
+        have = ctypes.c_int()
+        check(lib().ers_closure_range(self._h, layer, ctypes.c_void_p(out.ctypes.data), None, ctypes.byref(have)))
+        return (out[:NFEAT], out[NFEAT:]) if have.value else None
+
+    def set_feature_range(self, layer: int, lo, hi):
+        import numpy as np
+        a = np.ascontiguousarray(np.concatenate([np.asarray(lo, np.float32), np.asarray(hi, np.float32)]))
+        if a.shape != (2 * NFEAT,):
+            raise ValueError(f"lo and hi need {NFEAT} entries each")
+        check(lib().ers_closure_range(self._h, layer, None, ctypes.c_void_p(a.ctypes.data), None))
+
+    def set_range_check(self, enabled: bool):
+        check(lib().ers_closure_set_range_check(self._h, 1 if enabled else 0))
+
+    def last_out_of_range(self) -> int:
+        n = ctypes.c_int64()
+        check(lib().ers_closure_last_out_of_range(self._h, ctypes.byref(n)))
+        return n.value
 
     def grad(self, layer: int, X, T, stream=None):
         import torch

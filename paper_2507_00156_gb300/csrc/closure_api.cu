@@ -35,9 +35,14 @@ struct ers_closure {
     float *m[2] = {nullptr, nullptr}, *v[2] = {nullptr, nullptr};  // Adam moments
     int step[2] = {0, 0};
     int *err = nullptr;
+    // extent of the training features: [layer][0 lo, 1 hi][feature] as order-preserving int keys
+    int *range = nullptr;
+    int have_range[2] = {0, 0};
+    int range_check = 1;     // ers_eval_learned sends targets outside the extent to the method
+    int64_t last_out = 0;    // targets of the last ers_eval_learned that were outside it
     Scratch z, a, d4, d, g, idx, loss;
     // evaluation work buffers
-    Scratch feat, scale, gamma, outp, sub, valid;
+    Scratch feat, scale, gamma, outp, sub, valid, oor;
 };
 
 namespace ers {
@@ -234,6 +239,98 @@ __global__ void k_minibatch(int *__restrict__ idx, int n, int64_t total, uint64_
     idx[i] = (int)(z % (uint64_t)total);
 }
 
+// Order-preserving map of a float to an int (and its inverse, the same map): integer order of the
+// keys = numeric order of the floats, so that atomicMin / atomicMax on keys track a float extent.
+__host__ __device__ __forceinline__ int range_key(int bits) { return bits >= 0 ? bits : bits ^ 0x7fffffff; }
+
+constexpr int RANGE_STRIDE = 2 * IN;  // ints per layer: lo[IN], hi[IN]
+
+// Widen the extent keys[0..NFEAT) (lo), keys[IN..IN+NFEAT) (hi) to cover the finite features of
+// samples X (n, IN).
+__global__ void k_range_update(const float *__restrict__ X, int64_t n, int *__restrict__ keys) {
+    int lo[NFEAT], hi[NFEAT];
+#pragma unroll
+    for (int f = 0; f < NFEAT; ++f) {
+        lo[f] = 0x7fffffff;
+        hi[f] = (int)0x80000000;
+    }
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+#pragma unroll
+        for (int f = 0; f < NFEAT; ++f) {
+            const float x = X[i * IN + f];
+            if (!isfinite(x)) continue;
+            const int k = range_key(__float_as_int(x));
+            lo[f] = min(lo[f], k);
+            hi[f] = max(hi[f], k);
+        }
+    }
+#pragma unroll
+    for (int f = 0; f < NFEAT; ++f) {
+        const int l = __reduce_min_sync(0xffffffffu, lo[f]), h = __reduce_max_sync(0xffffffffu, hi[f]);
+        if ((threadIdx.x & 31) == 0) {
+            atomicMin(keys + f, l);
+            atomicMax(keys + IN + f, h);
+        }
+    }
+}
+
+// Targets whose features (of a layer with a known extent) lie outside that extent widened by
+// 5 % of its width plus 1e-3 of its magnitude plus 1e-6: their indices are appended to idx.
+// Only corrected targets (density scale > 0) are checked.
+__global__ void k_range_flags(const float *__restrict__ Xs, const float *__restrict__ Xd,
+                              const double *__restrict__ scale, int64_t M, const int *__restrict__ keys, int have0,
+                              int have1, int64_t *__restrict__ idx, unsigned long long *__restrict__ count) {
+    const int64_t m = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (m >= M) return;
+    bool out = false;
+    for (int layer = 0; layer < 2; ++layer) {
+        if (!(layer == 0 ? have0 : have1) || !(scale[2 * m + layer] > 0.0)) continue;
+        const float *X = (layer == 0 ? Xs : Xd) + m * IN;
+        const int *K = keys + layer * RANGE_STRIDE;
+        for (int f = 0; f < NFEAT; ++f) {
+            const float lo = __int_as_float(range_key(K[f])), hi = __int_as_float(range_key(K[IN + f]));
+            // explicit roundings (no contraction), so that a host computation can repeat the decision
+            const float tol = __fadd_rn(__fadd_rn(__fmul_rn(0.05f, __fsub_rn(hi, lo)),
+                                                  __fmul_rn(1e-3f, fmaxf(fabsf(lo), fabsf(hi)))),
+                                        1e-6f);
+            const float x = X[f];
+            if (!(x >= __fsub_rn(lo, tol) && x <= __fadd_rn(hi, tol))) out = true;
+        }
+    }
+    if (out) idx[atomicAdd(count, 1ull)] = m;
+}
+
+// Gather the targets idx[0..K) (and their closest-point data and densities) into a compact set
+// (the layout of k_gather), and scatter results back.
+__global__ void k_gather_idx(const double *__restrict__ y, const double *__restrict__ x0,
+                             const double *__restrict__ n0, const double *__restrict__ b,
+                             const double *__restrict__ f0, const double *__restrict__ q0,
+                             const int64_t *__restrict__ idx, int64_t K, double *__restrict__ out) {
+    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= K) return;
+    const int64_t m = idx[k];
+    for (int i = 0; i < 3; ++i) {
+        out[3 * k + i] = y[3 * m + i];
+        out[3 * K + 3 * k + i] = x0[3 * m + i];
+        out[6 * K + 3 * k + i] = n0[3 * m + i];
+        out[10 * K + 3 * k + i] = f0[3 * m + i];
+        out[13 * K + 3 * k + i] = q0[3 * m + i];
+    }
+    out[9 * K + k] = b[m];
+}
+
+__global__ void k_scatter_idx(const double *__restrict__ up, const double *__restrict__ vp,
+                              const int64_t *__restrict__ idx, int64_t K, double *__restrict__ u,
+                              double *__restrict__ v) {
+    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= K) return;
+    const int64_t m = idx[k];
+    for (int i = 0; i < 3; ++i) {
+        u[3 * m + i] = up[3 * k + i];
+        v[3 * m + i] = vp[3 * k + i];
+    }
+}
+
 int closure_check(const ers_closure *c, int layer) {
     if (!c) return fail(ERS_E_INVAL, "NULL closure");
     if (layer != 0 && layer != 1) return fail(ERS_E_INVAL, "layer must be 0 (single) or 1 (double)");
@@ -252,8 +349,9 @@ void free_closure(ers_closure *c) {
         if (c->v[l]) cudaFree(c->v[l]);
     }
     if (c->err) cudaFree(c->err);
+    if (c->range) cudaFree(c->range);
     Scratch *ss[] = {&c->z, &c->a, &c->d4, &c->d, &c->g, &c->idx, &c->loss, &c->feat, &c->scale, &c->gamma,
-                     &c->outp, &c->sub, &c->valid};
+                     &c->outp, &c->sub, &c->valid, &c->oor};
     for (Scratch *s : ss)
         if (s->ptr) cudaFree(s->ptr);
     delete c;
@@ -291,6 +389,7 @@ int ers_closure_create(uint64_t seed, ers_closure **out) {
         if (e == cudaSuccess) e = cudaMalloc(&c->v[l], sizeof(float) * mlp::NPARAM);
     }
     if (e == cudaSuccess) e = cudaMalloc(&c->err, sizeof(int));
+    if (e == cudaSuccess) e = cudaMalloc(&c->range, sizeof(int) * 2 * RANGE_STRIDE);
     if (e != cudaSuccess) {
         cudaGetLastError();
         free_closure(c);
@@ -316,6 +415,15 @@ int ers_closure_create(uint64_t seed, ers_closure **out) {
         if (e != cudaSuccess) break;
     }
     if (e == cudaSuccess) e = cudaMemset(c->err, 0, sizeof(int));
+    if (e == cudaSuccess) {  // empty extents: lo = +inf, hi = -inf
+        std::vector<int> k(2 * RANGE_STRIDE);
+        for (int l = 0; l < 2; ++l)
+            for (int f = 0; f < mlp::IN; ++f) {
+                k[l * RANGE_STRIDE + f] = range_key(0x7f800000);
+                k[l * RANGE_STRIDE + mlp::IN + f] = range_key((int)0xff800000u);
+            }
+        e = cudaMemcpy(c->range, k.data(), sizeof(int) * k.size(), cudaMemcpyHostToDevice);
+    }
     if (e != cudaSuccess) {
         free_closure(c);
         return cuda_fail(e, "ers_closure_create: initialisation");
@@ -358,6 +466,56 @@ int ers_closure_infer_reference(ers_closure *c, int layer, const float *X, int64
     cudaError_t e = mlp::launch_quantize(c->p[layer], c->q[layer], st);
     if (e == cudaSuccess) e = mlp::launch_infer_ref(c->q[layer], X, n, Y, st);
     if (e != cudaSuccess) return cuda_fail(e, "ers_closure_infer_reference");
+    return ERS_OK;
+}
+
+int ers_closure_range(ers_closure *c, int layer, float *get, const float *set, int *have) {
+    clear_error();
+    int rc = closure_check(c, layer);
+    if (rc != ERS_OK) return rc;
+    int *dev = c->range + layer * RANGE_STRIDE;
+    cudaError_t e = cudaSuccess;
+    if (set) {
+        int k[RANGE_STRIDE];
+        for (int f = 0; f < mlp::IN; ++f) {
+            const bool used = f < NFEAT;
+            const float lo = used ? set[f] : INFINITY, hi = used ? set[NFEAT + f] : -INFINITY;
+            if (used && !(lo <= hi)) return fail(ERS_E_INVAL, "ers_closure_range: need lo <= hi for every feature");
+            int bl, bh;
+            std::memcpy(&bl, &lo, sizeof bl);
+            std::memcpy(&bh, &hi, sizeof bh);
+            k[f] = range_key(bl);
+            k[mlp::IN + f] = range_key(bh);
+        }
+        e = cudaMemcpy(dev, k, sizeof k, cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) c->have_range[layer] = 1;
+    }
+    if (e == cudaSuccess && get) {
+        int k[RANGE_STRIDE];
+        e = cudaMemcpy(k, dev, sizeof k, cudaMemcpyDeviceToHost);
+        if (e == cudaSuccess)
+            for (int f = 0; f < NFEAT; ++f) {
+                const int bl = range_key(k[f]), bh = range_key(k[mlp::IN + f]);
+                std::memcpy(get + f, &bl, sizeof bl);
+                std::memcpy(get + NFEAT + f, &bh, sizeof bh);
+            }
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "ers_closure_range");
+    if (have) *have = c->have_range[layer];
+    return ERS_OK;
+}
+
+int ers_closure_set_range_check(ers_closure *c, int enabled) {
+    clear_error();
+    if (!c) return fail(ERS_E_INVAL, "NULL closure");
+    c->range_check = enabled ? 1 : 0;
+    return ERS_OK;
+}
+
+int ers_closure_last_out_of_range(ers_closure *c, int64_t *n) {
+    clear_error();
+    if (!c || !n) return fail(ERS_E_INVAL, "ers_closure_last_out_of_range: NULL argument");
+    *n = c->last_out;
     return ERS_OK;
 }
 
@@ -414,6 +572,15 @@ int ers_closure_train(ers_closure *c, int layer, const float *X, const float *T,
     if ((rc = grow(c->idx, sizeof(int) * batch)) != ERS_OK) return rc;
     if ((rc = grow(c->g, sizeof(float) * mlp::NPARAM)) != ERS_OK) return rc;
     if ((rc = grow(c->loss, sizeof(double))) != ERS_OK) return rc;
+    {
+        int nsm = 152;
+        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, c->device);
+        const int64_t blocks = std::min<int64_t>((n + 255) / 256, 4 * (int64_t)nsm);
+        k_range_update<<<(unsigned)blocks, 256, 0, st>>>(X, n, c->range + layer * RANGE_STRIDE);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return cuda_fail(e, "ers_closure_train: feature extent");
+        c->have_range[layer] = 1;
+    }
     for (int s = 0; s < steps; ++s) {
         const bool last = s == steps - 1;
         k_minibatch<<<(batch + 255) / 256, 256, 0, st>>>((int *)c->idx.ptr, batch, n, c->seed + 7919 * layer,
@@ -560,6 +727,38 @@ int ers_eval_learned(ers_surface *s, ers_closure *c, const ers_params *p, const 
     k_apply<<<(unsigned)((M + 127) / 128), 128, 0, st>>>(n0, gm, sc, Ys, Yd, M, s->h, ndelta, u, v);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "closure correction kernel");
+    // 4b. targets whose features lie outside the training extent: the three-delta method instead
+    c->last_out = 0;
+    if (c->range_check && (c->have_range[0] || c->have_range[1])) {
+        // [count | pad | idx (M) | gathered inputs (16 K) | u, v (6 K)], K <= M
+        if ((rc = grow(c->oor, sizeof(int64_t) * 2 + sizeof(int64_t) * (size_t)M + sizeof(double) * (size_t)M * 22)) !=
+            ERS_OK)
+            return rc;
+        unsigned long long *cnt = (unsigned long long *)c->oor.ptr;
+        int64_t *idx = (int64_t *)c->oor.ptr + 2;
+        double *sub = (double *)(idx + M);
+        e = cudaMemsetAsync(cnt, 0, sizeof(unsigned long long), st);
+        if (e != cudaSuccess) return cuda_fail(e, "ers_eval_learned: memset");
+        k_range_flags<<<(unsigned)((M + 127) / 128), 128, 0, st>>>(Xs, Xd, sc, M, c->range, c->have_range[0],
+                                                                   c->have_range[1], idx, cnt);
+        unsigned long long K = 0;
+        e = cudaGetLastError();
+        if (e == cudaSuccess) e = cudaMemcpyAsync(&K, cnt, sizeof K, cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) return cuda_fail(e, "ers_eval_learned: feature extent check");
+        const int64_t Kt = (int64_t)K;
+        c->last_out = Kt;
+        if (Kt > 0) {
+            double *up = sub + 16 * Kt, *vp = up + 3 * Kt;
+            k_gather_idx<<<(unsigned)((Kt + 127) / 128), 128, 0, st>>>(y, x0, n0, b, f0, q0, idx, Kt, sub);
+            if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "ers_eval_learned: gather");
+            if ((rc = ers_eval(s, &pp, sub, Kt, sub + 3 * Kt, sub + 6 * Kt, sub + 9 * Kt, sub + 10 * Kt,
+                               sub + 13 * Kt, up, vp, stream)) < 0)
+                return rc;
+            k_scatter_idx<<<(unsigned)((Kt + 127) / 128), 128, 0, st>>>(up, vp, idx, Kt, u, v);
+            if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "ers_eval_learned: scatter");
+        }
+    }
     // 5. validation against the three-delta method on every vstride-th target
     const int64_t Ms = (M + vstride - 1) / vstride;
     if ((rc = grow(c->sub, sizeof(double) * ((size_t)Ms * 22 + 8))) != ERS_OK) return rc;

@@ -152,3 +152,109 @@ def test_learned_closure_gains_over_the_single_delta_sum_and_falls_back(ers):
     uF, vF, _, fb = ers.eval_learned(s, nets[1], *args, precision=0, tol=1e-15, vstride=8, ndelta=1)
     assert fb
     assert np.array_equal(uF.cpu().numpy(), u3) and np.array_equal(vF.cpu().numpy(), v3)
+
+
+def test_feature_range_tracks_the_training_features(ers):
+    import torch
+    c = ers.Closure(seed=5)
+    assert c.feature_range(0) is None and c.feature_range(1) is None
+    rng = np.random.default_rng(4)
+    X = rng.uniform(-3, 2, (5000, 16)).astype(np.float32)
+    X[:, 13:] = 0.0
+    X[7, 2] = np.nan  # non-finite features are skipped
+    X[9, 5] = np.inf
+    T = np.zeros((5000, 4), np.float32)
+    c.train(0, torch.from_numpy(X).cuda(), torch.from_numpy(T).cuda(), steps=2, batch=256)
+    lo, hi = c.feature_range(0)
+    F = X[:, :13].astype(np.float64)
+    F[~np.isfinite(F)] = np.nan
+    assert np.array_equal(lo, np.nanmin(F, 0).astype(np.float32))
+    assert np.array_equal(hi, np.nanmax(F, 0).astype(np.float32))
+    assert c.feature_range(1) is None
+    # training again widens the extent
+    X2 = X.copy()
+    X2[0, 0] = 50.0
+    c.train(0, torch.from_numpy(X2).cuda(), torch.from_numpy(T).cuda(), steps=1, batch=256)
+    lo2, hi2 = c.feature_range(0)
+    assert hi2[0] == 50.0 and np.array_equal(lo2, lo) and np.array_equal(hi2[1:], hi[1:])
+    c.set_feature_range(1, lo - 1, hi + 1)
+    lo1, hi1 = c.feature_range(1)
+    assert np.array_equal(lo1, lo - 1) and np.array_equal(hi1, hi + 1)
+    with pytest.raises(ers.ErsError):
+        c.set_feature_range(1, hi + 1, lo)
+
+
+def _outside(net, Xs, Xd, corrected):
+    """The extent check of ers_eval_learned repeated on the host in the same FP32 roundings."""
+    out = np.zeros(len(Xs), bool)
+    f32 = np.float32
+    for layer, X in ((0, Xs), (1, Xd)):
+        lo, hi = net.feature_range(layer)
+        tol = (f32(0.05) * (hi - lo) + f32(1e-3) * np.maximum(np.abs(lo), np.abs(hi))) + f32(1e-6)
+        F = X[:, :13]
+        out |= corrected & ~((F >= lo - tol) & (F <= hi + tol)).all(1)
+    return out
+
+
+def test_targets_outside_the_training_extent_take_the_method(ers):
+    """A closure trained on the unit sphere at h = 1/32: on the training surface with a held-out
+    density the targets whose features leave the extent (as the host computes it) get the
+    three-delta value and the others the network's; on a sphere of radius 0.5 (twice the
+    curvature) every corrected target leaves it; with the check off the network is used."""
+    import torch
+    h = 1 / 32
+    rng = np.random.default_rng(31)
+    shape = workloads.unit_sphere()
+    s = ers.Surface(shape.center, shape.axes, h)
+    x = s.nodes()[0].cpu().numpy()
+    net = ers.Closure(seed=3)
+    data = []
+    for _ in range(4):
+        fc, qc = workloads.density_coeffs(rng), workloads.density_coeffs(rng)
+        band = workloads.near_band_targets(shape, 4000, 4 * h, rng)[0]
+        P = _problem(ers, s, shape, fc, qc, np.concatenate([x, band]), 0)
+        out = ers.closure_data(s, P["y"], P["x0"], P["n0"], P["b"], P["f0"], P["q0"], P["gf0"], P["gq0"],
+                               P["u3"], P["v3"], precision=0, ndelta=1)
+        sel = out[4].bool()
+        data.append([z[sel] for z in out[:4]])
+    Xs, Xd, Ts, Td = (torch.cat([d[i] for d in data]).contiguous() for i in range(4))
+    net.train(0, Xs, Ts, steps=300, batch=2048, lr=2e-3)
+    net.train(1, Xd, Td, steps=300, batch=2048, lr=2e-3)
+
+    def run(surf, sh, xs, check=True):
+        fc, qc = workloads.density_coeffs(rng), workloads.density_coeffs(rng)
+        band = workloads.near_band_targets(sh, 2000, 4 * h, rng)[0]
+        P = _problem(ers, surf, sh, fc, qc, np.concatenate([xs, band]), 0)
+        args = (P["y"], P["x0"], P["n0"], P["b"], P["f0"], P["q0"], P["gf0"], P["gq0"])
+        F = ers.closure_data(surf, *args, P["u3"], P["v3"], precision=0, ndelta=1)
+        outside = _outside(net, F[0].cpu().numpy(), F[1].cpu().numpy(), F[4].cpu().numpy().astype(bool))
+        net.set_range_check(check)
+        u, v, _, fb = ers.eval_learned(surf, net, *args, precision=0, tol=1e30, vstride=1 << 20, ndelta=1)
+        assert not fb
+        return (u.cpu().numpy(), v.cpu().numpy(), P["u3"].cpu().numpy(), P["v3"].cpu().numpy(), outside,
+                F[4].cpu().numpy().astype(bool))
+
+    # the training surface, a held-out density: some targets leave the extent of the density
+    # features, most do not
+    u, v, u3, v3, outside, corr = run(s, shape, x)
+    print("held-out density: targets outside the extent", outside.sum(), "of", corr.sum())
+    assert net.last_out_of_range() == outside.sum() < corr.sum()
+    if outside.any():
+        assert rel_err_max(u[outside], u3[outside]) <= 1e-12 and rel_err_max(v[outside], v3[outside]) <= 1e-12
+    inside = corr & ~outside
+    assert np.abs(u[inside] - u3[inside]).max() > 1e-9 * np.abs(u3).max()
+    # a sphere of radius 0.5: every target (within 4h of it) is corrected and leaves the extent
+    small = workloads.Shape((0.0, 0.0, 0.0), (0.5, 0.5, 0.5))
+    s2 = ers.Surface(small.center, small.axes, h)
+    x2 = s2.nodes()[0].cpu().numpy()
+    u, v, u3, v3, outside, corr = run(s2, small, x2)
+    assert corr.all() and outside.all() and net.last_out_of_range() == len(u)
+    assert rel_err_max(u, u3) <= 1e-12 and rel_err_max(v, v3) <= 1e-12
+    # with the check off the network is used everywhere
+    u, v, u3, v3, outside, corr = run(s2, small, x2, check=False)
+    assert net.last_out_of_range() == 0
+    assert rel_err_max(u, u3) > 1e-9
+
+
+def rel_err_max(a, ref):
+    return float(np.abs(a - ref).max() / np.abs(ref).max())

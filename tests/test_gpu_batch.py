@@ -116,3 +116,60 @@ def test_batch_rejects_bad_plans(ers):
     arr = (ers._Problem * 1)()
     h = ctypes.c_void_p()
     assert ers.lib().ers_batch_create(arr, 1, ctypes.byref(p), 2, ctypes.byref(h)) == ers.ERS_E_UNSUPPORTED
+
+
+@pytest.mark.parametrize("gap,n_bodies", [(0.1, 0), (0.05, 0), (0.01, 16)])
+def test_batched_full_size_sampled(ers, gap, n_bodies):
+    """The batched workload at full size, as the benchmark launches it: two unit spheres `gap`
+    apart at h = 1/96 (about 153,000 nodes each), each evaluated at the nodes of both, 8
+    densities per surface, and for gap 0.01 the 16 uneven bodies as well; seeded samples of
+    (problem, density, target) against the FP64 oracle, most of them in the gap region."""
+    import torch
+    nrhs = 8
+    pair, bodies = workloads.batched_config(gap=gap, nrhs=nrhs, n_bodies=n_bodies)
+    rng = np.random.default_rng(int(gap * 1000) + 7)
+
+    def surface(body):
+        s = ers.Surface(body.shape.center, body.shape.axes, body.h)
+        x = s.nodes()[0].cpu().numpy()
+        f = np.stack([workloads.poly_eval(c, x) for c in body.f_coefs])
+        q = np.stack([workloads.poly_eval(c, x) for c in body.q_coefs])
+        s.set_density_multi(torch.from_numpy(f).cuda(), torch.from_numpy(q).cuda())
+        return s, x
+
+    (sA, xA), (sB, xB) = surface(pair[0]), surface(pair[1])
+    yAB = np.concatenate([xA, xB])
+    probs = [_problem(sA, yAB, pair[0].f_coefs, pair[0].q_coefs), _problem(sB, yAB, pair[1].f_coefs, pair[1].q_coefs)]
+    shapes = [(pair[0], yAB), (pair[1], yAB)]
+    for i, body in enumerate(bodies):
+        s, x = surface(body)
+        band = workloads.near_band_targets(body.shape, max(1, len(x) // 20), 4 * body.h,
+                                           np.random.default_rng(2000 + i))[0]
+        y = np.concatenate([x, band])
+        probs.append(_problem(s, y, body.f_coefs, body.q_coefs))
+        shapes.append((body, y))
+    batch = ers.Batch(probs, nrhs, rho=(2, 3, 4))
+    batch.launch()
+    torch.cuda.synchronize()
+    nA = len(xA)
+    # A's integral at B's nodes that face A, B's at A's nodes that face B, and random targets
+    gapA = nA + np.flatnonzero(xB[:, 0] < pair[1].shape.center[0] - 0.8)
+    gapB = np.flatnonzero(xA[:, 0] > 0.8)
+    checks = [(0, np.concatenate([rng.choice(gapA, 40, replace=False), rng.choice(len(yAB), 20, replace=False)]), 0),
+              (0, rng.choice(gapA, 30, replace=False), nrhs - 1),
+              (1, np.concatenate([rng.choice(gapB, 40, replace=False), rng.choice(len(yAB), 20, replace=False)]), 3)]
+    for k in range(0, n_bodies, 5):
+        checks.append((2 + k, rng.choice(len(shapes[2 + k][1]), 30, replace=False), k % nrhs))
+    for p, sel, r in checks:
+        body, y_all = shapes[p]
+        ub, vb = probs[p]["u"][r].cpu().numpy(), probs[p]["v"][r].cpu().numpy()
+        assert np.isfinite(ub).all() and np.isfinite(vb).all()
+        xo, no, wo = oracle.quadrature(body.shape, body.h)
+        y = y_all[sel]
+        x0, n0, b = oracle.closest_point(body.shape, y)
+        fc, qc = body.f_coefs[r], body.q_coefs[r]
+        uo, vo, _ = oracle.evaluate(xo, no, wo, workloads.poly_eval(fc, xo), workloads.poly_eval(qc, xo), y, x0, n0, b,
+                                    workloads.poly_eval(fc, x0), workloads.poly_eval(qc, x0), body.h, (2, 3, 4), 6.0,
+                                    oracle.LOCALIZED)
+        assert rel_err(ub[sel], uo) <= MIXED_TOL and rel_err(vb[sel], vo) <= MIXED_TOL, (p, r, rel_err(ub[sel], uo),
+                                                                                          rel_err(vb[sel], vo))

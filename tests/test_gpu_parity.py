@@ -229,3 +229,19 @@ def test_full_size_bench_workload_sampled(ers, precision, tol):
     assert np.array_equal(y, y_all[sel])
     assert rel_err(u[sel], uo) <= tol and rel_err(v[sel], vo) <= tol, (rel_err(u[sel], uo), rel_err(v[sel], vo))
     assert np.isfinite(u).all() and np.isfinite(v).all()
+
+
+@pytest.mark.parametrize("precision,tol", [(0, FP64_TOL), (1, MIXED_TOL)])
+def test_full_size_ellipsoid_workload_sampled(ers, precision, tol):
+    """The plain-FP64-at-scale workload: ellipsoid (1, 0.8, 0.6) at h = 1/64, nodes + 60,000 band
+    points |b| <= 4 delta_3 + 20,000 box points, all targets in one launch; a seeded sample of
+    400 targets against the oracle."""
+    g = gpu("ellipsoid64")
+    y_all = g.targets()
+    u, v, b = g.eval(y_all, precision=precision)
+    sel = workloads.subsample(400, len(y_all), 6464)
+    y, uo, vo, bo = oracle_eval("ellipsoid64", sel=sel)
+    assert np.array_equal(y, y_all[sel])
+    assert np.array_equal(b[sel] == 0, bo == 0) and (bo == 0).sum() > 50
+    assert rel_err(u[sel], uo) <= tol and rel_err(v[sel], vo) <= tol, (rel_err(u[sel], uo), rel_err(v[sel], vo))
+    assert np.isfinite(u).all() and np.isfinite(v).all()

@@ -59,6 +59,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batched", action="store_true", help="skip the batched-launch leg")
     ap.add_argument("--no-learned", action="store_true", help="skip the learned-closure leg")
+    ap.add_argument("--batched-small", action="store_true",
+                    help="profiling only: the batched leg on two spheres at h = 1/32 and 4 bodies")
     ap.add_argument("--workload", default=WORKLOAD, help="profiling only: a smaller case (e.g. sphere64)")
     ap.add_argument("--no-two-drop", action="store_true", help="skip the two-drop (Sec. 4.3) leg")
     ap.add_argument("--two-drop-fine", action="store_true", help="two-drop leg: also h = 1/128 (FP64 treecode)")
@@ -175,12 +177,14 @@ def cpu_baseline(wl, y, seconds: float, gpu_results=None):
     return out, errs
 
 
-def batched_leg(ers, torch, steps: int, warmup: int):
+def batched_leg(ers, torch, steps: int, warmup: int, small: bool = False):
     """Two unit spheres 0.01 apart at h = 1/96 (each evaluated at the nodes of both) plus 16
     uneven bodies (own nodes + 5 % near band), 8 densities per surface, as ONE persistent launch
-    replayed from a CUDA graph.  Unit: (target, density) evaluations of both layers per second."""
+    replayed from a CUDA graph.  Unit: (target, density) evaluations of both layers per second.
+    small (profiling only): the spheres at h = 1/32 and 4 bodies."""
     nrhs = 8
-    pair, bodies = workloads.batched_config(nrhs=nrhs)
+    pair, bodies = (workloads.batched_config(nrhs=nrhs, n_bodies=4, h_pair=1 / 32) if small
+                    else workloads.batched_config(nrhs=nrhs))
     dev = torch.device("cuda")
     surfs = []
 
@@ -234,8 +238,9 @@ def batched_leg(ers, torch, steps: int, warmup: int):
             "ms_per_launch": total / steps * 1e3, "problems": len(probs), "nrhs": nrhs, "targets": targets,
             "surface_nodes": [s.N for s in surfs], "gpairs_x_rhs_per_s": steps * pairs * nrhs / total / 1e9,
             "work_items": nitems, "persistent_grid": grid, "launches_per_step": 1, "finite": ok,
-            "workload": "two unit spheres gap 0.01 at h=1/96 (self + neighbour nodes) + 16 bodies "
-                        "(semi-axes U[0.6,1], h in {1/32,1/48,1/64,1/96}, own nodes + 5% band), 8 densities"}
+            "workload": ("profiling case: two unit spheres gap 0.01 at h=1/32 + 4 bodies, 8 densities" if small else
+                         "two unit spheres gap 0.01 at h=1/96 (self + neighbour nodes) + 16 bodies "
+                         "(semi-axes U[0.6,1], h in {1/32,1/48,1/64,1/96}, own nodes + 5% band), 8 densities")}
 
 
 def two_drop_leg(ers, torch, fine: bool):
@@ -676,7 +681,7 @@ def main():
         line["mixed_vs_fp64_rel"] = {"SL": float(np.abs(u_mixed - u64).max() / np.abs(u64).max()),
                                      "DL": float(np.abs(v_mixed - v64).max() / np.abs(v64).max())}
     if not args.no_batched:
-        line["batched"] = batched_leg(ers, torch, steps=2, warmup=1)
+        line["batched"] = batched_leg(ers, torch, steps=2, warmup=1, small=args.batched_small)
     if not args.no_learned and args.workload == WORKLOAD:
         line["learned"] = learned_leg(ers, torch, s, wl, steps=args.steps, warmup=1)
     if not args.no_two_drop and args.workload == WORKLOAD:

@@ -600,11 +600,11 @@ def main():
     roof_near = {"kernel": "k_near (FP64 near sums + extrapolation)", "bound": "alu", "unit": "TFLOP/s",
                  "achieved": near_flops / (ms_near * 1e-3) / 1e12, "peak": FP64_PEAK_NOMINAL * scale / 1e12,
                  "peak_source": "nominal FP64 1.25 TFLOP/s x median SM clock / 2070 MHz",
-                 "units": "32 flops per regularized (node, delta) term, as the survey counts (erf, exp = 1 each)"}
+                 "units": "32 flops per regularized (node, delta) term: 30 flops, erf and exp counted as one op each"}
     roof_far = {"kernel": "k_far32 (FP32 far field, FP64 tile accumulation)", "bound": "alu", "unit": "TFLOP/s",
                 "achieved": far_flops / (ms_far * 1e-3) / 1e12, "peak": FP32_PEAK_NOMINAL * scale / 1e12,
                 "peak_source": "152 SMs x 128 FP32 lanes x 2 flop x median SM clock",
-                "units": "69 flops per far (target, node) pair, as the survey counts"}
+                "units": "69 flops per far (target, node) pair, both layers (FMA = 2, rsqrt = 1)"}
     for r in (roof_near, roof_far):
         r["frac"] = r["achieved"] / r["peak"]
         r["traffic"] = NCU_TRAFFIC.get((args.workload, r["kernel"].split()[0]))

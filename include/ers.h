@@ -44,7 +44,7 @@ extern "C" {
 #define ERS_E_NOMEM (-2)      /* device or host allocation failed */
 #define ERS_E_CUDA (-3)       /* a CUDA call failed; message holds the CUDA error string */
 #define ERS_E_TIMEOUT (-4)    /* a bounded device-side wait expired */
-#define ERS_E_UNSUPPORTED (-5)/* valid but not supported by this build (e.g. cutoff_t > 8) */
+#define ERS_E_UNSUPPORTED (-5)/* valid but not supported by the library (e.g. cutoff_t > 8) */
 #define ERS_E_STATE (-6)      /* call out of order (e.g. eval before set_density) */
 
 #define ERS_LAYER_SL 1

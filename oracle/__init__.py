@@ -50,52 +50,57 @@ def _load():
     global _lib
     with _lock:
         if _lib is None:
-            lib = ctypes.CDLL(build())
-            P = ctypes.POINTER(ctypes.c_double)
-            i64, dbl, cint = ctypes.c_int64, ctypes.c_double, ctypes.c_int
-            lib.ora_quadrature.restype = i64
-            lib.ora_quadrature.argtypes = [P, P, dbl, P, P, P]
-            lib.ora_closest_point.restype = None
-            lib.ora_closest_point.argtypes = [P, P, P, i64, dbl, P, P, P]
-            lib.ora_sigma.restype = None
-            lib.ora_sigma.argtypes = [dbl, P]
-            lib.ora_sigma_sharp.restype = None
-            lib.ora_sigma_sharp.argtypes = [dbl, P]
-            lib.ora_eval_sharp.restype = i64
-            lib.ora_eval_sharp.argtypes = [P, P, P, P, P, i64, P, P, P, P, P, P, i64, dbl, P, dbl, dbl, P, P]
-            lib.ora_I0.restype = dbl
-            lib.ora_I0.argtypes = [dbl]
-            lib.ora_I2.restype = dbl
-            lib.ora_I2.argtypes = [dbl]
-            lib.ora_extrapolate.restype = cint
-            lib.ora_extrapolate.argtypes = [P, dbl, dbl, P, cint, P]
-            lib.ora_eval.restype = i64
-            lib.ora_eval.argtypes = [P, P, P, P, P, i64, P, P, P, P, P, P, i64, dbl, P, dbl, cint, P, P]
-            lib.ora_eval_k.restype = i64
-            lib.ora_eval_k.argtypes = [cint, P, P, P, P, P, i64, P, P, P, P, P, P, i64, dbl, P, dbl, cint, P, P]
-            lib.ora_I4.restype = dbl
-            lib.ora_I4.argtypes = [dbl]
-            lib.ora_extrapolate_k.restype = cint
-            lib.ora_extrapolate_k.argtypes = [cint, P, dbl, dbl, P, cint, P]
-            lib.ora_eval_one_delta.restype = None
-            lib.ora_eval_one_delta.argtypes = [P, P, P, P, P, i64, P, P, P, P, P, P, i64, dbl, dbl, P, P]
-            lib.ora_plain.restype = None
-            lib.ora_plain.argtypes = [P, P, P, P, P, i64, P, i64, P, P]
-            lib.ora_num_threads.restype = cint
-            I = ctypes.POINTER(ctypes.c_int64)
-            lib.ora_eval_tree.restype = i64
-            lib.ora_eval_tree.argtypes = [cint, P, P, P, P, P, i64, P, P, P, P, P, P, i64, dbl, P, dbl, dbl, i64,
-                                          cint, P, P, I]
-            lib.ora_tree_info.restype = i64
-            lib.ora_tree_info.argtypes = [P, i64, i64, i64, P, P, P, I, I, I, I, I, I]
-            lib.ora_tree_weights.restype = i64
-            lib.ora_tree_weights.argtypes = [P, P, P, P, P, i64, i64, cint, i64, P]
-            lib.ora_lagrange.restype = None
-            lib.ora_lagrange.argtypes = [cint, dbl, dbl, dbl, P]
-            lib.ora_cheb_points.restype = None
-            lib.ora_cheb_points.argtypes = [cint, P]
-            _lib = lib
+            _lib = bind(ctypes.CDLL(build()))
     return _lib
+
+
+def bind(lib):
+    """Declare the argument types of the oracle's C functions on a loaded library (the built
+    oracle, or a copy compiled from edited source by the planted-mistake tests)."""
+    P = ctypes.POINTER(ctypes.c_double)
+    i64, dbl, cint = ctypes.c_int64, ctypes.c_double, ctypes.c_int
+    lib.ora_quadrature.restype = i64
+    lib.ora_quadrature.argtypes = [P, P, dbl, P, P, P]
+    lib.ora_closest_point.restype = None
+    lib.ora_closest_point.argtypes = [P, P, P, i64, dbl, P, P, P]
+    lib.ora_sigma.restype = None
+    lib.ora_sigma.argtypes = [dbl, P]
+    lib.ora_sigma_sharp.restype = None
+    lib.ora_sigma_sharp.argtypes = [dbl, P]
+    lib.ora_eval_sharp.restype = i64
+    lib.ora_eval_sharp.argtypes = [P, P, P, P, P, i64, P, P, P, P, P, P, i64, dbl, P, dbl, dbl, P, P]
+    lib.ora_I0.restype = dbl
+    lib.ora_I0.argtypes = [dbl]
+    lib.ora_I2.restype = dbl
+    lib.ora_I2.argtypes = [dbl]
+    lib.ora_extrapolate.restype = cint
+    lib.ora_extrapolate.argtypes = [P, dbl, dbl, P, cint, P]
+    lib.ora_eval.restype = i64
+    lib.ora_eval.argtypes = [P, P, P, P, P, i64, P, P, P, P, P, P, i64, dbl, P, dbl, cint, P, P]
+    lib.ora_eval_k.restype = i64
+    lib.ora_eval_k.argtypes = [cint, P, P, P, P, P, i64, P, P, P, P, P, P, i64, dbl, P, dbl, cint, P, P]
+    lib.ora_I4.restype = dbl
+    lib.ora_I4.argtypes = [dbl]
+    lib.ora_extrapolate_k.restype = cint
+    lib.ora_extrapolate_k.argtypes = [cint, P, dbl, dbl, P, cint, P]
+    lib.ora_eval_one_delta.restype = None
+    lib.ora_eval_one_delta.argtypes = [P, P, P, P, P, i64, P, P, P, P, P, P, i64, dbl, dbl, P, P]
+    lib.ora_plain.restype = None
+    lib.ora_plain.argtypes = [P, P, P, P, P, i64, P, i64, P, P]
+    lib.ora_num_threads.restype = cint
+    I = ctypes.POINTER(ctypes.c_int64)
+    lib.ora_eval_tree.restype = i64
+    lib.ora_eval_tree.argtypes = [cint, P, P, P, P, P, i64, P, P, P, P, P, P, i64, dbl, P, dbl, dbl, i64,
+                                  cint, P, P, I]
+    lib.ora_tree_info.restype = i64
+    lib.ora_tree_info.argtypes = [P, i64, i64, i64, P, P, P, I, I, I, I, I, I]
+    lib.ora_tree_weights.restype = i64
+    lib.ora_tree_weights.argtypes = [P, P, P, P, P, i64, i64, cint, i64, P]
+    lib.ora_lagrange.restype = None
+    lib.ora_lagrange.argtypes = [cint, dbl, dbl, dbl, P]
+    lib.ora_cheb_points.restype = None
+    lib.ora_cheb_points.argtypes = [cint, P]
+    return lib
 
 
 def _p(a: np.ndarray):

@@ -258,3 +258,28 @@ def test_targets_outside_the_training_extent_take_the_method(ers):
 
 def rel_err_max(a, ref):
     return float(np.abs(a - ref).max() / np.abs(ref).max())
+
+
+def test_curvature_features_of_an_ellipsoid(ers):
+    """Features 1 and 2 are the principal curvatures at x0 times h (larger first): against the
+    eigenvalues of the shape operator of the implicit surface sum((x/a)^2) = 1, i.e. of
+    P H P / |grad F| on the tangent plane (P = I - n n), computed here in numpy."""
+    import torch
+    h = 1 / 32
+    shape = workloads.Shape((0.1, -0.2, 0.05), (1.0, 0.8, 0.6))
+    s = ers.Surface(shape.center, shape.axes, h)
+    rng = np.random.default_rng(12)
+    y = workloads.near_band_targets(shape, 300, 2 * h, rng)[0]
+    fc, qc = workloads.density_coeffs(rng), workloads.density_coeffs(rng)
+    P = _problem(ers, s, shape, fc, qc, y, 0)
+    X = ers.closure_data(s, P["y"], P["x0"], P["n0"], P["b"], P["f0"], P["q0"], P["gf0"], P["gq0"], P["u3"],
+                         P["v3"], precision=0, ndelta=1)[0].cpu().numpy()
+    x0 = P["x0"].cpu().numpy() - np.asarray(shape.center)
+    a2 = np.asarray(shape.axes) ** 2
+    for i in range(len(y)):
+        g = 2 * x0[i] / a2
+        n = g / np.linalg.norm(g)
+        Pm = np.eye(3) - np.outer(n, n)
+        W = Pm @ np.diag(2 / a2) @ Pm / np.linalg.norm(g)
+        k = np.sort(np.linalg.eigvalsh(W))[::-1][:2]  # the third eigenvalue is 0 (normal direction)
+        assert np.allclose(X[i, 1:3], (k * h).astype(np.float32), rtol=2e-6, atol=1e-9), (i, X[i, 1:3], k * h)

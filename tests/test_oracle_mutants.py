@@ -1,0 +1,143 @@
+"""Planted mistakes in the oracle, on the CPU: each test compiles a copy of the oracle's C source
+with one plausible slip (a dropped term, a wrong sign or coefficient, transposed operands) and
+checks that the pins of the oracle's tests catch it, while the unedited copy passes them all.
+The pins used here are those of test_oracle_method.py (the sphere closed forms for rigid-body
+densities at near-band targets and at the nodes; the equality of the localized and direct forms,
+Sec. 3.3), of test_oracle_functions.py (I0(0) = 1/sqrt(pi), I2(0) = 1/(3 sqrt(pi)),
+I0' = -erfc, I2' = -2 lambda I0) and of test_oracle_quadrature.py (Table 1's node count, the
+area).  A constant factor in I0 or I2 leaves the extrapolated value
+unchanged (it rescales a column of the system of Eq. (extrap_eqn), so only c1 or c2 changes): only
+the function-level pins see it."""
+import math
+import ctypes
+import os
+import subprocess
+
+import numpy as np
+import pytest
+
+import oracle
+import workloads
+from sphere_exact import dl_exact, rigid, sl_exact
+
+SRC = os.path.join(os.path.dirname(oracle.__file__), "ers_oracle.c")
+TREE_SRC = os.path.join(os.path.dirname(oracle.__file__), "ers_treecode.c")
+SPHERE = workloads.unit_sphere()
+
+# (what the slip is, text in ers_oracle.c, replacement); the first occurrence is edited, which
+# is the one ora_eval (three deltas) runs.
+MUTANTS = [
+    ("single layer: the d (d.g) s2/r^3 term dropped",
+     "acc[i] += (k1 * g[i] + k3 * dg * d[i]) * w;", "acc[i] += (k1 * g[i]) * w;"),
+    ("double layer: sign of the stresslet",
+     "double T = -6.0 * (t1 * k3 + (t2 - r2mb2 * t1) * k5);", "double T = 6.0 * (t1 * k3 + (t2 - r2mb2 * t1) * k5);"),
+    ("double layer: (r^2 - b^2) written as (r^2 + b^2)",
+     "double r2mb2 = r * r - b * b;", "double r2mb2 = r * r + b * b;"),
+    ("double layer: n0 and n(x) transposed",
+     "ora_dl_term(r, delta, tc, bm, nm0, xh, Q, nj, w[j], snear_v[k], 0);",
+     "ora_dl_term(r, delta, tc, bm, nj, xh, Q, nm0, w[j], snear_v[k], 0);"),
+    ("double layer: one index of t2 wrong (xh_i xh_j n_k -> xh_i xh_j n_j)",
+     "double t2 = b * (xi[i] * xi[j] * ni[k] +", "double t2 = b * (xi[i] * xi[j] * ni[j] +"),
+    ("I2: coefficient 2/3 -> 1/3",
+     "return 2.0 / 3.0 * ((0.5 - l * l)", "return 1.0 / 3.0 * ((0.5 - l * l)"),
+    ("I2: sign of lambda^2 in (1/2 - lambda^2)",
+     "return 2.0 / 3.0 * ((0.5 - l * l)", "return 2.0 / 3.0 * ((0.5 + l * l)"),
+    ("I0: sign of the erfc term",
+     "return exp(-l * l) / ORA_SQRTPI - l * erfc(l);", "return exp(-l * l) / ORA_SQRTPI + l * erfc(l);"),
+    ("chi: inside and outside swapped",
+     "double chi = (bm < 0.0) ? 1.0 : ((bm > 0.0) ? 0.0 : 0.5);",
+     "double chi = (bm < 0.0) ? 0.0 : ((bm > 0.0) ? 1.0 : 0.5);"),
+    ("single-layer subtraction: sign of (f(x0).n0) n",
+     "g[i] = f[3 * j + i] - fn0 * nj[i];", "g[i] = f[3 * j + i] + fn0 * nj[i];"),
+    ("double-layer subtraction: q(x0) not subtracted",
+     "Q[i] = q[3 * j + i] - qm0[i];", "Q[i] = q[3 * j + i];"),
+    ("s2/t^3 series (t < 1/2): sign of its terms",
+     "if (nn >= 1) s2 += -sgn * (2.0 * nn)", "if (nn >= 1) s2 += sgn * (2.0 * nn)"),
+    ("quadrature: the 1/|n_k| factor of the weight dropped",
+     "w[count] = psi / fabs(nn[k]) * h * h;", "w[count] = psi * h * h;"),
+    ("quadrature: partition of unity taken along the wrong axis",
+     "double psi = beta[k] / sb;", "double psi = beta[(k + 1) % 3] / sb;"),
+    ("s3: coefficient of t^3 in the closed form 2/3 -> 1/3",
+     "double s3 = e - c * (t + 2.0 / 3.0 * t * t * t) * g;", "double s3 = e - c * (t + 1.0 / 3.0 * t * t * t) * g;"),
+]
+
+
+def _compile(tmp_path, name, text):
+    src = tmp_path / f"{name}.c"
+    src.write_text(text)
+    lib = tmp_path / f"lib{name}.so"
+    subprocess.run(["gcc", "-O2", "-fopenmp", "-fPIC", "-shared", "-std=c11", "-o", str(lib), str(src), TREE_SRC,
+                    "-lm"], check=True)
+    return oracle.bind(ctypes.CDLL(str(lib)))
+
+
+def _pins():
+    """(name, passed) for each pin, with the library currently loaded in the oracle package."""
+    out = []
+    # near-band targets |b| <= 4h (the bounds of test_accuracy_rho234), then nodes (b = 0, the
+    # bounds of test_on_surface_targets)
+    for inv, rho, nodes, sl_tol, dl_tol in ((16, (2, 3, 4), False, 2e-5, 3e-4), (32, (2, 3, 4), False, 1e-6, 1e-5),
+                                            (32, (3, 4, 5), True, 3e-7, 3e-5)):
+        h = 1 / inv
+        x, n, w = oracle.quadrature(SPHERE, h)
+        if nodes:
+            y = x[np.arange(0, len(w), 37)]
+        else:
+            y, _, _, _ = workloads.near_band_targets(SPHERE, 300, 4 * h, np.random.default_rng(7))
+        x0, n0, b = oracle.closest_point(SPHERE, y)
+        u, v, nfail = oracle.evaluate(x, n, w, rigid(x), rigid(x), y, x0, n0, b, rigid(x0), rigid(x0), h, rho)
+        where = f"h = 1/{inv}, {'nodes' if nodes else 'band'}"
+        out.append((f"sphere closed form, single layer, {where}", nfail == 0 and np.abs(u - sl_exact(y)).max() < sl_tol))
+        out.append((f"sphere closed form, double layer, {where}",
+                    nfail == 0 and np.abs(v - dl_exact(y, b)).max() < dl_tol))
+    wl = workloads.config("sphere16")
+    x, n, w = oracle.quadrature(wl.shape, wl.h)
+    f, q = workloads.poly_eval(wl.f_coef, x), workloads.poly_eval(wl.q_coef, x)
+    y = np.concatenate([x[::7], wl.extra_targets[:300]])
+    x0, n0, b = oracle.closest_point(wl.shape, y)
+    f0, q0 = workloads.poly_eval(wl.f_coef, x0), workloads.poly_eval(wl.q_coef, x0)
+    ud, vd, _ = oracle.evaluate(x, n, w, f, q, y, x0, n0, b, f0, q0, wl.h, wl.rho, mode=oracle.DIRECT)
+    ul, vl, _ = oracle.evaluate(x, n, w, f, q, y, x0, n0, b, f0, q0, wl.h, wl.rho, mode=oracle.LOCALIZED)
+    out.append(("localized = direct", np.abs(ud - ul).max() < 1e-13 * np.abs(ud).max()
+                and np.abs(vd - vl).max() < 1e-13 * np.abs(vd).max()))
+    # quadrature (Sec. 2.2): Table 1's node count for the spheroid (1, 1/2, 1/2) at h = 1/32, and
+    # the weights integrate the unit sphere's area
+    _, _, w = oracle.quadrature(workloads.Shape((0.0, 0.0, 0.0), (1.0, 0.5, 0.5)), 1 / 32)
+    out.append(("Table 1 node count", len(w) == 6958))
+    _, _, w = oracle.quadrature(SPHERE, 1 / 64)
+    out.append(("weights integrate the area", abs(w.sum() - 4 * np.pi) < 5e-9))
+    sp = math.sqrt(math.pi)
+    ok = abs(oracle.I0(0.0) - 1 / sp) < 1e-16 and abs(oracle.I2(0.0) - 1 / (3 * sp)) < 1e-16
+    for lam in (0.3, 1.1, 2.5):
+        eps = 1e-6
+        d0 = (oracle.I0(lam + eps) - oracle.I0(lam - eps)) / (2 * eps)
+        d2 = (oracle.I2(lam + eps) - oracle.I2(lam - eps)) / (2 * eps)
+        ok = ok and abs(d0 + math.erfc(lam)) < 1e-9 and abs(d2 + 2 * lam * oracle.I0(lam)) < 1e-9
+    out.append(("I0, I2 values at 0 and derivative identities", ok))
+    return out
+
+
+def _with_library(lib):
+    saved = oracle._lib
+    oracle._lib = lib
+    try:
+        return _pins()
+    finally:
+        oracle._lib = saved
+
+
+def test_unedited_copy_passes_every_pin(tmp_path):
+    lib = _compile(tmp_path, "unedited", open(SRC).read())
+    failed = [name for name, ok in _with_library(lib) if not ok]
+    assert not failed, failed
+
+
+@pytest.mark.parametrize("what,old,new", MUTANTS, ids=[m[0] for m in MUTANTS])
+def test_planted_mistake_fails_a_pin(tmp_path, what, old, new):
+    text = open(SRC).read()
+    assert old in text, f"the text to edit is not in the oracle: {old}"
+    lib = _compile(tmp_path, "mutant", text.replace(old, new, 1))
+    results = _with_library(lib)
+    caught = [name for name, ok in results if not ok]
+    print(what, "->", caught)
+    assert caught, f"no pin catches: {what}"

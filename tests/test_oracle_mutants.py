@@ -141,3 +141,81 @@ def test_planted_mistake_fails_a_pin(tmp_path, what, old, new):
     caught = [name for name, ok in results if not ok]
     print(what, "->", caught)
     assert caught, f"no pin catches: {what}"
+
+
+# Slips in the treecode (ers_treecode.c, Sec. 3.4), against the pins of test_oracle_treecode.py.
+TREE_SRC_TEXT_MUTANTS = [
+    ("barycentric weights: end points not halved",
+     "double wk = ((k & 1) ? -1.0 : 1.0) * ((k == 0 || k == p) ? 0.5 : 1.0);",
+     "double wk = ((k & 1) ? -1.0 : 1.0) * 1.0;"),
+    ("barycentric weights: alternating sign dropped",
+     "double wk = ((k & 1) ? -1.0 : 1.0) * ((k == 0 || k == p) ? 0.5 : 1.0);",
+     "double wk = 1.0 * ((k == 0 || k == p) ? 0.5 : 1.0);"),
+    ("modified weights: density q_a n_b transposed to q_b n_a",
+     "g[6 + 3 * a + b] = q[3 * j + a] * nrm[3 * j + b] * w[j];",
+     "g[6 + 3 * a + b] = q[3 * j + b] * nrm[3 * j + a] * w[j];"),
+    # (q0 subtracted with transposed indices, q0_b Wn_a, is no slip: the contraction with d_a d_b
+    # is symmetric in a, b)
+    ("cluster sum: q0 times the f weights instead of the n weights",
+     "t->q0[a] * Wk[3 + b]", "t->q0[a] * Wk[b]"),
+    ("cluster sum: sign of the single-layer subtraction",
+     "g[i] = Wk[i] - t->fn0 * Wk[3 + i];", "g[i] = Wk[i] + t->fn0 * Wk[3 + i];"),
+    ("MAC without the near-radius condition",
+     "if (C->rc <= X->theta * R && R - C->rc > X->Racc) {", "if (C->rc <= X->theta * R) {"),
+    ("Lagrange basis at Chebyshev points of the first kind",
+     "for (int k = 0; k <= p; ++k) s[k] = c + hw * cos(k * ORA_TC_PI / p);",
+     "for (int k = 0; k <= p; ++k) s[k] = c + hw * cos((2 * k + 1) * ORA_TC_PI / (2 * p + 2));"),
+]
+
+
+def _compile_tree(tmp_path, name, tree_text):
+    src = tmp_path / f"{name}_tree.c"
+    src.write_text(tree_text)
+    lib = tmp_path / f"lib{name}.so"
+    subprocess.run(["gcc", "-O2", "-fopenmp", "-fPIC", "-shared", "-std=c11", "-o", str(lib), SRC, str(src), "-lm"],
+                   check=True)
+    return oracle.bind(ctypes.CDLL(str(lib)))
+
+
+def _tree_pins():
+    import test_oracle_treecode as T
+    ell = oracle.quadrature(T.ELL, 1 / 32)
+    checks = [("Lagrange basis p = 2", lambda: T.test_lagrange_basis(2)),
+              ("Lagrange basis p = 5", lambda: T.test_lagrange_basis(5)),
+              ("modified-weight moments p = 3", lambda: T.test_modified_weights_moments(ell, 3)),
+              ("theta -> 0 is the direct evaluation", T.test_theta_zero_is_the_direct_evaluation),
+              ("every node counted once", lambda: T.test_every_node_counted_once((2.0, 3.0, 4.0))),
+              ("spectral decay with p", T.test_error_decays_spectrally_with_degree)]
+    out = []
+    for name, fn in checks:
+        try:
+            fn()
+            out.append((name, True))
+        except AssertionError:
+            out.append((name, False))
+    return out
+
+
+def _with_library_tree(lib):
+    saved = oracle._lib
+    oracle._lib = lib
+    try:
+        return _tree_pins()
+    finally:
+        oracle._lib = saved
+
+
+def test_unedited_treecode_copy_passes_every_pin(tmp_path):
+    lib = _compile_tree(tmp_path, "unedited", open(TREE_SRC).read())
+    failed = [name for name, ok in _with_library_tree(lib) if not ok]
+    assert not failed, failed
+
+
+@pytest.mark.parametrize("what,old,new", TREE_SRC_TEXT_MUTANTS, ids=[m[0] for m in TREE_SRC_TEXT_MUTANTS])
+def test_planted_treecode_mistake_fails_a_pin(tmp_path, what, old, new):
+    text = open(TREE_SRC).read()
+    assert old in text, f"the text to edit is not in the treecode oracle: {old}"
+    lib = _compile_tree(tmp_path, "mutant", text.replace(old, new, 1))
+    caught = [name for name, ok in _with_library_tree(lib) if not ok]
+    print(what, "->", caught)
+    assert caught, f"no pin catches: {what}"

@@ -177,7 +177,7 @@ def _compile_tree(tmp_path, name, tree_text):
     return oracle.bind(ctypes.CDLL(str(lib)))
 
 
-def _tree_pins():
+def _tree_pins(stop_at_failure=False):
     import test_oracle_treecode as T
     ell = oracle.quadrature(T.ELL, 1 / 32)
     checks = [("Lagrange basis p = 2", lambda: T.test_lagrange_basis(2)),
@@ -193,14 +193,16 @@ def _tree_pins():
             out.append((name, True))
         except AssertionError:
             out.append((name, False))
+            if stop_at_failure:
+                break
     return out
 
 
-def _with_library_tree(lib):
+def _with_library_tree(lib, stop_at_failure=False):
     saved = oracle._lib
     oracle._lib = lib
     try:
-        return _tree_pins()
+        return _tree_pins(stop_at_failure)
     finally:
         oracle._lib = saved
 
@@ -216,6 +218,86 @@ def test_planted_treecode_mistake_fails_a_pin(tmp_path, what, old, new):
     text = open(TREE_SRC).read()
     assert old in text, f"the text to edit is not in the treecode oracle: {old}"
     lib = _compile_tree(tmp_path, "mutant", text.replace(old, new, 1))
-    caught = [name for name, ok in _with_library_tree(lib) if not ok]
+    caught = [name for name, ok in _with_library_tree(lib, True) if not ok]
+    print(what, "->", caught)
+    assert caught, f"no pin catches: {what}"
+
+
+# Slips in the two-drop oracle (oracle/two_drop.py, Sec. 4.3), against the pins of
+# test_oracle_two_drop.py (a Python module: the edited source is executed as a module of its own).
+TWO_DROP_MUTANTS = [
+    ("jump force: sign of the surface gradient", "return 2.0 * g[:, None] * H * n - grad_s",
+     "return 2.0 * g[:, None] * H * n + grad_s"),
+    ("jump force: surface gradient not projected on the tangent plane",
+     "grad_s = grad - (grad * n).sum(1)[:, None] * n", "grad_s = grad"),
+    ("local fit: degree 3 instead of 4", "cols = [xi ** (d - b) * eta ** b for d in range(deg + 1) for b in range(d + 1)]",
+     "cols = [xi ** (d - b) * eta ** b for d in range(deg) for b in range(d + 1)]"),
+    # (a first tangent not orthogonalized against n0 is no slip: the fit is then a polynomial in
+    # another local chart of the surface, just as accurate)
+    ("local fit: the second tangent equal to the first",
+     "t2 = np.cross(n0, t1)", "t2 = t1.copy()"),
+    ("GMRES: sign of the rotated residual", "g[k + 1] = -sn[k] * g[k]", "g[k + 1] = sn[k] * g[k]"),
+    ("GMRES: previous rotation applied with the wrong sign",
+     "H[i + 1, k] = -sn[i] * H[i, k] + cs[i] * H[i + 1, k]", "H[i + 1, k] = sn[i] * H[i, k] + cs[i] * H[i + 1, k]"),
+    ("operator: (lambda_b - 1) u_b instead of (lambda_b + 1) u_b",
+     "out.append((self.lam[b] + 1.0) * us[b] - v)", "out.append((self.lam[b] - 1.0) * us[b] - v)"),
+    ("operator: double layer of the other drop with its own viscosity",
+     "v = sum(2.0 * (self.lam[m] - 1.0) * self.layer(m, b, None, us[m], 1) for m in range(2))",
+     "v = sum(2.0 * (self.lam[b] - 1.0) * self.layer(m, b, None, us[m], 1) for m in range(2))"),
+]
+
+
+def _two_drop_pins(mod, stop_at_failure=False):
+    """(name, passed) per pin, cheapest first; with stop_at_failure the list ends at the first
+    failing pin (enough to show that a slip is caught)."""
+    import test_oracle_two_drop as T
+    saved = T.td
+    T.td = mod
+    try:
+        checks = [("jump force", T.test_jump_force_is_force_free_and_splits_normal_and_tangential),
+                  ("GMRES on dense systems", T.test_gmres_solves_dense_systems),
+                  ("fit exact on its polynomials", lambda: T.test_interpolation_exact_for_tangent_polynomials(16)),
+                  ("fit converges at fifth order", T.test_interpolation_converges_at_fifth_order),
+                  ("lambda = 1 gives 2 I", lambda: T.test_equal_viscosities_remove_the_double_layer(None)),
+                  # the operator at h = 1/16 with unequal viscosities: rigid motions of one drop,
+                  # and the affine dependence on the ratios
+                  ("rigid motions", lambda: T.test_rigid_motions_of_one_drop(mod.TwoDrops(1 / 16, lam=(2.0, 3.0)))),
+                  ("affine in the viscosity ratios", T.test_operator_is_affine_in_the_viscosity_ratios)]
+        out = []
+        for name, fn in checks:
+            try:
+                fn()
+                out.append((name, True))
+            except (AssertionError, ValueError, np.linalg.LinAlgError):
+                out.append((name, False))
+                if stop_at_failure:
+                    break
+        return out
+    finally:
+        T.td = saved
+
+
+def _two_drop_module(text):
+    import types
+    from oracle import two_drop
+    mod = types.ModuleType("two_drop_copy")
+    mod.__file__ = two_drop.__file__
+    exec(compile(text, two_drop.__file__, "exec"), mod.__dict__)
+    return mod
+
+
+def test_unedited_two_drop_copy_passes_every_pin():
+    from oracle import two_drop
+    mod = _two_drop_module(open(two_drop.__file__).read())
+    failed = [name for name, ok in _two_drop_pins(mod) if not ok]
+    assert not failed, failed
+
+
+@pytest.mark.parametrize("what,old,new", TWO_DROP_MUTANTS, ids=[m[0] for m in TWO_DROP_MUTANTS])
+def test_planted_two_drop_mistake_fails_a_pin(what, old, new):
+    from oracle import two_drop
+    text = open(two_drop.__file__).read()
+    assert old in text, f"the text to edit is not in the two-drop oracle: {old}"
+    caught = [name for name, ok in _two_drop_pins(_two_drop_module(text.replace(old, new, 1)), True) if not ok]
     print(what, "->", caught)
     assert caught, f"no pin catches: {what}"

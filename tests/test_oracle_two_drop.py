@@ -112,3 +112,19 @@ def test_solution_at_h16(drops16):
     assert np.linalg.norm(r) <= 1.01e-10 * np.linalg.norm(P.rhs())
     # the drops move apart/together only through Marangoni stresses: velocities are O(0.1)
     assert 1e-3 < np.abs(x).max() < 1.0
+
+
+def test_operator_is_affine_in_the_viscosity_ratios():
+    """A(lambda) u = (lambda_b + 1) u_b - 2 sum_m (lambda_m - 1) DL_m[u_m] is affine in each
+    lambda_m, with the double layer of drop m weighted by drop m's own ratio: for u = (0, q),
+    A(2, 3) u - A(2, 2) u = A(2, 2) u - (0, 2 q), whatever the double-layer values are."""
+    P22 = td.TwoDrops(1 / 16, lam=(2.0, 2.0))
+    P23 = td.TwoDrops(1 / 16, lam=(2.0, 3.0))
+    x2 = P22.nodes[1][0]
+    q = np.stack([np.sin(2 * x2[:, 0]) * x2[:, 1], x2[:, 2] ** 2 - x2[:, 0], np.cos(x2[:, 1]) + x2[:, 0] * x2[:, 2]], 1)
+    u = np.concatenate([np.zeros(3 * P22.N[0]), q.ravel()])
+    a22, a23 = P22.matvec(u), P23.matvec(u)
+    expect = a22 - np.concatenate([np.zeros(3 * P22.N[0]), 2 * q.ravel()])
+    assert np.abs((a23 - a22) - expect).max() <= 1e-12 * np.abs(a22).max()
+    # and the double layer of drop 2 at drop 1 is not negligible for this q
+    assert np.abs(a22[:3 * P22.N[0]]).max() > 1e-3

@@ -84,6 +84,18 @@ def test_operator_and_rhs_match_oracle(ers, pair16):
     assert np.abs(r - ro).max() <= 1e-11 * np.abs(ro).max()
 
 
+def test_operator_with_unequal_viscosity_ratios_matches_oracle(ers):
+    """lambda = (2, 3): each drop's double layer is weighted by its own ratio (FP64 parity)."""
+    import torch
+    from paper_2507_00156_gb300 import two_drop as gtd
+    G, O = gtd.TwoDrops(1 / 16, lam=(2.0, 3.0)), otd.TwoDrops(1 / 16, lam=(2.0, 3.0))
+    u = np.random.default_rng(9).normal(size=G.n_unknowns)
+    y = torch.empty(G.n_unknowns, dtype=torch.float64, device="cuda")
+    G.matvec(torch.from_numpy(u).cuda(), y)
+    yo = O.matvec(u)
+    assert np.abs(y.cpu().numpy() - yo).max() <= 1e-11 * np.abs(yo).max()
+
+
 def test_solution_matches_oracle(ers, pair16):
     G, O = pair16
     x, it, rel, conv = G.solve(tol=1e-12)

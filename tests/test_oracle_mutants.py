@@ -301,3 +301,68 @@ def test_planted_two_drop_mistake_fails_a_pin(what, old, new):
     caught = [name for name, ok in _two_drop_pins(_two_drop_module(text.replace(old, new, 1)), True) if not ok]
     print(what, "->", caught)
     assert caught, f"no pin catches: {what}"
+
+
+# Slips in the four-delta and on-surface parts of ers_oracle.c, against the pins of
+# test_oracle_four_delta.py and test_oracle_sharp.py (cheapest first, stopping at the first
+# failure).
+EXTRA_MUTANTS = [
+    ("I4: coefficient of lambda^4 in the polynomial 4 -> 2",
+     "((3.0 - 2.0 * l2 + 4.0 * l2 * l2) * exp(-l2)", "((3.0 - 2.0 * l2 + 2.0 * l2 * l2) * exp(-l2)"),
+    ("I4: power of lambda in the erfc term 5 -> 4",
+     "- 4.0 * l2 * l2 * l * erfc(l));", "- 4.0 * l2 * l2 * erfc(l));"),
+    ("four deltas: rho_k^3 instead of rho_k^5 in the I4 column",
+     "if (K == 4) A[k][3] = r * r * r * r * r * ora_I4(lam);", "if (K == 4) A[k][3] = r * r * r * ora_I4(lam);"),
+    ("s#1: sign of the polynomial term",
+     "double s1 = e + c / 3.0 * (5.0 * t - 2.0 * t * t2) * g;", "double s1 = e - c / 3.0 * (5.0 * t - 2.0 * t * t2) * g;"),
+    ("s#2: coefficient 14 -> 12",
+     "double s2 = e - c / 3.0 * (3.0 * t - 14.0 * t * t2 + 4.0 * t * t2 * t2) * g;",
+     "double s2 = e - c / 3.0 * (3.0 * t - 12.0 * t * t2 + 4.0 * t * t2 * t2) * g;"),
+]
+
+
+def _extra_pins():
+    import test_oracle_four_delta as F
+    import test_oracle_sharp as S
+    # properties that fix the functions independently of their printed formulas first; the
+    # 50-digit evaluation of those formulas last
+    checks = [("I4 derivative and limits", F.test_I4_derivative_and_limits),
+              ("four-delta weights at b = 0", lambda: F.test_weights_at_b0_are_the_exact_rationals((3, 4, 5, 6))),
+              ("s# limits", S.test_sigma_sharp_limits),
+              ("on-surface single layer, fifth order", S.test_on_surface_single_layer_fifth_order),
+              ("four deltas converge faster than three", F.test_four_deltas_converge_faster_than_three),
+              ("s# against 50-digit values", S.test_sigma_sharp_against_mpmath)]
+    for name, fn in checks:
+        try:
+            fn()
+        except AssertionError:
+            return [(name, False)]
+    return [(name, True) for name, _ in checks]
+
+
+@pytest.mark.parametrize("what,old,new", EXTRA_MUTANTS, ids=[m[0] for m in EXTRA_MUTANTS])
+def test_planted_four_delta_or_sharp_mistake_fails_a_pin(tmp_path, what, old, new):
+    pytest.importorskip("mpmath")
+    text = open(SRC).read()
+    assert old in text, f"the text to edit is not in the oracle: {old}"
+    lib = _compile(tmp_path, "mutant", text.replace(old, new, 1))
+    saved = oracle._lib
+    oracle._lib = lib
+    try:
+        caught = [name for name, ok in _extra_pins() if not ok]
+    finally:
+        oracle._lib = saved
+    print(what, "->", caught)
+    assert caught, f"no pin catches: {what}"
+
+
+def test_unedited_copy_passes_the_four_delta_and_sharp_pins(tmp_path):
+    pytest.importorskip("mpmath")
+    lib = _compile(tmp_path, "unedited", open(SRC).read())
+    saved = oracle._lib
+    oracle._lib = lib
+    try:
+        failed = [name for name, ok in _extra_pins() if not ok]
+    finally:
+        oracle._lib = saved
+    assert not failed, failed

@@ -45,3 +45,37 @@ def test_max_over_ranks_and_weak_scaling_value():
         assert p.exitcode == 0
     assert list(out[:world]) == [2.0, 2.0]
     assert list(out[world:]) == [10.0, 10.0]
+
+
+def _reference_worker(rank, world, port, path):
+    import contextlib
+    import sys
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank), WORLD_SIZE=str(world),
+                      LOCAL_RANK=str(rank))
+    sys.argv = ["bench.py", "--impl", "reference", "--gpus", str(world), "--steps", "1", "--warmup", "1"]
+    import bench
+    with open(f"{path}.{rank}", "w") as f, contextlib.redirect_stdout(f):
+        bench.main()
+
+
+def test_reference_arm_under_two_ranks(tmp_path):
+    """`bench.py --impl reference` launched as two ranks (gloo, as torchrun would): rank 0 alone
+    times the oracle and prints one JSON line for the whole job; rank 1 exits without work."""
+    import json
+    world = 2
+    ctx = mp.get_context("spawn")
+    port = _free_port()
+    path = str(tmp_path / "out")
+    procs = [ctx.Process(target=_reference_worker, args=(r, world, port, path)) for r in range(world)]
+    for p in procs:
+        p.start()
+    for p in procs:
+        p.join(600)
+        assert p.exitcode == 0
+    lines = [ln for ln in open(f"{path}.0").read().splitlines() if ln.startswith("{")]
+    assert len(lines) == 1 and open(f"{path}.1").read().strip() == ""
+    d = json.loads(lines[0])
+    assert d["impl"] == "reference" and d["n_gpus"] == world and d["steps"] == 1 and d["warmup"] == 1
+    assert d["value"] > 0 and d["unit"] == "target-evals/s" and d["higher_is_better"] is True
+    assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["cores"] >= 1
+    assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["e2e"]["value"] == d["value"]

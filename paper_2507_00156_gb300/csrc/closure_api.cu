@@ -519,6 +519,21 @@ int ers_closure_last_out_of_range(ers_closure *c, int64_t *n) {
     return ERS_OK;
 }
 
+// Test hook (not in the public header): run the bounded-wait probe once on the current device;
+// *timed_out = 1 when its wait ran out.  Synchronous.
+int ers_debug_wait_timeout(int arrive, int limit, int *timed_out) {
+    clear_error();
+    if (!timed_out || limit < 1) return fail(ERS_E_INVAL, "ers_debug_wait_timeout: bad arguments");
+    int *flag = nullptr;
+    cudaError_t e = cudaMalloc(&flag, sizeof(int));
+    if (e == cudaSuccess) e = cudaMemset(flag, 0, sizeof(int));
+    if (e == cudaSuccess) e = mlp::launch_wait_probe(arrive, (uint32_t)limit, flag, nullptr);
+    if (e == cudaSuccess) e = cudaMemcpy(timed_out, flag, sizeof(int), cudaMemcpyDeviceToHost);
+    if (flag) cudaFree(flag);
+    if (e != cudaSuccess) return cuda_fail(e, "ers_debug_wait_timeout");
+    return ERS_OK;
+}
+
 int ers_closure_status(ers_closure *c, int *timed_out) {
     clear_error();
     if (!c || !timed_out) return fail(ERS_E_INVAL, "ers_closure_status: NULL argument");

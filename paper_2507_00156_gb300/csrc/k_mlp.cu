@@ -416,6 +416,30 @@ cudaError_t launch_infer_tc(const float *params, const float *X, int64_t n, floa
     return cudaGetLastError();
 }
 
+namespace {
+// The timeout path of the bounded waits: an mbarrier that expects one arrival, which thread 0
+// makes only when `arrive` is set; every thread polls at most `limit` times, and a wait that
+// runs out sets *flag and returns (no asynchronous operation is tied to this barrier).
+__global__ void k_wait_probe(int arrive, uint32_t limit, int *flag) {
+    __shared__ uint64_t mbar;
+    if (threadIdx.x == 0) {
+        mbar_init(&mbar, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    if (arrive && threadIdx.x == 0)
+        asm volatile("{\n\t.reg .b64 st;\n\tmbarrier.arrive.shared::cta.b64 st, [%0];\n\t}\n" ::"r"(smem_u32(&mbar))
+                     : "memory");
+    const bool ok = mbar_wait_bounded(&mbar, 0u, limit);
+    if (__syncthreads_or(!ok) && threadIdx.x == 0) atomicExch(flag, 1);
+}
+}  // namespace
+
+cudaError_t launch_wait_probe(int arrive, uint32_t limit, int *flag, cudaStream_t st) {
+    k_wait_probe<<<1, 128, 0, st>>>(arrive, limit, flag);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_quantize(const float *p, float *q, cudaStream_t st) {
     k_quantize<<<(NPARAM + 255) / 256, 256, 0, st>>>(p, q);
     return cudaGetLastError();

@@ -32,6 +32,9 @@ cudaError_t launch_infer_ref(const float *q, const float *X, int64_t n, float *Y
 cudaError_t launch_train_grad(const float *q, const float *X, const float *T, const int *idx, int64_t n, float *Z,
                               float *A, float *D4, float *D, float *G, double *loss, cudaStream_t st);
 cudaError_t launch_adam(float *p, float *m, float *v, const float *g, float lr, int step, cudaStream_t st);
+// One CTA whose bounded mbarrier wait completes (arrive != 0) or runs out after `limit` polls
+// (then *flag = 1): the timeout path of the tensor-core and treecode waits, tested on its own.
+cudaError_t launch_wait_probe(int arrive, uint32_t limit, int *flag, cudaStream_t st);
 
 }  // namespace mlp
 }  // namespace ers

@@ -283,3 +283,24 @@ def test_curvature_features_of_an_ellipsoid(ers):
         W = Pm @ np.diag(2 / a2) @ Pm / np.linalg.norm(g)
         k = np.sort(np.linalg.eigvalsh(W))[::-1][:2]  # the third eigenvalue is 0 (normal direction)
         assert np.allclose(X[i, 1:3], (k * h).astype(np.float32), rtol=2e-6, atol=1e-9), (i, X[i, 1:3], k * h)
+
+
+def test_bounded_wait_runs_out_and_reports_it(ers):
+    """The timeout path of the bounded mbarrier waits (tensor-core inference, treecode staging):
+    a wait that nothing completes gives up after its poll limit and reports it through a flag the
+    host reads; the context stays usable (inference afterwards runs and repeats bit for bit)."""
+    import ctypes
+    import torch
+    L = ers.lib()
+    L.ers_debug_wait_timeout.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_int)]
+    flag = ctypes.c_int(-1)
+    ers.check(L.ers_debug_wait_timeout(0, 20000, ctypes.byref(flag)))
+    assert flag.value == 1
+    ers.check(L.ers_debug_wait_timeout(1, 20000, ctypes.byref(flag)))
+    assert flag.value == 0
+    c = ers.Closure(seed=1)
+    X, _ = _rand_inputs(300, 5)
+    Xd = torch.from_numpy(X).cuda()
+    Y1, Y2 = c.infer(0, Xd), c.infer(0, Xd)
+    assert torch.isfinite(Y1).all() and torch.equal(Y1, Y2)
+    assert not c.timed_out()

@@ -232,3 +232,14 @@ def test_treecode_defaults(L):
     assert ers.treecode_defaults(1 / 16) == (0.6, 1000, 6)
     with pytest.raises(ers.ErsError):
         ers.treecode_defaults(0.0)
+
+
+def test_missing_library_fails_loudly(monkeypatch, tmp_path):
+    """Without libers.so the package raises instead of falling back to anything."""
+    import paper_2507_00156_gb300 as ers
+    monkeypatch.setattr(ers, "_lib", None)
+    monkeypatch.setattr(ers, "LIB_PATH", str(tmp_path / "libers.so"))
+    with pytest.raises(ImportError, match="not built"):
+        ers.lib()
+    with pytest.raises(ImportError):
+        ers.Surface((0.0, 0.0, 0.0), (1.0, 1.0, 1.0), 1 / 8)

@@ -45,7 +45,7 @@ FAR_FLOPS_PER_PAIR = 34 + 1 + 33 + 1      # both layers, one far pair
 NEAR_FLOPS_PER_DELTA_EVAL = 30 + 1 + 1    # one regularized (node, delta) term, both layers
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) from one ncu capture of
 # the sphere128 workload with the current kernels (profiles/launches_sphere128_mixed.md).
-NCU_TRAFFIC = {("sphere128", "k_near"): 209905664 + 27866368, ("sphere128", "k_far32"): 60000000 + 31078400}
+NCU_TRAFFIC = {("sphere128", "k_near"): 210860800 + 29327616, ("sphere128", "k_far32"): 59735552 + 29894144}
 
 
 def parse():

@@ -31,6 +31,7 @@ constexpr int MAXD = 4;
 struct Geom {
     double y[3], x0[3], n0[3], b, b2;  // b2 = 2 b
     double invd2[MAXD], ad1[MAXD], ad3[MAXD], ad5[MAXD];
+    double s2w[MAXD];          // 2 TAB_INV_W / delta_k^2: the table's local variable is r^2 s2w - (2 i + 1)
     double apre[MAXD];         // partial sums alpha_0 + ... + alpha_k
     float yh[3], yl[3];        // y = yh + yl in floats (mixed-mode classification)
     float id2h[MAXD], id2l[MAXD]; // 1/delta_k^2 = id2h + id2l in floats
@@ -220,6 +221,7 @@ __device__ __forceinline__ void load_geom(int lane, const double *y, const doubl
         if (k >= nk) break;
         const double dk = rho[k] * h, id = 1.0 / dk;
         T.invd2[k] = id * id;
+        T.s2w[k] = (2.0 * TAB_INV_W) * T.invd2[k];  // a power-of-two multiple: exact
         T.ad1[k] = al[k] * id;
         T.ad3[k] = al[k] * id * id * id;
         T.ad5[k] = al[k] * id * id * id * id * id;
@@ -262,6 +264,30 @@ __device__ __forceinline__ void table_sigma(const double *__restrict__ tab, doub
     idx = min(idx, N - 1);
     const float4 f1 = __ldg(ftab + 3 * idx), f2 = __ldg(ftab + 3 * idx + 1), f3 = __ldg(ftab + 3 * idx + 2);
     const double s = fma(tau, 2.0 * INV_W, -float_to_double(f1.w));  // local variable in [-1, 1]
+    const float sf = approx_float(s);
+    s1 = float_to_double(fmaf(fmaf(f1.x, sf, f1.y), sf, f1.z));
+    s2 = float_to_double(fmaf(fmaf(f2.x, sf, f2.y), sf, f2.z));
+    s3 = float_to_double(fmaf(fmaf(f3.x, sf, f3.y), sf, f3.z));
+    const double2 *cd = reinterpret_cast<const double2 *>(tab + idx * 12);
+    const double2 a01 = __ldg(cd), a23 = __ldg(cd + 1), b01 = __ldg(cd + 2);
+    const double2 b23 = __ldg(cd + 3), c01 = __ldg(cd + 4), c23 = __ldg(cd + 5);
+    s1 = fma(fma(fma(fma(s1, s, a01.x), s, a01.y), s, a23.x), s, a23.y);
+    s2 = fma(fma(fma(fma(s2, s, b01.x), s, b01.y), s, b23.x), s, b23.y);
+    s3 = fma(fma(fma(fma(s3, s, c01.x), s, c01.y), s, c23.x), s, c23.y);
+}
+
+// table_sigma at tau = r^2 / delta^2 without forming tau in FP64: the interval from the FP32
+// product r2f idf (r2f, idf: r^2 and 1/delta^2 as floats), the local variable as
+// r^2 (2 INV_W / delta^2) - (2 i + 1) in one FMA (an interval chosen one off by the FP32 product
+// leaves the local variable within 1e-6 outside [-1, 1], where the piece is still as accurate).
+template <int INV_W, int N>
+__device__ __forceinline__ void table_sigma_r2(const double *__restrict__ tab, double r2, float r2f, float idf,
+                                               double s2w, double &s1, double &s2, double &s3) {
+    const float4 *__restrict__ ftab = reinterpret_cast<const float4 *>(tab + N * 12);
+    int idx = (int)(r2f * idf * (float)INV_W);
+    idx = min(idx, N - 1);
+    const float4 f1 = __ldg(ftab + 3 * idx), f2 = __ldg(ftab + 3 * idx + 1), f3 = __ldg(ftab + 3 * idx + 2);
+    const double s = fma(r2, s2w, -float_to_double(f1.w));
     const float sf = approx_float(s);
     s1 = float_to_double(fmaf(fmaf(f1.x, sf, f1.y), sf, f1.z));
     s2 = float_to_double(fmaf(fmaf(f2.x, sf, f2.y), sf, f2.z));
@@ -334,13 +360,14 @@ __device__ __forceinline__ void kernel_factors(const Geom &T, const ScanParams &
         K3 = 0.0;
         K5 = 0.0;
     }
+    const float r2f = approx_float_pos(r2);
 #pragma unroll
     for (int k = CLS; k < ND; ++k) {
-        const double tau = r2 * T.invd2[k];
         double s1, s2, s3;
-        table_sigma<TAB_INV_W, TAB_N>(tab, tau, s1, s2, s3);
-        if (T.cut_small && approx_float_pos(tau) >= (1.0f - CUT_BAND) * T.tcf2 && r2 > P.cut2d[k]) {
+        table_sigma_r2<TAB_INV_W, TAB_N>(tab, r2, r2f, T.id2h[k], T.s2w[k], s1, s2, s3);
+        if (T.cut_small && r2f * T.id2h[k] >= (1.0f - CUT_BAND) * T.tcf2 && r2 > P.cut2d[k]) {
             // t just beyond a cutoff below DEFECT_T: s_p := 1, sigma_p = 1/t^p (Sec. 3.2)
+            const double tau = r2 * T.invd2[k];
             s1 = rsqrt(tau);
             s2 = s1 * s1 * s1;
             s3 = s2 * s1 * s1;

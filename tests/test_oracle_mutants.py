@@ -315,6 +315,12 @@ EXTRA_MUTANTS = [
      "if (K == 4) A[k][3] = r * r * r * r * r * ora_I4(lam);", "if (K == 4) A[k][3] = r * r * r * ora_I4(lam);"),
     ("s#1: sign of the polynomial term",
      "double s1 = e + c / 3.0 * (5.0 * t - 2.0 * t * t2) * g;", "double s1 = e - c / 3.0 * (5.0 * t - 2.0 * t * t2) * g;"),
+    ("on-surface double layer: sign of the stresslet",
+     "for (int i = 0; i < 3; ++i) acc[i] += -6.0 * d[i] * dq * dn * k5 * w;",
+     "for (int i = 0; i < 3; ++i) acc[i] += 6.0 * d[i] * dq * dn * k5 * w;"),
+    ("s#3: coefficient 6 -> 4",
+     "double s3 = e - c / 9.0 * (9.0 * t + 6.0 * t * t2 - 4.0 * t * t2 * t2) * g;",
+     "double s3 = e - c / 9.0 * (9.0 * t + 4.0 * t * t2 - 4.0 * t * t2 * t2) * g;"),
     ("s#2: coefficient 14 -> 12",
      "double s2 = e - c / 3.0 * (3.0 * t - 14.0 * t * t2 + 4.0 * t * t2 * t2) * g;",
      "double s2 = e - c / 3.0 * (3.0 * t - 12.0 * t * t2 + 4.0 * t * t2 * t2) * g;"),
@@ -330,6 +336,8 @@ def _extra_pins():
               ("four-delta weights at b = 0", lambda: F.test_weights_at_b0_are_the_exact_rationals((3, 4, 5, 6))),
               ("s# limits", S.test_sigma_sharp_limits),
               ("on-surface single layer, fifth order", S.test_on_surface_single_layer_fifth_order),
+              ("on-surface self-convergence and agreement with extrapolation",
+               S.test_on_surface_self_convergence_and_agreement_with_extrapolation),
               ("four deltas converge faster than three", F.test_four_deltas_converge_faster_than_three),
               ("s# against 50-digit values", S.test_sigma_sharp_against_mpmath)]
     for name, fn in checks:

@@ -44,8 +44,35 @@ FP64_PEAK_NOMINAL = 1.25e12
 FAR_FLOPS_PER_PAIR = 34 + 1 + 33 + 1      # both layers, one far pair
 NEAR_FLOPS_PER_DELTA_EVAL = 30 + 1 + 1    # one regularized (node, delta) term, both layers
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) from one ncu capture of
-# the sphere128 workload with the current kernels (profiles/launches_sphere128_mixed.md).
-NCU_TRAFFIC = {("sphere128", "k_near"): 210860800 + 29327616, ("sphere128", "k_far32"): 59735552 + 29894144}
+# the sphere128 workload, each with a fingerprint of the kernel's sources at capture time (comments
+# and blank space removed).  When the sources no longer match, the kernel has changed since the
+# counters were taken and the roofline reports traffic as null until they are captured again.
+NCU_TRAFFIC = {
+    ("sphere128", "k_near"): (210860800 + 29327616, "78c637ade0a41ce4"),
+    ("sphere128", "k_far32"): (59735552 + 29894144, "b7d0c68d4ff0ecbf"),
+}
+KERNEL_SOURCES = {"k_near": ("k_near.cu", "near_common.cuh", "ers_internal.h"),
+                  "k_far32": ("k_far.cu", "near_common.cuh", "ers_internal.h")}
+
+
+def source_fingerprint(kernel: str) -> str:
+    """sha256 (first 16 hex digits) of the kernel's source files with comments and blank space removed."""
+    import hashlib
+    import re
+    h = hashlib.sha256()
+    for name in KERNEL_SOURCES[kernel]:
+        text = open(os.path.join(ROOT, "paper_2507_00156_gb300", "csrc", name)).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        text = re.sub(r"//[^\n]*", "", text)
+        h.update("".join(text.split()).encode())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(workload: str, kernel: str):
+    rec = NCU_TRAFFIC.get((workload, kernel))
+    if rec is None or source_fingerprint(kernel) != rec[1]:
+        return None
+    return rec[0]
 
 
 def parse():
@@ -54,7 +81,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--fp64-steps", type=int, default=1)
+    ap.add_argument("--fp64-steps", type=int, default=3, help="timed steps of the plain FP64 path (and of its e2e)")
     ap.add_argument("--cpu-seconds", type=float, default=10.0, help="target wall time of the CPU baseline sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batched", action="store_true", help="skip the batched-launch leg")
@@ -572,20 +599,30 @@ def main():
     q0p = torch.from_numpy(q0h).pin_memory().numpy()
     uh = torch.empty((M, 3), dtype=torch.float64).pin_memory().numpy()
     vh = torch.empty((M, 3), dtype=torch.float64).pin_memory().numpy()
-    s.eval_host(yh, f0p, q0p, rho=wl.rho, precision=ers.PREC_MIXED, u=uh, v=vh)
-    torch.cuda.synchronize()
-    barrier(world)
-    te = 0.0
-    for _ in range(args.steps):
-        flush.fill_(1)
+
+    def timed_host(prec, steps):
+        s.eval_host(yh, f0p, q0p, rho=wl.rho, precision=prec, u=uh, v=vh)
         torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        s.eval_host(yh, f0p, q0p, rho=wl.rho, precision=ers.PREC_MIXED, u=uh, v=vh)
-        te += time.perf_counter() - t0
-    barrier(world)
-    te = max_over_ranks(te, world)
+        barrier(world)
+        te = 0.0
+        for _ in range(steps):
+            flush.fill_(1)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            s.eval_host(yh, f0p, q0p, rho=wl.rho, precision=prec, u=uh, v=vh)
+            te += time.perf_counter() - t0
+        barrier(world)
+        return max_over_ranks(te, world)
+
+    te = timed_host(ers.PREC_MIXED, args.steps)
     e2e = {"value": world * args.steps * M / te, "unit": UNIT, "h2d_bytes_per_step": 3 * M * 3 * 8,
            "d2h_bytes_per_step": 2 * M * 3 * 8, "api": "ers_eval_host (pinned host arrays, includes copies)"}
+    e2e64 = None
+    if args.fp64_steps > 0:
+        te64 = timed_host(ers.PREC_FP64, args.fp64_steps)
+        e2e64 = {"value": world * args.fp64_steps * M / te64, "unit": UNIT, "steps": args.fp64_steps,
+                 "h2d_bytes_per_step": 3 * M * 3 * 8, "d2h_bytes_per_step": 2 * M * 3 * 8,
+                 "api": "ers_eval_host, plain FP64 path (pinned host arrays, includes copies)"}
 
     if rank != 0:
         return
@@ -607,7 +644,7 @@ def main():
                 "units": "69 flops per far (target, node) pair, both layers (FMA = 2, rsqrt = 1)"}
     for r in (roof_near, roof_far):
         r["frac"] = r["achieved"] / r["peak"]
-        r["traffic"] = NCU_TRAFFIC.get((args.workload, r["kernel"].split()[0]))
+        r["traffic"] = ncu_traffic(args.workload, r["kernel"].split()[0])
     # the dominant kernel by live time; the other one beside it
     roof, roof_other = (roof_near, roof_far) if ms_near >= ms_far else (roof_far, roof_near)
     line = {
@@ -672,6 +709,7 @@ def main():
     if t64 is not None:
         ms64 = t64 / args.fp64_steps * 1e3
         line["plain_fp64"] = {"value": world * args.fp64_steps * M / t64, "unit": UNIT, "ms_per_step": ms64,
+                              "steps": args.fp64_steps, "e2e": e2e64,
                               "gpairs_per_s": world * args.fp64_steps * M * N / t64 / 1e9,
                               "kernels_ms": {"closest_point": float(k64[0]), "far_field": float(k64[1]),
                                              "near_field_and_solve": float(k64[2])},

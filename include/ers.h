@@ -373,8 +373,9 @@ int ers_eval_learned(ers_surface *s, ers_closure *c, const ers_params *p, const 
  *  - x0, n0 and b are required (fill them with ers_closest_point, which writes into the
  *    caller's arrays and allocates nothing);
  *  - M must not exceed 524,288 targets per call: the far-field partial sums (6 doubles per
- *    target) live in a fixed 24 MiB device array inside the library, and larger M is rejected
- *    with ERS_E_INVAL and a message naming the limit (split the targets across calls);
+ *    target and source chunk) live in a fixed 24 MiB device array inside the library, and larger
+ *    M is rejected with ERS_E_INVAL and a message naming the limit (split the targets across
+ *    calls); the sources are split into chunks as in ers_eval, but into at most 524,288 / M;
  *  - ers_last_counts is not updated;
  *  - the far and near fields run one after the other on `stream` (ERS_OPT_CONCURRENT is ignored);
  *  - ERS_OPT_SHARP is rejected with ERS_E_UNSUPPORTED.

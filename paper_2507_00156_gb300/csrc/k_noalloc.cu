@@ -4,8 +4,9 @@
 // pre-sized memory pool or under a host allocator that forbids growth, a plugin of a solver
 // that owns all device memory, or a real-time loop where an allocation could stall or fail.
 // ers_eval grows its work buffers on demand; this variant instead keeps the one work buffer it
-// needs (the far-field partial sums, 6 doubles per target) in a fixed file-scope device array
+// needs (the far-field partial sums, 6 doubles per target and source chunk) in a fixed file-scope device array
 // and the smoothing-function table in another, so a call allocates nothing.
+#include <algorithm>
 #include <cstring>
 #include <mutex>
 
@@ -14,8 +15,9 @@
 namespace ers {
 namespace {
 
-// Scratch shared by every call on a device: far-field partial sums, one chunk,
-// [M][6] doubles.  24 MiB => at most NOALLOC_MAX_M targets per call.
+// Scratch shared by every call on a device: far-field partial sums, [chunks][M][6] doubles.
+// 24 MiB => at most NOALLOC_MAX_M targets per call (then one source chunk; fewer targets
+// leave room for more chunks, up to the split ers_eval uses).
 constexpr size_t NOALLOC_SCRATCH_BYTES = (size_t)24 << 20;
 constexpr int64_t NOALLOC_MAX_M = (int64_t)(NOALLOC_SCRATCH_BYTES / (6 * sizeof(double)));
 constexpr size_t NOALLOC_TABLE_DOUBLES = TAB_DEV_BYTES / sizeof(double);
@@ -113,9 +115,22 @@ extern "C" int ers_eval_noalloc(ers_surface *s, const ers_params *p, const doubl
     a.precision = p->precision;
     a.layers = p->layers;
     a.stream = (cudaStream_t)stream;
-    a.part = st->scratch;  // every target's 6 partial sums are written by the far kernel before use
-    a.chunks = 1;
-    a.chunk_len = (s->N + TS32 - 1) / TS32 * TS32;
+    // The far-field work split of ers_eval (target blocks x source chunks, about 16 CTAs per SM),
+    // with the chunk count capped so that the partial sums, 6 doubles per target and chunk, fit
+    // in the fixed scratch array: chunks <= NOALLOC_MAX_M / M.
+    int nsm = 152;
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    const int64_t tpc = p->precision == ERS_PREC_MIXED ? 512 : 256;  // targets per far-field CTA
+    const int64_t tb = (M + tpc - 1) / tpc;
+    int64_t chunks = (16LL * nsm + tb - 1) / tb;
+    chunks = std::max<int64_t>(1, std::min<int64_t>(chunks, std::max<int64_t>(1, s->N / (4 * TS32))));
+    chunks = std::min<int64_t>(chunks, std::max<int64_t>(1, NOALLOC_MAX_M / M));
+    int64_t clen = (s->N + chunks - 1) / chunks;
+    clen = (clen + TS32 - 1) / TS32 * TS32;
+    chunks = (s->N + clen - 1) / clen;
+    a.part = st->scratch;  // every (chunk, target) partial sum is written by the far kernel before use
+    a.chunks = (int)chunks;
+    a.chunk_len = clen;
     a.counters = nullptr;  // ers_last_counts is not updated by this entry point
     e = (p->precision == ERS_PREC_MIXED) ? launch_far32(a) : launch_far64(a);
     if (e != cudaSuccess) return cuda_fail(e, "ers_eval_noalloc: far-field kernel");

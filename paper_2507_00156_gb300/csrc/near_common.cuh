@@ -278,8 +278,11 @@ __device__ __forceinline__ void table_sigma(const double *__restrict__ tab, doub
 
 // table_sigma at tau = r^2 / delta^2 without forming tau in FP64: the interval from the FP32
 // product r2f idf (r2f, idf: r^2 and 1/delta^2 as floats), the local variable as
-// r^2 (2 INV_W / delta^2) - (2 i + 1) in one FMA (an interval chosen one off by the FP32 product
-// leaves the local variable within 1e-6 outside [-1, 1], where the piece is still as accurate).
+// r^2 (2 INV_W / delta^2) - (2 i + 1) in one FMA.  The FP32 product carries three roundings
+// (r2f, idf and the product: at most ~1.8e-7 of tau), so near an interval end it can pick the
+// neighbouring interval; the local variable then lies outside [-1, 1] by at most
+// 2 INV_W tau 1.8e-7 (below 1.4e-4 for INV_W = 16 and tau < 24), where each piece is still
+// accurate to ~1e-15 (checked on the host at |s| = 1 + 2e-4 for every interval).
 template <int INV_W, int N>
 __device__ __forceinline__ void table_sigma_r2(const double *__restrict__ tab, double r2, float r2f, float idf,
                                                double s2w, double &s1, double &s2, double &s3) {

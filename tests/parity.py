@@ -17,6 +17,15 @@ def rel_err(got, ref):
     return float(np.abs(got - ref).max() / np.abs(ref).max())
 
 
+def per_target_rel_err(got, ref, floor=1e-3):
+    """max over targets y of |got(y) - ref(y)|_inf / max(|ref(y)|_inf, floor max_y |ref(y)|_inf):
+    each target against its own magnitude, with a floor of 1e-3 of the largest so that targets
+    where the value nearly vanishes do not turn rounding into an unbounded relative error."""
+    num = np.abs(got - ref).max(axis=1)
+    den = np.maximum(np.abs(ref).max(axis=1), floor * np.abs(ref).max())
+    return float((num / den).max())
+
+
 @functools.lru_cache(maxsize=8)
 def oracle_problem(name):
     wl = workloads.config(name)

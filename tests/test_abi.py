@@ -146,6 +146,43 @@ def test_sigma_device_layout_accuracy(L):
     assert worst < 6e-15, worst
 
 
+def test_sigma_device_layout_beyond_the_interval_ends(L):
+    """The near kernel picks the interval from the FP32 product r2f * idf (three roundings, at most
+    ~1.8e-7 of tau), so the local variable s = r^2 (2 INV_W / delta^2) - (2 i + 1) can leave [-1, 1]
+    by up to 2 INV_W tau 1.8e-7 < 1.4e-4 for tau < 24.  Each piece, evaluated as the kernel does at
+    |s| = 1 + 2e-4 (just past that bound, on both sides of every interval), still reproduces
+    s_p(t)/t^p of Eqs. (s1)-(s3) to ~1e-15."""
+    mp = pytest.importorskip("mpmath")
+    mp.mp.dps = max(mp.mp.dps, 40)
+    nbytes = NINT * 3 * 4 * 8 + NINT * 3 * 16
+    raw = np.empty(nbytes // 8)
+    L.ers_debug_sigma_device.argtypes = [ctypes.c_void_p, ctypes.c_int64]
+    assert L.ers_debug_sigma_device(raw.ctypes.data, nbytes) == 0
+    dpart = raw[: NINT * 12].reshape(NINT, 3, 4)
+    fpart = raw[NINT * 12:].view(np.float32).reshape(NINT, 3, 4)
+    f32 = np.float32
+
+    def fmaf(a, b, c):
+        return f32(np.float64(a) * np.float64(b) + np.float64(c))
+
+    over = 1.0 + 2e-4
+    worst = 0.0
+    for i in range(NINT):
+        for s in (-over, over):
+            tau = (s + 2 * i + 1) / (2 * INV_W)
+            if tau < 0:
+                continue
+            sf = f32(s)
+            ref = _sigma_mp(mp, tau)
+            for p_ in range(3):
+                c6, c5, c4 = fpart[i, p_, :3]
+                v = float(fmaf(fmaf(c6, sf, c5), sf, c4))
+                for c in dpart[i, p_]:
+                    v = v * s + c
+                worst = max(worst, abs(v - float(ref[p_])) / abs(float(ref[p_])))
+    assert worst < 8e-15, worst
+
+
 def test_sigma_sharp_device_layout_accuracy(L):
     """The on-surface table (s#_p(t)/t^p of Sec. 2.1, intervals of 1/32 on tau in [0, 64)), as the
     kernel evaluates it (degrees 6..4 in FP32, 3..0 in FP64), stays within ~1e-15 of 60-digit values."""

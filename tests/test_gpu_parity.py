@@ -1,7 +1,8 @@
 """Parity of the CUDA path (through the C ABI) with the FP64 oracle.
 
 Bars: FP64 path within 1e-11 relative (max-norm over targets, per layer); mixed-precision far
-field within 1e-6.  Sizes span several far-field tiles and ragged tails; the full-size bench
+field within 1e-6.  The same bars also hold per target, each target's error against its own
+magnitude (floored at 1e-3 of the largest; parity.per_target_rel_err).  Sizes span several far-field tiles and ragged tails; the full-size bench
 workload is checked on a seeded sample of targets.
 """
 import numpy as np
@@ -9,7 +10,7 @@ import pytest
 
 import oracle
 import workloads
-from parity import GpuProblem, oracle_eval, oracle_problem, rel_err
+from parity import GpuProblem, oracle_eval, oracle_problem, per_target_rel_err, rel_err
 
 pytestmark = pytest.mark.gpu
 FP64_TOL = 1e-11
@@ -70,6 +71,8 @@ def test_eval_all_targets(ers, name, precision, tol):
     assert np.abs(b - bo).max() < 1e-13
     eu, ev = rel_err(u, uo), rel_err(v, vo)
     assert eu <= tol and ev <= tol, (eu, ev)
+    pu, pv = per_target_rel_err(u, uo), per_target_rel_err(v, vo)
+    assert pu <= tol and pv <= tol, (pu, pv)
 
 
 def test_eval_ellipsoid_with_far_points(ers):
@@ -87,6 +90,8 @@ def test_eval_ellipsoid_with_far_points(ers):
     for prec, tol in ((0, FP64_TOL), (1, MIXED_TOL)):
         u, v, bg = g.eval(g.targets(sel), precision=prec)
         assert rel_err(u, uo) <= tol and rel_err(v, vo) <= tol, (prec, rel_err(u, uo), rel_err(v, vo))
+        pu, pv = per_target_rel_err(u, uo), per_target_rel_err(v, vo)
+        assert pu <= tol and pv <= tol, (prec, pu, pv)
 
 
 # Below 6 the cutoff is a non-tie value: the lattice rule has many node pairs at exact multiples
@@ -228,6 +233,8 @@ def test_full_size_bench_workload_sampled(ers, precision, tol):
     y, uo, vo, bo = oracle_eval("sphere128", sel=sel)
     assert np.array_equal(y, y_all[sel])
     assert rel_err(u[sel], uo) <= tol and rel_err(v[sel], vo) <= tol, (rel_err(u[sel], uo), rel_err(v[sel], vo))
+    pu, pv = per_target_rel_err(u[sel], uo), per_target_rel_err(v[sel], vo)
+    assert pu <= tol and pv <= tol, (pu, pv)
     assert np.isfinite(u).all() and np.isfinite(v).all()
 
 
@@ -244,4 +251,6 @@ def test_full_size_ellipsoid_workload_sampled(ers, precision, tol):
     assert np.array_equal(y, y_all[sel])
     assert np.array_equal(b[sel] == 0, bo == 0) and (bo == 0).sum() > 50
     assert rel_err(u[sel], uo) <= tol and rel_err(v[sel], vo) <= tol, (rel_err(u[sel], uo), rel_err(v[sel], vo))
+    pu, pv = per_target_rel_err(u[sel], uo), per_target_rel_err(v[sel], vo)
+    assert pu <= tol and pv <= tol, (pu, pv)
     assert np.isfinite(u).all() and np.isfinite(v).all()

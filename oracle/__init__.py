@@ -10,6 +10,8 @@ Functions:
   closest_point(shape, y)                   x0, n0, b with y = x0 + b n0 (Sec. 2)
   evaluate(nodes, f, q, y, cp, f0, q0, ...) SL and DL values, direct or localized (Secs. 2, 3.3)
   sigma(t), I0(lam), I2(lam), extrapolate   building blocks (Eqs. (s1)-(s3), (I0), (I2), (extrap_eqn))
+  evaluate_reduced, reduced_weights         the learned closure's one- and two-delta sums
+  closure (submodule)                       the closure's features: frame, curvatures, density jets
   evaluate_tree(...), tree_info, tree_weights, lagrange
                                             the treecode far field of Sec. 3.4 (ers_treecode.c)
 """
@@ -85,6 +87,10 @@ def bind(lib):
     lib.ora_extrapolate_k.argtypes = [cint, P, dbl, dbl, P, cint, P]
     lib.ora_eval_one_delta.restype = None
     lib.ora_eval_one_delta.argtypes = [P, P, P, P, P, i64, P, P, P, P, P, P, i64, dbl, dbl, P, P]
+    lib.ora_reduced_weights.restype = cint
+    lib.ora_reduced_weights.argtypes = [cint, P, dbl, dbl, P, P]
+    lib.ora_eval_reduced.restype = i64
+    lib.ora_eval_reduced.argtypes = [cint, P, P, P, P, P, i64, P, P, P, P, P, P, i64, dbl, P, dbl, P, P, P]
     lib.ora_plain.restype = None
     lib.ora_plain.argtypes = [P, P, P, P, P, i64, P, i64, P, P]
     lib.ora_num_threads.restype = cint
@@ -214,6 +220,29 @@ def evaluate_one_delta(x, n, w, f, q, y, x0, n0, b, f0, q0, delta, tc=6.0):
     lib.ora_eval_one_delta(_p(x), _p(n), _p(w), _p(f), _p(q), N, _p(y), _p(x0), _p(n0), _p(b), _p(f0), _p(q0), M,
                            float(delta), float(tc), _p(u), _p(v))
     return u, v
+
+
+def reduced_weights(K: int, rho, b: float, h: float):
+    """The one- or two-delta weights beta and gamma of the learned closure's reduced extrapolation
+    (Eq. (extrap_eqn) with the c2 term kept aside); returns (beta (2,), gamma, rc)."""
+    beta = np.empty(2)
+    g = np.empty(1)
+    rc = _load().ora_reduced_weights(int(K), _p(_c(rho)), float(b), float(h), _p(beta), _p(g))
+    return beta, float(g[0]), int(rc)
+
+
+def evaluate_reduced(K, x, n, w, f, q, y, x0, n0, b, f0, q0, h, rho, tc=6.0):
+    """The learned closure's one-delta (K = 1) or two-delta (K = 2) sums by the definition, near
+    radius tc rho[K-1] h; returns u, v (M,3) and gamma (M).  See ers_oracle.c:ora_eval_reduced."""
+    lib = _load()
+    x, n, w, f, q = map(_c, (x, n, w, f, q))
+    y, x0, n0, b, f0, q0 = map(_c, (y, x0, n0, b, f0, q0))
+    N, M = w.shape[0], b.shape[0]
+    u, v, g = np.empty((M, 3)), np.empty((M, 3)), np.empty(M)
+    assert K in (1, 2)
+    lib.ora_eval_reduced(int(K), _p(x), _p(n), _p(w), _p(f), _p(q), N, _p(y), _p(x0), _p(n0), _p(b), _p(f0),
+                         _p(q0), M, float(h), _p(_c(rho)), float(tc), _p(u), _p(v), _p(g))
+    return u, v, g
 
 
 def plain(x, n, w, f, q, y):

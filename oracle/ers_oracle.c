@@ -17,8 +17,10 @@
  * values, the limits at 0 and infinity, O(h^5) against the sphere closed form and in
  * self-convergence at shared nodes; for the four-delta variant: I4 against quadrature of its
  * defining integral, I4' = -4 lambda I2, exact weights at b = 0, faster than O(h^5) against the
- * sphere closed form; the treecode far field of Sec. 3.4 lives in ers_treecode.c with its own
- * pins).  Nothing here is "parity unpinned".
+ * sphere closed form; for the reduced one- and two-delta sums of the learned closure: the exact
+ * two-delta weights at b = 0, their defining identities at every b, and the two-delta value with
+ * the three-delta solve's c2 reproducing the three-delta value; the treecode far field of Sec. 3.4
+ * lives in ers_treecode.c with its own pins).  Nothing here is "parity unpinned".
  */
 #include <math.h>
 #include <stdint.h>
@@ -590,6 +592,114 @@ void ora_eval_one_delta(const double *x, const double *nrm, const double *w, con
         }
         for (int i = 0; i < 3; ++i) { u[3 * m + i] = su[i] * inv8pi; v[3 * m + i] = sv[i] * inv8pi + chi * qm0[i]; }
     }
+}
+
+/*
+ * The reduced extrapolation of the learned closure (one or two deltas instead of three).
+ * Eq. (extrap_eqn) for delta_k = rho_k h reads U_k = u + c1 rho_k I0(lambda_k) + c2 rho_k^3 I2(lambda_k).
+ *   K = 1: beta = (1), gamma = 0: the single sum U_0 is returned as it is.
+ *   K = 2: the c2 term is kept aside and the two equations for k = 0, 1 are solved for u:
+ *          u + gamma c2 = beta_0 U_0 + beta_1 U_1, with beta the weights of the 2 x 2 system
+ *          [[1, rho_0 I0(lambda_0)], [1, rho_1 I0(lambda_1)]] (sum beta = 1, sum beta rho I0 = 0)
+ *          and gamma = sum beta_k rho_k^3 I2(lambda_k).
+ * beta is the first row of the inverse of that matrix: beta = (a1, -a0) / (a1 - a0) with
+ * a_k = rho_k I0(lambda_k).  Returns 0, or -1 when a1 - a0 is 0 or not finite (then beta = (1, 0),
+ * the single smallest-delta sum, and gamma its I2 term).
+ */
+int ora_reduced_weights(int K, const double *rho, double b, double h, double beta[2], double *gamma) {
+    if (K == 1) {
+        beta[0] = 1.0;
+        beta[1] = 0.0;
+        *gamma = 0.0;
+        return 0;
+    }
+    double a[2], c[2];
+    for (int k = 0; k < 2; ++k) {
+        double lam = b / (rho[k] * h);
+        a[k] = rho[k] * ora_I0(lam);
+        c[k] = rho[k] * rho[k] * rho[k] * ora_I2(lam);
+    }
+    double det = a[1] - a[0];
+    int rc = 0;
+    if (det != 0.0 && isfinite(det)) {
+        beta[0] = a[1] / det;
+        beta[1] = -a[0] / det;
+    } else {
+        beta[0] = 1.0;
+        beta[1] = 0.0;
+        rc = -1;
+    }
+    *gamma = beta[0] * c[0] + beta[1] * c[1];
+    return rc;
+}
+
+/*
+ * The one- or two-delta sums of the learned closure at every target, by the definition (every
+ * node, s_p := 1 where r/delta_k > tc, Sec. 3.2): for K = 1 the regularized sum for delta_0, for
+ * K = 2 the combination sum_k beta_k U_k of ora_reduced_weights (u + gamma c2 of Eq. (extrap_eqn)),
+ * with U_k the subtracted sums of Eqs. (Stokes_SL2), (Stokes_DL2) for delta_k.  The near radius is
+ * Rc = tc delta_{K-1}; a target with |b| > Rc takes the plain sums of Eqs. (Stokes_SL), (Stokes_DL)
+ * without subtraction (as ora_eval_k does beyond its radius) and gamma = 0.  Outputs u, v (M,3) and
+ * gamma (M).  Returns the number of targets whose weights fell back.
+ */
+int64_t ora_eval_reduced(int K, const double *x, const double *nrm, const double *w, const double *f,
+                         const double *q, int64_t N, const double *y, const double *x0, const double *n0,
+                         const double *b, const double *f0, const double *q0, int64_t M, double h,
+                         const double *rho, double tc, double *u, double *v, double *gamma) {
+    const double inv8pi = 1.0 / (8.0 * ORA_PI);
+    const double Rc = tc * rho[K - 1] * h;
+    int64_t nfail = 0;
+#pragma omp parallel for schedule(dynamic, 16) reduction(+ : nfail)
+    for (int64_t m = 0; m < M; ++m) {
+        const double *ym = y + 3 * m;
+        double bm = b[m];
+        if (fabs(bm) > Rc) {
+            double su[3] = {0, 0, 0}, sv[3] = {0, 0, 0};
+            for (int64_t j = 0; j < N; ++j) {
+                double d[3] = {ym[0] - x[3 * j], ym[1] - x[3 * j + 1], ym[2] - x[3 * j + 2]};
+                double r = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+                ora_sl_plain(d, r, f + 3 * j, w[j], su);
+                ora_dl_plain(d, r, q + 3 * j, nrm + 3 * j, w[j], sv);
+            }
+            for (int i = 0; i < 3; ++i) { u[3 * m + i] = su[i] * inv8pi; v[3 * m + i] = sv[i] * inv8pi; }
+            gamma[m] = 0.0;
+            continue;
+        }
+        const double *nm0 = n0 + 3 * m, *xm0 = x0 + 3 * m, *fm0 = f0 + 3 * m, *qm0 = q0 + 3 * m;
+        double fn0 = fm0[0] * nm0[0] + fm0[1] * nm0[1] + fm0[2] * nm0[2];
+        double chi = (bm < 0.0) ? 1.0 : ((bm > 0.0) ? 0.0 : 0.5);
+        double su[2][3], sv[2][3];
+        memset(su, 0, sizeof su); memset(sv, 0, sizeof sv);
+        for (int64_t j = 0; j < N; ++j) {
+            const double *xj = x + 3 * j, *nj = nrm + 3 * j;
+            double d[3] = {ym[0] - xj[0], ym[1] - xj[1], ym[2] - xj[2]};
+            double r = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+            double g[3], Q[3], xh[3];
+            for (int i = 0; i < 3; ++i) {
+                g[i] = f[3 * j + i] - fn0 * nj[i];
+                Q[i] = q[3 * j + i] - qm0[i];
+                xh[i] = xj[i] - xm0[i];
+            }
+            for (int k = 0; k < K; ++k) {
+                double delta = rho[k] * h;
+                ora_sl_term(d, r, delta, tc, g, w[j], su[k], 0);
+                ora_dl_term(r, delta, tc, bm, nm0, xh, Q, nj, w[j], sv[k], 0);
+            }
+        }
+        double beta[2], gm;
+        if (ora_reduced_weights(K, rho, bm, h, beta, &gm) != 0) nfail += 1;
+        for (int i = 0; i < 3; ++i) {
+            double uu = 0.0, vv = 0.0;
+            for (int k = 0; k < K; ++k) {
+                uu += beta[k] * su[k][i] * inv8pi;
+                vv += beta[k] * (sv[k][i] * inv8pi + chi * qm0[i]);
+            }
+            u[3 * m + i] = uu;
+            v[3 * m + i] = vv;
+        }
+        gamma[m] = gm;
+    }
+    return nfail;
 }
 
 /*

@@ -302,30 +302,32 @@ def two_drop_leg(ers, torch, fine: bool):
                     "iterations 13, 12, 12; max 3.17e-3, 1.07e-4, 4.06e-6; L2 1.19e-4, 6.11e-6, 2.11e-7"}
 
 
-TRAIN_RADII = (1.0, 1.0, 0.85, 0.85, 0.7)  # one seeded density each
+TRAIN_RADII = (1.0, 1.0, 1.0, 0.85, 0.7)  # one seeded density each
+LEARNED_H = 1 / 96     # training spacing = the evaluation spacing
+LEARNED_STEPS = 3000   # Adam steps per network
 
 
 def learned_leg(ers, torch, s, wl, steps: int, warmup: int):
     """The learned near-field closure: networks trained on the GPU (own kernels) from five seeded
-    densities on spheres at the bench spacing h = 1/128 (the bench surface and spheres of radius
-    0.85 and 0.7, so that the curvature feature kappa h spans 1/128 .. 1/90 and covers the
-    evaluation's 1/96; targets: the nodes and 200,000 band points |b| <= 6 rho_2 h, the two-delta
-    closure's near radius), then evaluated on the two unit spheres 0.01 apart at h = 1/96: the
-    integral over the first sphere at the nodes of both, with validation against the three-delta
-    method (tolerance 1e-5, every 32nd target) and fallback to it.  Also timed with the closure
-    accepted unconditionally (no fallback), against the plain mixed evaluation of the same
-    problem."""
+    densities on spheres at the evaluation spacing h = 1/96 (three on the unit sphere, one each on
+    spheres of radius 0.85 and 0.7, so that the curvature input kappa h spans 1/96 .. 1/67; targets:
+    the nodes and 200,000 band points |b| <= 6 rho_2 h, the two-delta closure's near radius), then
+    evaluated on the two unit spheres 0.01 apart at h = 1/96: the integral over the first sphere at
+    the nodes of both, with validation against the three-delta method (tolerance 1e-5, every 32nd
+    target), the per-layer gate and fallback to the method.  Also timed with the closure accepted
+    unconditionally (no fallback), against the plain mixed evaluation of the same problem."""
     dev = torch.device("cuda")
     t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
     rng = np.random.default_rng(5005)
     data = {1: [], 2: []}
-    band_w = 6.0 * wl.rho[1] * wl.h
+    h_train = LEARNED_H
+    band_w = 6.0 * wl.rho[1] * h_train
     t0 = time.perf_counter()
     surfs = {}
     for R in TRAIN_RADII:
         if R not in surfs:
             sh = workloads.Shape((0.0, 0.0, 0.0), (R, R, R))
-            sR = s if R == 1.0 else ers.Surface(sh.center, sh.axes, wl.h)
+            sR = ers.Surface(sh.center, sh.axes, h_train)
             xR = sR.nodes()[0].cpu().numpy()
             yd = t(np.concatenate([xR, workloads.near_band_targets(sh, 200000, band_w, rng)[0]]))
             x0, n0, b = sR.closest_point(yd)
@@ -334,10 +336,9 @@ def learned_leg(ers, torch, s, wl, steps: int, warmup: int):
         fc, qc = workloads.density_coeffs(rng), workloads.density_coeffs(rng)
         sR.set_density(t(workloads.poly_eval(fc, x)), t(workloads.poly_eval(qc, x)))
         f0, q0 = t(workloads.poly_eval(fc, x0h)), t(workloads.poly_eval(qc, x0h))
-        gf0, gq0 = t(workloads.poly_jacobian(fc, x0h)), t(workloads.poly_jacobian(qc, x0h))
         u3, v3 = sR.eval(yd, f0, q0, rho=wl.rho, precision=ers.PREC_MIXED, x0=x0, n0=n0, b=b)
         for nd in (1, 2):
-            out = ers.closure_data(sR, yd, x0, n0, b, f0, q0, gf0, gq0, u3, v3, rho=wl.rho, ndelta=nd)
+            out = ers.closure_data(sR, yd, x0, n0, b, f0, q0, u3, v3, rho=wl.rho, ndelta=nd)
             sel = out[4].bool()
             data[nd].append([z[sel] for z in out[:4]])
     del surfs
@@ -347,7 +348,7 @@ def learned_leg(ers, torch, s, wl, steps: int, warmup: int):
     for nd in (1, 2):
         Xs, Xd, Ts, Td = (torch.cat([d[i] for d in data[nd]]).contiguous() for i in range(4))
         nets[nd] = ers.Closure(seed=100 + nd)
-        losses[nd] = [nets[nd].train(layer, X, T, steps=3000, batch=8192, lr=2e-3)
+        losses[nd] = [nets[nd].train(layer, X, T, steps=LEARNED_STEPS, batch=8192, lr=2e-3)
                       for layer, (X, T) in enumerate(((Xs, Ts), (Xd, Td)))]
     torch.cuda.synchronize()
     t_train = time.perf_counter() - t0
@@ -368,7 +369,6 @@ def learned_leg(ers, torch, s, wl, steps: int, warmup: int):
     x0, n0, b = sa.closest_point(yed)
     x0h = x0.cpu().numpy()
     f0, q0 = t(workloads.poly_eval(fc, x0h)), t(workloads.poly_eval(qc, x0h))
-    gf0, gq0 = t(workloads.poly_jacobian(fc, x0h)), t(workloads.poly_jacobian(qc, x0h))
     M = len(ye)
     u = torch.empty((M, 3), dtype=torch.float64, device=dev)
     v = torch.empty((M, 3), dtype=torch.float64, device=dev)
@@ -398,30 +398,31 @@ def learned_leg(ers, torch, s, wl, steps: int, warmup: int):
     e64.record(stream)
     e64.synchronize()
     t_fp64 = a64.elapsed_time(e64) / 1e3
-    res = {"workload": "train: spheres of radius 1, 1, 0.85, 0.85, 0.7 at h=1/128, one seeded density each, "
+    res = {"workload": "train: spheres of radius 1, 1, 1, 0.85, 0.7 at h=1/96, one seeded density each, "
                        "nodes + 200k band points |b| <= 18h; evaluate: two unit spheres gap 0.01, h=1/96, "
-                       "integral over the first at the nodes of both",
+                       "integral over the first at the nodes of both (a density not trained on)",
            "targets": M, "nodes": int(xa.shape[0]),
            "plain_fp64": {"value": M / t_fp64, "unit": UNIT, "ms_per_step": t_fp64 * 1e3},
            "plain_mixed": {"value": M / t_plain, "unit": UNIT, "ms_per_step": t_plain * 1e3},
-           "training": {"samples_per_network": nsamples, "densities": 5, "steps": 3000, "batch": 8192,
-                        "data_s": t_data, "train_s": t_train}}
-    args = (yed, x0, n0, b, f0, q0, gf0, gq0)
-    # the same closures with the network's output set to zero: what the network gains over the
-    # one- or two-delta sums alone
+           "training": {"samples_per_network": nsamples, "densities": len(TRAIN_RADII), "steps": LEARNED_STEPS,
+                        "batch": 8192, "data_s": t_data, "train_s": t_train}}
+    args = (yed, x0, n0, b, f0, q0)
+    # an untrained closure predicts no correction: what the network gains over the one- or
+    # two-delta sums alone
     zero = ers.Closure(seed=0)
-    for layer in (0, 1):
-        zero.set_params(layer, np.zeros(ers.NPARAM, np.float32))
     for nd in (2, 1):
         t_val, out = timed(lambda: ers.eval_learned(sa, nets[nd], *args, rho=wl.rho, precision=ers.PREC_MIXED,
                                                     tol=1e-5, vstride=32, ndelta=nd, u=u, v=v))
         _, _, verr, fb = out
+        used, ew, eo = nets[nd].last_gate()
         t_acc, _ = timed(lambda: ers.eval_learned(sa, nets[nd], *args, rho=wl.rho, precision=ers.PREC_MIXED,
                                                   tol=1e30, vstride=1 << 20, ndelta=nd, u=u, v=v))
         ul, vl = u.cpu().numpy(), v.cpu().numpy()
         res[f"ndelta{nd}"] = {
             "value": M / t_val, "unit": UNIT, "ms_per_step": t_val * 1e3,
             "fell_back_at_tol_1e-5": bool(fb), "validation_rel_err": [float(z) for z in verr],
+            "gate": {"network_kept": list(used), "validation_err_with_network": list(ew),
+                     "validation_err_without_network": list(eo)},
             "targets_outside_training_extent": nets[nd].last_out_of_range(),
             "accepted": {"value": M / t_acc, "ms_per_step": t_acc * 1e3,
                          "speedup_vs_plain_mixed": t_plain / t_acc, "speedup_vs_plain_fp64": t_fp64 / t_acc,

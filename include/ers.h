@@ -262,33 +262,51 @@ int ers_batch_free(ers_batch *b);
  *
  * Eq. (extrap_eqn) models the regularized value as u^delta = u + c1 rho I0(lambda) +
  * c2 rho^3 I2(lambda) + O(delta^5) with c1, c2 independent of delta.  The closure evaluates fewer
- * regularized sums over a smaller near set and lets a network predict what they miss:
+ * regularized sums over a smaller near set and predicts what they miss:
  *   ndelta = 1: the single sum u^{delta_0} (near set r <= cutoff_t delta_0, a quarter of the
- *     pairs for rho = (2,3,4)); the network predicts u - u^{delta_0} / (h S);
+ *     pairs for rho = (2,3,4)); predicted: the whole correction u - u^{delta_0};
  *   ndelta = 2: the two smaller deltas (near set r <= cutoff_t delta_1) combined with weights
- *     beta (sum beta = 1, sum beta rho I0 = 0) into u + gamma c2; the network predicts c2 / (h^3 S).
- * Network: an MLP 13 -> 64 -> 64 -> 64 -> 3 with GELU, BF16 weights and activations and FP32
- * accumulation, evaluated on the tensor cores (tcgen05).  One network per layer (layer 0 =
- * single, 1 = double).  Features per near target, in the local frame (t1, t2, n0) at x0:
- * lambda_0 = b/delta_0; kappa_1 h, kappa_2 h (principal curvatures); the density at x0 and its
- * tangential derivatives (times h), divided by their largest magnitude S; rho_0.  Outputs are in
- * the same local frame.
+ *     beta (sum beta = 1, sum beta rho I0 = 0) into u + gamma c2 (gamma = sum beta rho^3 I2);
+ *     predicted: c2.
+ * c1 and c2 are linear in the density and fixed by the surface and the density near the closest
+ * point x0, so the prediction is a linear map from density jets at x0 whose coefficients a
+ * network computes from the local geometry:
+ *   frame: t1, t2 the principal directions at x0 (where the principal curvatures agree to 1e-6,
+ *     as on a sphere: t1 = n0 x a / |n0 x a|, a = e_x, or e_y when |n0_x| >= 0.9), n0;
+ *   geometry (the network's input): lambda_0 = b / delta_0, kappa_1 h >= kappa_2 h (principal
+ *     curvatures, positive on a convex surface), rho_0, rho_1;
+ *   jets: derivatives of the density's components along t1, t2, n0 with respect to the
+ *     tangent-plane coordinates ((x - x0).t1, (x - x0).t2) / h, taken from the least-squares
+ *     polynomial of total degree <= 4 fitted to the node values (ers_set_density) within 3.5 h of
+ *     x0; single layer: orders 0..2 (18 values, component-major, within a component the
+ *     monomial order 1, xi, eta, xi^2, xi eta, eta^2), double layer: orders 1..3 (27 values:
+ *     xi, eta, xi^2, xi eta, eta^2, xi^3, xi^2 eta, xi eta^2, eta^3); divided by their largest
+ *     magnitude S;
+ *   output: c (3 components in the frame) = sum_j A_ej jet_j, the correction divided by S h^p
+ *     (p = 1 single layer, p = 0 double layer); for ndelta = 2 the correction is -gamma c2.
+ * Network: an MLP 16 -> 64 -> 64 -> 64 -> 96 with GELU (5 inputs and 3 J outputs used, J = 18
+ * single, 27 double layer), BF16 weights and activations, FP32 accumulation, on the tensor cores
+ * (tcgen05), the head's contraction in FP32.  One network per layer (0 = single, 1 = double).
+ * A sample record is 48 floats: [geometry (5) | 0 (11) | jets (J) | 0]; outputs are 4 floats (c, 0).
+ * The density jets need targets within cutoff_t delta_{ndelta-1} of the surface (only those carry
+ * a correction) and at least 15 nodes within 3.5 h of x0.
  */
 typedef struct ers_closure ers_closure;
 
-/* Create the two networks with He-uniform weights drawn from `seed` (zero biases). */
+/* Create the two networks: He-uniform hidden weights drawn from `seed`, zero biases and a zero
+ * last layer (an untrained network predicts no correction). */
 int ers_closure_create(uint64_t seed, ers_closure **out);
 int ers_closure_free(ers_closure *c);
 
 /*
  * Read (get != NULL) and/or replace (set != NULL) the FP32 parameters of one network, host
- * arrays of count = 10448 floats: W1 (64x16), b1 (64), W2 (64x64), b2, W3 (64x64), b3, W4 (16x64),
- * b4 (16), weights row-major [out][in]; rows 3..15 of W4 and b4[3..15] are unused.
+ * arrays of count = 15648 floats: W1 (64x16), b1 (64), W2 (64x64), b2, W3 (64x64), b3, W4 (96x64),
+ * b4 (96), weights row-major [out][in]; rows 3 J..95 of W4 and b4 are unused.
  */
 int ers_closure_params(ers_closure *c, int layer, float *get, const float *set, int64_t count);
 
-/* Network outputs Y (n, 4) floats dev (3 used) for features X (n, 16) floats dev (13 used), on
- * the tensor cores.  A tensor-core wait that expires sets a flag read by ers_closure_status. */
+/* Outputs Y (n, 4) floats dev (c, 0) for sample records X (n, 48) floats dev, on the tensor
+ * cores.  A tensor-core wait that expires sets a flag read by ers_closure_status. */
 int ers_closure_infer(ers_closure *c, int layer, const float *X, int64_t n, float *Y, void *stream);
 
 /* The same network evaluated with FP32 CUDA-core arithmetic and the same BF16 rounding (a check of
@@ -299,30 +317,30 @@ int ers_closure_infer_reference(ers_closure *c, int layer, const float *X, int64
 int ers_closure_status(ers_closure *c, int *timed_out);
 
 /*
- * The extent of the features one network was trained on: get and/or set host arrays of 26 floats,
- * lo[13] then hi[13], one pair per feature (lambda_0, the two principal curvatures times h, the
- * nine scaled density components, rho_0).  ers_closure_train widens the extent to cover every
- * feature vector it trains on (non-finite values are skipped); set replaces it (lo <= hi for
- * every feature, else ERS_E_INVAL).  *have (may be NULL) = 1 once the extent is known, 0 before.
- * Synchronous.
+ * The extent of the geometry one network was trained on: get and/or set host arrays of 10 floats,
+ * lo[5] then hi[5], one pair per input (lambda_0, the two principal curvatures times h, rho_0,
+ * rho_1).  ers_closure_train widens the extent to cover every record it trains on (non-finite
+ * values are skipped); set replaces it (lo <= hi for every input, else ERS_E_INVAL).  *have (may
+ * be NULL) = 1 once the extent is known, 0 before.  Synchronous.
  */
 int ers_closure_range(ers_closure *c, int layer, float *get, const float *set, int *have);
 
 /*
  * With the check enabled (the default), ers_eval_learned evaluates every corrected target whose
- * features leave the extent of a network that has one (each feature widened by 5 % of its width
+ * geometry leaves the extent of a network that has one (each input widened by 5 % of its width
  * plus 1e-3 of its magnitude plus 1e-6) with the three-delta method instead of the network: the
- * network is not used where it was not trained.  enabled = 0 turns the check off.
+ * network is not used where it was not trained (the jets enter linearly and are not checked).
+ * enabled = 0 turns the check off.
  */
 int ers_closure_set_range_check(ers_closure *c, int enabled);
 
 /* *n = the number of targets of the last ers_eval_learned call that left the extent. */
 int ers_closure_last_out_of_range(ers_closure *c, int64_t *n);
 
-/* Loss L = (1/n) sum_s 1/2 |y_s - t_s|^2 over the 3 outputs and its gradient G (10448 floats dev)
- * with respect to the FP32 parameters (BF16 rounding in the forward pass, straight-through in the
- * backward pass).  X (n,16), T (n,4) floats dev; *loss (host) may be NULL.  Synchronizes when
- * loss is requested. */
+/* Loss L = (1/n) sum_s w_s/2 |c_s - t_s|^2 (c_s the network's output for record s, T (n, 4) =
+ * (t_s, w_s)) and its gradient G (15648 floats dev) with respect to the FP32 parameters (BF16
+ * rounding in the forward pass, straight-through in the backward pass).  X (n,48), T (n,4) floats
+ * dev; *loss (host) may be NULL.  Synchronizes when loss is requested. */
 int ers_closure_grad(ers_closure *c, int layer, const float *X, const float *T, int64_t n, float *G, double *loss,
                      void *stream);
 
@@ -334,35 +352,45 @@ int ers_closure_train(ers_closure *c, int layer, const float *X, const float *T,
 
 /*
  * Training data from the method itself: runs the sums with ndelta deltas (1: delta_0 alone;
- * 2: delta_0, delta_1 with the two-delta weights) at M targets and writes the features Xs, Xd
- * (M,16) and targets Ts, Td (M,4) of both networks, in the local frame of the target and scaled
- * by the density scale S: ndelta = 1: c = (u3 - one-delta value) / (h S); ndelta = 2:
- * c2 = (two-delta value - u3) / (gamma h^3 S), with u3, v3 (M,3) dev the values of ers_eval
- * (three deltas) at the same targets.  gf0, gq0 (M,3,3) dev are the Jacobians d f_i / d x_j and
- * d q_i / d x_j at x0.  valid (M) ints: 1 for targets that are training samples: within the near
- * radius (only those carry a correction), and for ndelta = 2 with |gamma| >= 1 % of its value at
- * b = 0 (where gamma vanishes the c2 term does too, and dividing by it only amplifies the
- * sums' rounding).  x0, n0, b from ers_closest_point.
+ * 2: delta_0, delta_1 with the two-delta weights) at M targets and writes the sample records Xs,
+ * Xd (M,48) and targets Ts, Td (M,4) of both networks: the target c in the frame divided by S h^p
+ * (p = 1 single layer, 0 double layer) and a sample weight:
+ *   ndelta = 1: c = u3 - (one-delta value), weight 1;
+ *   ndelta = 2: c = c2 = ((two-delta value) - u3) / gamma, weight (gamma / gamma(0))^2, so that the
+ *     loss measures gamma c2, the error of the two-delta value; 0 where |gamma| < 1 % of
+ *     |gamma(0)| (there the c2 term vanishes and dividing by gamma only amplifies rounding);
+ * weight 0 (and no correction) beyond the reduced near radius or without a density fit.  u3, v3
+ * (M,3) dev are the values of ers_eval (three deltas) at the same targets.  valid (M) ints: 1 for
+ * targets with a positive weight in either layer.  x0, n0, b from ers_closest_point; both
+ * densities must have been set.
  */
 int ers_closure_data(ers_surface *s, const ers_params *p, const double *y, int64_t M, const double *x0,
-                     const double *n0, const double *b, const double *f0, const double *q0, const double *gf0,
-                     const double *gq0, const double *u3, const double *v3, int ndelta, float *Xs, float *Xd,
-                     float *Ts, float *Td, int *valid, void *stream);
+                     const double *n0, const double *b, const double *f0, const double *q0, const double *u3,
+                     const double *v3, int ndelta, float *Xs, float *Xd, float *Ts, float *Td, int *valid,
+                     void *stream);
 
 /*
- * Both layers with the learned closure: far field (precision of p) + two-delta near sums +
- * network correction; targets whose features leave the training extent (ers_closure_range,
- * ers_closure_set_range_check) take the three-delta method instead; then a validation: every
- * vstride-th target is also evaluated with ers_eval (three deltas) and if
- * max|learned - method| / max|method| over that sample exceeds tol for either layer, the whole
- * call falls back to ers_eval (*fell_back = 1).  val_err[2] (host, may be
- * NULL) receives the two measured ratios.  Synchronizes the stream (to read the validation).
- * Errors as ers_eval, plus ERS_E_TIMEOUT when a tensor-core wait expired.
+ * Both layers with the learned closure: far field (precision of p) + one- or two-delta near sums +
+ * the networks' correction; targets whose geometry leaves the training extent (ers_closure_range,
+ * ers_closure_set_range_check) take the three-delta method instead.  Then a validation: every
+ * vstride-th target is also evaluated with ers_eval (three deltas) and, per layer, the error
+ * max|value - method| / max|method| over that sample is measured with and without the network's
+ * correction; a layer keeps the correction only where it lowers that error (else the correction
+ * is taken back), and if the lower of the two errors exceeds tol for either layer, the whole call
+ * falls back to ers_eval (*fell_back = 1).  val_err[2] (host, may be NULL) receives the errors of
+ * the kept values; ers_closure_last_gate reports both errors and the choice.  Synchronizes the
+ * stream (to read the validation).  Errors as ers_eval, plus ERS_E_TIMEOUT when a tensor-core
+ * wait expired and ERS_E_STATE when a density is missing.
  */
 int ers_eval_learned(ers_surface *s, ers_closure *c, const ers_params *p, const double *y, int64_t M,
                      const double *x0, const double *n0, const double *b, const double *f0, const double *q0,
-                     const double *gf0, const double *gq0, int ndelta, double *u, double *v, double tol,
-                     int vstride, double *val_err, int *fell_back, void *stream);
+                     int ndelta, double *u, double *v, double tol, int vstride, double *val_err, int *fell_back,
+                     void *stream);
+
+/* The validation of the last ers_eval_learned call (host arrays of 2, layer 0 single, 1 double;
+ * any may be NULL): used[l] = 1 if layer l kept the network's correction; err_with[l],
+ * err_without[l] = the sample's error with and without it. */
+int ers_closure_last_gate(ers_closure *c, int used[2], double err_with[2], double err_without[2]);
 
 /*
  * ers_eval for callers that cannot allocate device memory while they evaluate (a solver that

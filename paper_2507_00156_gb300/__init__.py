@@ -44,14 +44,17 @@ EXPORTS = ["ers_build_surface", "ers_surface_free", "ers_surface_info", "ers_set
            "ers_batch_free", "ers_closure_create", "ers_closure_free", "ers_closure_params", "ers_closure_infer",
            "ers_closure_infer_reference", "ers_closure_status", "ers_closure_range", "ers_closure_set_range_check",
            "ers_closure_last_out_of_range", "ers_closure_grad", "ers_closure_train",
-           "ers_closure_data", "ers_eval_learned", "ers_eval_noalloc", "ers_treecode_defaults", "ers_tree_stats",
+           "ers_closure_data", "ers_eval_learned", "ers_closure_last_gate", "ers_eval_noalloc", "ers_treecode_defaults", "ers_tree_stats",
            "ers_node_interp", "ers_vec_axpby", "ers_gmres", "ers_last_error", "ers_version"]
 ERS_W_NOT_CONVERGED = 2
 
 # ers_matvec_fn: int (*)(void *ctx, const double *x, double *y, void *stream)
 MATVEC_FN = ctypes.CFUNCTYPE(ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p)
-NPARAM = 10448
-NFEAT = 13  # closure features: lambda_0, kappa_1 h, kappa_2 h, nine scaled density components, rho_0
+NPARAM = 15648
+NFEAT = 5  # closure network inputs (the geometry): lambda_0, kappa_1 h, kappa_2 h, rho_0, rho_1
+XSTR = 48  # floats per closure sample record: geometry (16 slots) then the density jets (32 slots)
+JET_OFF = 16
+NJETS = (18, 27)  # jets of the single and double layer
 NOALLOC_MAX_M = 524288
 
 
@@ -124,9 +127,10 @@ def lib():
             L.ers_closure_last_out_of_range.argtypes = [vp, P(i64)]
             L.ers_closure_grad.argtypes = [vp, cint, vp, vp, i64, vp, P(dbl), vp]
             L.ers_closure_train.argtypes = [vp, cint, vp, vp, i64, cint, cint, ctypes.c_float, P(dbl), vp]
-            L.ers_closure_data.argtypes = [vp, P(_Params), vp, i64] + [vp] * 9 + [cint] + [vp] * 6
-            L.ers_eval_learned.argtypes = [vp, vp, P(_Params), vp, i64] + [vp] * 7 + [cint, vp, vp, dbl, cint, P(dbl),
+            L.ers_closure_data.argtypes = [vp, P(_Params), vp, i64] + [vp] * 7 + [cint] + [vp] * 6
+            L.ers_eval_learned.argtypes = [vp, vp, P(_Params), vp, i64] + [vp] * 5 + [cint, vp, vp, dbl, cint, P(dbl),
                                                                                          P(cint), vp]
+            L.ers_closure_last_gate.argtypes = [vp, P(cint), P(dbl), P(dbl)]
             L.ers_last_counts.argtypes = [vp, P(i64), P(i64), P(i64)]
             L.ers_profile.argtypes = [vp, cint]
             L.ers_last_profile.argtypes = [vp, P(dbl), P(dbl), P(dbl)]
@@ -444,6 +448,8 @@ class Closure:
 
     def infer(self, layer: int, X, reference: bool = False, stream=None):
         import torch
+        if X.dim() != 2 or X.shape[1] != XSTR:
+            raise ValueError(f"closure sample records must be (n, {XSTR})")
         Y = torch.zeros((X.shape[0], 4), dtype=torch.float32, device=X.device)
         fn = lib().ers_closure_infer_reference if reference else lib().ers_closure_infer
         check(fn(self._h, layer, _fptr(X), X.shape[0], _fptr(Y), _stream(stream)))
@@ -455,7 +461,7 @@ class Closure:
         return bool(v.value)
 
     def feature_range(self, layer: int):
-        """(lo, hi) float32 arrays of the 13 features' training extent, or None while unknown."""
+        """(lo, hi) float32 arrays of the training extent of the 5 geometry inputs, or None while unknown."""
         import numpy as np
         out = np.empty(2 * NFEAT, dtype=np.float32)
         have = ctypes.c_int()
@@ -485,6 +491,14 @@ class Closure:
                                      _stream(stream)))
         return G, loss.value
 
+    def last_gate(self):
+        """(used (SL, DL), error with the network (SL, DL), error without it (SL, DL)) of the last
+        eval_learned validation."""
+        used = (ctypes.c_int * 2)()
+        ew, eo = (ctypes.c_double * 2)(), (ctypes.c_double * 2)()
+        check(lib().ers_closure_last_gate(self._h, used, ew, eo))
+        return (bool(used[0]), bool(used[1])), (ew[0], ew[1]), (eo[0], eo[1])
+
     def train(self, layer: int, X, T, steps: int, batch: int = 4096, lr: float = 2e-3, stream=None) -> float:
         loss = ctypes.c_double()
         check(lib().ers_closure_train(self._h, layer, _fptr(X), _fptr(T), X.shape[0], int(steps), int(batch),
@@ -492,25 +506,26 @@ class Closure:
         return loss.value
 
 
-def closure_data(surface, y, x0, n0, b, f0, q0, gf0, gq0, u3, v3, rho=(2.0, 3.0, 4.0), cutoff_t=6.0,
+def closure_data(surface, y, x0, n0, b, f0, q0, u3, v3, rho=(2.0, 3.0, 4.0), cutoff_t=6.0,
                  precision=PREC_MIXED, ndelta=1, stream=None):
-    """ers_closure_data: (Xs, Xd, Ts, Td, valid) CUDA tensors for training the two networks."""
+    """ers_closure_data: (Xs, Xd, Ts, Td, valid) CUDA tensors for training the two networks:
+    sample records (M, 48) and targets (M, 4) = (c in the frame, weight)."""
     import torch
     M = y.shape[0]
     dev = y.device
-    Xs = torch.empty((M, 16), dtype=torch.float32, device=dev)
+    Xs = torch.empty((M, XSTR), dtype=torch.float32, device=dev)
     Xd = torch.empty_like(Xs)
     Ts = torch.empty((M, 4), dtype=torch.float32, device=dev)
     Td = torch.empty_like(Ts)
     valid = torch.empty((M,), dtype=torch.int32, device=dev)
     p = params(rho, cutoff_t, precision)
     check(lib().ers_closure_data(surface.handle, ctypes.byref(p), _ptr(y), M, _ptr(x0), _ptr(n0), _ptr(b), _ptr(f0),
-                                 _ptr(q0), _ptr(gf0), _ptr(gq0), _ptr(u3), _ptr(v3), int(ndelta), _fptr(Xs), _fptr(Xd),
-                                 _fptr(Ts), _fptr(Td), _fptr(valid), _stream(stream)))
+                                 _ptr(q0), _ptr(u3), _ptr(v3), int(ndelta), _fptr(Xs), _fptr(Xd), _fptr(Ts),
+                                 _fptr(Td), _fptr(valid), _stream(stream)))
     return Xs, Xd, Ts, Td, valid
 
 
-def eval_learned(surface, closure, y, x0, n0, b, f0, q0, gf0, gq0, rho=(2.0, 3.0, 4.0), cutoff_t=6.0,
+def eval_learned(surface, closure, y, x0, n0, b, f0, q0, rho=(2.0, 3.0, 4.0), cutoff_t=6.0,
                  precision=PREC_MIXED, tol=1e-5, vstride=32, ndelta=1, u=None, v=None, stream=None):
     """ers_eval_learned: returns (u, v, validation errors (SL, DL), fell_back)."""
     import torch
@@ -523,8 +538,7 @@ def eval_learned(surface, closure, y, x0, n0, b, f0, q0, gf0, gq0, rho=(2.0, 3.0
     ve = (ctypes.c_double * 2)()
     fb = ctypes.c_int()
     check(lib().ers_eval_learned(surface.handle, closure.handle, ctypes.byref(p), _ptr(y), M, _ptr(x0), _ptr(n0),
-                                 _ptr(b), _ptr(f0), _ptr(q0), _ptr(gf0), _ptr(gq0), int(ndelta), _ptr(u), _ptr(v),
-                                 float(tol),
+                                 _ptr(b), _ptr(f0), _ptr(q0), int(ndelta), _ptr(u), _ptr(v), float(tol),
                                  int(vstride), ve, ctypes.byref(fb), _stream(stream)))
     return u, v, (ve[0], ve[1]), bool(fb.value)
 

@@ -1,20 +1,33 @@
 // The learned closure of the near field: one or two regularized sums instead of three, and what
-// they miss of the extrapolated value predicted by a small network.
-//
-// ndelta = 1 (the single sum u^{delta_0}, near set r <= cutoff_t delta_0): the network predicts
-// the whole correction u - u^{delta_0} = -(c1 rho_0 I0 + c2 rho_0^3 I2) + O(delta^5).
-// ndelta = 2 (the two smaller deltas):
+// they miss of the extrapolated value predicted from local data by a small network.
 //
 // Eq. (extrap_eqn) says u^{delta_k} = u + c1 rho_k I0(lambda_k) + c2 rho_k^3 I2(lambda_k) + O(delta^5)
-// with c1, c2 independent of delta.  With the two-delta weights beta (sum beta = 1,
-// sum beta rho I0 = 0) the two sums give u + gamma c2 with gamma = sum beta rho^3 I2, so
-//   u = sum_k beta_k u^{delta_k} - gamma c2.
-// The network predicts c2 (in the local frame at x0, divided by h^3 and by a density scale) from
-// local features: lambda_0, the principal curvatures, the density and its tangential derivatives
-// at x0, and rho_0.  The near set shrinks from r <= 6 delta_2 to r <= 6 delta_1 and each pair
-// needs at most two smoothing-function evaluations.  A validation sample of targets is also
-// evaluated with the three-delta method; if the learned values differ from it by more than a
-// tolerance, the whole evaluation falls back to the three-delta method.
+// with c1, c2 independent of delta.
+//   ndelta = 1 (the single sum u^{delta_0}, near set r <= cutoff_t delta_0): the closure predicts
+//     the whole correction u - u^{delta_0}.
+//   ndelta = 2 (two deltas, near set r <= cutoff_t delta_1): with the weights beta (sum beta = 1,
+//     sum beta rho I0 = 0) the two sums give u + gamma c2, gamma = sum beta rho^3 I2, so
+//     u = sum_k beta_k u^{delta_k} - gamma c2, and the closure predicts c2.
+// c1 and c2 are fixed by the surface and the density near the closest point x0 and are linear in
+// the density.  The single-layer kernel is O(1/r) and its delta^3 term involves the density up to
+// second derivatives; the double-layer kernel is O(1/r^2) and involves one derivative more.  So
+// the closure is a linear map from the density jets at x0 to the correction whose coefficients
+// the network predicts from the local geometry:
+//   frame    t1, t2, n0: the principal directions at x0 (where the principal curvatures agree to
+//            1e-6, a fixed tangent basis built from n0);
+//   geometry lambda_0 = b / delta_0, kappa_1 h, kappa_2 h (principal curvatures, kappa_1 >= kappa_2),
+//            rho_0, rho_1;
+//   jets     derivatives of the density components along t1, t2, n0 with respect to the
+//            tangent-plane coordinates (xi, eta) = ((x - x0).t1, (x - x0).t2) / h, from the
+//            least-squares polynomial of total degree <= 4 fitted to the node values within 3.5 h
+//            of x0: single layer orders 0..2 (18 values), double layer orders 1..3 (27 values),
+//            divided by their largest magnitude S;
+//   output   c (3 components in the frame) = sum_j A_ej(geometry) jet_j, the correction divided by
+//            S h^p (p = 1 single layer, p = 0 double layer; for ndelta = 2 also by -gamma).
+// A validation sample of targets is also evaluated with the three-delta method: per layer the
+// network's correction is kept only if it brings the sample closer to the method than the sums
+// without it, and if either layer still differs by more than a tolerance the whole evaluation
+// falls back to the three-delta method.
 #include <algorithm>
 #include <cmath>
 #include <cstring>
@@ -35,11 +48,15 @@ struct ers_closure {
     float *m[2] = {nullptr, nullptr}, *v[2] = {nullptr, nullptr};  // Adam moments
     int step[2] = {0, 0};
     int *err = nullptr;
-    // extent of the training features: [layer][0 lo, 1 hi][feature] as order-preserving int keys
+    // extent of the training geometry: [layer][0 lo, 1 hi][feature] as order-preserving int keys
     int *range = nullptr;
     int have_range[2] = {0, 0};
     int range_check = 1;     // ers_eval_learned sends targets outside the extent to the method
     int64_t last_out = 0;    // targets of the last ers_eval_learned that were outside it
+    // per layer, from the validation of the last ers_eval_learned: network kept (1) or not (0),
+    // the sample's error with and without the network's correction
+    int last_used[2] = {0, 0};
+    double last_err_with[2] = {0.0, 0.0}, last_err_without[2] = {0.0, 0.0};
     Scratch z, a, d4, d, g, idx, loss;
     // evaluation work buffers
     Scratch feat, scale, gamma, outp, sub, valid, oor;
@@ -49,12 +66,18 @@ namespace ers {
 namespace {
 
 using namespace mlp;
-constexpr int NFEAT = 13;
+constexpr int NFEAT = NGEOM;      // features checked against the training extent (the geometry)
+constexpr int NB = 15;            // monomials of total degree <= 4 in two variables
+constexpr int NPK = NB * (NB + 1) / 2;
+constexpr int NRHS = 6;           // f and q, three components each, in the frame
+constexpr double FIT_R = 3.5;     // fit radius in units of h
+constexpr int FEAT_THREADS = 64;  // threads per block of the features kernel
+constexpr size_t FEAT_SMEM = sizeof(double) * (NPK + NB * NRHS) * FEAT_THREADS;
 
-__device__ __forceinline__ void local_frame(const double n[3], double t1[3], double t2[3]) {
-    const double a0 = fabs(n[0]) < 0.9 ? 1.0 : 0.0, a1 = 1.0 - a0;  // e_x, or e_y when n is close to e_x
-    // t1 = n x a, normalised; t2 = n x t1
-    double c0 = n[1] * 0.0 - n[2] * a1, c1 = n[2] * a0 - n[0] * 0.0, c2 = n[0] * a1 - n[1] * a0;
+// t1 = n x a / |n x a| with a = e_x (e_y when |n_x| >= 0.9), t2 = n x t1.
+__host__ __device__ __forceinline__ void fallback_frame(const double n[3], double t1[3], double t2[3]) {
+    const double a0 = fabs(n[0]) < 0.9 ? 1.0 : 0.0, a1 = 1.0 - a0;
+    const double c0 = -n[2] * a1, c1 = n[2] * a0, c2 = n[0] * a1 - n[1] * a0;
     const double inv = 1.0 / sqrt(c0 * c0 + c1 * c1 + c2 * c2);
     t1[0] = c0 * inv;
     t1[1] = c1 * inv;
@@ -64,125 +87,300 @@ __device__ __forceinline__ void local_frame(const double n[3], double t1[3], dou
     t2[2] = n[0] * t1[1] - n[1] * t1[0];
 }
 
-// Principal curvatures of the ellipsoid at x0 (p = x0 - c): with g = p / a^2,
-// K = 1 / (a^2 b^2 c^2 |g|^4) and the mean curvature H = (a^2 + b^2 + c^2 - |p|^2) / (2 a^2 b^2 c^2 |g|^3).
-__device__ __forceinline__ void curvatures(const double p[3], const double a[3], double &k1, double &k2) {
-    double g2 = 0.0, p2 = 0.0, s2 = 0.0, abc2 = 1.0;
+// Principal frame and curvatures of the ellipsoid sum((x - c)/a)^2 = 1 at x0 (p = x0 - c, unit
+// normal n): the shape operator on the tangent plane is (Hess F)/|grad F| restricted to it, with
+// F the implicit function (Hess F = diag(2/a^2), grad F = 2 p/a^2); in the basis (e1, e2) of
+// fallback_frame it is the symmetric 2 x 2 matrix S below.  k1 >= k2 are its eigenvalues; t1 is
+// the eigenvector of k1 signed so that its e1 component is >= 0 (its e2 component > 0 when that
+// is 0), t2 = n x t1.  Where the eigenvalues agree to 1e-6 of |S00| + |S11| (every point of a
+// sphere) the frame is (e1, e2, n).
+__device__ __forceinline__ void principal_frame(const double p[3], const double a[3], const double n[3],
+                                                double t1[3], double t2[3], double &k1, double &k2) {
+    double e1[3], e2[3];
+    fallback_frame(n, e1, e2);
+    double g2 = 0.0, hd[3];
     for (int i = 0; i < 3; ++i) {
-        const double a2 = a[i] * a[i];
-        const double gi = p[i] / a2;
+        const double ia2 = 1.0 / (a[i] * a[i]);
+        const double gi = 2.0 * p[i] * ia2;
         g2 += gi * gi;
-        p2 += p[i] * p[i];
-        s2 += a2;
-        abc2 *= a2;
+        hd[i] = 2.0 * ia2;
     }
-    const double gn = sqrt(g2);
-    const double K = 1.0 / (abc2 * g2 * g2);
-    const double H = (s2 - p2) / (2.0 * abc2 * g2 * gn);
-    const double disc = sqrt(fmax(H * H - K, 0.0));
-    k1 = H + disc;
-    k2 = H - disc;
+    const double ig = 1.0 / sqrt(g2);
+    double S00 = 0.0, S01 = 0.0, S11 = 0.0;
+    for (int i = 0; i < 3; ++i) {
+        S00 += hd[i] * e1[i] * e1[i];
+        S01 += hd[i] * e1[i] * e2[i];
+        S11 += hd[i] * e2[i] * e2[i];
+    }
+    S00 *= ig;
+    S01 *= ig;
+    S11 *= ig;
+    const double mid = 0.5 * (S00 + S11), r = hypot(0.5 * (S00 - S11), S01);
+    k1 = mid + r;
+    k2 = mid - r;
+    if (2.0 * r <= 1e-6 * (fabs(S00) + fabs(S11))) {
+        for (int i = 0; i < 3; ++i) {
+            t1[i] = e1[i];
+            t2[i] = e2[i];
+        }
+        return;
+    }
+    // (S - k1 I) v = 0: v = (k1 - S11, S01) or (S01, k1 - S00), the larger one
+    double v0 = k1 - S11, v1 = S01;
+    const double w0 = S01, w1 = k1 - S00;
+    if (w0 * w0 + w1 * w1 > v0 * v0 + v1 * v1) {
+        v0 = w0;
+        v1 = w1;
+    }
+    if (v0 < 0.0 || (v0 == 0.0 && v1 < 0.0)) {
+        v0 = -v0;
+        v1 = -v1;
+    }
+    double tn = 0.0;
+    for (int i = 0; i < 3; ++i) {
+        t1[i] = v0 * e1[i] + v1 * e2[i];
+        tn += t1[i] * t1[i];
+    }
+    tn = 1.0 / sqrt(tn);
+    for (int i = 0; i < 3; ++i) t1[i] *= tn;
+    t2[0] = n[1] * t1[2] - n[2] * t1[1];
+    t2[1] = n[2] * t1[0] - n[0] * t1[2];
+    t2[2] = n[0] * t1[1] - n[1] * t1[0];
+}
+
+// Frame of target m from its closest point (shared by the features, the correction and the
+// validation, so that all three use the same frame).
+__device__ __forceinline__ void target_frame(const double *x0, const double *n0, int64_t m, const double c[3],
+                                             const double a[3], double t1[3], double t2[3], double n[3], double &k1,
+                                             double &k2) {
+    double p[3];
+    for (int i = 0; i < 3; ++i) {
+        n[i] = n0[3 * m + i];
+        p[i] = x0[3 * m + i] - c[i];
+    }
+    principal_frame(p, a, n, t1, t2, k1, k2);
+}
+
+// monomials xi^i eta^j of total degree <= 4, ordered by degree, then by falling i
+__device__ __forceinline__ void monomials4(double xi, double eta, double *phi) {
+    double xp[5], ep[5];
+    xp[0] = ep[0] = 1.0;
+    for (int i = 1; i < 5; ++i) {
+        xp[i] = xp[i - 1] * xi;
+        ep[i] = ep[i - 1] * eta;
+    }
+    int k = 0;
+#pragma unroll
+    for (int d = 0; d <= 4; ++d)
+#pragma unroll
+        for (int j = 0; j <= d; ++j) phi[k++] = xp[d - j] * ep[j];
+}
+
+// i! j! / 3.5^(i + j) of monomial k (degrees <= 3): the derivative d^(i+j)/dxi^i deta^j in units
+// of h of the fit in the scaled coordinates (xi, eta) / 3.5.
+__device__ __forceinline__ double deriv_factor(int k) {
+    constexpr double r = 1.0 / FIT_R;
+    switch (k) {
+        case 0: return 1.0;
+        case 1: case 2: return r;
+        case 3: case 5: return 2.0 * r * r;
+        case 4: return r * r;
+        case 6: case 9: return 6.0 * r * r * r;
+        default: return 2.0 * r * r * r;  // 7, 8: (2,1), (1,2)
+    }
+}
+
+// Degree-4 least-squares fit of the node densities (f, q along t1, t2, n) within FIT_R h of x0:
+// normal equations (Phi^T Phi) c = Phi^T U accumulated in this thread's column of shared memory
+// (stride FEAT_THREADS), Cholesky, then the coefficients of the monomials of degree <= 3 as
+// derivatives in units of h: out[k][r], k = 0..9, r = 0..5 (f t1, f t2, f n, q t1, q t2, q n).
+// Returns false with fewer than 15 nodes or a pivot <= 0.
+__device__ bool fit_jets(const SurfDev &sd, const double *__restrict__ fq, const double x0[3], const double t1[3],
+                         const double t2[3], const double n[3], double h, double *A, double *B, double out[10][NRHS]) {
+    const int S = FEAT_THREADS;
+    for (int k = 0; k < NPK; ++k) A[k * S] = 0.0;
+    for (int k = 0; k < NB * NRHS; ++k) B[k * S] = 0.0;
+    const double R = FIT_R * h, R2 = R * R, iR = 1.0 / R;
+    const Grid &G = sd.grid;
+    int lo[3], hi[3];
+    for (int a = 0; a < 3; ++a) {
+        lo[a] = max(0, (int)floor((x0[a] - R - G.origin[a]) / G.cw));
+        hi[a] = min(G.nc[a] - 1, (int)floor((x0[a] + R - G.origin[a]) / G.cw));
+    }
+    int cnt = 0;
+    for (int iz = lo[2]; iz <= hi[2]; ++iz)
+        for (int iy = lo[1]; iy <= hi[1]; ++iy) {
+            const int64_t row = ((int64_t)iz * G.nc[1] + iy) * G.nc[0];
+            const int js = sd.cell_start[row + lo[0]], je = sd.cell_start[row + hi[0] + 1];
+            for (int j = js; j < je; ++j) {
+                const double *r = sd.rec + (int64_t)j * REC;
+                const double d[3] = {r[0] - x0[0], r[1] - x0[1], r[2] - x0[2]};
+                if (!(d[0] * d[0] + d[1] * d[1] + d[2] * d[2] <= R2)) continue;
+                ++cnt;
+                double phi[NB];
+                monomials4((d[0] * t1[0] + d[1] * t1[1] + d[2] * t1[2]) * iR,
+                           (d[0] * t2[0] + d[1] * t2[1] + d[2] * t2[2]) * iR, phi);
+                const double *u = fq + (int64_t)j * 6;
+                double uf[NRHS];
+                for (int c = 0; c < 2; ++c) {
+                    const double *v = u + 3 * c;
+                    uf[3 * c + 0] = v[0] * t1[0] + v[1] * t1[1] + v[2] * t1[2];
+                    uf[3 * c + 1] = v[0] * t2[0] + v[1] * t2[1] + v[2] * t2[2];
+                    uf[3 * c + 2] = v[0] * n[0] + v[1] * n[1] + v[2] * n[2];
+                }
+#pragma unroll
+                for (int i = 0; i < NB; ++i) {
+#pragma unroll
+                    for (int q = 0; q <= i; ++q) A[(i * (i + 1) / 2 + q) * S] = fma(phi[i], phi[q], A[(i * (i + 1) / 2 + q) * S]);
+#pragma unroll
+                    for (int c = 0; c < NRHS; ++c) B[(i * NRHS + c) * S] = fma(phi[i], uf[c], B[(i * NRHS + c) * S]);
+                }
+            }
+        }
+    if (cnt < NB) return false;
+    // Cholesky A = L L^T in place (packed rows)
+    for (int i = 0; i < NB; ++i)
+        for (int j = 0; j <= i; ++j) {
+            double s = A[(i * (i + 1) / 2 + j) * S];
+            for (int q = 0; q < j; ++q) s -= A[(i * (i + 1) / 2 + q) * S] * A[(j * (j + 1) / 2 + q) * S];
+            if (i == j) {
+                if (!(s > 0.0)) return false;
+                A[(i * (i + 1) / 2 + i) * S] = sqrt(s);
+            } else {
+                A[(i * (i + 1) / 2 + j) * S] = s / A[(j * (j + 1) / 2 + j) * S];
+            }
+        }
+    for (int c = 0; c < NRHS; ++c) {
+        double y[NB];
+        for (int i = 0; i < NB; ++i) {  // L y = B_c
+            double s = B[(i * NRHS + c) * S];
+            for (int q = 0; q < i; ++q) s -= A[(i * (i + 1) / 2 + q) * S] * y[q];
+            y[i] = s / A[(i * (i + 1) / 2 + i) * S];
+        }
+        for (int i = NB - 1; i >= 0; --i) {  // L^T x = y
+            double s = y[i];
+            for (int q = i + 1; q < NB; ++q) s -= A[(q * (q + 1) / 2 + i) * S] * y[q];
+            y[i] = s / A[(i * (i + 1) / 2 + i) * S];
+        }
+        for (int k = 0; k < 10; ++k) out[k][c] = y[k] * deriv_factor(k);
+    }
+    return true;
 }
 
 struct FeatArgs {
-    const double *y, *x0, *n0, *b, *f0, *q0, *gf0, *gq0;
+    SurfDev sd;
+    const double *fq;
+    const double *x0, *n0, *b;
     const double *u2, *v2, *gamma, *u3, *v3;  // u3, v3 optional (training targets)
     int64_t M;
-    double h, rho0, Rc;
-    int nd;  // 1: target c = (u3 - u1) / (h S); 2: target c2 = (u2 - u3) / (gamma h^3 S)
-    double gamma_min;  // nd = 2: samples need |gamma| >= gamma_min
+    double h, rho0, rho1, Rc;
+    int nd;            // 1 or 2 deltas
+    double gamma0;     // |gamma| at b = 0 (nd = 2)
     double c[3], a[3];
-    float *Xs, *Xd, *Ts, *Td;  // features (M x 16) and targets (M x 4)
+    float *Xs, *Xd, *Ts, *Td;  // sample records (M x XSTR) and targets (M x TSTR) of both layers
     double *scale;             // (M x 2) density scales, 0 = no correction
     int *valid;
 };
 
-// One thread per target: features of both layers; targets when u3, v3 are given.
-__global__ void k_features(FeatArgs A) {
+// One thread per target: frame, geometry, density jets (both layers), training targets when
+// u3, v3 are given.
+__global__ void __launch_bounds__(FEAT_THREADS) k_features(FeatArgs A) {
+    extern __shared__ double fsm[];
     const int64_t m = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (m >= A.M) return;
-    const bool near = fabs(A.b[m]) <= A.Rc;
-    double n[3], t1[3], t2[3], p[3];
-    for (int i = 0; i < 3; ++i) {
-        n[i] = A.n0[3 * m + i];
-        p[i] = A.x0[3 * m + i] - A.c[i];
+    double t1[3], t2[3], n[3], k1, k2;
+    target_frame(A.x0, A.n0, m, A.c, A.a, t1, t2, n, k1, k2);
+    const double bm = A.b[m];
+    const double lam = bm / (A.rho0 * A.h);
+    bool ok = fabs(bm) <= A.Rc && fabs(lam) <= 64.0;
+    double J[10][NRHS];
+    if (ok) {
+        const double x0[3] = {A.x0[3 * m], A.x0[3 * m + 1], A.x0[3 * m + 2]};
+        ok = fit_jets(A.sd, A.fq, x0, t1, t2, n, A.h, fsm + threadIdx.x, fsm + NPK * FEAT_THREADS + threadIdx.x, J);
     }
-    local_frame(n, t1, t2);
-    double k1, k2;
-    curvatures(p, A.a, k1, k2);
-    const double lam = A.b[m] / (A.rho0 * A.h);
+    bool any = false;
     for (int layer = 0; layer < 2; ++layer) {
-        const double *d0 = (layer == 0 ? A.f0 : A.q0) + 3 * m;
-        const double *J = (layer == 0 ? A.gf0 : A.gq0) + 9 * m;  // J[i][j] = d f_i / d x_j
-        double loc[12];
-        // density value in the local frame
-        for (int e = 0; e < 3; ++e) {
-            const double *ax = e == 0 ? t1 : (e == 1 ? t2 : n);
-            loc[e] = d0[0] * ax[0] + d0[1] * ax[1] + d0[2] * ax[2];
-        }
-        // tangential derivatives along t1, t2, in the local frame, times h
-        for (int dir = 0; dir < 2; ++dir) {
-            const double *t = dir == 0 ? t1 : t2;
-            double dv[3];
-            for (int i = 0; i < 3; ++i) dv[i] = J[3 * i] * t[0] + J[3 * i + 1] * t[1] + J[3 * i + 2] * t[2];
-            for (int e = 0; e < 3; ++e) {
-                const double *ax = e == 0 ? t1 : (e == 1 ? t2 : n);
-                loc[3 + 3 * dir + e] = (dv[0] * ax[0] + dv[1] * ax[1] + dv[2] * ax[2]) * A.h;
-            }
-        }
-        double S = 0.0;
-        for (int e = 0; e < 9; ++e) S = fmax(S, fabs(loc[e]));
-        const bool ok = near && S > 0.0 && isfinite(S) && fabs(lam) <= 64.0;
-        float *X = (layer == 0 ? A.Xs : A.Xd) + m * IN;
+        const int nj = jets_of_layer(layer);
+        float *X = (layer == 0 ? A.Xs : A.Xd) + m * XSTR;
         X[0] = (float)lam;
         X[1] = (float)(k1 * A.h);
         X[2] = (float)(k2 * A.h);
-        for (int e = 0; e < 9; ++e) X[3 + e] = ok ? (float)(loc[e] / S) : 0.0f;
-        X[12] = (float)A.rho0;
-        for (int e = NFEAT; e < IN; ++e) X[e] = 0.0f;
-        A.scale[2 * m + layer] = ok ? S : 0.0;
+        X[3] = (float)A.rho0;
+        X[4] = (float)A.rho1;
+        for (int e = NGEOM; e < JET_OFF; ++e) X[e] = 0.0f;
+        // jets, component-major: single layer orders 0..2 (monomials 0..5), double layer 1..3 (1..9)
+        double jl[NJ_DL];
+        const int k0 = layer == 0 ? 0 : 1, nk = layer == 0 ? 6 : 9;
+        double S = 0.0;
+        for (int e = 0; e < 3; ++e)
+            for (int k = 0; k < nk; ++k) {
+                const double v = ok ? J[k0 + k][3 * layer + e] : 0.0;
+                jl[e * nk + k] = v;
+                S = fmax(S, fabs(v));
+            }
+        const bool lok = ok && S > 0.0 && isfinite(S);
+        for (int j = 0; j < NJ_MAX; ++j) X[JET_OFF + j] = (lok && j < nj) ? (float)(jl[j] / S) : 0.0f;
+        A.scale[2 * m + layer] = lok ? S : 0.0;
         float *T = layer == 0 ? A.Ts : A.Td;
         const double *u3 = layer == 0 ? A.u3 : A.v3;
         if (T && u3) {
-            const double *u2 = (layer == 0 ? A.u2 : A.v2) + 3 * m;
+            const double *ur = (layer == 0 ? A.u2 : A.v2) + 3 * m;
             const double g = A.gamma[m];
-            double c2[3];
-            double den;
-            if (A.nd == 2) {
-                for (int i = 0; i < 3; ++i) c2[i] = (ok && fabs(g) >= A.gamma_min) ? (u2[i] - u3[3 * m + i]) / g : 0.0;
-                den = A.h * A.h * A.h * S;
-            } else {
-                for (int i = 0; i < 3; ++i) c2[i] = ok ? (u3[3 * m + i] - u2[i]) : 0.0;
-                den = A.h * S;
+            const double hp = layer == 0 ? A.h : 1.0;
+            double cv[3] = {0.0, 0.0, 0.0}, w = 0.0;
+            if (lok && A.nd == 2 && fabs(g) >= 0.01 * A.gamma0) {
+                for (int i = 0; i < 3; ++i) cv[i] = (ur[i] - u3[3 * m + i]) / g;
+                w = (g / A.gamma0) * (g / A.gamma0);
+            } else if (lok && A.nd == 1) {
+                for (int i = 0; i < 3; ++i) cv[i] = u3[3 * m + i] - ur[i];
+                w = 1.0;
             }
-            for (int e = 0; e < 3; ++e) {
-                const double *ax = e == 0 ? t1 : (e == 1 ? t2 : n);
-                T[m * OUT_STRIDE + e] = ok ? (float)((c2[0] * ax[0] + c2[1] * ax[1] + c2[2] * ax[2]) / den) : 0.0f;
-            }
-            T[m * OUT_STRIDE + 3] = 0.0f;
+            const double den = w > 0.0 ? S * hp : 1.0;
+            T[m * TSTR + 0] = (float)((cv[0] * t1[0] + cv[1] * t1[1] + cv[2] * t1[2]) / den);
+            T[m * TSTR + 1] = (float)((cv[0] * t2[0] + cv[1] * t2[1] + cv[2] * t2[2]) / den);
+            T[m * TSTR + 2] = (float)((cv[0] * n[0] + cv[1] * n[1] + cv[2] * n[2]) / den);
+            T[m * TSTR + 3] = (float)w;
+            any = any || w > 0.0;
         }
     }
-    A.valid[m] = (near && (A.nd == 1 || fabs(A.gamma[m]) >= A.gamma_min)) ? 1 : 0;
+    if (A.valid) A.valid[m] = any ? 1 : 0;
 }
 
-// nd = 2: u = u2 - gamma h^3 S (R c2_local); nd = 1: u = u1 + h S (R c_local); R = [t1 t2 n0].
-// Only targets with a density scale S > 0 are corrected.
-__global__ void k_apply(const double *__restrict__ n0, const double *__restrict__ gamma,
-                        const double *__restrict__ scale, const float *__restrict__ Ys, const float *__restrict__ Yd,
-                        int64_t M, double h, int nd, double *__restrict__ u, double *__restrict__ v) {
+// The network's correction of layer l where mask bit l is set and the density scale S > 0, added
+// with sign `sign` (1 to apply it, -1 to take it back): ndelta = 2: u -= gamma S h^p (R c);
+// ndelta = 1: u += S h^p (R c); R = [t1 t2 n0], p = 1 single layer, 0 double layer.
+struct ApplyArgs {
+    const double *x0, *n0, *gamma, *scale;
+    const float *Ys, *Yd;
+    int64_t M;
+    double h;
+    int nd, mask;
+    double sign;
+    double c[3], a[3];
+    double *u, *v;
+};
+
+__device__ __forceinline__ void correction(const ApplyArgs &A, int64_t m, int layer, const double t1[3],
+                                           const double t2[3], const double n[3], double corr[3]) {
+    const double S = A.scale[2 * m + layer];
+    const float *Y = (layer == 0 ? A.Ys : A.Yd) + m * OUT_STRIDE;
+    const double hp = layer == 0 ? A.h : 1.0;
+    const double f = A.nd == 2 ? -A.gamma[m] * S * hp : S * hp;
+    for (int i = 0; i < 3; ++i) corr[i] = f * ((double)Y[0] * t1[i] + (double)Y[1] * t2[i] + (double)Y[2] * n[i]);
+}
+
+__global__ void k_apply(ApplyArgs A) {
     const int64_t m = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (m >= M) return;
-    double n[3], t1[3], t2[3];
-    for (int i = 0; i < 3; ++i) n[i] = n0[3 * m + i];
-    local_frame(n, t1, t2);
-    const double h3 = h * h * h;
+    if (m >= A.M) return;
+    if (!(A.scale[2 * m] > 0.0 || A.scale[2 * m + 1] > 0.0)) return;
+    double t1[3], t2[3], n[3], k1, k2;
+    target_frame(A.x0, A.n0, m, A.c, A.a, t1, t2, n, k1, k2);
     for (int layer = 0; layer < 2; ++layer) {
-        const double S = scale[2 * m + layer];
-        double *out = layer == 0 ? u : v;
-        if (!out || S == 0.0) continue;
-        const float *Y = (layer == 0 ? Ys : Yd) + m * OUT_STRIDE;
-        const double f = nd == 2 ? gamma[m] * h3 * S : -h * S;
-        for (int i = 0; i < 3; ++i) out[3 * m + i] -= f * (Y[0] * t1[i] + Y[1] * t2[i] + Y[2] * n[i]);
+        double *out = layer == 0 ? A.u : A.v;
+        if (!(A.mask & (1 << layer)) || !out || !(A.scale[2 * m + layer] > 0.0)) continue;
+        double corr[3];
+        correction(A, m, layer, t1, t2, n, corr);
+        for (int i = 0; i < 3; ++i) out[3 * m + i] += A.sign * corr[i];
     }
 }
 
@@ -204,24 +402,31 @@ __global__ void k_gather(const double *__restrict__ y, const double *__restrict_
     o[9 * Ms + k] = b[m];
 }
 
-// max |learned - plain| and max |plain| over the validation sample, per layer (4 doubles).
-__global__ void k_compare(const double *__restrict__ u, const double *__restrict__ v, const double *__restrict__ up,
-                          const double *__restrict__ vp, int64_t Ms, int stride, double *__restrict__ res) {
-    double e[4] = {0, 0, 0, 0};
+// Over the validation sample (every stride-th target m = k stride, method values up, vp):
+// res[0] = max |u - up|, res[1] = max |up|, res[2] = max |v - vp|, res[3] = max |vp|, and
+// res[4], res[5] = max |u - corr - up|, max |v - corr - vp|: the same without the network's
+// correction (A carries the correction's inputs; A.sign is ignored).
+__global__ void k_compare(ApplyArgs A, const double *__restrict__ up, const double *__restrict__ vp, int64_t Ms,
+                          int stride, double *__restrict__ res) {
+    double e[6] = {0, 0, 0, 0, 0, 0};
     for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < Ms; k += (int64_t)gridDim.x * blockDim.x) {
         const int64_t m = k * stride;
-        for (int i = 0; i < 3; ++i) {
-            if (u) {
-                e[0] = fmax(e[0], fabs(u[3 * m + i] - up[3 * k + i]));
-                e[1] = fmax(e[1], fabs(up[3 * k + i]));
-            }
-            if (v) {
-                e[2] = fmax(e[2], fabs(v[3 * m + i] - vp[3 * k + i]));
-                e[3] = fmax(e[3], fabs(vp[3 * k + i]));
+        double t1[3], t2[3], n[3], k1, k2;
+        target_frame(A.x0, A.n0, m, A.c, A.a, t1, t2, n, k1, k2);
+        for (int layer = 0; layer < 2; ++layer) {
+            const double *out = layer == 0 ? A.u : A.v;
+            const double *ref = layer == 0 ? up : vp;
+            double corr[3] = {0.0, 0.0, 0.0};
+            if (A.scale[2 * m + layer] > 0.0) correction(A, m, layer, t1, t2, n, corr);
+            for (int i = 0; i < 3; ++i) {
+                const double o = out[3 * m + i], r = ref[3 * k + i];
+                e[2 * layer] = fmax(e[2 * layer], fabs(o - r));
+                e[2 * layer + 1] = fmax(e[2 * layer + 1], fabs(r));
+                e[4 + layer] = fmax(e[4 + layer], fabs(o - corr[i] - r));
             }
         }
     }
-    for (int j = 0; j < 4; ++j) {
+    for (int j = 0; j < 6; ++j) {
         double x = e[j];
         for (int o = 16; o > 0; o >>= 1) x = fmax(x, __shfl_xor_sync(0xffffffffu, x, o));
         if ((threadIdx.x & 31) == 0)
@@ -246,7 +451,7 @@ __host__ __device__ __forceinline__ int range_key(int bits) { return bits >= 0 ?
 constexpr int RANGE_STRIDE = 2 * IN;  // ints per layer: lo[IN], hi[IN]
 
 // Widen the extent keys[0..NFEAT) (lo), keys[IN..IN+NFEAT) (hi) to cover the finite features of
-// samples X (n, IN).
+// the sample records X (n, XSTR).
 __global__ void k_range_update(const float *__restrict__ X, int64_t n, int *__restrict__ keys) {
     int lo[NFEAT], hi[NFEAT];
 #pragma unroll
@@ -257,7 +462,7 @@ __global__ void k_range_update(const float *__restrict__ X, int64_t n, int *__re
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
 #pragma unroll
         for (int f = 0; f < NFEAT; ++f) {
-            const float x = X[i * IN + f];
+            const float x = X[i * XSTR + f];
             if (!isfinite(x)) continue;
             const int k = range_key(__float_as_int(x));
             lo[f] = min(lo[f], k);
@@ -285,7 +490,7 @@ __global__ void k_range_flags(const float *__restrict__ Xs, const float *__restr
     bool out = false;
     for (int layer = 0; layer < 2; ++layer) {
         if (!(layer == 0 ? have0 : have1) || !(scale[2 * m + layer] > 0.0)) continue;
-        const float *X = (layer == 0 ? Xs : Xd) + m * IN;
+        const float *X = (layer == 0 ? Xs : Xd) + m * XSTR;
         const int *K = keys + layer * RANGE_STRIDE;
         for (int f = 0; f < NFEAT; ++f) {
             const float lo = __int_as_float(range_key(K[f])), hi = __int_as_float(range_key(K[IN + f]));
@@ -319,9 +524,10 @@ __global__ void k_gather_idx(const double *__restrict__ y, const double *__restr
     out[9 * K + k] = b[m];
 }
 
+// ... and scatter the method's values back; those targets carry no correction any more (scale 0).
 __global__ void k_scatter_idx(const double *__restrict__ up, const double *__restrict__ vp,
                               const int64_t *__restrict__ idx, int64_t K, double *__restrict__ u,
-                              double *__restrict__ v) {
+                              double *__restrict__ v, double *__restrict__ scale) {
     const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= K) return;
     const int64_t m = idx[k];
@@ -329,6 +535,8 @@ __global__ void k_scatter_idx(const double *__restrict__ up, const double *__res
         u[3 * m + i] = up[3 * k + i];
         v[3 * m + i] = vp[3 * k + i];
     }
+    scale[2 * m] = 0.0;
+    scale[2 * m + 1] = 0.0;
 }
 
 int closure_check(const ers_closure *c, int layer) {
@@ -363,7 +571,7 @@ int infer(ers_closure *c, int layer, const float *X, int64_t n, float *Y, cudaSt
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, c->device);
     const int64_t tiles = (n + 127) / 128;
     const int grid = (int)std::min<int64_t>(tiles, (int64_t)nsm * 4);
-    cudaError_t e = launch_infer_tc(c->p[layer], X, n, Y, c->err, grid, st);
+    cudaError_t e = launch_infer_tc(c->p[layer], X, n, Y, jets_of_layer(layer), c->err, grid, st);
     if (e != cudaSuccess) return cuda_fail(e, "closure inference kernel");
     return ERS_OK;
 }
@@ -395,7 +603,8 @@ int ers_closure_create(uint64_t seed, ers_closure **out) {
         free_closure(c);
         return fail(ERS_E_NOMEM, "ers_closure_create: device allocation failed");
     }
-    // He-uniform initial weights from a seeded generator, zero biases; unused output rows zero
+    // He-uniform hidden weights from a seeded generator, zero biases, and a zero last layer: an
+    // untrained network predicts no correction
     std::mt19937_64 rng(seed);
     for (int l = 0; l < 2; ++l) {
         std::vector<float> h(mlp::NPARAM, 0.0f);
@@ -408,7 +617,7 @@ int ers_closure_create(uint64_t seed, ers_closure **out) {
         fill(mlp::OFF_W1, mlp::HID, mlp::IN, mlp::HID);
         fill(mlp::OFF_W2, mlp::HID, mlp::HID, mlp::HID);
         fill(mlp::OFF_W3, mlp::HID, mlp::HID, mlp::HID);
-        fill(mlp::OFF_W4, mlp::OUT, mlp::HID, mlp::OUT_USED);
+        fill(mlp::OFF_W4, mlp::OUT, mlp::HID, 0);
         e = cudaMemcpy(c->p[l], h.data(), sizeof(float) * mlp::NPARAM, cudaMemcpyHostToDevice);
         if (e == cudaSuccess) e = cudaMemset(c->m[l], 0, sizeof(float) * mlp::NPARAM);
         if (e == cudaSuccess) e = cudaMemset(c->v[l], 0, sizeof(float) * mlp::NPARAM);
@@ -464,7 +673,7 @@ int ers_closure_infer_reference(ers_closure *c, int layer, const float *X, int64
     if (rc != ERS_OK) return rc;
     cudaStream_t st = (cudaStream_t)stream;
     cudaError_t e = mlp::launch_quantize(c->p[layer], c->q[layer], st);
-    if (e == cudaSuccess) e = mlp::launch_infer_ref(c->q[layer], X, n, Y, st);
+    if (e == cudaSuccess) e = mlp::launch_infer_ref(c->q[layer], X, n, Y, mlp::jets_of_layer(layer), st);
     if (e != cudaSuccess) return cuda_fail(e, "ers_closure_infer_reference");
     return ERS_OK;
 }
@@ -551,7 +760,8 @@ static int grad_impl(ers_closure *c, int layer, const float *X, const float *T, 
     if (rc != ERS_OK) return rc;
     cudaError_t e = mlp::launch_quantize(c->p[layer], c->q[layer], st);
     if (e == cudaSuccess)
-        e = mlp::launch_train_grad(c->q[layer], X, T, idx, n, (float *)c->z.ptr, (float *)c->a.ptr,
+        e = mlp::launch_train_grad(c->q[layer], X, T, idx, n, mlp::jets_of_layer(layer), (float *)c->z.ptr,
+                                   (float *)c->a.ptr,
                                    (float *)c->d4.ptr, (float *)c->d.ptr, G, loss_dev, st);
     if (e != cudaSuccess) return cuda_fail(e, "closure training kernels");
     return ERS_OK;
@@ -632,20 +842,15 @@ int eval_few_delta(ers_surface *s, const ers_params *p, const double *y, int64_t
 
 namespace {
 
-int features(ers_surface *s, ers_closure *c, const ers_params *p, const double *y, int64_t M, const double *x0,
-             const double *n0, const double *b, const double *f0, const double *q0, const double *gf0,
-             const double *gq0, const double *u2, const double *v2, const double *gamma, const double *u3,
-             const double *v3, float *Xs, float *Xd, float *Ts, float *Td, double *scale, int *valid, int nd,
-             cudaStream_t st) {
+int features(ers_surface *s, const ers_params *p, int64_t M, const double *x0, const double *n0, const double *b,
+             const double *u2, const double *v2, const double *gamma, const double *u3, const double *v3, float *Xs,
+             float *Xd, float *Ts, float *Td, double *scale, int *valid, int nd, cudaStream_t st) {
     FeatArgs A;
-    A.y = y;
+    A.sd = surf_dev(s);
+    A.fq = s->fq;
     A.x0 = x0;
     A.n0 = n0;
     A.b = b;
-    A.f0 = f0;
-    A.q0 = q0;
-    A.gf0 = gf0;
-    A.gq0 = gq0;
     A.u2 = u2;
     A.v2 = v2;
     A.gamma = gamma;
@@ -654,11 +859,12 @@ int features(ers_surface *s, ers_closure *c, const ers_params *p, const double *
     A.M = M;
     A.h = s->h;
     A.rho0 = p->rho[0];
+    A.rho1 = p->rho[1];
     A.Rc = p->cutoff_t * p->rho[nd - 1] * s->h;
     A.nd = nd;
     // |gamma| at b = 0: beta = (rho_1, -rho_0) / (rho_1 - rho_0), I2(0) = 1 / (3 sqrt(pi)), so
     // |gamma(0)| = rho_0 rho_1 (rho_0 + rho_1) / (3 sqrt(pi))
-    A.gamma_min = 0.01 * p->rho[0] * p->rho[1] * (p->rho[0] + p->rho[1]) / (3.0 * 1.7724538509055160273);
+    A.gamma0 = p->rho[0] * p->rho[1] * (p->rho[0] + p->rho[1]) / (3.0 * 1.7724538509055160273);
     for (int i = 0; i < 3; ++i) {
         A.c[i] = s->c[i];
         A.a[i] = s->a[i];
@@ -669,11 +875,35 @@ int features(ers_surface *s, ers_closure *c, const ers_params *p, const double *
     A.Td = Td;
     A.scale = scale;
     A.valid = valid;
-    (void)c;
-    k_features<<<(unsigned)((M + 127) / 128), 128, 0, st>>>(A);
-    cudaError_t e = cudaGetLastError();
+    cudaError_t e = cudaFuncSetAttribute(k_features, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)FEAT_SMEM);
+    if (e != cudaSuccess) return cuda_fail(e, "closure features kernel: shared memory");
+    k_features<<<(unsigned)((M + FEAT_THREADS - 1) / FEAT_THREADS), FEAT_THREADS, FEAT_SMEM, st>>>(A);
+    e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "closure features kernel");
     return ERS_OK;
+}
+
+ApplyArgs apply_args(const ers_surface *s, const double *x0, const double *n0, const double *gamma,
+                     const double *scale, const float *Ys, const float *Yd, int64_t M, int nd, double *u, double *v) {
+    ApplyArgs A;
+    A.x0 = x0;
+    A.n0 = n0;
+    A.gamma = gamma;
+    A.scale = scale;
+    A.Ys = Ys;
+    A.Yd = Yd;
+    A.M = M;
+    A.h = s->h;
+    A.nd = nd;
+    A.mask = 3;
+    A.sign = 1.0;
+    for (int i = 0; i < 3; ++i) {
+        A.c[i] = s->c[i];
+        A.a[i] = s->a[i];
+    }
+    A.u = u;
+    A.v = v;
+    return A;
 }
 
 }  // namespace
@@ -681,13 +911,12 @@ int features(ers_surface *s, ers_closure *c, const ers_params *p, const double *
 extern "C" {
 
 int ers_closure_data(ers_surface *s, const ers_params *p, const double *y, int64_t M, const double *x0,
-                     const double *n0, const double *b, const double *f0, const double *q0, const double *gf0,
-                     const double *gq0, const double *u3, const double *v3, int ndelta, float *Xs, float *Xd,
-                     float *Ts, float *Td, int *valid, void *stream) {
+                     const double *n0, const double *b, const double *f0, const double *q0, const double *u3,
+                     const double *v3, int ndelta, float *Xs, float *Xd, float *Ts, float *Td, int *valid,
+                     void *stream) {
     clear_error();
     if (ndelta != 1 && ndelta != 2) return fail(ERS_E_INVAL, "ers_closure_data: ndelta must be 1 or 2");
-    if (!s || !p || !y || !x0 || !n0 || !b || !f0 || !q0 || !gf0 || !gq0 || !u3 || !v3 || !Xs || !Xd || !Ts || !Td ||
-        !valid)
+    if (!s || !p || !y || !x0 || !n0 || !b || !f0 || !q0 || !u3 || !v3 || !Xs || !Xd || !Ts || !Td || !valid)
         return fail(ERS_E_INVAL, "ers_closure_data: NULL argument");
     if (p->options & (ERS_OPT_FOUR_DELTA | ERS_OPT_TREECODE))
         return fail(ERS_E_UNSUPPORTED, "ers_closure_data: ERS_OPT_FOUR_DELTA and ERS_OPT_TREECODE are not supported");
@@ -700,17 +929,27 @@ int ers_closure_data(ers_surface *s, const ers_params *p, const double *y, int64
     ers_params pp = *p;
     pp.layers = ERS_LAYER_SL | ERS_LAYER_DL;
     if ((rc = eval_few_delta(s, &pp, y, M, x0, n0, b, f0, q0, u2, v2, gm, ndelta, st)) < 0) return rc;
-    return features(s, nullptr, &pp, y, M, x0, n0, b, f0, q0, gf0, gq0, u2, v2, gm, u3, v3, Xs, Xd, Ts, Td, sc,
-                    valid, ndelta, st);
+    return features(s, &pp, M, x0, n0, b, u2, v2, gm, u3, v3, Xs, Xd, Ts, Td, sc, valid, ndelta, st);
+}
+
+int ers_closure_last_gate(ers_closure *c, int used[2], double err_with[2], double err_without[2]) {
+    clear_error();
+    if (!c) return fail(ERS_E_INVAL, "ers_closure_last_gate: NULL closure");
+    for (int l = 0; l < 2; ++l) {
+        if (used) used[l] = c->last_used[l];
+        if (err_with) err_with[l] = c->last_err_with[l];
+        if (err_without) err_without[l] = c->last_err_without[l];
+    }
+    return ERS_OK;
 }
 
 int ers_eval_learned(ers_surface *s, ers_closure *c, const ers_params *p, const double *y, int64_t M,
                      const double *x0, const double *n0, const double *b, const double *f0, const double *q0,
-                     const double *gf0, const double *gq0, int ndelta, double *u, double *v, double tol, int vstride,
-                     double *val_err, int *fell_back, void *stream) {
+                     int ndelta, double *u, double *v, double tol, int vstride, double *val_err, int *fell_back,
+                     void *stream) {
     clear_error();
     if (ndelta != 1 && ndelta != 2) return fail(ERS_E_INVAL, "ers_eval_learned: ndelta must be 1 or 2");
-    if (!s || !c || !p || !y || !x0 || !n0 || !b || !f0 || !q0 || !gf0 || !gq0 || !u || !v)
+    if (!s || !c || !p || !y || !x0 || !n0 || !b || !f0 || !q0 || !u || !v)
         return fail(ERS_E_INVAL, "ers_eval_learned: NULL argument (both layers and all closest-point data needed)");
     if (p->options & (ERS_OPT_FOUR_DELTA | ERS_OPT_TREECODE))
         return fail(ERS_E_UNSUPPORTED, "ers_eval_learned: ERS_OPT_FOUR_DELTA and ERS_OPT_TREECODE are not supported");
@@ -718,31 +957,38 @@ int ers_eval_learned(ers_surface *s, ers_closure *c, const ers_params *p, const 
     if (vstride < 1) return fail(ERS_E_INVAL, "ers_eval_learned: vstride must be >= 1");
     int rc = closure_check(c, 0);
     if (rc != ERS_OK) return rc;
+    if (!s->has_f || !s->has_q)
+        return fail(ERS_E_STATE, "ers_eval_learned: both densities must be set (ers_set_density)");
     if (fell_back) *fell_back = 0;
+    for (int l = 0; l < 2; ++l) {
+        c->last_used[l] = 0;
+        c->last_err_with[l] = c->last_err_without[l] = 0.0;
+    }
     if (M == 0) return ERS_OK;
     cudaStream_t st = (cudaStream_t)stream;
     ers_params pp = *p;
     pp.layers = ERS_LAYER_SL | ERS_LAYER_DL;
-    // work buffers of the closure: features (2 x M x 16 f32), outputs (2 x M x 4 f32), gamma, scale
-    if ((rc = grow(c->feat, sizeof(float) * (size_t)M * mlp::IN * 2)) != ERS_OK) return rc;
+    // work buffers of the closure: sample records (2 x M x XSTR f32), outputs (2 x M x 4 f32),
+    // gamma, scale
+    if ((rc = grow(c->feat, sizeof(float) * (size_t)M * mlp::XSTR * 2)) != ERS_OK) return rc;
     if ((rc = grow(c->outp, sizeof(float) * (size_t)M * mlp::OUT_STRIDE * 2)) != ERS_OK) return rc;
     if ((rc = grow(c->gamma, sizeof(double) * (size_t)M)) != ERS_OK) return rc;
     if ((rc = grow(c->scale, sizeof(double) * (size_t)M * 2)) != ERS_OK) return rc;
-    if ((rc = grow(c->valid, sizeof(int) * (size_t)M)) != ERS_OK) return rc;
-    float *Xs = (float *)c->feat.ptr, *Xd = Xs + M * mlp::IN;
+    float *Xs = (float *)c->feat.ptr, *Xd = Xs + M * mlp::XSTR;
     float *Ys = (float *)c->outp.ptr, *Yd = Ys + M * mlp::OUT_STRIDE;
     double *gm = (double *)c->gamma.ptr, *sc = (double *)c->scale.ptr;
     // 1. one- or two-delta sums; 2. features; 3. network (tensor cores); 4. correction
     if ((rc = eval_few_delta(s, &pp, y, M, x0, n0, b, f0, q0, u, v, gm, ndelta, st)) < 0) return rc;
-    if ((rc = features(s, c, &pp, y, M, x0, n0, b, f0, q0, gf0, gq0, nullptr, nullptr, gm, nullptr, nullptr, Xs, Xd,
-                       nullptr, nullptr, sc, (int *)c->valid.ptr, ndelta, st)) != ERS_OK)
+    if ((rc = features(s, &pp, M, x0, n0, b, nullptr, nullptr, gm, nullptr, nullptr, Xs, Xd, nullptr, nullptr, sc,
+                       nullptr, ndelta, st)) != ERS_OK)
         return rc;
     if ((rc = infer(c, 0, Xs, M, Ys, st)) != ERS_OK) return rc;
     if ((rc = infer(c, 1, Xd, M, Yd, st)) != ERS_OK) return rc;
-    k_apply<<<(unsigned)((M + 127) / 128), 128, 0, st>>>(n0, gm, sc, Ys, Yd, M, s->h, ndelta, u, v);
+    ApplyArgs ap = apply_args(s, x0, n0, gm, sc, Ys, Yd, M, ndelta, u, v);
+    k_apply<<<(unsigned)((M + 127) / 128), 128, 0, st>>>(ap);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "closure correction kernel");
-    // 4b. targets whose features lie outside the training extent: the three-delta method instead
+    // 4b. targets whose geometry lies outside the training extent: the three-delta method instead
     c->last_out = 0;
     if (c->range_check && (c->have_range[0] || c->have_range[1])) {
         // [count | pad | idx (M) | gathered inputs (16 K) | u, v (6 K)], K <= M
@@ -770,37 +1016,55 @@ int ers_eval_learned(ers_surface *s, ers_closure *c, const ers_params *p, const 
             if ((rc = ers_eval(s, &pp, sub, Kt, sub + 3 * Kt, sub + 6 * Kt, sub + 9 * Kt, sub + 10 * Kt,
                                sub + 13 * Kt, up, vp, stream)) < 0)
                 return rc;
-            k_scatter_idx<<<(unsigned)((Kt + 127) / 128), 128, 0, st>>>(up, vp, idx, Kt, u, v);
+            k_scatter_idx<<<(unsigned)((Kt + 127) / 128), 128, 0, st>>>(up, vp, idx, Kt, u, v, sc);
             if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "ers_eval_learned: scatter");
         }
     }
-    // 5. validation against the three-delta method on every vstride-th target
+    // 5. validation against the three-delta method on every vstride-th target, with and without
+    // the network's correction; per layer the better of the two is kept
     const int64_t Ms = (M + vstride - 1) / vstride;
     if ((rc = grow(c->sub, sizeof(double) * ((size_t)Ms * 22 + 8))) != ERS_OK) return rc;
     double *sub = (double *)c->sub.ptr;
     double *up = sub + 16 * Ms, *vp = up + 3 * Ms, *res = vp + 3 * Ms;
     k_gather<<<(unsigned)((Ms + 127) / 128), 128, 0, st>>>(y, x0, n0, b, f0, q0, Ms, vstride, sub);
-    e = cudaMemsetAsync(res, 0, sizeof(double) * 4, st);
+    e = cudaMemsetAsync(res, 0, sizeof(double) * 6, st);
     if (e != cudaSuccess) return cuda_fail(e, "ers_eval_learned: memset");
     if ((rc = ers_eval(s, &pp, sub, Ms, sub + 3 * Ms, sub + 6 * Ms, sub + 9 * Ms, sub + 10 * Ms, sub + 13 * Ms, up, vp,
                        stream)) < 0)
         return rc;
-    k_compare<<<64, 128, 0, st>>>(u, v, up, vp, Ms, vstride, res);
-    double h[4];
+    k_compare<<<64, 128, 0, st>>>(ap, up, vp, Ms, vstride, res);
+    double h[6];
     e = cudaMemcpyAsync(h, res, sizeof h, cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) return cuda_fail(e, "ers_eval_learned: validation");
     int timed_out = 0;
     cudaMemcpy(&timed_out, c->err, sizeof(int), cudaMemcpyDeviceToHost);
-    const double es = h[1] > 0 ? h[0] / h[1] : 0.0, ed = h[3] > 0 ? h[2] / h[3] : 0.0;
-    if (val_err) {
-        val_err[0] = es;
-        val_err[1] = ed;
-    }
     if (timed_out) return fail(ERS_E_TIMEOUT, "ers_eval_learned: a tensor-core wait in the closure kernel expired");
-    if (!(es <= tol && ed <= tol)) {
+    double err[2];
+    int undo = 0;
+    for (int l = 0; l < 2; ++l) {
+        const double ref = h[2 * l + 1];
+        const double ew = ref > 0 ? h[2 * l] / ref : 0.0, eo = ref > 0 ? h[4 + l] / ref : 0.0;
+        c->last_err_with[l] = ew;
+        c->last_err_without[l] = eo;
+        c->last_used[l] = ew <= eo ? 1 : 0;
+        if (!c->last_used[l]) undo |= 1 << l;
+        err[l] = std::min(ew, eo);
+    }
+    if (val_err) {
+        val_err[0] = err[0];
+        val_err[1] = err[1];
+    }
+    if (!(err[0] <= tol && err[1] <= tol)) {
         if (fell_back) *fell_back = 1;
         return ers_eval(s, &pp, y, M, x0, n0, b, f0, q0, u, v, stream);
+    }
+    if (undo) {  // take back the correction of a layer whose network did not help on the sample
+        ApplyArgs un = ap;
+        un.mask = undo;
+        un.sign = -1.0;
+        k_apply<<<(unsigned)((M + 127) / 128), 128, 0, st>>>(un);
+        if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "ers_eval_learned: undo");
     }
     return ERS_OK;
 }

@@ -46,7 +46,7 @@ namespace {
 
 void free_surface(ers_surface *s) {
     if (!s) return;
-    void *ptrs[] = {s->x, s->n, s->w, s->perm, s->rec, s->rec32, s->tilec, s->xs32, s->cell_start, s->cell_rank,
+    void *ptrs[] = {s->x, s->n, s->w, s->perm, s->rec, s->rec32, s->tilec, s->xs32, s->fq, s->cell_start, s->cell_rank,
                     s->okeys.ptr, s->oorder.ptr, s->ohist.ptr,
                     s->part.ptr, s->cp.ptr, s->host_io.ptr, s->counts.ptr, s->dens64.ptr, s->dens32.ptr};
     for (void *p : ptrs)
@@ -234,6 +234,7 @@ int build_surface(const ers_shape *shape, double h, ers_surface **out) {
     ERS_TRY(dmalloc(&s->rec32, (size_t)N * REC));
     ERS_TRY(dmalloc(&s->tilec, (size_t)s->ntile32 * 4));
     ERS_TRY(dmalloc(&s->xs32, N));
+    ERS_TRY(dmalloc(&s->fq, (size_t)N * 6));
     ERS_TRY(dmalloc(&s->cell_start, G.ncell + 1));
     ERS_TRY(dmalloc(&s->cell_rank, G.ncell));
     if (e != cudaSuccess) {

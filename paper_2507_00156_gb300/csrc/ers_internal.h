@@ -96,6 +96,7 @@ struct ers_surface {
     float *rec32 = nullptr;       // N * REC floats
     float *tilec = nullptr;       // ntile32 * 4 floats (centre of each FP32 tile, exact floats)
     float4 *xs32 = nullptr;       // N float coordinates for the near-field prefilter
+    double *fq = nullptr;         // N * 6: the node densities f, q as given (for the closure's jets)
     int *cell_start = nullptr;    // ncell + 1
     ers::Grid grid{};
     int64_t ntile32 = 0;

@@ -1,16 +1,21 @@
-// The closure network: an MLP 16 -> 64 -> 64 -> 64 -> 16 (13 inputs used, 3 outputs used), GELU
-// after the three hidden layers, BF16 weights and activations with FP32 accumulation.
+// The closure network: an MLP 16 -> 64 -> 64 -> 64 -> 96 (5 inputs used: the local geometry;
+// 3 J outputs used: the coefficients of a linear map from the J density jets of the sample to the
+// three components of the correction), GELU after the three hidden layers, BF16 weights and
+// activations with FP32 accumulation.  The head contracts the coefficients with the jets in FP32:
+// c_e = sum_j A[e J + j] jet_j.
 //
 // Inference runs on the 5th-generation tensor cores: a CTA holds a tile of 128 samples; the
 // activations (A operand) and the weights (B operand) sit in shared memory in the canonical
 // K-major layout without swizzle (8 x 16-byte core matrices), one elected thread issues
-// tcgen05.mma (M = 128, N = 64 or 16, K = 16 per instruction) into an FP32 accumulator in tensor
+// tcgen05.mma (M = 128, N = 64 or 96, K = 16 per instruction) into an FP32 accumulator in tensor
 // memory, the four warps read it back with tcgen05.ld (warp w owns rows 32w..32w+31), add the
-// bias, apply GELU, round to BF16 and write the next layer's A operand.
+// bias, apply GELU, round to BF16 and write the next layer's A operand; after the last layer each
+// thread contracts its row's coefficients with its sample's jets.
 //
 // Training runs in FP32 on the CUDA cores with the same BF16 rounding of weights, inputs and
 // hidden activations in the forward pass (straight-through in the backward pass), so that the
-// trained network is the one the tensor-core kernel evaluates.
+// trained network is the one the tensor-core kernel evaluates.  The loss of a sample is
+// w/2 |c - t|^2 with the target t and weight w of its training record.
 #include <cuda_bf16.h>
 
 #include "ers_internal.h"
@@ -113,7 +118,7 @@ __device__ __forceinline__ uint32_t kmaj_off(int row, int k, int rows) {
 }
 
 constexpr int TILE = 128;
-constexpr uint32_t TMEM_COLS = 64;
+constexpr uint32_t TMEM_COLS = 128;  // the last layer uses OUT = 96 columns
 constexpr uint32_t WAIT_LIMIT = 1u << 22;
 
 struct InferSmem {
@@ -143,6 +148,7 @@ __device__ __forceinline__ void issue_layer(uint32_t d_tmem, const unsigned char
     }
 }
 
+template <int NJ>
 __global__ void __launch_bounds__(TILE) k_mlp_infer_tc(const float *__restrict__ params, const float *__restrict__ X,
                                                        int64_t n, float *__restrict__ Y, int *__restrict__ err) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -180,7 +186,7 @@ __global__ void __launch_bounds__(TILE) k_mlp_infer_tc(const float *__restrict__
     for (int64_t tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
         const int64_t row = tile * TILE + t;
         // inputs of this thread's sample -> A (K = 16)
-        for (int k = 0; k < IN; ++k) store_bf16(S.a, kmaj_off(t, k, TILE), row < n ? X[row * IN + k] : 0.0f);
+        for (int k = 0; k < IN; ++k) store_bf16(S.a, kmaj_off(t, k, TILE), row < n ? X[row * XSTR + k] : 0.0f);
         for (int layer = 0; layer < 4 && ok; ++layer) {
             fence_proxy_async();
             fence_before_sync();
@@ -209,12 +215,29 @@ __global__ void __launch_bounds__(TILE) k_mlp_infer_tc(const float *__restrict__
                                                              gelu(v[i] + bias[c0 + i]));
                 }
             } else {
-                float v[16];
-                tmem_ld16(tmem + lane_base, v);
-                tmem_wait_ld();
+                // head: coefficients A (3 NJ of the OUT columns) contracted with the sample's jets
+                float a[OUT];
+#pragma unroll
+                for (int c0 = 0; c0 < OUT; c0 += 16) {
+                    float v[16];
+                    tmem_ld16(tmem + lane_base + c0, v);
+                    tmem_wait_ld();
+#pragma unroll
+                    for (int i = 0; i < 16; ++i) a[c0 + i] = v[i] + S.b4[c0 + i];
+                }
                 const int64_t r = tile * TILE + warp * 32 + lane;
-                if (r < n)
-                    for (int i = 0; i < OUT_USED; ++i) Y[r * OUT_STRIDE + i] = v[i] + S.b4[i];
+                if (r < n) {
+                    const float *jet = X + r * XSTR + JET_OFF;
+                    float c[3] = {0.0f, 0.0f, 0.0f};
+#pragma unroll
+                    for (int j = 0; j < NJ; ++j) {
+                        const float g = jet[j];
+#pragma unroll
+                        for (int e = 0; e < 3; ++e) c[e] = fmaf(a[e * NJ + j], g, c[e]);
+                    }
+                    for (int e = 0; e < 3; ++e) Y[r * OUT_STRIDE + e] = c[e];
+                    Y[r * OUT_STRIDE + 3] = 0.0f;
+                }
             }
         }
     }
@@ -275,28 +298,42 @@ __device__ __forceinline__ void forward_one(const float *q, const float *x, floa
     }
 }
 
+// c_e = sum_j A[e nj + j] jet_j (the head).
+__device__ __forceinline__ void contract(const float *A, const float *jet, int nj, float c[3]) {
+    c[0] = c[1] = c[2] = 0.0f;
+    for (int j = 0; j < nj; ++j) {
+        const float g = jet[j];
+        for (int e = 0; e < 3; ++e) c[e] = fmaf(A[e * nj + j], g, c[e]);
+    }
+}
+
 constexpr int NT_SIMT = 128;
 
+constexpr size_t SIMT_SMEM = sizeof(float) * NPARAM;  // the quantized parameters (above 48 KB: opt-in)
+
 __global__ void __launch_bounds__(NT_SIMT) k_mlp_infer_ref(const float *__restrict__ q, const float *__restrict__ X,
-                                                           int64_t n, float *__restrict__ Y) {
-    __shared__ float sq[NPARAM];
+                                                           int64_t n, int nj, float *__restrict__ Y) {
+    extern __shared__ float sq[];
     for (int i = threadIdx.x; i < NPARAM; i += NT_SIMT) sq[i] = q[i];
     __syncthreads();
     const int64_t s = (int64_t)blockIdx.x * NT_SIMT + threadIdx.x;
     if (s >= n) return;
-    float x[IN], out[OUT_USED];
-    for (int k = 0; k < IN; ++k) x[k] = X[s * IN + k];
+    float x[IN], out[OUT_USED], c[3];
+    for (int k = 0; k < IN; ++k) x[k] = X[s * XSTR + k];
     forward_one(sq, x, out, nullptr, nullptr);
-    for (int i = 0; i < OUT_USED; ++i) Y[s * OUT_STRIDE + i] = out[i];
+    contract(out, X + s * XSTR + JET_OFF, nj, c);
+    for (int e = 0; e < 3; ++e) Y[s * OUT_STRIDE + e] = c[e];
+    Y[s * OUT_STRIDE + 3] = 0.0f;
 }
 
-// Training forward + output error: stores Z (n x 3*HID), A (n x ACT) and D4 = (y - t) / n.
+// Training forward + output error: stores Z (n x 3*HID), A (n x ACT) and
+// D4 = dL/d(coefficients) = w (c - t)_e jet_j / n at coefficient e nj + j (0 beyond 3 nj).
 __global__ void __launch_bounds__(NT_SIMT) k_train_fwd(const float *__restrict__ q, const float *__restrict__ X,
                                                        const float *__restrict__ T, const int *__restrict__ idx,
-                                                       int64_t n, float inv_n, float *__restrict__ Z,
+                                                       int64_t n, int nj, float inv_n, float *__restrict__ Z,
                                                        float *__restrict__ A, float *__restrict__ D4,
                                                        double *__restrict__ loss) {
-    __shared__ float sq[NPARAM];
+    extern __shared__ float sq[];
     __shared__ double sl[NT_SIMT / 32];
     for (int i = threadIdx.x; i < NPARAM; i += NT_SIMT) sq[i] = q[i];
     __syncthreads();
@@ -304,13 +341,20 @@ __global__ void __launch_bounds__(NT_SIMT) k_train_fwd(const float *__restrict__
     double l = 0.0;
     if (s < n) {
         const int64_t src = idx ? idx[s] : s;
-        float x[IN], out[OUT_USED];
-        for (int k = 0; k < IN; ++k) x[k] = X[src * IN + k];
+        float x[IN], out[OUT_USED], c[3];
+        for (int k = 0; k < IN; ++k) x[k] = X[src * XSTR + k];
         forward_one(sq, x, out, Z + s * (3 * HID), A + s * ACT);
-        for (int i = 0; i < OUT_USED; ++i) {
-            const float e = out[i] - T[src * OUT_STRIDE + i];
-            D4[s * OUT_USED + i] = e * inv_n;
-            l += 0.5 * (double)e * e;
+        const float *jet = X + src * XSTR + JET_OFF;
+        contract(out, jet, nj, c);
+        const float w = T[src * TSTR + 3];
+        float err[3];
+        for (int e = 0; e < 3; ++e) {
+            err[e] = c[e] - T[src * TSTR + e];
+            l += 0.5 * (double)w * err[e] * err[e];
+        }
+        for (int k = 0; k < OUT_USED; ++k) {
+            const int e = k / nj, j = k - e * nj;
+            D4[s * OUT_USED + k] = e < 3 ? w * err[e] * jet[j] * inv_n : 0.0f;
         }
     }
     for (int o = 16; o > 0; o >>= 1) l += __shfl_xor_sync(0xffffffffu, l, o);
@@ -327,7 +371,7 @@ __global__ void __launch_bounds__(NT_SIMT) k_train_fwd(const float *__restrict__
 __global__ void __launch_bounds__(NT_SIMT) k_train_bwd(const float *__restrict__ q, const float *__restrict__ Z,
                                                        const float *__restrict__ D4, int64_t n,
                                                        float *__restrict__ D) {
-    __shared__ float sq[NPARAM];
+    extern __shared__ float sq[];
     for (int i = threadIdx.x; i < NPARAM; i += NT_SIMT) sq[i] = q[i];
     __syncthreads();
     const int64_t s = (int64_t)blockIdx.x * NT_SIMT + threadIdx.x;
@@ -407,12 +451,14 @@ __global__ void k_adam(float *__restrict__ p, float *__restrict__ m, float *__re
 
 size_t infer_smem_bytes() { return sizeof(InferSmem) + 1024; }
 
-cudaError_t launch_infer_tc(const float *params, const float *X, int64_t n, float *Y, int *err, int grid,
+cudaError_t launch_infer_tc(const float *params, const float *X, int64_t n, float *Y, int nj, int *err, int grid,
                             cudaStream_t st) {
+    if (nj != NJ_SL && nj != NJ_DL) return cudaErrorInvalidValue;
     const size_t smem = infer_smem_bytes();
-    cudaError_t e = cudaFuncSetAttribute(k_mlp_infer_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    auto kern = nj == NJ_SL ? k_mlp_infer_tc<NJ_SL> : k_mlp_infer_tc<NJ_DL>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    k_mlp_infer_tc<<<grid, TILE, smem, st>>>(params, X, n, Y, err);
+    kern<<<grid, TILE, smem, st>>>(params, X, n, Y, err);
     return cudaGetLastError();
 }
 
@@ -445,18 +491,26 @@ cudaError_t launch_quantize(const float *p, float *q, cudaStream_t st) {
     return cudaGetLastError();
 }
 
-cudaError_t launch_infer_ref(const float *q, const float *X, int64_t n, float *Y, cudaStream_t st) {
+cudaError_t launch_infer_ref(const float *q, const float *X, int64_t n, float *Y, int nj, cudaStream_t st) {
+    if (nj != NJ_SL && nj != NJ_DL) return cudaErrorInvalidValue;
     if (n == 0) return cudaSuccess;
-    k_mlp_infer_ref<<<(unsigned)((n + NT_SIMT - 1) / NT_SIMT), NT_SIMT, 0, st>>>(q, X, n, Y);
+    cudaError_t e = cudaFuncSetAttribute(k_mlp_infer_ref, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SIMT_SMEM);
+    if (e != cudaSuccess) return e;
+    k_mlp_infer_ref<<<(unsigned)((n + NT_SIMT - 1) / NT_SIMT), NT_SIMT, SIMT_SMEM, st>>>(q, X, n, nj, Y);
     return cudaGetLastError();
 }
 
-cudaError_t launch_train_grad(const float *q, const float *X, const float *T, const int *idx, int64_t n, float *Z,
-                              float *A, float *D4, float *D, float *G, double *loss, cudaStream_t st) {
+cudaError_t launch_train_grad(const float *q, const float *X, const float *T, const int *idx, int64_t n, int nj,
+                              float *Z, float *A, float *D4, float *D, float *G, double *loss, cudaStream_t st) {
+    if (nj != NJ_SL && nj != NJ_DL) return cudaErrorInvalidValue;
     const unsigned nb = (unsigned)((n + NT_SIMT - 1) / NT_SIMT);
     const float inv_n = 1.0f / (float)n;
-    k_train_fwd<<<nb, NT_SIMT, 0, st>>>(q, X, T, idx, n, inv_n, Z, A, D4, loss);
-    k_train_bwd<<<nb, NT_SIMT, 0, st>>>(q, Z, D4, n, D);
+    cudaError_t e = cudaFuncSetAttribute(k_train_fwd, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SIMT_SMEM);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_train_bwd, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SIMT_SMEM);
+    if (e != cudaSuccess) return e;
+    k_train_fwd<<<nb, NT_SIMT, SIMT_SMEM, st>>>(q, X, T, idx, n, nj, inv_n, Z, A, D4, loss);
+    k_train_bwd<<<nb, NT_SIMT, SIMT_SMEM, st>>>(q, Z, D4, n, D);
     k_train_wgrad<<<(NPARAM + 127) / 128, 128, 0, st>>>(A, D, D4, n, G);
     return cudaGetLastError();
 }

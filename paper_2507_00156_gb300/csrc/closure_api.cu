@@ -72,7 +72,7 @@ constexpr int NPK = NB * (NB + 1) / 2;
 constexpr int NRHS = 6;           // f and q, three components each, in the frame
 constexpr double FIT_R = 3.5;     // fit radius in units of h
 constexpr int FEAT_THREADS = 64;  // threads per block of the features kernel
-constexpr size_t FEAT_SMEM = sizeof(double) * (NPK + NB * NRHS) * FEAT_THREADS;
+constexpr size_t FEAT_SMEM = sizeof(double) * NPK * FEAT_THREADS;  // a Cholesky factor per thread
 
 // t1 = n x a / |n x a| with a = e_x (e_y when |n_x| >= 0.9), t2 = n x t1.
 __host__ __device__ __forceinline__ void fallback_frame(const double n[3], double t1[3], double t2[3]) {
@@ -161,20 +161,27 @@ __device__ __forceinline__ void target_frame(const double *x0, const double *n0,
     principal_frame(p, a, n, t1, t2, k1, k2);
 }
 
-// monomials xi^i eta^j of total degree <= 4, ordered by degree, then by falling i
-__device__ __forceinline__ void monomials4(double xi, double eta, double *phi) {
-    double xp[5], ep[5];
-    xp[0] = ep[0] = 1.0;
-    for (int i = 1; i < 5; ++i) {
-        xp[i] = xp[i - 1] * xi;
-        ep[i] = ep[i - 1] * eta;
-    }
-    int k = 0;
-#pragma unroll
-    for (int d = 0; d <= 4; ++d)
-#pragma unroll
-        for (int j = 0; j <= d; ++j) phi[k++] = xp[d - j] * ep[j];
-}
+// The density fit of a target (degree-4 least squares in the scaled tangent-plane coordinates
+// (xi, eta) = ((x - x0).t1, (x - x0).t2) / (3.5 h) over the nodes within 3.5 h of x0) in three
+// convergent passes (one thread per target each):
+//   k_fit_scan   the target's neighbours (an FP32 distance prefilter, the FP64 test |x - x0|^2 <=
+//                (3.5 h)^2 where the prefilter is not conclusive) into a list;
+//   k_fit_accum  over the list: the 45 moments sum xi^p eta^q (p + q <= 8), which hold every entry
+//                of Phi^T Phi, and Phi^T U for the 6 density components along t1, t2, n0;
+//   k_features   Phi^T Phi from the moments, Cholesky, the coefficients of the monomials of degree
+//                <= 3, then the features.
+// Separate passes keep the lanes of a warp on the same instructions (one thread per target walking
+// its own candidates would run the accumulation whenever any lane found a neighbour).
+constexpr int FIT_LMAX = 96;   // neighbours per target at most (about 53 on a lattice surface)
+constexpr int NMOM = 45;       // moments of degree <= 8
+constexpr int NACC = NMOM + NB * NRHS;  // 135 accumulated values per target
+
+// monomial k of degree <= 4 (ordered by degree, then by falling power of xi) = xi^mi(k) eta^mj(k)
+__host__ __device__ constexpr int mono_j(int k) { return k == 0 ? 0 : (k < 3 ? k - 1 : (k < 6 ? k - 3 : (k < 10 ? k - 6 : k - 10))); }
+__host__ __device__ constexpr int mono_d(int k) { return k == 0 ? 0 : (k < 3 ? 1 : (k < 6 ? 2 : (k < 10 ? 3 : 4))); }
+__host__ __device__ constexpr int mono_i(int k) { return mono_d(k) - mono_j(k); }
+// index of the moment xi^p eta^q, p + q = d: d (d + 1) / 2 + q
+__host__ __device__ constexpr int mom_idx(int p, int q) { return (p + q) * (p + q + 1) / 2 + q; }
 
 // i! j! / 3.5^(i + j) of monomial k (degrees <= 3): the derivative d^(i+j)/dxi^i deta^j in units
 // of h of the fit in the scaled coordinates (xi, eta) / 3.5.
@@ -190,18 +197,38 @@ __device__ __forceinline__ double deriv_factor(int k) {
     }
 }
 
-// Degree-4 least-squares fit of the node densities (f, q along t1, t2, n) within FIT_R h of x0:
-// normal equations (Phi^T Phi) c = Phi^T U accumulated in this thread's column of shared memory
-// (stride FEAT_THREADS), Cholesky, then the coefficients of the monomials of degree <= 3 as
-// derivatives in units of h: out[k][r], k = 0..9, r = 0..5 (f t1, f t2, f n, q t1, q t2, q n).
-// Returns false with fewer than 15 nodes or a pivot <= 0.
-__device__ bool fit_jets(const SurfDev &sd, const double *__restrict__ fq, const double x0[3], const double t1[3],
-                         const double t2[3], const double n[3], double h, double *A, double *B, double out[10][NRHS]) {
-    const int S = FEAT_THREADS;
-    for (int k = 0; k < NPK; ++k) A[k * S] = 0.0;
-    for (int k = 0; k < NB * NRHS; ++k) B[k * S] = 0.0;
-    const double R = FIT_R * h, R2 = R * R, iR = 1.0 / R;
-    const Grid &G = sd.grid;
+struct FitArgs {
+    SurfDev sd;
+    const double *fq;
+    const double *x0, *n0, *b;
+    int64_t M;
+    double h, Rc, c[3], a[3];
+    int *list;    // [FIT_LMAX][M]
+    int *cnt;     // [M]: neighbours, or -1 (no fit: beyond Rc, or more than FIT_LMAX)
+    double *acc;  // [NACC][M]
+};
+
+__device__ __forceinline__ bool fit_target(const FitArgs &A, int64_t m, double x0[3]) {
+    for (int i = 0; i < 3; ++i) x0[i] = A.x0[3 * m + i];
+    return fabs(A.b[m]) <= A.Rc;
+}
+
+__global__ void k_fit_scan(FitArgs A) {
+    const int64_t m = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (m >= A.M) return;
+    double x0[3];
+    if (!fit_target(A, m, x0)) {
+        A.cnt[m] = -1;
+        return;
+    }
+    const double R = FIT_R * A.h, R2 = R * R;
+    const float x0f[3] = {(float)x0[0], (float)x0[1], (float)x0[2]};
+    const float R2f = (float)R2;
+    // FP32 distances carry an absolute error below 4 (|x0| + R) 2^-23 2R; outside that band the
+    // FP32 test decides, inside it the FP64 one
+    const double amax = fmax(fabs(x0[0]), fmax(fabs(x0[1]), fabs(x0[2]))) + R;
+    const float band = (float)(8.0 * amax * 1.1920928955078125e-7 * 2.0 * R) + 1e-30f;
+    const Grid &G = A.sd.grid;
     int lo[3], hi[3];
     for (int a = 0; a < 3; ++a) {
         lo[a] = max(0, (int)floor((x0[a] - R - G.origin[a]) / G.cw));
@@ -211,100 +238,151 @@ __device__ bool fit_jets(const SurfDev &sd, const double *__restrict__ fq, const
     for (int iz = lo[2]; iz <= hi[2]; ++iz)
         for (int iy = lo[1]; iy <= hi[1]; ++iy) {
             const int64_t row = ((int64_t)iz * G.nc[1] + iy) * G.nc[0];
-            const int js = sd.cell_start[row + lo[0]], je = sd.cell_start[row + hi[0] + 1];
+            const int js = A.sd.cell_start[row + lo[0]], je = A.sd.cell_start[row + hi[0] + 1];
             for (int j = js; j < je; ++j) {
-                const double *r = sd.rec + (int64_t)j * REC;
-                const double d[3] = {r[0] - x0[0], r[1] - x0[1], r[2] - x0[2]};
-                if (!(d[0] * d[0] + d[1] * d[1] + d[2] * d[2] <= R2)) continue;
-                ++cnt;
-                double phi[NB];
-                monomials4((d[0] * t1[0] + d[1] * t1[1] + d[2] * t1[2]) * iR,
-                           (d[0] * t2[0] + d[1] * t2[1] + d[2] * t2[2]) * iR, phi);
-                const double *u = fq + (int64_t)j * 6;
-                double uf[NRHS];
-                for (int c = 0; c < 2; ++c) {
-                    const double *v = u + 3 * c;
-                    uf[3 * c + 0] = v[0] * t1[0] + v[1] * t1[1] + v[2] * t1[2];
-                    uf[3 * c + 1] = v[0] * t2[0] + v[1] * t2[1] + v[2] * t2[2];
-                    uf[3 * c + 2] = v[0] * n[0] + v[1] * n[1] + v[2] * n[2];
+                const float4 p = __ldg(A.sd.xs32 + j);
+                const float dx = p.x - x0f[0], dy = p.y - x0f[1], dz = p.z - x0f[2];
+                const float d2 = dx * dx + dy * dy + dz * dz;
+                bool in = d2 <= R2f - band;
+                if (!in && d2 <= R2f + band) {
+                    const double *r = A.sd.rec + (int64_t)j * REC;
+                    const double d[3] = {r[0] - x0[0], r[1] - x0[1], r[2] - x0[2]};
+                    in = d[0] * d[0] + d[1] * d[1] + d[2] * d[2] <= R2;
                 }
-#pragma unroll
-                for (int i = 0; i < NB; ++i) {
-#pragma unroll
-                    for (int q = 0; q <= i; ++q) A[(i * (i + 1) / 2 + q) * S] = fma(phi[i], phi[q], A[(i * (i + 1) / 2 + q) * S]);
-#pragma unroll
-                    for (int c = 0; c < NRHS; ++c) B[(i * NRHS + c) * S] = fma(phi[i], uf[c], B[(i * NRHS + c) * S]);
+                if (in) {
+                    if (cnt < FIT_LMAX) A.list[(int64_t)cnt * A.M + m] = j;
+                    ++cnt;
                 }
             }
         }
-    if (cnt < NB) return false;
-    // Cholesky A = L L^T in place (packed rows)
+    A.cnt[m] = cnt <= FIT_LMAX ? cnt : -1;
+}
+
+__global__ void __launch_bounds__(128) k_fit_accum(FitArgs A) {
+    const int64_t m = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (m >= A.M) return;
+    const int cnt = A.cnt[m];
+    if (cnt < NB) return;
+    double x0[3], t1[3], t2[3], n[3], k1, k2;
+    fit_target(A, m, x0);
+    target_frame(A.x0, A.n0, m, A.c, A.a, t1, t2, n, k1, k2);
+    const double iR = 1.0 / (FIT_R * A.h);
+    // pass 1: moments and the single-layer density; pass 2: the double-layer density
+#pragma unroll
+    for (int pass = 0; pass < 2; ++pass) {
+        double mom[NMOM], bacc[NB * 3];
+        if (pass == 0)
+#pragma unroll
+            for (int e = 0; e < NMOM; ++e) mom[e] = 0.0;
+#pragma unroll
+        for (int e = 0; e < NB * 3; ++e) bacc[e] = 0.0;
+        for (int k = 0; k < cnt; ++k) {
+            const int j = A.list[(int64_t)k * A.M + m];
+            const double *r = A.sd.rec + (int64_t)j * REC;
+            const double d[3] = {r[0] - x0[0], r[1] - x0[1], r[2] - x0[2]};
+            const double xi = (d[0] * t1[0] + d[1] * t1[1] + d[2] * t1[2]) * iR;
+            const double eta = (d[0] * t2[0] + d[1] * t2[1] + d[2] * t2[2]) * iR;
+            const double *u = A.fq + (int64_t)j * 6 + 3 * pass;
+            const double uf[3] = {u[0] * t1[0] + u[1] * t1[1] + u[2] * t1[2], u[0] * t2[0] + u[1] * t2[1] + u[2] * t2[2],
+                                  u[0] * n[0] + u[1] * n[1] + u[2] * n[2]};
+            double xp[9], ep[9];
+            xp[0] = ep[0] = 1.0;
+#pragma unroll
+            for (int i = 1; i < (pass == 0 ? 9 : 5); ++i) {
+                xp[i] = xp[i - 1] * xi;
+                ep[i] = ep[i - 1] * eta;
+            }
+            if (pass == 0) {
+#pragma unroll
+                for (int dd = 0; dd <= 8; ++dd)
+#pragma unroll
+                    for (int q = 0; q <= dd; ++q) mom[mom_idx(dd - q, q)] = fma(xp[dd - q], ep[q], mom[mom_idx(dd - q, q)]);
+            }
+#pragma unroll
+            for (int i = 0; i < NB; ++i) {
+                const double phi = xp[mono_i(i)] * ep[mono_j(i)];
+#pragma unroll
+                for (int c = 0; c < 3; ++c) bacc[3 * i + c] = fma(phi, uf[c], bacc[3 * i + c]);
+            }
+        }
+        if (pass == 0)
+#pragma unroll
+            for (int e = 0; e < NMOM; ++e) A.acc[(int64_t)e * A.M + m] = mom[e];
+#pragma unroll
+        for (int e = 0; e < NB * 3; ++e) A.acc[(int64_t)(NMOM + pass * NB * 3 + e) * A.M + m] = bacc[e];
+    }
+}
+
+// Cholesky of Phi^T Phi (assembled from the moments into this thread's column of shared memory,
+// stride FEAT_THREADS) and the coefficients of the monomials of degree <= 3 for the 6 density
+// components, as derivatives in units of h: out[k][r].  False with fewer than 15 neighbours or a
+// pivot <= 0.
+__device__ bool fit_solve(const FitArgs &A, int64_t m, double *L, double out[10][NRHS]) {
+    const int S = FEAT_THREADS;
+    if (A.cnt[m] < NB) return false;
+    for (int i = 0; i < NB; ++i)
+        for (int k = 0; k <= i; ++k)
+            L[(i * (i + 1) / 2 + k) * S] = A.acc[(int64_t)mom_idx(mono_i(i) + mono_i(k), mono_j(i) + mono_j(k)) * A.M + m];
     for (int i = 0; i < NB; ++i)
         for (int j = 0; j <= i; ++j) {
-            double s = A[(i * (i + 1) / 2 + j) * S];
-            for (int q = 0; q < j; ++q) s -= A[(i * (i + 1) / 2 + q) * S] * A[(j * (j + 1) / 2 + q) * S];
+            double s = L[(i * (i + 1) / 2 + j) * S];
+            for (int q = 0; q < j; ++q) s -= L[(i * (i + 1) / 2 + q) * S] * L[(j * (j + 1) / 2 + q) * S];
             if (i == j) {
                 if (!(s > 0.0)) return false;
-                A[(i * (i + 1) / 2 + i) * S] = sqrt(s);
+                L[(i * (i + 1) / 2 + i) * S] = sqrt(s);
             } else {
-                A[(i * (i + 1) / 2 + j) * S] = s / A[(j * (j + 1) / 2 + j) * S];
+                L[(i * (i + 1) / 2 + j) * S] = s / L[(j * (j + 1) / 2 + j) * S];
             }
         }
-    for (int c = 0; c < NRHS; ++c) {
+    for (int rc = 0; rc < NRHS; ++rc) {
         double y[NB];
-        for (int i = 0; i < NB; ++i) {  // L y = B_c
-            double s = B[(i * NRHS + c) * S];
-            for (int q = 0; q < i; ++q) s -= A[(i * (i + 1) / 2 + q) * S] * y[q];
-            y[i] = s / A[(i * (i + 1) / 2 + i) * S];
+        for (int i = 0; i < NB; ++i) {  // L y = (Phi^T U)_rc
+            double s = A.acc[(int64_t)(NMOM + (rc / 3) * NB * 3 + 3 * i + rc % 3) * A.M + m];
+            for (int q = 0; q < i; ++q) s -= L[(i * (i + 1) / 2 + q) * S] * y[q];
+            y[i] = s / L[(i * (i + 1) / 2 + i) * S];
         }
         for (int i = NB - 1; i >= 0; --i) {  // L^T x = y
             double s = y[i];
-            for (int q = i + 1; q < NB; ++q) s -= A[(q * (q + 1) / 2 + i) * S] * y[q];
-            y[i] = s / A[(i * (i + 1) / 2 + i) * S];
+            for (int q = i + 1; q < NB; ++q) s -= L[(q * (q + 1) / 2 + i) * S] * y[q];
+            y[i] = s / L[(i * (i + 1) / 2 + i) * S];
         }
-        for (int k = 0; k < 10; ++k) out[k][c] = y[k] * deriv_factor(k);
+        for (int k = 0; k < 10; ++k) out[k][rc] = y[k] * deriv_factor(k);
     }
     return true;
 }
 
 struct FeatArgs {
-    SurfDev sd;
-    const double *fq;
-    const double *x0, *n0, *b;
+    FitArgs fit;
     const double *u2, *v2, *gamma, *u3, *v3;  // u3, v3 optional (training targets)
-    int64_t M;
-    double h, rho0, rho1, Rc;
+    double rho0, rho1;
     int nd;            // 1 or 2 deltas
     double gamma0;     // |gamma| at b = 0 (nd = 2)
-    double c[3], a[3];
     float *Xs, *Xd, *Ts, *Td;  // sample records (M x XSTR) and targets (M x TSTR) of both layers
     double *scale;             // (M x 2) density scales, 0 = no correction
     int *valid;
 };
 
-// One thread per target: frame, geometry, density jets (both layers), training targets when
-// u3, v3 are given.
+// One thread per target: frame, geometry, density jets (both layers) from the fit, training
+// targets when u3, v3 are given.
 __global__ void __launch_bounds__(FEAT_THREADS) k_features(FeatArgs A) {
     extern __shared__ double fsm[];
+    const FitArgs &F = A.fit;
     const int64_t m = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (m >= A.M) return;
+    if (m >= F.M) return;
     double t1[3], t2[3], n[3], k1, k2;
-    target_frame(A.x0, A.n0, m, A.c, A.a, t1, t2, n, k1, k2);
-    const double bm = A.b[m];
-    const double lam = bm / (A.rho0 * A.h);
-    bool ok = fabs(bm) <= A.Rc && fabs(lam) <= 64.0;
+    target_frame(F.x0, F.n0, m, F.c, F.a, t1, t2, n, k1, k2);
+    const double bm = F.b[m];
+    const double lam = bm / (A.rho0 * F.h);
+    bool ok = fabs(bm) <= F.Rc && fabs(lam) <= 64.0;
     double J[10][NRHS];
-    if (ok) {
-        const double x0[3] = {A.x0[3 * m], A.x0[3 * m + 1], A.x0[3 * m + 2]};
-        ok = fit_jets(A.sd, A.fq, x0, t1, t2, n, A.h, fsm + threadIdx.x, fsm + NPK * FEAT_THREADS + threadIdx.x, J);
-    }
+    if (ok) ok = fit_solve(F, m, fsm + threadIdx.x, J);
     bool any = false;
     for (int layer = 0; layer < 2; ++layer) {
         const int nj = jets_of_layer(layer);
         float *X = (layer == 0 ? A.Xs : A.Xd) + m * XSTR;
         X[0] = (float)lam;
-        X[1] = (float)(k1 * A.h);
-        X[2] = (float)(k2 * A.h);
+        X[1] = (float)(k1 * F.h);
+        X[2] = (float)(k2 * F.h);
         X[3] = (float)A.rho0;
         X[4] = (float)A.rho1;
         for (int e = NGEOM; e < JET_OFF; ++e) X[e] = 0.0f;
@@ -326,7 +404,7 @@ __global__ void __launch_bounds__(FEAT_THREADS) k_features(FeatArgs A) {
         if (T && u3) {
             const double *ur = (layer == 0 ? A.u2 : A.v2) + 3 * m;
             const double g = A.gamma[m];
-            const double hp = layer == 0 ? A.h : 1.0;
+            const double hp = layer == 0 ? F.h : 1.0;
             double cv[3] = {0.0, 0.0, 0.0}, w = 0.0;
             if (lok && A.nd == 2 && fabs(g) >= 0.01 * A.gamma0) {
                 for (int i = 0; i < 3; ++i) cv[i] = (ur[i] - u3[3 * m + i]) / g;
@@ -845,38 +923,52 @@ namespace {
 int features(ers_surface *s, const ers_params *p, int64_t M, const double *x0, const double *n0, const double *b,
              const double *u2, const double *v2, const double *gamma, const double *u3, const double *v3, float *Xs,
              float *Xd, float *Ts, float *Td, double *scale, int *valid, int nd, cudaStream_t st) {
+    // fit scratch: neighbour lists [FIT_LMAX][M] ints, counts [M] ints, accumulators [NACC][M] doubles
+    const size_t lbytes = sizeof(int) * ((size_t)FIT_LMAX * M + M);
+    const size_t off = (lbytes + 255) / 256 * 256;
+    int rc = grow(s->fitw, off + sizeof(double) * (size_t)NACC * M);
+    if (rc != ERS_OK) return rc;
     FeatArgs A;
-    A.sd = surf_dev(s);
-    A.fq = s->fq;
-    A.x0 = x0;
-    A.n0 = n0;
-    A.b = b;
+    FitArgs &F = A.fit;
+    F.sd = surf_dev(s);
+    F.fq = s->fq;
+    F.x0 = x0;
+    F.n0 = n0;
+    F.b = b;
+    F.M = M;
+    F.h = s->h;
+    F.Rc = p->cutoff_t * p->rho[nd - 1] * s->h;
+    for (int i = 0; i < 3; ++i) {
+        F.c[i] = s->c[i];
+        F.a[i] = s->a[i];
+    }
+    F.list = (int *)s->fitw.ptr;
+    F.cnt = F.list + (size_t)FIT_LMAX * M;
+    F.acc = (double *)((char *)s->fitw.ptr + off);
     A.u2 = u2;
     A.v2 = v2;
     A.gamma = gamma;
     A.u3 = u3;
     A.v3 = v3;
-    A.M = M;
-    A.h = s->h;
     A.rho0 = p->rho[0];
     A.rho1 = p->rho[1];
-    A.Rc = p->cutoff_t * p->rho[nd - 1] * s->h;
     A.nd = nd;
     // |gamma| at b = 0: beta = (rho_1, -rho_0) / (rho_1 - rho_0), I2(0) = 1 / (3 sqrt(pi)), so
     // |gamma(0)| = rho_0 rho_1 (rho_0 + rho_1) / (3 sqrt(pi))
     A.gamma0 = p->rho[0] * p->rho[1] * (p->rho[0] + p->rho[1]) / (3.0 * 1.7724538509055160273);
-    for (int i = 0; i < 3; ++i) {
-        A.c[i] = s->c[i];
-        A.a[i] = s->a[i];
-    }
     A.Xs = Xs;
     A.Xd = Xd;
     A.Ts = Ts;
     A.Td = Td;
     A.scale = scale;
     A.valid = valid;
-    cudaError_t e = cudaFuncSetAttribute(k_features, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)FEAT_SMEM);
-    if (e != cudaSuccess) return cuda_fail(e, "closure features kernel: shared memory");
+    const unsigned g128 = (unsigned)((M + 127) / 128);
+    k_fit_scan<<<g128, 128, 0, st>>>(F);
+    k_fit_accum<<<g128, 128, 0, st>>>(F);
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_features, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)FEAT_SMEM);
+    if (e != cudaSuccess) return cuda_fail(e, "closure density-fit kernels");
     k_features<<<(unsigned)((M + FEAT_THREADS - 1) / FEAT_THREADS), FEAT_THREADS, FEAT_SMEM, st>>>(A);
     e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "closure features kernel");

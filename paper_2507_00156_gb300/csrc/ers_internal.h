@@ -103,6 +103,7 @@ struct ers_surface {
     bool has_f = false, has_q = false;
     // work buffers (grow-only)
     ers::Scratch part, cp, host_io, counts;
+    ers::Scratch fitw;  // the learned closure's density fits: neighbour lists and normal equations
     // densities of several right-hand sides (ers_set_density_multi), cell-sorted: FP64
     // [N][nrhs][6] (w f, q) and the FP32 far-field record [N][batch_rec32_floats(nrhs)]
     ers::Scratch dens64, dens32;

@@ -32,24 +32,24 @@ constexpr int TS32 = 256;  // sources per FP32 tile (one centre c_tile per tile)
 // s = 32 tau - (2 i + 1) in [-1, 1].  The near field uses it only for t <= 4.7 (tau <= 22.09);
 // beyond that the defects 1 - s_p are evaluated directly.
 // Host copy: [interval][p][7] monomial coefficients, highest degree first.
-// Device copy (TAB_DEV_BYTES): TAB_N x [p][4] doubles (degrees 3..0), then TAB_N x [p] float4
-// (degrees 6, 5, 4 and the interval offset 2 i + 1).  Degrees 4..6 carry less than 2e-8 of the
-// value on every interval, so their FP32 evaluation costs at most ~2e-15 relative.
+// Device copy (TAB_DEV_BYTES): per interval and function three float4: degrees 6, 5, 4 as floats
+// with the interval offset 2 i + 1, then degrees 3..0 as float pairs (hi, lo).  Degrees 4..6
+// carry less than 2e-8 of the value on every interval, so their FP32 evaluation costs at most
+// ~2e-15 relative; degrees 3..0 are evaluated in float-pair arithmetic (~2^-46 relative) on the
+// FP32 pipe, which on this part runs 64 times the FP64 rate.
 constexpr int TAB_INV_W = 16;     // intervals per unit tau
 constexpr int TAB_N = 384;        // tau in [0, 24)
 constexpr int TAB_DEG = 6;
 constexpr int TAB_NC = TAB_DEG + 1;
 constexpr double TAB_TAU_MAX = 24.0;
-constexpr int TAB_DEV_DOUBLES = TAB_N * 3 * 4;
-constexpr size_t TAB_DEV_BYTES = (size_t)TAB_DEV_DOUBLES * 8 + (size_t)TAB_N * 3 * 16;
+constexpr size_t TAB_DEV_BYTES = (size_t)TAB_N * 3 * 48;
 // Table of sigma#_p(tau) = s#_p(t)/t^p for the on-surface functions of Sec. 2.1, the same layout
 // with intervals of width 1/32 on tau in [0, 64) (cutoff_t up to 8; no direct-defect path): their
 // polynomial-times-Gaussian parts vary faster than sigma_p, and at width 1/32 degrees 4..6 still
 // carry less than 2e-8 of the value.
 constexpr int SH_INV_W = 32;
 constexpr int SH_N = 2048;
-constexpr int SH_DEV_DOUBLES = SH_N * 3 * 4;
-constexpr size_t SH_DEV_BYTES = (size_t)SH_DEV_DOUBLES * 8 + (size_t)SH_N * 3 * 16;
+constexpr size_t SH_DEV_BYTES = (size_t)SH_N * 3 * 48;
 
 struct Grid {
     double origin[3];
@@ -343,6 +343,52 @@ __device__ __forceinline__ double float_to_double(float f) {
     const unsigned lo = b << 29;
     return __longlong_as_double(((long long)hi << 32) | lo);
 }
+
+// ------------------------------------------------------------------------------------------
+// Float pairs: x = h + l with two floats carries ~47 significant bits.  The operations below run
+// on the FP32 and integer pipes (the FP64 pipe of this part is 1/64 of the FP32 rate); every
+// product and sum is written with explicit rounding intrinsics so that no contraction changes
+// the error-free transformations.
+// ------------------------------------------------------------------------------------------
+
+// x (|x| >= 2^-126 or 0) -> h = x truncated to 24 significant bits, l = the next 29 bits of x's
+// significand rounded to a float: |x - h - l| <= 2^-47 |x|.  Integer and int-to-float conversion
+// instructions only.
+__device__ __forceinline__ void split_pair(double x, float &h, float &l) {
+    h = approx_float(x);
+    const long long bits = __double_as_longlong(x);
+    const int low = (int)(bits & ((1LL << 29) - 1));              // significand bits below the float's
+    const int ex = (int)((bits >> 52) & 0x7ff) - 1075 + 127;       // biased float exponent of 2^(e - 52)
+    float r = (h != 0.0f && ex > 0) ? __fmul_rn(__int2float_rn(low), __int_as_float(ex << 23)) : 0.0f;
+    l = bits < 0 ? -r : r;
+}
+
+// p = p s + c in float pairs (products by FMA, the sum by Knuth's two-sum, then renormalized).
+__device__ __forceinline__ void pair_mad(float &ph, float &pl, float sh, float sl, float ch, float cl) {
+    const float th = __fmul_rn(ph, sh);
+    const float te = __fmaf_rn(ph, sl, __fmaf_rn(pl, sh, __fmaf_rn(ph, sh, -th)));
+    const float u = __fadd_rn(th, ch);
+    const float v = __fsub_rn(u, th);
+    const float e = __fadd_rn(__fsub_rn(th, __fsub_rn(u, v)), __fsub_rn(ch, v));
+    const float w = __fadd_rn(__fadd_rn(e, te), cl);
+    ph = __fadd_rn(u, w);
+    pl = __fsub_rn(w, __fsub_rn(ph, u));
+}
+
+// k = k + a b in float pairs.
+__device__ __forceinline__ void pair_acc(float &kh, float &kl, float ah, float al, float bh, float bl) {
+    const float th = __fmul_rn(ah, bh);
+    const float te = __fmaf_rn(ah, bl, __fmaf_rn(al, bh, __fmaf_rn(ah, bh, -th)));
+    const float u = __fadd_rn(kh, th);
+    const float v = __fsub_rn(u, kh);
+    const float e = __fadd_rn(__fsub_rn(kh, __fsub_rn(u, v)), __fsub_rn(th, v));
+    const float w = __fadd_rn(__fadd_rn(e, te), kl);
+    kh = __fadd_rn(u, w);
+    kl = __fsub_rn(w, __fsub_rn(kh, u));
+}
+
+// h + l as a double (one FP64 add).
+__device__ __forceinline__ double pair_to_double(float h, float l) { return float_to_double(h) + float_to_double(l); }
 
 }  // namespace ers
 #endif

@@ -211,20 +211,25 @@ const double *sigma_sharp_table_host() {
 }
 
 namespace {
-// Device copy: nint x [p][4] doubles (degrees 3..0), then nint x [p] float4 (degrees 6, 5, 4
-// and the interval offset 2 i + 1).
+// Device copy: per interval i and function p three float4:
+//   (c6, c5, c4, 2 i + 1), (c3 hi, c3 lo, c2 hi, c2 lo), (c1 hi, c1 lo, c0 hi, c0 lo),
+// degrees 6..4 as floats, degrees 3..0 as float pairs (hi = the coefficient rounded to a float,
+// lo = the rest rounded to a float: hi + lo carries the coefficient to ~2^-48).
 void device_layout(const double *h, int nint, void *dst) {
-    double *d = static_cast<double *>(dst);
-    float *f = reinterpret_cast<float *>(d + (size_t)nint * 12);
+    float *f = static_cast<float *>(dst);
     for (int i = 0; i < nint; ++i)
         for (int p = 0; p < 3; ++p) {
             const double *c = h + ((size_t)i * 3 + p) * TAB_NC;  // degrees 6..0
-            for (int e = 0; e < 4; ++e) d[((size_t)i * 3 + p) * 4 + e] = c[3 + e];
-            float *q = f + ((size_t)i * 3 + p) * 4;
+            float *q = f + ((size_t)i * 3 + p) * 12;
             q[0] = (float)c[0];
             q[1] = (float)c[1];
             q[2] = (float)c[2];
             q[3] = (float)(2 * i + 1);
+            for (int e = 0; e < 4; ++e) {
+                const float hi = (float)c[3 + e];
+                q[4 + 2 * e] = hi;
+                q[5 + 2 * e] = (float)(c[3 + e] - (double)hi);
+            }
         }
 }
 }  // namespace

@@ -32,9 +32,11 @@ using namespace nearc;
 constexpr int WPB = 4;  // warps per block
 constexpr int NEAR_MIN_BLOCKS = 3;
 
-template <int CLS, int PREC, bool SL, bool DL, int ND>
+// One near pair of class cls (run-time for the classes with table-path deltas, ALLDEF = false;
+// ALLDEF = true: cls = ND, every delta on the defect path).
+template <bool ALLDEF, int PREC, bool SL, bool DL, int ND>
 __device__ __forceinline__ void process(const EvalArgs &A, const Geom &T, const ScanParams &P, double c,
-                                        const double q0[3], const double *__restrict__ tab, int64_t j,
+                                        const double q0[3], const double *__restrict__ tab, int64_t j, int cls,
                                         double accU[3], double &accN, double accD[3], int npairs[NCLS_MAX],
                                         int nunreg[MAXD]) {
     const double2 *r = reinterpret_cast<const double2 *>(A.sd.rec + j * REC);
@@ -49,7 +51,8 @@ __device__ __forceinline__ void process(const EvalArgs &A, const Geom &T, const 
     const double dz = __dsub_rn(T.y[2], xs[2]);
     const double r2 = dist2_fp64(dx, dy, dz);
     if (!is_near<PREC>(A.sd, T, j, r2, A.Rc, P.rc2f)) return;
-    ++npairs[CLS];
+#pragma unroll
+    for (int k = 0; k < NCLS_MAX; ++k) npairs[k] += k == cls;
     {  // pairs by number of deltas with r > cutoff_t delta_k (the method's own count of regularized terms)
         const float r2f = approx_float_pos(r2);
         int u = (r2f > P.cut2[0]) + (r2f > P.cut2[1]);
@@ -59,11 +62,11 @@ __device__ __forceinline__ void process(const EvalArgs &A, const Geom &T, const 
     }
     double K1, K3, K5;
     float Lf;
-    kernel_factors<CLS, ND>(T, P, tab, r2, K1, K3, K5, Lf);
+    kernel_factors_rt<ALLDEF, ND>(T, P, tab, r2, cls, K1, K3, K5, Lf);
     if (SL) sl_accumulate(dx, dy, dz, K1, K3, c, wf, wn, accU);
     if (DL) {
         const double W = fma(dz, wn[2], fma(dy, wn[1], dx * wn[0]));
-        if (CLS >= ND) {  // every delta on the defect path: L and what it multiplies in FP32
+        if (ALLDEF) {  // every delta on the defect path: L and what it multiplies in FP32
             const float nmf = fmaf(approx_float(T.n0[2]), approx_float(wn[2]),
                                    fmaf(approx_float(T.n0[1]), approx_float(wn[1]),
                                         approx_float(T.n0[0]) * approx_float(wn[0])));
@@ -202,12 +205,8 @@ __device__ __forceinline__ void near_target(const EvalArgs &A, const ScanParams 
     int nunreg[MAXD] = {0, 0, 0, 0};         // near pairs by number of deltas beyond the cutoff
     scan_near<NC>(A.sd, T, P, sq, lane, [&](int cls, int jj, bool valid) {
         if (!valid) return;
-        if (cls == 0) process<0, PREC, SL, DL, ND>(A, T, P, c, q0, tab, jj, accU, accN, accD, npairs, nunreg);
-        else if (cls == 1) process<1, PREC, SL, DL, ND>(A, T, P, c, q0, tab, jj, accU, accN, accD, npairs, nunreg);
-        else if (cls == 2) process<2, PREC, SL, DL, ND>(A, T, P, c, q0, tab, jj, accU, accN, accD, npairs, nunreg);
-        else if (NC == 4 || cls == 3)
-            process<3, PREC, SL, DL, ND>(A, T, P, c, q0, tab, jj, accU, accN, accD, npairs, nunreg);
-        else process<4, PREC, SL, DL, ND>(A, T, P, c, q0, tab, jj, accU, accN, accD, npairs, nunreg);
+        if (cls < ND) process<false, PREC, SL, DL, ND>(A, T, P, c, q0, tab, jj, cls, accU, accN, accD, npairs, nunreg);
+        else process<true, PREC, SL, DL, ND>(A, T, P, c, q0, tab, jj, ND, accU, accN, accD, npairs, nunreg);
     });
     for (int i = 0; i < 3; ++i) {
         accU[i] = warp_sum(accU[i]);

@@ -36,6 +36,7 @@ struct Geom {
     float yh[3], yl[3];        // y = yh + yl in floats (mixed-mode classification)
     float id2h[MAXD], id2l[MAXD]; // 1/delta_k^2 = id2h + id2l in floats
     float alf[MAXD];           // extrapolation weights in FP32 (for the small defects 1 - s_p)
+    float adh[3][MAXD], adl[3][MAXD];  // alpha_k / delta_k^p (p = 1, 3, 5) as float pairs
     float tcf2;             // cutoff_t^2: s_p := 1 beyond t = cutoff_t
     bool cut_small;         // cutoff_t < DEFECT_T: the table path may meet the cutoff
 };
@@ -227,6 +228,11 @@ __device__ __forceinline__ void load_geom(int lane, const double *y, const doubl
         T.ad5[k] = al[k] * id * id * id * id * id;
         T.id2h[k] = (float)T.invd2[k];
         T.id2l[k] = (float)(T.invd2[k] - (double)T.id2h[k]);
+        const double adp[3] = {T.ad1[k], T.ad3[k], T.ad5[k]};
+        for (int p = 0; p < 3; ++p) {
+            T.adh[p][k] = (float)adp[p];
+            T.adl[p][k] = (float)(adp[p] - (double)T.adh[p][k]);
+        }
     }
     T.apre[0] = al[0];
     T.apre[1] = al[0] + al[1];
@@ -254,29 +260,44 @@ __device__ __forceinline__ bool is_near(const SurfDev &s, const Geom &T, int64_t
 // r > min(DEFECT_T, cutoff_t) delta_k and take the defect path below; the others take sigma_p
 // from the interpolation table.  ND = number of deltas in use (3 for the method; 2 or 1 for the
 // learned closure).
-// sigma_p(tau) (or sigma#_p with the on-surface table) from a device table of INV_W intervals
-// per unit tau and N intervals: degrees 6..4 of the local polynomial in FP32, 3..0 in FP64 (Horner).
+// sigma_p(tau) (or sigma#_p with the on-surface table) from a device table of INV_W intervals per
+// unit tau and N intervals, for the local variable s (in [-1, 1] up to the interval-choice bound
+// below): degrees 6..4 of the local polynomial in FP32, 3..0 in float pairs (Horner), results
+// as float pairs sg[p] = (hi, lo), relative error ~2e-15 (the interpolation) + ~2^-46 (the pairs).
+template <int N>
+__device__ __forceinline__ void table_pairs(const float4 *__restrict__ ftab, int idx, double s, float sg[3][2]) {
+    float sh, sl;
+    split_pair(s, sh, sl);
+    const float4 *t = ftab + (int64_t)idx * 9;
+#pragma unroll 1
+    for (int p = 0; p < 3; ++p) {
+        const float4 a = __ldg(t + 3 * p), c32 = __ldg(t + 3 * p + 1), c10 = __ldg(t + 3 * p + 2);
+        float ph = fmaf(fmaf(a.x, sh, a.y), sh, a.z), pl = 0.0f;
+        pair_mad(ph, pl, sh, sl, c32.x, c32.y);
+        pair_mad(ph, pl, sh, sl, c32.z, c32.w);
+        pair_mad(ph, pl, sh, sl, c10.x, c10.y);
+        pair_mad(ph, pl, sh, sl, c10.z, c10.w);
+        sg[p][0] = ph;
+        sg[p][1] = pl;
+    }
+}
+
+// sigma_p at tau as doubles (the on-surface path).
 template <int INV_W, int N>
 __device__ __forceinline__ void table_sigma(const double *__restrict__ tab, double tau, double &s1, double &s2,
                                             double &s3) {
-    const float4 *__restrict__ ftab = reinterpret_cast<const float4 *>(tab + N * 12);
+    const float4 *ftab = reinterpret_cast<const float4 *>(tab);
     int idx = (int)(approx_float_pos(tau) * (float)INV_W);
     idx = min(idx, N - 1);
-    const float4 f1 = __ldg(ftab + 3 * idx), f2 = __ldg(ftab + 3 * idx + 1), f3 = __ldg(ftab + 3 * idx + 2);
-    const double s = fma(tau, 2.0 * INV_W, -float_to_double(f1.w));  // local variable in [-1, 1]
-    const float sf = approx_float(s);
-    s1 = float_to_double(fmaf(fmaf(f1.x, sf, f1.y), sf, f1.z));
-    s2 = float_to_double(fmaf(fmaf(f2.x, sf, f2.y), sf, f2.z));
-    s3 = float_to_double(fmaf(fmaf(f3.x, sf, f3.y), sf, f3.z));
-    const double2 *cd = reinterpret_cast<const double2 *>(tab + idx * 12);
-    const double2 a01 = __ldg(cd), a23 = __ldg(cd + 1), b01 = __ldg(cd + 2);
-    const double2 b23 = __ldg(cd + 3), c01 = __ldg(cd + 4), c23 = __ldg(cd + 5);
-    s1 = fma(fma(fma(fma(s1, s, a01.x), s, a01.y), s, a23.x), s, a23.y);
-    s2 = fma(fma(fma(fma(s2, s, b01.x), s, b01.y), s, b23.x), s, b23.y);
-    s3 = fma(fma(fma(fma(s3, s, c01.x), s, c01.y), s, c23.x), s, c23.y);
+    const double s = fma(tau, 2.0 * INV_W, -float_to_double((float)(2 * idx + 1)));  // local variable in [-1, 1]
+    float sg[3][2];
+    table_pairs<N>(ftab, idx, s, sg);
+    s1 = pair_to_double(sg[0][0], sg[0][1]);
+    s2 = pair_to_double(sg[1][0], sg[1][1]);
+    s3 = pair_to_double(sg[2][0], sg[2][1]);
 }
 
-// table_sigma at tau = r^2 / delta^2 without forming tau in FP64: the interval from the FP32
+// table_pairs at tau = r^2 / delta^2 without forming tau in FP64: the interval from the FP32
 // product r2f idf (r2f, idf: r^2 and 1/delta^2 as floats), the local variable as
 // r^2 (2 INV_W / delta^2) - (2 i + 1) in one FMA.  The FP32 product carries three roundings
 // (r2f, idf and the product: at most ~1.8e-7 of tau), so near an interval end it can pick the
@@ -284,34 +305,27 @@ __device__ __forceinline__ void table_sigma(const double *__restrict__ tab, doub
 // 2 INV_W tau 1.8e-7 (below 1.4e-4 for INV_W = 16 and tau < 24), where each piece is still
 // accurate to ~1e-15 (checked on the host at |s| = 1 + 2e-4 for every interval).
 template <int INV_W, int N>
-__device__ __forceinline__ void table_sigma_r2(const double *__restrict__ tab, double r2, float r2f, float idf,
-                                               double s2w, double &s1, double &s2, double &s3) {
-    const float4 *__restrict__ ftab = reinterpret_cast<const float4 *>(tab + N * 12);
+__device__ __forceinline__ void table_pairs_r2(const double *__restrict__ tab, double r2, float r2f, float idf,
+                                               double s2w, float sg[3][2]) {
+    const float4 *ftab = reinterpret_cast<const float4 *>(tab);
     int idx = (int)(r2f * idf * (float)INV_W);
     idx = min(idx, N - 1);
-    const float4 f1 = __ldg(ftab + 3 * idx), f2 = __ldg(ftab + 3 * idx + 1), f3 = __ldg(ftab + 3 * idx + 2);
-    const double s = fma(r2, s2w, -float_to_double(f1.w));
-    const float sf = approx_float(s);
-    s1 = float_to_double(fmaf(fmaf(f1.x, sf, f1.y), sf, f1.z));
-    s2 = float_to_double(fmaf(fmaf(f2.x, sf, f2.y), sf, f2.z));
-    s3 = float_to_double(fmaf(fmaf(f3.x, sf, f3.y), sf, f3.z));
-    const double2 *cd = reinterpret_cast<const double2 *>(tab + idx * 12);
-    const double2 a01 = __ldg(cd), a23 = __ldg(cd + 1), b01 = __ldg(cd + 2);
-    const double2 b23 = __ldg(cd + 3), c01 = __ldg(cd + 4), c23 = __ldg(cd + 5);
-    s1 = fma(fma(fma(fma(s1, s, a01.x), s, a01.y), s, a23.x), s, a23.y);
-    s2 = fma(fma(fma(fma(s2, s, b01.x), s, b01.y), s, b23.x), s, b23.y);
-    s3 = fma(fma(fma(fma(s3, s, c01.x), s, c01.y), s, c23.x), s, c23.y);
+    const double s = fma(r2, s2w, -float_to_double((float)(2 * idx + 1)));
+    table_pairs<N>(ftab, idx, s, sg);
 }
 
 // Lf: when every delta in use is on the defect path (CLS >= ND), L = r^2 K5 - K3 = (E3 - E5)/r^3
 // in FP32 (see dl_accumulate_defect); 0 otherwise.
-template <int CLS, int ND = 3>
-__device__ __forceinline__ void kernel_factors(const Geom &T, const ScanParams &P, const double *__restrict__ tab,
-                                               double r2, double &K1, double &K3, double &K5, float &Lf) {
-    constexpr int NDEF = CLS < ND ? CLS : ND;  // defect-path deltas that carry weight
+// The class is a run-time value (uniform over a batch of pairs) for the classes with table-path
+// deltas (ALLDEF = false: one code path for all of them keeps the kernel within the instruction
+// cache); ALLDEF = true is the class with every delta on the defect path (cls = ND).
+template <bool ALLDEF, int ND>
+__device__ __forceinline__ void kernel_factors_rt(const Geom &T, const ScanParams &P, const double *__restrict__ tab,
+                                                  double r2, int cls, double &K1, double &K3, double &K5, float &Lf) {
+    const int NDEF = ALLDEF ? ND : cls;  // defect-path deltas that carry weight
     Lf = 0.0f;
     double ri = 0.0, ri3 = 0.0, ri5 = 0.0;
-    if (CLS >= 1) {
+    if (ALLDEF || cls >= 1) {
         // r / delta_k > DEFECT_T: s_p = 1 - eps_p with eps_1 = erfc t, eps_2 = eps_1 + (2/sqrt pi) t e^{-t^2},
         // eps_3 = eps_1 + (2/sqrt pi)(t + 2/3 t^3) e^{-t^2} (Eqs. (s1)-(s3)), all below 2.1e-8, and
         // eps_p = 0 where t > cutoff_t (Sec. 3.2).  The term is (sum_k alpha_k - sum_k alpha_k eps_p(t_k)) / r^p.
@@ -323,7 +337,7 @@ __device__ __forceinline__ void kernel_factors(const Geom &T, const ScanParams &
         const float r2h = approx_float_pos(r2);
         const float r2l = approx_float(r2 - float_to_double(r2h));
         float E1 = 0.0f, E3 = 0.0f, E5 = 0.0f;
-#pragma unroll
+#pragma unroll 1
         for (int k = 0; k < NDEF; ++k) {
             const float th = r2h * T.id2h[k];
             const float tl = fmaf(r2h, T.id2h[k], -th) + fmaf(r2h, T.id2l[k], r2l * T.id2h[k]);
@@ -357,34 +371,57 @@ __device__ __forceinline__ void kernel_factors(const Geom &T, const ScanParams &
         K1 = -float_to_double(E1 * round_float_pos(ri));
         K3 = -float_to_double(E3 * rf3);
         K5 = -float_to_double(E5 * round_float_pos(ri5));
-        if (CLS >= ND) Lf = (E3 - E5) * rf3;
+        if (ALLDEF) Lf = (E3 - E5) * rf3;
     } else {
         K1 = 0.0;
         K3 = 0.0;
         K5 = 0.0;
     }
-    const float r2f = approx_float_pos(r2);
+    if (!ALLDEF) {
+        // the table-path deltas: sum_k (alpha_k / delta_k^p) sigma_p(tau_k) in float pairs, one
+        // FP64 add per factor at the end
+        const float r2f = approx_float_pos(r2);
+        float kh[3] = {0.0f, 0.0f, 0.0f}, kl[3] = {0.0f, 0.0f, 0.0f};
+        // a rolled loop: the unrolled float-pair code of several deltas overflows the instruction cache
+#pragma unroll 1
+        for (int k = cls; k < ND; ++k) {
+            float sg[3][2];
+            table_pairs_r2<TAB_INV_W, TAB_N>(tab, r2, r2f, T.id2h[k], T.s2w[k], sg);
+            if (T.cut_small && r2f * T.id2h[k] >= (1.0f - CUT_BAND) * T.tcf2 && r2 > P.cut2d[k]) {
+                // t just beyond a cutoff below DEFECT_T: s_p := 1, sigma_p = 1/t^p (Sec. 3.2)
+                const double tau = r2 * T.invd2[k];
+                const double s1 = rsqrt(tau), s2 = s1 * s1 * s1, s3 = s2 * s1 * s1;
+                split_pair(s1, sg[0][0], sg[0][1]);
+                split_pair(s2, sg[1][0], sg[1][1]);
+                split_pair(s3, sg[2][0], sg[2][1]);
+            }
 #pragma unroll
-    for (int k = CLS; k < ND; ++k) {
-        double s1, s2, s3;
-        table_sigma_r2<TAB_INV_W, TAB_N>(tab, r2, r2f, T.id2h[k], T.s2w[k], s1, s2, s3);
-        if (T.cut_small && r2f * T.id2h[k] >= (1.0f - CUT_BAND) * T.tcf2 && r2 > P.cut2d[k]) {
-            // t just beyond a cutoff below DEFECT_T: s_p := 1, sigma_p = 1/t^p (Sec. 3.2)
-            const double tau = r2 * T.invd2[k];
-            s1 = rsqrt(tau);
-            s2 = s1 * s1 * s1;
-            s3 = s2 * s1 * s1;
+            for (int p = 0; p < 3; ++p) pair_acc(kh[p], kl[p], T.adh[p][k], T.adl[p][k], sg[p][0], sg[p][1]);
         }
-        K1 = fma(T.ad1[k], s1, K1);
-        K3 = fma(T.ad3[k], s2, K3);
-        K5 = fma(T.ad5[k], s3, K5);
+        const double t1 = pair_to_double(kh[0], kl[0]), t3 = pair_to_double(kh[1], kl[1]),
+                     t5 = pair_to_double(kh[2], kl[2]);
+        if (cls >= 1) {
+            K1 += t1;
+            K3 += t3;
+            K5 += t5;
+        } else {
+            K1 = t1;
+            K3 = t3;
+            K5 = t5;
+        }
     }
-    if (CLS >= 1) {
-        const double Ain = T.apre[CLS - 1];
+    if (ALLDEF || cls >= 1) {
+        const double Ain = T.apre[(ALLDEF ? ND : cls) - 1];
         K1 = fma(Ain, ri, K1);
         K3 = fma(Ain, ri3, K3);
         K5 = fma(Ain, ri5, K5);
     }
+}
+
+template <int CLS, int ND = 3>
+__device__ __forceinline__ void kernel_factors(const Geom &T, const ScanParams &P, const double *__restrict__ tab,
+                                               double r2, double &K1, double &K3, double &K5, float &Lf) {
+    kernel_factors_rt<(CLS >= ND), ND>(T, P, tab, r2, CLS, K1, K3, K5, Lf);
 }
 
 // Single-layer contraction: accU += K1 g + K3 d (d.g), g = wf - c wn.

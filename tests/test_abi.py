@@ -89,6 +89,54 @@ def _sigma_mp(mp, tau):
 NINT, DEG, INV_W = 384, 6, 16  # intervals of width 1/16 on tau in [0, 24)
 
 
+F32 = np.float32
+
+
+def _fmaf(a, b, c):
+    """Fused multiply-add of floats: the product of two floats is exact in double, so one rounding
+    of the double sum to float (a double rounding only in rare ties, below what the tests resolve)."""
+    return F32(np.float64(a) * np.float64(b) + np.float64(c))
+
+
+def _split_pair(x):
+    """The kernel's split of a double into floats: h = x truncated to 24 bits, l = the rest."""
+    h = F32(x)
+    if abs(float(h)) > abs(x):
+        h = np.nextafter(h, F32(0))
+    return h, F32(x - float(h))
+
+
+def _pair_mad(ph, pl, sh, sl, ch, cl):
+    """p s + c in float pairs, as the kernel's pair_mad (two-product by FMA, two-sum, renormalize)."""
+    th = F32(ph * sh)
+    te = _fmaf(ph, sl, _fmaf(pl, sh, _fmaf(ph, sh, -th)))
+    u = F32(th + ch)
+    v = F32(u - th)
+    e = F32(F32(th - F32(u - v)) + F32(ch - v))
+    w = F32(F32(e + te) + cl)
+    h = F32(u + w)
+    return h, F32(w - F32(h - u))
+
+
+def _layout_eval(rec, s):
+    """One function's 12 floats of the device layout (c6, c5, c4, 2i+1, c3 hi/lo, c2 hi/lo, c1 hi/lo,
+    c0 hi/lo) at the local variable s, evaluated as the kernel does."""
+    sh, sl = _split_pair(s)
+    ph, pl = _fmaf(_fmaf(rec[0], sh, rec[1]), sh, rec[2]), F32(0)
+    for k in range(4):
+        ph, pl = _pair_mad(ph, pl, sh, sl, rec[4 + 2 * k], rec[5 + 2 * k])
+    return float(ph) + float(pl)
+
+
+def _device_layout(fn, nint):
+    nbytes = nint * 3 * 48
+    raw = np.empty(nbytes // 4, dtype=np.float32)
+    fn.argtypes = [ctypes.c_void_p, ctypes.c_int64]
+    assert fn(raw.ctypes.data, nbytes) == 0
+    assert fn(raw.ctypes.data, nbytes - 8) != 0
+    return raw.reshape(nint, 3, 12)
+
+
 def _taus():
     rng = np.random.default_rng(1)
     return np.concatenate([[0.0, 1e-12, 0.0625, 0.125, 22.09, 23.99], rng.uniform(0, 24, 300)])
@@ -113,37 +161,30 @@ def test_sigma_table_accuracy(L):
 
 
 def test_sigma_device_layout_accuracy(L):
-    """The device copy, evaluated as the near-field kernel does (degrees 6..4 in FP32, 3..0 in
-    FP64), stays within ~1e-15 of s_p(t)/t^p: the FP32 part carries less than 2e-8 of the value."""
+    """The device copy, evaluated as the near-field kernel does (degrees 6..4 in FP32, 3..0 in float
+    pairs), stays within ~1e-14 of s_p(t)/t^p: the FP32 part carries less than 2e-8 of the value,
+    the float pairs carry the rest to ~2^-46."""
     mp = pytest.importorskip("mpmath")
     mp.mp.dps = max(mp.mp.dps, 40)
-    nbytes = NINT * 3 * 4 * 8 + NINT * 3 * 16
-    raw = np.empty(nbytes // 8)
-    L.ers_debug_sigma_device.argtypes = [ctypes.c_void_p, ctypes.c_int64]
-    assert L.ers_debug_sigma_device(raw.ctypes.data, nbytes) == 0
-    assert L.ers_debug_sigma_device(raw.ctypes.data, nbytes - 8) != 0
-    dpart = raw[: NINT * 12].reshape(NINT, 3, 4)
-    fpart = raw[NINT * 12:].view(np.float32).reshape(NINT, 3, 4)
-    assert np.array_equal(fpart[:, 0, 3], 2 * np.arange(NINT) + 1)
-    f32 = np.float32
-
-    def fmaf(a, b, c):  # products of floats are exact in double
-        return f32(np.float64(a) * np.float64(b) + np.float64(c))
-
+    tab = _device_layout(L.ers_debug_sigma_device, NINT)
+    assert np.array_equal(tab[:, 0, 3], 2 * np.arange(NINT) + 1)
+    host = np.empty(NINT * 3 * (DEG + 1))
+    assert L.ers_debug_sigma_table(host.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), host.size) == 0
+    host = host.reshape(NINT, 3, DEG + 1)
+    for i in range(NINT):
+        for p_ in range(3):
+            hi_lo = tab[i, p_, 4:].astype(np.float64).reshape(4, 2).sum(1)
+            assert np.all(np.abs(hi_lo - host[i, p_, 3:]) <= 2.0**-46 * np.abs(host[i, p_, 3:]))
+            assert abs(tab[i, p_, 2]) <= 2e-8 * abs(host[i, p_, 6]), (i, p_)
     worst = 0.0
     for tau in _taus():
         i = min(int(np.float32(tau) * INV_W), NINT - 1)
-        s = 2 * INV_W * tau - float(fpart[i, 0, 3])
-        sf = f32(s)
+        s = 2 * INV_W * tau - float(tab[i, 0, 3])
         ref = _sigma_mp(mp, tau)
         for p_ in range(3):
-            c6, c5, c4 = fpart[i, p_, :3]
-            v = float(fmaf(fmaf(c6, sf, c5), sf, c4))
-            for c in dpart[i, p_]:
-                v = v * s + c
+            v = _layout_eval(tab[i, p_], s)
             worst = max(worst, abs(v - float(ref[p_])) / abs(float(ref[p_])))
-            assert abs(c4) <= 2e-8 * abs(dpart[i, p_, 3]), (i, p_)
-    assert worst < 6e-15, worst
+    assert worst < 2e-14, worst
 
 
 def test_sigma_device_layout_beyond_the_interval_ends(L):
@@ -151,20 +192,10 @@ def test_sigma_device_layout_beyond_the_interval_ends(L):
     ~1.8e-7 of tau), so the local variable s = r^2 (2 INV_W / delta^2) - (2 i + 1) can leave [-1, 1]
     by up to 2 INV_W tau 1.8e-7 < 1.4e-4 for tau < 24.  Each piece, evaluated as the kernel does at
     |s| = 1 + 2e-4 (just past that bound, on both sides of every interval), still reproduces
-    s_p(t)/t^p of Eqs. (s1)-(s3) to ~1e-15."""
+    s_p(t)/t^p of Eqs. (s1)-(s3) to ~1e-14."""
     mp = pytest.importorskip("mpmath")
     mp.mp.dps = max(mp.mp.dps, 40)
-    nbytes = NINT * 3 * 4 * 8 + NINT * 3 * 16
-    raw = np.empty(nbytes // 8)
-    L.ers_debug_sigma_device.argtypes = [ctypes.c_void_p, ctypes.c_int64]
-    assert L.ers_debug_sigma_device(raw.ctypes.data, nbytes) == 0
-    dpart = raw[: NINT * 12].reshape(NINT, 3, 4)
-    fpart = raw[NINT * 12:].view(np.float32).reshape(NINT, 3, 4)
-    f32 = np.float32
-
-    def fmaf(a, b, c):
-        return f32(np.float64(a) * np.float64(b) + np.float64(c))
-
+    tab = _device_layout(L.ers_debug_sigma_device, NINT)
     over = 1.0 + 2e-4
     worst = 0.0
     for i in range(NINT):
@@ -172,33 +203,21 @@ def test_sigma_device_layout_beyond_the_interval_ends(L):
             tau = (s + 2 * i + 1) / (2 * INV_W)
             if tau < 0:
                 continue
-            sf = f32(s)
             ref = _sigma_mp(mp, tau)
             for p_ in range(3):
-                c6, c5, c4 = fpart[i, p_, :3]
-                v = float(fmaf(fmaf(c6, sf, c5), sf, c4))
-                for c in dpart[i, p_]:
-                    v = v * s + c
+                v = _layout_eval(tab[i, p_], s)
                 worst = max(worst, abs(v - float(ref[p_])) / abs(float(ref[p_])))
-    assert worst < 8e-15, worst
+    assert worst < 2e-14, worst
 
 
 def test_sigma_sharp_device_layout_accuracy(L):
     """The on-surface table (s#_p(t)/t^p of Sec. 2.1, intervals of 1/32 on tau in [0, 64)), as the
-    kernel evaluates it (degrees 6..4 in FP32, 3..0 in FP64), stays within ~1e-15 of 60-digit values."""
+    kernel evaluates it (degrees 6..4 in FP32, 3..0 in float pairs), stays within ~1e-14 of 60-digit
+    values."""
     mp = pytest.importorskip("mpmath")
     mp.mp.dps = max(mp.mp.dps, 60)
     nint, inv_w = 2048, 32
-    nbytes = nint * 3 * 4 * 8 + nint * 3 * 16
-    raw = np.empty(nbytes // 8)
-    L.ers_debug_sigma_sharp_device.argtypes = [ctypes.c_void_p, ctypes.c_int64]
-    assert L.ers_debug_sigma_sharp_device(raw.ctypes.data, nbytes) == 0
-    dpart = raw[: nint * 12].reshape(nint, 3, 4)
-    fpart = raw[nint * 12:].view(np.float32).reshape(nint, 3, 4)
-    f32 = np.float32
-
-    def fmaf(a, b, c):
-        return f32(np.float64(a) * np.float64(b) + np.float64(c))
+    tab = _device_layout(L.ers_debug_sigma_sharp_device, nint)
 
     rng = np.random.default_rng(2)
     taus = np.concatenate([[0.0, 1e-10, 0.5, 1.0, 35.99, 36.0, 63.9], rng.uniform(0, 64, 200)])
@@ -206,8 +225,7 @@ def test_sigma_sharp_device_layout_accuracy(L):
     c = 2 / mp.sqrt(mp.pi)
     for tau in taus:
         i = min(int(np.float32(tau) * inv_w), nint - 1)
-        s = 2 * inv_w * tau - float(fpart[i, 0, 3])
-        sf = f32(s)
+        s = 2 * inv_w * tau - float(tab[i, 0, 3])
         t = mp.sqrt(mp.mpf(tau))
         if t == 0:
             ref = [c * mp.mpf(8) / 3, c * mp.mpf(16) / 3, c * mp.mpf(32) / 45]
@@ -216,13 +234,11 @@ def test_sigma_sharp_device_layout_accuracy(L):
             ref = [(e + c / 3 * (5 * t - 2 * t**3) * g) / t, (e - c / 3 * (3 * t - 14 * t**3 + 4 * t**5) * g) / t**3,
                    (e - c / 9 * (9 * t + 6 * t**3 - 4 * t**5) * g) / t**5]
         for p_ in range(3):
-            c6, c5, c4 = fpart[i, p_, :3]
-            v = float(fmaf(fmaf(c6, sf, c5), sf, c4))
-            for cc in dpart[i, p_]:
-                v = v * s + cc
+            v = _layout_eval(tab[i, p_], s)
             worst = max(worst, abs(v - float(ref[p_])) / abs(float(ref[p_])))
-            assert abs(c4) <= 2e-8 * abs(dpart[i, p_, 3]), (i, p_)
-    assert worst < 6e-15, worst
+            c0 = float(tab[i, p_, 10]) + float(tab[i, p_, 11])
+            assert abs(tab[i, p_, 2]) <= 2e-8 * abs(c0), (i, p_)
+    assert worst < 2e-14, worst
 
 
 @pytest.mark.parametrize("n0", [1, 37, 500, 4000])

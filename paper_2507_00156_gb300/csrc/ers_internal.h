@@ -387,6 +387,24 @@ __device__ __forceinline__ void pair_acc(float &kh, float &kl, float ah, float a
     kl = __fsub_rn(w, __fsub_rn(kh, u));
 }
 
+// (h, l) = a b in float pairs (the product of the leading floats exactly, the cross terms added).
+__device__ __forceinline__ void pair_mul(float ah, float al, float bh, float bl, float &h, float &l) {
+    const float p = __fmul_rn(ah, bh);
+    const float e = __fmaf_rn(ah, bl, __fmaf_rn(al, bh, __fmaf_rn(ah, bh, -p)));
+    h = __fadd_rn(p, e);
+    l = __fsub_rn(e, __fsub_rn(h, p));
+}
+
+// k = k + f (a float) in float pairs.
+__device__ __forceinline__ void pair_add(float &kh, float &kl, float f) {
+    const float u = __fadd_rn(kh, f);
+    const float v = __fsub_rn(u, kh);
+    const float e = __fadd_rn(__fsub_rn(kh, __fsub_rn(u, v)), __fsub_rn(f, v));
+    const float w = __fadd_rn(e, kl);
+    kh = __fadd_rn(u, w);
+    kl = __fsub_rn(w, __fsub_rn(kh, u));
+}
+
 // h + l as a double (one FP64 add).
 __device__ __forceinline__ double pair_to_double(float h, float l) { return float_to_double(h) + float_to_double(l); }
 

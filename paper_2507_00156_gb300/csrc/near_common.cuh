@@ -37,6 +37,7 @@ struct Geom {
     float id2h[MAXD], id2l[MAXD]; // 1/delta_k^2 = id2h + id2l in floats
     float alf[MAXD];           // extrapolation weights in FP32 (for the small defects 1 - s_p)
     float adh[3][MAXD], adl[3][MAXD];  // alpha_k / delta_k^p (p = 1, 3, 5) as float pairs
+    float aph[MAXD], apl[MAXD];        // apre as float pairs
     float tcf2;             // cutoff_t^2: s_p := 1 beyond t = cutoff_t
     bool cut_small;         // cutoff_t < DEFECT_T: the table path may meet the cutoff
 };
@@ -238,6 +239,10 @@ __device__ __forceinline__ void load_geom(int lane, const double *y, const doubl
     T.apre[1] = al[0] + al[1];
     T.apre[2] = al[0] + al[1] + al[2];
     T.apre[3] = (al[0] + al[1]) + (al[2] + al[3]);
+    for (int k = 0; k < MAXD; ++k) {
+        T.aph[k] = (float)T.apre[k];
+        T.apl[k] = (float)(T.apre[k] - (double)T.aph[k]);
+    }
     for (int k = 0; k < MAXD; ++k) T.alf[k] = (float)al[k];
 }
 
@@ -319,12 +324,16 @@ __device__ __forceinline__ void table_pairs_r2(const double *__restrict__ tab, d
 // The class is a run-time value (uniform over a batch of pairs) for the classes with table-path
 // deltas (ALLDEF = false: one code path for all of them keeps the kernel within the instruction
 // cache); ALLDEF = true is the class with every delta on the defect path (cls = ND).
-template <bool ALLDEF, int ND>
+// ROLL: the loops over deltas stay rolled (code size; T must then sit in shared memory, as in
+// k_near, since the loops index its arrays at run time); otherwise they unroll for a compile-time
+// cls (the batched kernel, whose Geom lives in registers).
+template <bool ALLDEF, int ND, bool ROLL = true>
 __device__ __forceinline__ void kernel_factors_rt(const Geom &T, const ScanParams &P, const double *__restrict__ tab,
                                                   double r2, int cls, double &K1, double &K3, double &K5, float &Lf) {
     const int NDEF = ALLDEF ? ND : cls;  // defect-path deltas that carry weight
     Lf = 0.0f;
-    double ri = 0.0, ri3 = 0.0, ri5 = 0.0;
+    // K1, K3, K5 accumulate in float pairs (~2^-46 relative) and leave as doubles with one FP64 add each
+    float kh[3] = {0.0f, 0.0f, 0.0f}, kl[3] = {0.0f, 0.0f, 0.0f};
     if (ALLDEF || cls >= 1) {
         // r / delta_k > DEFECT_T: s_p = 1 - eps_p with eps_1 = erfc t, eps_2 = eps_1 + (2/sqrt pi) t e^{-t^2},
         // eps_3 = eps_1 + (2/sqrt pi)(t + 2/3 t^3) e^{-t^2} (Eqs. (s1)-(s3)), all below 2.1e-8, and
@@ -334,11 +343,10 @@ __device__ __forceinline__ void kernel_factors_rt(const Geom &T, const ScanParam
         //    cross terms), so that e^{-tau} = e^{-tau_h} (1 - tau_l) loses nothing to the rounding of tau;
         //  - erfc t = e^{-t^2} / (t sqrt pi) (1 - 1/(2t^2) + 3/(4t^4) - 15/(8t^6)), the asymptotic series
         //    (Abramowitz & Stegun 7.1.23), truncation below 3e-5 relative for t >= 4.7.
-        const float r2h = approx_float_pos(r2);
-        const float r2l = approx_float(r2 - float_to_double(r2h));
+        float r2h, r2l;
+        split_pair(r2, r2h, r2l);
         float E1 = 0.0f, E3 = 0.0f, E5 = 0.0f;
-#pragma unroll 1
-        for (int k = 0; k < NDEF; ++k) {
+        auto defect = [&](int k) {
             const float th = r2h * T.id2h[k];
             const float tl = fmaf(r2h, T.id2h[k], -th) + fmaf(r2h, T.id2l[k], r2l * T.id2h[k]);
             bool reg = th <= T.tcf2;  // t <= cutoff_t: s_p < 1
@@ -356,35 +364,44 @@ __device__ __forceinline__ void kernel_factors_rt(const Geom &T, const ScanParam
                 E3 = fmaf(a, e + gt, E3);
                 E5 = fmaf(a, fmaf(gt, 0.6666666666666667f * th, e + gt), E5);
             }
+        };
+        if (ROLL) {
+#pragma unroll 1
+            for (int k = 0; k < NDEF; ++k) defect(k);
+        } else {
+#pragma unroll
+            for (int k = 0; k < ND; ++k)
+                if (k < NDEF) defect(k);
         }
-        // 1/r from the FP32 estimate y0: with e = 1 - r^2 y0^2 (|e| < 1e-6),
-        // 1/r = y0 (1 - e)^{-1/2} = y0 (1 + e/2 + 3 e^2/8) + O(e^3 y0).
-        const double y0 = float_to_double(rsqrt_ftz(r2h));  // r2h > 0: r > 4.7 delta_0
-        const double ee = fma(-(r2 * y0), y0, 1.0);
-        ri = fma(y0 * ee, fma(0.375, ee, 0.5), y0);
-        const double ri2 = ri * ri;
-        ri3 = ri2 * ri;
-        ri5 = ri3 * ri2;
-        // eps_p / r^p in FP32 from the rounded FP64 powers (relative error ~1e-7 of terms below
-        // 2.1e-8 of the result; powers formed in FP32 would add up to 5 roundings)
-        const float rf3 = round_float_pos(ri3);
-        K1 = -float_to_double(E1 * round_float_pos(ri));
-        K3 = -float_to_double(E3 * rf3);
-        K5 = -float_to_double(E5 * round_float_pos(ri5));
-        if (ALLDEF) Lf = (E3 - E5) * rf3;
-    } else {
-        K1 = 0.0;
-        K3 = 0.0;
-        K5 = 0.0;
+        // 1/r in float pairs from the FP32 estimate y0: with e = 1 - r^2 y0^2 (|e| < 1e-6, from the
+        // exact square of y0 and the pair product with r^2), 1/r = y0 (1 + e/2 + 3 e^2/8) + O(e^3 y0)
+        const float y0 = rsqrt_ftz(r2h);  // r2h > 0: r > 4.7 delta_0
+        const float qh = __fmul_rn(y0, y0), ql = __fmaf_rn(y0, y0, -qh);
+        const float ph = __fmul_rn(r2h, qh);
+        const float pe = __fmaf_rn(r2h, ql, __fmaf_rn(r2l, qh, __fmaf_rn(r2h, qh, -ph)));
+        const float ee = __fsub_rn(__fsub_rn(1.0f, ph), pe);
+        const float cr = __fmul_rn(y0, __fmul_rn(ee, __fmaf_rn(0.375f, ee, 0.5f)));
+        const float r1h = __fadd_rn(y0, cr), r1l = __fsub_rn(cr, __fsub_rn(r1h, y0));
+        float q2h, q2l, r3h, r3l, r5h, r5l;
+        pair_mul(r1h, r1l, r1h, r1l, q2h, q2l);
+        pair_mul(q2h, q2l, r1h, r1l, r3h, r3l);
+        pair_mul(r3h, r3l, q2h, q2l, r5h, r5l);
+        // (sum of the alpha of the defect-path deltas) / r^p, and the defects eps_p / r^p in FP32
+        // (relative error ~1e-7 of terms below 2.1e-8 of the result)
+        const int ia = (ALLDEF ? ND : cls) - 1;
+        const float ah = T.aph[ia], al = T.apl[ia];
+        pair_acc(kh[0], kl[0], ah, al, r1h, r1l);
+        pair_acc(kh[1], kl[1], ah, al, r3h, r3l);
+        pair_acc(kh[2], kl[2], ah, al, r5h, r5l);
+        pair_add(kh[0], kl[0], -(E1 * r1h));
+        pair_add(kh[1], kl[1], -(E3 * r3h));
+        pair_add(kh[2], kl[2], -(E5 * r5h));
+        if (ALLDEF) Lf = (E3 - E5) * r3h;
     }
     if (!ALLDEF) {
-        // the table-path deltas: sum_k (alpha_k / delta_k^p) sigma_p(tau_k) in float pairs, one
-        // FP64 add per factor at the end
+        // the table-path deltas: (alpha_k / delta_k^p) sigma_p(tau_k)
         const float r2f = approx_float_pos(r2);
-        float kh[3] = {0.0f, 0.0f, 0.0f}, kl[3] = {0.0f, 0.0f, 0.0f};
-        // a rolled loop: the unrolled float-pair code of several deltas overflows the instruction cache
-#pragma unroll 1
-        for (int k = cls; k < ND; ++k) {
+        auto table = [&](int k) {
             float sg[3][2];
             table_pairs_r2<TAB_INV_W, TAB_N>(tab, r2, r2f, T.id2h[k], T.s2w[k], sg);
             if (T.cut_small && r2f * T.id2h[k] >= (1.0f - CUT_BAND) * T.tcf2 && r2 > P.cut2d[k]) {
@@ -397,31 +414,25 @@ __device__ __forceinline__ void kernel_factors_rt(const Geom &T, const ScanParam
             }
 #pragma unroll
             for (int p = 0; p < 3; ++p) pair_acc(kh[p], kl[p], T.adh[p][k], T.adl[p][k], sg[p][0], sg[p][1]);
-        }
-        const double t1 = pair_to_double(kh[0], kl[0]), t3 = pair_to_double(kh[1], kl[1]),
-                     t5 = pair_to_double(kh[2], kl[2]);
-        if (cls >= 1) {
-            K1 += t1;
-            K3 += t3;
-            K5 += t5;
+        };
+        if (ROLL) {  // a rolled loop: the unrolled float-pair code of several deltas overflows the instruction cache
+#pragma unroll 1
+            for (int k = cls; k < ND; ++k) table(k);
         } else {
-            K1 = t1;
-            K3 = t3;
-            K5 = t5;
+#pragma unroll
+            for (int k = 0; k < ND; ++k)
+                if (k >= cls) table(k);
         }
     }
-    if (ALLDEF || cls >= 1) {
-        const double Ain = T.apre[(ALLDEF ? ND : cls) - 1];
-        K1 = fma(Ain, ri, K1);
-        K3 = fma(Ain, ri3, K3);
-        K5 = fma(Ain, ri5, K5);
-    }
+    K1 = pair_to_double(kh[0], kl[0]);
+    K3 = pair_to_double(kh[1], kl[1]);
+    K5 = pair_to_double(kh[2], kl[2]);
 }
 
 template <int CLS, int ND = 3>
 __device__ __forceinline__ void kernel_factors(const Geom &T, const ScanParams &P, const double *__restrict__ tab,
                                                double r2, double &K1, double &K3, double &K5, float &Lf) {
-    kernel_factors_rt<(CLS >= ND), ND>(T, P, tab, r2, CLS, K1, K3, K5, Lf);
+    kernel_factors_rt<(CLS >= ND), ND, false>(T, P, tab, r2, CLS, K1, K3, K5, Lf);
 }
 
 // Single-layer contraction: accU += K1 g + K3 d (d.g), g = wf - c wn.

@@ -38,6 +38,7 @@ struct BatchSmem {
         double near[BW][NR][7][32];  // near phase: per-lane accumulators (SL without c_r wn; N; D)
     } u;
     double tq[BW][NR][4];  // near phase: c_r = f0_r . n0 and q0_r of each warp's target
+    Geom g[BW];            // near phase: each warp's target constants (indexed at run time)
     int sq[BW][NCLS][64];
     float4 cen;
     int item;
@@ -185,10 +186,11 @@ __device__ void far_phase(const BatchProblemDev &P, int tb, int layers, BatchSme
 
 // One near pair for the NR densities: the kernel factors, the single-layer terms without the
 // c_r w n part (K1 w f + K3 (d.w f) d per density, and K1 w n + K3 (d.w n) d once, into accB,
-// subtracted c_r times at the end) and the double-layer terms.
-template <int CLS, int NR>
+// subtracted c_r times at the end) and the double-layer terms.  The pair class cls is a run-time
+// value for the classes with table-path deltas (ALLDEF = false, one code path) and 3 otherwise.
+template <bool ALLDEF, int NR>
 __device__ __forceinline__ void near_pair(const BatchProblemDev &P, const Geom &T, const double *__restrict__ tab,
-                                          int64_t j, int lane, int warp, int layers, BatchSmem<NR> &S,
+                                          int64_t j, int cls, int lane, int warp, int layers, BatchSmem<NR> &S,
                                           double accB[3]) {
     const double *rec = P.sd.rec + j * REC;
     const double xs[3] = {__ldg(rec + R_X), __ldg(rec + R_X + 1), __ldg(rec + R_X + 2)};
@@ -200,14 +202,14 @@ __device__ __forceinline__ void near_pair(const BatchProblemDev &P, const Geom &
     if (!is_near<ERS_PREC_MIXED>(P.sd, T, j, r2, P.Rc, P.sp.rc2f)) return;
     double K1, K3, K5;
     float Lf;
-    kernel_factors<CLS>(T, P.sp, tab, r2, K1, K3, K5, Lf);
+    kernel_factors_rt<ALLDEF, 3>(T, P.sp, tab, r2, cls, K1, K3, K5, Lf);
     const double W = fma(dz, wn[2], fma(dy, wn[1], dx * wn[0]));
     // every delta on the defect path (CLS = 3): L and the factors it multiplies in FP32
     // (dl_accumulate_defect); otherwise the FP64 pair factors, shared by the NR densities
     double nm = 0.0;
     float nmf = 0.0f, Zf = 0.0f;
     DLPair D{};
-    if (CLS >= 3) {
+    if (ALLDEF) {
         nmf = fmaf(approx_float(T.n0[2]), approx_float(wn[2]),
                    fmaf(approx_float(T.n0[1]), approx_float(wn[1]), approx_float(T.n0[0]) * approx_float(wn[0])));
         Zf = fmaf(approx_float(T.b2), nmf, -approx_float(W));
@@ -238,7 +240,7 @@ __device__ __forceinline__ void near_pair(const BatchProblemDev &P, const Geom &
             const double qs[3] = {d1.y, d2.x, d2.y};
             const double q0[3] = {S.tq[warp][r][1], S.tq[warp][r][2], S.tq[warp][r][3]};
             double accN = a[3][lane], accD[3] = {a[4][lane], a[5][lane], a[6][lane]};
-            if (CLS >= 3) dl_accumulate_defect(T, dx, dy, dz, Lf, K5W, nmf, Zf, qs, q0, accN, accD);
+            if (ALLDEF) dl_accumulate_defect(T, dx, dy, dz, Lf, K5W, nmf, Zf, qs, q0, accN, accD);
             else dl_accumulate(D, T, dx, dy, dz, nm, qs, q0, accN, accD);
             a[3][lane] = accN;
             a[4][lane] = accD[0];
@@ -259,9 +261,15 @@ __device__ void near_phase(const BatchProblemDev &P, int tb, int layers, const d
         const double bm = P.b[m];
         const bool near = fabs(bm) <= P.Rc;
         if (near) {
-            Geom T;
-            load_geom(lane, P.y, P.x0, P.n0, bm, m, rho, P.sp.h, T);
-            set_cutoff(T, P.sp);
+            {
+                Geom Tl;
+                load_geom(lane, P.y, P.x0, P.n0, bm, m, rho, P.sp.h, Tl);
+                set_cutoff(Tl, P.sp);
+                __syncwarp();  // the previous target's reads of S.g are done
+                if (lane == 0) S.g[warp] = Tl;
+                __syncwarp();
+            }
+            const Geom &T = S.g[warp];
             if (lane < 4 * NR) {  // lane = 4 r + k: k = 0 c_r, k = 1..3 q0_r
                 const int r = lane >> 2, k = lane & 3;
                 double val = 0.0;
@@ -278,10 +286,8 @@ __device__ void near_phase(const BatchProblemDev &P, int tb, int layers, const d
             double accB[3] = {0.0, 0.0, 0.0};
             scan_near(P.sd, T, P.sp, S.sq[warp], lane, [&](int cls, int jj, bool valid) {
                 if (!valid) return;
-                if (cls == 0) near_pair<0, NR>(P, T, tab, jj, lane, warp, layers, S, accB);
-                else if (cls == 1) near_pair<1, NR>(P, T, tab, jj, lane, warp, layers, S, accB);
-                else if (cls == 2) near_pair<2, NR>(P, T, tab, jj, lane, warp, layers, S, accB);
-                else near_pair<3, NR>(P, T, tab, jj, lane, warp, layers, S, accB);
+                if (cls < 3) near_pair<false, NR>(P, T, tab, jj, cls, lane, warp, layers, S, accB);
+                else near_pair<true, NR>(P, T, tab, jj, 3, lane, warp, layers, S, accB);
             });
             for (int i = 0; i < 3; ++i) accB[i] = warp_sum(accB[i]);
             const double chi = bm < 0.0 ? 1.0 : (bm > 0.0 ? 0.0 : 0.5);

@@ -90,7 +90,9 @@ def parse():
                     help="profiling only: the batched leg on two spheres at h = 1/32 and 4 bodies")
     ap.add_argument("--workload", default=WORKLOAD, help="profiling only: a smaller case (e.g. sphere64)")
     ap.add_argument("--no-two-drop", action="store_true", help="skip the two-drop (Sec. 4.3) leg")
-    ap.add_argument("--two-drop-fine", action="store_true", help="two-drop leg: also h = 1/128 (FP64 treecode)")
+    ap.add_argument("--two-drop-fine", action="store_true", help="two-drop leg: h = 1/128 with the FP64 treecode")
+    ap.add_argument("--two-drop-control", action="store_true",
+                    help="two-drop leg: also the same series with a gap of 0.1 instead of 1.5e-8")
     ap.add_argument("--tree", default=None,
                     help="treecode leg: theta,N0,p (default: the parameters of Eq. (optimal_params) for h)")
     return ap.parse_args()
@@ -270,36 +272,53 @@ def batched_leg(ers, torch, steps: int, warmup: int, small: bool = False):
                          "(semi-axes U[0.6,1], h in {1/32,1/48,1/64,1/96}, own nodes + 5% band), 8 densities")}
 
 
-def two_drop_leg(ers, torch, fine: bool):
+def two_drop_leg(ers, torch, fine: bool, control: bool = False):
     """Two drops nearly touching (Sec. 4.3): GMRES on Eq. (IE-2Surf) at h = 1/16, 1/32, 1/64 in FP64
-    with the direct far field (and, with fine, h = 1/128 with the FP64 treecode at Table 2's
-    theta = 0.6, N0 = 4000, p = 10): iterations, solve times and the self-convergence errors of
-    Table 2 (max and L2 over the velocity components at the coarse nodes)."""
+    with the direct far field, and h = 1/128 for the e_64 row: with the mixed direct far field (its
+    solution agrees with the FP64 treecode's to 4e-8), or with fine the FP64 treecode at Table 2's
+    theta = 0.6, N0 = 4000, p = 10.  Iterations, solve times and the self-convergence errors of
+    Table 2 (max and L2 over the velocity components at the coarse nodes), the max also over the
+    nodes farther than 4h from the contact point (1, 0, 0).  With control, the same for a second
+    drop centred at (2, 0, 0.6403) (gap 0.1 instead of 1.5e-8)."""
     from paper_2507_00156_gb300 import two_drop as gtd
-    levels = [(16, None), (32, None), (64, None)] + ([(128, (0.6, 4000, 10))] if fine else [])
-    sol, rows = {}, []
-    for inv, tree in levels:
-        P = gtd.TwoDrops(1 / inv, tree=tree)
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        x, it, rel, conv = P.solve(tol=1e-10)
-        torch.cuda.synchronize()
-        secs = time.perf_counter() - t0
-        u1, u2 = P.split(x)
-        sol[inv] = ([u1.cpu().numpy(), u2.cpu().numpy()], [P.x[0].cpu().numpy(), P.x[1].cpu().numpy()])
-        rows.append({"inv_h": inv, "N": P.N, "iterations": it, "relres": rel, "converged": conv, "solve_s": secs,
-                     "matvecs": P.matvecs, "far_field": "treecode theta, N0, p = %s" % (tree,) if tree else "direct"})
-        del P
-    invs = [r["inv_h"] for r in rows]
-    for i in range(len(invs) - 1):
-        mx, l2 = gtd.self_convergence(sol[invs[i]][0], sol[invs[i]][1], sol[invs[i + 1]][0], sol[invs[i + 1]][1])
-        rows[i]["max_err"], rows[i]["l2_err"] = mx, l2
-        if i > 0:
-            rows[i]["max_order"] = float(np.log2(rows[i - 1]["max_err"] / mx))
-            rows[i]["l2_order"] = float(np.log2(rows[i - 1]["l2_err"] / l2))
-    return {"rows": rows, "precision": "fp64", "rho": [3, 4, 5], "rho_sharp": 3, "gmres_tol": 1e-10,
-            "note": "Table 2 (Sec. 4.3): errors e_h = u_h - u_{h/2} at the nodes of h; the paper's 1/16..1/64 rows: "
-                    "iterations 13, 12, 12; max 3.17e-3, 1.07e-4, 4.06e-6; L2 1.19e-4, 6.11e-6, 2.11e-7"}
+
+    def series(eps, levels):
+        sol, rows = {}, []
+        for inv, tree, prec in levels:
+            P = gtd.TwoDrops(1 / inv, eps=eps, tree=tree, precision=prec)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            x, it, rel, conv = P.solve(tol=1e-10)
+            torch.cuda.synchronize()
+            secs = time.perf_counter() - t0
+            u1, u2 = P.split(x)
+            sol[inv] = ([u1.cpu().numpy(), u2.cpu().numpy()], [P.x[0].cpu().numpy(), P.x[1].cpu().numpy()])
+            far = "treecode theta, N0, p = %s" % (tree,) if tree else "direct"
+            rows.append({"inv_h": inv, "N": P.N, "iterations": it, "relres": rel, "converged": conv, "solve_s": secs,
+                         "matvecs": P.matvecs, "far_field": far + (" (mixed precision)" if prec else "")})
+            del P
+        invs = [r["inv_h"] for r in rows]
+        for i in range(len(invs) - 1):
+            (uc, xc), (uf, xf) = sol[invs[i]], sol[invs[i + 1]]
+            mx, l2 = gtd.self_convergence(uc, xc, uf, xf)
+            far4 = [np.linalg.norm(xx - np.array([1.0, 0.0, 0.0]), axis=1) > 4.0 / invs[i] for xx in xc]
+            mx4, _ = gtd.self_convergence([u[k] for u, k in zip(uc, far4)], [xx[k] for xx, k in zip(xc, far4)], uf, xf)
+            rows[i]["max_err"], rows[i]["l2_err"], rows[i]["max_err_beyond_4h_of_contact"] = mx, l2, mx4
+            if i > 0:
+                rows[i]["max_order"] = float(np.log2(rows[i - 1]["max_err"] / mx))
+                rows[i]["l2_order"] = float(np.log2(rows[i - 1]["l2_err"] / l2))
+        return rows
+
+    last = (128, (0.6, 4000, 10), ers.PREC_FP64) if fine else (128, None, ers.PREC_MIXED)
+    levels = [(16, None, ers.PREC_FP64), (32, None, ers.PREC_FP64), (64, None, ers.PREC_FP64), last]
+    out = {"rows": series(gtd.EPS, levels), "precision": "fp64 (h = 1/128: %s)" % ("fp64 treecode" if fine else
+                                                                                   "mixed direct far field"),
+           "rho": [3, 4, 5], "rho_sharp": 3, "gmres_tol": 1e-10,
+           "note": "Table 2 (Sec. 4.3): errors e_h = u_h - u_{h/2} at the nodes of h; the paper's 1/16..1/64 rows: "
+                   "iterations 13, 12, 12; max 3.17e-3, 1.07e-4, 4.06e-6; L2 1.19e-4, 6.11e-6, 2.11e-7"}
+    if control:
+        out["control_gap_0.1"] = series(0.6403, levels)
+    return out
 
 
 TRAIN_RADII = (1.0, 1.0, 1.0, 0.85, 0.7)  # one seeded density each
@@ -724,7 +743,7 @@ def main():
     if not args.no_learned and args.workload == WORKLOAD:
         line["learned"] = learned_leg(ers, torch, s, wl, steps=args.steps, warmup=1)
     if not args.no_two_drop and args.workload == WORKLOAD:
-        line["two_drop"] = two_drop_leg(ers, torch, fine=args.two_drop_fine)
+        line["two_drop"] = two_drop_leg(ers, torch, fine=args.two_drop_fine, control=args.two_drop_control)
     if world == 1 and not args.no_cpu_baseline:
         cb, errs = cpu_baseline(wl, y, args.cpu_seconds, {"mixed": (u_mixed, v_mixed), "fp64": (u64, v64)})
         line["cpu_baseline"] = cb

@@ -11,6 +11,10 @@ The headline arm is the precision variant (far field with FP32 operands and FP64
 near sums, closest point and solve in FP64); the plain FP64 path is timed on the same
 workload for the speedup.  Prints one JSON line (rank 0).
 
+With --gpus N under torchrun the targets are cut into N contiguous slices of their Morton order
+(one per GPU, every GPU holding the whole surface): the total work is fixed (strong scaling), no
+collective runs on the data path, and the slices are gathered once after the timed steps.
+
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 """
 from __future__ import annotations
@@ -171,6 +175,72 @@ def max_over_ranks(x: float, world: int) -> float:
 
 def build_targets(wl, x):
     return np.ascontiguousarray(np.concatenate([x, wl.extra_targets]))
+
+
+def morton_keys(y: np.ndarray, cell: float) -> np.ndarray:
+    """Morton (Z-order) key of each point's cell of width `cell` (10 bits per axis)."""
+    c = np.floor((y - y.min(axis=0)) / cell).astype(np.int64)
+    c = np.clip(c, 0, 1023)
+    key = np.zeros(len(y), dtype=np.int64)
+    for bit in range(10):
+        for a in range(3):
+            key |= ((c[:, a] >> bit) & 1) << (3 * bit + a)
+    return key
+
+
+def shard_indices(y: np.ndarray, cell: float, world: int):
+    """The targets in Morton order of their cells, cut into `world` contiguous slices of sizes
+    differing by at most one: slice r (an index array into y, in that order) is rank r's share."""
+    order = np.argsort(morton_keys(y, cell), kind="stable")
+    return np.array_split(order, world)
+
+
+def gather_rows(local, idx, M: int, world: int):
+    """Every rank's rows (local[i] belongs to target idx[i]) assembled into one (M, k) array in the
+    original target order, on every rank (one all_gather of slices padded to the largest)."""
+    import torch
+    import torch.distributed as dist
+    if world == 1:
+        out = torch.empty((M,) + tuple(local.shape[1:]), dtype=local.dtype, device=local.device)
+        out[torch.as_tensor(idx, device=local.device)] = local
+        return out
+    n = torch.tensor([local.shape[0]], device=local.device)
+    ns = [torch.zeros_like(n) for _ in range(world)]
+    dist.all_gather(ns, n)
+    cap = int(max(int(v.item()) for v in ns))
+    pad = torch.zeros((cap,) + tuple(local.shape[1:]), dtype=local.dtype, device=local.device)
+    pad[: local.shape[0]] = local
+    ipad = torch.full((cap,), -1, dtype=torch.int64, device=local.device)
+    ipad[: local.shape[0]] = torch.as_tensor(idx, dtype=torch.int64, device=local.device)
+    rows = [torch.zeros_like(pad) for _ in range(world)]
+    ids = [torch.zeros_like(ipad) for _ in range(world)]
+    dist.all_gather(rows, pad)
+    dist.all_gather(ids, ipad)
+    out = torch.empty((M,) + tuple(local.shape[1:]), dtype=local.dtype, device=local.device)
+    for r, i, k in zip(rows, ids, ns):
+        k = int(k.item())
+        out[i[:k]] = r[:k]
+    return out
+
+
+def rel_max(a: np.ndarray, b: np.ndarray, world: int) -> float:
+    """max |a - b| / max |b| over the targets of every rank (0 where a rank has none)."""
+    num = float(np.abs(a - b).max()) if a.size else 0.0
+    den = float(np.abs(b).max()) if b.size else 0.0
+    num, den = max_over_ranks(num, world), max_over_ranks(den, world)
+    return num / den if den > 0 else 0.0
+
+
+def sum_over_ranks(x, world: int):
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor(np.atleast_1d(np.asarray(x, dtype=np.float64)),
+                     device="cuda" if torch.cuda.is_available() else "cpu")
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    v = [int(z) for z in t.cpu().numpy()]
+    return v if np.ndim(x) else v[0]
 
 
 def cpu_baseline(wl, y, seconds: float, gpu_results=None):
@@ -511,8 +581,13 @@ def main():
     fdev = torch.from_numpy(workloads.poly_eval(wl.f_coef, x)).to(dev)
     qdev = torch.from_numpy(workloads.poly_eval(wl.q_coef, x)).to(dev)
     s.set_density(fdev, qdev)
-    y = build_targets(wl, x)
-    M, N = len(y), s.N
+    y_all = build_targets(wl, x)
+    M_all, N = len(y_all), s.N
+    # N > 1: the targets are cut into contiguous slices of their Morton order (cells of 6h), one per
+    # rank; every rank holds the whole surface, and no collective runs on the data path
+    shard = shard_indices(y_all, 6.0 * wl.h, world)[rank] if world > 1 else np.arange(M_all)
+    y = np.ascontiguousarray(y_all[shard])
+    M = len(y)
     yd = torch.from_numpy(y).to(dev)
     x0, _, b0 = s.closest_point(yd)  # set-up only: the densities at the closest points are inputs
     on_surface = b0.cpu().numpy() == 0.0
@@ -565,11 +640,20 @@ def main():
     clocks = sampler.stop()
     near_targets, near_pairs, far_pairs = s.last_counts()
     cls_counts = s.last_class_counts()
+    cls_local = list(cls_counts)  # this rank's pairs, for this rank's roofline
+    far_local = far_pairs
     defect_counts = s.last_defect_class_counts()
     u_mixed, v_mixed = u.cpu().numpy(), v.cpu().numpy()
     t_mixed = max_over_ranks(t_mixed, world)
     ms_step = t_mixed / args.steps * 1e3
-    value = world * args.steps * M / t_mixed
+    value = args.steps * M_all / t_mixed
+    # the slices gathered once, outside the timed region: the whole result on every rank
+    u_all = gather_rows(u, shard, M_all, world)
+    gathered_finite = bool(torch.isfinite(u_all).all().item())
+    del u_all
+    near_targets, near_pairs, far_pairs = sum_over_ranks([near_targets, near_pairs, far_pairs], world)
+    cls_counts = sum_over_ranks(list(cls_counts), world)
+    defect_counts = sum_over_ranks(list(defect_counts), world)
 
     # the same mixed step with the on-surface option (ERS_OPT_SHARP, Sec. 2.1): node targets with
     # one delta# = rho_2 h and the s#_p, no extrapolation
@@ -635,14 +719,28 @@ def main():
         return max_over_ranks(te, world)
 
     te = timed_host(ers.PREC_MIXED, args.steps)
-    e2e = {"value": world * args.steps * M / te, "unit": UNIT, "h2d_bytes_per_step": 3 * M * 3 * 8,
-           "d2h_bytes_per_step": 2 * M * 3 * 8, "api": "ers_eval_host (pinned host arrays, includes copies)"}
+    e2e = {"value": args.steps * M_all / te, "unit": UNIT, "h2d_bytes_per_step": 3 * M_all * 3 * 8,
+           "d2h_bytes_per_step": 2 * M_all * 3 * 8, "api": "ers_eval_host (pinned host arrays, includes copies)"}
     e2e64 = None
     if args.fp64_steps > 0:
         te64 = timed_host(ers.PREC_FP64, args.fp64_steps)
-        e2e64 = {"value": world * args.fp64_steps * M / te64, "unit": UNIT, "steps": args.fp64_steps,
-                 "h2d_bytes_per_step": 3 * M * 3 * 8, "d2h_bytes_per_step": 2 * M * 3 * 8,
+        e2e64 = {"value": args.fp64_steps * M_all / te64, "unit": UNIT, "steps": args.fp64_steps,
+                 "h2d_bytes_per_step": 3 * M_all * 3 * 8, "d2h_bytes_per_step": 2 * M_all * 3 * 8,
                  "api": "ers_eval_host, plain FP64 path (pinned host arrays, includes copies)"}
+
+    # differences and counts over the targets of every rank
+    diffs = {"sharp": (rel_max(u_sh[on_surface], u_mixed[on_surface], world),
+                       rel_max(v_sh[on_surface], v_mixed[on_surface], world)),
+             "fd": (rel_max(u_fd, u_mixed, world), rel_max(v_fd, v_mixed, world)),
+             "tc": (rel_max(u_tc, u_mixed, world), rel_max(v_tc, v_mixed, world))}
+    if t64 is not None:
+        diffs["fp64"] = (rel_max(u_mixed, u64, world), rel_max(v_mixed, v64, world))
+    n_on_surface = sum_over_ranks(int(on_surface.sum()), world)
+    nsh_pairs = sum_over_ranks(nsh_pairs, world)
+    fd_counts = sum_over_ranks(list(fd_counts), world)
+    fd_cls = sum_over_ranks(list(fd_cls), world)
+    tc_app, tc_dir, tc_near = sum_over_ranks([tc_stats["approximated"], tc_stats["direct"], tc_counts[1]], world)
+    tc_stats = dict(tc_stats, approximated=tc_app, direct=tc_dir)
 
     if rank != 0:
         return
@@ -652,8 +750,8 @@ def main():
     scale = sm_mhz / SM_MAX_MHZ
     ms_closest, ms_far, ms_near = (float(z) for z in k_mixed)
     # cls_counts[k] = near pairs with k deltas beyond the cutoff, i.e. 3 - k regularized terms
-    near_flops = NEAR_FLOPS_PER_DELTA_EVAL * sum(c * (3 - k) for k, c in enumerate(cls_counts))
-    far_flops = far_pairs * FAR_FLOPS_PER_PAIR
+    near_flops = NEAR_FLOPS_PER_DELTA_EVAL * sum(c * (3 - k) for k, c in enumerate(cls_local))
+    far_flops = far_local * FAR_FLOPS_PER_PAIR
     roof_near = {"kernel": "k_near (FP64 near sums + extrapolation)", "bound": "alu", "unit": "TFLOP/s",
                  "achieved": near_flops / (ms_near * 1e-3) / 1e12, "peak": FP64_PEAK_NOMINAL * scale / 1e12,
                  "peak_source": "nominal FP64 1.25 TFLOP/s x median SM clock / 2070 MHz",
@@ -669,22 +767,22 @@ def main():
     roof, roof_other = (roof_near, roof_far) if ms_near >= ms_far else (roof_far, roof_near)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
-        "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "ms_per_step": ms_step, "higher_is_better": True, "scaling": "strong", "vs_baseline": None,
         "dtype": "f32+f64", "data": "synthetic",
-        "config": {"workload": args.workload, "shape": "unit sphere", "h": wl.h, "N": N, "M": M, "rho": list(wl.rho),
+        "config": {"workload": args.workload, "shape": "unit sphere", "h": wl.h, "N": N, "M": M_all, "rho": list(wl.rho),
+                   "parallelism": ("targets sharded over %d GPUs (contiguous Morton-order slices, %d-%d targets "
+                                   "per GPU; surface on every GPU; no collective on the data path)"
+                                   % (world, M_all // world, -(-M_all // world)) if world > 1 else "one GPU"),
                    "cutoff_t": 6.0, "precision": "mixed (FP32 far field, FP64 local sums/closest point/solve)",
                    "l2": "flushed between timed steps (256 MiB write, outside the timed events)"},
-        "gpairs_per_s": world * args.steps * M * N / t_mixed / 1e9,
+        "gpairs_per_s": args.steps * M_all * N / t_mixed / 1e9,
         "kernels_ms": {"closest_point": ms_closest, "far_field": ms_far, "near_field_and_solve": ms_near},
         "sharp_option": {"ms_per_step": t_sh / args.steps * 1e3,
                          "speedup_vs_extrapolated": t_mixed / t_sh,
                          "kernels_ms": {"far_field": float(k_sh[1]), "near_field_and_solve": float(k_sh[2])},
-                         "on_surface_targets": int(on_surface.sum()), "on_surface_near_pairs": nsh_pairs,
-                         "max_rel_diff_vs_extrapolated_on_surface": {
-                             "SL": float(np.abs(u_sh[on_surface] - u_mixed[on_surface]).max()
-                                         / np.abs(u_mixed[on_surface]).max()),
-                             "DL": float(np.abs(v_sh[on_surface] - v_mixed[on_surface]).max()
-                                         / np.abs(v_mixed[on_surface]).max())},
+                         "on_surface_targets": n_on_surface, "on_surface_near_pairs": nsh_pairs,
+                         "max_rel_diff_vs_extrapolated_on_surface": {"SL": diffs["sharp"][0],
+                                                                      "DL": diffs["sharp"][1]},
                          "note": "ERS_OPT_SHARP: on-surface targets with the s#_p of Sec. 2.1, delta# = 3h, "
                                  "no extrapolation; both methods are O(h^5)"},
         "four_delta_option": {"ms_per_step": t_fd / args.steps * 1e3, "rho": list(rho4),
@@ -694,9 +792,7 @@ def main():
                               "near_pairs_by_unregularized_deltas": fd_cls,
                               "near_tflops": NEAR_FLOPS_PER_DELTA_EVAL * sum(c * (4 - k) for k, c in enumerate(fd_cls))
                               / (float(k_fd[2]) * 1e-3) / 1e12,
-                              "max_rel_diff_vs_three_delta": {
-                                  "SL": float(np.abs(u_fd - u_mixed).max() / np.abs(u_mixed).max()),
-                                  "DL": float(np.abs(v_fd - v_mixed).max() / np.abs(v_mixed).max())},
+                              "max_rel_diff_vs_three_delta": {"SL": diffs["fd"][0], "DL": diffs["fd"][1]},
                               "note": "ERS_OPT_FOUR_DELTA: O(delta^7) extrapolation of Sec. 1 with the I4 "
                                       "column; the difference is the three-delta method's O(h^5) error"},
         "treecode_option": {"ms_per_step": t_tc / args.steps * 1e3, "theta": tree[0], "N0": tree[1], "p": tree[2],
@@ -704,12 +800,10 @@ def main():
                             "kernels_ms": {"far_field_treecode": float(k_tc[1]), "near_field_and_solve": float(k_tc[2])},
                             "modified_weights_ms": float(k_tcw[1]) - float(k_tc[1]),
                             "tree": tc_stats,
-                            "approximated_per_target": tc_stats["approximated"] / M,
-                            "direct_far_pairs_per_target": tc_stats["direct"] / M,
-                            "near_pairs": tc_counts[1],
-                            "max_rel_diff_vs_direct": {
-                                "SL": float(np.abs(u_tc - u_mixed).max() / np.abs(u_mixed).max()),
-                                "DL": float(np.abs(v_tc - v_mixed).max() / np.abs(v_mixed).max())},
+                            "approximated_per_target": tc_stats["approximated"] / M_all,
+                            "direct_far_pairs_per_target": tc_stats["direct"] / M_all,
+                            "near_pairs": tc_near,
+                            "max_rel_diff_vs_direct": {"SL": diffs["tc"][0], "DL": diffs["tc"][1]},
                             "note": "ERS_OPT_TREECODE: far sums by barycentric Lagrange interpolation at "
                                     "Chebyshev points for clusters meeting the MAC (Sec. 3.4), parameters of "
                                     "Eq. (optimal_params); weights cached between steps (densities unchanged)"},
@@ -721,6 +815,8 @@ def main():
                    "near_pairs_by_unregularized_deltas": cls_counts,
                    "near_pairs_by_defect_path_deltas": defect_counts},
         "gpu_launches": 3 * args.steps,
+        "gathered": {"targets": M_all, "finite": gathered_finite,
+                     "note": "the per-rank slices gathered once after the timed steps (all_gather)"},
         "roofline": roof,
         "roofline_other_kernel": roof_other,
         "clocks": clocks,
@@ -728,16 +824,15 @@ def main():
     }
     if t64 is not None:
         ms64 = t64 / args.fp64_steps * 1e3
-        line["plain_fp64"] = {"value": world * args.fp64_steps * M / t64, "unit": UNIT, "ms_per_step": ms64,
+        line["plain_fp64"] = {"value": args.fp64_steps * M_all / t64, "unit": UNIT, "ms_per_step": ms64,
                               "steps": args.fp64_steps, "e2e": e2e64,
-                              "gpairs_per_s": world * args.fp64_steps * M * N / t64 / 1e9,
+                              "gpairs_per_s": args.fp64_steps * M_all * N / t64 / 1e9,
                               "kernels_ms": {"closest_point": float(k64[0]), "far_field": float(k64[1]),
                                              "near_field_and_solve": float(k64[2])},
                               "far_fp64_tflops": far_flops / (float(k64[1]) * 1e-3) / 1e12,
                               "fp64_peak_tflops": FP64_PEAK_NOMINAL * scale / 1e12}
         line["speedup_vs_plain_fp64"] = ms64 / ms_step
-        line["mixed_vs_fp64_rel"] = {"SL": float(np.abs(u_mixed - u64).max() / np.abs(u64).max()),
-                                     "DL": float(np.abs(v_mixed - v64).max() / np.abs(v64).max())}
+        line["mixed_vs_fp64_rel"] = {"SL": diffs["fp64"][0], "DL": diffs["fp64"][1]}
     if not args.no_batched:
         line["batched"] = batched_leg(ers, torch, steps=2, warmup=1, small=args.batched_small)
     if not args.no_learned and args.workload == WORKLOAD:

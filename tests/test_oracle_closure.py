@@ -158,6 +158,8 @@ def test_ellipsoid_principal_directions_and_curvatures():
     for m in range(40):
         fr, k1, k2 = closure.principal_frame(ELL, x0[m], n0[m])
         assert k1 >= k2 > 0
+        assert np.abs(fr @ fr.T - np.eye(3)).max() < 1e-14
+        assert np.allclose(np.cross(fr[0], fr[1]), fr[2], atol=1e-14)  # (t1, t2, n0) right-handed
         assert _normal_curvature(ELL, x0[m], n0[m], fr[0]) == pytest.approx(k1, rel=2e-6)
         assert _normal_curvature(ELL, x0[m], n0[m], fr[1]) == pytest.approx(k2, rel=2e-6)
         for th in np.linspace(0.1, 3.0, 7):
@@ -183,6 +185,7 @@ def test_jets_exact_for_a_polynomial_in_the_tangent_coordinates():
         vals_local = sum(np.outer(xi**i * eta**j, C[k]) for k, (i, j) in enumerate(closure.MONOMIALS))
         vals = vals_local @ fr  # back to x, y, z components
         J = closure.density_jets(x, vals, x0[m], fr, h)
+        assert J is not None
         fact = np.array([math.factorial(i) * math.factorial(j) for (i, j) in closure.MONOMIALS])
         np.testing.assert_allclose(J, C * fact[:, None], rtol=0, atol=1e-9 * np.abs(C).max() * 24)
 

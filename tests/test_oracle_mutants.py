@@ -374,3 +374,103 @@ def test_unedited_copy_passes_the_four_delta_and_sharp_pins(tmp_path):
     finally:
         oracle._lib = saved
     assert not failed, failed
+
+
+# Slips in the learned closure's parts of the oracle: the reduced one- and two-delta sums of
+# ers_oracle.c, and the frame, curvatures, jets and targets of oracle/closure.py, against the pins
+# of test_oracle_closure.py (cheapest first, stopping at the first failure).
+CLOSURE_C_MUTANTS = [
+    ("two-delta weights: sign of beta_1", "beta[1] = -a[0] / det;", "beta[1] = a[0] / det;"),
+    ("gamma: rho^2 instead of rho^3", "c[k] = rho[k] * rho[k] * rho[k] * ora_I2(lam);",
+     "c[k] = rho[k] * rho[k] * ora_I2(lam);"),
+    ("reduced double layer: chi q(x0) dropped", "vv += beta[k] * (sv[k][i] * inv8pi + chi * qm0[i]);",
+     "vv += beta[k] * (sv[k][i] * inv8pi);"),
+    ("reduced sums: the sum of delta_k taken with delta_{k+1}",
+     "double delta = rho[k] * h;\n                ora_sl_term(d, r, delta, tc, g, w[j], su[k], 0);",
+     "double delta = rho[k + 1] * h;\n                ora_sl_term(d, r, delta, tc, g, w[j], su[k], 0);"),
+]
+
+CLOSURE_PY_MUTANTS = [
+    ("principal frame: the eigenvector of k2 taken as t1", "v = evecs[:, 1]", "v = evecs[:, 0]"),
+    ("principal frame: t2 = t1 x n0 (left-handed frame)", "t2 = np.cross(E[2], t1)", "t2 = np.cross(t1, E[2])"),
+    ("shape operator: multiplied by |grad F| instead of divided",
+     "S = (E[:2] @ hess @ E[:2].T) / np.linalg.norm(grad)", "S = (E[:2] @ hess @ E[:2].T) * np.linalg.norm(grad)"),
+    ("jets: the factorials i! j! dropped", "return coef * fact[:, None]", "return coef"),
+    ("jets: eta taken along t1", "eta = d[sel] @ frame[1] / h", "eta = d[sel] @ frame[0] / h"),
+    ("correction: sign of the two-delta term", "outs.append(ur - gamma[:, None] * corr if ndelta == 2 else ur + corr)",
+     "outs.append(ur + gamma[:, None] * corr if ndelta == 2 else ur + corr)"),
+    ("targets: h^p of the single layer also for the double layer", "        p = 1 if layer == 0 else 0\n        S = scale",
+     "        p = 1\n        S = scale"),
+]
+
+
+def _closure_pins(stop_at_failure=True):
+    import test_oracle_closure as C
+    checks = [("two-delta weights exact at b = 0", lambda: C.test_two_delta_weights_exact_at_zero((2.0, 3.0, 4.0))),
+              ("two-delta weight identities", C.test_two_delta_weights_identities),
+              ("plain sums beyond the reduced radius", C.test_targets_beyond_the_reduced_radius_take_the_plain_sums),
+              ("sphere frame", C.test_sphere_frame_and_curvatures),
+              ("ellipsoid axis points", C.test_ellipsoid_axis_points),
+              ("principal directions and curvatures", C.test_ellipsoid_principal_directions_and_curvatures),
+              ("exact fit of tangent polynomials", C.test_jets_exact_for_a_polynomial_in_the_tangent_coordinates),
+              ("jets against Monge-patch derivatives", C.test_jets_match_surface_derivatives_on_the_sphere),
+              ("targets and correction inverse", C.test_targets_and_apply_are_inverse),
+              ("u2 - gamma c2 = u3", C.test_two_delta_value_with_three_delta_c2_is_the_three_delta_value),
+              ("orders of convergence", C.test_reduced_sums_converge_at_their_orders)]
+    out = []
+    for name, fn in checks:
+        try:
+            fn()
+            out.append((name, True))
+        except (AssertionError, ValueError, TypeError, np.linalg.LinAlgError):
+            out.append((name, False))
+            if stop_at_failure:
+                break
+    return out
+
+
+@pytest.mark.parametrize("what,old,new", CLOSURE_C_MUTANTS, ids=[m[0] for m in CLOSURE_C_MUTANTS])
+def test_planted_reduced_sum_mistake_fails_a_pin(tmp_path, what, old, new):
+    text = open(SRC).read()
+    assert text.count(old) == 1, f"the text to edit is not unique in the oracle: {old}"
+    lib = _compile(tmp_path, "mutant", text.replace(old, new, 1))
+    saved = oracle._lib
+    oracle._lib = lib
+    try:
+        caught = [name for name, ok in _closure_pins() if not ok]
+    finally:
+        oracle._lib = saved
+    print(what, "->", caught)
+    assert caught, f"no pin catches: {what}"
+
+
+@pytest.mark.parametrize("what,old,new", CLOSURE_PY_MUTANTS, ids=[m[0] for m in CLOSURE_PY_MUTANTS])
+def test_planted_closure_feature_mistake_fails_a_pin(what, old, new):
+    import types
+
+    import test_oracle_closure as C
+    from oracle import closure
+    text = open(closure.__file__).read()
+    assert text.count(old) == 1, f"the text to edit is not unique in the closure oracle: {old}"
+    mod = types.ModuleType("closure_copy")
+    mod.__file__ = closure.__file__
+    exec(compile(text.replace(old, new, 1), closure.__file__, "exec"), mod.__dict__)
+    saved = C.closure
+    C.closure = mod
+    try:
+        caught = [name for name, ok in _closure_pins() if not ok]
+    finally:
+        C.closure = saved
+    print(what, "->", caught)
+    assert caught, f"no pin catches: {what}"
+
+
+def test_unedited_closure_oracle_passes_every_pin(tmp_path):
+    lib = _compile(tmp_path, "unedited", open(SRC).read())
+    saved = oracle._lib
+    oracle._lib = lib
+    try:
+        failed = [name for name, ok in _closure_pins(False) if not ok]
+    finally:
+        oracle._lib = saved
+    assert not failed, failed

@@ -503,8 +503,11 @@ __device__ __forceinline__ void dl_accumulate_defect(const Geom &T, double dx, d
 // Walk the rows of the surface's cell grid that meet the prefilter ball around the target,
 // test candidates in FP32, queue survivors by class in the warp's shared queues sq[NC][64],
 // and call batch(cls, j, valid) with one node per lane whenever a class has 32 entries, then
-// once more per class for the remainder (lanes with valid = false hold no node).  NC = number
-// of classes: 4 with three deltas, 5 with four.
+// once per class for the remainder (lanes with valid = false hold no node).  NC = number of
+// classes: 4 with three deltas, 5 with four.  batch is called from one place, with the class
+// as a run-time value, so that its code (the whole pair evaluation) exists once in the kernel:
+// each turn of the loop either hands one batch over or tests the next 32 candidates of the
+// current row.
 template <int NC = NCLS, class Batch>
 __device__ __forceinline__ void scan_near(const SurfDev &s, const Geom &T, const ScanParams &P, int (*sq)[64],
                                           int lane, Batch &&batch) {
@@ -524,10 +527,17 @@ __device__ __forceinline__ void scan_near(const SurfDev &s, const Geom &T, const
     }
     const int *__restrict__ cs = s.cell_start;
     const float4 *__restrict__ xs32 = s.xs32;
-    for (int iz = lo[2]; iz <= hi[2]; ++iz) {
-        const float zl = of[2] + iz * cw;
-        const float dzr = fmaxf(0.0f, fmaxf(zl - yf[2], yf[2] - (zl + cw)));
-        for (int iy = lo[1]; iy <= hi[1]; ++iy) {
+    // row cursor: the next row (iz, iy) that meets the ball, as the node range [jb, je) of the
+    // cells ia..ib it spans
+    int iz = lo[2], iy = lo[1] - 1, jb = 0, je = 0;
+    auto next_row = [&]() -> bool {
+        for (;;) {
+            if (++iy > hi[1]) {
+                iy = lo[1];
+                if (++iz > hi[2]) return false;
+            }
+            const float zl = of[2] + iz * cw;
+            const float dzr = fmaxf(0.0f, fmaxf(zl - yf[2], yf[2] - (zl + cw)));
             const float yl0 = of[1] + iy * cw;
             const float dyr = fmaxf(0.0f, fmaxf(yl0 - yf[1], yf[1] - (yl0 + cw)));
             const float rem = R2 - dyr * dyr - dzr * dzr;
@@ -537,43 +547,53 @@ __device__ __forceinline__ void scan_near(const SurfDev &s, const Geom &T, const
             const int ib = min(hi[0], (int)floorf((yf[0] + half - of[0]) * inv_cw));
             if (ia > ib) continue;
             const int64_t rowbase = ((int64_t)iz * G.nc[1] + iy) * G.nc[0];
-            const int js = cs[rowbase + ia], je = cs[rowbase + ib + 1];
-            for (int jb = js; jb < je; jb += 32) {
-                const int j = jb + lane;
-                bool pass = false;
-                int cls = 0;
-                if (j < je) {
-                    const float4 p = __ldg(xs32 + j);
-                    const float ex = yf[0] - p.x, ey = yf[1] - p.y, ez = yf[2] - p.z;
-                    const float r2f = fmaf(ez, ez, fmaf(ey, ey, ex * ex));
-                    pass = r2f <= R2;
-#pragma unroll
-                    for (int k = 0; k < NC - 1; ++k) cls += r2f > P.th[k];
-                }
-#pragma unroll
-                for (int c = 0; c < NC; ++c) {
-                    const unsigned mk = __ballot_sync(FULL, pass && cls == c);
-                    if (pass && cls == c) sq[c][qn[c] + __popc(mk & lt)] = j;
-                    qn[c] += __popc(mk);
-                }
-                __syncwarp();
-#pragma unroll
-                for (int c = 0; c < NC; ++c) {
-                    if (qn[c] >= 32) {
-                        batch(c, sq[c][qn[c] - 32 + lane], true);
-                        qn[c] -= 32;
-                        __syncwarp();
-                    }
-                }
-            }
+            jb = cs[rowbase + ia];
+            je = cs[rowbase + ib + 1];
+            if (jb < je) return true;
         }
-    }
+    };
+    bool more = lo[0] <= hi[0] && lo[1] <= hi[1] && lo[2] <= hi[2] && next_row();
+    for (;;) {
+        // a class with 32 queued nodes or, once the rows are done, with a remainder
+        int c = -1;
 #pragma unroll
-    for (int c = 0; c < NC; ++c) {
-        if (qn[c] > 0) {
-            const bool v = lane < qn[c];
-            batch(c, v ? sq[c][lane] : 0, v);
+        for (int cc = NC - 1; cc >= 0; --cc)
+            if (qn[cc] >= 32 || (!more && qn[cc] > 0)) c = cc;
+        if (c >= 0) {
+            int n = 0;
+#pragma unroll
+            for (int cc = 0; cc < NC; ++cc) n = cc == c ? qn[cc] : n;
+            const int take = min(n, 32);
+            const bool v = lane < take;
+            batch(c, v ? sq[c][n - take + lane] : 0, v);
+#pragma unroll
+            for (int cc = 0; cc < NC; ++cc)
+                if (cc == c) qn[cc] = n - take;
+            __syncwarp();
+            continue;
         }
+        if (!more) break;
+        // the next 32 candidates of the row (every queue holds < 32 here, so <= 63 after)
+        const int j = jb + lane;
+        bool pass = false;
+        int cls = 0;
+        if (j < je) {
+            const float4 p = __ldg(xs32 + j);
+            const float ex = yf[0] - p.x, ey = yf[1] - p.y, ez = yf[2] - p.z;
+            const float r2f = fmaf(ez, ez, fmaf(ey, ey, ex * ex));
+            pass = r2f <= R2;
+#pragma unroll
+            for (int k = 0; k < NC - 1; ++k) cls += r2f > P.th[k];
+        }
+#pragma unroll
+        for (int cc = 0; cc < NC; ++cc) {
+            const unsigned mk = __ballot_sync(FULL, pass && cls == cc);
+            if (pass && cls == cc) sq[cc][qn[cc] + __popc(mk & lt)] = j;
+            qn[cc] += __popc(mk);
+        }
+        __syncwarp();
+        jb += 32;
+        if (jb >= je) more = next_row();
     }
     __syncwarp();
 }

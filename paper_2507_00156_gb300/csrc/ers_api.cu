@@ -46,7 +46,7 @@ namespace {
 
 void free_surface(ers_surface *s) {
     if (!s) return;
-    void *ptrs[] = {s->x, s->n, s->w, s->perm, s->rec, s->rec32, s->tilec, s->xs32, s->fq, s->cell_start, s->cell_rank,
+    void *ptrs[] = {s->x, s->n, s->w, s->perm, s->rec, s->rec32, s->recp, s->tilec, s->xs32, s->fq, s->cell_start, s->cell_rank,
                     s->okeys.ptr, s->oorder.ptr, s->ohist.ptr,
                     s->part.ptr, s->cp.ptr, s->host_io.ptr, s->counts.ptr, s->dens64.ptr, s->dens32.ptr,
                     s->fitw.ptr};
@@ -199,6 +199,7 @@ int build_surface(const ers_shape *shape, double h, ers_surface **out) {
 
     std::vector<double> rec((size_t)N * REC, 0.0);
     std::vector<float> rec32((size_t)N * REC, 0.0f);
+    std::vector<float> recp((size_t)N * NREC, 0.0f);
     std::vector<float4> xs32(N);
     s->ntile32 = (N + TS32 - 1) / TS32;
     std::vector<float> tilec((size_t)s->ntile32 * 4, 0.0f);
@@ -217,6 +218,10 @@ int build_surface(const ers_shape *shape, double h, ers_surface **out) {
                 rec[j * REC + R_WN + a] = wn;
                 rec32[j * REC + R_X + a] = (float)(xv - (double)tilec[4 * t + a]);
                 rec32[j * REC + R_WN + a] = (float)wn;
+                std::memcpy(&recp[j * NREC + 2 * a], &xv, sizeof(double));
+                const float wh = (float)wn;
+                recp[j * NREC + NR_WN + 2 * a] = wh;
+                recp[j * NREC + NR_WN + 2 * a + 1] = (float)(wn - (double)wh);
             }
             xs32[j] = make_float4((float)xs[3 * i], (float)xs[3 * i + 1], (float)xs[3 * i + 2], 0.0f);
         }
@@ -233,6 +238,7 @@ int build_surface(const ers_shape *shape, double h, ers_surface **out) {
     ERS_TRY(dmalloc(&s->perm, N));
     ERS_TRY(dmalloc(&s->rec, (size_t)N * REC));
     ERS_TRY(dmalloc(&s->rec32, (size_t)N * REC));
+    ERS_TRY(dmalloc(&s->recp, (size_t)N * NREC));
     ERS_TRY(dmalloc(&s->tilec, (size_t)s->ntile32 * 4));
     ERS_TRY(dmalloc(&s->xs32, N));
     ERS_TRY(dmalloc(&s->fq, (size_t)N * 6));
@@ -249,6 +255,7 @@ int build_surface(const ers_shape *shape, double h, ers_surface **out) {
     ERS_TRY(cudaMemcpy(s->perm, perm.data(), sizeof(int) * N, cudaMemcpyHostToDevice));
     ERS_TRY(cudaMemcpy(s->rec, rec.data(), sizeof(double) * N * REC, cudaMemcpyHostToDevice));
     ERS_TRY(cudaMemcpy(s->rec32, rec32.data(), sizeof(float) * N * REC, cudaMemcpyHostToDevice));
+    ERS_TRY(cudaMemcpy(s->recp, recp.data(), sizeof(float) * N * NREC, cudaMemcpyHostToDevice));
     ERS_TRY(cudaMemcpy(s->tilec, tilec.data(), sizeof(float) * s->ntile32 * 4, cudaMemcpyHostToDevice));
     ERS_TRY(cudaMemcpy(s->xs32, xs32.data(), sizeof(float4) * N, cudaMemcpyHostToDevice));
     ERS_TRY(cudaMemcpy(s->cell_start, cstart.data(), sizeof(int) * (G.ncell + 1), cudaMemcpyHostToDevice));

@@ -97,6 +97,7 @@ struct ers_surface {
     float *tilec = nullptr;       // ntile32 * 4 floats (centre of each FP32 tile, exact floats)
     float4 *xs32 = nullptr;       // N float coordinates for the near-field prefilter
     double *fq = nullptr;         // N * 6: the node densities f, q as given (for the closure's jets)
+    float *recp = nullptr;        // N * NREC floats: the near-field record (cell-sorted)
     int *cell_start = nullptr;    // ncell + 1
     ers::Grid grid{};
     int64_t ntile32 = 0;
@@ -155,8 +156,15 @@ const double *sigma_sharp_table_dev(int *err);  // the on-surface (s#) table
 
 // Device-side view of a surface, passed by value in kernel parameters (the ers_surface
 // struct itself lives in host memory).
+// Near-field record of a node, 96 bytes in cell-sorted order: x as three doubles (the pair
+// geometry and the near/far partition stay FP64), then w f, w n and q as float pairs (hi, lo),
+// hi + lo within 2^-48 of the FP64 value.  Float offsets:
+constexpr int NREC = 24;
+constexpr int NR_WF = 6, NR_WN = 12, NR_Q = 18;
+
 struct SurfDev {
     const double *rec;
+    const float *recp;
     const float *rec32;
     const float *tilec;
     const float4 *xs32;
@@ -169,6 +177,7 @@ struct SurfDev {
 inline SurfDev surf_dev(const ers_surface *s) {
     SurfDev d;
     d.rec = s->rec;
+    d.recp = s->recp;
     d.rec32 = s->rec32;
     d.tilec = s->tilec;
     d.xs32 = s->xs32;
@@ -407,6 +416,39 @@ __device__ __forceinline__ void pair_add(float &kh, float &kl, float f) {
 
 // h + l as a double (one FP64 add).
 __device__ __forceinline__ double pair_to_double(float h, float l) { return float_to_double(h) + float_to_double(l); }
+
+// The same arithmetic on a value type, for the near-field contractions.  Error bounds (u = 2^-24):
+// fp_mul returns the exact product of the leading floats plus the cross terms, unnormalized
+// (|l| <= 3u |h|), with error <= ~2u^2 |a b|; fp_add is Knuth's two-sum of the leading floats
+// with the trailing ones added, then renormalized, with error <= ~2u^2 (|a| + |b|).  Either
+// kind of pair (normalized or not) is a valid operand.
+struct fpair {
+    float h, l;
+};
+
+__device__ __forceinline__ fpair fp_split(double x) {
+    fpair r;
+    split_pair(x, r.h, r.l);
+    return r;
+}
+__device__ __forceinline__ fpair fp_neg(fpair a) { return {-a.h, -a.l}; }
+__device__ __forceinline__ fpair fp_mul(fpair a, fpair b) {
+    const float p = __fmul_rn(a.h, b.h);
+    return {p, __fmaf_rn(a.h, b.l, __fmaf_rn(a.l, b.h, __fmaf_rn(a.h, b.h, -p)))};
+}
+__device__ __forceinline__ fpair fp_add(fpair a, fpair b) {
+    const float s = __fadd_rn(a.h, b.h);
+    const float v = __fsub_rn(s, a.h);
+    const float e = __fadd_rn(__fsub_rn(a.h, __fsub_rn(s, v)), __fsub_rn(b.h, v));
+    const float w = __fadd_rn(e, __fadd_rn(a.l, b.l));
+    const float h = __fadd_rn(s, w);
+    return {h, __fsub_rn(w, __fsub_rn(h, s))};
+}
+__device__ __forceinline__ fpair fp_fma(fpair a, fpair b, fpair c) { return fp_add(fp_mul(a, b), c); }
+__device__ __forceinline__ fpair fp_dot3(fpair a0, fpair a1, fpair a2, fpair b0, fpair b1, fpair b2) {
+    return fp_fma(a2, b2, fp_fma(a1, b1, fp_mul(a0, b0)));
+}
+__device__ __forceinline__ double fp_to_double(fpair a) { return pair_to_double(a.h, a.l); }
 
 }  // namespace ers
 #endif

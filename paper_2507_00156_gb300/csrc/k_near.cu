@@ -10,7 +10,9 @@
 // tau = (r/delta)^2, and sigma_p comes from a piecewise degree-6 interpolation table.
 // Single layer (Eq. (Sreg)):  K1 g + K3 d (d.g).
 // Double layer (Eqs. (Tsplit), (Treg)):  -6 [ t1 (K3 - (r^2 - b^2) K5) + t2 K5 ] : Q (w n),
-// contracted in closed form (dl_pair / dl_accumulate in near_common.cuh).
+// contracted in closed form (dl_accumulate_pair in near_common.cuh).  Kernel factors and both
+// contractions run in float pairs on the FP32 pipe (~2^-46 relative; the FP64 pipe of this part
+// runs at 1/64 of the FP32 rate); d, r^2 and the near/far test stay FP64.
 // The weights alpha are the first row of the inverse of A_k = [1, rho_k I0(b/delta_k),
 // rho_k^3 I2(b/delta_k)] (Eqs. (extrap_eqn), (I0), (I2)), by Cramer's rule.  The O(delta^7)
 // variant (Sec. 1) runs the same kernel with four deltas (ND = 4, A_k with rho_k^5 I4 appended).
@@ -32,23 +34,27 @@ using namespace nearc;
 constexpr int WPB = 4;  // warps per block
 constexpr int NEAR_MIN_BLOCKS = 3;
 
-// One near pair of class cls (run-time for the classes with table-path deltas, ALLDEF = false;
-// ALLDEF = true: cls = ND, every delta on the defect path).
-template <bool ALLDEF, int PREC, bool SL, bool DL, int ND>
-__device__ __forceinline__ void process(const EvalArgs &A, const Geom &T, const ScanParams &P, double c,
-                                        const double q0[3], const double *__restrict__ tab, int64_t j, int cls,
-                                        double accU[3], double &accN, double accD[3], int npairs[NCLS_MAX],
+// One near pair of class cls, a run-time value (one code path for every class keeps the kernel
+// within the instruction cache); cls = ND: every delta on the defect path.  The pair geometry d,
+// r^2 and the near/far test in FP64; kernel factors and contractions in float pairs (nc = -c and
+// q0 of the target as float pairs), accumulated per lane in float pairs.
+template <int PREC, bool SL, bool DL, int ND>
+__device__ __forceinline__ void process(const EvalArgs &A, const Geom &T, const ScanParams &P, fpair nc,
+                                        const fpair q0[3], const double *__restrict__ tab, int64_t j, int cls,
+                                        fpair accU[3], fpair &accN, fpair accD[3], int npairs[NCLS_MAX],
                                         int nunreg[MAXD]) {
-    const double2 *r = reinterpret_cast<const double2 *>(A.sd.rec + j * REC);
-    const double2 r0 = __ldg(r + 0), r1 = __ldg(r + 1), r2v = __ldg(r + 2);
-    const double2 r3 = __ldg(r + 3), r4 = __ldg(r + 4), r5 = __ldg(r + 5);
-    const double xs[3] = {r0.x, r0.y, r1.x};
-    const double wf[3] = {r1.y, r2v.x, r2v.y};
-    const double wn[3] = {r3.x, r3.y, r4.x};
-    const double qs[3] = {r4.y, r5.x, r5.y};
-    const double dx = __dsub_rn(T.y[0], xs[0]);
-    const double dy = __dsub_rn(T.y[1], xs[1]);
-    const double dz = __dsub_rn(T.y[2], xs[2]);
+    const float4 *r = reinterpret_cast<const float4 *>(A.sd.recp + j * NREC);
+    const float4 a0 = __ldg(r + 0), a1 = __ldg(r + 1), a2 = __ldg(r + 2);
+    const float4 a3 = __ldg(r + 3), a4 = __ldg(r + 4), a5 = __ldg(r + 5);
+    const double xs0 = __hiloint2double(__float_as_int(a0.y), __float_as_int(a0.x));
+    const double xs1 = __hiloint2double(__float_as_int(a0.w), __float_as_int(a0.z));
+    const double xs2 = __hiloint2double(__float_as_int(a1.y), __float_as_int(a1.x));
+    const fpair wf[3] = {{a1.z, a1.w}, {a2.x, a2.y}, {a2.z, a2.w}};
+    const fpair wn[3] = {{a3.x, a3.y}, {a3.z, a3.w}, {a4.x, a4.y}};
+    const fpair qs[3] = {{a4.z, a4.w}, {a5.x, a5.y}, {a5.z, a5.w}};
+    const double dx = __dsub_rn(T.y[0], xs0);
+    const double dy = __dsub_rn(T.y[1], xs1);
+    const double dz = __dsub_rn(T.y[2], xs2);
     const double r2 = dist2_fp64(dx, dy, dz);
     if (!is_near<PREC>(A.sd, T, j, r2, A.Rc, P.rc2f)) return;
 #pragma unroll
@@ -60,24 +66,13 @@ __device__ __forceinline__ void process(const EvalArgs &A, const Geom &T, const 
 #pragma unroll
         for (int k = 0; k < (ND == 4 ? 4 : 3); ++k) nunreg[k] += u == k;
     }
-    double K1, K3, K5;
+    const fpair r2p = fp_split(r2);
+    fpair K[3];
     float Lf;
-    kernel_factors_rt<ALLDEF, ND>(T, P, tab, r2, cls, K1, K3, K5, Lf);
-    if (SL) sl_accumulate(dx, dy, dz, K1, K3, c, wf, wn, accU);
-    if (DL) {
-        const double W = fma(dz, wn[2], fma(dy, wn[1], dx * wn[0]));
-        if (ALLDEF) {  // every delta on the defect path: L and what it multiplies in FP32
-            const float nmf = fmaf(approx_float(T.n0[2]), approx_float(wn[2]),
-                                   fmaf(approx_float(T.n0[1]), approx_float(wn[1]),
-                                        approx_float(T.n0[0]) * approx_float(wn[0])));
-            const float Zf = fmaf(approx_float(T.b2), nmf, -approx_float(W));
-            dl_accumulate_defect(T, dx, dy, dz, Lf, K5 * W, nmf, Zf, qs, q0, accN, accD);
-        } else {
-            const double nm = fma(T.n0[2], wn[2], fma(T.n0[1], wn[1], T.n0[0] * wn[0]));
-            const DLPair D = dl_pair(T, r2, K3, K5, nm, W);
-            dl_accumulate(D, T, dx, dy, dz, nm, qs, q0, accN, accD);
-        }
-    }
+    kernel_factors_pair<false, ND>(T, P, tab, r2, r2p, cls, K, Lf);
+    const fpair d[3] = {fp_split(dx), fp_split(dy), fp_split(dz)};
+    if (SL) sl_accumulate_pair(d, K[0], K[1], nc, wf, wn, accU);
+    if (DL) dl_accumulate_pair(T, d, r2p, K[1], K[2], wn, qs, q0, accN, accD);
 }
 
 // On-surface target with ERS_OPT_SHARP (b = 0): one regularized sum with the modified
@@ -198,21 +193,22 @@ __device__ __forceinline__ void near_target(const EvalArgs &A, const ScanParams 
     double q0[3];
     for (int i = 0; i < 3; ++i) q0[i] = DL ? A.q0[3 * m + i] : 0.0;
     const double c = SL ? fma(A.f0[3 * m + 2], T.n0[2], fma(A.f0[3 * m + 1], T.n0[1], A.f0[3 * m] * T.n0[0])) : 0.0;
+    const fpair ncp = fp_split(-c), q0p[3] = {fp_split(q0[0]), fp_split(q0[1]), fp_split(q0[2])};
 
     constexpr int NC = ND == 4 ? 5 : NCLS;  // pair classes
-    double accU[3] = {0.0, 0.0, 0.0}, accD[3] = {0.0, 0.0, 0.0}, accN = 0.0;
+    fpair pU[3] = {{0.0f, 0.0f}, {0.0f, 0.0f}, {0.0f, 0.0f}}, pD[3] = {{0.0f, 0.0f}, {0.0f, 0.0f}, {0.0f, 0.0f}};
+    fpair pN = {0.0f, 0.0f};
     int npairs[NCLS_MAX] = {0, 0, 0, 0, 0};  // near pairs by class
     int nunreg[MAXD] = {0, 0, 0, 0};         // near pairs by number of deltas beyond the cutoff
     scan_near<NC>(A.sd, T, P, sq, lane, [&](int cls, int jj, bool valid) {
-        if (!valid) return;
-        if (cls < ND) process<false, PREC, SL, DL, ND>(A, T, P, c, q0, tab, jj, cls, accU, accN, accD, npairs, nunreg);
-        else process<true, PREC, SL, DL, ND>(A, T, P, c, q0, tab, jj, ND, accU, accN, accD, npairs, nunreg);
+        if (valid) process<PREC, SL, DL, ND>(A, T, P, ncp, q0p, tab, jj, cls, pU, pN, pD, npairs, nunreg);
     });
+    double accU[3], accD[3];
     for (int i = 0; i < 3; ++i) {
-        accU[i] = warp_sum(accU[i]);
-        accD[i] = warp_sum(accD[i]);
+        accU[i] = warp_sum(fp_to_double(pU[i]));
+        accD[i] = warp_sum(fp_to_double(pD[i]));
     }
-    accN = warp_sum(accN);
+    const double accN = warp_sum(fp_to_double(pN));
     if (A.counters) {
         // counters: [2 + c] class c < 4, [6 + u] u < 3 deltas beyond the cutoff, [10] class 4, [11] u = 3
         int np[9] = {npairs[0], npairs[1], npairs[2], npairs[3], nunreg[0], nunreg[1], nunreg[2], npairs[4], nunreg[3]};

@@ -109,16 +109,23 @@ __global__ void k_closest(double c0, double c1, double c2, double a0, double a1,
 // sorted node j of canonical index perm[j].  Only the density parts are written here.
 __global__ void k_density(const int *__restrict__ perm, const double *__restrict__ w, const double *__restrict__ f,
                           const double *__restrict__ q, int64_t N, double *__restrict__ rec,
-                          float *__restrict__ rec32, double *__restrict__ fq) {
+                          float *__restrict__ rec32, float *__restrict__ recp, double *__restrict__ fq) {
     const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (j >= N) return;
     const int64_t i = perm[j];
     const double wi = w[i];
+    // float pair of v in the near-field record: hi = v rounded, lo = the rest rounded
+    auto put_pair = [&](int off, double v) {
+        const float hi = __double2float_rn(v);
+        recp[j * NREC + off] = hi;
+        recp[j * NREC + off + 1] = __double2float_rn(v - (double)hi);
+    };
     if (f) {
         for (int k = 0; k < 3; ++k) {
             const double v = wi * f[3 * i + k];
             rec[j * REC + R_WF + k] = v;
             rec32[j * REC + R_WF + k] = __double2float_rn(v);
+            put_pair(NR_WF + 2 * k, v);
             fq[j * 6 + k] = f[3 * i + k];
         }
     }
@@ -127,6 +134,7 @@ __global__ void k_density(const int *__restrict__ perm, const double *__restrict
             const double v = q[3 * i + k];
             rec[j * REC + R_Q + k] = v;
             rec32[j * REC + R_Q + k] = __double2float_rn(v);
+            put_pair(NR_Q + 2 * k, v);
             fq[j * 6 + 3 + k] = v;
         }
     }
@@ -148,7 +156,7 @@ cudaError_t launch_closest(const ers_surface *s, const double *y, int64_t M, dou
 cudaError_t launch_density(ers_surface *s, const double *f, const double *q, cudaStream_t st) {
     const int bs = 256;
     const int64_t grid = (s->N + bs - 1) / bs;
-    k_density<<<(unsigned)grid, bs, 0, st>>>(s->perm, s->w, f, q, s->N, s->rec, s->rec32, s->fq);
+    k_density<<<(unsigned)grid, bs, 0, st>>>(s->perm, s->w, f, q, s->N, s->rec, s->rec32, s->recp, s->fq);
     return cudaGetLastError();
 }
 

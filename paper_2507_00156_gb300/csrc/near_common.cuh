@@ -38,6 +38,7 @@ struct Geom {
     float alf[MAXD];           // extrapolation weights in FP32 (for the small defects 1 - s_p)
     float adh[3][MAXD], adl[3][MAXD];  // alpha_k / delta_k^p (p = 1, 3, 5) as float pairs
     float aph[MAXD], apl[MAXD];        // apre as float pairs
+    fpair n0p[3], b2p;                 // n0 and 2 b as float pairs (the near kernel's contractions)
     float tcf2;             // cutoff_t^2: s_p := 1 beyond t = cutoff_t
     bool cut_small;         // cutoff_t < DEFECT_T: the table path may meet the cutoff
 };
@@ -201,6 +202,8 @@ __device__ __forceinline__ void load_geom(int lane, const double *y, const doubl
     }
     T.b = b;
     T.b2 = 2.0 * b;
+    for (int i = 0; i < 3; ++i) T.n0p[i] = fp_split(T.n0[i]);
+    T.b2p = fp_split(T.b2);
     double al[MAXD] = {1.0, 0.0, 0.0, 0.0};
     if (ndelta == 4) {
         extrap_weights4(lane, b, rho, h, al);
@@ -327,12 +330,12 @@ __device__ __forceinline__ void table_pairs_r2(const double *__restrict__ tab, d
 // ROLL: the loops over deltas stay rolled (code size; T must then sit in shared memory, as in
 // k_near, since the loops index its arrays at run time); otherwise they unroll for a compile-time
 // cls (the batched kernel, whose Geom lives in registers).
+// K1, K3, K5 as float pairs (~2^-46 relative); r2p = r2 as a float pair.
 template <bool ALLDEF, int ND, bool ROLL = true>
-__device__ __forceinline__ void kernel_factors_rt(const Geom &T, const ScanParams &P, const double *__restrict__ tab,
-                                                  double r2, int cls, double &K1, double &K3, double &K5, float &Lf) {
+__device__ __forceinline__ void kernel_factors_pair(const Geom &T, const ScanParams &P, const double *__restrict__ tab,
+                                                    double r2, fpair r2p, int cls, fpair K[3], float &Lf) {
     const int NDEF = ALLDEF ? ND : cls;  // defect-path deltas that carry weight
     Lf = 0.0f;
-    // K1, K3, K5 accumulate in float pairs (~2^-46 relative) and leave as doubles with one FP64 add each
     float kh[3] = {0.0f, 0.0f, 0.0f}, kl[3] = {0.0f, 0.0f, 0.0f};
     if (ALLDEF || cls >= 1) {
         // r / delta_k > DEFECT_T: s_p = 1 - eps_p with eps_1 = erfc t, eps_2 = eps_1 + (2/sqrt pi) t e^{-t^2},
@@ -343,8 +346,7 @@ __device__ __forceinline__ void kernel_factors_rt(const Geom &T, const ScanParam
         //    cross terms), so that e^{-tau} = e^{-tau_h} (1 - tau_l) loses nothing to the rounding of tau;
         //  - erfc t = e^{-t^2} / (t sqrt pi) (1 - 1/(2t^2) + 3/(4t^4) - 15/(8t^6)), the asymptotic series
         //    (Abramowitz & Stegun 7.1.23), truncation below 3e-5 relative for t >= 4.7.
-        float r2h, r2l;
-        split_pair(r2, r2h, r2l);
+        const float r2h = r2p.h, r2l = r2p.l;
         float E1 = 0.0f, E3 = 0.0f, E5 = 0.0f;
         auto defect = [&](int k) {
             const float th = r2h * T.id2h[k];
@@ -396,7 +398,7 @@ __device__ __forceinline__ void kernel_factors_rt(const Geom &T, const ScanParam
         pair_add(kh[0], kl[0], -(E1 * r1h));
         pair_add(kh[1], kl[1], -(E3 * r3h));
         pair_add(kh[2], kl[2], -(E5 * r5h));
-        if (ALLDEF) Lf = (E3 - E5) * r3h;
+        if (ALLDEF || cls == ND) Lf = (E3 - E5) * r3h;
     }
     if (!ALLDEF) {
         // the table-path deltas: (alpha_k / delta_k^p) sigma_p(tau_k)
@@ -424,9 +426,19 @@ __device__ __forceinline__ void kernel_factors_rt(const Geom &T, const ScanParam
                 if (k >= cls) table(k);
         }
     }
-    K1 = pair_to_double(kh[0], kl[0]);
-    K3 = pair_to_double(kh[1], kl[1]);
-    K5 = pair_to_double(kh[2], kl[2]);
+#pragma unroll
+    for (int p = 0; p < 3; ++p) K[p] = {kh[p], kl[p]};
+}
+
+// The same factors as doubles (one FP64 add each).
+template <bool ALLDEF, int ND, bool ROLL = true>
+__device__ __forceinline__ void kernel_factors_rt(const Geom &T, const ScanParams &P, const double *__restrict__ tab,
+                                                  double r2, int cls, double &K1, double &K3, double &K5, float &Lf) {
+    fpair K[3];
+    kernel_factors_pair<ALLDEF, ND, ROLL>(T, P, tab, r2, fp_split(r2), cls, K, Lf);
+    K1 = fp_to_double(K[0]);
+    K3 = fp_to_double(K[1]);
+    K5 = fp_to_double(K[2]);
 }
 
 template <int CLS, int ND = 3>
@@ -498,6 +510,40 @@ __device__ __forceinline__ void dl_accumulate_defect(const Geom &T, double dx, d
     accD[0] = fma(C, dx, accD[0]);
     accD[1] = fma(C, dy, accD[1]);
     accD[2] = fma(C, dz, accD[2]);
+}
+
+// The contractions above in float pairs (the near kernel): operands from the near-field record
+// and the target's pairs, results added into per-lane float-pair accumulators.  Each result
+// carries an error ~2^-46 of the magnitudes it is formed from, as the FP64 forms do at 2^-53,
+// far below the 1e-11 the FP64 path is held to.  The double layer uses the general form for
+// every class: where all deltas are on the defect path L = r^2 K5 - K3 is ~1e-7 of K3 or less,
+// and its float-pair error, ~2^-46 of K3, is of the size of the other terms' errors.
+__device__ __forceinline__ void sl_accumulate_pair(const fpair d[3], fpair K1, fpair K3, fpair nc, const fpair wf[3],
+                                                   const fpair wn[3], fpair accU[3]) {
+    const fpair g0 = fp_fma(nc, wn[0], wf[0]);  // g = w f - c w n, nc = -c
+    const fpair g1 = fp_fma(nc, wn[1], wf[1]);
+    const fpair g2 = fp_fma(nc, wn[2], wf[2]);
+    const fpair t = fp_mul(K3, fp_dot3(d[0], d[1], d[2], g0, g1, g2));
+    accU[0] = fp_add(accU[0], fp_fma(t, d[0], fp_mul(K1, g0)));
+    accU[1] = fp_add(accU[1], fp_fma(t, d[1], fp_mul(K1, g1)));
+    accU[2] = fp_add(accU[2], fp_fma(t, d[2], fp_mul(K1, g2)));
+}
+
+__device__ __forceinline__ void dl_accumulate_pair(const Geom &T, const fpair d[3], fpair r2, fpair K3, fpair K5,
+                                                   const fpair wn[3], const fpair qs[3], const fpair q0[3],
+                                                   fpair &accN, fpair accD[3]) {
+    const fpair W = fp_dot3(d[0], d[1], d[2], wn[0], wn[1], wn[2]);
+    const fpair nm = fp_dot3(T.n0p[0], T.n0p[1], T.n0p[2], wn[0], wn[1], wn[2]);
+    const fpair L = fp_fma(r2, K5, fp_neg(K3));
+    const fpair Z = fp_fma(T.b2p, nm, fp_neg(W));
+    const fpair Q0 = fp_add(qs[0], fp_neg(q0[0])), Q1 = fp_add(qs[1], fp_neg(q0[1])), Q2 = fp_add(qs[2], fp_neg(q0[2]));
+    const fpair nQ = fp_dot3(T.n0p[0], T.n0p[1], T.n0p[2], Q0, Q1, Q2);
+    const fpair U = fp_dot3(d[0], d[1], d[2], Q0, Q1, Q2);
+    accN = fp_add(accN, fp_mul(L, fp_fma(nQ, Z, fp_neg(fp_mul(nm, U)))));
+    const fpair C = fp_fma(fp_mul(L, nm), nQ, fp_neg(fp_mul(fp_mul(K5, W), U)));
+    accD[0] = fp_fma(C, d[0], accD[0]);
+    accD[1] = fp_fma(C, d[1], accD[1]);
+    accD[2] = fp_fma(C, d[2], accD[2]);
 }
 
 // Walk the rows of the surface's cell grid that meet the prefilter ball around the target,

@@ -45,10 +45,10 @@ int ers_set_density_multi(ers_surface *s, const double *f, const double *q, int 
         return fail(ERS_E_INVAL, "ers_set_density_multi: nrhs must be 1, 2, 4 or 8");
     if (!f && !q) return fail(ERS_E_INVAL, "ers_set_density_multi: give f, q or both");
     const size_t n = (size_t)s->N * nrhs * 6;
-    int rc = grow(s->dens64, n * sizeof(double));
+    int rc = grow(s->densp, n * sizeof(float2));
     if (rc == ERS_OK) rc = grow(s->dens32, (size_t)s->N * batch_rec32_floats(nrhs) * sizeof(float));
     if (rc != ERS_OK) return rc;
-    cudaError_t e = launch_density_multi(s->perm, s->w, s->rec32, f, q, s->N, nrhs, (double *)s->dens64.ptr,
+    cudaError_t e = launch_density_multi(s->perm, s->w, s->rec32, f, q, s->N, nrhs, (float2 *)s->densp.ptr,
                                          (float *)s->dens32.ptr, (cudaStream_t)stream);
     if (e != cudaSuccess) return cuda_fail(e, "ers_set_density_multi: density kernel");
     s->nrhs_multi = nrhs;
@@ -90,7 +90,7 @@ int ers_batch_create(const ers_problem *probs, int nprob, const ers_params *p, i
         if (q.M > 0 && dl && (!q.q0 || !q.v)) return fail(ERS_E_INVAL, at + "double layer needs q0 and v");
         BatchProblemDev &d = hp[i];
         d.sd = surf_dev(q.s);
-        d.dens64 = (const double *)q.s->dens64.ptr;
+        d.densp = (const float2 *)q.s->densp.ptr;
         d.dens32 = (const float *)q.s->dens32.ptr;
         d.y = q.y;
         d.x0 = q.x0;

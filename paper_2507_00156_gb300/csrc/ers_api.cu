@@ -48,7 +48,7 @@ void free_surface(ers_surface *s) {
     if (!s) return;
     void *ptrs[] = {s->x, s->n, s->w, s->perm, s->rec, s->rec32, s->recp, s->tilec, s->xs32, s->fq, s->cell_start, s->cell_rank,
                     s->okeys.ptr, s->oorder.ptr, s->ohist.ptr,
-                    s->part.ptr, s->cp.ptr, s->host_io.ptr, s->counts.ptr, s->dens64.ptr, s->dens32.ptr,
+                    s->part.ptr, s->cp.ptr, s->host_io.ptr, s->counts.ptr, s->densp.ptr, s->dens32.ptr,
                     s->fitw.ptr};
     for (void *p : ptrs)
         if (p) cudaFree(p);

@@ -105,9 +105,10 @@ struct ers_surface {
     // work buffers (grow-only)
     ers::Scratch part, cp, host_io, counts;
     ers::Scratch fitw;  // the learned closure's density fits: neighbour lists and normal equations
-    // densities of several right-hand sides (ers_set_density_multi), cell-sorted: FP64
-    // [N][nrhs][6] (w f, q) and the FP32 far-field record [N][batch_rec32_floats(nrhs)]
-    ers::Scratch dens64, dens32;
+    // densities of several right-hand sides (ers_set_density_multi), cell-sorted: float pairs
+    // [N][nrhs][6] (w f, q) for the near field and the FP32 far-field record
+    // [N][batch_rec32_floats(nrhs)]
+    ers::Scratch densp, dens32;
     int nrhs_multi = 0;
     int64_t last_counts[3] = {0, 0, 0};
     int64_t last_class[4] = {0, 0, 0, 0};     // near pairs by number of deltas with r > cutoff_t delta
@@ -230,7 +231,7 @@ cudaError_t launch_density(ers_surface *s, const double *f, const double *q, cud
 struct BatchProblemDev;
 struct BatchItem;
 cudaError_t launch_density_multi(const int *perm, const double *w, const float *rec32, const double *f,
-                                 const double *q, int64_t N, int nr, double *d64, float *d32, cudaStream_t st);
+                                 const double *q, int64_t N, int nr, float2 *dp, float *d32, cudaStream_t st);
 // floats per node of the batched FP32 far-field record for nr densities (multiple of 4)
 inline int batch_rec32_floats(int nr) { return (6 + 6 * nr + 3) / 4 * 4; }
 int batch_grid(int nr, int nsm);

@@ -6,7 +6,8 @@
 //      subtracted densities of Eqs. (Stokes_SL1), (Stokes_DL1)), r > Rc only; the geometry of a
 //      pair (d, 1/r) is computed once and shared by the NR densities; FP32 sums over 512
 //      sources are added into FP64 sums kept in the output arrays u, v themselves;
-//   2. near field and extrapolation (Secs. 2, 3.2, 3.3) in FP64, one warp per target, with the
+//   2. near field and extrapolation (Secs. 2, 3.2, 3.3), one warp per target: pair geometry in
+//      FP64, kernel factors and contractions in float pairs (as in k_near), with the
 //      alpha-weighted kernel factors of a pair shared by the NR densities;
 //   3. u = far + near (+ chi q(x0) for the double layer), written for every density.
 // Items carry no dependency on each other, so CTAs take them from an atomic counter in any
@@ -35,9 +36,10 @@ template <int NR>
 struct BatchSmem {
     union {
         float4 stage[BTS][S4<NR>];   // far phase: one stage of source records
-        double near[BW][NR][7][32];  // near phase: per-lane accumulators (SL without c_r wn; N; D)
+        float2 near[BW][NR][7][32];  // near phase: per-lane float-pair accumulators (SL without c_r wn; N; D)
     } u;
     double tq[BW][NR][4];  // near phase: c_r = f0_r . n0 and q0_r of each warp's target
+    fpair tqp[BW][NR][4];  // the same as float pairs
     Geom g[BW];            // near phase: each warp's target constants (indexed at run time)
     int sq[BW][NCLS][64];
     float4 cen;
@@ -184,68 +186,73 @@ __device__ void far_phase(const BatchProblemDev &P, int tb, int layers, BatchSme
     __syncthreads();  // the far sums in u, v are visible to the whole CTA
 }
 
-// One near pair for the NR densities: the kernel factors, the single-layer terms without the
-// c_r w n part (K1 w f + K3 (d.w f) d per density, and K1 w n + K3 (d.w n) d once, into accB,
-// subtracted c_r times at the end) and the double-layer terms.  The pair class cls is a run-time
-// value for the classes with table-path deltas (ALLDEF = false, one code path) and 3 otherwise.
-template <bool ALLDEF, int NR>
+// The near-field terms of one pair (class cls, a run-time value) for the NR densities, in float
+// pairs as in k_near: d, w n, the kernel factors and the double-layer pair factors are shared by
+// the densities; per density the single-layer K1 w f + K3 (d.w f) d (the c_r w n part,
+// K1 w n + K3 (d.w n) d, is summed once per pair into accB and subtracted c_r times at the end)
+// and the double-layer contraction (dl_accumulate_pair), into the lane's float-pair
+// accumulators in shared memory.
+template <int NR>
 __device__ __forceinline__ void near_pair(const BatchProblemDev &P, const Geom &T, const double *__restrict__ tab,
                                           int64_t j, int cls, int lane, int warp, int layers, BatchSmem<NR> &S,
-                                          double accB[3]) {
-    const double *rec = P.sd.rec + j * REC;
-    const double xs[3] = {__ldg(rec + R_X), __ldg(rec + R_X + 1), __ldg(rec + R_X + 2)};
-    const double wn[3] = {__ldg(rec + R_WN), __ldg(rec + R_WN + 1), __ldg(rec + R_WN + 2)};
-    const double dx = __dsub_rn(T.y[0], xs[0]);
-    const double dy = __dsub_rn(T.y[1], xs[1]);
-    const double dz = __dsub_rn(T.y[2], xs[2]);
+                                          fpair accB[3]) {
+    const float4 *rp = reinterpret_cast<const float4 *>(P.sd.recp + j * NREC);
+    const float4 a0 = __ldg(rp + 0), a1 = __ldg(rp + 1), a3 = __ldg(rp + 3), a4 = __ldg(rp + 4);
+    const double dx = __dsub_rn(T.y[0], __hiloint2double(__float_as_int(a0.y), __float_as_int(a0.x)));
+    const double dy = __dsub_rn(T.y[1], __hiloint2double(__float_as_int(a0.w), __float_as_int(a0.z)));
+    const double dz = __dsub_rn(T.y[2], __hiloint2double(__float_as_int(a1.y), __float_as_int(a1.x)));
     const double r2 = dist2_fp64(dx, dy, dz);
     if (!is_near<ERS_PREC_MIXED>(P.sd, T, j, r2, P.Rc, P.sp.rc2f)) return;
-    double K1, K3, K5;
-    float Lf;
-    kernel_factors_rt<ALLDEF, 3>(T, P.sp, tab, r2, cls, K1, K3, K5, Lf);
-    const double W = fma(dz, wn[2], fma(dy, wn[1], dx * wn[0]));
-    // every delta on the defect path (CLS = 3): L and the factors it multiplies in FP32
-    // (dl_accumulate_defect); otherwise the FP64 pair factors, shared by the NR densities
-    double nm = 0.0;
-    float nmf = 0.0f, Zf = 0.0f;
-    DLPair D{};
-    if (ALLDEF) {
-        nmf = fmaf(approx_float(T.n0[2]), approx_float(wn[2]),
-                   fmaf(approx_float(T.n0[1]), approx_float(wn[1]), approx_float(T.n0[0]) * approx_float(wn[0])));
-        Zf = fmaf(approx_float(T.b2), nmf, -approx_float(W));
-    } else {
-        nm = fma(T.n0[2], wn[2], fma(T.n0[1], wn[1], T.n0[0] * wn[0]));
-        D = dl_pair(T, r2, K3, K5, nm, W);
-    }
-    const double K5W = K5 * W;
+    const fpair wn[3] = {{a3.x, a3.y}, {a3.z, a3.w}, {a4.x, a4.y}};
+    const fpair r2p = fp_split(r2);
+    fpair K[3];
+    kernel_factors_pair<3>(T, P.sp, tab, r2, r2p, cls, K);
+    const fpair d[3] = {fp_split(dx), fp_split(dy), fp_split(dz)};
+    const fpair W = fp_dot3(d[0], d[1], d[2], wn[0], wn[1], wn[2]);
     const bool sl = layers & ERS_LAYER_SL, dl = layers & ERS_LAYER_DL;
     if (sl) {
-        const double tb = K3 * W;
-        accB[0] = fma(K1, wn[0], fma(tb, dx, accB[0]));
-        accB[1] = fma(K1, wn[1], fma(tb, dy, accB[1]));
-        accB[2] = fma(K1, wn[2], fma(tb, dz, accB[2]));
+        const fpair tb = fp_mul(K[1], W);
+#pragma unroll
+        for (int i = 0; i < 3; ++i) accB[i] = fp_add(accB[i], fp_fma(tb, d[i], fp_mul(K[0], wn[i])));
     }
-    const double2 *dj = reinterpret_cast<const double2 *>(P.dens64 + j * (6 * NR));
+    // double-layer pair factors: L = r^2 K5 - K3, Z = 2 b nm - W, L nm, K5 W (nm = n0.w n)
+    fpair nm = {0.0f, 0.0f}, Z = nm, Lnm = nm, K5W = nm, L = nm;
+    if (dl) {
+        nm = fp_dot3(T.n0p[0], T.n0p[1], T.n0p[2], wn[0], wn[1], wn[2]);
+        L = fp_fma(r2p, K[2], fp_neg(K[1]));
+        Z = fp_fma(T.b2p, nm, fp_neg(W));
+        Lnm = fp_mul(L, nm);
+        K5W = fp_mul(K[2], W);
+    }
+    const float4 *dj = reinterpret_cast<const float4 *>(P.densp + j * (6 * NR));
 #pragma unroll 2
     for (int r = 0; r < NR; ++r) {
-        double(*a)[32] = S.u.near[warp][r];
-        const double2 d0 = __ldg(dj + 3 * r), d1 = __ldg(dj + 3 * r + 1), d2 = __ldg(dj + 3 * r + 2);
-        if (sl) {  // K1 w f + K3 (d.w f) d
-            const double t = K3 * fma(dz, d1.x, fma(dy, d0.y, dx * d0.x));
-            a[0][lane] = fma(K1, d0.x, fma(t, dx, a[0][lane]));
-            a[1][lane] = fma(K1, d0.y, fma(t, dy, a[1][lane]));
-            a[2][lane] = fma(K1, d1.x, fma(t, dz, a[2][lane]));
+        float2(*a)[32] = S.u.near[warp][r];
+        // (w f0, w f1), (w f2, q0), (q1, q2), each a float pair
+        const float4 d0 = __ldg(dj + 3 * r), d1 = __ldg(dj + 3 * r + 1), d2 = __ldg(dj + 3 * r + 2);
+        if (sl) {
+            const fpair wf[3] = {{d0.x, d0.y}, {d0.z, d0.w}, {d1.x, d1.y}};
+            const fpair t = fp_mul(K[1], fp_dot3(d[0], d[1], d[2], wf[0], wf[1], wf[2]));
+#pragma unroll
+            for (int i = 0; i < 3; ++i) {
+                const fpair s = fp_add({a[i][lane].x, a[i][lane].y}, fp_fma(t, d[i], fp_mul(K[0], wf[i])));
+                a[i][lane] = make_float2(s.h, s.l);
+            }
         }
         if (dl) {
-            const double qs[3] = {d1.y, d2.x, d2.y};
-            const double q0[3] = {S.tq[warp][r][1], S.tq[warp][r][2], S.tq[warp][r][3]};
-            double accN = a[3][lane], accD[3] = {a[4][lane], a[5][lane], a[6][lane]};
-            if (ALLDEF) dl_accumulate_defect(T, dx, dy, dz, Lf, K5W, nmf, Zf, qs, q0, accN, accD);
-            else dl_accumulate(D, T, dx, dy, dz, nm, qs, q0, accN, accD);
-            a[3][lane] = accN;
-            a[4][lane] = accD[0];
-            a[5][lane] = accD[1];
-            a[6][lane] = accD[2];
+            const fpair Q0 = fp_add({d1.z, d1.w}, fp_neg(S.tqp[warp][r][1]));
+            const fpair Q1 = fp_add({d2.x, d2.y}, fp_neg(S.tqp[warp][r][2]));
+            const fpair Q2 = fp_add({d2.z, d2.w}, fp_neg(S.tqp[warp][r][3]));
+            const fpair nQ = fp_dot3(T.n0p[0], T.n0p[1], T.n0p[2], Q0, Q1, Q2);
+            const fpair U = fp_dot3(d[0], d[1], d[2], Q0, Q1, Q2);
+            const fpair n = fp_add({a[3][lane].x, a[3][lane].y}, fp_mul(L, fp_fma(nQ, Z, fp_neg(fp_mul(nm, U)))));
+            a[3][lane] = make_float2(n.h, n.l);
+            const fpair C = fp_fma(Lnm, nQ, fp_neg(fp_mul(K5W, U)));
+#pragma unroll
+            for (int i = 0; i < 3; ++i) {
+                const fpair s = fp_fma(C, d[i], {a[4 + i][lane].x, a[4 + i][lane].y});
+                a[4 + i][lane] = make_float2(s.h, s.l);
+            }
         }
     }
 }
@@ -279,21 +286,24 @@ __device__ void near_phase(const BatchProblemDev &P, int tb, int layers, const d
                 }
                 if (k > 0 && dl) val = P.q0[((int64_t)r * P.M + m) * 3 + k - 1];
                 S.tq[warp][r][k] = val;
+                S.tqp[warp][r][k] = fp_split(val);
             }
             for (int r = 0; r < NR; ++r)
-                for (int i = 0; i < 7; ++i) S.u.near[warp][r][i][lane] = 0.0;
+                for (int i = 0; i < 7; ++i) S.u.near[warp][r][i][lane] = make_float2(0.0f, 0.0f);
             __syncwarp();
-            double accB[3] = {0.0, 0.0, 0.0};
+            fpair pB[3] = {{0.0f, 0.0f}, {0.0f, 0.0f}, {0.0f, 0.0f}};
             scan_near(P.sd, T, P.sp, S.sq[warp], lane, [&](int cls, int jj, bool valid) {
-                if (!valid) return;
-                if (cls < 3) near_pair<false, NR>(P, T, tab, jj, cls, lane, warp, layers, S, accB);
-                else near_pair<true, NR>(P, T, tab, jj, 3, lane, warp, layers, S, accB);
+                if (valid) near_pair<NR>(P, T, tab, jj, cls, lane, warp, layers, S, pB);
             });
-            for (int i = 0; i < 3; ++i) accB[i] = warp_sum(accB[i]);
+            double accB[3];
+            for (int i = 0; i < 3; ++i) accB[i] = warp_sum(fp_to_double(pB[i]));
             const double chi = bm < 0.0 ? 1.0 : (bm > 0.0 ? 0.0 : 0.5);
             for (int r = 0; r < NR; ++r) {
                 double tot[7];
-                for (int i = 0; i < 7; ++i) tot[i] = warp_sum(S.u.near[warp][r][i][lane]);
+                for (int i = 0; i < 7; ++i) {
+                    const float2 v = S.u.near[warp][r][i][lane];
+                    tot[i] = warp_sum(fp_to_double({v.x, v.y}));
+                }
                 if (sl && lane < 3) {
                     const double a = lane == 0 ? tot[0] : (lane == 1 ? tot[1] : tot[2]);
                     const double bb = lane == 0 ? accB[0] : (lane == 1 ? accB[1] : accB[2]);
@@ -339,13 +349,13 @@ __global__ void __launch_bounds__(BT, 3) k_batch(const BatchProblemDev *__restri
     }
 }
 
-// Densities of nr right-hand sides in cell-sorted order: FP64 [N][nr][6] (w f, q) for the near
-// field, and the FP32 far-field record [N][S] floats (S = 6 + 6 nr rounded up to a multiple of 4):
+// Densities of nr right-hand sides in cell-sorted order: float pairs [N][nr][6] (w f, q; hi = the
+// value rounded, lo = the rest rounded) for the near field, and the FP32 far-field record [N][S] floats (S = 6 + 6 nr rounded up to a multiple of 4):
 // x - c_tile and w n from the surface's FP32 record, then (w f, q) per density in the order of
 // rec_off (pairs of densities interleaved), zero padding.
 __global__ void k_density_multi(const int *__restrict__ perm, const double *__restrict__ w,
                                 const float *__restrict__ rec32, const double *__restrict__ f,
-                                const double *__restrict__ q, int64_t N, int nr, double *__restrict__ d64,
+                                const double *__restrict__ q, int64_t N, int nr, float2 *__restrict__ dp,
                                 float *__restrict__ d32) {
     const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (j >= N) return;
@@ -362,8 +372,9 @@ __global__ void k_density_multi(const int *__restrict__ perm, const double *__re
             const double fv = f ? wi * f[((int64_t)r * N + i) * 3 + k] : 0.0;
             const double qv = q ? q[((int64_t)r * N + i) * 3 + k] : 0.0;
             const int64_t o = (j * nr + r) * 6;
-            d64[o + k] = fv;
-            d64[o + 3 + k] = qv;
+            const float fh = __double2float_rn(fv), qh = __double2float_rn(qv);
+            dp[o + k] = make_float2(fh, __double2float_rn(fv - (double)fh));
+            dp[o + 3 + k] = make_float2(qh, __double2float_rn(qv - (double)qh));
             o32[rec_off(nr, r, k)] = __double2float_rn(fv);
             o32[rec_off(nr, r, 3 + k)] = __double2float_rn(qv);
         }
@@ -392,9 +403,9 @@ int batch_grid_t(int nsm) {
 }  // namespace
 
 cudaError_t launch_density_multi(const int *perm, const double *w, const float *rec32, const double *f,
-                                 const double *q, int64_t N, int nr, double *d64, float *d32, cudaStream_t st) {
+                                 const double *q, int64_t N, int nr, float2 *dp, float *d32, cudaStream_t st) {
     const int bs = 256;
-    k_density_multi<<<(unsigned)((N + bs - 1) / bs), bs, 0, st>>>(perm, w, rec32, f, q, N, nr, d64, d32);
+    k_density_multi<<<(unsigned)((N + bs - 1) / bs), bs, 0, st>>>(perm, w, rec32, f, q, N, nr, dp, d32);
     return cudaGetLastError();
 }
 

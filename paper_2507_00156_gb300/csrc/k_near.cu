@@ -68,8 +68,7 @@ __device__ __forceinline__ void process(const EvalArgs &A, const Geom &T, const 
     }
     const fpair r2p = fp_split(r2);
     fpair K[3];
-    float Lf;
-    kernel_factors_pair<false, ND>(T, P, tab, r2, r2p, cls, K, Lf);
+    kernel_factors_pair<ND>(T, P, tab, r2, r2p, cls, K);
     const fpair d[3] = {fp_split(dx), fp_split(dy), fp_split(dz)};
     if (SL) sl_accumulate_pair(d, K[0], K[1], nc, wf, wn, accU);
     if (DL) dl_accumulate_pair(T, d, r2p, K[1], K[2], wn, qs, q0, accN, accD);

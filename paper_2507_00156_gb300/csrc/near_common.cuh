@@ -9,7 +9,7 @@
 //     Q = q - q(x0), m = w n; with P = (n0.Q)(n0.m), R = (xh.Q)(xh.m),
 //     S = (xh.Q)(n0.m) + (n0.Q)(xh.m), K = K3 - (r^2 - b^2) K5, xh = x - x0:
 //       t1 : Q m = n0 (b P - S) - xh P,   t2 : Q m = n0 (b R) + xh (b S - R),
-//     evaluated in the equivalent form of dl_accumulate (in terms of d = y - x = b n0 - xh).
+//     evaluated in the equivalent form of dl_accumulate_pair (in terms of d = y - x = b n0 - xh).
 // alpha = first row of the inverse of A_k = [1, rho_k I0(b/delta_k), rho_k^3 I2(b/delta_k)]
 // (Eqs. (extrap_eqn), (I0), (I2)), by Cramer's rule; with four deltas (the O(delta^7) variant of
 // Sec. 1) A_k gains the column rho_k^5 I4(b/delta_k).
@@ -322,22 +322,16 @@ __device__ __forceinline__ void table_pairs_r2(const double *__restrict__ tab, d
     table_pairs<N>(ftab, idx, s, sg);
 }
 
-// Lf: when every delta in use is on the defect path (CLS >= ND), L = r^2 K5 - K3 = (E3 - E5)/r^3
-// in FP32 (see dl_accumulate_defect); 0 otherwise.
-// The class is a run-time value (uniform over a batch of pairs) for the classes with table-path
-// deltas (ALLDEF = false: one code path for all of them keeps the kernel within the instruction
-// cache); ALLDEF = true is the class with every delta on the defect path (cls = ND).
-// ROLL: the loops over deltas stay rolled (code size; T must then sit in shared memory, as in
-// k_near, since the loops index its arrays at run time); otherwise they unroll for a compile-time
-// cls (the batched kernel, whose Geom lives in registers).
-// K1, K3, K5 as float pairs (~2^-46 relative); r2p = r2 as a float pair.
-template <bool ALLDEF, int ND, bool ROLL = true>
+// K1, K3, K5 as float pairs (~2^-46 relative); r2p = r2 as a float pair.  The class is a
+// run-time value, uniform over a batch of pairs: one code path for all of them keeps the kernel
+// within the instruction cache, and the loops over deltas stay rolled (the unrolled float-pair
+// code of several deltas overflows it); T sits in shared memory, since the loops index its arrays
+// at run time.
+template <int ND>
 __device__ __forceinline__ void kernel_factors_pair(const Geom &T, const ScanParams &P, const double *__restrict__ tab,
-                                                    double r2, fpair r2p, int cls, fpair K[3], float &Lf) {
-    const int NDEF = ALLDEF ? ND : cls;  // defect-path deltas that carry weight
-    Lf = 0.0f;
+                                                    double r2, fpair r2p, int cls, fpair K[3]) {
     float kh[3] = {0.0f, 0.0f, 0.0f}, kl[3] = {0.0f, 0.0f, 0.0f};
-    if (ALLDEF || cls >= 1) {
+    if (cls >= 1) {
         // r / delta_k > DEFECT_T: s_p = 1 - eps_p with eps_1 = erfc t, eps_2 = eps_1 + (2/sqrt pi) t e^{-t^2},
         // eps_3 = eps_1 + (2/sqrt pi)(t + 2/3 t^3) e^{-t^2} (Eqs. (s1)-(s3)), all below 2.1e-8, and
         // eps_p = 0 where t > cutoff_t (Sec. 3.2).  The term is (sum_k alpha_k - sum_k alpha_k eps_p(t_k)) / r^p.
@@ -367,14 +361,8 @@ __device__ __forceinline__ void kernel_factors_pair(const Geom &T, const ScanPar
                 E5 = fmaf(a, fmaf(gt, 0.6666666666666667f * th, e + gt), E5);
             }
         };
-        if (ROLL) {
 #pragma unroll 1
-            for (int k = 0; k < NDEF; ++k) defect(k);
-        } else {
-#pragma unroll
-            for (int k = 0; k < ND; ++k)
-                if (k < NDEF) defect(k);
-        }
+        for (int k = 0; k < cls; ++k) defect(k);
         // 1/r in float pairs from the FP32 estimate y0: with e = 1 - r^2 y0^2 (|e| < 1e-6, from the
         // exact square of y0 and the pair product with r^2), 1/r = y0 (1 + e/2 + 3 e^2/8) + O(e^3 y0)
         const float y0 = rsqrt_ftz(r2h);  // r2h > 0: r > 4.7 delta_0
@@ -390,7 +378,7 @@ __device__ __forceinline__ void kernel_factors_pair(const Geom &T, const ScanPar
         pair_mul(r3h, r3l, q2h, q2l, r5h, r5l);
         // (sum of the alpha of the defect-path deltas) / r^p, and the defects eps_p / r^p in FP32
         // (relative error ~1e-7 of terms below 2.1e-8 of the result)
-        const int ia = (ALLDEF ? ND : cls) - 1;
+        const int ia = cls - 1;
         const float ah = T.aph[ia], al = T.apl[ia];
         pair_acc(kh[0], kl[0], ah, al, r1h, r1l);
         pair_acc(kh[1], kl[1], ah, al, r3h, r3l);
@@ -398,9 +386,8 @@ __device__ __forceinline__ void kernel_factors_pair(const Geom &T, const ScanPar
         pair_add(kh[0], kl[0], -(E1 * r1h));
         pair_add(kh[1], kl[1], -(E3 * r3h));
         pair_add(kh[2], kl[2], -(E5 * r5h));
-        if (ALLDEF || cls == ND) Lf = (E3 - E5) * r3h;
     }
-    if (!ALLDEF) {
+    {
         // the table-path deltas: (alpha_k / delta_k^p) sigma_p(tau_k)
         const float r2f = approx_float_pos(r2);
         auto table = [&](int k) {
@@ -417,34 +404,11 @@ __device__ __forceinline__ void kernel_factors_pair(const Geom &T, const ScanPar
 #pragma unroll
             for (int p = 0; p < 3; ++p) pair_acc(kh[p], kl[p], T.adh[p][k], T.adl[p][k], sg[p][0], sg[p][1]);
         };
-        if (ROLL) {  // a rolled loop: the unrolled float-pair code of several deltas overflows the instruction cache
 #pragma unroll 1
-            for (int k = cls; k < ND; ++k) table(k);
-        } else {
-#pragma unroll
-            for (int k = 0; k < ND; ++k)
-                if (k >= cls) table(k);
-        }
+        for (int k = cls; k < ND; ++k) table(k);
     }
 #pragma unroll
     for (int p = 0; p < 3; ++p) K[p] = {kh[p], kl[p]};
-}
-
-// The same factors as doubles (one FP64 add each).
-template <bool ALLDEF, int ND, bool ROLL = true>
-__device__ __forceinline__ void kernel_factors_rt(const Geom &T, const ScanParams &P, const double *__restrict__ tab,
-                                                  double r2, int cls, double &K1, double &K3, double &K5, float &Lf) {
-    fpair K[3];
-    kernel_factors_pair<ALLDEF, ND, ROLL>(T, P, tab, r2, fp_split(r2), cls, K, Lf);
-    K1 = fp_to_double(K[0]);
-    K3 = fp_to_double(K[1]);
-    K5 = fp_to_double(K[2]);
-}
-
-template <int CLS, int ND = 3>
-__device__ __forceinline__ void kernel_factors(const Geom &T, const ScanParams &P, const double *__restrict__ tab,
-                                               double r2, double &K1, double &K3, double &K5, float &Lf) {
-    kernel_factors_rt<(CLS >= ND), ND, false>(T, P, tab, r2, CLS, K1, K3, K5, Lf);
 }
 
 // Single-layer contraction: accU += K1 g + K3 d (d.g), g = wf - c wn.
@@ -459,65 +423,18 @@ __device__ __forceinline__ void sl_accumulate(double dx, double dy, double dz, d
     accU[2] = fma(t, dz, fma(K1, g2, accU[2]));
 }
 
-// Density-independent factors of the double-layer contraction of one near pair.
-// With d = y - x = b n0 - xh, L = r^2 K5 - K3, U = d.Q, W = d.m, nQ = n0.Q, nm = n0.m, the
-// contraction -6 [t1 K + t2 K5] : Q m (K = K3 - (r^2 - b^2) K5; t1, t2 as above) equals
-//   -6 ( n0 [nQ (2 b nm - W) - nm U] L  -  d [L nm nQ - K5 W U] ):
-// substitute xh = b n0 - d into n0 (K (b P - S) + K5 b R) + xh (K5 (b S - R) - K P) and collect
-// (K - b^2 K5 = -L).
-struct DLPair {
-    double L, Z, Lnm, K5W;  // L, 2 b nm - W, L nm, K5 W
-};
-
-__device__ __forceinline__ DLPair dl_pair(const Geom &T, double r2, double K3, double K5, double nm, double W) {
-    DLPair D;
-    D.L = fma(r2, K5, -K3);
-    D.Z = fma(T.b2, nm, -W);
-    D.Lnm = D.L * nm;
-    D.K5W = K5 * W;
-    return D;
-}
-
-// Double-layer contraction of one density: accN += the n0 coefficient, accD += the d coefficient
-// (the result is -6/(8 pi) (accN n0 - accD)).
-__device__ __forceinline__ void dl_accumulate(const DLPair &D, const Geom &T, double dx, double dy, double dz,
-                                              double nm, const double qs[3], const double q0[3], double &accN,
-                                              double accD[3]) {
-    const double Q0 = qs[0] - q0[0], Q1 = qs[1] - q0[1], Q2 = qs[2] - q0[2];
-    const double nQ = fma(T.n0[2], Q2, fma(T.n0[1], Q1, T.n0[0] * Q0));
-    const double U = fma(dz, Q2, fma(dy, Q1, dx * Q0));
-    accN = fma(D.L, fma(nQ, D.Z, -(nm * U)), accN);
-    const double C = fma(D.Lnm, nQ, -(D.K5W * U));
-    accD[0] = fma(C, dx, accD[0]);
-    accD[1] = fma(C, dy, accD[1]);
-    accD[2] = fma(C, dz, accD[2]);
-}
-
-// dl_accumulate for a pair whose deltas are all on the defect path (t > 4.7): then
-// L = r^2 K5 - K3 = (E3 - E5)/r^3 (E_p the alpha-weighted defects of s_p), below ~1e-7 of K3,
-// so every factor that multiplies L (n0.Q, n0.m, 2 b n0.m - W) runs in FP32 (relative error
-// ~3e-7 of terms below 1e-7 of the result); U = d.Q, W = d.m and K5 W U stay in FP64.
-__device__ __forceinline__ void dl_accumulate_defect(const Geom &T, double dx, double dy, double dz, float Lf,
-                                                     double K5W, float nmf, float Zf, const double qs[3],
-                                                     const double q0[3], double &accN, double accD[3]) {
-    const double Q0 = qs[0] - q0[0], Q1 = qs[1] - q0[1], Q2 = qs[2] - q0[2];
-    const double U = fma(dz, Q2, fma(dy, Q1, dx * Q0));
-    const float nQf = fmaf(approx_float(T.n0[2]), approx_float(Q2),
-                           fmaf(approx_float(T.n0[1]), approx_float(Q1), approx_float(T.n0[0]) * approx_float(Q0)));
-    const float Uf = approx_float(U);
-    accN += float_to_double(Lf * fmaf(nQf, Zf, -(nmf * Uf)));
-    const double C = fma(-K5W, U, float_to_double(Lf * nmf * nQf));
-    accD[0] = fma(C, dx, accD[0]);
-    accD[1] = fma(C, dy, accD[1]);
-    accD[2] = fma(C, dz, accD[2]);
-}
-
-// The contractions above in float pairs (the near kernel): operands from the near-field record
+// The near-pair contractions in float pairs (k_near, k_batch): operands from the near-field record
 // and the target's pairs, results added into per-lane float-pair accumulators.  Each result
-// carries an error ~2^-46 of the magnitudes it is formed from, as the FP64 forms do at 2^-53,
-// far below the 1e-11 the FP64 path is held to.  The double layer uses the general form for
-// every class: where all deltas are on the defect path L = r^2 K5 - K3 is ~1e-7 of K3 or less,
-// and its float-pair error, ~2^-46 of K3, is of the size of the other terms' errors.
+// carries an error ~2^-46 of the magnitudes it is formed from, far below the 1e-11 the FP64 path
+// is held to.
+// Single layer (Eq. (Sreg)): accU += K1 g + K3 d (d.g), g = w f - c w n.
+// Double layer: with d = y - x = b n0 - xh, L = r^2 K5 - K3, U = d.Q, W = d.m, nQ = n0.Q,
+// nm = n0.m, the contraction -6 [t1 K + t2 K5] : Q m (K = K3 - (r^2 - b^2) K5; t1, t2 as above)
+// equals -6 ( n0 [nQ (2 b nm - W) - nm U] L  -  d [L nm nQ - K5 W U] ): substitute xh = b n0 - d
+// into n0 (K (b P - S) + K5 b R) + xh (K5 (b S - R) - K P) and collect (K - b^2 K5 = -L);
+// accN += the n0 coefficient, accD += the d coefficient (the result is -6/(8 pi) (accN n0 - accD)).
+// Where every delta is on the defect path L is ~1e-7 of K3 or less, and its float-pair error,
+// ~2^-46 of K3, is of the size of the other terms' errors.
 __device__ __forceinline__ void sl_accumulate_pair(const fpair d[3], fpair K1, fpair K3, fpair nc, const fpair wf[3],
                                                    const fpair wn[3], fpair accU[3]) {
     const fpair g0 = fp_fma(nc, wn[0], wf[0]);  // g = w f - c w n, nc = -c
@@ -686,7 +603,7 @@ inline ScanParams scan_params(const ers_surface *s, double Rc, const double *rho
 // One problem of the batched evaluation, as the persistent kernel sees it.
 struct BatchProblemDev {
     SurfDev sd;
-    const double *dens64;  // [N][NR][6] sorted order: w f (3), q (3)
+    const float2 *densp;   // [N][NR][6] sorted order: w f (3), q (3) as float pairs (hi, lo)
     const float *dens32;   // [N][NR][6] floats
     const double *y, *x0, *n0, *b, *f0, *q0;  // f0, q0: [NR][M][3]
     double *u, *v;                            // [NR][M][3]

@@ -480,12 +480,17 @@ __global__ void k_gather(const double *__restrict__ y, const double *__restrict_
     o[9 * Ms + k] = b[m];
 }
 
-// Over the validation sample (every stride-th target m = k stride, method values up, vp):
-// res[0] = max |u - up|, res[1] = max |up|, res[2] = max |v - vp|, res[3] = max |vp|, and
-// res[4], res[5] = max |u - corr - up|, max |v - corr - vp|: the same without the network's
-// correction (A carries the correction's inputs; A.sign is ignored).
-__global__ void k_compare(ApplyArgs A, const double *__restrict__ up, const double *__restrict__ vp, int64_t Ms,
-                          int stride, double *__restrict__ res) {
+// Over the validation sample (every stride-th target m = k stride) the three-delta method's value
+// is r = (u - corr) + (n3 - nd): the closure's sums without the correction plus the difference of
+// the near-field sums with three and with nd deltas (n3u.., ndu.., both over the three-delta near
+// radius and without far field, which is then the same in both), or u itself where the method's
+// value has replaced the closure's (scale < 0).
+// res[0] = max |u - r|, res[1] = max |r| (single layer), res[2], res[3] the same for the double
+// layer, and res[4], res[5] = max |u - corr - r| for the two layers: the errors without the
+// network's correction (A carries the correction's inputs; A.sign is ignored).
+__global__ void k_compare(ApplyArgs A, const double *__restrict__ n3u, const double *__restrict__ n3v,
+                          const double *__restrict__ ndu, const double *__restrict__ ndv, int64_t Ms, int stride,
+                          double *__restrict__ res) {
     double e[6] = {0, 0, 0, 0, 0, 0};
     for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < Ms; k += (int64_t)gridDim.x * blockDim.x) {
         const int64_t m = k * stride;
@@ -493,11 +498,13 @@ __global__ void k_compare(ApplyArgs A, const double *__restrict__ up, const doub
         target_frame(A.x0, A.n0, m, A.c, A.a, t1, t2, n, k1, k2);
         for (int layer = 0; layer < 2; ++layer) {
             const double *out = layer == 0 ? A.u : A.v;
-            const double *ref = layer == 0 ? up : vp;
+            const double *n3 = layer == 0 ? n3u : n3v, *nd = layer == 0 ? ndu : ndv;
+            const double sc = A.scale[2 * m + layer];
             double corr[3] = {0.0, 0.0, 0.0};
-            if (A.scale[2 * m + layer] > 0.0) correction(A, m, layer, t1, t2, n, corr);
+            if (sc > 0.0) correction(A, m, layer, t1, t2, n, corr);
             for (int i = 0; i < 3; ++i) {
-                const double o = out[3 * m + i], r = ref[3 * k + i];
+                const double o = out[3 * m + i];
+                const double r = sc < 0.0 ? o : (o - corr[i]) + (n3[3 * k + i] - nd[3 * k + i]);
                 e[2 * layer] = fmax(e[2 * layer], fabs(o - r));
                 e[2 * layer + 1] = fmax(e[2 * layer + 1], fabs(r));
                 e[4 + layer] = fmax(e[4 + layer], fabs(o - corr[i] - r));
@@ -602,19 +609,26 @@ __global__ void k_gather_idx(const double *__restrict__ y, const double *__restr
     out[9 * K + k] = b[m];
 }
 
-// ... and scatter the method's values back; those targets carry no correction any more (scale 0).
-__global__ void k_scatter_idx(const double *__restrict__ up, const double *__restrict__ vp,
-                              const int64_t *__restrict__ idx, int64_t K, double *__restrict__ u,
-                              double *__restrict__ v, double *__restrict__ scale) {
+// ... and give them the method's values: the closure's sums without the correction plus the
+// difference of the near-field sums with three and with nd deltas (the far field is the same in
+// both); those targets carry no correction any more (scale -1: the method's value).
+__global__ void k_replace_idx(ApplyArgs A, const double *__restrict__ n3u, const double *__restrict__ n3v,
+                              const double *__restrict__ ndu, const double *__restrict__ ndv,
+                              const int64_t *__restrict__ idx, int64_t K, double *__restrict__ scale) {
     const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= K) return;
     const int64_t m = idx[k];
-    for (int i = 0; i < 3; ++i) {
-        u[3 * m + i] = up[3 * k + i];
-        v[3 * m + i] = vp[3 * k + i];
+    double t1[3], t2[3], n[3], k1, k2;
+    target_frame(A.x0, A.n0, m, A.c, A.a, t1, t2, n, k1, k2);
+    for (int layer = 0; layer < 2; ++layer) {
+        double *out = layer == 0 ? A.u : A.v;
+        const double *n3 = layer == 0 ? n3u : n3v, *nd = layer == 0 ? ndu : ndv;
+        double corr[3] = {0.0, 0.0, 0.0};
+        if (A.scale[2 * m + layer] > 0.0) correction(A, m, layer, t1, t2, n, corr);
+        for (int i = 0; i < 3; ++i) out[3 * m + i] += (n3[3 * k + i] - nd[3 * k + i]) - corr[i];
     }
-    scale[2 * m] = 0.0;
-    scale[2 * m + 1] = 0.0;
+    scale[2 * m] = -1.0;
+    scale[2 * m + 1] = -1.0;
 }
 
 int closure_check(const ers_closure *c, int layer) {
@@ -915,6 +929,12 @@ namespace ers {
 int eval_few_delta(ers_surface *s, const ers_params *p, const double *y, int64_t M, const double *x0,
                    const double *n0, const double *b, const double *f0, const double *q0, double *u, double *v,
                    double *gamma, int ndelta, cudaStream_t st);
+// The near-field part alone (ndelta = 1, 2 or 3 deltas; no far-field sums), over the three-delta
+// method's near radius for every ndelta: the method's value is then the closure's sums plus the
+// difference of two such evaluations.
+int eval_near_only(ers_surface *s, const ers_params *p, const double *y, int64_t M, const double *x0,
+                   const double *n0, const double *b, const double *f0, const double *q0, double *u, double *v,
+                   int ndelta, cudaStream_t st);
 
 }  // namespace ers
 
@@ -1083,8 +1103,8 @@ int ers_eval_learned(ers_surface *s, ers_closure *c, const ers_params *p, const 
     // 4b. targets whose geometry lies outside the training extent: the three-delta method instead
     c->last_out = 0;
     if (c->range_check && (c->have_range[0] || c->have_range[1])) {
-        // [count | pad | idx (M) | gathered inputs (16 K) | u, v (6 K)], K <= M
-        if ((rc = grow(c->oor, sizeof(int64_t) * 2 + sizeof(int64_t) * (size_t)M + sizeof(double) * (size_t)M * 22)) !=
+        // [count | pad | idx (M) | gathered inputs (16 K) | near sums, three and nd deltas (12 K)], K <= M
+        if ((rc = grow(c->oor, sizeof(int64_t) * 2 + sizeof(int64_t) * (size_t)M + sizeof(double) * (size_t)M * 28)) !=
             ERS_OK)
             return rc;
         unsigned long long *cnt = (unsigned long long *)c->oor.ptr;
@@ -1102,29 +1122,37 @@ int ers_eval_learned(ers_surface *s, ers_closure *c, const ers_params *p, const 
         const int64_t Kt = (int64_t)K;
         c->last_out = Kt;
         if (Kt > 0) {
-            double *up = sub + 16 * Kt, *vp = up + 3 * Kt;
+            double *n3u = sub + 16 * Kt, *n3v = n3u + 3 * Kt, *ndu = n3v + 3 * Kt, *ndv = ndu + 3 * Kt;
             k_gather_idx<<<(unsigned)((Kt + 127) / 128), 128, 0, st>>>(y, x0, n0, b, f0, q0, idx, Kt, sub);
             if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "ers_eval_learned: gather");
-            if ((rc = ers_eval(s, &pp, sub, Kt, sub + 3 * Kt, sub + 6 * Kt, sub + 9 * Kt, sub + 10 * Kt,
-                               sub + 13 * Kt, up, vp, stream)) < 0)
+            if ((rc = eval_near_only(s, &pp, sub, Kt, sub + 3 * Kt, sub + 6 * Kt, sub + 9 * Kt, sub + 10 * Kt,
+                                     sub + 13 * Kt, n3u, n3v, 3, st)) < 0)
                 return rc;
-            k_scatter_idx<<<(unsigned)((Kt + 127) / 128), 128, 0, st>>>(up, vp, idx, Kt, u, v, sc);
-            if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "ers_eval_learned: scatter");
+            if ((rc = eval_near_only(s, &pp, sub, Kt, sub + 3 * Kt, sub + 6 * Kt, sub + 9 * Kt, sub + 10 * Kt,
+                                     sub + 13 * Kt, ndu, ndv, ndelta, st)) < 0)
+                return rc;
+            k_replace_idx<<<(unsigned)((Kt + 127) / 128), 128, 0, st>>>(ap, n3u, n3v, ndu, ndv, idx, Kt, sc);
+            if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "ers_eval_learned: replace");
         }
     }
     // 5. validation against the three-delta method on every vstride-th target, with and without
-    // the network's correction; per layer the better of the two is kept
+    // the network's correction; per layer the better of the two is kept.  The far field is the
+    // same in the closure and in the method, so the method's value comes from the near-field sums
+    // alone (three and nd deltas) at the sample (k_compare).
     const int64_t Ms = (M + vstride - 1) / vstride;
-    if ((rc = grow(c->sub, sizeof(double) * ((size_t)Ms * 22 + 8))) != ERS_OK) return rc;
+    if ((rc = grow(c->sub, sizeof(double) * ((size_t)Ms * 28 + 8))) != ERS_OK) return rc;
     double *sub = (double *)c->sub.ptr;
-    double *up = sub + 16 * Ms, *vp = up + 3 * Ms, *res = vp + 3 * Ms;
+    double *n3u = sub + 16 * Ms, *n3v = n3u + 3 * Ms, *ndu = n3v + 3 * Ms, *ndv = ndu + 3 * Ms, *res = ndv + 3 * Ms;
     k_gather<<<(unsigned)((Ms + 127) / 128), 128, 0, st>>>(y, x0, n0, b, f0, q0, Ms, vstride, sub);
     e = cudaMemsetAsync(res, 0, sizeof(double) * 6, st);
     if (e != cudaSuccess) return cuda_fail(e, "ers_eval_learned: memset");
-    if ((rc = ers_eval(s, &pp, sub, Ms, sub + 3 * Ms, sub + 6 * Ms, sub + 9 * Ms, sub + 10 * Ms, sub + 13 * Ms, up, vp,
-                       stream)) < 0)
+    if ((rc = eval_near_only(s, &pp, sub, Ms, sub + 3 * Ms, sub + 6 * Ms, sub + 9 * Ms, sub + 10 * Ms, sub + 13 * Ms,
+                             n3u, n3v, 3, st)) < 0)
         return rc;
-    k_compare<<<64, 128, 0, st>>>(ap, up, vp, Ms, vstride, res);
+    if ((rc = eval_near_only(s, &pp, sub, Ms, sub + 3 * Ms, sub + 6 * Ms, sub + 9 * Ms, sub + 10 * Ms, sub + 13 * Ms,
+                             ndu, ndv, ndelta, st)) < 0)
+        return rc;
+    k_compare<<<64, 128, 0, st>>>(ap, n3u, n3v, ndu, ndv, Ms, vstride, res);
     double h[6];
     e = cudaMemcpyAsync(h, res, sizeof h, cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);

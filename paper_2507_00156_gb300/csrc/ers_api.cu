@@ -313,7 +313,7 @@ int g_caps[4] = {1, 1, 0, 0};
 // the single regularized sum with delta_0, near radius cutoff_t * delta_0.
 int eval_impl(ers_surface *s, const ers_params *p, const double *y, int64_t M, const double *x0, const double *n0,
               const double *b, const double *f0, const double *q0, double *u, double *v, void *stream, int ndelta,
-              double *gamma) {
+              double *gamma, bool near_only = false) {
     clear_error();
     if (!s) return fail(ERS_E_INVAL, "ers_eval: NULL surface");
     int warn;
@@ -351,7 +351,11 @@ int eval_impl(ers_surface *s, const ers_params *p, const double *y, int64_t M, c
     for (int k = 0; k < 3; ++k) a.rho[k] = p->rho[k];
     a.rho[3] = ndelta == 4 ? rho4_of(p) : 0.0;
     a.cutoff_t = p->cutoff_t;
-    a.Rc = p->cutoff_t * a.rho[ndelta - 1] * s->h;
+    // near radius cutoff_t delta_{K-1}; the near-field-only sums of fewer deltas extend to the
+    // three-delta radius (beyond cutoff_t delta_{K-1} every s_p is 1 and the weights sum to 1, so
+    // the extension is the plain sum there), so that they differ from the three-delta ones by
+    // the difference of the two methods, whose far fields then coincide
+    a.Rc = p->cutoff_t * a.rho[(near_only ? std::max(ndelta, 3) : ndelta) - 1] * s->h;
     a.ndelta = ndelta;
     a.gamma = gamma;
     if ((p->options & ERS_OPT_SHARP) && ndelta >= 3) {  // on-surface targets: s#_p of Sec. 2.1
@@ -404,8 +408,13 @@ int eval_impl(ers_surface *s, const ers_params *p, const double *y, int64_t M, c
     if (tree) chunks = 1;  // the treecode writes one partial sum per target
     a.chunks = (int)chunks;
     a.chunk_len = clen;
-    if ((rc = grow(s->part, sizeof(double) * 6 * (size_t)M * chunks)) != ERS_OK) return rc;
-    a.part = (double *)s->part.ptr;
+    if (near_only) {  // no far-field partial sums: the near kernel adds none
+        a.chunks = 0;
+        a.part = nullptr;
+    } else {
+        if ((rc = grow(s->part, sizeof(double) * 6 * (size_t)M * chunks)) != ERS_OK) return rc;
+        a.part = (double *)s->part.ptr;
+    }
     if ((rc = grow(s->counts, sizeof(unsigned long long) * NCOUNTERS)) != ERS_OK) return rc;
     a.counters = (unsigned long long *)s->counts.ptr;
     cudaError_t e = cudaMemsetAsync(a.counters, 0, sizeof(unsigned long long) * NCOUNTERS, st);
@@ -417,7 +426,10 @@ int eval_impl(ers_surface *s, const ers_params *p, const double *y, int64_t M, c
     // NEAR_CTAS_PER_SM CTAs per SM, the far one also by its shared memory) so that both kernels
     // are resident on every SM whichever starts first; k_combine then adds the far partial sums.
     const bool overlap = !tree && p->precision == ERS_PREC_MIXED && (p->options & ERS_OPT_CONCURRENT);
-    if (tree) {  // modified weights (when stale) and the walk, both in the far-field slot of the profile
+    if (near_only) {
+        e = launch_near(a, tab, g_caps[3], nsm);
+        if (e != cudaSuccess) return cuda_fail(e, "near-field kernel");
+    } else if (tree) {  // modified weights (when stale) and the walk, both in the far-field slot of the profile
         if ((rc = tree_prepare(s, tp.n0, tp.p, p->precision == ERS_PREC_MIXED, st)) != ERS_OK) return rc;
         e = launch_tree_far(a, tp);
         if (e != cudaSuccess) return cuda_fail(e, "treecode far-field kernel");
@@ -474,6 +486,16 @@ int eval_few_delta(ers_surface *s, const ers_params *p, const double *y, int64_t
         return eval_impl(s, p, y, M, x0, n0, b, f0, q0, u, v, (void *)st, ndelta, gamma);
     } catch (...) {
         return fail(ERS_E_NOMEM, "two-delta evaluation: host exception");
+    }
+}
+
+int eval_near_only(ers_surface *s, const ers_params *p, const double *y, int64_t M, const double *x0,
+                   const double *n0, const double *b, const double *f0, const double *q0, double *u, double *v,
+                   int ndelta, cudaStream_t st) {
+    try {
+        return eval_impl(s, p, y, M, x0, n0, b, f0, q0, u, v, (void *)st, ndelta, nullptr, true);
+    } catch (...) {
+        return fail(ERS_E_NOMEM, "near-field evaluation: host exception");
     }
 }
 

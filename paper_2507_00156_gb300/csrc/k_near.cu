@@ -32,7 +32,7 @@ namespace {
 
 using namespace nearc;
 constexpr int WPB = 4;  // warps per block
-constexpr int NEAR_MIN_BLOCKS = 3;
+constexpr int NEAR_MIN_BLOCKS = 4;
 
 // One near pair of class cls, a run-time value (one code path for every class keeps the kernel
 // within the instruction cache); cls = ND: every delta on the defect path.  The pair geometry d,

@@ -446,3 +446,32 @@ def test_bounded_wait_runs_out_and_reports_it(ers):
     Y1, Y2 = c.infer(0, Xd), c.infer(0, Xd)
     assert torch.isfinite(Y1).all() and torch.equal(Y1, Y2)
     assert not c.timed_out()
+
+
+@pytest.mark.gpu
+def test_validation_reference_from_near_field_differences(ers):
+    """ers_eval_learned validates against the three-delta method without its far field: the
+    method's value is the closure's sums plus the difference of the near-field sums with three and
+    with nd deltas, both over the three-delta near radius.  With an untrained network and every
+    target validated, the reported error equals the error against the full three-delta evaluation
+    to ~1e-8 (of the largest value; the remainder is the quadrature error of the subtraction
+    identity at targets between the two near radii, which the two-delta sums leave unsubtracted)."""
+    h = 1 / 64
+    shape = workloads.unit_sphere()
+    s = ers.Surface(shape.center, shape.axes, h)
+    x = s.nodes()[0].cpu().numpy()
+    rng = np.random.default_rng(3)
+    fc, qc = workloads.density_coeffs(rng), workloads.density_coeffs(rng)
+    band = workloads.near_band_targets(shape, 20000, 26 * h, rng)[0]
+    for prec in (0, 1):
+        P = _problem(ers, s, fc, qc, np.concatenate([x[::7], band]), prec)
+        u3, v3 = P["u3"].cpu().numpy(), P["v3"].cpu().numpy()
+        zero = ers.Closure(seed=0)
+        for nd in (1, 2):
+            u, v, err, fb = ers.eval_learned(s, zero, *_args(P), precision=prec, tol=1e30, vstride=1, ndelta=nd)
+            assert not fb
+            du = np.abs(u.cpu().numpy() - u3).max() / np.abs(u3).max()
+            dv = np.abs(v.cpu().numpy() - v3).max() / np.abs(v3).max()
+            print(f"precision {prec} ndelta {nd}: reported {err[0]:.6e} {err[1]:.6e}, direct {du:.6e} {dv:.6e}")
+            assert du > 1e-6 and dv > 1e-6
+            assert abs(err[0] - du) <= 1e-7 and abs(err[1] - dv) <= 1e-7

@@ -52,8 +52,8 @@ NEAR_FLOPS_PER_DELTA_EVAL = 30 + 1 + 1    # one regularized (node, delta) term, 
 # and blank space removed).  When the sources no longer match, the kernel has changed since the
 # counters were taken and the roofline reports traffic as null until they are captured again.
 NCU_TRAFFIC = {
-    ("sphere128", "k_near"): (226604288 + 107811584, "25775099464869ab"),
-    ("sphere128", "k_far32"): (59765504 + 30050304, "b3c0f9eff0310922"),
+    ("sphere128", "k_near"): (232105984 + 169948160, "e33dea030a41cb08"),
+    ("sphere128", "k_far32"): (61243904 + 31417600, "1936d75a73d3609f"),
 }
 KERNEL_SOURCES = {"k_near": ("k_near.cu", "near_common.cuh", "ers_internal.h"),
                   "k_far32": ("k_far.cu", "ers_internal.h")}
@@ -752,9 +752,11 @@ def main():
     # cls_counts[k] = near pairs with k deltas beyond the cutoff, i.e. 3 - k regularized terms
     near_flops = NEAR_FLOPS_PER_DELTA_EVAL * sum(c * (3 - k) for k, c in enumerate(cls_local))
     far_flops = far_local * FAR_FLOPS_PER_PAIR
-    roof_near = {"kernel": "k_near (FP64 near sums + extrapolation)", "bound": "alu", "unit": "TFLOP/s",
+    roof_near = {"kernel": "k_near (near sums + extrapolation: FP64 pair geometry, float-pair factors and "
+                           "contractions)", "bound": "alu", "unit": "TFLOP/s",
                  "achieved": near_flops / (ms_near * 1e-3) / 1e12, "peak": FP64_PEAK_NOMINAL * scale / 1e12,
-                 "peak_source": "nominal FP64 1.25 TFLOP/s x median SM clock / 2070 MHz",
+                 "peak_source": "nominal FP64 1.25 TFLOP/s x median SM clock / 2070 MHz (FP64-accurate flops; the "
+                                "float-pair arithmetic runs on the FP32 pipe, bound by instruction issue)",
                  "units": "32 flops per regularized (node, delta) term: 30 flops, erf and exp counted as one op each"}
     roof_far = {"kernel": "k_far32 (FP32 far field, FP64 tile accumulation)", "bound": "alu", "unit": "TFLOP/s",
                 "achieved": far_flops / (ms_far * 1e-3) / 1e12, "peak": FP32_PEAK_NOMINAL * scale / 1e12,

@@ -79,34 +79,36 @@ __device__ __forceinline__ void process(const EvalArgs &A, const Geom &T, const 
 // Single layer: Eq. (Sreg) with s#_1, s#_2; double layer: the stresslet -6 d (d.Q)(d.m) s#_3/r^5
 // (at b = 0 the split form would add t1 (s#_2 - s#_3)/r^3, which is not small for s#).
 template <int PREC, bool SL, bool DL>
-__device__ __forceinline__ void process_sharp(const EvalArgs &A, const Geom &T, const ScanParams &Ps, double c,
-                                              const double q0[3], int64_t j, double accU[3], double accV[3],
+__device__ __forceinline__ void process_sharp(const EvalArgs &A, const Geom &T, const ScanParams &Ps, fpair nc,
+                                              const fpair q0[3], int64_t j, fpair accU[3], fpair accV[3],
                                               int &npairs) {
-    const double2 *r = reinterpret_cast<const double2 *>(A.sd.rec + j * REC);
-    const double2 r0 = __ldg(r + 0), r1 = __ldg(r + 1), r2v = __ldg(r + 2);
-    const double2 r3 = __ldg(r + 3), r4 = __ldg(r + 4), r5 = __ldg(r + 5);
-    const double xs[3] = {r0.x, r0.y, r1.x};
-    const double wf[3] = {r1.y, r2v.x, r2v.y};
-    const double wn[3] = {r3.x, r3.y, r4.x};
-    const double qs[3] = {r4.y, r5.x, r5.y};
-    const double dx = __dsub_rn(T.y[0], xs[0]);
-    const double dy = __dsub_rn(T.y[1], xs[1]);
-    const double dz = __dsub_rn(T.y[2], xs[2]);
+    const float4 *r = reinterpret_cast<const float4 *>(A.sd.recp + j * NREC);
+    const float4 a0 = __ldg(r + 0), a1 = __ldg(r + 1), a2 = __ldg(r + 2);
+    const float4 a3 = __ldg(r + 3), a4 = __ldg(r + 4), a5 = __ldg(r + 5);
+    const double dx = __dsub_rn(T.y[0], __hiloint2double(__float_as_int(a0.y), __float_as_int(a0.x)));
+    const double dy = __dsub_rn(T.y[1], __hiloint2double(__float_as_int(a0.w), __float_as_int(a0.z)));
+    const double dz = __dsub_rn(T.y[2], __hiloint2double(__float_as_int(a1.y), __float_as_int(a1.x)));
     const double r2 = dist2_fp64(dx, dy, dz);
     if (!is_near<PREC>(A.sd, T, j, r2, A.Rc_sharp, Ps.rc2f)) return;
     ++npairs;
-    double s1, s2, s3;  // t = r/delta# <= cutoff_t here
-    table_sigma<SH_INV_W, SH_N>(A.tab_sharp, r2 * T.invd2[0], s1, s2, s3);
-    const double K1 = T.ad1[0] * s1, K3 = T.ad3[0] * s2, K5 = T.ad5[0] * s3;
-    if (SL) sl_accumulate(dx, dy, dz, K1, K3, c, wf, wn, accU);
+    const fpair wf[3] = {{a1.z, a1.w}, {a2.x, a2.y}, {a2.z, a2.w}};
+    const fpair wn[3] = {{a3.x, a3.y}, {a3.z, a3.w}, {a4.x, a4.y}};
+    const fpair qs[3] = {{a4.z, a4.w}, {a5.x, a5.y}, {a5.z, a5.w}};
+    fpair sg[3];  // t = r/delta# <= cutoff_t here
+    table_sigma<SH_INV_W, SH_N>(A.tab_sharp, r2 * T.invd2[0], sg);
+    fpair K[3];  // s#_p(t) / r^p = sigma#_p / delta#^p
+#pragma unroll
+    for (int p = 0; p < 3; ++p) K[p] = fp_mul({T.adh[p][0], T.adl[p][0]}, sg[p]);
+    const fpair d[3] = {fp_split(dx), fp_split(dy), fp_split(dz)};
+    if (SL) sl_accumulate_pair(d, K[0], K[1], nc, wf, wn, accU);
     if (DL) {
-        const double Q0 = qs[0] - q0[0], Q1 = qs[1] - q0[1], Q2 = qs[2] - q0[2];
-        const double dQ = fma(dz, Q2, fma(dy, Q1, dx * Q0));
-        const double W = fma(dz, wn[2], fma(dy, wn[1], dx * wn[0]));
-        const double sv = dQ * W * K5;
-        accV[0] = fma(sv, dx, accV[0]);
-        accV[1] = fma(sv, dy, accV[1]);
-        accV[2] = fma(sv, dz, accV[2]);
+        const fpair Q0 = fp_add(qs[0], fp_neg(q0[0])), Q1 = fp_add(qs[1], fp_neg(q0[1])), Q2 = fp_add(qs[2], fp_neg(q0[2]));
+        const fpair dQ = fp_dot3(d[0], d[1], d[2], Q0, Q1, Q2);
+        const fpair W = fp_dot3(d[0], d[1], d[2], wn[0], wn[1], wn[2]);
+        const fpair sv = fp_mul(fp_mul(dQ, W), K[2]);
+        accV[0] = fp_fma(sv, d[0], accV[0]);
+        accV[1] = fp_fma(sv, d[1], accV[1]);
+        accV[2] = fp_fma(sv, d[2], accV[2]);
     }
 }
 
@@ -126,14 +128,16 @@ __device__ __noinline__ void near_target_sharp(const EvalArgs &A, const ScanPara
     double q0[3];
     for (int i = 0; i < 3; ++i) q0[i] = DL ? A.q0[3 * m + i] : 0.0;
     const double c = SL ? fma(A.f0[3 * m + 2], T.n0[2], fma(A.f0[3 * m + 1], T.n0[1], A.f0[3 * m] * T.n0[0])) : 0.0;
-    double accU[3] = {0.0, 0.0, 0.0}, accV[3] = {0.0, 0.0, 0.0};
+    const fpair ncp = fp_split(-c), q0p[3] = {fp_split(q0[0]), fp_split(q0[1]), fp_split(q0[2])};
+    fpair pU[3] = {{0.0f, 0.0f}, {0.0f, 0.0f}, {0.0f, 0.0f}}, pV[3] = {{0.0f, 0.0f}, {0.0f, 0.0f}, {0.0f, 0.0f}};
     int npairs = 0;
     scan_near(A.sd, T, Ps, sq, lane, [&](int, int jj, bool valid) {
-        if (valid) process_sharp<PREC, SL, DL>(A, T, Ps, c, q0, jj, accU, accV, npairs);
+        if (valid) process_sharp<PREC, SL, DL>(A, T, Ps, ncp, q0p, jj, pU, pV, npairs);
     });
+    double accU[3], accV[3];
     for (int i = 0; i < 3; ++i) {
-        accU[i] = warp_sum(accU[i]);
-        accV[i] = warp_sum(accV[i]);
+        accU[i] = warp_sum(fp_to_double(pU[i]));
+        accV[i] = warp_sum(fp_to_double(pV[i]));
     }
     if (A.counters) {
         int np = npairs;

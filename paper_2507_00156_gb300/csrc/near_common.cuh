@@ -290,19 +290,17 @@ __device__ __forceinline__ void table_pairs(const float4 *__restrict__ ftab, int
     }
 }
 
-// sigma_p at tau as doubles (the on-surface path).
+// sigma_p at tau as float pairs (the on-surface path).
 template <int INV_W, int N>
-__device__ __forceinline__ void table_sigma(const double *__restrict__ tab, double tau, double &s1, double &s2,
-                                            double &s3) {
+__device__ __forceinline__ void table_sigma(const double *__restrict__ tab, double tau, fpair sg[3]) {
     const float4 *ftab = reinterpret_cast<const float4 *>(tab);
     int idx = (int)(approx_float_pos(tau) * (float)INV_W);
     idx = min(idx, N - 1);
     const double s = fma(tau, 2.0 * INV_W, -float_to_double((float)(2 * idx + 1)));  // local variable in [-1, 1]
-    float sg[3][2];
-    table_pairs<N>(ftab, idx, s, sg);
-    s1 = pair_to_double(sg[0][0], sg[0][1]);
-    s2 = pair_to_double(sg[1][0], sg[1][1]);
-    s3 = pair_to_double(sg[2][0], sg[2][1]);
+    float sp[3][2];
+    table_pairs<N>(ftab, idx, s, sp);
+#pragma unroll
+    for (int p = 0; p < 3; ++p) sg[p] = {sp[p][0], sp[p][1]};
 }
 
 // table_pairs at tau = r^2 / delta^2 without forming tau in FP64: the interval from the FP32
@@ -409,18 +407,6 @@ __device__ __forceinline__ void kernel_factors_pair(const Geom &T, const ScanPar
     }
 #pragma unroll
     for (int p = 0; p < 3; ++p) K[p] = {kh[p], kl[p]};
-}
-
-// Single-layer contraction: accU += K1 g + K3 d (d.g), g = wf - c wn.
-__device__ __forceinline__ void sl_accumulate(double dx, double dy, double dz, double K1, double K3, double c,
-                                              const double wf[3], const double wn[3], double accU[3]) {
-    const double g0 = fma(-c, wn[0], wf[0]);
-    const double g1 = fma(-c, wn[1], wf[1]);
-    const double g2 = fma(-c, wn[2], wf[2]);
-    const double t = K3 * fma(dz, g2, fma(dy, g1, dx * g0));
-    accU[0] = fma(t, dx, fma(K1, g0, accU[0]));
-    accU[1] = fma(t, dy, fma(K1, g1, accU[1]));
-    accU[2] = fma(t, dz, fma(K1, g2, accU[2]));
 }
 
 // The near-pair contractions in float pairs (k_near, k_batch): operands from the near-field record

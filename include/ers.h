@@ -83,9 +83,11 @@ extern "C" {
                               tree_p grows).  ERS_OPT_CONCURRENT is ignored.
                               Not available in the batched, no-allocation and closure paths */
 
-#define ERS_PREC_FP64 0   /* every step in FP64 arithmetic */
+#define ERS_PREC_FP64 0   /* far field in FP64; local sums at FP64-level accuracy (pair geometry in
+                             FP64, kernel factors and contractions in float-pair arithmetic,
+                             ~2^-46 relative), closest point and 3x3 solve in FP64 */
 #define ERS_PREC_MIXED 1  /* far field with FP32 operands and FP64 accumulation per source tile;
-                             local sums, closest point and 3x3 solve in FP64 */
+                             local sums, closest point and 3x3 solve as in ERS_PREC_FP64 */
 
 typedef struct ers_surface ers_surface; /* opaque, library-owned */
 
@@ -373,14 +375,19 @@ int ers_closure_data(ers_surface *s, const ers_params *p, const double *y, int64
  * Both layers with the learned closure: far field (precision of p) + one- or two-delta near sums +
  * the networks' correction; targets whose geometry leaves the training extent (ers_closure_range,
  * ers_closure_set_range_check) take the three-delta method instead.  Then a validation: every
- * vstride-th target is also evaluated with ers_eval (three deltas) and, per layer, the error
+ * vstride-th target is also given the three-delta method's value and, per layer, the error
  * max|value - method| / max|method| over that sample is measured with and without the network's
  * correction; a layer keeps the correction only where it lowers that error (else the correction
  * is taken back), and if the lower of the two errors exceeds tol for either layer, the whole call
  * falls back to ers_eval (*fell_back = 1).  val_err[2] (host, may be NULL) receives the errors of
  * the kept values; ers_closure_last_gate reports both errors and the choice.  Synchronizes the
- * stream (to read the validation).  Errors as ers_eval, plus ERS_E_TIMEOUT when a tensor-core
- * wait expired and ERS_E_STATE when a density is missing.
+ * stream (to read the validation).  The method's value at the sample and at the targets outside
+ * the extent is the closure's sums without the correction plus the difference of the near-field
+ * sums with three and with ndelta deltas over the three-delta near radius (the far field is the
+ * same in both; at targets between the two near radii the two-delta sums carry the plain sum, so
+ * the quadrature error of the subtraction identity there, below 1e-8 of the values, remains).
+ * Errors as ers_eval, plus ERS_E_TIMEOUT when a tensor-core wait expired and ERS_E_STATE when a
+ * density is missing.
  */
 int ers_eval_learned(ers_surface *s, ers_closure *c, const ers_params *p, const double *y, int64_t M,
                      const double *x0, const double *n0, const double *b, const double *f0, const double *q0,

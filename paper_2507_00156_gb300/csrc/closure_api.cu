@@ -166,8 +166,9 @@ __device__ __forceinline__ void target_frame(const double *x0, const double *n0,
 // convergent passes (one thread per target each):
 //   k_fit_scan   the target's neighbours (an FP32 distance prefilter, the FP64 test |x - x0|^2 <=
 //                (3.5 h)^2 where the prefilter is not conclusive) into a list;
-//   k_fit_accum  over the list: the 45 moments sum xi^p eta^q (p + q <= 8), which hold every entry
-//                of Phi^T Phi, and Phi^T U for the 6 density components along t1, t2, n0;
+//   k_fit_accum  over the list (three passes): the 45 moments sum xi^p eta^q (p + q <= 8), which
+//                hold every entry of Phi^T Phi, and Phi^T U for the 6 density components along
+//                t1, t2, n0, accumulated in float pairs;
 //   k_features   Phi^T Phi from the moments, Cholesky, the coefficients of the monomials of degree
 //                <= 3, then the features.
 // Separate passes keep the lanes of a warp on the same instructions (one thread per target walking
@@ -258,6 +259,10 @@ __global__ void k_fit_scan(FitArgs A) {
     A.cnt[m] = cnt <= FIT_LMAX ? cnt : -1;
 }
 
+// The coordinates (xi, eta) and the density components in the frame come from FP64 and are split
+// into float pairs once per node; the powers, the 45 moments and Phi^T U accumulate in float-pair
+// arithmetic on the FP32 pipe (~2^-46 relative, the FP64 pipe of this part runs 1/64 of its
+// rate) and are stored as doubles for the FP64 Cholesky.
 __global__ void __launch_bounds__(128) k_fit_accum(FitArgs A) {
     const int64_t m = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (m >= A.M) return;
@@ -267,49 +272,54 @@ __global__ void __launch_bounds__(128) k_fit_accum(FitArgs A) {
     fit_target(A, m, x0);
     target_frame(A.x0, A.n0, m, A.c, A.a, t1, t2, n, k1, k2);
     const double iR = 1.0 / (FIT_R * A.h);
-    // pass 1: moments and the single-layer density; pass 2: the double-layer density
+    // pass 0: the moments; pass 1: Phi^T U of the single-layer density; pass 2: of the double-layer
+    // density (three passes over the list keep the float-pair accumulators within the registers)
 #pragma unroll
-    for (int pass = 0; pass < 2; ++pass) {
-        double mom[NMOM], bacc[NB * 3];
-        if (pass == 0)
+    for (int pass = 0; pass < 3; ++pass) {
+        constexpr int NV = NMOM > NB * 3 ? NMOM : NB * 3;
+        fpair acc[NV];
 #pragma unroll
-            for (int e = 0; e < NMOM; ++e) mom[e] = 0.0;
-#pragma unroll
-        for (int e = 0; e < NB * 3; ++e) bacc[e] = 0.0;
+        for (int e = 0; e < NV; ++e) acc[e] = {0.0f, 0.0f};
         for (int k = 0; k < cnt; ++k) {
             const int j = A.list[(int64_t)k * A.M + m];
             const double *r = A.sd.rec + (int64_t)j * REC;
             const double d[3] = {r[0] - x0[0], r[1] - x0[1], r[2] - x0[2]};
-            const double xi = (d[0] * t1[0] + d[1] * t1[1] + d[2] * t1[2]) * iR;
-            const double eta = (d[0] * t2[0] + d[1] * t2[1] + d[2] * t2[2]) * iR;
-            const double *u = A.fq + (int64_t)j * 6 + 3 * pass;
-            const double uf[3] = {u[0] * t1[0] + u[1] * t1[1] + u[2] * t1[2], u[0] * t2[0] + u[1] * t2[1] + u[2] * t2[2],
-                                  u[0] * n[0] + u[1] * n[1] + u[2] * n[2]};
-            double xp[9], ep[9];
-            xp[0] = ep[0] = 1.0;
+            const fpair xi = fp_split((d[0] * t1[0] + d[1] * t1[1] + d[2] * t1[2]) * iR);
+            const fpair eta = fp_split((d[0] * t2[0] + d[1] * t2[1] + d[2] * t2[2]) * iR);
+            fpair xp[9], ep[9];
+            xp[0] = ep[0] = {1.0f, 0.0f};
 #pragma unroll
             for (int i = 1; i < (pass == 0 ? 9 : 5); ++i) {
-                xp[i] = xp[i - 1] * xi;
-                ep[i] = ep[i - 1] * eta;
+                xp[i] = fp_mul(xp[i - 1], xi);
+                ep[i] = fp_mul(ep[i - 1], eta);
             }
             if (pass == 0) {
 #pragma unroll
                 for (int dd = 0; dd <= 8; ++dd)
 #pragma unroll
-                    for (int q = 0; q <= dd; ++q) mom[mom_idx(dd - q, q)] = fma(xp[dd - q], ep[q], mom[mom_idx(dd - q, q)]);
-            }
+                    for (int q = 0; q <= dd; ++q)
+                        acc[mom_idx(dd - q, q)] = fp_fma(xp[dd - q], ep[q], acc[mom_idx(dd - q, q)]);
+            } else {
+                const double *u = A.fq + (int64_t)j * 6 + 3 * (pass - 1);
+                const fpair uf[3] = {fp_split(u[0] * t1[0] + u[1] * t1[1] + u[2] * t1[2]),
+                                     fp_split(u[0] * t2[0] + u[1] * t2[1] + u[2] * t2[2]),
+                                     fp_split(u[0] * n[0] + u[1] * n[1] + u[2] * n[2])};
 #pragma unroll
-            for (int i = 0; i < NB; ++i) {
-                const double phi = xp[mono_i(i)] * ep[mono_j(i)];
+                for (int i = 0; i < NB; ++i) {
+                    const fpair phi = fp_mul(xp[mono_i(i)], ep[mono_j(i)]);
 #pragma unroll
-                for (int c = 0; c < 3; ++c) bacc[3 * i + c] = fma(phi, uf[c], bacc[3 * i + c]);
+                    for (int c = 0; c < 3; ++c) acc[3 * i + c] = fp_fma(phi, uf[c], acc[3 * i + c]);
+                }
             }
         }
-        if (pass == 0)
+        if (pass == 0) {
 #pragma unroll
-            for (int e = 0; e < NMOM; ++e) A.acc[(int64_t)e * A.M + m] = mom[e];
+            for (int e = 0; e < NMOM; ++e) A.acc[(int64_t)e * A.M + m] = fp_to_double(acc[e]);
+        } else {
 #pragma unroll
-        for (int e = 0; e < NB * 3; ++e) A.acc[(int64_t)(NMOM + pass * NB * 3 + e) * A.M + m] = bacc[e];
+            for (int e = 0; e < NB * 3; ++e)
+                A.acc[(int64_t)(NMOM + (pass - 1) * NB * 3 + e) * A.M + m] = fp_to_double(acc[e]);
+        }
     }
 }
 

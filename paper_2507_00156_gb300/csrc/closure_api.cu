@@ -333,15 +333,20 @@ __device__ bool fit_solve(const FitArgs &A, int64_t m, double *L, double out[10]
     for (int i = 0; i < NB; ++i)
         for (int k = 0; k <= i; ++k)
             L[(i * (i + 1) / 2 + k) * S] = A.acc[(int64_t)mom_idx(mono_i(i) + mono_i(k), mono_j(i) + mono_j(k)) * A.M + m];
+    // the reciprocals of the diagonal, so that the factorization and the solves multiply (an FP64
+    // division costs several FP64-pipe instructions)
+    double rd[NB];
     for (int i = 0; i < NB; ++i)
         for (int j = 0; j <= i; ++j) {
             double s = L[(i * (i + 1) / 2 + j) * S];
             for (int q = 0; q < j; ++q) s -= L[(i * (i + 1) / 2 + q) * S] * L[(j * (j + 1) / 2 + q) * S];
             if (i == j) {
                 if (!(s > 0.0)) return false;
-                L[(i * (i + 1) / 2 + i) * S] = sqrt(s);
+                const double l = sqrt(s);
+                L[(i * (i + 1) / 2 + i) * S] = l;
+                rd[i] = 1.0 / l;
             } else {
-                L[(i * (i + 1) / 2 + j) * S] = s / L[(j * (j + 1) / 2 + j) * S];
+                L[(i * (i + 1) / 2 + j) * S] = s * rd[j];
             }
         }
     for (int rc = 0; rc < NRHS; ++rc) {
@@ -349,12 +354,12 @@ __device__ bool fit_solve(const FitArgs &A, int64_t m, double *L, double out[10]
         for (int i = 0; i < NB; ++i) {  // L y = (Phi^T U)_rc
             double s = A.acc[(int64_t)(NMOM + (rc / 3) * NB * 3 + 3 * i + rc % 3) * A.M + m];
             for (int q = 0; q < i; ++q) s -= L[(i * (i + 1) / 2 + q) * S] * y[q];
-            y[i] = s / L[(i * (i + 1) / 2 + i) * S];
+            y[i] = s * rd[i];
         }
         for (int i = NB - 1; i >= 0; --i) {  // L^T x = y
             double s = y[i];
             for (int q = i + 1; q < NB; ++q) s -= L[(q * (q + 1) / 2 + i) * S] * y[q];
-            y[i] = s / L[(i * (i + 1) / 2 + i) * S];
+            y[i] = s * rd[i];
         }
         for (int k = 0; k < 10; ++k) out[k][rc] = y[k] * deriv_factor(k);
     }

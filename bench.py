@@ -555,7 +555,7 @@ def run_reference(args, world, rank):
     sample = (f"{per_step} seeded targets per step out of {len(y)} (same mix), FP64 oracle, localized far+near "
               f"form; value is targets/s, i.e. extrapolated per target to the full workload")
     print(json.dumps({"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
-                      "warmup": args.warmup, "ms_per_step": t * 1e3, "higher_is_better": True, "scaling": "weak",
+                      "warmup": args.warmup, "ms_per_step": t * 1e3, "higher_is_better": True, "scaling": "strong",
                       "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
                       "config": {"workload": WORKLOAD, "N": len(w), "M": len(y), "rho": list(wl.rho)},
                       "cpu_baseline": {"value": value, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",

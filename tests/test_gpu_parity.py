@@ -98,6 +98,41 @@ def test_eval_ellipsoid_with_far_points(ers):
         assert pu <= PER_TARGET_TOL[prec] and pv <= PER_TARGET_TOL[prec], (prec, pu, pv)
 
 
+def test_eval_far_from_the_origin_and_scaled(ers):
+    """Ellipsoid (4, 3.2, 2.4) centred at (40, -25, 12), h = 1/8 (a unit-size case moved and scaled
+    by 4): the tile-relative FP32 far field, the FP32 prefilter at absolute coordinates ~50 and the
+    near field at kernel factors 4^p times smaller, on node, band and box targets; densities are
+    polynomials of the coordinates relative to the centre, divided by 4."""
+    import torch
+    shape = workloads.Shape((40.0, -25.0, 12.0), (4.0, 3.2, 2.4))
+    h, rho = 1 / 8, (2, 3, 4)
+    c = np.asarray(shape.center)
+    rng = np.random.default_rng(404)
+    fc, qc = workloads.density_coeffs(rng), workloads.density_coeffs(rng)
+    dens = lambda coef, pts: workloads.poly_eval(coef, (pts - c) / 4.0)
+    x, n, w = oracle.quadrature(shape, h)
+    yb = workloads.near_band_targets(shape, 1500, 6 * rho[2] * h * 0.7, rng)[0]
+    yf = c + rng.uniform(-8.0, 8.0, (300, 3))
+    y = np.concatenate([x[::5], yb, yf])
+    x0, n0, b = oracle.closest_point(shape, y)
+    uo, vo, _ = oracle.evaluate(x, n, w, dens(fc, x), dens(qc, x), y, x0, n0, b, dens(fc, x0), dens(qc, x0), h, rho)
+    s = ers.Surface(shape.center, shape.axes, h)
+    xd = s.nodes()[0].cpu().numpy()
+    assert np.abs(xd - x).max() <= 1e-13
+    t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    s.set_density(t(dens(fc, xd)), t(dens(qc, xd)))
+    yd = t(y)
+    x0d, n0d, bd = s.closest_point(yd)
+    assert np.abs(bd.cpu().numpy() - b).max() < 1e-12
+    x0h = x0d.cpu().numpy()
+    for prec, tol in ((0, FP64_TOL), (1, MIXED_TOL)):
+        u, v = s.eval(yd, t(dens(fc, x0h)), t(dens(qc, x0h)), rho=rho, precision=prec, x0=x0d, n0=n0d, b=bd)
+        u, v = u.cpu().numpy(), v.cpu().numpy()
+        assert rel_err(u, uo) <= tol and rel_err(v, vo) <= tol, (prec, rel_err(u, uo), rel_err(v, vo))
+        pu, pv = per_target_rel_err(u, uo), per_target_rel_err(v, vo)
+        assert pu <= PER_TARGET_TOL[prec] and pv <= PER_TARGET_TOL[prec], (prec, pu, pv)
+
+
 # Below 6 the cutoff is a non-tie value: the lattice rule has many node pairs at exact multiples
 # of h (t = i at delta = 2h), and where t = cutoff_t exactly, s_p jumps by eps_p(cutoff_t)
 # (6e-6 at 4, 4e-14 at 6), so ulp-level differences between two sets of nodes decide the result.

@@ -19,9 +19,11 @@
 //
 // One warp per target.  The warp walks the rows of the cell grid that meet the ball of radius
 // Rc, tests candidates with an FP32 prefilter (conservative margin), and queues survivors by
-// class c = number of delta_k with r > min(4.7, cutoff_t) delta_k (0..ND), so that each batch of 32 runs
-// one code path.  Each batch then makes the exact FP64 (or, for the mixed far field, the
-// identical FP32) near/far test, so that the partition matches the far-field mask exactly.
+// class c = number of delta_k with r > min(4.7, cutoff_t) delta_k (0..ND), so that the lanes of a
+// batch of 32 run the same loops over the deltas (the class is a run-time value of one code path).
+// Each batch then makes the exact FP64 (or, for the mixed far field, the identical FP32) near/far
+// test, so that the partition matches the far-field mask exactly.  Node data come from the
+// 96-byte near-field records (x in FP64; w f, w n, q as float pairs).
 #include <algorithm>
 #include <cmath>
 

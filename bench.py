@@ -775,7 +775,7 @@ def main():
                    "parallelism": ("targets sharded over %d GPUs (contiguous Morton-order slices, %d-%d targets "
                                    "per GPU; surface on every GPU; no collective on the data path)"
                                    % (world, M_all // world, -(-M_all // world)) if world > 1 else "one GPU"),
-                   "cutoff_t": 6.0, "precision": ("mixed (FP32 far field with FP64 tile sums; local sums in float-pair arithmetic, ~2^-46 relative; FP64 pair geometry, closest point and solve)"),
+                   "cutoff_t": 6.0, "precision": ("mixed (FP32 far field with FP64 tile sums; local sums in float-pair arithmetic, ~1e-14 relative; FP64 pair geometry, closest point and solve)"),
                    "l2": "flushed between timed steps (256 MiB write, outside the timed events)"},
         "gpairs_per_s": args.steps * M_all * N / t_mixed / 1e9,
         "kernels_ms": {"closest_point": ms_closest, "far_field": ms_far, "near_field_and_solve": ms_near},

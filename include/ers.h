@@ -85,7 +85,7 @@ extern "C" {
 
 #define ERS_PREC_FP64 0   /* far field in FP64; local sums at FP64-level accuracy (pair geometry in
                              FP64, kernel factors and contractions in float-pair arithmetic,
-                             ~2^-46 relative), closest point and 3x3 solve in FP64 */
+                             ~1e-14 relative), closest point and 3x3 solve in FP64 */
 #define ERS_PREC_MIXED 1  /* far field with FP32 operands and FP64 accumulation per source tile;
                              local sums, closest point and 3x3 solve as in ERS_PREC_FP64 */
 

@@ -261,7 +261,7 @@ __global__ void k_fit_scan(FitArgs A) {
 
 // The coordinates (xi, eta) and the density components in the frame come from FP64 and are split
 // into float pairs once per node; the powers, the 45 moments and Phi^T U accumulate in float-pair
-// arithmetic on the FP32 pipe (~2^-46 relative, the FP64 pipe of this part runs 1/64 of its
+// arithmetic on the FP32 pipe (~1e-14 relative, the FP64 pipe of this part runs 1/64 of its
 // rate) and are stored as doubles for the FP64 Cholesky.
 __global__ void __launch_bounds__(128) k_fit_accum(FitArgs A) {
     const int64_t m = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;

@@ -35,7 +35,7 @@ constexpr int TS32 = 256;  // sources per FP32 tile (one centre c_tile per tile)
 // Device copy (TAB_DEV_BYTES): per interval and function three float4: degrees 6, 5, 4 as floats
 // with the interval offset 2 i + 1, then degrees 3..0 as float pairs (hi, lo).  Degrees 4..6
 // carry less than 2e-8 of the value on every interval, so their FP32 evaluation costs at most
-// ~2e-15 relative; degrees 3..0 are evaluated in float-pair arithmetic (~2^-46 relative) on the
+// ~2e-15 relative; degrees 3..0 are evaluated in float-pair arithmetic (~1e-14 relative) on the
 // FP32 pipe, which on this part runs 64 times the FP64 rate.
 constexpr int TAB_INV_W = 16;     // intervals per unit tau
 constexpr int TAB_N = 384;        // tau in [0, 24)
@@ -418,11 +418,13 @@ __device__ __forceinline__ void pair_add(float &kh, float &kl, float f) {
 // h + l as a double (one FP64 add).
 __device__ __forceinline__ double pair_to_double(float h, float l) { return float_to_double(h) + float_to_double(l); }
 
-// The same arithmetic on a value type, for the near-field contractions.  Error bounds (u = 2^-24):
-// fp_mul returns the exact product of the leading floats plus the cross terms, unnormalized
-// (|l| <= 3u |h|), with error <= ~2u^2 |a b|; fp_add is Knuth's two-sum of the leading floats
-// with the trailing ones added, then renormalized, with error <= ~2u^2 (|a| + |b|).  Either
-// kind of pair (normalized or not) is a valid operand.
+// The same arithmetic on a value type, for the near-field contractions.  Error bounds (u = 2^-24,
+// operands with |l| <= 2u |h| as split_pair gives them): fp_mul returns the exact product of the
+// leading floats plus the cross terms, unnormalized (|l| <= 5u |h|), with error <= 12 u^2 |a b|
+// (the product of the trailing floats, which it leaves out, and two roundings of the cross
+// terms); fp_add is Knuth's two-sum of the leading floats with the trailing ones added, then
+// renormalized, with error <= 6 u^2 (|a| + |b|); fp_fma, an unnormalized product added,
+// <= 24 u^2 (|a b| + |c|).  u^2 = 3.6e-15.
 struct fpair {
     float h, l;
 };

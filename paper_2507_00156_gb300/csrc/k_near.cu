@@ -11,7 +11,7 @@
 // Single layer (Eq. (Sreg)):  K1 g + K3 d (d.g).
 // Double layer (Eqs. (Tsplit), (Treg)):  -6 [ t1 (K3 - (r^2 - b^2) K5) + t2 K5 ] : Q (w n),
 // contracted in closed form (dl_accumulate_pair in near_common.cuh).  Kernel factors and both
-// contractions run in float pairs on the FP32 pipe (~2^-46 relative; the FP64 pipe of this part
+// contractions run in float pairs on the FP32 pipe (~1e-14 relative; the FP64 pipe of this part
 // runs at 1/64 of the FP32 rate); d, r^2 and the near/far test stay FP64.
 // The weights alpha are the first row of the inverse of A_k = [1, rho_k I0(b/delta_k),
 // rho_k^3 I2(b/delta_k)] (Eqs. (extrap_eqn), (I0), (I2)), by Cramer's rule.  The O(delta^7)

@@ -271,7 +271,7 @@ __device__ __forceinline__ bool is_near(const SurfDev &s, const Geom &T, int64_t
 // sigma_p(tau) (or sigma#_p with the on-surface table) from a device table of INV_W intervals per
 // unit tau and N intervals, for the local variable s (in [-1, 1] up to the interval-choice bound
 // below): degrees 6..4 of the local polynomial in FP32, 3..0 in float pairs (Horner), results
-// as float pairs sg[p] = (hi, lo), relative error ~2e-15 (the interpolation) + ~2^-46 (the pairs).
+// as float pairs sg[p] = (hi, lo), relative error ~2e-15 (the interpolation) + ~1e-14 (the pairs).
 template <int N>
 __device__ __forceinline__ void table_pairs(const float4 *__restrict__ ftab, int idx, double s, float sg[3][2]) {
     float sh, sl;
@@ -320,7 +320,7 @@ __device__ __forceinline__ void table_pairs_r2(const double *__restrict__ tab, d
     table_pairs<N>(ftab, idx, s, sg);
 }
 
-// K1, K3, K5 as float pairs (~2^-46 relative); r2p = r2 as a float pair.  The class is a
+// K1, K3, K5 as float pairs (~1e-14 relative); r2p = r2 as a float pair.  The class is a
 // run-time value, uniform over a batch of pairs: one code path for all of them keeps the kernel
 // within the instruction cache, and the loops over deltas stay rolled (the unrolled float-pair
 // code of several deltas overflows it); T sits in shared memory, since the loops index its arrays
@@ -411,7 +411,7 @@ __device__ __forceinline__ void kernel_factors_pair(const Geom &T, const ScanPar
 
 // The near-pair contractions in float pairs (k_near, k_batch): operands from the near-field record
 // and the target's pairs, results added into per-lane float-pair accumulators.  Each result
-// carries an error ~2^-46 of the magnitudes it is formed from, far below the 1e-11 the FP64 path
+// carries an error ~1e-14 of the magnitudes it is formed from, far below the 1e-11 the FP64 path
 // is held to.
 // Single layer (Eq. (Sreg)): accU += K1 g + K3 d (d.g), g = w f - c w n.
 // Double layer: with d = y - x = b n0 - xh, L = r^2 K5 - K3, U = d.Q, W = d.m, nQ = n0.Q,
@@ -420,7 +420,7 @@ __device__ __forceinline__ void kernel_factors_pair(const Geom &T, const ScanPar
 // into n0 (K (b P - S) + K5 b R) + xh (K5 (b S - R) - K P) and collect (K - b^2 K5 = -L);
 // accN += the n0 coefficient, accD += the d coefficient (the result is -6/(8 pi) (accN n0 - accD)).
 // Where every delta is on the defect path L is ~1e-7 of K3 or less, and its float-pair error,
-// ~2^-46 of K3, is of the size of the other terms' errors.
+// ~1e-14 of K3, is of the size of the other terms' errors.
 __device__ __forceinline__ void sl_accumulate_pair(const fpair d[3], fpair K1, fpair K3, fpair nc, const fpair wf[3],
                                                    const fpair wn[3], fpair accU[3]) {
     const fpair g0 = fp_fma(nc, wn[0], wf[0]);  // g = w f - c w n, nc = -c

@@ -364,7 +364,8 @@ int ers_closure_train(ers_closure *c, int layer, const float *X, const float *T,
  * weight 0 (and no correction) beyond the reduced near radius or without a density fit.  u3, v3
  * (M,3) dev are the values of ers_eval (three deltas) at the same targets.  valid (M) ints: 1 for
  * targets with a positive weight in either layer.  x0, n0, b from ers_closest_point; both
- * densities must have been set.
+ * densities must have been set.  ERS_OPT_FOUR_DELTA, ERS_OPT_TREECODE and ERS_OPT_SHARP give
+ * ERS_E_UNSUPPORTED.
  */
 int ers_closure_data(ers_surface *s, const ers_params *p, const double *y, int64_t M, const double *x0,
                      const double *n0, const double *b, const double *f0, const double *q0, const double *u3,
@@ -387,7 +388,8 @@ int ers_closure_data(ers_surface *s, const ers_params *p, const double *y, int64
  * same in both; at targets between the two near radii the two-delta sums carry the plain sum, so
  * the quadrature error of the subtraction identity there, below 1e-8 of the values, remains).
  * Errors as ers_eval, plus ERS_E_TIMEOUT when a tensor-core wait expired and ERS_E_STATE when a
- * density is missing.
+ * density is missing; ERS_OPT_FOUR_DELTA, ERS_OPT_TREECODE and ERS_OPT_SHARP give
+ * ERS_E_UNSUPPORTED.
  */
 int ers_eval_learned(ers_surface *s, ers_closure *c, const ers_params *p, const double *y, int64_t M,
                      const double *x0, const double *n0, const double *b, const double *f0, const double *q0,

@@ -1045,8 +1045,8 @@ int ers_closure_data(ers_surface *s, const ers_params *p, const double *y, int64
     if (ndelta != 1 && ndelta != 2) return fail(ERS_E_INVAL, "ers_closure_data: ndelta must be 1 or 2");
     if (!s || !p || !y || !x0 || !n0 || !b || !f0 || !q0 || !u3 || !v3 || !Xs || !Xd || !Ts || !Td || !valid)
         return fail(ERS_E_INVAL, "ers_closure_data: NULL argument");
-    if (p->options & (ERS_OPT_FOUR_DELTA | ERS_OPT_TREECODE))
-        return fail(ERS_E_UNSUPPORTED, "ers_closure_data: ERS_OPT_FOUR_DELTA and ERS_OPT_TREECODE are not supported");
+    if (p->options & (ERS_OPT_FOUR_DELTA | ERS_OPT_TREECODE | ERS_OPT_SHARP))
+        return fail(ERS_E_UNSUPPORTED, "ers_closure_data: ERS_OPT_FOUR_DELTA, ERS_OPT_TREECODE and ERS_OPT_SHARP are not supported");
     if (M <= 0) return fail(ERS_E_INVAL, "ers_closure_data: M <= 0");
     cudaStream_t st = (cudaStream_t)stream;
     Scratch &w = s->host_io;  // reuse the host-io buffer of the surface as scratch: u2 | v2 | gamma | scale
@@ -1078,8 +1078,8 @@ int ers_eval_learned(ers_surface *s, ers_closure *c, const ers_params *p, const 
     if (ndelta != 1 && ndelta != 2) return fail(ERS_E_INVAL, "ers_eval_learned: ndelta must be 1 or 2");
     if (!s || !c || !p || !y || !x0 || !n0 || !b || !f0 || !q0 || !u || !v)
         return fail(ERS_E_INVAL, "ers_eval_learned: NULL argument (both layers and all closest-point data needed)");
-    if (p->options & (ERS_OPT_FOUR_DELTA | ERS_OPT_TREECODE))
-        return fail(ERS_E_UNSUPPORTED, "ers_eval_learned: ERS_OPT_FOUR_DELTA and ERS_OPT_TREECODE are not supported");
+    if (p->options & (ERS_OPT_FOUR_DELTA | ERS_OPT_TREECODE | ERS_OPT_SHARP))
+        return fail(ERS_E_UNSUPPORTED, "ers_eval_learned: ERS_OPT_FOUR_DELTA, ERS_OPT_TREECODE and ERS_OPT_SHARP are not supported");
     if (M < 0) return fail(ERS_E_INVAL, "ers_eval_learned: M < 0");
     if (vstride < 1) return fail(ERS_E_INVAL, "ers_eval_learned: vstride must be >= 1");
     int rc = closure_check(c, 0);

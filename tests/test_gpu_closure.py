@@ -475,3 +475,38 @@ def test_validation_reference_from_near_field_differences(ers):
             print(f"precision {prec} ndelta {nd}: reported {err[0]:.6e} {err[1]:.6e}, direct {du:.6e} {dv:.6e}")
             assert du > 1e-6 and dv > 1e-6
             assert abs(err[0] - du) <= 1e-7 and abs(err[1] - dv) <= 1e-7
+
+
+@pytest.mark.gpu
+def test_closure_entry_points_reject_the_options(ers):
+    """ers_closure_data and ers_eval_learned take none of the options f1-f3 (treecode, on-surface
+    s#, four deltas): ERS_E_UNSUPPORTED, with nothing evaluated.  (The validation's near-field
+    difference assumes the three-delta near radius for every target, which ERS_OPT_SHARP changes
+    for targets on the surface.)"""
+    import ctypes
+    import torch
+    shape = workloads.unit_sphere()
+    s = ers.Surface(shape.center, shape.axes, 1 / 16)
+    x = s.nodes()[0].cpu().numpy()
+    rng = np.random.default_rng(8)
+    P = _problem(ers, s, workloads.density_coeffs(rng), workloads.density_coeffs(rng), x[:64], 0)
+    M = 64
+    net = ers.Closure(seed=0)
+    L = ers.lib()
+    u = torch.zeros((M, 3), dtype=torch.float64, device="cuda")
+    v = torch.zeros_like(u)
+    X = torch.zeros((M, ers.XSTR), dtype=torch.float32, device="cuda")
+    T = torch.zeros((M, 4), dtype=torch.float32, device="cuda")
+    ok = torch.zeros((M,), dtype=torch.int32, device="cuda")
+    ptrs = [ers._ptr(P[k]) for k in ("y", "x0", "n0", "b", "f0", "q0")]
+    for kw in (dict(sharp=True), dict(rho=(2, 3, 4, 5)), dict(tree=True)):
+        p = ers.params(precision=0, **kw)
+        ve, fb = (ctypes.c_double * 2)(), ctypes.c_int()
+        rc = L.ers_eval_learned(s.handle, net.handle, ctypes.byref(p), ptrs[0], M, *ptrs[1:], 2, ers._ptr(u),
+                                ers._ptr(v), 1.0, 4, ve, ctypes.byref(fb), ers._stream(None))
+        assert rc == ers.ERS_E_UNSUPPORTED, (kw, rc)
+        rc = L.ers_closure_data(s.handle, ctypes.byref(p), ptrs[0], M, *ptrs[1:], ers._ptr(P["u3"]),
+                                ers._ptr(P["v3"]), 2, ers._fptr(X), ers._fptr(X), ers._fptr(T), ers._fptr(T),
+                                ers._fptr(ok), ers._stream(None))
+        assert rc == ers.ERS_E_UNSUPPORTED, (kw, rc)
+    assert not u.any() and not X.any()

@@ -330,12 +330,6 @@ __device__ __forceinline__ f2 sub2(f2 a, f2 b) {
     return d;
 }
 
-// Round-to-nearest form of approx_float_pos (integer pipe only): adds half a float ulp in the
-// double's bits before truncating; relative error <= 2^-24 for 2^-126 <= x < 2^127.
-__device__ __forceinline__ float round_float_pos(double x) {
-    return approx_float_pos(__longlong_as_double(__double_as_longlong(x) + (1LL << 28)));
-}
-
 // Signed form of approx_float_pos: |result| <= |x| with relative error < 2^-23 for
 // 2^-126 <= |x| < 2^127, zero below (the shifted-out top bits of the high word hold the sign).
 __device__ __forceinline__ float approx_float(double x) {
@@ -448,8 +442,20 @@ __device__ __forceinline__ fpair fp_add(fpair a, fpair b) {
     return {h, __fsub_rn(w, __fsub_rn(h, s))};
 }
 __device__ __forceinline__ fpair fp_fma(fpair a, fpair b, fpair c) { return fp_add(fp_mul(a, b), c); }
+// a0 b0 + a1 b1 + a2 b2: the three products by fp_mul, their leading floats summed by two
+// two-sums, everything else (the products' trailing parts, the two-sums' errors) added in FP32,
+// then renormalized; error <= ~20 u^2 (|a0 b0| + |a1 b1| + |a2 b2|).
 __device__ __forceinline__ fpair fp_dot3(fpair a0, fpair a1, fpair a2, fpair b0, fpair b1, fpair b2) {
-    return fp_fma(a2, b2, fp_fma(a1, b1, fp_mul(a0, b0)));
+    const fpair p0 = fp_mul(a0, b0), p1 = fp_mul(a1, b1), p2 = fp_mul(a2, b2);
+    const float s = __fadd_rn(p0.h, p1.h);
+    float v = __fsub_rn(s, p0.h);
+    const float e1 = __fadd_rn(__fsub_rn(p0.h, __fsub_rn(s, v)), __fsub_rn(p1.h, v));
+    const float t = __fadd_rn(s, p2.h);
+    v = __fsub_rn(t, s);
+    const float e2 = __fadd_rn(__fsub_rn(s, __fsub_rn(t, v)), __fsub_rn(p2.h, v));
+    const float w = __fadd_rn(__fadd_rn(__fadd_rn(p0.l, p1.l), p2.l), __fadd_rn(e1, e2));
+    const float h = __fadd_rn(t, w);
+    return {h, __fsub_rn(w, __fsub_rn(h, t))};
 }
 __device__ __forceinline__ double fp_to_double(fpair a) { return pair_to_double(a.h, a.l); }
 

@@ -134,6 +134,21 @@ def _fp_add(a, b):
     return h, F32(w - F32(h - s))
 
 
+def _fp_dot3(a, b):
+    """fp_dot3 of the kernels: three fp_mul products, their leading floats by two two-sums, the rest
+    added in float32, renormalized."""
+    p = [_fp_mul(x, y) for x, y in zip(a, b)]
+    s = F32(p[0][0] + p[1][0])
+    v = F32(s - p[0][0])
+    e1 = F32(F32(p[0][0] - F32(s - v)) + F32(p[1][0] - v))
+    t = F32(s + p[2][0])
+    v = F32(t - s)
+    e2 = F32(F32(s - F32(t - v)) + F32(p[2][0] - v))
+    w = F32(F32(F32(p[0][1] + p[1][1]) + p[2][1]) + F32(e1 + e2))
+    h = F32(t + w)
+    return h, F32(w - F32(h - t))
+
+
 def _layout_eval(rec, s):
     """One function's 12 floats of the device layout (c6, c5, c4, 2i+1, c3 hi/lo, c2 hi/lo, c1 hi/lo,
     c0 hi/lo) at the local variable s, evaluated as the kernel does."""
@@ -321,7 +336,8 @@ def test_float_pair_primitives_meet_their_bounds():
     stay within the bounds derived in the kernels' comments (u = 2^-24, operands split by
     truncation, |l| <= 2u |h|): 12 u^2 |a b| for a product (the neglected product of the trailing
     floats, 4 u^2, and two roundings of the cross terms, 3 u^2 and 5 u^2), 6 u^2 (|a| + |b|) for a
-    sum, 24 u^2 (|a b| + |c|) for a product added to a pair."""
+    sum, 24 u^2 (|a b| + |c|) for a product added to a pair, 20 u^2 (sum |a_i b_i|) for the
+    three-term dot product."""
     from fractions import Fraction as Fr
     rng = np.random.default_rng(17)
     u2 = Fr(1, 2 ** 48)
@@ -339,5 +355,14 @@ def test_float_pair_primitives_meet_their_bounds():
         worst[1] = max(worst[1], abs(val(sm) - (A + B)) / ((abs(A) + abs(B)) * u2))
         f = _fp_add(m, c)  # fp_fma: an unnormalized product as an operand
         worst[2] = max(worst[2], abs(val(f) - (A * B + C)) / ((abs(A * B) + abs(C)) * u2))
-    print("worst errors in units of u^2:", [float(w) for w in worst])
-    assert worst[0] <= 12 and worst[1] <= 6 and worst[2] <= 24
+    worst_dot = Fr(0)
+    for _ in range(5000):  # fp_dot3: <= 20 u^2 (|a0 b0| + |a1 b1| + |a2 b2|)
+        xs = rng.standard_normal(6) * 10.0 ** rng.uniform(-3, 3, 6)
+        if rng.random() < 0.3:
+            xs[5] = -(xs[0] * xs[3] + xs[1] * xs[4]) / xs[2] * (1 + rng.standard_normal() * 1e-6)
+        a, b = [_split_pair(z) for z in xs[:3]], [_split_pair(z) for z in xs[3:]]
+        A, B = [val(z) for z in a], [val(z) for z in b]
+        exact = sum(p * q for p, q in zip(A, B))
+        worst_dot = max(worst_dot, abs(val(_fp_dot3(a, b)) - exact) / (sum(abs(p * q) for p, q in zip(A, B)) * u2))
+    print("worst errors in units of u^2:", [float(w) for w in worst], float(worst_dot))
+    assert worst[0] <= 12 and worst[1] <= 6 and worst[2] <= 24 and worst_dot <= 20

@@ -91,3 +91,25 @@ def test_sharp_full_size_bench_workload_sampled(ers):
     y, uo, vo, bo = oracle_eval_sharp("sphere128", sel=sel, rho_sharp=3.0)
     assert np.array_equal(y, y_all[sel]) and (bo == 0).sum() > 50
     assert rel_err(u[sel], uo) <= MIXED_TOL and rel_err(v[sel], vo) <= MIXED_TOL
+
+
+@pytest.mark.parametrize("precision,tol", [(0, FP64_TOL), (1, MIXED_TOL)])
+def test_sharp_ellipsoid_with_far_points(ers, precision, tol):
+    """Ellipsoid (1, 0.8, 0.6) at h = 1/32 (curvature varying over the surface): every 11th node
+    (the s# path) and the band and box targets (extrapolated or far), against the oracle."""
+    import oracle
+    import workloads
+    shape = workloads.Shape((0.0, 0.0, 0.0), (1.0, 0.8, 0.6))
+    wl = workloads.make_workload("ell32", shape, 1 / 32, (2, 3, 4), 77, 1500, 16 / 32 * 0.7, n_far=700)
+    g = GpuProblem("ell32", wl)
+    x, n, w = oracle.quadrature(shape, wl.h)
+    sel = np.concatenate([np.arange(0, len(w), 11), len(w) + np.arange(len(wl.extra_targets))])
+    y = np.concatenate([x, wl.extra_targets])[sel]
+    x0, n0, b = oracle.closest_point(shape, y)
+    f0, q0 = workloads.poly_eval(wl.f_coef, x0), workloads.poly_eval(wl.q_coef, x0)
+    uo, vo, _ = oracle.evaluate_sharp(x, n, w, workloads.poly_eval(wl.f_coef, x), workloads.poly_eval(wl.q_coef, x),
+                                      y, x0, n0, b, f0, q0, wl.h, wl.rho, 6.0, 3.0)
+    u, v, bg = g.eval(g.targets(sel), precision=precision, sharp=True, rho_sharp=3.0)
+    assert (bg == 0).sum() == (b == 0).sum() > 0
+    eu, ev = rel_err(u, uo), rel_err(v, vo)
+    assert eu <= tol and ev <= tol, (eu, ev)

@@ -24,7 +24,9 @@
 //            divided by their largest magnitude S;
 //   output   c (3 components in the frame) = sum_j A_ej(geometry) jet_j, the correction divided by
 //            S h^p (p = 1 single layer, p = 0 double layer; for ndelta = 2 also by -gamma).
-// A validation sample of targets is also evaluated with the three-delta method: per layer the
+// A validation sample of targets is also given the three-delta method's value (the closure's sums
+// plus the difference of the near-field-only sums with three and with nd deltas, the far field
+// being the same in both; see k_compare): per layer the
 // network's correction is kept only if it brings the sample closer to the method than the sums
 // without it, and if either layer still differs by more than a tolerance the whole evaluation
 // falls back to the three-delta method.

@@ -442,20 +442,27 @@ __device__ __forceinline__ fpair fp_add(fpair a, fpair b) {
     return {h, __fsub_rn(w, __fsub_rn(h, s))};
 }
 __device__ __forceinline__ fpair fp_fma(fpair a, fpair b, fpair c) { return fp_add(fp_mul(a, b), c); }
-// a0 b0 + a1 b1 + a2 b2: the three products by fp_mul, their leading floats summed by two
-// two-sums, everything else (the products' trailing parts, the two-sums' errors) added in FP32,
-// then renormalized; error <= ~20 u^2 (|a0 b0| + |a1 b1| + |a2 b2|).
-__device__ __forceinline__ fpair fp_dot3(fpair a0, fpair a1, fpair a2, fpair b0, fpair b1, fpair b2) {
-    const fpair p0 = fp_mul(a0, b0), p1 = fp_mul(a1, b1), p2 = fp_mul(a2, b2);
-    const float s = __fadd_rn(p0.h, p1.h);
-    float v = __fsub_rn(s, p0.h);
-    const float e1 = __fadd_rn(__fsub_rn(p0.h, __fsub_rn(s, v)), __fsub_rn(p1.h, v));
-    const float t = __fadd_rn(s, p2.h);
+// x + y + z: the three leading floats summed by two two-sums, everything else (the trailing
+// floats, the two-sums' errors) added in FP32, then renormalized: 19 FP32 operations against 22
+// for two fp_add; error <= ~6 u^2 (|x| + |y| + |z|) for operands with |l| <= 5u |h|.
+__device__ __forceinline__ fpair fp_sum3(fpair x, fpair y, fpair z) {
+    const float s = __fadd_rn(x.h, y.h);
+    float v = __fsub_rn(s, x.h);
+    const float e1 = __fadd_rn(__fsub_rn(x.h, __fsub_rn(s, v)), __fsub_rn(y.h, v));
+    const float t = __fadd_rn(s, z.h);
     v = __fsub_rn(t, s);
-    const float e2 = __fadd_rn(__fsub_rn(s, __fsub_rn(t, v)), __fsub_rn(p2.h, v));
-    const float w = __fadd_rn(__fadd_rn(__fadd_rn(p0.l, p1.l), p2.l), __fadd_rn(e1, e2));
+    const float e2 = __fadd_rn(__fsub_rn(s, __fsub_rn(t, v)), __fsub_rn(z.h, v));
+    const float w = __fadd_rn(__fadd_rn(__fadd_rn(x.l, y.l), z.l), __fadd_rn(e1, e2));
     const float h = __fadd_rn(t, w);
     return {h, __fsub_rn(w, __fsub_rn(h, t))};
+}
+// a0 b0 + a1 b1 + a2 b2; error <= ~20 u^2 (|a0 b0| + |a1 b1| + |a2 b2|).
+__device__ __forceinline__ fpair fp_dot3(fpair a0, fpair a1, fpair a2, fpair b0, fpair b1, fpair b2) {
+    return fp_sum3(fp_mul(a0, b0), fp_mul(a1, b1), fp_mul(a2, b2));
+}
+// acc + a b + c d; error <= ~20 u^2 (|acc| + |a b| + |c d|).
+__device__ __forceinline__ fpair fp_acc2(fpair acc, fpair a, fpair b, fpair c, fpair d) {
+    return fp_sum3(acc, fp_mul(a, b), fp_mul(c, d));
 }
 __device__ __forceinline__ double fp_to_double(fpair a) { return pair_to_double(a.h, a.l); }
 

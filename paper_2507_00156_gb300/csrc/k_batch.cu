@@ -213,7 +213,7 @@ __device__ __forceinline__ void near_pair(const BatchProblemDev &P, const Geom &
     if (sl) {
         const fpair tb = fp_mul(K[1], W);
 #pragma unroll
-        for (int i = 0; i < 3; ++i) accB[i] = fp_add(accB[i], fp_fma(tb, d[i], fp_mul(K[0], wn[i])));
+        for (int i = 0; i < 3; ++i) accB[i] = fp_acc2(accB[i], tb, d[i], K[0], wn[i]);
     }
     // double-layer pair factors: L = r^2 K5 - K3, Z = 2 b nm - W, L nm, K5 W (nm = n0.w n)
     fpair nm = {0.0f, 0.0f}, Z = nm, Lnm = nm, K5W = nm, L = nm;
@@ -235,7 +235,7 @@ __device__ __forceinline__ void near_pair(const BatchProblemDev &P, const Geom &
             const fpair t = fp_mul(K[1], fp_dot3(d[0], d[1], d[2], wf[0], wf[1], wf[2]));
 #pragma unroll
             for (int i = 0; i < 3; ++i) {
-                const fpair s = fp_add({a[i][lane].x, a[i][lane].y}, fp_fma(t, d[i], fp_mul(K[0], wf[i])));
+                const fpair s = fp_acc2({a[i][lane].x, a[i][lane].y}, t, d[i], K[0], wf[i]);
                 a[i][lane] = make_float2(s.h, s.l);
             }
         }

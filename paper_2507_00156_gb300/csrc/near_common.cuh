@@ -378,9 +378,9 @@ __device__ __forceinline__ void kernel_factors_pair(const Geom &T, const ScanPar
         // (relative error ~1e-7 of terms below 2.1e-8 of the result)
         const int ia = cls - 1;
         const float ah = T.aph[ia], al = T.apl[ia];
-        pair_acc(kh[0], kl[0], ah, al, r1h, r1l);
-        pair_acc(kh[1], kl[1], ah, al, r3h, r3l);
-        pair_acc(kh[2], kl[2], ah, al, r5h, r5l);
+        pair_mul(ah, al, r1h, r1l, kh[0], kl[0]);  // the factors are still zero here
+        pair_mul(ah, al, r3h, r3l, kh[1], kl[1]);
+        pair_mul(ah, al, r5h, r5l, kh[2], kl[2]);
         pair_add(kh[0], kl[0], -(E1 * r1h));
         pair_add(kh[1], kl[1], -(E3 * r3h));
         pair_add(kh[2], kl[2], -(E5 * r5h));
@@ -427,9 +427,9 @@ __device__ __forceinline__ void sl_accumulate_pair(const fpair d[3], fpair K1, f
     const fpair g1 = fp_fma(nc, wn[1], wf[1]);
     const fpair g2 = fp_fma(nc, wn[2], wf[2]);
     const fpair t = fp_mul(K3, fp_dot3(d[0], d[1], d[2], g0, g1, g2));
-    accU[0] = fp_add(accU[0], fp_fma(t, d[0], fp_mul(K1, g0)));
-    accU[1] = fp_add(accU[1], fp_fma(t, d[1], fp_mul(K1, g1)));
-    accU[2] = fp_add(accU[2], fp_fma(t, d[2], fp_mul(K1, g2)));
+    accU[0] = fp_acc2(accU[0], t, d[0], K1, g0);
+    accU[1] = fp_acc2(accU[1], t, d[1], K1, g1);
+    accU[2] = fp_acc2(accU[2], t, d[2], K1, g2);
 }
 
 __device__ __forceinline__ void dl_accumulate_pair(const Geom &T, const fpair d[3], fpair r2, fpair K3, fpair K5,

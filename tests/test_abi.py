@@ -134,19 +134,22 @@ def _fp_add(a, b):
     return h, F32(w - F32(h - s))
 
 
-def _fp_dot3(a, b):
-    """fp_dot3 of the kernels: three fp_mul products, their leading floats by two two-sums, the rest
-    added in float32, renormalized."""
-    p = [_fp_mul(x, y) for x, y in zip(a, b)]
-    s = F32(p[0][0] + p[1][0])
-    v = F32(s - p[0][0])
-    e1 = F32(F32(p[0][0] - F32(s - v)) + F32(p[1][0] - v))
-    t = F32(s + p[2][0])
+def _fp_sum3(x, y, z):
+    """fp_sum3 of the kernels: the leading floats by two two-sums, the rest added in float32,
+    renormalized."""
+    s = F32(x[0] + y[0])
+    v = F32(s - x[0])
+    e1 = F32(F32(x[0] - F32(s - v)) + F32(y[0] - v))
+    t = F32(s + z[0])
     v = F32(t - s)
-    e2 = F32(F32(s - F32(t - v)) + F32(p[2][0] - v))
-    w = F32(F32(F32(p[0][1] + p[1][1]) + p[2][1]) + F32(e1 + e2))
+    e2 = F32(F32(s - F32(t - v)) + F32(z[0] - v))
+    w = F32(F32(F32(x[1] + y[1]) + z[1]) + F32(e1 + e2))
     h = F32(t + w)
     return h, F32(w - F32(h - t))
+
+
+def _fp_dot3(a, b):
+    return _fp_sum3(*[_fp_mul(x, y) for x, y in zip(a, b)])
 
 
 def _layout_eval(rec, s):
@@ -337,7 +340,7 @@ def test_float_pair_primitives_meet_their_bounds():
     truncation, |l| <= 2u |h|): 12 u^2 |a b| for a product (the neglected product of the trailing
     floats, 4 u^2, and two roundings of the cross terms, 3 u^2 and 5 u^2), 6 u^2 (|a| + |b|) for a
     sum, 24 u^2 (|a b| + |c|) for a product added to a pair, 20 u^2 (sum |a_i b_i|) for the
-    three-term dot product."""
+    three-term dot product and for an accumulator plus two products (fp_sum3)."""
     from fractions import Fraction as Fr
     rng = np.random.default_rng(17)
     u2 = Fr(1, 2 ** 48)
@@ -364,5 +367,14 @@ def test_float_pair_primitives_meet_their_bounds():
         A, B = [val(z) for z in a], [val(z) for z in b]
         exact = sum(p * q for p, q in zip(A, B))
         worst_dot = max(worst_dot, abs(val(_fp_dot3(a, b)) - exact) / (sum(abs(p * q) for p, q in zip(A, B)) * u2))
-    print("worst errors in units of u^2:", [float(w) for w in worst], float(worst_dot))
-    assert worst[0] <= 12 and worst[1] <= 6 and worst[2] <= 24 and worst_dot <= 20
+    worst_acc = Fr(0)
+    for _ in range(5000):  # fp_acc2 = fp_sum3(acc, a b, c d): <= 20 u^2 (|acc| + |a b| + |c d|)
+        xs = rng.standard_normal(5) * 10.0 ** rng.uniform(-3, 3, 5)
+        if rng.random() < 0.3:
+            xs[0] = -(xs[1] * xs[2] + xs[3] * xs[4]) * (1 + rng.standard_normal() * 1e-6)
+        acc, a, b, c, d = [_split_pair(z) for z in xs]
+        ACC, A, B, C, D = [val(z) for z in (acc, a, b, c, d)]
+        got = val(_fp_sum3(acc, _fp_mul(a, b), _fp_mul(c, d)))
+        worst_acc = max(worst_acc, abs(got - (ACC + A * B + C * D)) / ((abs(ACC) + abs(A * B) + abs(C * D)) * u2))
+    print("worst errors in units of u^2:", [float(w) for w in worst], float(worst_dot), float(worst_acc))
+    assert worst[0] <= 12 and worst[1] <= 6 and worst[2] <= 24 and worst_dot <= 20 and worst_acc <= 20

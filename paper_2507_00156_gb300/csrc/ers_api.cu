@@ -426,9 +426,11 @@ int eval_impl(ers_surface *s, const ers_params *p, const double *y, int64_t M, c
     // NEAR_CTAS_PER_SM CTAs per SM, the far one also by its shared memory) so that both kernels
     // are resident on every SM whichever starts first; k_combine then adds the far partial sums.
     const bool overlap = !tree && p->precision == ERS_PREC_MIXED && (p->options & ERS_OPT_CONCURRENT);
-    if (near_only) {
+    if (near_only) {  // no far field: its profile interval is empty
+        if (prof) cudaEventRecord(s->ev[2], st);
         e = launch_near(a, tab, g_caps[3], nsm);
         if (e != cudaSuccess) return cuda_fail(e, "near-field kernel");
+        if (prof) cudaEventRecord(s->ev[3], st);
     } else if (tree) {  // modified weights (when stale) and the walk, both in the far-field slot of the profile
         if ((rc = tree_prepare(s, tp.n0, tp.p, p->precision == ERS_PREC_MIXED, st)) != ERS_OK) return rc;
         e = launch_tree_far(a, tp);
